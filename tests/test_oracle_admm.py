@@ -1,0 +1,216 @@
+"""Pins for the oracle's ADMM pieces: D, shrinkage, preconditioner, PCG (Eq. 12), the
+iteration (Eq. 9-13), its operation counts (Table 1) and its convergence."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import admm, projector
+from synth import geometry as G
+from synth import spectra
+
+
+def _dense_D(ny, nx):
+    """D as an explicit matrix from the forward-difference definition."""
+    n = ny * nx
+    Dm = np.zeros((2 * n, n))
+    for j in range(ny):
+        for i in range(nx):
+            p = j * nx + i
+            if i < nx - 1:
+                Dm[p, p], Dm[p, p + 1] = -1.0, 1.0
+            if j < ny - 1:
+                Dm[n + p, p], Dm[n + p, p + nx] = -1.0, 1.0
+    return Dm
+
+
+def test_grad_and_adjoint_against_explicit_matrix():
+    rng = np.random.default_rng(0)
+    x = rng.normal(size=(5, 7))
+    y = rng.normal(size=(2, 5, 7))
+    Dm = _dense_D(5, 7)
+    assert np.allclose(admm.grad(x).ravel(), Dm @ x.ravel())
+    assert np.allclose(admm.grad_t(y).ravel(), Dm.T @ y.ravel())
+    assert np.allclose(admm.grad(np.full((4, 4), 3.0)), 0.0)
+
+
+def test_shrinkage_closed_form():
+    t = np.array([-3.0, -1.0, -0.5, 0.0, 0.2, 1.0, 2.5])
+    assert np.allclose(admm.shrinkage(t, 1.0), [-2.0, 0.0, 0.0, 0.0, 0.0, 0.0, 1.5])
+    assert np.allclose(admm.shrinkage(t, 0.0), t)
+    # it is the proximal map of tau*|.|: minimises tau|y| + (y - t)^2 / 2 over a fine grid
+    grid = np.linspace(-4, 4, 80001)
+    for ti in t:
+        yb = grid[np.argmin(1.0 * np.abs(grid) + 0.5 * (grid - ti) ** 2)]
+        assert admm.shrinkage(np.array([ti]), 1.0)[0] == pytest.approx(yb, abs=1e-4)
+
+
+def test_xi_metric():
+    x = np.ones(10)
+    assert admm.xi_db(1.1 * x, x) == pytest.approx(-20.0)
+    assert admm.xi_db(2.0 * x, x) == pytest.approx(0.0)
+
+
+def test_pad_size():
+    assert [admm.pad_size(n) for n in (8, 64, 96, 512, 1000)] == [16, 128, 256, 1024, 2048]
+
+
+def test_preconditioner_symmetric_positive_definite():
+    g = G.parallel_geometry(12, 20, 18, 0.1, 0.1)
+    H = admm.precond_response(g)
+    assert np.all(H > 0) and np.all(H <= 1.0)
+    # even in frequency: H(k) = H(-k), so M^-1 is a real symmetric operator
+    assert np.allclose(H, np.roll(H[::-1, ::-1], 1, axis=(0, 1)))
+    n = 144
+    M = np.stack([admm.apply_precond(H, e.reshape(12, 12)).ravel() for e in np.eye(n)], axis=1)
+    assert np.allclose(M, M.T, atol=1e-12)
+    assert np.linalg.eigvalsh(0.5 * (M + M.T)).min() > 0
+
+
+def test_preconditioner_models_the_operator_at_low_frequency():
+    # for a shift-invariant model (image centre), M^-1 A applied to a smooth centred bump is close to it
+    g = G.parallel_geometry(48, 96, 72, 0.1, 0.1)
+    H = admm.precond_response(g)
+    yy, xx = np.mgrid[0:48, 0:48] - 23.5
+    bump = np.exp(-(xx**2 + yy**2) / (2 * 4.0**2))
+    A = projector.backproject(g, projector.project(g, bump)) + admm.grad_t(admm.grad(bump)) + bump
+    ratio = np.vdot(admm.apply_precond(H, A), bump) / np.vdot(bump, bump)
+    assert 0.9 < ratio < 1.1
+    # without preconditioning the same ratio is the operator's size, orders of magnitude off
+    assert np.vdot(A, bump) / np.vdot(bump, bump) > 10
+
+
+def _eq12_dense(g):
+    Rm = projector.matrix(g)
+    Dm = _dense_D(g.ny, g.nx)
+    return Rm, Dm, Rm.T @ Rm + Dm.T @ Dm + np.eye(g.n_pixels)
+
+
+@pytest.mark.parametrize("precondition", [False, True])
+def test_pcg_converges_to_dense_cholesky_solution(precondition):
+    g = G.parallel_geometry(8, 9, 12, 0.1, 0.1, angle0_rad=0.05)
+    Rm, Dm, A = _eq12_dense(g)
+    rng = np.random.default_rng(1)
+    P = admm.Params(precondition=precondition)
+    t = spectra.SpectralTables()
+    prob = admm.Problem(g, t, np.zeros((9, 12)), np.zeros((9, 12)), np.ones((9, 12)), np.ones((9, 12)), P)
+    st = admm.state_from_image(prob, rng.normal(size=(8, 8)), rng.normal(size=(8, 8)))
+    st.a = rng.normal(size=st.a.shape)
+    st.ua = rng.normal(size=st.ua.shape)
+    st.y = rng.normal(size=st.y.shape)
+    st.uy = rng.normal(size=st.uy.shape)
+    st.z = rng.normal(size=st.z.shape)
+    st.uz = rng.normal(size=st.uz.shape)
+    admm.pcg_x_update(prob, st, 64, True, prob.H)
+    L = np.linalg.cholesky(A)
+    for b in (0, 1):
+        rhs = Rm.T @ (st.a[b] + st.ua[b]).ravel() + Dm.T @ (st.y[b] + st.uy[b]).ravel() + (st.z[b] + st.uz[b]).ravel()
+        sol = np.linalg.solve(L.T, np.linalg.solve(L, rhs))
+        assert np.allclose(st.x[b].ravel(), sol, rtol=1e-10, atol=1e-10)
+        # the carried R x equals R applied to the final x
+        assert np.allclose(st.Rx[b].ravel(), Rm @ st.x[b].ravel(), atol=1e-10)
+
+
+def test_preconditioner_speeds_up_cg():
+    g = G.parallel_geometry(32, 48, 48, 0.1, 0.1)
+    rng = np.random.default_rng(2)
+    errs = {}
+    for pc in (False, True):
+        P = admm.Params(precondition=pc)
+        t = spectra.SpectralTables()
+        prob = admm.Problem(g, t, np.zeros((48, 48)), np.zeros((48, 48)), np.ones((48, 48)), np.ones((48, 48)), P)
+        st = admm.state_from_image(prob, np.zeros((32, 32)), np.zeros((32, 32)))
+        st.a = np.stack([projector.project(g, rng.uniform(size=(32, 32)))] * 2)
+        ref = st.copy()
+        admm.pcg_x_update(prob, ref, 300, True, prob.H)
+        admm.pcg_x_update(prob, st, 8, True, prob.H)
+        errs[pc] = np.linalg.norm(st.x - ref.x) / np.linalg.norm(ref.x)
+    assert errs[True] < 0.5 * errs[False]
+
+
+@pytest.mark.parametrize("m,n", [(1, 1), (2, 3), (3, 1)])
+def test_table1_operation_counts(m, n):
+    # UDM(m)-PCG(n): R 2n, R^T 2(n+1), f 4m per ADMM iteration (both bases)
+    g = G.parallel_geometry(16, 12, 24, 0.1, 0.1)
+    t = spectra.SpectralTables()
+    rng = np.random.default_rng(3)
+    m_h = rng.uniform(0.1, 1.0, (12, 24))
+    P = admm.Params(m_udm=m, n_pcg=n)
+    prob = admm.Problem(g, t, m_h, m_h * 1.1, np.full((12, 24), 1e4), np.full((12, 24), 1e4), P)
+    st = admm.state_from_image(prob, np.full((16, 16), 0.1), np.full((16, 16), 1e-3))
+    before = (prob.count.R, prob.count.RT, prob.count.f)
+    for _ in range(3):
+        st = admm.admm_iteration(prob, st)
+    assert prob.count.R - before[0] == 3 * 2 * n
+    assert prob.count.RT - before[1] == 3 * 2 * (n + 1)
+    assert prob.count.f - before[2] == 3 * 4 * m
+
+
+class _Mono:
+    def __init__(self):
+        e = np.array([50.0, 90.0])
+        self.energy_kev = e
+        self.s_high = np.array([0.0, 1.0])
+        self.s_low = np.array([1.0, 0.0])
+        self.f_kn = spectra.klein_nishina(e)
+        self.f_p = spectra.photoelectric(e, 60.0)
+
+
+def _mono_problem(lam=(0.0, 0.0), rho0=(0.1, 0.1)):
+    g = G.parallel_geometry(16, 30, 24, 1.0, 1.0)
+    s = _Mono()
+    yy, xx = np.mgrid[0:16, 0:16] - 7.5
+    xc = 0.2 + 0.1 * ((xx / 6) ** 2 + (yy / 5) ** 2 < 1)
+    xp = 0.05 + 0.05 * ((xx + 2) ** 2 + (yy - 1) ** 2 < 9)
+    Rc, Rp = projector.project(g, xc), projector.project(g, xp)
+    m_h = s.f_kn[1] * Rc + s.f_p[1] * Rp
+    m_l = s.f_kn[0] * Rc + s.f_p[0] * Rp
+    P = admm.Params(lam=lam, rho0=rho0, m_udm=2, n_pcg=4)
+    return admm.Problem(g, s, m_h, m_l, np.ones_like(m_h), np.ones_like(m_h), P), xc, xp
+
+
+def test_admm_truth_is_a_fixed_point_noise_free_monochromatic():
+    # exact data, lambda = 0: starting at the phantom with zero duals, an iteration changes nothing
+    prob, xc, xp = _mono_problem()
+    st0 = admm.state_from_image(prob, xc, xp)
+    st = admm.admm_iteration(prob, st0)
+    assert np.allclose(st.x, st0.x, atol=1e-12)
+    assert np.allclose(st.a, st0.a, atol=1e-12)
+    assert np.allclose(st.ua, 0.0, atol=1e-12) and np.allclose(st.uy, 0.0, atol=1e-12)
+    assert np.allclose(st.uz, 0.0, atol=1e-12)
+
+
+def test_admm_converges_to_exact_solution_noise_free_monochromatic():
+    # noise-free, linear f, lambda = 0, positive truth: the MAP point is the phantom itself;
+    # ADMM drives x towards it and both residuals towards zero
+    prob, xc, xp = _mono_problem()
+    st = admm.state_from_image(prob, np.full((16, 16), 0.1), np.full((16, 16), 0.05))
+    err0 = (np.linalg.norm(st.x[0] - xc) / np.linalg.norm(xc), np.linalg.norm(st.x[1] - xp) / np.linalg.norm(xp))
+    first = None
+    for it in range(300):
+        st = admm.admm_iteration(prob, st)
+        if first is None:
+            first = (st.r_pri.copy(), st.r_dual.copy())
+    err_c = np.linalg.norm(st.x[0] - xc) / np.linalg.norm(xc)
+    err_p = np.linalg.norm(st.x[1] - xp) / np.linalg.norm(xp)
+    assert err_c < 1e-2 * err0[0] * 10 and err_c < 5e-3 and err_p < 1e-2
+    assert np.all(st.r_pri < 1e-2 * first[0]) and np.all(st.r_dual < 1e-1 * first[1])
+
+
+def test_small_case_objective_and_residuals_trend():
+    # the small parallel-beam workload: MAP objective (Eq. 4) falls well below its start and
+    # the primal residual of both bases shrinks over 20 iterations
+    from synth.workloads import small_parallel_case
+    c = small_parallel_case()
+    prob = admm.Problem(c["geom"], c["spectra"], c["m_h"], c["m_l"], c["w_h"], c["w_l"], admm.Params())
+    xc0, xp0 = admm.initial_image(prob)
+    st = admm.state_from_image(prob, xc0, xp0)
+    obj0 = admm.map_objective(prob, st.x)
+    st = admm.admm_iteration(prob, st)
+    r0 = st.r_pri.copy()
+    for _ in range(19):
+        st = admm.admm_iteration(prob, st)
+    assert admm.map_objective(prob, st.x) < 0.2 * obj0
+    assert np.all(st.r_pri < r0)
+    # the Compton estimate improves on the initial image over the first iterations
+    assert admm.xi_db(st.x[0], c["truth_c"]) < admm.xi_db(xc0, c["truth_c"]) + 3.0
