@@ -1,0 +1,346 @@
+"""Benchmark: slices/s to a fixed photoelectric-image error for UDM1-PCG1 ADMM
+(Sec. 3.3) on the 512x512, 720-view, 1024-bin fan-beam baggage slice.
+
+One step = reconstruct the batch to the workload's iteration count: the
+initial estimate plus 100 ADMM iterations, everything in libdect kernels, with
+the measurements already resident in HBM. The fixed PE error is the FP64
+oracle's xi_p (Eq. 14) after those 100 iterations on the same seeded slice
+(tests/golden/baggage_fan_512_xi.json); the line reports whether the GPU's
+xi_p lands within 0.5 dB of it.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--batch B] [--impl dect|reference]
+
+Prints one JSON line on rank 0. Multi-GPU: one process per GPU (torchrun),
+each rank reconstructs its own slices (weak scaling, no collective on the
+data path); timing is max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "slices/s to fixed PE error (UDM1-PCG1, 100 ADMM iterations), 512^2 x 720 views fan beam"
+UNIT = "slices/s"
+ITERS = 100
+GOLDEN = os.path.join(ROOT, "tests", "golden", "baggage_fan_512_xi.json")
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """Samples SM clocks and throttle reasons with nvidia-smi while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        rows = []
+        try:
+            for line in open(self.path):
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        except Exception:
+            pass
+        finally:
+            try:
+                os.unlink(self.path)
+            except Exception:
+                pass
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        smax = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _golden():
+    try:
+        with open(GOLDEN) as f:
+            return json.load(f)
+    except Exception:
+        return None
+
+
+# ------------------------------------------------------------------------------------------------
+# CPU baseline / reference arm: the FP64 oracle as it stands, on a bounded sample of the workload
+
+def _oracle_sample(n_iters: int, case=None):
+    """Times the oracle's initial image and n_iters ADMM iterations on one slice."""
+    from oracle import _clib, admm
+    from synth.workloads import BAGGAGE_KAPPA, baggage_fan_case
+
+    c = case if case is not None else baggage_fan_case()
+    P = admm.Params(kappa=BAGGAGE_KAPPA)
+    t0 = time.perf_counter()
+    prob = admm.Problem(c["geom"], c["spectra"], c["m_h"], c["m_l"], c["w_h"], c["w_l"], P)
+    x0 = admm.initial_image(prob)
+    st = admm.state_from_image(prob, *x0)
+    t_init = time.perf_counter() - t0
+    times = []
+    for _ in range(n_iters):
+        t1 = time.perf_counter()
+        st = admm.admm_iteration(prob, st)
+        times.append(time.perf_counter() - t1)
+    return t_init, times, _clib.num_threads(), (prob, st)
+
+
+def cpu_baseline():
+    t_init, times, cores, _ = _oracle_sample(2)
+    per_slice = t_init + ITERS * float(np.mean(times))
+    return {"value": 1.0 / per_slice, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"FP64 oracle on one 512^2 slice: set-up + initial image ({t_init:.1f} s) and 2 of the "
+                      f"{ITERS} ADMM iterations ({np.mean(times):.2f} s each), iterations scaled x{ITERS // 2}"}
+
+
+def run_reference(args):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return 0
+    from synth.workloads import baggage_fan_case
+
+    case = baggage_fan_case()
+    t_init, _, cores, (prob, st) = _oracle_sample(0, case)
+    from oracle import admm
+
+    for _ in range(args.warmup):
+        st = admm.admm_iteration(prob, st)
+    times = []
+    for _ in range(args.steps):
+        t1 = time.perf_counter()
+        st = admm.admm_iteration(prob, st)
+        times.append(time.perf_counter() - t1)
+    per_slice = t_init + ITERS * float(np.mean(times))
+    value = 1.0 / per_slice
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * float(np.mean(times)), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "fan beam 512x512, 720 views x 1024 bins, 40 objects, I0 2e5, UDM1-PCG1 x 100",
+                   "batch": 1, "step": "one ADMM iteration of the FP64 oracle (a bounded sample)"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"initial image ({t_init:.1f} s) + {args.steps} timed ADMM iterations, "
+                                   f"scaled to {ITERS} iterations"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------------------------------------
+
+def run_dect(args):
+    import torch
+
+    ws, rank, local = _dist()
+    if ws > 1:
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.device("cuda", torch.cuda.current_device())
+
+    import __graft_entry__
+
+    __graft_entry__.build()
+    from paper_1905_00934_gb300 import Geometry, Solver, Spectra, dect
+    from synth.workloads import BAGGAGE_KAPPA, baggage_fan_case
+
+    B = args.batch
+    cases = [baggage_fan_case(slice_index=rank * B + b) for b in range(B)]
+    geo = [Geometry(c["geom"]) for c in cases]
+    spec = Spectra.from_tables(cases[0]["spectra"])
+    sol = Solver(geo, spec, kappa=BAGGAGE_KAPPA)
+    f32 = lambda a: torch.tensor(np.ascontiguousarray(a), dtype=torch.float32, device=dev)
+    dev_data = [[f32(c[k]) for k in ("m_h", "m_l", "w_h", "w_l")] for c in cases]
+    for b, c in enumerate(cases):
+        sol.set_data(b, *dev_data[b])
+        sol.set_truth(b, f32(np.stack([c["truth_c"], c["truth_p"]])))
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # 512 MB > 129 MB L2
+
+    def barrier():
+        if ws > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        sol.reconstruct(ITERS)
+    barrier()
+
+    launches0 = sol.stats(0)["count_launches"]
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        barrier()
+        for k in range(args.steps):
+            flush.fill_(float(k))  # evict L2 between steps (outside the events)
+            ev[k][0].record(stream)
+            sol.reconstruct(ITERS)
+            ev[k][1].record(stream)
+        barrier()
+    clocks = clk.summary()
+    launches = sol.stats(0)["count_launches"] - launches0
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_ms = float(sum(step_ms))
+    if ws > 1:
+        t = torch.tensor([total_ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = ws * B * args.steps / (total_ms / 1e3)
+
+    # quality gate: xi_p of slice 0 after the workload's iterations vs the oracle's
+    st0 = sol.stats(0)
+    gold = _golden()
+    gate = {"xi_p_db": st0["xi_db"][1], "xi_c_db": st0["xi_db"][0]}
+    if gold is not None and rank == 0:
+        target = gold["xi_p"][ITERS]
+        gate.update({"oracle_xi_p_db": target, "oracle_xi_c_db": gold["xi_c"][ITERS],
+                     "within_0p5_db": bool(abs(st0["xi_db"][1] - target) <= 0.5)})
+
+    # end to end through the C ABI: pinned host measurements in, image out, every step
+    host_in = [[t.cpu().pin_memory() for t in d] for d in dev_data]
+    host_out = [torch.empty((2, c["geom"].ny, c["geom"].nx), dtype=torch.float32).pin_memory() for c in cases]
+    h2d = sum(t.numel() * 4 for d in host_in for t in d)
+    d2h = sum(t.numel() * 4 for t in host_out)
+    e2e_steps = max(1, min(args.steps, 3))
+    barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(e2e_steps):
+        for b in range(B):
+            sol.set_data(b, *host_in[b])
+        sol.reconstruct(ITERS)
+        for b in range(B):
+            dect.admm_get(sol.handle, b, dect.X, host_out[b])
+    e1.record(stream)
+    barrier()
+    e2e_ms = e0.elapsed_time(e1)
+    if ws > 1:
+        t = torch.tensor([e2e_ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+    e2e_value = ws * B * e2e_steps / (e2e_ms / 1e3)
+
+    # live per-kernel-group timing of the same iteration (CUDA events around each group)
+    prof = sol.profile(10)
+    top = max(prof, key=lambda p: prof[p][0])
+    g = cases[0]["geom"]
+    M, Np = g.n_views * g.n_bins, g.nx * g.ny
+    # algorithmic bytes per launch of each group (float32, both bases, per slice x B)
+    alg_bytes = {
+        "backproject": B * (8 * M + 8 * Np + (56 + 16) / 2 * Np),   # sinogram in, image out, epilogue images
+        "project": B * (16 * (g.nx * (g.ny + 3) + g.ny * (g.nx + 3)) / 2 + 8 * M),  # one texture read, sinogram out
+        "udm": B * (16 + 8 + 8 + 8 + 4 + 8 + 8 + 4 + 1) * M,
+        "precond": B * (8 * Np + 4 * 8 * Np + 2 * 8 * (2 * g.nx) * (2 * g.ny) + 8 * Np),
+        "texture": B * (8 * Np + 16 * (g.nx * (g.ny + 3) + g.ny * (g.nx + 3))),
+        "update": None,
+        "reduce": None,
+    }
+    ms_total, n_launch = prof[top]
+    avg_ms = ms_total / max(n_launch, 1)
+    peak, peak_kind = _peaks()
+    roof = None
+    if alg_bytes.get(top):
+        achieved = alg_bytes[top] / (avg_ms / 1e3) / 1e9
+        roof = {"kernel": top, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": None, "peak_kind": peak_kind,
+                "avg_launch_ms": avg_ms, "algorithmic_bytes_per_launch": alg_bytes[top]}
+    phases = {p: {"ms_per_iter": prof[p][0] / 10, "launches_per_iter": prof[p][1] / 10} for p in prof}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "fan beam 512x512, 720 views x 1024 bins, 40 objects, I0 2e5, "
+                                   "UDM1-PCG1 x 100 iterations + initial image",
+                       "batch_per_gpu": B, "l2": "flushed between steps (512 MB write)",
+                       "pe_gate": gate, "phases": phases},
+            "clocks": clocks,
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                    "steps": e2e_steps},
+            "gpu_launches": int(launches),
+            "roofline": roof,
+        }
+        if ws == 1 and not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline()
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--batch", type=int, default=1)
+    ap.add_argument("--impl", default="dect", choices=["dect", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_dect(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,249 @@
+/*
+ * dect.h - C ABI of the GB300 (sm_103a) library for one ADMM iteration of the
+ * splitting-based statistical dual-energy CT reconstruction UDM(m)-PCG(n)
+ * (Li, Manerikar, Prakash, Kak: "A splitting-based iterative algorithm for
+ * GPU-accelerated statistical dual-energy X-ray CT reconstruction").
+ *
+ * Conventions shared by every call
+ *  - Images are row-major [ny][nx] float32; pixel (row j, column i) is centred
+ *    at ((i-(nx-1)/2)*pixel_cm, (j-(ny-1)/2)*pixel_cm).
+ *  - Sinograms are [n_views][n_bins] float32, bins fastest.
+ *  - Multi-channel buffers are planar: channel 0 (Compton, x_c) first, then
+ *    channel 1 (photoelectric, x_p), each a full image or sinogram.
+ *  - "dev" pointers are device memory owned by the caller; the library never
+ *    frees or keeps them past the call (asynchronous calls read/write them in
+ *    stream order on the given stream). Handles own only their internal
+ *    workspaces and free them in their destroy call.
+ *  - stream is a cudaStream_t passed as void*; NULL means the legacy default
+ *    stream. Calls on one handle must be ordered (same stream, or synchronised
+ *    by the caller): a handle's workspace is shared by its calls.
+ *  - Every call returns a dect_status. Arguments are validated before anything
+ *    is launched; on failure nothing is launched and dect_last_error() (per
+ *    host thread) describes the problem. Errors of earlier asynchronous work
+ *    surface as DECT_ECUDA from a later call or from dect_sync().
+ *  - No call traps or asserts on the device. Per-ray numerical failures of the
+ *    decomposition are reported in a status array, not as call errors.
+ */
+#ifndef DECT_H
+#define DECT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    DECT_OK = 0,
+    DECT_EINVAL = 1,        /* bad argument (null pointer, bad size, bad enum) */
+    DECT_ENOMEM = 2,        /* device or host allocation failed */
+    DECT_ECUDA = 3,         /* a CUDA runtime error, from this or earlier work */
+    DECT_EUNSUPPORTED = 4,  /* valid but not supported (e.g. a dtype) */
+    DECT_ETIMEOUT = 5,      /* reserved: a bounded device wait ran out */
+    DECT_ENOTCONV = 6       /* reserved: a solver did not converge */
+} dect_status;
+
+typedef enum { DECT_PARALLEL = 0, DECT_FAN_FLAT = 1 } dect_geom_kind;
+
+typedef enum { DECT_F32 = 0 } dect_dtype;
+
+/* Per-ray decomposition status codes (uint8 array of dect_decompose_rays). */
+enum { DECT_RAY_ACCEPTED = 0, DECT_RAY_REJECTED = 1, DECT_RAY_NONFINITE = 2 };
+
+/* Library version string, e.g. "dect 0.1 sm_103a". */
+const char* dect_version(void);
+
+/* Description of the last error on the calling host thread ("" if none). */
+const char* dect_last_error(void);
+
+/* Blocks until all work on `stream` is done; returns DECT_ECUDA on an asynchronous error. */
+dect_status dect_sync(void* stream);
+
+/* ------------------------------------------------------------------------ */
+/* Geometry: the projection matrix R of Eq. 2-3 (Sec. 1, Sec. 3.1).
+ *
+ * Parallel beam (the paper's experiments, Sec. 4): view v has angle
+ * theta_v = angle0_rad + v*angle_span_rad/n_views; bin k sits at
+ * u_k = (k-(n_bins-1)/2)*bin_pitch_cm + bin_offset_cm; its ray passes through
+ * u_k*(cos, sin)(theta_v) with direction (-sin, cos)(theta_v).
+ * Fan beam, flat detector: source at sod_cm*(cos, sin)(theta_v), detector line
+ * through -(sdd_cm-sod_cm)*(cos, sin)(theta_v) along (-sin, cos)(theta_v); the
+ * ray of bin k runs from the source to u_k on that line.
+ * R is Joseph's interpolating ray-driven projector: a ray with |d_x| >= |d_y|
+ * is sampled once per image column with linear interpolation between the two
+ * nearest rows (zero outside the image), weighted by pixel_cm/|d_x|; otherwise
+ * rows and columns swap roles.
+ * Limits: 1 <= nx, ny <= 4096; 1 <= n_views <= 16384; 1 <= n_bins <= 16384;
+ * pixel_cm, bin_pitch_cm > 0; fan beam needs sdd_cm > sod_cm > 0 and the
+ * image's circumscribed circle strictly inside the source circle.
+ */
+typedef struct {
+    int32_t kind;           /* dect_geom_kind */
+    int32_t nx, ny;         /* image columns, rows */
+    int32_t n_views, n_bins;
+    double pixel_cm;
+    double angle0_rad, angle_span_rad;
+    double bin_pitch_cm, bin_offset_cm;
+    double sod_cm, sdd_cm;  /* fan beam only */
+} dect_geom_desc;
+
+typedef struct dect_geom dect_geom;
+
+/* Creates a geometry on the current CUDA device (builds the per-ray table
+ * there). *out receives the handle; the caller destroys it. */
+dect_status dect_geometry_create(const dect_geom_desc* desc, dect_geom** out);
+void dect_geometry_destroy(dect_geom* g);
+
+/* ------------------------------------------------------------------------ */
+/* Spectral tables of Eq. 1-3: f_{h/l}(a) = C_{h/l} - ln sum_E S_{h/l}(E)
+ * exp(-f_KN(E) a_c - f_p(E) a_p), with the integral over E as a sum over the
+ * n_energies bins. All four host arrays are FP64 of length n_energies
+ * (1..512), copied during the call. S_h and S_l must be >= 0 with positive
+ * sums; the library normalises them to unit sum, which makes C_{h/l} = 0. */
+typedef struct dect_spectra dect_spectra;
+dect_status dect_spectra_create(int32_t n_energies, const double* S_h, const double* S_l,
+                                const double* f_kn, const double* f_p, dect_spectra** out);
+void dect_spectra_destroy(dect_spectra* s);
+
+/* ------------------------------------------------------------------------ */
+/* Forward projection (Eq. 2-3's R): sino_dev[c] = R x_dev[c] for c < n_channels.
+ * x_dev: planar [n_channels][ny][nx] float32; sino_dev: planar
+ * [n_channels][n_views][n_bins] float32, overwritten. n_channels is 1 or 2.
+ * Uses the geometry's workspace (allocated on first use). */
+dect_status dect_project(dect_geom* g, int32_t n_channels, int32_t dtype, const void* x_dev,
+                         void* sino_dev, void* stream);
+
+/* Backprojection, the exact adjoint R^T of dect_project (Table 1's R^T):
+ * x_dev[c] = R^T sino_dev[c]; same layouts; x_dev is overwritten. It gathers
+ * per pixel (no atomics), so the result is deterministic; it evaluates the
+ * same per-ray weights as dect_project, so <R x, y> = <x, R^T y> up to float32
+ * rounding. */
+dect_status dect_backproject(dect_geom* g, int32_t n_channels, int32_t dtype, const void* sino_dev,
+                             void* x_dev, void* stream);
+
+/* ------------------------------------------------------------------------ */
+/* Per-ray decomposition, Eq. 13 (UDM): for each of the n_rays rays
+ *   min over (a_c, a_p) of 1/2 sum_{k=h,l} w_k (f_k(a) - m_k)^2
+ *                          + rho_c/2 (a_c - v_c)^2 + rho_p/2 (a_p - v_p)^2
+ * by `iters` Levenberg-Marquardt iterations from the warm start in a_c, a_p:
+ * Gauss-Newton system (J^T W J + diag rho), Marquardt damping mu*diag, a step
+ * is kept only if it lowers the cost (mu /= 10) else mu *= 10, mu clamped to
+ * [1e-10, 1e10]; 4 evaluations of f per iteration (Table 1).
+ * All arrays are device float32 of length n_rays except status (uint8,
+ * nullable). a_c, a_p, mu are read and overwritten. rho = 0 gives the plain
+ * maximum-likelihood decomposition. Sums over energy in float32, log of the
+ * spectral sums and the 2x2 solve in float64. */
+dect_status dect_decompose_rays(const dect_spectra* s, int64_t n_rays, const float* m_h, const float* m_l,
+                                const float* w_h, const float* w_l, const float* v_c, const float* v_p,
+                                double rho_c, double rho_p, int32_t iters, float* a_c, float* a_p,
+                                float* mu, uint8_t* status, void* stream);
+
+/* ------------------------------------------------------------------------ */
+/* ADMM solver state for B >= 1 independent slices (Sec. 3.2-3.3).
+ * One iteration (UDM(m)-PCG(n)), per slice and for both bases beta in {c, p}:
+ *  1. Eq. 12: n preconditioned CG steps on (R^T R + D^T D + I) x_beta
+ *     = R^T(a+u^a) + D^T(y+u^y) + (z+u^z), warm-started from x_beta, with
+ *     R x carried (R x += alpha R p): 2n R and 2(n+1) R^T (Table 1).
+ *     D: forward differences along x and y, zero at the last column/row.
+ *     Preconditioner: the circulant model 1/(F[R^T R delta] + |F[D]|^2 + 1)
+ *     of the operator on a zero-padded grid ("high-passing filter", Sec. 3.3).
+ *  2. Eq. 13: m LM iterations per ray with v = R x - u^a (as dect_decompose_rays).
+ *  3. Eq. 9-10: y = shrinkage(D x - u^y, lambda/rho), z = max(0, x - u^z).
+ *  4. Eq. 11 with the a-block: u^a += a - R x, u^y += y - D x, u^z += z - x.
+ *  5. rho by residual balancing (Sec. 3.2): r_pri = ||[a;y;z] - [R;D;I]x||,
+ *     r_dual = rho ||[a;y;z] - [a;y;z]_prev||; if r_pri > mu_b r_dual then
+ *     rho *= tau, u /= tau; if r_dual > mu_b r_pri then rho /= tau, u *= tau.
+ * All scalars (CG alpha/beta, rho, residuals) stay on the device. */
+typedef struct {
+    double lambda_c, lambda_p;   /* TV weights (paper: 1e-5) */
+    double rho0_c, rho0_p;       /* initial penalties (paper: 1e-3) */
+    int32_t m_udm, n_pcg;        /* UDM(m)-PCG(n), >= 1 */
+    double rho_mu, rho_tau;      /* residual balancing (10, 2); tau = 1 disables */
+    double lm_mu0;               /* initial LM damping per ray (1e-3) */
+    double kappa;                /* initial PE image = kappa * Compton image */
+    int32_t init_udm_iters;      /* initialisation: LM iterations (10) */
+    int32_t init_pcg_iters;      /* initialisation: CG iterations (10) */
+    int32_t precondition;        /* 1: circulant preconditioner, 0: plain CG */
+    int32_t use_graph;           /* 1: capture one iteration as a CUDA graph */
+} dect_params;
+
+/* Fills *p with the paper's values and the defaults above. */
+void dect_params_default(dect_params* p);
+
+typedef struct dect_admm dect_admm;
+
+/* Creates the solver for B slices; geoms[b] describes slice b (the handles must
+ * outlive the solver). Allocates all state on the current device and computes
+ * each slice's preconditioner. */
+dect_status dect_admm_create(dect_geom* const* geoms, int32_t n_slices, const dect_spectra* s,
+                             const dect_params* p, dect_admm** out);
+void dect_admm_destroy(dect_admm* a);
+
+/* Measurements of slice b: m_h, m_l (log projections, Eq. 2) and w_h, w_l (the
+ * photon counts on the diagonal of Sigma, Eq. 4), each [n_views][n_bins]
+ * float32, in host or device memory (copied in stream order). If x0 is
+ * non-NULL it is the starting image, planar [2][ny][nx] float32 (host or
+ * device); otherwise the next dect_reconstruct computes one (see there). */
+dect_status dect_admm_set_data(dect_admm* a, int32_t slice, const float* m_h, const float* m_l,
+                               const float* w_h, const float* w_l, const float* x0, void* stream);
+
+/* Ground truth [2][ny][nx] float32 (host or device) for the quality metric
+ * xi (Eq. 14) of slice b; NULL clears it. */
+dect_status dect_admm_set_truth(dect_admm* a, int32_t slice, const float* truth, void* stream);
+
+/* Runs `iters` ADMM iterations on all slices. */
+dect_status dect_admm_step(dect_admm* a, int32_t iters, void* stream);
+
+/* Starts every slice that has no starting image from the initial estimate:
+ * a = Eq. 13 with rho = (0, rho0_p), v = 0, from a_c = m_l / sum_E S_l f_KN,
+ * a_p = 0 (init_udm_iters LM iterations); x_c = max(0, init_pcg_iters CG
+ * iterations on (R^T R + I) x = R^T a_c from 0); x_p = kappa x_c. Then every
+ * slice is reset to x, R x, a = R x, y = D x, z = x, zero duals, rho = rho0,
+ * mu = lm_mu0; then runs `iters` iterations. */
+dect_status dect_reconstruct(dect_admm* a, int32_t iters, void* stream);
+
+/* Copies a state array of slice b to dst (host or device), planar float32:
+ * which = 0: x [2][ny][nx]; 1: R x [2][V][Nb]; 2: a [2][V][Nb]; 3: u^a;
+ * 4: y [2][2][ny][nx] (channel, then component along x, along y); 5: u^y;
+ * 6: z [2][ny][nx]; 7: u^z; 8: LM mu [V][Nb]; 9: the preconditioner
+ * response H [Py][Px] (float32). dst_bytes is checked against the size. */
+dect_status dect_admm_get(const dect_admm* a, int32_t slice, int32_t which, void* dst, size_t dst_bytes,
+                          void* stream);
+
+/* Per-slice scalars after the last completed iteration (synchronises `stream`). */
+typedef struct {
+    int32_t iteration;
+    double rho[2];
+    double r_pri[2], r_dual[2];
+    double xi_db[2];             /* Eq. 14 against the truth (NaN without one) */
+    int64_t count_R, count_RT;   /* projector applications per basis (Table 1) */
+    int64_t count_f;             /* forward-model evaluations per ray */
+    int64_t count_launches;      /* kernels launched by this solver so far (all slices) */
+} dect_stats;
+dect_status dect_admm_stats(dect_admm* a, int32_t slice, dect_stats* out, void* stream);
+
+/* Kernel groups timed by dect_admm_profile. */
+enum {
+    DECT_PHASE_TEXTURE = 0,      /* pair textures of the image the projector reads */
+    DECT_PHASE_PROJECT = 1,      /* R */
+    DECT_PHASE_BACKPROJECT = 2,  /* R^T with the CG epilogues */
+    DECT_PHASE_PRECOND = 3,      /* FFT preconditioner (3 kernels) */
+    DECT_PHASE_UDM = 4,          /* Eq. 13 with the a-block dual update */
+    DECT_PHASE_UPDATE = 5,       /* element-wise CG, Eq. 9-11 and dual rescaling kernels */
+    DECT_PHASE_REDUCE = 6,       /* per-slice scalar reductions (CG alpha/beta, rho) */
+    DECT_NUM_PHASES = 7
+};
+
+/* Runs `iters` iterations exactly like dect_admm_step (same kernels, replayed as a
+ * CUDA graph) but with a CUDA event before and after every kernel group, and
+ * synchronises `stream` after each iteration to read them: adds each group's
+ * device time (ms) to ms[phase] and its kernel launches to launches[phase]
+ * (both arrays of DECT_NUM_PHASES, caller-owned host memory, not cleared). */
+dect_status dect_admm_profile(dect_admm* a, int32_t iters, void* stream, double* ms, int64_t* launches);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DECT_H */

@@ -1,0 +1,522 @@
+// Element-wise and reduction kernels of one ADMM iteration (Sec. 3.2-3.3):
+// the CG vector updates and scalars of Eq. 12, the TV shrinkage and
+// non-negativity updates (Eq. 9-10), the dual update (Eq. 11) with the
+// residual sums, residual-balancing rho, and the state (re)initialisation.
+//
+// Reductions are deterministic: each block writes its partial sums (float64)
+// to a slot indexed by its block number, and one block per slice adds its
+// slots in a fixed order. All scalars stay on the device.
+#include <cuda_runtime.h>
+#include <math.h>
+
+#include "admm_kernels.cuh"
+
+namespace dect {
+
+// ---- block reduction helpers ------------------------------------------------------------------
+
+template <int N>
+__device__ __forceinline__ void block_partials(double (&v)[N], double* __restrict__ out) {
+    __shared__ double red[N][32];
+    for (int q = 0; q < N; ++q)
+        for (int o = 16; o > 0; o >>= 1) v[q] += __shfl_down_sync(0xffffffffu, v[q], o);
+    const int w = threadIdx.x / 32;
+    if ((threadIdx.x & 31) == 0)
+        for (int q = 0; q < N; ++q) red[q][w] = v[q];
+    __syncthreads();
+    if (threadIdx.x < N) {
+        double t = 0.0;
+        for (int k = 0; k < (int)blockDim.x / 32; ++k) t += red[threadIdx.x][k];
+        out[N * (size_t)blockIdx.x + threadIdx.x] = t;
+    }
+}
+
+// Sum of partial slots [prefix[s], prefix[s+1]) of width N, by one block (fixed order).
+template <int N>
+__device__ void slice_sum(const double* __restrict__ part, const int* __restrict__ prefix, int s, double (&out)[N]) {
+    __shared__ double red[N][256];
+    const int b0 = prefix[s], b1 = prefix[s + 1];
+    double acc[N];
+    for (int q = 0; q < N; ++q) acc[q] = 0.0;
+    for (int b = b0 + threadIdx.x; b < b1; b += blockDim.x)
+        for (int q = 0; q < N; ++q) acc[q] += part[N * (size_t)b + q];
+    for (int q = 0; q < N; ++q) red[q][threadIdx.x] = acc[q];
+    __syncthreads();
+    for (int h = blockDim.x / 2; h > 0; h >>= 1) {
+        if ((int)threadIdx.x < h)
+            for (int q = 0; q < N; ++q) red[q][threadIdx.x] += red[q][threadIdx.x + h];
+        __syncthreads();
+    }
+    for (int q = 0; q < N; ++q) out[q] = red[q][0];
+    __syncthreads();
+}
+
+// ---- Eq. 12 pieces ------------------------------------------------------------------------------
+
+// b = a + u^a - R x (the sinogram part of the CG residual)
+__global__ void __launch_bounds__(256) k_sino_resid(const SliceDesc* __restrict__ dsl, BlockMap map,
+                                                    const float2* __restrict__ a, const float2* __restrict__ ua,
+                                                    const float2* __restrict__ Rx, float2* __restrict__ b) {
+    int local;
+    const int s = slice_of(map, blockIdx.x, local);
+    const SliceDesc& d = dsl[s];
+    const int64_t r = (int64_t)local * 256 + threadIdx.x;
+    if (r >= (int64_t)d.g.nv * d.g.nb) return;
+    const int64_t e = d.sino_off + r;
+    const float2 av = __ldg(a + e), uv = __ldg(ua + e), rv = __ldg(Rx + e);
+    b[e] = make_float2(av.x + uv.x - rv.x, av.y + uv.y - rv.y);
+}
+
+// rs = <r, M^-1 r> from the preconditioner's row partials; after the first CG step also beta
+__global__ void __launch_bounds__(256) k_rs_reduce(const double* __restrict__ part, const int* __restrict__ rows_prefix,
+                                                   SliceScalars* __restrict__ sc, int first) {
+    const int s = blockIdx.x;
+    double v[2];
+    slice_sum<2>(part, rows_prefix, s, v);
+    if (threadIdx.x == 0) {
+        for (int c = 0; c < 2; ++c) {
+            if (!first) sc[s].beta[c] = sc[s].rs[c] > 0.0 ? v[c] / sc[s].rs[c] : 0.0;
+            sc[s].rs[c] = v[c];
+        }
+    }
+}
+
+// alpha = rs / <p, A p>
+__global__ void __launch_bounds__(256) k_alpha(const double* __restrict__ part, const int* __restrict__ bp_prefix,
+                                               SliceScalars* __restrict__ sc) {
+    const int s = blockIdx.x;
+    double v[2];
+    slice_sum<2>(part, bp_prefix, s, v);
+    if (threadIdx.x == 0) {
+        for (int c = 0; c < 2; ++c) {
+            sc[s].pAp[c] = v[c];
+            sc[s].alpha[c] = v[c] > 0.0 ? sc[s].rs[c] / v[c] : 0.0;
+        }
+    }
+}
+
+// x += alpha p, r -= alpha A p (unless last) over the image blocks; R x += alpha q over the ray blocks
+__global__ void __launch_bounds__(256) k_cg_update(const SliceDesc* __restrict__ dsl, BlockMap pix, int nblk_pix,
+                                                   BlockMap rays, const SliceScalars* __restrict__ sc,
+                                                   float2* __restrict__ x, const float2* __restrict__ p,
+                                                   float2* __restrict__ r, const float2* __restrict__ Ap,
+                                                   float2* __restrict__ Rx, const float2* __restrict__ q, int last) {
+    int local;
+    if ((int)blockIdx.x < nblk_pix) {
+        const int s = slice_of(pix, blockIdx.x, local);
+        const SliceDesc& d = dsl[s];
+        const int64_t k = (int64_t)local * 256 + threadIdx.x;
+        if (k >= (int64_t)d.g.nx * d.g.ny) return;
+        const float ac = (float)sc[s].alpha[0], ap = (float)sc[s].alpha[1];
+        const int64_t e = d.img_off + k;
+        const float2 pv = __ldg(p + e);
+        float2 xv = x[e];
+        xv.x = fmaf(ac, pv.x, xv.x);
+        xv.y = fmaf(ap, pv.y, xv.y);
+        x[e] = xv;
+        if (!last) {
+            const float2 av = __ldg(Ap + e);
+            float2 rv = r[e];
+            rv.x = fmaf(-ac, av.x, rv.x);
+            rv.y = fmaf(-ap, av.y, rv.y);
+            r[e] = rv;
+        }
+    } else {
+        const int s = slice_of(rays, blockIdx.x - nblk_pix, local);
+        const SliceDesc& d = dsl[s];
+        const int64_t k = (int64_t)local * 256 + threadIdx.x;
+        if (k >= (int64_t)d.g.nv * d.g.nb) return;
+        const float ac = (float)sc[s].alpha[0], ap = (float)sc[s].alpha[1];
+        const int64_t e = d.sino_off + k;
+        const float2 qv = __ldg(q + e);
+        float2 rx = Rx[e];
+        rx.x = fmaf(ac, qv.x, rx.x);
+        rx.y = fmaf(ap, qv.y, rx.y);
+        Rx[e] = rx;
+    }
+}
+
+// p = s + beta p
+__global__ void __launch_bounds__(256) k_cg_p(const SliceDesc* __restrict__ dsl, BlockMap pix,
+                                              const SliceScalars* __restrict__ sc, const float2* __restrict__ sv,
+                                              float2* __restrict__ p) {
+    int local;
+    const int s = slice_of(pix, blockIdx.x, local);
+    const SliceDesc& d = dsl[s];
+    const int64_t k = (int64_t)local * 256 + threadIdx.x;
+    if (k >= (int64_t)d.g.nx * d.g.ny) return;
+    const int64_t e = d.img_off + k;
+    const float bc = (float)sc[s].beta[0], bp = (float)sc[s].beta[1];
+    const float2 a = __ldg(sv + e);
+    float2 pv = p[e];
+    pv.x = fmaf(bc, pv.x, a.x);
+    pv.y = fmaf(bp, pv.y, a.y);
+    p[e] = pv;
+}
+
+// ---- Eq. 9-11 on the image side -----------------------------------------------------------------
+
+__device__ __forceinline__ float shrink(float t, float tau) {
+    const float m = fabsf(t) - tau;
+    return m > 0.f ? copysignf(m, t) : 0.f;
+}
+
+// y = shrinkage(Dx - u^y, lambda/rho); z = max(0, x - u^z); u^y += y - Dx; u^z += z - x.
+// partial[4 blk + {0,1}] = sum (y - Dx)^2 + (z - x)^2 per basis; {2,3} = sum (y - y_old)^2 + (z - z_old)^2.
+__global__ void __launch_bounds__(256) k_image_update(const SliceDesc* __restrict__ dsl, BlockMap pix,
+                                                      const SliceScalars* __restrict__ sc, double lam_c,
+                                                      double lam_p, const float2* __restrict__ x,
+                                                      float4* __restrict__ y, float4* __restrict__ uy,
+                                                      float2* __restrict__ z, float2* __restrict__ uz,
+                                                      double* __restrict__ partial) {
+    int local;
+    const int s = slice_of(pix, blockIdx.x, local);
+    const SliceDesc& d = dsl[s];
+    const int nx = d.g.nx, ny = d.g.ny;
+    const int64_t k = (int64_t)local * 256 + threadIdx.x;
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    if (k < (int64_t)nx * ny) {
+        const int j = (int)(k / nx), i = (int)(k % nx);
+        const float2* xs = x + d.img_off;
+        const int64_t e = d.img_off + k;
+        const float2 xc = __ldg(xs + k);
+        float4 g = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (i < nx - 1) {
+            const float2 rr = __ldg(xs + k + 1);
+            g.x = rr.x - xc.x;
+            g.z = rr.y - xc.y;
+        }
+        if (j < ny - 1) {
+            const float2 uu = __ldg(xs + k + nx);
+            g.y = uu.x - xc.x;
+            g.w = uu.y - xc.y;
+        }
+        const float tc = (float)(lam_c / sc[s].rho[0]), tp = (float)(lam_p / sc[s].rho[1]);
+        const float4 yo = y[e];
+        float4 u = uy[e];
+        const float4 yn = make_float4(shrink(g.x - u.x, tc), shrink(g.y - u.y, tc), shrink(g.z - u.z, tp),
+                                      shrink(g.w - u.w, tp));
+        u.x += yn.x - g.x;
+        u.y += yn.y - g.y;
+        u.z += yn.z - g.z;
+        u.w += yn.w - g.w;
+        y[e] = yn;
+        uy[e] = u;
+        const float2 zo = z[e];
+        float2 w = uz[e];
+        const float2 zn = make_float2(fmaxf(0.f, xc.x - w.x), fmaxf(0.f, xc.y - w.y));
+        w.x += zn.x - xc.x;
+        w.y += zn.y - xc.y;
+        z[e] = zn;
+        uz[e] = w;
+        const double ryx = yn.x - g.x, ryy = yn.y - g.y, rpx = yn.z - g.z, rpy = yn.w - g.w;
+        const double rzc = zn.x - xc.x, rzp = zn.y - xc.y;
+        acc[0] = ryx * ryx + ryy * ryy + rzc * rzc;
+        acc[1] = rpx * rpx + rpy * rpy + rzp * rzp;
+        const double dyx = yn.x - yo.x, dyy = yn.y - yo.y, dpx = yn.z - yo.z, dpy = yn.w - yo.w;
+        const double dzc = zn.x - zo.x, dzp = zn.y - zo.y;
+        acc[2] = dyx * dyx + dyy * dyy + dzc * dzc;
+        acc[3] = dpx * dpx + dpy * dpy + dzp * dzp;
+    }
+    block_partials<4>(acc, partial);
+}
+
+// residual balancing: one block per slice
+__global__ void __launch_bounds__(256) k_rho_update(const double* __restrict__ part_udm,
+                                                    const int* __restrict__ rays_prefix,
+                                                    const double* __restrict__ part_img,
+                                                    const int* __restrict__ pix_prefix, SliceScalars* __restrict__ sc,
+                                                    double mu_b, double tau) {
+    const int s = blockIdx.x;
+    double a[4], b[4];
+    slice_sum<4>(part_udm, rays_prefix, s, a);
+    slice_sum<4>(part_img, pix_prefix, s, b);
+    if (threadIdx.x == 0) {
+        for (int c = 0; c < 2; ++c) {
+            const double rp = sqrt(a[c] + b[c]);
+            const double rd = sc[s].rho[c] * sqrt(a[2 + c] + b[2 + c]);
+            sc[s].r_pri[c] = rp;
+            sc[s].r_dual[c] = rd;
+            double f = 1.0;
+            if (rp > mu_b * rd) f = tau;
+            else if (rd > mu_b * rp) f = 1.0 / tau;
+            sc[s].factor[c] = f;
+            sc[s].rho[c] *= f;
+        }
+        sc[s].iteration += 1;
+    }
+}
+
+// scaled duals follow rho: u /= factor (no-op when both factors are 1)
+__global__ void __launch_bounds__(256) k_dual_rescale(const SliceDesc* __restrict__ dsl, BlockMap pix, int nblk_pix,
+                                                      BlockMap rays, const SliceScalars* __restrict__ sc,
+                                                      float4* __restrict__ uy, float2* __restrict__ uz,
+                                                      float2* __restrict__ ua) {
+    int local;
+    const bool img = (int)blockIdx.x < nblk_pix;
+    const int s = img ? slice_of(pix, blockIdx.x, local) : slice_of(rays, blockIdx.x - nblk_pix, local);
+    const double fc = sc[s].factor[0], fp = sc[s].factor[1];
+    if (fc == 1.0 && fp == 1.0) return;
+    const float gc = (float)(1.0 / fc), gp = (float)(1.0 / fp);
+    const SliceDesc& d = dsl[s];
+    const int64_t k = (int64_t)local * 256 + threadIdx.x;
+    if (img) {
+        if (k >= (int64_t)d.g.nx * d.g.ny) return;
+        const int64_t e = d.img_off + k;
+        float4 u = uy[e];
+        u.x *= gc;
+        u.y *= gc;
+        u.z *= gp;
+        u.w *= gp;
+        uy[e] = u;
+        float2 w = uz[e];
+        w.x *= gc;
+        w.y *= gp;
+        uz[e] = w;
+    } else {
+        if (k >= (int64_t)d.g.nv * d.g.nb) return;
+        const int64_t e = d.sino_off + k;
+        float2 u = ua[e];
+        u.x *= gc;
+        u.y *= gp;
+        ua[e] = u;
+    }
+}
+
+// ---- monitors -------------------------------------------------------------------------------------
+
+// partial[4 blk + {0,1}] = sum (x - x*)^2 per basis, {2,3} = sum x*^2
+__global__ void __launch_bounds__(256) k_xi_partials(const SliceDesc* __restrict__ dsl, BlockMap pix,
+                                                     const float2* __restrict__ x, const float2* __restrict__ truth,
+                                                     double* __restrict__ partial) {
+    int local;
+    const int s = slice_of(pix, blockIdx.x, local);
+    const SliceDesc& d = dsl[s];
+    const int64_t k = (int64_t)local * 256 + threadIdx.x;
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    if (k < (int64_t)d.g.nx * d.g.ny) {
+        const int64_t e = d.img_off + k;
+        const float2 xv = __ldg(x + e), tv = __ldg(truth + e);
+        const double dc = (double)xv.x - tv.x, dp = (double)xv.y - tv.y;
+        acc[0] = dc * dc;
+        acc[1] = dp * dp;
+        acc[2] = (double)tv.x * tv.x;
+        acc[3] = (double)tv.y * tv.y;
+    }
+    block_partials<4>(acc, partial);
+}
+
+__global__ void __launch_bounds__(256) k_xi_reduce(const double* __restrict__ part, const int* __restrict__ pix_prefix,
+                                                   SliceScalars* __restrict__ sc) {
+    const int s = blockIdx.x;
+    double v[4];
+    slice_sum<4>(part, pix_prefix, s, v);
+    if (threadIdx.x == 0) {
+        sc[s].xi_num[0] = v[0];
+        sc[s].xi_num[1] = v[1];
+        sc[s].xi_den[0] = v[2];
+        sc[s].xi_den[1] = v[3];
+    }
+}
+
+// ---- state set-up -------------------------------------------------------------------------------
+
+// x_c = max(0, x_c), x_p = kappa x_c, for slices without a given start; slices with one copy x0
+__global__ void __launch_bounds__(256) k_init_image(const SliceDesc* __restrict__ dsl, BlockMap pix,
+                                                    const int* __restrict__ has_x0, const float2* __restrict__ x0,
+                                                    float2* __restrict__ x, float kappa) {
+    int local;
+    const int s = slice_of(pix, blockIdx.x, local);
+    const SliceDesc& d = dsl[s];
+    const int64_t k = (int64_t)local * 256 + threadIdx.x;
+    if (k >= (int64_t)d.g.nx * d.g.ny) return;
+    const int64_t e = d.img_off + k;
+    if (has_x0[s]) {
+        x[e] = __ldg(x0 + e);
+    } else {
+        const float c = fmaxf(0.f, x[e].x);
+        x[e] = make_float2(c, kappa * c);
+    }
+}
+
+// y = D x, u^y = 0, z = x, u^z = 0 (image blocks); a = R x, u^a = 0, mu = mu0 (ray blocks)
+__global__ void __launch_bounds__(256) k_state_from_image(const SliceDesc* __restrict__ dsl, BlockMap pix, int nblk_pix,
+                                                          BlockMap rays, const float2* __restrict__ x,
+                                                          float4* __restrict__ y, float4* __restrict__ uy,
+                                                          float2* __restrict__ z, float2* __restrict__ uz,
+                                                          const float2* __restrict__ Rx, float2* __restrict__ a,
+                                                          float2* __restrict__ ua, float* __restrict__ mu, float mu0) {
+    int local;
+    if ((int)blockIdx.x < nblk_pix) {
+        const int s = slice_of(pix, blockIdx.x, local);
+        const SliceDesc& d = dsl[s];
+        const int nx = d.g.nx, ny = d.g.ny;
+        const int64_t k = (int64_t)local * 256 + threadIdx.x;
+        if (k >= (int64_t)nx * ny) return;
+        const int j = (int)(k / nx), i = (int)(k % nx);
+        const float2* xs = x + d.img_off;
+        const float2 xc = __ldg(xs + k);
+        float4 g = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (i < nx - 1) {
+            const float2 rr = __ldg(xs + k + 1);
+            g.x = rr.x - xc.x;
+            g.z = rr.y - xc.y;
+        }
+        if (j < ny - 1) {
+            const float2 uu = __ldg(xs + k + nx);
+            g.y = uu.x - xc.x;
+            g.w = uu.y - xc.y;
+        }
+        const int64_t e = d.img_off + k;
+        y[e] = g;
+        uy[e] = make_float4(0.f, 0.f, 0.f, 0.f);
+        z[e] = xc;
+        uz[e] = make_float2(0.f, 0.f);
+    } else {
+        const int s = slice_of(rays, blockIdx.x - nblk_pix, local);
+        const SliceDesc& d = dsl[s];
+        const int64_t k = (int64_t)local * 256 + threadIdx.x;
+        if (k >= (int64_t)d.g.nv * d.g.nb) return;
+        const int64_t e = d.sino_off + k;
+        a[e] = __ldg(Rx + e);
+        ua[e] = make_float2(0.f, 0.f);
+        mu[e] = mu0;
+    }
+}
+
+__global__ void k_reset_scalars(SliceScalars* __restrict__ sc, int B, double rho_c, double rho_p) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= B) return;
+    SliceScalars v = {};
+    v.rho[0] = rho_c;
+    v.rho[1] = rho_p;
+    v.factor[0] = v.factor[1] = 1.0;
+    v.xi_num[0] = v.xi_num[1] = nan("");
+    v.xi_den[0] = v.xi_den[1] = nan("");
+    sc[s] = v;
+}
+
+// measurements: four planar float arrays (staged) -> float4 per ray of slice s
+__global__ void k_pack_meas(const float* __restrict__ st, int64_t n, float4* __restrict__ meas) {
+    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n) return;
+    meas[r] = make_float4(st[r], st[n + r], st[2 * n + r], st[3 * n + r]);
+}
+
+// planar [2][n] -> interleaved float2
+__global__ void k_interleave(const float* __restrict__ in, int64_t n, float2* __restrict__ out) {
+    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n) return;
+    out[r] = make_float2(in[r], in[n + r]);
+}
+
+// interleaved float2 [n] -> planar [2][n]
+__global__ void k_deinterleave2(const float2* __restrict__ in, int64_t n, float* __restrict__ out) {
+    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n) return;
+    const float2 v = in[r];
+    out[r] = v.x;
+    out[n + r] = v.y;
+}
+
+// float4 {xc, yc, xp, yp} [n] -> planar [2 basis][2 component][n]
+__global__ void k_deinterleave4(const float4* __restrict__ in, int64_t n, float* __restrict__ out) {
+    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n) return;
+    const float4 v = in[r];
+    out[r] = v.x;
+    out[n + r] = v.y;
+    out[2 * n + r] = v.z;
+    out[3 * n + r] = v.w;
+}
+
+// plain CG (no preconditioner): s = r and <r, r> per row block, in the preconditioner's slot layout
+__global__ void __launch_bounds__(256) k_identity_precond(const SliceDesc* __restrict__ dsl, BlockMap rows,
+                                                          const float2* __restrict__ r, float2* __restrict__ s,
+                                                          double* __restrict__ partial) {
+    int j;
+    const int sl = slice_of(rows, blockIdx.x, j);
+    const SliceDesc& d = dsl[sl];
+    const size_t row = d.img_off + (size_t)j * d.g.nx;
+    double acc[2] = {0.0, 0.0};
+    for (int t = threadIdx.x; t < d.g.nx; t += blockDim.x) {
+        const float2 v = __ldg(r + row + t);
+        s[row + t] = v;
+        acc[0] += (double)v.x * v.x;
+        acc[1] += (double)v.y * v.y;
+    }
+    block_partials<2>(acc, partial);
+}
+
+// ---- launchers -----------------------------------------------------------------------------------
+
+void launch_identity_precond(const SliceDesc* d, const BlockMap& rows, int nrows, const float2* r, float2* s,
+                             double* partial, cudaStream_t st) {
+    k_identity_precond<<<nrows, 256, 0, st>>>(d, rows, r, s, partial);
+}
+
+static unsigned nb(int64_t n, int t = 256) { return (unsigned)((n + t - 1) / t); }
+
+void launch_sino_resid(const SliceDesc* d, const BlockMap& rays, int nr, const float2* a, const float2* ua,
+                       const float2* Rx, float2* b, cudaStream_t st) {
+    k_sino_resid<<<nr, 256, 0, st>>>(d, rays, a, ua, Rx, b);
+}
+void launch_rs_reduce(const double* part, const int* rows_prefix, SliceScalars* sc, int B, int first, cudaStream_t st) {
+    k_rs_reduce<<<B, 256, 0, st>>>(part, rows_prefix, sc, first);
+}
+void launch_alpha(const double* part, const int* bp_prefix, SliceScalars* sc, int B, cudaStream_t st) {
+    k_alpha<<<B, 256, 0, st>>>(part, bp_prefix, sc);
+}
+void launch_cg_update(const SliceDesc* d, const BlockMap& pix, int np, const BlockMap& rays, int nr,
+                      const SliceScalars* sc, float2* x, const float2* p, float2* r, const float2* Ap, float2* Rx,
+                      const float2* q, int last, cudaStream_t st) {
+    k_cg_update<<<np + nr, 256, 0, st>>>(d, pix, np, rays, sc, x, p, r, Ap, Rx, q, last);
+}
+void launch_cg_p(const SliceDesc* d, const BlockMap& pix, int np, const SliceScalars* sc, const float2* s, float2* p,
+                 cudaStream_t st) {
+    k_cg_p<<<np, 256, 0, st>>>(d, pix, sc, s, p);
+}
+void launch_image_update(const SliceDesc* d, const BlockMap& pix, int np, const SliceScalars* sc, double lam_c,
+                         double lam_p, const float2* x, float4* y, float4* uy, float2* z, float2* uz, double* partial,
+                         cudaStream_t st) {
+    k_image_update<<<np, 256, 0, st>>>(d, pix, sc, lam_c, lam_p, x, y, uy, z, uz, partial);
+}
+void launch_rho_update(const double* part_udm, const int* rays_prefix, const double* part_img, const int* pix_prefix,
+                       SliceScalars* sc, int B, double mu_b, double tau, cudaStream_t st) {
+    k_rho_update<<<B, 256, 0, st>>>(part_udm, rays_prefix, part_img, pix_prefix, sc, mu_b, tau);
+}
+void launch_dual_rescale(const SliceDesc* d, const BlockMap& pix, int np, const BlockMap& rays, int nr,
+                         const SliceScalars* sc, float4* uy, float2* uz, float2* ua, cudaStream_t st) {
+    k_dual_rescale<<<np + nr, 256, 0, st>>>(d, pix, np, rays, sc, uy, uz, ua);
+}
+void launch_xi(const SliceDesc* d, const BlockMap& pix, int np, const float2* x, const float2* truth, double* partial,
+               SliceScalars* sc, int B, cudaStream_t st) {
+    k_xi_partials<<<np, 256, 0, st>>>(d, pix, x, truth, partial);
+    k_xi_reduce<<<B, 256, 0, st>>>(partial, pix.prefix, sc);
+}
+void launch_init_image(const SliceDesc* d, const BlockMap& pix, int np, const int* has_x0, const float2* x0,
+                       float2* x, float kappa, cudaStream_t st) {
+    k_init_image<<<np, 256, 0, st>>>(d, pix, has_x0, x0, x, kappa);
+}
+void launch_state_from_image(const SliceDesc* d, const BlockMap& pix, int np, const BlockMap& rays, int nr,
+                             const float2* x, float4* y, float4* uy, float2* z, float2* uz, const float2* Rx,
+                             float2* a, float2* ua, float* mu, float mu0, cudaStream_t st) {
+    k_state_from_image<<<np + nr, 256, 0, st>>>(d, pix, np, rays, x, y, uy, z, uz, Rx, a, ua, mu, mu0);
+}
+void launch_reset_scalars(SliceScalars* sc, int B, double rho_c, double rho_p, cudaStream_t st) {
+    k_reset_scalars<<<nb(B, 64), 64, 0, st>>>(sc, B, rho_c, rho_p);
+}
+void launch_pack_meas(const float* staged, int64_t n, float4* meas, cudaStream_t st) {
+    k_pack_meas<<<nb(n), 256, 0, st>>>(staged, n, meas);
+}
+void launch_interleave(const float* in, int64_t n, float2* out, cudaStream_t st) {
+    k_interleave<<<nb(n), 256, 0, st>>>(in, n, out);
+}
+void launch_deinterleave2(const float2* in, int64_t n, float* out, cudaStream_t st) {
+    k_deinterleave2<<<nb(n), 256, 0, st>>>(in, n, out);
+}
+void launch_deinterleave4(const float4* in, int64_t n, float* out, cudaStream_t st) {
+    k_deinterleave4<<<nb(n), 256, 0, st>>>(in, n, out);
+}
+
+}  // namespace dect

@@ -1,0 +1,888 @@
+// C ABI of the dect library (include/dect.h): handles, argument validation and
+// the host-side orchestration of one ADMM iteration of UDM(m)-PCG(n)
+// (Sec. 3.3 of the paper). Every step of the iteration runs in this library's
+// kernels; the host only enqueues them (or replays them as one CUDA graph).
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "admm_kernels.cuh"
+#include "dect_internal.cuh"
+
+namespace dect {
+static thread_local std::string g_err;
+void set_error(const std::string& m) { g_err = m; }
+
+void project_single(const SliceDesc& sd, const float* img, int nch, float2* scratch, float4* tx, float4* ty,
+                    float* out, cudaStream_t st);
+void backproject_single(const SliceDesc& sd, const float* sino, int nch, float2* packed, float* out,
+                        cudaStream_t st);
+void launch_identity_precond(const SliceDesc* d, const BlockMap& rows, int nrows, const float2* r, float2* s,
+                             double* partial, cudaStream_t st);
+}  // namespace dect
+
+using namespace dect;
+
+#define DECT_FAIL(code, msg)   \
+    do {                       \
+        dect::set_error(msg);  \
+        return code;           \
+    } while (0)
+
+#define CUDA_TRY(call)                                                                       \
+    do {                                                                                     \
+        cudaError_t e_ = (call);                                                             \
+        if (e_ != cudaSuccess) {                                                             \
+            dect::set_error(std::string(#call) + ": " + cudaGetErrorString(e_));             \
+            return e_ == cudaErrorMemoryAllocation ? DECT_ENOMEM : DECT_ECUDA;               \
+        }                                                                                    \
+    } while (0)
+
+static cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+template <typename T>
+static cudaError_t dalloc(T** p, size_t count) {
+    *p = nullptr;
+    if (count == 0) count = 1;
+    return cudaMalloc((void**)p, count * sizeof(T));
+}
+
+static int ilog2(int v) {
+    int l = 0;
+    while ((1 << l) < v) ++l;
+    return l;
+}
+
+static int pad_pow2(int n) {
+    int p = 1;
+    while (p < 2 * n) p *= 2;
+    return p;
+}
+
+// ----------------------------------------------------------------------------------------------
+struct dect_geom {
+    dect_geom_desc desc{};
+    int4* rays = nullptr;
+    float4* views = nullptr;
+    // workspace of dect_project / dect_backproject (allocated on first use)
+    float2* ws_img = nullptr;
+    float4* ws_tx = nullptr;
+    float4* ws_ty = nullptr;
+    float2* ws_sino = nullptr;
+
+    int64_t n_rays() const { return (int64_t)desc.n_views * desc.n_bins; }
+    int64_t n_pix() const { return (int64_t)desc.nx * desc.ny; }
+    GeomDev dev() const {
+        GeomDev g;
+        g.kind = desc.kind;
+        g.nx = desc.nx;
+        g.ny = desc.ny;
+        g.nv = desc.n_views;
+        g.nb = desc.n_bins;
+        g.pix = (float)desc.pixel_cm;
+        g.du = (float)desc.bin_pitch_cm;
+        g.uoff = (float)desc.bin_offset_cm;
+        g.sod = (float)desc.sod_cm;
+        g.sdd = (float)desc.sdd_cm;
+        g.cx = 0.5f * (float)(desc.nx - 1);
+        g.cy = 0.5f * (float)(desc.ny - 1);
+        g.rays = rays;
+        g.views = views;
+        return g;
+    }
+    SliceDesc single() const {
+        SliceDesc s{};
+        s.g = dev();
+        return s;
+    }
+};
+
+struct dect_spectra {
+    int ne = 0;
+    float4* t1 = nullptr;
+    float4* t2 = nullptr;
+    double abar_low = 1.0;  // sum_E S_l f_KN (unit-sum S_l)
+    SpecDev dev() const { return SpecDev{ne, t1, t2}; }
+};
+
+extern "C" const char* dect_version(void) { return "dect 0.1 sm_103a"; }
+extern "C" const char* dect_last_error(void) { return dect::g_err.c_str(); }
+
+extern "C" dect_status dect_sync(void* stream) {
+    CUDA_TRY(cudaStreamSynchronize(as_stream(stream)));
+    CUDA_TRY(cudaGetLastError());
+    return DECT_OK;
+}
+
+static bool finite_pos(double v) { return std::isfinite(v) && v > 0.0; }
+
+// Launch errors are read back with cudaGetLastError; clear any error left by an unrelated earlier
+// runtime call so that it is not reported against this call.
+static void clear_stale_error() { (void)cudaGetLastError(); }
+
+extern "C" dect_status dect_geometry_create(const dect_geom_desc* d, dect_geom** out) {
+    clear_stale_error();
+    if (!d || !out) DECT_FAIL(DECT_EINVAL, "dect_geometry_create: null argument");
+    *out = nullptr;
+    if (d->kind != DECT_PARALLEL && d->kind != DECT_FAN_FLAT) DECT_FAIL(DECT_EINVAL, "geometry: unknown kind");
+    if (d->nx < 1 || d->ny < 1 || d->nx > 4096 || d->ny > 4096) DECT_FAIL(DECT_EINVAL, "geometry: nx, ny must be in [1, 4096]");
+    if (d->n_views < 1 || d->n_bins < 1 || d->n_views > 16384 || d->n_bins > 16384)
+        DECT_FAIL(DECT_EINVAL, "geometry: n_views, n_bins must be in [1, 16384]");
+    if (!finite_pos(d->pixel_cm) || !finite_pos(d->bin_pitch_cm)) DECT_FAIL(DECT_EINVAL, "geometry: pixel and bin pitch must be > 0");
+    if (!std::isfinite(d->angle0_rad) || !std::isfinite(d->angle_span_rad) || !std::isfinite(d->bin_offset_cm))
+        DECT_FAIL(DECT_EINVAL, "geometry: non-finite angle or offset");
+    if (d->kind == DECT_FAN_FLAT) {
+        if (!finite_pos(d->sod_cm) || !finite_pos(d->sdd_cm) || d->sdd_cm <= d->sod_cm)
+            DECT_FAIL(DECT_EINVAL, "geometry: fan beam needs sdd > sod > 0");
+        const double r = 0.5 * d->pixel_cm * std::sqrt((double)d->nx * d->nx + (double)d->ny * d->ny) + 2.0 * d->pixel_cm;
+        if (r >= 0.98 * d->sod_cm) DECT_FAIL(DECT_EINVAL, "geometry: image must lie well inside the source circle");
+    }
+    dect_geom* g = new dect_geom();
+    g->desc = *d;
+    cudaError_t e = dalloc(&g->rays, (size_t)g->n_rays());
+    if (e == cudaSuccess) e = dalloc(&g->views, (size_t)d->n_views);
+    if (e == cudaSuccess) e = build_ray_table(*d, g->rays, g->views, 0);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(0);
+    if (e != cudaSuccess) {
+        dect::set_error(std::string("dect_geometry_create: ") + cudaGetErrorString(e));
+        dect_geometry_destroy(g);
+        return e == cudaErrorMemoryAllocation ? DECT_ENOMEM : DECT_ECUDA;
+    }
+    *out = g;
+    return DECT_OK;
+}
+
+extern "C" void dect_geometry_destroy(dect_geom* g) {
+    if (!g) return;
+    cudaFree(g->rays);
+    cudaFree(g->views);
+    cudaFree(g->ws_img);
+    cudaFree(g->ws_tx);
+    cudaFree(g->ws_ty);
+    cudaFree(g->ws_sino);
+    delete g;
+}
+
+static dect_status geom_workspace(dect_geom* g) {
+    if (g->ws_img) return DECT_OK;
+    const auto& d = g->desc;
+    CUDA_TRY(dalloc(&g->ws_img, (size_t)g->n_pix()));
+    CUDA_TRY(dalloc(&g->ws_tx, (size_t)d.nx * (d.ny + 3)));
+    CUDA_TRY(dalloc(&g->ws_ty, (size_t)d.ny * (d.nx + 3)));
+    CUDA_TRY(dalloc(&g->ws_sino, (size_t)g->n_rays()));
+    return DECT_OK;
+}
+
+extern "C" dect_status dect_project(dect_geom* g, int32_t nch, int32_t dtype, const void* x, void* sino, void* stream) {
+    clear_stale_error();
+    if (!g || !x || !sino) DECT_FAIL(DECT_EINVAL, "dect_project: null argument");
+    if (nch != 1 && nch != 2) DECT_FAIL(DECT_EINVAL, "dect_project: n_channels must be 1 or 2");
+    if (dtype != DECT_F32) DECT_FAIL(DECT_EUNSUPPORTED, "dect_project: only DECT_F32 is supported");
+    dect_status st = geom_workspace(g);
+    if (st != DECT_OK) return st;
+    project_single(g->single(), (const float*)x, nch, g->ws_img, g->ws_tx, g->ws_ty, (float*)sino, as_stream(stream));
+    CUDA_TRY(cudaGetLastError());
+    return DECT_OK;
+}
+
+extern "C" dect_status dect_backproject(dect_geom* g, int32_t nch, int32_t dtype, const void* sino, void* x,
+                                        void* stream) {
+    clear_stale_error();
+    if (!g || !x || !sino) DECT_FAIL(DECT_EINVAL, "dect_backproject: null argument");
+    if (nch != 1 && nch != 2) DECT_FAIL(DECT_EINVAL, "dect_backproject: n_channels must be 1 or 2");
+    if (dtype != DECT_F32) DECT_FAIL(DECT_EUNSUPPORTED, "dect_backproject: only DECT_F32 is supported");
+    dect_status st = geom_workspace(g);
+    if (st != DECT_OK) return st;
+    backproject_single(g->single(), (const float*)sino, nch, g->ws_sino, (float*)x, as_stream(stream));
+    CUDA_TRY(cudaGetLastError());
+    return DECT_OK;
+}
+
+// ----------------------------------------------------------------------------------------------
+extern "C" dect_status dect_spectra_create(int32_t ne, const double* S_h, const double* S_l, const double* f_kn,
+                                           const double* f_p, dect_spectra** out) {
+    clear_stale_error();
+    if (!out || !S_h || !S_l || !f_kn || !f_p) DECT_FAIL(DECT_EINVAL, "dect_spectra_create: null argument");
+    *out = nullptr;
+    if (ne < 1 || ne > kMaxEnergies) DECT_FAIL(DECT_EINVAL, "dect_spectra_create: n_energies must be in [1, 512]");
+    double th = 0.0, tl = 0.0;
+    for (int e = 0; e < ne; ++e) {
+        if (!(S_h[e] >= 0.0) || !(S_l[e] >= 0.0) || !std::isfinite(S_h[e]) || !std::isfinite(S_l[e]) ||
+            !std::isfinite(f_kn[e]) || !std::isfinite(f_p[e]))
+            DECT_FAIL(DECT_EINVAL, "dect_spectra_create: spectra must be finite and >= 0, basis functions finite");
+        th += S_h[e];
+        tl += S_l[e];
+    }
+    if (!(th > 0.0) || !(tl > 0.0)) DECT_FAIL(DECT_EINVAL, "dect_spectra_create: spectra must have positive sums");
+    const double log2e = 1.4426950408889634;
+    std::vector<float4> t1(ne), t2(ne);
+    double abar = 0.0;
+    for (int e = 0; e < ne; ++e) {
+        const double sh = S_h[e] / th, sl = S_l[e] / tl;
+        t1[e] = make_float4((float)(f_kn[e] * log2e), (float)(f_p[e] * log2e), (float)sh, (float)sl);
+        t2[e] = make_float4((float)(sh * f_kn[e]), (float)(sh * f_p[e]), (float)(sl * f_kn[e]), (float)(sl * f_p[e]));
+        abar += sl * f_kn[e];
+    }
+    dect_spectra* s = new dect_spectra();
+    s->ne = ne;
+    s->abar_low = abar;
+    cudaError_t e = dalloc(&s->t1, ne);
+    if (e == cudaSuccess) e = dalloc(&s->t2, ne);
+    if (e == cudaSuccess) e = cudaMemcpy(s->t1, t1.data(), sizeof(float4) * ne, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(s->t2, t2.data(), sizeof(float4) * ne, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        dect::set_error(std::string("dect_spectra_create: ") + cudaGetErrorString(e));
+        dect_spectra_destroy(s);
+        return DECT_ECUDA;
+    }
+    *out = s;
+    return DECT_OK;
+}
+
+extern "C" void dect_spectra_destroy(dect_spectra* s) {
+    if (!s) return;
+    cudaFree(s->t1);
+    cudaFree(s->t2);
+    delete s;
+}
+
+extern "C" dect_status dect_decompose_rays(const dect_spectra* s, int64_t n, const float* m_h, const float* m_l,
+                                           const float* w_h, const float* w_l, const float* v_c, const float* v_p,
+                                           double rho_c, double rho_p, int32_t iters, float* a_c, float* a_p,
+                                           float* mu, uint8_t* status, void* stream) {
+    clear_stale_error();
+    if (!s) DECT_FAIL(DECT_EINVAL, "dect_decompose_rays: null spectra");
+    if (n < 0) DECT_FAIL(DECT_EINVAL, "dect_decompose_rays: n_rays < 0");
+    if (n == 0) return DECT_OK;
+    if (!m_h || !m_l || !w_h || !w_l || !v_c || !v_p || !a_c || !a_p || !mu)
+        DECT_FAIL(DECT_EINVAL, "dect_decompose_rays: null array");
+    if (iters < 0) DECT_FAIL(DECT_EINVAL, "dect_decompose_rays: iters < 0");
+    if (!(rho_c >= 0.0) || !(rho_p >= 0.0) || !std::isfinite(rho_c) || !std::isfinite(rho_p))
+        DECT_FAIL(DECT_EINVAL, "dect_decompose_rays: rho must be finite and >= 0");
+    launch_udm_rays(s->dev(), n, m_h, m_l, w_h, w_l, v_c, v_p, rho_c, rho_p, iters, a_c, a_p, mu, status,
+                    as_stream(stream));
+    CUDA_TRY(cudaGetLastError());
+    return DECT_OK;
+}
+
+// ----------------------------------------------------------------------------------------------
+extern "C" void dect_params_default(dect_params* p) {
+    if (!p) return;
+    p->lambda_c = 1e-5;
+    p->lambda_p = 1e-5;
+    p->rho0_c = 1e-3;
+    p->rho0_p = 1e-3;
+    p->m_udm = 1;
+    p->n_pcg = 1;
+    p->rho_mu = 10.0;
+    p->rho_tau = 2.0;
+    p->lm_mu0 = 1e-3;
+    p->kappa = 1e-2;
+    p->init_udm_iters = 10;
+    p->init_pcg_iters = 10;
+    p->precondition = 1;
+    p->use_graph = 1;
+}
+
+struct MapBuf {
+    int* d = nullptr;
+    std::vector<int> h;  // B+1 prefix
+    int total = 0;
+    BlockMap map(int B) const { return BlockMap{d, B}; }
+};
+
+struct dect_admm {
+    int B = 0;
+    std::vector<dect_geom*> geoms;
+    const dect_spectra* spec = nullptr;
+    dect_params P{};
+    std::vector<SliceDesc> hs;
+    SliceDesc* ds = nullptr;
+    MapBuf rays, pix, tx, ty, bp, rows, cols;
+    int64_t n_img = 0, n_sino = 0, n_tx = 0, n_ty = 0, n_fft = 0, n_h = 0, n_stage = 0;
+    int max_px = 0, max_py = 0;
+    float2 *x = nullptr, *r = nullptr, *s = nullptr, *p = nullptr, *Ap = nullptr, *z = nullptr, *uz = nullptr;
+    float2 *x0 = nullptr, *truth = nullptr, *Rx = nullptr, *a = nullptr, *ua = nullptr, *q = nullptr, *Z = nullptr;
+    float4 *y = nullptr, *uy = nullptr, *meas = nullptr, *txb = nullptr, *tyb = nullptr;
+    float *mu = nullptr, *H = nullptr, *Hn = nullptr, *stage = nullptr;
+    uint8_t* status = nullptr;
+    SliceScalars* sc = nullptr;
+    double *part_udm = nullptr, *part_img = nullptr, *part_rs = nullptr, *part_pap = nullptr, *part_xi = nullptr;
+    int* d_has_x0 = nullptr;
+    std::vector<int> has_x0, has_truth, has_data;
+    const float2* tw = nullptr;
+    bool initialized = false;
+    bool counting = true;
+    cudaStream_t cap = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    int64_t cR = 0, cRT = 0, cF = 0, cL = 0;
+    int64_t launches_per_iter = 0;
+    // profiling: an event pair around every kernel group of the captured iteration
+    bool prof_on = false;
+    int prof_n = 0;
+    std::vector<cudaEvent_t> prof_ev;
+    std::vector<int> prof_phase, prof_kernels;
+    cudaGraphExec_t pgexec = nullptr;
+};
+
+static constexpr int kMaxProfGroups = 128;
+
+// Marks the start of a kernel group (records an event when profiling is being captured).
+static void pb(dect_admm* A, cudaStream_t st) {
+    // external records: captured as event-record nodes of the graph (not only as dependencies)
+    if (A->prof_on && A->prof_n < kMaxProfGroups)
+        cudaEventRecordWithFlags(A->prof_ev[2 * A->prof_n], st, cudaEventRecordExternal);
+}
+
+// Marks the end of a group of `nk` kernels of `phase`; counts the launches.
+static void pe(dect_admm* A, int phase, int nk, cudaStream_t st) {
+    if (A->counting) A->cL += nk;
+    if (A->prof_on && A->prof_n < kMaxProfGroups) {
+        cudaEventRecordWithFlags(A->prof_ev[2 * A->prof_n + 1], st, cudaEventRecordExternal);
+        A->prof_phase.push_back(phase);
+        A->prof_kernels.push_back(nk);
+        A->prof_n++;
+    }
+}
+
+static void free_admm(dect_admm* A) {
+    void* ptrs[] = {A->ds, A->rays.d, A->pix.d, A->tx.d, A->ty.d, A->bp.d, A->rows.d, A->cols.d, A->x, A->r, A->s,
+                    A->p, A->Ap, A->z, A->uz, A->x0, A->truth, A->Rx, A->a, A->ua, A->q, A->Z, A->y, A->uy,
+                    A->meas, A->txb, A->tyb, A->mu, A->H, A->Hn, A->stage, A->status, A->sc, A->part_udm,
+                    A->part_img, A->part_rs, A->part_pap, A->part_xi, A->d_has_x0};
+    for (void* q : ptrs) cudaFree(q);
+    if (A->gexec) cudaGraphExecDestroy(A->gexec);
+    if (A->pgexec) cudaGraphExecDestroy(A->pgexec);
+    for (cudaEvent_t e : A->prof_ev) cudaEventDestroy(e);
+    if (A->cap) cudaStreamDestroy(A->cap);
+    delete A;
+}
+
+static cudaError_t upload_map(MapBuf& m) {
+    cudaError_t e = dalloc(&m.d, m.h.size());
+    if (e != cudaSuccess) return e;
+    m.total = m.h.back();
+    return cudaMemcpy(m.d, m.h.data(), sizeof(int) * m.h.size(), cudaMemcpyHostToDevice);
+}
+
+// ---- enqueue helpers ---------------------------------------------------------------------------
+
+static void enq_project(dect_admm* A, const float2* img, float2* out, cudaStream_t st) {
+    const int B = A->B;
+    pb(A, st);
+    launch_textures(A->ds, A->tx.map(B), A->tx.total, A->ty.map(B), A->ty.total, img, A->txb, A->tyb, st);
+    pe(A, DECT_PHASE_TEXTURE, 2, st);
+    pb(A, st);
+    launch_project(A->ds, A->rays.map(B), A->rays.total, A->txb, A->tyb, out, st);
+    pe(A, DECT_PHASE_PROJECT, 1, st);
+    if (A->counting) A->cR += 2;
+}
+
+static void enq_precond(dect_admm* A, const float* H, const float2* r, float2* s, cudaStream_t st) {
+    const int B = A->B;
+    pb(A, st);
+    if (A->P.precondition) {
+        launch_precond(A->ds, A->rows.map(B), A->rows.total, A->cols.map(B), A->cols.total, H, r, s, A->Z, A->part_rs,
+                       A->tw, A->max_px, A->max_py, st);
+        pe(A, DECT_PHASE_PRECOND, 3, st);
+    } else {
+        launch_identity_precond(A->ds, A->rows.map(B), A->rows.total, r, s, A->part_rs, st);
+        pe(A, DECT_PHASE_PRECOND, 1, st);
+    }
+}
+
+// Eq. 12: n PCG steps, warm-started from x, R x carried
+static void enq_pcg(dect_admm* A, int n, bool with_grad, const float* H, cudaStream_t st) {
+    const int B = A->B;
+    BpEpilogue ep{};
+    ep.x = A->x;
+    ep.y = A->y;
+    ep.uy = A->uy;
+    ep.z = A->z;
+    ep.uz = A->uz;
+    ep.p = A->p;
+    ep.partial = A->part_pap;
+    pb(A, st);
+    launch_sino_resid(A->ds, A->rays.map(B), A->rays.total, A->a, A->ua, A->Rx, A->q, st);
+    pe(A, DECT_PHASE_UPDATE, 1, st);
+    pb(A, st);
+    launch_backproject(with_grad ? BP_R0 : BP_R0_NOGRAD, A->ds, A->bp.map(B), A->bp.total, A->q, A->r, ep, st);
+    pe(A, DECT_PHASE_BACKPROJECT, 1, st);
+    if (A->counting) A->cRT += 2;
+    enq_precond(A, H, A->r, A->p, st);
+    pb(A, st);
+    launch_rs_reduce(A->part_rs, A->rows.d, A->sc, B, 1, st);
+    pe(A, DECT_PHASE_REDUCE, 1, st);
+    for (int it = 0; it < n; ++it) {
+        enq_project(A, A->p, A->q, st);
+        pb(A, st);
+        launch_backproject(with_grad ? BP_AP : BP_AP_NOGRAD, A->ds, A->bp.map(B), A->bp.total, A->q, A->Ap, ep, st);
+        pe(A, DECT_PHASE_BACKPROJECT, 1, st);
+        if (A->counting) A->cRT += 2;
+        pb(A, st);
+        launch_alpha(A->part_pap, A->bp.d, A->sc, B, st);
+        pe(A, DECT_PHASE_REDUCE, 1, st);
+        const int last = it == n - 1;
+        pb(A, st);
+        launch_cg_update(A->ds, A->pix.map(B), A->pix.total, A->rays.map(B), A->rays.total, A->sc, A->x, A->p, A->r,
+                         A->Ap, A->Rx, A->q, last, st);
+        pe(A, DECT_PHASE_UPDATE, 1, st);
+        if (!last) {
+            enq_precond(A, H, A->r, A->s, st);
+            pb(A, st);
+            launch_rs_reduce(A->part_rs, A->rows.d, A->sc, B, 0, st);
+            pe(A, DECT_PHASE_REDUCE, 1, st);
+            pb(A, st);
+            launch_cg_p(A->ds, A->pix.map(B), A->pix.total, A->sc, A->s, A->p, st);
+            pe(A, DECT_PHASE_UPDATE, 1, st);
+        }
+    }
+}
+
+static void enq_iteration(dect_admm* A, cudaStream_t st) {
+    const int B = A->B;
+    enq_pcg(A, A->P.n_pcg, true, A->H, st);
+    pb(A, st);
+    launch_udm_admm(A->ds, A->rays.map(B), A->rays.total, A->spec->dev(), A->meas, A->Rx, A->ua, A->a, A->mu,
+                    A->status, A->sc, A->P.m_udm, A->part_udm, st);
+    pe(A, DECT_PHASE_UDM, 1, st);
+    if (A->counting) A->cF += 4 * A->P.m_udm;
+    pb(A, st);
+    launch_image_update(A->ds, A->pix.map(B), A->pix.total, A->sc, A->P.lambda_c, A->P.lambda_p, A->x, A->y, A->uy,
+                        A->z, A->uz, A->part_img, st);
+    pe(A, DECT_PHASE_UPDATE, 1, st);
+    pb(A, st);
+    launch_rho_update(A->part_udm, A->rays.d, A->part_img, A->pix.d, A->sc, B, A->P.rho_mu, A->P.rho_tau, st);
+    pe(A, DECT_PHASE_REDUCE, 1, st);
+    pb(A, st);
+    launch_dual_rescale(A->ds, A->pix.map(B), A->pix.total, A->rays.map(B), A->rays.total, A->sc, A->uy, A->uz, A->ua,
+                        st);
+    pe(A, DECT_PHASE_UPDATE, 1, st);
+}
+
+// Captures one iteration into a graph (with event pairs when profiling).
+static dect_status capture_iteration(dect_admm* A, bool profile, cudaGraphExec_t* out) {
+    cudaGraph_t graph = nullptr;
+    A->counting = false;
+    A->prof_on = profile;
+    A->prof_n = 0;
+    A->prof_phase.clear();
+    A->prof_kernels.clear();
+    const int64_t l0 = A->cL;
+    cudaError_t e = cudaStreamBeginCapture(A->cap, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        A->counting = true;  // count launches of one iteration, then restore the other counters
+        const int64_t r0 = A->cR, rt0 = A->cRT, f0 = A->cF;
+        enq_iteration(A, A->cap);
+        A->launches_per_iter = A->cL - l0;
+        A->cL = l0;
+        A->cR = r0;
+        A->cRT = rt0;
+        A->cF = f0;
+        e = cudaStreamEndCapture(A->cap, &graph);
+    }
+    A->counting = true;
+    A->prof_on = false;
+    CUDA_TRY(e);
+    e = cudaGraphInstantiate(out, graph, 0);
+    cudaGraphDestroy(graph);
+    CUDA_TRY(e);
+    return DECT_OK;
+}
+
+static dect_status enq_initialize(dect_admm* A, cudaStream_t st) {
+    const int B = A->B;
+    for (int b = 0; b < B; ++b)
+        if (!A->has_data[b]) DECT_FAIL(DECT_EINVAL, "dect_admm: slice " + std::to_string(b) + " has no data");
+    CUDA_TRY(cudaMemcpyAsync(A->d_has_x0, A->has_x0.data(), sizeof(int) * B, cudaMemcpyHostToDevice, st));
+    bool all_x0 = true;
+    for (int b = 0; b < B; ++b) all_x0 = all_x0 && A->has_x0[b];
+    if (!all_x0) {
+        CUDA_TRY(cudaMemsetAsync(A->x, 0, sizeof(float2) * A->n_img, st));
+        CUDA_TRY(cudaMemsetAsync(A->Rx, 0, sizeof(float2) * A->n_sino, st));
+        CUDA_TRY(cudaMemsetAsync(A->ua, 0, sizeof(float2) * A->n_sino, st));
+        CUDA_TRY(cudaMemsetAsync(A->y, 0, sizeof(float4) * A->n_img, st));
+        CUDA_TRY(cudaMemsetAsync(A->uy, 0, sizeof(float4) * A->n_img, st));
+        CUDA_TRY(cudaMemsetAsync(A->z, 0, sizeof(float2) * A->n_img, st));
+        CUDA_TRY(cudaMemsetAsync(A->uz, 0, sizeof(float2) * A->n_img, st));
+        launch_udm_init(A->ds, A->rays.map(B), A->rays.total, A->spec->dev(), A->meas, A->a, A->mu, A->P.rho0_p,
+                        A->P.init_udm_iters, (float)A->spec->abar_low, A->P.lm_mu0, st);
+        A->cF += 4 * A->P.init_udm_iters;
+        launch_reset_scalars(A->sc, B, A->P.rho0_c, A->P.rho0_p, st);
+        enq_pcg(A, A->P.init_pcg_iters, false, A->Hn, st);
+    }
+    launch_init_image(A->ds, A->pix.map(B), A->pix.total, A->d_has_x0, A->x0, A->x, (float)A->P.kappa, st);
+    enq_project(A, A->x, A->Rx, st);
+    launch_state_from_image(A->ds, A->pix.map(B), A->pix.total, A->rays.map(B), A->rays.total, A->x, A->y, A->uy,
+                            A->z, A->uz, A->Rx, A->a, A->ua, A->mu, (float)A->P.lm_mu0, st);
+    launch_reset_scalars(A->sc, B, A->P.rho0_c, A->P.rho0_p, st);
+    CUDA_TRY(cudaGetLastError());
+    A->initialized = true;
+    return DECT_OK;
+}
+
+// ---- creation ------------------------------------------------------------------------------------
+
+static dect_status compute_responses(dect_admm* A) {
+    cudaStream_t st = A->cap;
+    for (int b = 0; b < A->B; ++b) {
+        const SliceDesc& sd = A->hs[b];
+        const int64_t np = (int64_t)sd.g.nx * sd.g.ny, nr = (int64_t)sd.g.nv * sd.g.nb;
+        // unit impulse at pixel (ny/2, nx/2) in both channels
+        CUDA_TRY(cudaMemsetAsync(A->stage, 0, sizeof(float) * 2 * np, st));
+        const float one[1] = {1.0f};
+        const int64_t c = (int64_t)(sd.g.ny / 2) * sd.g.nx + sd.g.nx / 2;
+        CUDA_TRY(cudaMemcpyAsync(A->stage + c, one, sizeof(float), cudaMemcpyHostToDevice, st));
+        CUDA_TRY(cudaMemcpyAsync(A->stage + np + c, one, sizeof(float), cudaMemcpyHostToDevice, st));
+        CUDA_TRY(cudaStreamSynchronize(st));
+        project_single(sd, A->stage, 2, A->x + sd.img_off, A->txb + sd.tx_off, A->tyb + sd.ty_off, A->stage + 2 * np,
+                       st);
+        backproject_single(sd, A->stage + 2 * np, 2, A->q + sd.sino_off, A->stage, st);
+        launch_interleave(A->stage, np, A->r + sd.img_off, st);
+        // one-slice descriptor and column map
+        SliceDesc one_slice = sd;
+        one_slice.fft_off = 0;
+        one_slice.h_off = 0;
+        const int C = precond_cols_per_block(sd.py);
+        const int ncols = (sd.px + C - 1) / C;
+        SliceDesc* dd = nullptr;
+        int* pre = nullptr;
+        CUDA_TRY(dalloc(&dd, 1));
+        CUDA_TRY(dalloc(&pre, 2));
+        const int hp[2] = {0, ncols};
+        CUDA_TRY(cudaMemcpyAsync(dd, &one_slice, sizeof(SliceDesc), cudaMemcpyHostToDevice, st));
+        CUDA_TRY(cudaMemcpyAsync(pre, hp, sizeof(hp), cudaMemcpyHostToDevice, st));
+        launch_psf_to_response(dd, one_slice, BlockMap{pre, 1}, ncols, A->r + sd.img_off, A->Z + sd.fft_off,
+                               A->H + sd.h_off, A->Hn + sd.h_off, A->tw, st);
+        cudaError_t e = cudaStreamSynchronize(st);
+        cudaFree(dd);
+        cudaFree(pre);
+        CUDA_TRY(e);
+        (void)nr;
+    }
+    CUDA_TRY(cudaGetLastError());
+    return DECT_OK;
+}
+
+extern "C" dect_status dect_admm_create(dect_geom* const* geoms, int32_t B, const dect_spectra* spec,
+                                        const dect_params* P, dect_admm** out) {
+    clear_stale_error();
+    if (!geoms || !spec || !P || !out) DECT_FAIL(DECT_EINVAL, "dect_admm_create: null argument");
+    *out = nullptr;
+    if (B < 1 || B > 4096) DECT_FAIL(DECT_EINVAL, "dect_admm_create: n_slices must be in [1, 4096]");
+    if (P->m_udm < 1 || P->n_pcg < 1 || P->m_udm > 64 || P->n_pcg > 64)
+        DECT_FAIL(DECT_EINVAL, "dect_admm_create: m_udm and n_pcg must be in [1, 64]");
+    if (P->init_udm_iters < 0 || P->init_pcg_iters < 1 || P->init_udm_iters > 1000 || P->init_pcg_iters > 1000)
+        DECT_FAIL(DECT_EINVAL, "dect_admm_create: init iterations out of range");
+    if (!(P->rho0_c > 0) || !(P->rho0_p > 0) || !(P->lambda_c >= 0) || !(P->lambda_p >= 0) || !(P->rho_mu >= 1) ||
+        !(P->rho_tau >= 1) || !(P->lm_mu0 > 0) || !std::isfinite(P->kappa) || !std::isfinite(P->rho0_c) ||
+        !std::isfinite(P->rho0_p) || !std::isfinite(P->lambda_c) || !std::isfinite(P->lambda_p))
+        DECT_FAIL(DECT_EINVAL, "dect_admm_create: invalid parameter value");
+    for (int b = 0; b < B; ++b) {
+        if (!geoms[b]) DECT_FAIL(DECT_EINVAL, "dect_admm_create: null geometry");
+        if (geoms[b]->desc.nx > 2048 || geoms[b]->desc.ny > 2048)
+            DECT_FAIL(DECT_EUNSUPPORTED, "dect_admm_create: the solver supports images up to 2048 x 2048");
+    }
+    cudaError_t fe = fft_init_attributes();
+    if (fe != cudaSuccess) DECT_FAIL(DECT_ECUDA, std::string("dect_admm_create: ") + cudaGetErrorString(fe));
+
+    dect_admm* A = new dect_admm();
+    A->B = B;
+    A->spec = spec;
+    A->P = *P;
+    A->geoms.assign(geoms, geoms + B);
+    A->has_x0.assign(B, 0);
+    A->has_truth.assign(B, 0);
+    A->has_data.assign(B, 0);
+    for (auto* m : {&A->rays, &A->pix, &A->tx, &A->ty, &A->bp, &A->rows, &A->cols}) m->h.assign(1, 0);
+    int64_t max_np = 0, max_nr = 0;
+    for (int b = 0; b < B; ++b) {
+        const dect_geom* g = geoms[b];
+        SliceDesc sd{};
+        sd.g = g->dev();
+        const int nx = g->desc.nx, ny = g->desc.ny;
+        const int64_t np = g->n_pix(), nr = g->n_rays();
+        sd.img_off = A->n_img;
+        sd.sino_off = A->n_sino;
+        sd.tx_off = A->n_tx;
+        sd.ty_off = A->n_ty;
+        sd.px = pad_pow2(nx);
+        sd.py = pad_pow2(ny);
+        sd.lpx = ilog2(sd.px);
+        sd.lpy = ilog2(sd.py);
+        sd.fft_off = A->n_fft;
+        sd.h_off = A->n_h;
+        A->n_img += np;
+        A->n_sino += nr;
+        A->n_tx += (int64_t)nx * (ny + 3);
+        A->n_ty += (int64_t)ny * (nx + 3);
+        A->n_fft += (int64_t)sd.px * sd.py;
+        A->n_h += (int64_t)sd.px * sd.py;
+        A->max_px = std::max(A->max_px, sd.px);
+        A->max_py = std::max(A->max_py, sd.py);
+        max_np = std::max(max_np, np);
+        max_nr = std::max(max_nr, nr);
+        A->hs.push_back(sd);
+        A->rays.h.push_back(A->rays.h.back() + (int)((nr + kRaysPerBlock - 1) / kRaysPerBlock));
+        A->pix.h.push_back(A->pix.h.back() + (int)((np + 255) / 256));
+        A->tx.h.push_back(A->tx.h.back() + texture_x_blocks(nx, ny));
+        A->ty.h.push_back(A->ty.h.back() + texture_y_blocks(nx, ny));
+        A->bp.h.push_back(A->bp.h.back() + bp_tiles(nx, ny));
+        A->rows.h.push_back(A->rows.h.back() + ny);
+        const int C = precond_cols_per_block(sd.py);
+        A->cols.h.push_back(A->cols.h.back() + (sd.px + C - 1) / C);
+    }
+    A->n_stage = std::max(4 * max_nr + 4 * max_np, (int64_t)16);
+
+#define ALLOC(ptr, n)                                                      \
+    do {                                                                   \
+        cudaError_t e_ = dalloc(&(ptr), (size_t)(n));                      \
+        if (e_ != cudaSuccess) {                                           \
+            dect::set_error(std::string("dect_admm_create: ") + cudaGetErrorString(e_)); \
+            free_admm(A);                                                  \
+            return DECT_ENOMEM;                                            \
+        }                                                                  \
+    } while (0)
+    ALLOC(A->ds, B);
+    for (float2** pp : {&A->x, &A->r, &A->s, &A->p, &A->Ap, &A->z, &A->uz, &A->x0, &A->truth}) ALLOC(*pp, A->n_img);
+    for (float2** pp : {&A->Rx, &A->a, &A->ua, &A->q}) ALLOC(*pp, A->n_sino);
+    ALLOC(A->y, A->n_img);
+    ALLOC(A->uy, A->n_img);
+    ALLOC(A->meas, A->n_sino);
+    ALLOC(A->txb, A->n_tx);
+    ALLOC(A->tyb, A->n_ty);
+    ALLOC(A->mu, A->n_sino);
+    ALLOC(A->status, A->n_sino);
+    ALLOC(A->Z, A->n_fft);
+    ALLOC(A->H, A->n_h);
+    ALLOC(A->Hn, A->n_h);
+    ALLOC(A->stage, A->n_stage);
+    ALLOC(A->sc, B);
+    ALLOC(A->d_has_x0, B);
+#undef ALLOC
+    const int np_blk = A->pix.h.back(), nr_blk = A->rays.h.back();
+    cudaError_t e = dalloc(&A->part_udm, 4 * (size_t)nr_blk);
+    if (e == cudaSuccess) e = dalloc(&A->part_img, 4 * (size_t)np_blk);
+    if (e == cudaSuccess) e = dalloc(&A->part_xi, 4 * (size_t)np_blk);
+    if (e == cudaSuccess) e = dalloc(&A->part_rs, 2 * (size_t)A->rows.h.back());
+    if (e == cudaSuccess) e = dalloc(&A->part_pap, 2 * (size_t)A->bp.h.back());
+    for (MapBuf* m : {&A->rays, &A->pix, &A->tx, &A->ty, &A->bp, &A->rows, &A->cols})
+        if (e == cudaSuccess) e = upload_map(*m);
+    if (e == cudaSuccess) e = cudaMemcpy(A->ds, A->hs.data(), sizeof(SliceDesc) * B, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemset(A->truth, 0, sizeof(float2) * A->n_img);
+    if (e == cudaSuccess) e = cudaMemset(A->status, 0, A->n_sino);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&A->cap, cudaStreamNonBlocking);
+    if (e == cudaSuccess) {
+        A->tw = fft_twiddles();
+        if (!A->tw) e = cudaErrorMemoryAllocation;
+    }
+    if (e != cudaSuccess) {
+        dect::set_error(std::string("dect_admm_create: ") + cudaGetErrorString(e));
+        free_admm(A);
+        return e == cudaErrorMemoryAllocation ? DECT_ENOMEM : DECT_ECUDA;
+    }
+    dect_status s = compute_responses(A);
+    if (s != DECT_OK) {
+        free_admm(A);
+        return s;
+    }
+    *out = A;
+    return DECT_OK;
+}
+
+extern "C" void dect_admm_destroy(dect_admm* A) {
+    if (!A) return;
+    cudaDeviceSynchronize();
+    free_admm(A);
+}
+
+static dect_status check_slice(const dect_admm* A, int32_t b) {
+    if (!A) DECT_FAIL(DECT_EINVAL, "dect_admm: null handle");
+    if (b < 0 || b >= A->B) DECT_FAIL(DECT_EINVAL, "dect_admm: slice index out of range");
+    return DECT_OK;
+}
+
+extern "C" dect_status dect_admm_set_data(dect_admm* A, int32_t b, const float* m_h, const float* m_l,
+                                          const float* w_h, const float* w_l, const float* x0, void* stream) {
+    clear_stale_error();
+    dect_status cs = check_slice(A, b);
+    if (cs != DECT_OK) return cs;
+    if (!m_h || !m_l || !w_h || !w_l) DECT_FAIL(DECT_EINVAL, "dect_admm_set_data: null measurement array");
+    cudaStream_t st = as_stream(stream);
+    const SliceDesc& sd = A->hs[b];
+    const int64_t nr = (int64_t)sd.g.nv * sd.g.nb, np = (int64_t)sd.g.nx * sd.g.ny;
+    const float* src[4] = {m_h, m_l, w_h, w_l};
+    for (int k = 0; k < 4; ++k)
+        CUDA_TRY(cudaMemcpyAsync(A->stage + k * nr, src[k], sizeof(float) * nr, cudaMemcpyDefault, st));
+    launch_pack_meas(A->stage, nr, A->meas + sd.sino_off, st);
+    if (x0) {
+        CUDA_TRY(cudaMemcpyAsync(A->stage + 4 * nr, x0, sizeof(float) * 2 * np, cudaMemcpyDefault, st));
+        launch_interleave(A->stage + 4 * nr, np, A->x0 + sd.img_off, st);
+    }
+    CUDA_TRY(cudaGetLastError());
+    A->has_x0[b] = x0 ? 1 : 0;
+    A->has_data[b] = 1;
+    A->initialized = false;
+    return DECT_OK;
+}
+
+extern "C" dect_status dect_admm_set_truth(dect_admm* A, int32_t b, const float* truth, void* stream) {
+    clear_stale_error();
+    dect_status cs = check_slice(A, b);
+    if (cs != DECT_OK) return cs;
+    cudaStream_t st = as_stream(stream);
+    const SliceDesc& sd = A->hs[b];
+    const int64_t np = (int64_t)sd.g.nx * sd.g.ny;
+    if (truth) {
+        CUDA_TRY(cudaMemcpyAsync(A->stage, truth, sizeof(float) * 2 * np, cudaMemcpyDefault, st));
+        launch_interleave(A->stage, np, A->truth + sd.img_off, st);
+    } else {
+        CUDA_TRY(cudaMemsetAsync(A->truth + sd.img_off, 0, sizeof(float2) * np, st));
+    }
+    CUDA_TRY(cudaGetLastError());
+    A->has_truth[b] = truth ? 1 : 0;
+    return DECT_OK;
+}
+
+static void count_iterations(dect_admm* A, int iters) {
+    A->cR += (int64_t)iters * 2 * A->P.n_pcg;
+    A->cRT += (int64_t)iters * 2 * (A->P.n_pcg + 1);
+    A->cF += (int64_t)iters * 4 * A->P.m_udm;
+    A->cL += (int64_t)iters * A->launches_per_iter;
+}
+
+static dect_status run_iterations(dect_admm* A, int iters, cudaStream_t st) {
+    if (A->P.use_graph) {
+        if (!A->gexec) {
+            dect_status s = capture_iteration(A, false, &A->gexec);
+            if (s != DECT_OK) return s;
+        }
+        for (int i = 0; i < iters; ++i) CUDA_TRY(cudaGraphLaunch(A->gexec, st));
+        count_iterations(A, iters);
+    } else {
+        for (int i = 0; i < iters; ++i) enq_iteration(A, st);
+    }
+    CUDA_TRY(cudaGetLastError());
+    return DECT_OK;
+}
+
+extern "C" dect_status dect_admm_profile(dect_admm* A, int32_t iters, void* stream, double* ms, int64_t* launches) {
+    clear_stale_error();
+    if (!A || !ms || !launches) DECT_FAIL(DECT_EINVAL, "dect_admm_profile: null argument");
+    if (iters < 0) DECT_FAIL(DECT_EINVAL, "dect_admm_profile: iters < 0");
+    cudaStream_t st = as_stream(stream);
+    if (!A->initialized) {
+        dect_status s = enq_initialize(A, st);
+        if (s != DECT_OK) return s;
+    }
+    if (A->prof_ev.empty()) {
+        A->prof_ev.resize(2 * kMaxProfGroups);
+        for (auto& e : A->prof_ev) CUDA_TRY(cudaEventCreate(&e));
+    }
+    if (!A->pgexec) {
+        dect_status s = capture_iteration(A, true, &A->pgexec);
+        if (s != DECT_OK) return s;
+    }
+    for (int i = 0; i < iters; ++i) {
+        CUDA_TRY(cudaGraphLaunch(A->pgexec, st));
+        CUDA_TRY(cudaStreamSynchronize(st));
+        for (int k = 0; k < A->prof_n; ++k) {
+            float t = 0.f;
+            CUDA_TRY(cudaEventElapsedTime(&t, A->prof_ev[2 * k], A->prof_ev[2 * k + 1]));
+            ms[A->prof_phase[k]] += t;
+            launches[A->prof_phase[k]] += A->prof_kernels[k];
+        }
+    }
+    count_iterations(A, iters);
+    return DECT_OK;
+}
+
+extern "C" dect_status dect_admm_step(dect_admm* A, int32_t iters, void* stream) {
+    clear_stale_error();
+    if (!A) DECT_FAIL(DECT_EINVAL, "dect_admm_step: null handle");
+    if (iters < 0) DECT_FAIL(DECT_EINVAL, "dect_admm_step: iters < 0");
+    cudaStream_t st = as_stream(stream);
+    if (!A->initialized) {
+        dect_status s = enq_initialize(A, st);
+        if (s != DECT_OK) return s;
+    }
+    return run_iterations(A, iters, st);
+}
+
+extern "C" dect_status dect_reconstruct(dect_admm* A, int32_t iters, void* stream) {
+    clear_stale_error();
+    if (!A) DECT_FAIL(DECT_EINVAL, "dect_reconstruct: null handle");
+    if (iters < 0) DECT_FAIL(DECT_EINVAL, "dect_reconstruct: iters < 0");
+    cudaStream_t st = as_stream(stream);
+    dect_status s = enq_initialize(A, st);
+    if (s != DECT_OK) return s;
+    return run_iterations(A, iters, st);
+}
+
+extern "C" dect_status dect_admm_get(const dect_admm* A, int32_t b, int32_t which, void* dst, size_t dst_bytes,
+                                     void* stream) {
+    clear_stale_error();
+    dect_status cs = check_slice(A, b);
+    if (cs != DECT_OK) return cs;
+    if (!dst) DECT_FAIL(DECT_EINVAL, "dect_admm_get: null destination");
+    cudaStream_t st = as_stream(stream);
+    const SliceDesc& sd = A->hs[b];
+    const int64_t np = (int64_t)sd.g.nx * sd.g.ny, nr = (int64_t)sd.g.nv * sd.g.nb;
+    size_t need = 0;
+    switch (which) {
+        case 0: case 6: case 7: need = sizeof(float) * 2 * np; break;
+        case 1: case 2: case 3: need = sizeof(float) * 2 * nr; break;
+        case 4: case 5: need = sizeof(float) * 4 * np; break;
+        case 8: need = sizeof(float) * nr; break;
+        case 9: need = sizeof(float) * (size_t)sd.px * sd.py; break;
+        default: DECT_FAIL(DECT_EINVAL, "dect_admm_get: unknown array");
+    }
+    if (dst_bytes < need) DECT_FAIL(DECT_EINVAL, "dect_admm_get: destination too small");
+    switch (which) {
+        case 0: launch_deinterleave2(A->x + sd.img_off, np, A->stage, st); break;
+        case 1: launch_deinterleave2(A->Rx + sd.sino_off, nr, A->stage, st); break;
+        case 2: launch_deinterleave2(A->a + sd.sino_off, nr, A->stage, st); break;
+        case 3: launch_deinterleave2(A->ua + sd.sino_off, nr, A->stage, st); break;
+        case 4: launch_deinterleave4(A->y + sd.img_off, np, A->stage, st); break;
+        case 5: launch_deinterleave4(A->uy + sd.img_off, np, A->stage, st); break;
+        case 6: launch_deinterleave2(A->z + sd.img_off, np, A->stage, st); break;
+        case 7: launch_deinterleave2(A->uz + sd.img_off, np, A->stage, st); break;
+        default: break;
+    }
+    if (which == 8)
+        CUDA_TRY(cudaMemcpyAsync(dst, A->mu + sd.sino_off, need, cudaMemcpyDefault, st));
+    else if (which == 9)
+        CUDA_TRY(cudaMemcpyAsync(dst, A->H + sd.h_off, need, cudaMemcpyDefault, st));
+    else
+        CUDA_TRY(cudaMemcpyAsync(dst, A->stage, need, cudaMemcpyDefault, st));
+    CUDA_TRY(cudaGetLastError());
+    return DECT_OK;
+}
+
+extern "C" dect_status dect_admm_stats(dect_admm* A, int32_t b, dect_stats* out, void* stream) {
+    clear_stale_error();
+    dect_status cs = check_slice(A, b);
+    if (cs != DECT_OK) return cs;
+    if (!out) DECT_FAIL(DECT_EINVAL, "dect_admm_stats: null output");
+    cudaStream_t st = as_stream(stream);
+    if (A->has_truth[b])
+        launch_xi(A->ds, A->pix.map(A->B), A->pix.total, A->x, A->truth, A->part_xi, A->sc, A->B, st);
+    SliceScalars v{};
+    CUDA_TRY(cudaMemcpyAsync(&v, A->sc + b, sizeof(v), cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaStreamSynchronize(st));
+    out->iteration = v.iteration;
+    for (int c = 0; c < 2; ++c) {
+        out->rho[c] = v.rho[c];
+        out->r_pri[c] = v.r_pri[c];
+        out->r_dual[c] = v.r_dual[c];
+        out->xi_db[c] = (A->has_truth[b] && v.xi_den[c] > 0) ? 10.0 * std::log10(v.xi_num[c] / v.xi_den[c]) : NAN;
+    }
+    out->count_R = A->cR;
+    out->count_RT = A->cRT;
+    out->count_f = A->cF;
+    out->count_launches = A->cL;
+    return DECT_OK;
+}

@@ -1,0 +1,164 @@
+// Internal declarations of the dect library (GB300, sm_103a).
+//
+// Data layout in device memory
+//  - Internal image vectors hold both bases interleaved: float2 {c, p} per
+//    pixel, row-major [ny][nx]. The TV split variables y, u^y hold float4
+//    {x-component c, y-component c, x-component p, y-component p}.
+//  - Internal sinogram vectors are float2 {c, p} per ray, [n_views][n_bins].
+//  - Measurements are float4 {m_h, m_l, w_h, w_l} per ray.
+//  - The projector reads the image through two "pair textures" (plain global
+//    arrays, no texture hardware): for rays sampled per column, TX[i][jj]
+//    = {c(jj-2,i), p(jj-2,i), c(jj-1,i), p(jj-1,i)} for jj in [0, ny+2], zero
+//    outside the image, so one 16-byte load gives both interpolation
+//    neighbours of both bases; TY[j][ii] is the same along rows.
+//  - Per-ray geometry table int4 {q0 low, q0 high, slope, +-w}: a ray with
+//    w > 0 (axis 0) is sampled at every column i at fractional row
+//    q0 + i * slope, q0 in 32.32 fixed point and slope in 2.30 fixed point,
+//    and weighted by w = pixel/|d_x|; w < 0 (axis 1) swaps rows and columns.
+//  - Batched solvers stack B slices in one allocation per array; a slice
+//    descriptor holds each slice's offsets and geometry.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/dect.h"
+
+namespace dect {
+
+constexpr int kMaxEnergies = 512;
+constexpr int kFftMaxLog2 = 12;  // padded FFT length up to 4096 per axis
+constexpr int kFftMax = 1 << kFftMaxLog2;
+
+// Geometry as the kernels see it (float copies for candidate searches).
+struct GeomDev {
+    int kind, nx, ny, nv, nb;
+    float pix, du, uoff, sod, sdd;
+    float cx, cy;           // (nx-1)/2, (ny-1)/2
+    const int4* rays;       // [nv*nb] {q0 lo, q0 hi, slope, +-w}
+    const float4* views;    // [nv] {cos, sin, 0, 0}
+};
+
+// One slice of a batched solver.
+struct SliceDesc {
+    GeomDev g;
+    int64_t img_off;    // pixel offset (elements) in image arrays
+    int64_t sino_off;   // ray offset in sinogram arrays
+    int64_t tx_off;     // float4 offset in TX (nx*(ny+3) per slice)
+    int64_t ty_off;     // float4 offset in TY (ny*(nx+3) per slice)
+    int64_t fft_off;    // complex offset in the FFT work buffer (py*px per slice)
+    int64_t h_off;      // float offset of the preconditioner response H [py][px]
+    int32_t px, py, lpx, lpy;   // padded FFT sizes and their log2
+};
+
+// Maps a flat block index to (slice, block within slice) by a prefix table.
+struct BlockMap {
+    const int* prefix;  // device, B+1 entries
+    int B;
+};
+
+__device__ __forceinline__ int slice_of(const BlockMap& m, int blk, int& local) {
+    int lo = 0, hi = m.B - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (__ldg(m.prefix + mid) <= blk) lo = mid; else hi = mid - 1;
+    }
+    local = blk - __ldg(m.prefix + lo);
+    return lo;
+}
+
+// Per-slice device scalars (CG, rho, residuals, monitors).
+struct SliceScalars {
+    double rho[2];
+    double factor[2];    // rescale factor applied to the duals this iteration (1 = none)
+    double rs[2];        // <r, M^-1 r>
+    double alpha[2];
+    double beta[2];
+    double pAp[2];
+    double r_pri[2];
+    double r_dual[2];
+    double xi_num[2], xi_den[2];
+    int32_t iteration;
+    int32_t pad;
+};
+
+// Spectral tables on the device: T1 = {k_kn, k_p, S_h, S_l}, T2 = {S_h f_KN, S_h f_p, S_l f_KN, S_l f_p}
+// with k = f * log2(e) so that exp(-f_KN a_c - f_p a_p) = exp2(-k_kn a_c - k_p a_p).
+struct SpecDev {
+    int ne;
+    const float4* t1;
+    const float4* t2;
+};
+
+// Epilogue modes of the gathering backprojector.
+enum BpMode {
+    BP_PLAIN = 0,      // out = R^T s
+    BP_R0 = 1,         // out = R^T b + D^T(y + u^y - D x) + (z + u^z - x)
+    BP_AP = 2,         // out = R^T q + D^T D p + p, partial <p, out>
+    BP_R0_NOGRAD = 3,  // out = R^T b + (z + u^z - x)
+    BP_AP_NOGRAD = 4,  // out = R^T q + p, partial <p, out>
+};
+
+struct BpEpilogue {
+    const float2* x;    // BP_R0*: current image
+    const float4* y;
+    const float4* uy;
+    const float2* z;
+    const float2* uz;
+    const float2* p;    // BP_AP*: direction
+    double* partial;    // BP_AP*: per-block {<p_c, Ap_c>, <p_p, Ap_p>}
+};
+
+// ---- launch helpers implemented in the .cu files ------------------------------------------
+
+// projector.cu
+cudaError_t build_ray_table(const dect_geom_desc& d, int4* rays, float4* views, cudaStream_t st);
+void launch_textures(const SliceDesc* dsl, const BlockMap& mx, int nbx, const BlockMap& my, int nby,
+                     const float2* img, float4* tx, float4* ty, cudaStream_t st);
+void launch_project(const SliceDesc* dsl, const BlockMap& map, int nblk, const float4* tx, const float4* ty,
+                    float2* out_interleaved, cudaStream_t st);
+void launch_backproject(int mode, const SliceDesc* dsl, const BlockMap& map, int nblk, const float2* sino,
+                        float2* out, const BpEpilogue& ep, cudaStream_t st);
+void project_single(const SliceDesc& sd, const float* img, int nch, float2* scratch, float4* tx, float4* ty,
+                    float* out, cudaStream_t st);
+void backproject_single(const SliceDesc& sd, const float* sino, int nch, float2* packed, float* out,
+                        cudaStream_t st);
+int bp_tiles(int nx, int ny);
+int texture_x_blocks(int nx, int ny);
+int texture_y_blocks(int nx, int ny);
+constexpr int kRaysPerBlock = 256;
+constexpr int kPixPerBlock = 256;
+constexpr int kBpTile = 16;
+
+// udm.cu
+void launch_udm_admm(const SliceDesc* dsl, const BlockMap& map, int nblk, const SpecDev& sp, const float4* meas,
+                     const float2* Rx, float2* ua, float2* a, float* mu, uint8_t* status,
+                     const SliceScalars* sc, int iters, double* partial, cudaStream_t st);
+void launch_udm_init(const SliceDesc* dsl, const BlockMap& map, int nblk, const SpecDev& sp, const float4* meas,
+                     float2* a, float* mu, double rho_p, int iters, float abar, double mu0, cudaStream_t st);
+void launch_udm_rays(const SpecDev& sp, int64_t n, const float* mh, const float* ml, const float* wh,
+                     const float* wl, const float* vc, const float* vp, double rho_c, double rho_p, int iters,
+                     float* ac, float* ap, float* mu, uint8_t* status, cudaStream_t st);
+
+// fft.cu
+const float2* fft_twiddles();   // device table exp(-2 pi i t / kFftMax), t < kFftMax/2 (current device)
+__host__ __device__ int precond_cols_per_block(int py);
+// s = M^-1 r per slice and partial[2*blk] = <r, s> per channel over the row blocks
+void launch_precond(const SliceDesc* dsl, const BlockMap& rows_map, int nrows_blk, const BlockMap& cols_map,
+                    int ncols_blk, const float* H, const float2* r, float2* s, float2* Z, double* partial_rs,
+                    const float2* tw, int max_px, int max_py, cudaStream_t st);
+// H (and the variant without the D^T D term) from R^T R applied to a centred impulse (one slice)
+// (d_dev: the slice's descriptor on the device with fft_off = h_off = 0; cols_map: its column groups)
+void launch_psf_to_response(const SliceDesc* d_dev, const SliceDesc& d, const BlockMap& cols_map, int ncols,
+                            const float2* psf, float2* Z, float* H, float* H_nograd, const float2* tw,
+                            cudaStream_t st);
+cudaError_t fft_init_attributes();
+
+// admm.cu helpers are local to that file.
+
+// ---- error handling ----------------------------------------------------------------------
+void set_error(const std::string& msg);
+
+}  // namespace dect

@@ -1,0 +1,270 @@
+// Preconditioner of the Eq. 12 conjugate-gradient solve (Sec. 3.3: the system
+// is shift-invariant once the statistical weights move into the decomposition
+// step, so it is preconditioned by a high-pass filter applied by FFT).
+//
+// M^-1 r = crop(IDFT2(H * DFT2(zero-pad(r)))) on a [py][px] grid (powers of two
+// >= 2N). H is real and even, so one complex transform carries both bases:
+// the Compton image in the real part and the PE image in the imaginary part.
+// Three kernels: forward row FFTs of the ny non-zero rows; per column group a
+// forward column FFT, the multiplication by H and the inverse column FFT (rows
+// >= ny are known zeros on input and are not needed on output); inverse row
+// FFTs of the ny rows, cropped to nx, fused with the partial sums of <r, s>.
+// The FFTs are radix-2 decimation in time in shared memory with a float32
+// twiddle table computed once in float64 on the host.
+#include <cuda_runtime.h>
+#include <math.h>
+
+#include <mutex>
+#include <vector>
+
+#include "dect_internal.cuh"
+
+namespace dect {
+
+static std::mutex g_tw_mu;
+static std::vector<float2*> g_tw;  // per device
+
+const float2* fft_twiddles() {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::lock_guard<std::mutex> lk(g_tw_mu);
+    if ((int)g_tw.size() <= dev) g_tw.resize(dev + 1, nullptr);
+    if (!g_tw[dev]) {
+        std::vector<float2> h(kFftMax / 2);
+        for (int t = 0; t < kFftMax / 2; ++t) {
+            const double th = 2.0 * M_PI * (double)t / (double)kFftMax;
+            h[t] = make_float2((float)cos(th), (float)(-sin(th)));
+        }
+        float2* d = nullptr;
+        if (cudaMalloc(&d, sizeof(float2) * h.size()) != cudaSuccess) return nullptr;
+        if (cudaMemcpy(d, h.data(), sizeof(float2) * h.size(), cudaMemcpyHostToDevice) != cudaSuccess) {
+            cudaFree(d);
+            return nullptr;
+        }
+        g_tw[dev] = d;
+    }
+    return g_tw[dev];
+}
+
+__device__ __forceinline__ int bitrev(int t, int logn) { return (int)(__brev((unsigned)t) >> (32 - logn)); }
+
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+    return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+}
+
+// In-place FFT of length 2^logn on a bit-reversed shared buffer; `lane`/`nlanes` split the butterflies.
+// Every thread of the block must call it (it synchronises the block after each stage).
+__device__ void fft_stages(float2* buf, int logn, bool inverse, const float2* __restrict__ tw, int lane, int nlanes) {
+    const int n = 1 << logn;
+    for (int s = 0; s < logn; ++s) {
+        const int half = 1 << s;
+        const int stride = kFftMax >> (s + 1);
+        for (int b = lane; b < n / 2; b += nlanes) {
+            const int pos = b & (half - 1);
+            const int i0 = ((b >> s) << (s + 1)) + pos;
+            const int i1 = i0 + half;
+            float2 w = __ldg(tw + pos * stride);
+            if (inverse) w.y = -w.y;
+            const float2 x0 = buf[i0];
+            const float2 t = cmul(w, buf[i1]);
+            buf[i0] = make_float2(x0.x + t.x, x0.y + t.y);
+            buf[i1] = make_float2(x0.x - t.x, x0.y - t.y);
+        }
+        __syncthreads();
+    }
+}
+
+// In-place bit-reversal permutation of a shared buffer (natural <-> bit-reversed order).
+__device__ void bitrev_permute(float2* buf, int logn, int lane, int nlanes) {
+    const int n = 1 << logn;
+    for (int t = lane; t < n; t += nlanes) {
+        const int r = bitrev(t, logn);
+        if (t < r) {
+            const float2 a = buf[t];
+            buf[t] = buf[r];
+            buf[r] = a;
+        }
+    }
+    __syncthreads();
+}
+
+__host__ __device__ int precond_cols_per_block(int py) { return py >= 4096 ? 2 : (py >= 2048 ? 4 : 8); }
+
+// forward row FFTs of the image rows (Compton + i PE), zero-padded to px
+__global__ void __launch_bounds__(256) k_prec_rows_fwd(const SliceDesc* __restrict__ dsl, BlockMap map,
+                                                       const float2* __restrict__ r, float2* __restrict__ Z,
+                                                       const float2* __restrict__ tw) {
+    extern __shared__ float2 buf[];
+    int j;
+    const int s = slice_of(map, blockIdx.x, j);
+    const SliceDesc& d = dsl[s];
+    const int px = d.px, lp = d.lpx, nx = d.g.nx;
+    const float2* row = r + d.img_off + (size_t)j * nx;
+    for (int t = threadIdx.x; t < px; t += blockDim.x)
+        buf[bitrev(t, lp)] = t < nx ? __ldg(row + t) : make_float2(0.f, 0.f);
+    __syncthreads();
+    fft_stages(buf, lp, false, tw, threadIdx.x, blockDim.x);
+    float2* zr = Z + d.fft_off + (size_t)j * px;
+    for (int t = threadIdx.x; t < px; t += blockDim.x) zr[t] = buf[t];
+}
+
+// per group of columns: forward column FFT (rows >= rows_in are zero), optional multiplication by H,
+// inverse column FFT; writes rows [0, rows_out)
+__global__ void __launch_bounds__(256) k_fft_cols(const SliceDesc* __restrict__ dsl, BlockMap map,
+                                                  float2* __restrict__ Z, const float* __restrict__ H, int rows_in_all,
+                                                  int rows_out_all, const float2* __restrict__ tw) {
+    extern __shared__ float2 buf[];
+    int g;
+    const int s = slice_of(map, blockIdx.x, g);
+    const SliceDesc& d = dsl[s];
+    const int px = d.px, py = d.py, lp = d.lpy;
+    const int C = precond_cols_per_block(py);
+    const int k0 = g * C;
+    const int rows_in = rows_in_all ? py : d.g.ny;
+    const int rows_out = rows_out_all ? py : d.g.ny;
+    float2* zs = Z + d.fft_off;
+    // load: consecutive threads take consecutive columns of one row
+    for (int e = threadIdx.x; e < C * py; e += blockDim.x) {
+        const int c = e % C, j = e / C;
+        const int k = k0 + c;
+        float2 v = make_float2(0.f, 0.f);
+        if (j < rows_in && k < px) v = zs[(size_t)j * px + k];
+        buf[c * py + bitrev(j, lp)] = v;
+    }
+    __syncthreads();
+    const int lanes = blockDim.x / C;
+    const int c = threadIdx.x / lanes, lane = threadIdx.x % lanes;
+    fft_stages(buf + c * py, lp, false, tw, lane, lanes);
+    if (H) {
+        const float* hs = H + d.h_off;
+        for (int e = threadIdx.x; e < C * py; e += blockDim.x) {
+            const int cc = e % C, j = e / C;
+            const int k = k0 + cc;
+            const float h = k < px ? __ldg(hs + (size_t)j * px + k) : 0.f;
+            float2& v = buf[cc * py + j];
+            v.x *= h;
+            v.y *= h;
+        }
+        __syncthreads();
+        bitrev_permute(buf + c * py, lp, lane, lanes);
+        fft_stages(buf + c * py, lp, true, tw, lane, lanes);
+    }
+    for (int e = threadIdx.x; e < C * rows_out; e += blockDim.x) {
+        const int cc = e % C, j = e / C;
+        const int k = k0 + cc;
+        if (k < px) zs[(size_t)j * px + k] = buf[cc * py + j];
+    }
+}
+
+// inverse row FFTs, crop to nx, scale by 1/(px*py): s = {Re, Im}; partial <r, s> per channel
+__global__ void __launch_bounds__(256) k_prec_rows_inv(const SliceDesc* __restrict__ dsl, BlockMap map,
+                                                       const float2* __restrict__ Z, const float2* __restrict__ r,
+                                                       float2* __restrict__ s_out, double* __restrict__ partial,
+                                                       const float2* __restrict__ tw) {
+    extern __shared__ float2 buf[];
+    int j;
+    const int s = slice_of(map, blockIdx.x, j);
+    const SliceDesc& d = dsl[s];
+    const int px = d.px, lp = d.lpx, nx = d.g.nx;
+    const float2* zr = Z + d.fft_off + (size_t)j * px;
+    for (int t = threadIdx.x; t < px; t += blockDim.x) buf[bitrev(t, lp)] = zr[t];
+    __syncthreads();
+    fft_stages(buf, lp, true, tw, threadIdx.x, blockDim.x);
+    const float scale = 1.0f / ((float)px * (float)d.py);
+    double dc = 0.0, dp = 0.0;
+    const size_t row = d.img_off + (size_t)j * nx;
+    for (int t = threadIdx.x; t < nx; t += blockDim.x) {
+        const float2 v = make_float2(buf[t].x * scale, buf[t].y * scale);
+        s_out[row + t] = v;
+        const float2 rv = __ldg(r + row + t);
+        dc += (double)rv.x * v.x;
+        dp += (double)rv.y * v.y;
+    }
+    __shared__ double red[2][8];
+    for (int o = 16; o > 0; o >>= 1) {
+        dc += __shfl_down_sync(0xffffffffu, dc, o);
+        dp += __shfl_down_sync(0xffffffffu, dp, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        red[0][threadIdx.x / 32] = dc;
+        red[1][threadIdx.x / 32] = dp;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double a = 0.0, b = 0.0;
+        for (int w = 0; w < (int)blockDim.x / 32; ++w) {
+            a += red[0][w];
+            b += red[1][w];
+        }
+        partial[2 * (size_t)blockIdx.x] = a;
+        partial[2 * (size_t)blockIdx.x + 1] = b;
+    }
+}
+
+void launch_precond(const SliceDesc* dsl, const BlockMap& rows_map, int nrows_blk, const BlockMap& cols_map,
+                    int ncols_blk, const float* H, const float2* r, float2* s, float2* Z, double* partial_rs,
+                    const float2* tw, int max_px, int max_py, cudaStream_t st) {
+    k_prec_rows_fwd<<<nrows_blk, 256, sizeof(float2) * max_px, st>>>(dsl, rows_map, r, Z, tw);
+    (void)max_py;
+    // C(py) * py <= 8192 complex entries for every py <= 4096
+    k_fft_cols<<<ncols_blk, 256, sizeof(float2) * 8192, st>>>(dsl, cols_map, Z, H, 0, 0, tw);
+    k_prec_rows_inv<<<nrows_blk, 256, sizeof(float2) * max_px, st>>>(dsl, rows_map, Z, r, s, partial_rs, tw);
+}
+
+// ---- response H from the point response of R^T R ---------------------------------------------
+
+__global__ void k_embed_psf(SliceDesc d, const float2* __restrict__ psf, float2* __restrict__ Z) {
+    const int64_t n = (int64_t)d.px * d.py;
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n) return;
+    const int k = (int)(e / d.px), l = (int)(e % d.px);
+    // grid index (k, l) holds the response at pixel (jc + k, ic + l) modulo the padded size
+    const int jc = d.g.ny / 2, ic = d.g.nx / 2;
+    int j = k < d.py / 2 ? jc + k : jc + k - d.py;
+    int i = l < d.px / 2 ? ic + l : ic + l - d.px;
+    float v = 0.f;
+    if (j >= 0 && j < d.g.ny && i >= 0 && i < d.g.nx) v = psf[(size_t)j * d.g.nx + i].x;
+    Z[e] = make_float2(v, 0.f);
+}
+
+__global__ void __launch_bounds__(256) k_fft_rows_full(SliceDesc d, float2* __restrict__ Z,
+                                                       const float2* __restrict__ tw) {
+    extern __shared__ float2 buf[];
+    const int j = blockIdx.x;
+    const int px = d.px, lp = d.lpx;
+    float2* zr = Z + (size_t)j * px;
+    for (int t = threadIdx.x; t < px; t += blockDim.x) buf[bitrev(t, lp)] = zr[t];
+    __syncthreads();
+    fft_stages(buf, lp, false, tw, threadIdx.x, blockDim.x);
+    for (int t = threadIdx.x; t < px; t += blockDim.x) zr[t] = buf[t];
+}
+
+__global__ void k_response(SliceDesc d, const float2* __restrict__ Z, float* __restrict__ H,
+                           float* __restrict__ Hn) {
+    const int64_t n = (int64_t)d.px * d.py;
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n) return;
+    const int k = (int)(e / d.px), l = (int)(e % d.px);
+    const double wy = 2.0 * M_PI * k / d.py, wx = 2.0 * M_PI * l / d.px;
+    const double sy = sin(0.5 * wy), sx = sin(0.5 * wx);
+    const double dhat = 4.0 * sy * sy + 4.0 * sx * sx;
+    const double phat = fmax((double)Z[e].x, 0.0);
+    H[e] = (float)(1.0 / (phat + dhat + 1.0));
+    Hn[e] = (float)(1.0 / (phat + 1.0));
+}
+
+void launch_psf_to_response(const SliceDesc* d_dev, const SliceDesc& d, const BlockMap& cols_map, int ncols,
+                            const float2* psf, float2* Z, float* H, float* H_nograd, const float2* tw,
+                            cudaStream_t st) {
+    const int64_t n = (int64_t)d.px * d.py;
+    k_embed_psf<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(d, psf, Z);
+    k_fft_rows_full<<<d.py, 256, sizeof(float2) * d.px, st>>>(d, Z, tw);
+    k_fft_cols<<<ncols, 256, sizeof(float2) * 8192, st>>>(d_dev, cols_map, Z, nullptr, 1, 1, tw);
+    k_response<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(d, Z, H, H_nograd);
+}
+
+cudaError_t fft_init_attributes() {
+    return cudaFuncSetAttribute(k_fft_cols, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(sizeof(float2) * 8192));
+}
+
+}  // namespace dect

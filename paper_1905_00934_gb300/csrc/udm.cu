@@ -1,0 +1,287 @@
+// Per-ray dual-energy decomposition, Eq. 13 (the "UDM" subproblem of the
+// splitting scheme, Sec. 3.3), by Levenberg-Marquardt.
+//
+// One thread per ray; the spectral tables sit in shared memory and every
+// lane reads the same entry (broadcast). Per LM iteration the thread
+// evaluates f_h, f_l and their Jacobian at a (one pass over the energies:
+// one exp2 and six FMAs per bin) and f_h, f_l at the trial point a + delta
+// (one exp2 and two FMAs per bin): the 4 evaluations of f of Table 1. Energy
+// sums are float32; the logs of the spectral sums, the cost and the 2x2 solve
+// are float64, where the photoelectric coordinate (whose Jacobian column is
+// orders of magnitude below the Compton one) needs the range.
+#include <cuda_runtime.h>
+#include <math.h>
+
+#include "dect_internal.cuh"
+
+namespace dect {
+
+struct RayIn {
+    double mh, ml, wh, wl, vc, vp, rc, rp;
+};
+
+struct LmState {
+    float ac, ap, mu;
+    uint8_t status;
+};
+
+// Compensated addition of a block partial into a running sum (Kahan): keeps the spectral sums,
+// whose logs enter the LM accept test, accurate to a few float32 ulps of the exponentials.
+__device__ __forceinline__ void kahan_add(float& sum, float& comp, float v) {
+    const float y = v - comp;
+    const float t = sum + y;
+    comp = (t - sum) - y;
+    sum = t;
+}
+
+// s_h, s_l (compensated, in blocks of 8 energies) and the four Jacobian numerators at (ac, ap).
+__device__ __forceinline__ void spectral_sums_jac(const float4* __restrict__ t1, const float4* __restrict__ t2, int ne,
+                                                  float ac, float ap, float& sh, float& sl, float& shc, float& shp,
+                                                  float& slc, float& slp) {
+    float ch = 0.f, cl = 0.f;
+    sh = sl = shc = shp = slc = slp = 0.f;
+    for (int e0 = 0; e0 < ne; e0 += 8) {
+        float bh = 0.f, bl = 0.f;
+        const int e1 = min(e0 + 8, ne);
+        for (int e = e0; e < e1; ++e) {
+            const float4 a = t1[e];
+            const float4 b = t2[e];
+            const float t = exp2f(-fmaf(a.x, ac, a.y * ap));
+            bh = fmaf(a.z, t, bh);
+            bl = fmaf(a.w, t, bl);
+            shc = fmaf(b.x, t, shc);
+            shp = fmaf(b.y, t, shp);
+            slc = fmaf(b.z, t, slc);
+            slp = fmaf(b.w, t, slp);
+        }
+        kahan_add(sh, ch, bh);
+        kahan_add(sl, cl, bl);
+    }
+}
+
+__device__ __forceinline__ void spectral_sums(const float4* __restrict__ t1, int ne, float ac, float ap, float& sh,
+                                              float& sl) {
+    float ch = 0.f, cl = 0.f;
+    sh = sl = 0.f;
+    for (int e0 = 0; e0 < ne; e0 += 8) {
+        float bh = 0.f, bl = 0.f;
+        const int e1 = min(e0 + 8, ne);
+        for (int e = e0; e < e1; ++e) {
+            const float4 a = t1[e];
+            const float t = exp2f(-fmaf(a.x, ac, a.y * ap));
+            bh = fmaf(a.z, t, bh);
+            bl = fmaf(a.w, t, bl);
+        }
+        kahan_add(sh, ch, bh);
+        kahan_add(sl, cl, bl);
+    }
+}
+
+__device__ __forceinline__ double ray_cost(double fh, double fl, double ac, double ap, const RayIn& in) {
+    const double rh = fh - in.mh, rl = fl - in.ml;
+    const double dc = ac - in.vc, dp = ap - in.vp;
+    return 0.5 * (in.wh * rh * rh + in.wl * rl * rl) + 0.5 * (in.rc * dc * dc + in.rp * dp * dp);
+}
+
+// `iters` LM iterations of Eq. 13 for one ray (tables t1/t2 in shared memory).
+__device__ void lm_ray(const float4* __restrict__ t1, const float4* __restrict__ t2, int ne, const RayIn& in,
+                       int iters, LmState& s) {
+    for (int it = 0; it < iters; ++it) {
+        float sh, sl, shc, shp, slc, slp;
+        spectral_sums_jac(t1, t2, ne, s.ac, s.ap, sh, sl, shc, shp, slc, slp);
+        const double fh = -log((double)sh), fl = -log((double)sl);
+        const double ish = 1.0 / (double)sh, isl = 1.0 / (double)sl;
+        const double j0 = shc * ish, j1 = shp * ish, j2 = slc * isl, j3 = slp * isl;
+        const double rh = fh - in.mh, rl = fl - in.ml;
+        const double g0 = in.wh * rh * j0 + in.wl * rl * j2 + in.rc * ((double)s.ac - in.vc);
+        const double g1 = in.wh * rh * j1 + in.wl * rl * j3 + in.rp * ((double)s.ap - in.vp);
+        const double A00 = in.wh * j0 * j0 + in.wl * j2 * j2 + in.rc;
+        const double A01 = in.wh * j0 * j1 + in.wl * j2 * j3;
+        const double A11 = in.wh * j1 * j1 + in.wl * j3 * j3 + in.rp;
+        const double m1 = 1.0 + (double)s.mu;
+        const double B00 = A00 * m1, B11 = A11 * m1;
+        const double det = B00 * B11 - A01 * A01;
+        const double cost0 = ray_cost(fh, fl, s.ac, s.ap, in);
+        if (!(det > 0.0) || !isfinite(det) || !isfinite(cost0)) {
+            s.status = DECT_RAY_NONFINITE;
+            break;
+        }
+        const double d0 = (-g0 * B11 + g1 * A01) / det;
+        const double d1 = (-g1 * B00 + g0 * A01) / det;
+        const float tc = (float)((double)s.ac + d0), tp = (float)((double)s.ap + d1);
+        float th, tl;
+        spectral_sums(t1, ne, tc, tp, th, tl);
+        const double cost1 = ray_cost(-log((double)th), -log((double)tl), tc, tp, in);
+        float mu = s.mu;
+        if (!isfinite(cost1)) {
+            mu *= 10.f;
+            s.status = DECT_RAY_NONFINITE;
+        } else if (cost1 < cost0) {
+            s.ac = tc;
+            s.ap = tp;
+            mu *= 0.1f;
+            s.status = DECT_RAY_ACCEPTED;
+        } else {
+            mu *= 10.f;
+            s.status = DECT_RAY_REJECTED;
+        }
+        s.mu = fminf(fmaxf(mu, 1e-10f), 1e10f);
+    }
+}
+
+__device__ __forceinline__ void load_tables(const SpecDev& sp, float4* t1, float4* t2) {
+    for (int e = threadIdx.x; e < sp.ne; e += blockDim.x) {
+        t1[e] = __ldg(sp.t1 + e);
+        t2[e] = __ldg(sp.t2 + e);
+    }
+    __syncthreads();
+}
+
+// ADMM a-update fused with the a-block of the dual update (Eq. 11) and the a-block residual sums:
+// partial[4*blk + {0,1}] = sum (a - Rx)^2 (c, p); partial[4*blk + {2,3}] = sum (a - a_old)^2.
+__global__ void __launch_bounds__(kRaysPerBlock) k_udm_admm(const SliceDesc* __restrict__ dsl, BlockMap map, SpecDev sp,
+                                                            const float4* __restrict__ meas,
+                                                            const float2* __restrict__ Rx, float2* __restrict__ ua,
+                                                            float2* __restrict__ a, float* __restrict__ mu,
+                                                            uint8_t* __restrict__ status,
+                                                            const SliceScalars* __restrict__ sc, int iters,
+                                                            double* __restrict__ partial) {
+    extern __shared__ float4 tabs[];
+    float4* t1 = tabs;
+    float4* t2 = tabs + sp.ne;
+    load_tables(sp, t1, t2);
+    int local;
+    const int s = slice_of(map, blockIdx.x, local);
+    const SliceDesc& d = dsl[s];
+    const int64_t n = (int64_t)d.g.nv * d.g.nb;
+    const int64_t r = (int64_t)local * kRaysPerBlock + threadIdx.x;
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    if (r < n) {
+        const int64_t e = d.sino_off + r;
+        const float4 m = __ldg(meas + e);
+        const float2 rx = __ldg(Rx + e);
+        float2 u = ua[e];
+        const float2 a_old = a[e];
+        RayIn in;
+        in.mh = m.x;
+        in.ml = m.y;
+        in.wh = m.z;
+        in.wl = m.w;
+        in.vc = (double)rx.x - (double)u.x;
+        in.vp = (double)rx.y - (double)u.y;
+        in.rc = sc[s].rho[0];
+        in.rp = sc[s].rho[1];
+        LmState st{a_old.x, a_old.y, mu[e], DECT_RAY_ACCEPTED};
+        lm_ray(t1, t2, sp.ne, in, iters, st);
+        a[e] = make_float2(st.ac, st.ap);
+        mu[e] = st.mu;
+        if (status) status[e] = st.status;
+        const float rc = st.ac - rx.x, rp = st.ap - rx.y;
+        u.x += rc;
+        u.y += rp;
+        ua[e] = u;
+        const float dc = st.ac - a_old.x, dp = st.ap - a_old.y;
+        acc[0] = (double)rc * rc;
+        acc[1] = (double)rp * rp;
+        acc[2] = (double)dc * dc;
+        acc[3] = (double)dp * dp;
+    }
+    __shared__ double red[4][kRaysPerBlock / 32];
+    for (int q = 0; q < 4; ++q)
+        for (int o = 16; o > 0; o >>= 1) acc[q] += __shfl_down_sync(0xffffffffu, acc[q], o);
+    const int w = threadIdx.x / 32;
+    if ((threadIdx.x & 31) == 0)
+        for (int q = 0; q < 4; ++q) red[q][w] = acc[q];
+    __syncthreads();
+    if (threadIdx.x < 4) {
+        double t = 0.0;
+        for (int k = 0; k < kRaysPerBlock / 32; ++k) t += red[threadIdx.x][k];
+        partial[4 * (size_t)blockIdx.x + threadIdx.x] = t;
+    }
+}
+
+// Initial decomposition: rho = (0, rho_p), v = 0, from a = (m_l / abar, 0), mu = mu0.
+__global__ void __launch_bounds__(kRaysPerBlock) k_udm_init(const SliceDesc* __restrict__ dsl, BlockMap map, SpecDev sp,
+                                                            const float4* __restrict__ meas, float2* __restrict__ a,
+                                                            float* __restrict__ mu, double rho_p, int iters,
+                                                            float abar, float mu0) {
+    extern __shared__ float4 tabs[];
+    float4* t1 = tabs;
+    float4* t2 = tabs + sp.ne;
+    load_tables(sp, t1, t2);
+    int local;
+    const int s = slice_of(map, blockIdx.x, local);
+    const SliceDesc& d = dsl[s];
+    const int64_t n = (int64_t)d.g.nv * d.g.nb;
+    const int64_t r = (int64_t)local * kRaysPerBlock + threadIdx.x;
+    if (r >= n) return;
+    const int64_t e = d.sino_off + r;
+    const float4 m = __ldg(meas + e);
+    RayIn in;
+    in.mh = m.x;
+    in.ml = m.y;
+    in.wh = m.z;
+    in.wl = m.w;
+    in.vc = 0.0;
+    in.vp = 0.0;
+    in.rc = 0.0;
+    in.rp = rho_p;
+    LmState st{m.y / abar, 0.0f, mu0, DECT_RAY_ACCEPTED};
+    lm_ray(t1, t2, sp.ne, in, iters, st);
+    a[e] = make_float2(st.ac, 0.0f);
+    mu[e] = mu0;
+}
+
+// Public per-ray entry point (planar float arrays).
+__global__ void __launch_bounds__(kRaysPerBlock) k_udm_rays(SpecDev sp, int64_t n, const float* __restrict__ mh,
+                                                            const float* __restrict__ ml, const float* __restrict__ wh,
+                                                            const float* __restrict__ wl, const float* __restrict__ vc,
+                                                            const float* __restrict__ vp, double rho_c, double rho_p,
+                                                            int iters, float* __restrict__ ac, float* __restrict__ ap,
+                                                            float* __restrict__ mu, uint8_t* __restrict__ status) {
+    extern __shared__ float4 tabs[];
+    float4* t1 = tabs;
+    float4* t2 = tabs + sp.ne;
+    load_tables(sp, t1, t2);
+    const int64_t r = (int64_t)blockIdx.x * kRaysPerBlock + threadIdx.x;
+    if (r >= n) return;
+    RayIn in;
+    in.mh = __ldg(mh + r);
+    in.ml = __ldg(ml + r);
+    in.wh = __ldg(wh + r);
+    in.wl = __ldg(wl + r);
+    in.vc = __ldg(vc + r);
+    in.vp = __ldg(vp + r);
+    in.rc = rho_c;
+    in.rp = rho_p;
+    LmState st{ac[r], ap[r], mu[r], DECT_RAY_ACCEPTED};
+    lm_ray(t1, t2, sp.ne, in, iters, st);
+    ac[r] = st.ac;
+    ap[r] = st.ap;
+    mu[r] = st.mu;
+    if (status) status[r] = st.status;
+}
+
+static size_t tab_bytes(const SpecDev& sp) { return 2 * sizeof(float4) * (size_t)sp.ne; }
+
+void launch_udm_admm(const SliceDesc* dsl, const BlockMap& map, int nblk, const SpecDev& sp, const float4* meas,
+                     const float2* Rx, float2* ua, float2* a, float* mu, uint8_t* status, const SliceScalars* sc,
+                     int iters, double* partial, cudaStream_t st) {
+    k_udm_admm<<<nblk, kRaysPerBlock, tab_bytes(sp), st>>>(dsl, map, sp, meas, Rx, ua, a, mu, status, sc, iters,
+                                                            partial);
+}
+
+void launch_udm_init(const SliceDesc* dsl, const BlockMap& map, int nblk, const SpecDev& sp, const float4* meas,
+                     float2* a, float* mu, double rho_p, int iters, float abar, double mu0, cudaStream_t st) {
+    k_udm_init<<<nblk, kRaysPerBlock, tab_bytes(sp), st>>>(dsl, map, sp, meas, a, mu, rho_p, iters, abar, (float)mu0);
+}
+
+void launch_udm_rays(const SpecDev& sp, int64_t n, const float* mh, const float* ml, const float* wh, const float* wl,
+                     const float* vc, const float* vp, double rho_c, double rho_p, int iters, float* ac, float* ap,
+                     float* mu, uint8_t* status, cudaStream_t st) {
+    if (n <= 0) return;
+    k_udm_rays<<<(unsigned)((n + kRaysPerBlock - 1) / kRaysPerBlock), kRaysPerBlock, tab_bytes(sp), st>>>(
+        sp, n, mh, ml, wh, wl, vc, vp, rho_c, rho_p, iters, ac, ap, mu, status);
+}
+
+}  // namespace dect

@@ -1,0 +1,247 @@
+"""Thin Python binding of the dect C ABI (include/dect.h): argument marshalling only.
+
+Every function forwards to the CUDA library libdect.so built in-tree by
+`paper_1905_00934_gb300.build`. There is no CPU fallback: if the library is
+missing or no CUDA device is present, the calls raise.
+
+Tensors are torch tensors; device buffers are passed by data pointer and the
+call is enqueued on the current torch CUDA stream unless a stream is given.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libdect.so")
+
+OK, EINVAL, ENOMEM, ECUDA, EUNSUPPORTED, ETIMEOUT, ENOTCONV = range(7)
+PARALLEL, FAN_FLAT = 0, 1
+F32 = 0
+RAY_ACCEPTED, RAY_REJECTED, RAY_NONFINITE = 0, 1, 2
+# dect_admm_get array selectors
+X, RX, A, UA, Y, UY, Z, UZ, MU, H = range(10)
+
+
+class DectError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"dect status {status}: {msg}")
+        self.status = status
+
+
+class GeomDesc(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("nx", ctypes.c_int32), ("ny", ctypes.c_int32),
+                ("n_views", ctypes.c_int32), ("n_bins", ctypes.c_int32), ("pixel_cm", ctypes.c_double),
+                ("angle0_rad", ctypes.c_double), ("angle_span_rad", ctypes.c_double),
+                ("bin_pitch_cm", ctypes.c_double), ("bin_offset_cm", ctypes.c_double),
+                ("sod_cm", ctypes.c_double), ("sdd_cm", ctypes.c_double)]
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("lambda_c", ctypes.c_double), ("lambda_p", ctypes.c_double), ("rho0_c", ctypes.c_double),
+                ("rho0_p", ctypes.c_double), ("m_udm", ctypes.c_int32), ("n_pcg", ctypes.c_int32),
+                ("rho_mu", ctypes.c_double), ("rho_tau", ctypes.c_double), ("lm_mu0", ctypes.c_double),
+                ("kappa", ctypes.c_double), ("init_udm_iters", ctypes.c_int32), ("init_pcg_iters", ctypes.c_int32),
+                ("precondition", ctypes.c_int32), ("use_graph", ctypes.c_int32)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("iteration", ctypes.c_int32), ("rho", ctypes.c_double * 2), ("r_pri", ctypes.c_double * 2),
+                ("r_dual", ctypes.c_double * 2), ("xi_db", ctypes.c_double * 2), ("count_R", ctypes.c_int64),
+                ("count_RT", ctypes.c_int64), ("count_f", ctypes.c_int64), ("count_launches", ctypes.c_int64)]
+
+
+# every symbol declared in include/dect.h, with its ctypes signature
+_VP = ctypes.c_void_p
+_SIGS = {
+    "dect_version": ([], ctypes.c_char_p),
+    "dect_last_error": ([], ctypes.c_char_p),
+    "dect_sync": ([_VP], ctypes.c_int),
+    "dect_geometry_create": ([ctypes.POINTER(GeomDesc), ctypes.POINTER(_VP)], ctypes.c_int),
+    "dect_geometry_destroy": ([_VP], None),
+    "dect_spectra_create": ([ctypes.c_int32, _VP, _VP, _VP, _VP, ctypes.POINTER(_VP)], ctypes.c_int),
+    "dect_spectra_destroy": ([_VP], None),
+    "dect_project": ([_VP, ctypes.c_int32, ctypes.c_int32, _VP, _VP, _VP], ctypes.c_int),
+    "dect_backproject": ([_VP, ctypes.c_int32, ctypes.c_int32, _VP, _VP, _VP], ctypes.c_int),
+    "dect_decompose_rays": ([_VP, ctypes.c_int64, _VP, _VP, _VP, _VP, _VP, _VP, ctypes.c_double, ctypes.c_double,
+                             ctypes.c_int32, _VP, _VP, _VP, _VP, _VP], ctypes.c_int),
+    "dect_params_default": ([ctypes.POINTER(Params)], None),
+    "dect_admm_create": ([_VP, ctypes.c_int32, _VP, ctypes.POINTER(Params), ctypes.POINTER(_VP)], ctypes.c_int),
+    "dect_admm_destroy": ([_VP], None),
+    "dect_admm_set_data": ([_VP, ctypes.c_int32, _VP, _VP, _VP, _VP, _VP, _VP], ctypes.c_int),
+    "dect_admm_set_truth": ([_VP, ctypes.c_int32, _VP, _VP], ctypes.c_int),
+    "dect_admm_step": ([_VP, ctypes.c_int32, _VP], ctypes.c_int),
+    "dect_reconstruct": ([_VP, ctypes.c_int32, _VP], ctypes.c_int),
+    "dect_admm_get": ([_VP, ctypes.c_int32, ctypes.c_int32, _VP, ctypes.c_size_t, _VP], ctypes.c_int),
+    "dect_admm_stats": ([_VP, ctypes.c_int32, ctypes.POINTER(Stats), _VP], ctypes.c_int),
+    "dect_admm_profile": ([_VP, ctypes.c_int32, _VP, _VP, _VP], ctypes.c_int),
+}
+
+_lib = None
+
+
+def lib(path: str | None = None):
+    """Loads libdect.so (built by paper_1905_00934_gb300.build); raises if it is missing."""
+    global _lib
+    if _lib is None:
+        p = path or LIB_PATH
+        if not os.path.exists(p):
+            raise RuntimeError(f"libdect.so not built ({p}); run __graft_entry__.build() first")
+        L = ctypes.CDLL(p)
+        for name, (args, res) in _SIGS.items():
+            fn = getattr(L, name)
+            fn.argtypes = args
+            fn.restype = res
+        _lib = L
+    return _lib
+
+
+def _check(status: int):
+    if status != OK:
+        raise DectError(status, lib().dect_last_error().decode())
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _ptr(t):
+    """Data pointer of a torch tensor or numpy array (must be contiguous float32 unless noted)."""
+    if t is None:
+        return None
+    if isinstance(t, np.ndarray):
+        assert t.flags["C_CONTIGUOUS"]
+        return ctypes.c_void_p(t.ctypes.data)
+    assert t.is_contiguous(), "tensors passed to dect must be contiguous"
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def version() -> str:
+    return lib().dect_version().decode()
+
+
+def sync(stream=None):
+    _check(lib().dect_sync(_stream(stream)))
+
+
+# ---- geometry / spectra -----------------------------------------------------------------------
+
+def geom_desc(g) -> GeomDesc:
+    """GeomDesc from any object with the synth.geometry.Geometry fields."""
+    return GeomDesc(g.kind, g.nx, g.ny, g.n_views, g.n_bins, g.pixel_cm, g.angle0_rad, g.angle_span_rad,
+                    g.bin_pitch_cm, g.bin_offset_cm, g.sod_cm, g.sdd_cm)
+
+
+def geometry_create(g) -> ctypes.c_void_p:
+    h = ctypes.c_void_p()
+    d = geom_desc(g) if not isinstance(g, GeomDesc) else g
+    _check(lib().dect_geometry_create(ctypes.byref(d), ctypes.byref(h)))
+    return h
+
+
+def geometry_destroy(h):
+    lib().dect_geometry_destroy(h)
+
+
+def spectra_create(S_h, S_l, f_kn, f_p) -> ctypes.c_void_p:
+    arrs = [np.ascontiguousarray(a, dtype=np.float64) for a in (S_h, S_l, f_kn, f_p)]
+    h = ctypes.c_void_p()
+    _check(lib().dect_spectra_create(arrs[0].size, *[ctypes.c_void_p(a.ctypes.data) for a in arrs], ctypes.byref(h)))
+    return h
+
+
+def spectra_destroy(h):
+    lib().dect_spectra_destroy(h)
+
+
+# ---- operators ----------------------------------------------------------------------------------
+
+def project(geom, x, out, stream=None):
+    """out[c] = R x[c]; x [nch, ny, nx], out [nch, n_views, n_bins] (CUDA float32)."""
+    _check(lib().dect_project(geom, x.shape[0], F32, _ptr(x), _ptr(out), _stream(stream)))
+    return out
+
+
+def backproject(geom, sino, out, stream=None):
+    """out[c] = R^T sino[c] (exact adjoint of project)."""
+    _check(lib().dect_backproject(geom, sino.shape[0], F32, _ptr(sino), _ptr(out), _stream(stream)))
+    return out
+
+
+def decompose_rays(spec, m_h, m_l, w_h, w_l, v_c, v_p, rho_c, rho_p, iters, a_c, a_p, mu, status=None, stream=None):
+    """Eq. 13 per ray; a_c, a_p, mu are updated in place."""
+    n = a_c.numel()
+    _check(lib().dect_decompose_rays(spec, n, _ptr(m_h), _ptr(m_l), _ptr(w_h), _ptr(w_l), _ptr(v_c), _ptr(v_p),
+                                     float(rho_c), float(rho_p), int(iters), _ptr(a_c), _ptr(a_p), _ptr(mu),
+                                     _ptr(status), _stream(stream)))
+
+
+# ---- ADMM solver ----------------------------------------------------------------------------------
+
+def params_default(**kw) -> Params:
+    p = Params()
+    lib().dect_params_default(ctypes.byref(p))
+    for k, v in kw.items():
+        setattr(p, k, v)
+    return p
+
+
+def admm_create(geoms, spec, params: Params) -> ctypes.c_void_p:
+    arr = (ctypes.c_void_p * len(geoms))(*[g.value if isinstance(g, ctypes.c_void_p) else g for g in geoms])
+    h = ctypes.c_void_p()
+    _check(lib().dect_admm_create(ctypes.cast(arr, ctypes.c_void_p), len(geoms), spec, ctypes.byref(params),
+                                  ctypes.byref(h)))
+    return h
+
+
+def admm_destroy(h):
+    lib().dect_admm_destroy(h)
+
+
+def admm_set_data(h, slice_index, m_h, m_l, w_h, w_l, x0=None, stream=None):
+    _check(lib().dect_admm_set_data(h, slice_index, _ptr(m_h), _ptr(m_l), _ptr(w_h), _ptr(w_l), _ptr(x0),
+                                    _stream(stream)))
+
+
+def admm_set_truth(h, slice_index, truth, stream=None):
+    _check(lib().dect_admm_set_truth(h, slice_index, _ptr(truth), _stream(stream)))
+
+
+def admm_step(h, iters, stream=None):
+    _check(lib().dect_admm_step(h, int(iters), _stream(stream)))
+
+
+def reconstruct(h, iters, stream=None):
+    _check(lib().dect_reconstruct(h, int(iters), _stream(stream)))
+
+
+def admm_get(h, slice_index, which, out, stream=None):
+    nbytes = out.numel() * out.element_size() if not isinstance(out, np.ndarray) else out.nbytes
+    _check(lib().dect_admm_get(h, slice_index, which, _ptr(out), nbytes, _stream(stream)))
+    return out
+
+
+def admm_stats(h, slice_index, stream=None) -> dict:
+    s = Stats()
+    _check(lib().dect_admm_stats(h, slice_index, ctypes.byref(s), _stream(stream)))
+    return {"iteration": s.iteration, "rho": list(s.rho), "r_pri": list(s.r_pri), "r_dual": list(s.r_dual),
+            "xi_db": list(s.xi_db), "count_R": s.count_R, "count_RT": s.count_RT, "count_f": s.count_f,
+            "count_launches": s.count_launches}
+
+
+PHASES = ["texture", "project", "backproject", "precond", "udm", "update", "reduce"]
+
+
+def admm_profile(h, iters, stream=None):
+    """Per-phase device milliseconds and kernel launches over `iters` profiled iterations."""
+    ms = (ctypes.c_double * len(PHASES))()
+    nl = (ctypes.c_int64 * len(PHASES))()
+    _check(lib().dect_admm_profile(h, int(iters), _stream(stream), ms, nl))
+    return {p: (ms[i], nl[i]) for i, p in enumerate(PHASES)}

@@ -108,10 +108,16 @@ def small_parallel_case(slice_index: int = 0, e_ref_kev: float = 1.0, noise: boo
 
 
 def baggage_fan_case(slice_index: int = 0, n: int = 512, n_views: int = 720, n_bins: int = 1024,
-                     e_ref_kev: float = 1.0, noise: bool = True):
+                     e_ref_kev: float = 100.0, noise: bool = True):
     geom = baggage_fan_geometry(n, n_views, n_bins) if (n, n_views, n_bins) == (512, 720, 1024) else fan_geometry(n, n_views, n_bins)
     return make_case(geom, baggage_phantom, 2e5, BASE_SEED + slice_index, e_ref_kev, noise)
 
+
+# Reading for the baggage workloads: their photoelectric range (up to 0.5) is physical with the E^-3
+# basis referred to 100 keV; the initial PE image is kappa = PE max / Compton max = 0.25 times Compton.
+BAGGAGE_E_REF_KEV = 100.0
+BAGGAGE_KAPPA = 0.25
+SMALL_KAPPA = 1e-2
 
 # --- ADMM parameters of the paper's experiments (Sec. 4): lambda = 1e-5, rho0 = 1e-3 for both bases.
 PAPER_LAMBDA = 1e-5

@@ -1,0 +1,175 @@
+"""GPU ADMM iteration UDM(m)-PCG(n) (Sec. 3.3) against the FP64 oracle.
+
+Both sides get the same float32-rounded measurements and the same starting image.
+Compton / PE images: relative L2 <= 1e-4 after the fixed iteration count, PE reported
+separately. With the photoelectric basis referred to 100 keV both bases meet it. With the
+literal 1 keV reference of the small workload the PE signal (f_p a_p ~ 1e-8 of the Compton
+attenuation) is below float32 resolution of the measurements; the per-ray PE update then
+amplifies rounding by w J_p / rho ~ 500 and flips LM accept/reject decisions, so there only
+the Compton image is held to 1e-4 and the PE deviation is reported (bounded loosely)."""
+import numpy as np
+import pytest
+import torch
+
+from conftest import rel_l2, to_dev
+from oracle import admm as oadmm
+from synth.workloads import small_parallel_case
+
+pytestmark = pytest.mark.gpu
+
+
+def _solver(c, dev, x0=None, **params):
+    from paper_1905_00934_gb300 import Geometry, Solver, Spectra
+
+    geo = Geometry(c["geom"])
+    sp = Spectra.from_tables(c["spectra"])
+    sol = Solver([geo], sp, **params)
+    f = lambda a: to_dev(a, dev)
+    sol.set_data(0, f(c["m_h"]), f(c["m_l"]), f(c["w_h"]), f(c["w_l"]), None if x0 is None else f(x0))
+    sol.set_truth(0, f(np.stack([c["truth_c"], c["truth_p"]])))
+    return sol
+
+
+def _r32(a):
+    return np.float32(a).astype(np.float64)
+
+
+def _case(e_ref):
+    c = small_parallel_case(e_ref_kev=e_ref)
+    for k in ("m_h", "m_l", "w_h", "w_l"):
+        c[k] = _r32(c[k])
+    prob = oadmm.Problem(c["geom"], c["spectra"], c["m_h"], c["m_l"], c["w_h"], c["w_l"], oadmm.Params())
+    x0 = _r32(np.stack(oadmm.initial_image(prob)))
+    return c, prob, x0
+
+
+@pytest.fixture(scope="module")
+def small():
+    return _case(1.0)
+
+
+@pytest.fixture(scope="module")
+def small100():
+    return _case(100.0)
+
+
+def test_profile_counts_every_kernel_group(cuda_dev, small100):
+    c, _, x0 = small100
+    sol = _solver(c, cuda_dev, x0)
+    sol.step(2)
+    l0 = sol.stats(0)["count_launches"]
+    prof = sol.profile(3)
+    launched = sum(v[1] for v in prof.values())
+    assert sol.stats(0)["count_launches"] - l0 == launched
+    assert all(v[0] > 0 for k, v in prof.items() if k != "texture" or v[1] > 0)
+    assert prof["backproject"][1] == 3 * 2 and prof["project"][1] == 3 and prof["udm"][1] == 3
+
+
+def test_preconditioner_response_matches_oracle(cuda_dev, small):
+    from paper_1905_00934_gb300 import dect
+
+    c, prob, x0 = small
+    sol = _solver(c, cuda_dev, x0)
+    H = sol.get(0, dect.H).cpu().numpy()
+    assert rel_l2(H, prob.H) <= 1e-5
+
+
+def test_initial_image_matches_oracle(cuda_dev, small):
+    from paper_1905_00934_gb300 import dect
+
+    c, prob, x0 = small
+    sol = _solver(c, cuda_dev)
+    sol.reconstruct(0)
+    x = sol.get(0, dect.X).cpu().numpy()
+    assert rel_l2(x[0], x0[0]) <= 1e-4
+    assert rel_l2(x[1], x0[1]) <= 1e-4
+
+
+def _run_pair(c, x0, dev, iters, m=1, n=1):
+    P = oadmm.Params(m_udm=m, n_pcg=n)
+    prob = oadmm.Problem(c["geom"], c["spectra"], c["m_h"], c["m_l"], c["w_h"], c["w_l"], P)
+    st = oadmm.state_from_image(prob, x0[0], x0[1])
+    sol = _solver(c, dev, x0, m_udm=m, n_pcg=n)
+    hist = []
+    for it in range(iters):
+        st = oadmm.admm_iteration(prob, st)
+        sol.step(1)
+        s = sol.stats(0)
+        hist.append((st.rho.copy(), np.array(s["rho"]), st.r_pri.copy(), np.array(s["r_pri"])))
+    return st, sol, hist
+
+
+@pytest.mark.parametrize("m,n,iters", [(1, 1, 20), (2, 3, 6)])
+def test_iterations_match_oracle(cuda_dev, small100, m, n, iters):
+    from paper_1905_00934_gb300 import dect
+
+    c, _, x0 = small100
+    st, sol, hist = _run_pair(c, x0, cuda_dev, iters, m, n)
+    for it, (rho_o, rho_g, rp_o, rp_g) in enumerate(hist):
+        assert np.array_equal(rho_o, rho_g), f"rho decision differs at iteration {it + 1}"
+        assert np.allclose(rp_g, rp_o, rtol=1e-3)
+    x = sol.get(0, dect.X).cpu().numpy()
+    e_c, e_p = rel_l2(x[0], st.x[0]), rel_l2(x[1], st.x[1])
+    print(f"E_ref 100 keV, m={m} n={n} iters={iters}: Compton rel-L2 {e_c:.2e}, PE rel-L2 {e_p:.2e}")
+    assert e_c <= 1e-4 and e_p <= 1e-4
+    a = sol.get(0, dect.A).cpu().numpy()
+    assert rel_l2(a[0], st.a[0]) <= 1e-4 and rel_l2(a[1], st.a[1]) <= 1e-4
+    xi = sol.stats(0)["xi_db"]
+    assert abs(xi[0] - oadmm.xi_db(st.x[0], c["truth_c"])) < 0.01
+    assert abs(xi[1] - oadmm.xi_db(st.x[1], c["truth_p"])) < 0.01
+
+
+def test_iterations_literal_pe_reference(cuda_dev, small):
+    from paper_1905_00934_gb300 import dect
+
+    c, _, x0 = small
+    st, sol, hist = _run_pair(c, x0, cuda_dev, 20)
+    for it, (rho_o, rho_g, rp_o, rp_g) in enumerate(hist):
+        assert rho_o[0] == rho_g[0], f"Compton rho decision differs at iteration {it + 1}"
+        assert rp_g[0] == pytest.approx(rp_o[0], rel=1e-3)
+    x = sol.get(0, dect.X).cpu().numpy()
+    e_c, e_p = rel_l2(x[0], st.x[0]), rel_l2(x[1], st.x[1])
+    print(f"E_ref 1 keV, 20 iterations: Compton rel-L2 {e_c:.2e}, PE rel-L2 {e_p:.2e} (PE reported)")
+    assert e_c <= 1e-4
+    assert e_p <= 0.25
+
+
+def test_table1_counts(cuda_dev, small100):
+    c, _, x0 = small100
+    for m, n in [(1, 1), (3, 2)]:
+        sol = _solver(c, cuda_dev, x0, m_udm=m, n_pcg=n)
+        sol.step(0)
+        s0 = sol.stats(0)
+        sol.step(4)
+        s1 = sol.stats(0)
+        assert s1["count_R"] - s0["count_R"] == 4 * 2 * n
+        assert s1["count_RT"] - s0["count_RT"] == 4 * 2 * (n + 1)
+        assert s1["count_f"] - s0["count_f"] == 4 * 4 * m
+        assert s1["iteration"] == 4
+
+
+def test_graph_and_eager_are_bitwise_equal_and_deterministic(cuda_dev, small100):
+    from paper_1905_00934_gb300 import dect
+
+    c, _, x0 = small100
+    outs = []
+    for use_graph in (1, 0, 1):
+        sol = _solver(c, cuda_dev, x0, use_graph=use_graph)
+        sol.step(5)
+        outs.append(sol.get(0, dect.X).cpu().numpy())
+    assert np.array_equal(outs[0], outs[1]) and np.array_equal(outs[0], outs[2])
+
+
+def test_unpreconditioned_cg_matches_oracle(cuda_dev, small100):
+    from paper_1905_00934_gb300 import dect
+
+    c, _, x0 = small100
+    P = oadmm.Params(precondition=False, n_pcg=2)
+    prob = oadmm.Problem(c["geom"], c["spectra"], c["m_h"], c["m_l"], c["w_h"], c["w_l"], P)
+    st = oadmm.state_from_image(prob, x0[0], x0[1])
+    for _ in range(3):
+        st = oadmm.admm_iteration(prob, st)
+    sol = _solver(c, cuda_dev, x0, precondition=0, n_pcg=2)
+    sol.step(3)
+    x = sol.get(0, dect.X).cpu().numpy()
+    assert rel_l2(x[0], st.x[0]) <= 1e-4 and rel_l2(x[1], st.x[1]) <= 1e-4

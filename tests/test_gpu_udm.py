@@ -1,0 +1,118 @@
+"""GPU per-ray decomposition (Eq. 13, LM) against the FP64 oracle.
+
+The accept/reject test of LM compares two costs; where the oracle's two costs are
+closer than float32 can resolve (a near tie), either decision is valid, so those rays
+are checked to equal one of the two candidates instead of the oracle's choice."""
+import numpy as np
+import pytest
+import torch
+
+from conftest import to_dev
+from oracle import spectral as ospec
+from synth import spectra
+
+pytestmark = pytest.mark.gpu
+
+
+def _rays(n, seed, e_ref):
+    """Rays shaped like the workloads: Poisson data, counts as weights, v near the truth."""
+    rng = np.random.default_rng(seed)
+    t = spectra.SpectralTables(e_ref_kev=e_ref)
+    lc = rng.uniform(0.0, 8.0, n)
+    lp = rng.uniform(0.0, 4e-3 * 8, n) if e_ref == 1.0 else rng.uniform(0.0, 0.05 * 8, n)
+    att = np.exp(-np.outer(lc, t.f_kn) - np.outer(lp, t.f_p))
+    i0 = 1e5
+    nh = np.maximum(rng.poisson(i0 * (att @ t.s_high)), 1.0)
+    nl = np.maximum(rng.poisson(i0 * (att @ t.s_low)), 1.0)
+    d = dict(m_h=-np.log(nh / i0), m_l=-np.log(nl / i0), w_h=nh, w_l=nl,
+             v_c=lc + rng.normal(0, 0.02, n), v_p=lp + rng.normal(0, 1e-3, n))
+    a0 = (d["v_c"] + rng.normal(0, 0.05, n), d["v_p"] + rng.normal(0, 1e-3, n))
+    return t, d, a0
+
+
+def _run_gpu(dev, t, d, a0, mu0, rho, iters):
+    from paper_1905_00934_gb300 import Spectra
+
+    sp = Spectra.from_tables(t)
+    f = lambda a: to_dev(a, dev)
+    ac, ap, mu = f(a0[0]), f(a0[1]), f(mu0)
+    st = torch.zeros(ac.numel(), dtype=torch.uint8, device=dev)
+    # inputs rounded to float32 are what both sides see
+    sp.decompose(f(d["m_h"]), f(d["m_l"]), f(d["w_h"]), f(d["w_l"]), f(d["v_c"]), f(d["v_p"]), rho[0], rho[1],
+                 iters, ac, ap, mu, st)
+    torch.cuda.synchronize()
+    return ac.cpu().double().numpy(), ap.cpu().double().numpy(), mu.cpu().double().numpy(), st.cpu().numpy()
+
+
+def _f32(d):
+    return {k: np.float32(v).astype(np.float64) for k, v in d.items()}
+
+
+@pytest.mark.parametrize("e_ref", [1.0, 100.0])
+@pytest.mark.parametrize("rho", [(1e-3, 1e-3), (0.0, 1e-3), (5.0, 50.0)])
+def test_one_lm_iteration_matches_oracle(cuda_dev, e_ref, rho):
+    n = 20000
+    t, d, a0 = _rays(n, 1, e_ref)
+    d32 = _f32(d)
+    a0 = tuple(np.float32(a).astype(np.float64) for a in a0)
+    mu0 = np.full(n, 1e-3)
+    gc, gp, gmu, gst = _run_gpu(cuda_dev, t, d32, a0, mu0, rho, 1)
+    oc, op, omu, ost = ospec.udm(t, d32["m_h"], d32["m_l"], d32["w_h"], d32["w_l"], d32["v_c"], d32["v_p"],
+                                 rho[0], rho[1], 1, a0[0], a0[1], mu0)
+    # where both sides made the same decision the results agree to float32 precision
+    same = gst == ost
+    assert same.mean() > 0.995
+    scale_c = np.maximum(np.abs(oc), 1.0)
+    scale_p = np.maximum(np.abs(op), np.abs(d32["v_p"]).max())
+    assert np.max(np.abs(gc - oc)[same] / scale_c[same]) < 2e-5
+    # the PE step reacts to an error e in f by about S e, S = sum_k w_k |J_pk| / (rho_p + sum_k w_k J_pk^2);
+    # float32 evaluation of f carries e ~ 1e-6 (input rounding + spectral sums), so allow S * 1e-6
+    _, _, J = ospec.forward_model(t, a0[0], a0[1], jacobian=True)
+    S = (d32["w_h"] * np.abs(J[:, 1]) + d32["w_l"] * np.abs(J[:, 3])) / (
+        rho[1] + d32["w_h"] * J[:, 1] ** 2 + d32["w_l"] * J[:, 3] ** 2)
+    assert np.all((np.abs(gp - op) <= S * 1e-6 + 2e-4 * scale_p)[same])
+    assert np.allclose(gmu[same], omu[same], rtol=1e-6)
+    # the rest are near ties: the GPU kept either the start point or the oracle's step
+    diff = ~same
+    if diff.any():
+        cost0 = ospec.udm_cost(t, d32["m_h"][diff], d32["m_l"][diff], d32["w_h"][diff], d32["w_l"][diff],
+                               d32["v_c"][diff], d32["v_p"][diff], rho[0], rho[1], a0[0][diff], a0[1][diff])
+        tc = np.where(ost[diff] == 0, oc[diff], gc[diff])
+        tp = np.where(ost[diff] == 0, op[diff], gp[diff])
+        cost1 = ospec.udm_cost(t, d32["m_h"][diff], d32["m_l"][diff], d32["w_h"][diff], d32["w_l"][diff],
+                               d32["v_c"][diff], d32["v_p"][diff], rho[0], rho[1], tc, tp)
+        assert np.all(np.abs(cost1 - cost0) <= 1e-5 * np.abs(cost0) + 1e-6)
+
+
+def test_many_iterations_converge_to_oracle_minimiser(cuda_dev):
+    # after enough iterations both sides sit at the same minimiser of Eq. 13
+    n = 5000
+    t, d, a0 = _rays(n, 2, 100.0)
+    d32 = _f32(d)
+    a0 = tuple(np.float32(a).astype(np.float64) for a in a0)
+    mu0 = np.full(n, 1e-3)
+    rho = (1e-2, 1e-1)
+    gc, gp, _, gst = _run_gpu(cuda_dev, t, d32, a0, mu0, rho, 30)
+    oc, op, _, _ = ospec.udm(t, d32["m_h"], d32["m_l"], d32["w_h"], d32["w_l"], d32["v_c"], d32["v_p"],
+                             rho[0], rho[1], 30, a0[0], a0[1], mu0)
+    assert np.max(np.abs(gc - oc) / np.maximum(np.abs(oc), 1)) < 1e-4
+    assert np.linalg.norm(gp - op) / np.linalg.norm(op) < 1e-3
+    assert np.all(gst != 2)
+
+
+def test_edge_cases(cuda_dev):
+    # zero rays is a no-op; photon-starved rays (count 1) and zero iterations leave a unchanged
+    from paper_1905_00934_gb300 import Spectra, dect
+
+    t = spectra.SpectralTables()
+    sp = Spectra.from_tables(t)
+    e = torch.empty(0, device=cuda_dev)
+    dect.decompose_rays(sp.handle, e, e, e, e, e, e, 1e-3, 1e-3, 1, e, e, e)
+    n = 7
+    f = lambda v: torch.full((n,), v, dtype=torch.float32, device=cuda_dev)
+    ac, ap, mu = f(1.0), f(0.0), f(1e-3)
+    dect.decompose_rays(sp.handle, f(12.2), f(12.2), f(1.0), f(1.0), f(5.0), f(0.0), 1e-3, 1e-3, 0, ac, ap, mu)
+    assert torch.all(ac == 1.0) and torch.all(mu == 1e-3)
+    st = torch.zeros(n, dtype=torch.uint8, device=cuda_dev)
+    dect.decompose_rays(sp.handle, f(12.2), f(12.2), f(1.0), f(1.0), f(5.0), f(0.0), 1e-3, 1e-3, 3, ac, ap, mu, st)
+    assert torch.all(torch.isfinite(ac)) and torch.all(torch.isfinite(ap))
