@@ -114,6 +114,27 @@ void dect_spectra_destroy(dect_spectra* s);
 dect_status dect_project(dect_geom* g, int32_t n_channels, int32_t dtype, const void* x_dev,
                          void* sino_dev, void* stream);
 
+/* Size of the fixed scratch array used by dect_project_noalloc (4 MiB). */
+#define DECT_NOALLOC_SCRATCH_BYTES (4u * 1024u * 1024u)
+
+/* Forward projection without any device allocation. The paper has no counterpart:
+ * this is a library convenience for callers that cannot call cudaMalloc (code
+ * running during CUDA stream capture, code whose device memory belongs to its
+ * own pool or framework allocator, fixed-budget deployments). Same operation,
+ * layouts and results as dect_project, but its scratch (pair textures and an
+ * interleaved image copy, 16*(nx*(ny+3) + ny*(nx+3)) + 8*nx*ny bytes) lives in
+ * a fixed DECT_NOALLOC_SCRATCH_BYTES array of device global memory inside the
+ * library, which every GPU that loads the library holds until exit; images up
+ * to about 320 x 320 fit. Larger images are rejected with DECT_EINVAL and a
+ * message, before anything is launched. The first call on a device looks up
+ * the array's device address (cudaGetSymbolAddress) with that device current;
+ * make that first call before any stream capture. All calls share the array:
+ * calls that overlap on the GPU (other streams, other host threads) race and
+ * must be ordered by the caller. Each call rewrites all scratch it reads, so
+ * nothing needs clearing between calls. */
+dect_status dect_project_noalloc(const dect_geom* g, int32_t n_channels, const float* x_dev, float* sino_dev,
+                                 void* stream);
+
 /* Backprojection, the exact adjoint R^T of dect_project (Table 1's R^T):
  * x_dev[c] = R^T sino_dev[c]; same layouts; x_dev is overwritten. It gathers
  * per pixel (no atomics), so the result is deterministic; it evaluates the

@@ -100,6 +100,12 @@ struct dect_geom {
     }
 };
 
+namespace dect {
+// accessors for the no-allocation projector (project_noalloc.cu)
+const dect_geom_desc* geom_desc_of(const dect_geom* g) { return &g->desc; }
+SliceDesc geom_single_of(const dect_geom* g) { return g->single(); }
+}  // namespace dect
+
 struct dect_spectra {
     int ne = 0;
     float4* t1 = nullptr;

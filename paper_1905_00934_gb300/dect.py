@@ -65,6 +65,7 @@ _SIGS = {
     "dect_spectra_destroy": ([_VP], None),
     "dect_project": ([_VP, ctypes.c_int32, ctypes.c_int32, _VP, _VP, _VP], ctypes.c_int),
     "dect_backproject": ([_VP, ctypes.c_int32, ctypes.c_int32, _VP, _VP, _VP], ctypes.c_int),
+    "dect_project_noalloc": ([_VP, ctypes.c_int32, _VP, _VP, _VP], ctypes.c_int),
     "dect_decompose_rays": ([_VP, ctypes.c_int64, _VP, _VP, _VP, _VP, _VP, _VP, ctypes.c_double, ctypes.c_double,
                              ctypes.c_int32, _VP, _VP, _VP, _VP, _VP], ctypes.c_int),
     "dect_params_default": ([ctypes.POINTER(Params)], None),
@@ -166,6 +167,19 @@ def spectra_destroy(h):
 def project(geom, x, out, stream=None):
     """out[c] = R x[c]; x [nch, ny, nx], out [nch, n_views, n_bins] (CUDA float32)."""
     _check(lib().dect_project(geom, x.shape[0], F32, _ptr(x), _ptr(out), _stream(stream)))
+    return out
+
+
+NOALLOC_SCRATCH_BYTES = 4 * 1024 * 1024
+
+
+def project_noalloc(geom, x, out, stream=None):
+    """Like project, but with the library's fixed scratch array instead of any allocation.
+
+    For callers that must not allocate device memory (e.g. while a stream is being captured).
+    Images must fit the fixed scratch (about 320 x 320); calls must not overlap on the GPU.
+    """
+    _check(lib().dect_project_noalloc(geom, x.shape[0], _ptr(x), _ptr(out), _stream(stream)))
     return out
 
 
