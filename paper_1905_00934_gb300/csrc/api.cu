@@ -89,6 +89,9 @@ struct dect_geom {
         g.sdd = (float)desc.sdd_cm;
         g.cx = 0.5f * (float)(desc.nx - 1);
         g.cy = 0.5f * (float)(desc.ny - 1);
+        g.inv_du = (float)(1.0 / desc.bin_pitch_cm);
+        g.k0 = (float)(0.5 * (desc.n_bins - 1) - desc.bin_offset_cm / desc.bin_pitch_cm);
+        g.k1 = (float)(desc.sdd_cm / desc.bin_pitch_cm);
         g.rays = rays;
         g.views = views;
         return g;
@@ -145,6 +148,9 @@ extern "C" dect_status dect_geometry_create(const dect_geom_desc* d, dect_geom**
             DECT_FAIL(DECT_EINVAL, "geometry: fan beam needs sdd > sod > 0");
         const double r = 0.5 * d->pixel_cm * std::sqrt((double)d->nx * d->nx + (double)d->ny * d->ny) + 2.0 * d->pixel_cm;
         if (r >= 0.98 * d->sod_cm) DECT_FAIL(DECT_EINVAL, "geometry: image must lie well inside the source circle");
+        // the rays through any 3x3-pixel neighbourhood then span less than 60 degrees, which the
+        // backprojector's per-window axis test relies on
+        if (d->sod_cm - r < 4.25 * d->pixel_cm) DECT_FAIL(DECT_EINVAL, "geometry: source too close to the image");
     }
     dect_geom* g = new dect_geom();
     g->desc = *d;
@@ -310,6 +316,7 @@ struct dect_admm {
     MapBuf rays, pix, tx, ty, bp, rows, cols;
     int64_t n_img = 0, n_sino = 0, n_tx = 0, n_ty = 0, n_fft = 0, n_h = 0, n_stage = 0;
     int max_px = 0, max_py = 0;
+    int bp_G = 4;  // view groups per backprojector tile
     float2 *x = nullptr, *r = nullptr, *s = nullptr, *p = nullptr, *Ap = nullptr, *z = nullptr, *uz = nullptr;
     float2 *x0 = nullptr, *truth = nullptr, *Rx = nullptr, *a = nullptr, *ua = nullptr, *q = nullptr, *Z = nullptr;
     float4 *y = nullptr, *uy = nullptr, *meas = nullptr, *txb = nullptr, *tyb = nullptr;
@@ -415,7 +422,7 @@ static void enq_pcg(dect_admm* A, int n, bool with_grad, const float* H, cudaStr
     launch_sino_resid(A->ds, A->rays.map(B), A->rays.total, A->a, A->ua, A->Rx, A->q, st);
     pe(A, DECT_PHASE_UPDATE, 1, st);
     pb(A, st);
-    launch_backproject(with_grad ? BP_R0 : BP_R0_NOGRAD, A->ds, A->bp.map(B), A->bp.total, A->q, A->r, ep, st);
+    launch_backproject(with_grad ? BP_R0 : BP_R0_NOGRAD, A->ds, A->bp.map(B), A->bp.total, A->q, A->r, ep, A->bp_G, st);
     pe(A, DECT_PHASE_BACKPROJECT, 1, st);
     if (A->counting) A->cRT += 2;
     enq_precond(A, H, A->r, A->p, st);
@@ -425,7 +432,7 @@ static void enq_pcg(dect_admm* A, int n, bool with_grad, const float* H, cudaStr
     for (int it = 0; it < n; ++it) {
         enq_project(A, A->p, A->q, st);
         pb(A, st);
-        launch_backproject(with_grad ? BP_AP : BP_AP_NOGRAD, A->ds, A->bp.map(B), A->bp.total, A->q, A->Ap, ep, st);
+        launch_backproject(with_grad ? BP_AP : BP_AP_NOGRAD, A->ds, A->bp.map(B), A->bp.total, A->q, A->Ap, ep, A->bp_G, st);
         pe(A, DECT_PHASE_BACKPROJECT, 1, st);
         if (A->counting) A->cRT += 2;
         pb(A, st);
@@ -677,6 +684,7 @@ extern "C" dect_status dect_admm_create(dect_geom* const* geoms, int32_t B, cons
     if (e == cudaSuccess) e = dalloc(&A->part_pap, 2 * (size_t)A->bp.h.back());
     for (MapBuf* m : {&A->rays, &A->pix, &A->tx, &A->ty, &A->bp, &A->rows, &A->cols})
         if (e == cudaSuccess) e = upload_map(*m);
+    A->bp_G = bp_groups(A->bp.h.back());
     if (e == cudaSuccess) e = cudaMemcpy(A->ds, A->hs.data(), sizeof(SliceDesc) * B, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemset(A->truth, 0, sizeof(float2) * A->n_img);
     if (e == cudaSuccess) e = cudaMemset(A->status, 0, A->n_sino);

@@ -37,6 +37,8 @@ struct GeomDev {
     int kind, nx, ny, nv, nb;
     float pix, du, uoff, sod, sdd;
     float cx, cy;           // (nx-1)/2, (ny-1)/2
+    float inv_du;           // 1 / du
+    float k0, k1;           // fractional bin of detector coordinate u: k = u * inv_du + k0; k1 = sdd * inv_du
     const int4* rays;       // [nv*nb] {q0 lo, q0 hi, slope, +-w}
     const float4* views;    // [nv] {cos, sin, 0, 0}
 };
@@ -120,7 +122,8 @@ void launch_textures(const SliceDesc* dsl, const BlockMap& mx, int nbx, const Bl
 void launch_project(const SliceDesc* dsl, const BlockMap& map, int nblk, const float4* tx, const float4* ty,
                     float2* out_interleaved, cudaStream_t st);
 void launch_backproject(int mode, const SliceDesc* dsl, const BlockMap& map, int nblk, const float2* sino,
-                        float2* out, const BpEpilogue& ep, cudaStream_t st);
+                        float2* out, const BpEpilogue& ep, int groups, cudaStream_t st);
+int bp_groups(int tiles);
 void project_single(const SliceDesc& sd, const float* img, int nch, float2* scratch, float4* tx, float4* ty,
                     float* out, cudaStream_t st);
 void backproject_single(const SliceDesc& sd, const float* sino, int nch, float2* packed, float* out,

@@ -2,10 +2,11 @@
 // Eq. 2-3; Table 1 counts their applications), for parallel and flat-detector
 // fan beams.
 //
-// Sample positions are 32.32 fixed point. A ray is sampled once per column
+// Sample positions are 34.30 fixed point. A ray is sampled once per column
 // (axis 0) or row (axis 1) at position q(t) = q0 + t * slope (t the column or
-// row index), so stepping is an exact 64-bit integer add: the integer part is
-// the lower interpolation neighbour and the top 23 fraction bits give the
+// row index), so a position is one exact 32x32+64-bit integer multiply-add and
+// stepping is an exact 64-bit add: the integer part is the lower
+// interpolation neighbour and the top 23 fraction bits give the
 // interpolation weight by a bit-cast, without float rounding or conversions.
 // Positions carry ~1e-7 pixel error against the exact geometry (float32
 // positions would carry ~3e-5 near |q| = 512).
@@ -71,7 +72,7 @@ __global__ void k_ray_table(dect_geom_desc d, int4* __restrict__ rays, float4* _
         w = d.pixel_cm / fabs(dy);
         axis = 1;
     }
-    const long long q0_fx = llrint(q0 * 4294967296.0);        // 32.32
+    const long long q0_fx = llrint(q0 * 1073741824.0);        // 34.30
     const int slope_fx = (int)llrint(slope * 1073741824.0);    // 2.30, |slope| <= 1
     const float wf = (float)w;
     rays[r] = make_int4((int)(unsigned)(q0_fx & 0xffffffffll), (int)(q0_fx >> 32), slope_fx,
@@ -157,17 +158,21 @@ __global__ void k_pack_planar(const float* __restrict__ in, int nch, int64_t n, 
 // ---------------------------------------------------------------------------------------------
 // forward projector
 
-// Fixed-point helpers: a ray entry is {q0 low word, q0 high word, slope * 2^30, +-w} with the sign of
-// w giving the axis (negative: sampled per row).
+// Fixed-point helpers: a ray entry is {q0 low word, q0 high word, slope, +-w}, q0 and slope in units
+// of 2^-30 pixel, with the sign of w giving the axis (negative: sampled per row).
 __device__ __forceinline__ long long ray_q0(const int4 P) {
     return ((long long)P.y << 32) | (long long)(unsigned)P.x;
 }
-__device__ __forceinline__ long long ray_step(const int4 P) { return (long long)P.z << 2; }
+__device__ __forceinline__ long long ray_step(const int4 P) { return (long long)P.z; }
 __device__ __forceinline__ bool ray_axis(const int4 P) { return P.w < 0; }
 __device__ __forceinline__ float ray_w(const int4 P) { return fabsf(__int_as_float(P.w)); }
-// interpolation weight of the upper neighbour: the top 23 fraction bits as a float in [0, 1)
+// position of the sample at index t
+__device__ __forceinline__ long long ray_pos(const int4 P, int t) { return ray_q0(P) + (long long)t * P.z; }
+// lower interpolation neighbour (floor of the position)
+__device__ __forceinline__ int pos_floor(long long q) { return (int)(q >> 30); }
+// interpolation weight of the upper neighbour: the top 23 of the 30 fraction bits as a float in [0, 1)
 __device__ __forceinline__ float frac_of(long long q) {
-    return __uint_as_float(0x3f800000u | ((unsigned)q >> 9)) - 1.0f;
+    return __uint_as_float(0x3f800000u | (((unsigned)q >> 7) & 0x7fffffu)) - 1.0f;
 }
 
 // Index range [lo, hi] along the sampled axis whose positions lie in [-1.5, n_across + 0.5): it
@@ -175,7 +180,7 @@ __device__ __forceinline__ float frac_of(long long q) {
 // neighbour in [-2, n_across]. Float estimate; the 0.5-pixel margins absorb its rounding.
 __device__ __forceinline__ void sample_range(const int4 P, int n_along, int n_across, int& lo, int& hi) {
     const float q0 = (float)P.y * 4294967296.0f + (float)(unsigned)P.x;
-    const float q0f = q0 * 2.3283064365386963e-10f;  // 2^-32
+    const float q0f = q0 * 9.313225746154785e-10f;  // 2^-30
     const float c1 = (float)P.z * 9.313225746154785e-10f;  // 2^-30
     float a, b;
     if (fabsf(c1) < 1e-30f) {
@@ -205,7 +210,7 @@ __device__ __forceinline__ float2 ray_sum(const int4 P, const GeomDev& g, const 
     long long q = ray_q0(P) + (long long)lo * step;
     const float4* row = tex + (size_t)lo * ld;
     for (int t = lo; t <= hi; ++t, q += step, row += ld) {
-        const int jj = min(max((int)(q >> 32) + 2, 0), n_across + 2);
+        const int jj = min(max(pos_floor(q) + 2, 0), n_across + 2);
         const float f = frac_of(q);
         const float4 v = __ldg(row + jj);
         ac += fmaf(f, v.z - v.x, v.x);
@@ -253,30 +258,34 @@ struct CandRange {
     int lo, hi;
 };
 
-// Bins whose rays can have a non-zero weight at pixel centre (x, y) (cm) in view (cs, sn).
-__device__ __forceinline__ CandRange candidates(const GeomDev& g, float cs, float sn, float x, float y) {
+// Bins whose rays can have a non-zero weight at any pixel of a 2x2 block centred at (xc, yc) (cm)
+// in view (cs, sn). The block's interpolation support is, for rays sampled per column (axis 0), the
+// two vertical segments x = xc -+ pix/2, |y - yc| <= 1.5 pix, and for rays sampled per row (axis 1)
+// the transposed pair; AX = -1 bounds both (the square of half-side 1.5 pix). A segment's
+// projection onto the detector is bounded by its end points' projections (fan) or by the projected
+// half-width (parallel). eps absorbs float32 rounding and the rays' fixed-point quantisation (both
+// far below 0.02 bins).
+template <int AX>
+__device__ __forceinline__ CandRange block_candidates(const GeomDev& g, float cs, float sn, float xc, float yc) {
     const float eps = 0.02f;
-    const float half_nb = 0.5f * (g.nb - 1);
+    const float hx = (AX == 0 ? 0.5f : 1.5f) * g.pix, hy = (AX == 1 ? 0.5f : 1.5f) * g.pix;
     float kmin, kmax;
     if (g.kind == DECT_PARALLEL) {
-        const float uc = fmaf(x, cs, y * sn);
-        const float h = g.pix * fmaxf(fabsf(cs), fabsf(sn));
-        kmin = (uc - h - g.uoff) / g.du + half_nb;
-        kmax = (uc + h - g.uoff) / g.du + half_nb;
+        const float kc = fmaf(fmaf(xc, cs, yc * sn), g.inv_du, g.k0);
+        const float h = fmaf(hx, fabsf(cs), hy * fabsf(sn)) * g.inv_du;
+        kmin = kc - h;
+        kmax = kc + h;
     } else {
-        // u(P) = sdd (P . e) / (sod - P . n), e = (-sin, cos), n = (cos, sin); the pixel's
-        // interpolation support is the cross {x} x (y-pix, y+pix) U (x-pix, x+pix) x {y}
-        const float num = fmaf(-x, sn, y * cs);
-        const float den = g.sod - fmaf(x, cs, y * sn);
-        const float dc = g.pix * cs, ds = g.pix * sn;
-        const float u1 = __fdividef(num + dc, den - ds);
-        const float u2 = __fdividef(num - dc, den + ds);
-        const float u3 = __fdividef(num - ds, den - dc);
-        const float u4 = __fdividef(num + ds, den + dc);
-        const float umin = g.sdd * fminf(fminf(u1, u2), fminf(u3, u4));
-        const float umax = g.sdd * fmaxf(fmaxf(u1, u2), fmaxf(u3, u4));
-        kmin = (umin - g.uoff) / g.du + half_nb;
-        kmax = (umax - g.uoff) / g.du + half_nb;
+        // u(P) = sdd (P . e) / (sod - P . n), e = (-sin, cos), n = (cos, sin)
+        const float num = fmaf(-xc, sn, yc * cs), den = g.sod - fmaf(xc, cs, yc * sn);
+        const float nx_ = -hx * sn, dx_ = -hx * cs;  // change of num / den for x += hx
+        const float ny_ = hy * cs, dy_ = -hy * sn;   // change of num / den for y += hy
+        const float u1 = __fdividef(num + nx_ + ny_, den + dx_ + dy_);
+        const float u2 = __fdividef(num + nx_ - ny_, den + dx_ - dy_);
+        const float u3 = __fdividef(num - nx_ + ny_, den - dx_ + dy_);
+        const float u4 = __fdividef(num - nx_ - ny_, den - dx_ - dy_);
+        kmin = fmaf(g.k1, fminf(fminf(u1, u2), fminf(u3, u4)), g.k0);
+        kmax = fmaf(g.k1, fmaxf(fmaxf(u1, u2), fmaxf(u3, u4)), g.k0);
     }
     CandRange c;
     c.lo = max(0, (int)ceilf(fmaxf(kmin - eps, -1.0f)));
@@ -284,36 +293,74 @@ __device__ __forceinline__ CandRange candidates(const GeomDev& g, float cs, floa
     return c;
 }
 
-// Weight with which ray P samples pixel (i, j) (without the ray's w): the same integers as ray_sum.
-__device__ __forceinline__ float pixel_weight(const int4 P, int i, int j) {
-    const bool ax = ray_axis(P);
-    const int t = ax ? j : i, across = ax ? i : j;
-    const long long q = ray_q0(P) + (long long)t * ray_step(P);
-    const int q0 = (int)(q >> 32);
-    const float f = frac_of(q);
-    return q0 == across ? 1.0f - f : (q0 + 1 == across ? f : 0.0f);
+// Interpolation weights of one sample for the two pixels across at offsets 0 and 1 (d = lower
+// neighbour minus the first across index): the lower neighbour gets 1 - f and the upper one f,
+// exactly as the forward interpolation.
+__device__ __forceinline__ void across_weights(int d, float f, float& w0, float& w1) {
+    w0 = d == 0 ? 1.0f - f : (d == -1 ? f : 0.0f);
+    w1 = d == 1 ? 1.0f - f : (d == 0 ? f : 0.0f);
 }
 
-__device__ __forceinline__ float2 gather_pixel(const GeomDev& g, const float2* __restrict__ sino, int i, int j) {
-    const float x = ((float)i - g.cx) * g.pix, y = ((float)j - g.cy) * g.pix;
-    float ac = 0.f, ap = 0.f;
-    for (int v = 0; v < g.nv; ++v) {
+// Accumulators of a 2x2 pixel block, both bases: pixel (dy, dx) -> a[dy][dx].
+struct Block2x2 {
+    float c00, c01, c10, c11, p00, p01, p10, p11;
+};
+
+// One candidate ray for the block with top-left pixel (i, j). AX: 0 or 1 when the ray's axis is
+// known to the caller, -1 to read it from the entry.
+template <int AX>
+__device__ __forceinline__ void block_ray(const int4 P, const float2* __restrict__ sv, int i, int j, Block2x2& a) {
+    const bool ax = AX < 0 ? ray_axis(P) : (AX == 1);
+    // samples at the block's two columns (axis 0) or rows (axis 1)
+    const long long qa = ray_pos(P, ax ? j : i);
+    const long long qb = qa + ray_step(P);
+    const int c0 = ax ? i : j;
+    const int da = pos_floor(qa) - c0, db = pos_floor(qb) - c0;
+    if ((unsigned)(da + 1) > 2u && (unsigned)(db + 1) > 2u) return;  // no weight on the block
+    float a0, a1, b0, b1;
+    across_weights(da, frac_of(qa), a0, a1);
+    across_weights(db, frac_of(qb), b0, b1);
+    // axis 0: sample s at column i + s, across offset r at row j + r -> pixel (r, s)
+    // axis 1: sample s at row j + s, across offset r at column i + r -> pixel (s, r)
+    const float w01 = ax ? a1 : b0, w10 = ax ? b0 : a1;
+    const float2 s2 = __ldg(sv);
+    const float wr = ray_w(P);
+    const float sc = wr * s2.x, sp = wr * s2.y;
+    a.c00 = fmaf(a0, sc, a.c00);
+    a.p00 = fmaf(a0, sp, a.p00);
+    a.c01 = fmaf(w01, sc, a.c01);
+    a.p01 = fmaf(w01, sp, a.p01);
+    a.c10 = fmaf(w10, sc, a.c10);
+    a.p10 = fmaf(w10, sp, a.p10);
+    a.c11 = fmaf(b1, sc, a.c11);
+    a.p11 = fmaf(b1, sp, a.p11);
+}
+
+// Gathers views v0, v0 + dv, ... for the 2x2 block with top-left pixel (i, j). The candidates of one
+// view pass within 1.5 pixels of the block, so their directions span less than 60 degrees (the
+// geometry check keeps the source at least 4.25 pixels away) and their sampling axis changes at
+// most once, where the direction crosses a diagonal: when the first and last candidate share an
+// axis, every candidate between them does too (specialised loop).
+__device__ __forceinline__ void gather_block(const GeomDev& g, const float2* __restrict__ sino, int i, int j, int v0,
+                                             int dv, Block2x2& a) {
+    const float xc = ((float)i + 0.5f - g.cx) * g.pix, yc = ((float)j + 0.5f - g.cy) * g.pix;
+    for (int v = v0; v < g.nv; v += dv) {
         const float4 V = __ldg(g.views + v);
-        const CandRange cr = candidates(g, V.x, V.y, x, y);
+        const CandRange cr = block_candidates<-1>(g, V.x, V.y, xc, yc);
+        if (cr.lo > cr.hi) continue;
         const int4* rv = g.rays + (size_t)v * g.nb;
         const float2* sv = sino + (size_t)v * g.nb;
-        for (int k = cr.lo; k <= cr.hi; ++k) {
-            const int4 P = __ldg(rv + k);
-            const float wgt = pixel_weight(P, i, j);
-            if (wgt != 0.0f) {
-                const float2 sv2 = __ldg(sv + k);
-                const float ww = ray_w(P) * wgt;
-                ac = fmaf(ww, sv2.x, ac);
-                ap = fmaf(ww, sv2.y, ap);
+        const bool ax_lo = __ldg(&rv[cr.lo].w) < 0, ax_hi = __ldg(&rv[cr.hi].w) < 0;
+        if (ax_lo == ax_hi) {
+            if (ax_lo) {
+                for (int k = cr.lo; k <= cr.hi; ++k) block_ray<1>(__ldg(rv + k), sv + k, i, j, a);
+            } else {
+                for (int k = cr.lo; k <= cr.hi; ++k) block_ray<0>(__ldg(rv + k), sv + k, i, j, a);
             }
+        } else {
+            for (int k = cr.lo; k <= cr.hi; ++k) block_ray<-1>(__ldg(rv + k), sv + k, i, j, a);
         }
     }
-    return make_float2(ac, ap);
 }
 
 __device__ __forceinline__ float2 f2(const float2* __restrict__ a, int nx, int ny, int j, int i) {
@@ -360,25 +407,50 @@ __device__ __forceinline__ float4 grad_of(const float2* __restrict__ p, int nx, 
     return grad_at(p, nx, ny, j, i);
 }
 
+// Backprojector tile: 16 x 16 pixels; 64 threads per view group, each owning a 2x2 pixel block; G
+// view groups (views v = group, group + G, ...) with G chosen by the host so that the grid fills
+// the GPU in one wave where possible. The G partial sums of each pixel are added in a fixed order,
+// so the result is deterministic.
+constexpr int kBpMaxGroups = 8;
+
 template <int MODE>
-__global__ void __launch_bounds__(kBpTile * kBpTile) k_backproject(const SliceDesc* __restrict__ dsl, BlockMap map,
-                                                                   const float2* __restrict__ sino,
-                                                                   float2* __restrict__ out, BpEpilogue ep) {
-    int local;
-    const int s = slice_of(map, blockIdx.x, local);
-    const SliceDesc& d = dsl[s];
+__device__ __forceinline__ void backproject_tile(const SliceDesc& d, int local, const float2* __restrict__ sino,
+                                                 float2* __restrict__ out, const BpEpilogue& ep, float* __restrict__ planar,
+                                                 int nch) {
+    __shared__ float red[kBpMaxGroups][8][64];
+    const int G = blockDim.x / 64;
     const int nx = d.g.nx, ny = d.g.ny;
     const int tiles_x = (nx + kBpTile - 1) / kBpTile;
-    const int i = (local % tiles_x) * kBpTile + (threadIdx.x % kBpTile);
-    const int j = (local / tiles_x) * kBpTile + (threadIdx.x / kBpTile);
-    const bool valid = (i < nx) && (j < ny);
-    float2 acc = make_float2(0.f, 0.f);
-    if (valid) acc = gather_pixel(d.g, sino + d.sino_off, i, j);
+    const int ti = (local % tiles_x) * kBpTile, tj = (local / tiles_x) * kBpTile;
+    {
+        const int grp = threadIdx.x / 64, b = threadIdx.x % 64;
+        const int bi = ti + 2 * (b % 8), bj = tj + 2 * (b / 8);
+        Block2x2 a = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        if (bi < nx && bj < ny) gather_block(d.g, sino + d.sino_off, bi, bj, grp, G, a);
+        red[grp][0][b] = a.c00;
+        red[grp][1][b] = a.p00;
+        red[grp][2][b] = a.c01;
+        red[grp][3][b] = a.p01;
+        red[grp][4][b] = a.c10;
+        red[grp][5][b] = a.p10;
+        red[grp][6][b] = a.c11;
+        red[grp][7][b] = a.p11;
+    }
+    __syncthreads();
+    // epilogue: the block's threads walk the tile's 256 pixels
     double dot_c = 0.0, dot_p = 0.0;
-    if (valid) {
+    for (int px = threadIdx.x; px < kBpTile * kBpTile; px += blockDim.x) {
+        const int pi = px % kBpTile, pj = px / kBpTile;
+        const int i = ti + pi, j = tj + pj;
+        if (i >= nx || j >= ny) continue;
+        const int b = (pj / 2) * 8 + (pi / 2), q = 2 * (2 * (pj % 2) + (pi % 2));
+        float2 r = make_float2(0.f, 0.f);
+        for (int grp = 0; grp < G; ++grp) {
+            r.x += red[grp][q][b];
+            r.y += red[grp][q + 1][b];
+        }
         const int64_t off = d.img_off;
         const size_t e = (size_t)j * nx + i;
-        float2 r = acc;
         if (MODE == BP_R0 || MODE == BP_R0_NOGRAD) {
             const float2 xc = __ldg(ep.x + off + e), z = __ldg(ep.z + off + e), uz = __ldg(ep.uz + off + e);
             r.x += z.x + uz.x - xc.x;
@@ -404,29 +476,34 @@ __global__ void __launch_bounds__(kBpTile * kBpTile) k_backproject(const SliceDe
                 r.x += dt.x;
                 r.y += dt.y;
             }
-            dot_c = (double)pc.x * (double)r.x;
-            dot_p = (double)pc.y * (double)r.y;
+            dot_c += (double)pc.x * (double)r.x;
+            dot_p += (double)pc.y * (double)r.y;
         }
-        out[off + e] = r;
+        if (planar) {
+            planar[e] = r.x;
+            if (nch > 1) planar[(size_t)nx * ny + e] = r.y;
+        } else {
+            out[off + e] = r;
+        }
     }
     if (MODE == BP_AP || MODE == BP_AP_NOGRAD) {
         // deterministic block reduction of the two partial dot products
-        __shared__ double red[2][kBpTile * kBpTile / 32];
+        __shared__ double dred[2][kBpMaxGroups * 2];
         for (int o = 16; o > 0; o >>= 1) {
             dot_c += __shfl_down_sync(0xffffffffu, dot_c, o);
             dot_p += __shfl_down_sync(0xffffffffu, dot_p, o);
         }
         const int w = threadIdx.x / 32, l = threadIdx.x % 32;
         if (l == 0) {
-            red[0][w] = dot_c;
-            red[1][w] = dot_p;
+            dred[0][w] = dot_c;
+            dred[1][w] = dot_p;
         }
         __syncthreads();
         if (threadIdx.x == 0) {
             double sc = 0.0, sp = 0.0;
-            for (int q = 0; q < kBpTile * kBpTile / 32; ++q) {
-                sc += red[0][q];
-                sp += red[1][q];
+            for (int k = 0; k < (int)blockDim.x / 32; ++k) {
+                sc += dred[0][k];
+                sp += dred[1][k];
             }
             ep.partial[2 * (size_t)blockIdx.x] = sc;
             ep.partial[2 * (size_t)blockIdx.x + 1] = sp;
@@ -434,24 +511,43 @@ __global__ void __launch_bounds__(kBpTile * kBpTile) k_backproject(const SliceDe
     }
 }
 
-__global__ void __launch_bounds__(kBpTile * kBpTile) k_backproject_planar(SliceDesc d, const float2* __restrict__ sino,
+template <int MODE>
+__global__ void __launch_bounds__(64 * kBpMaxGroups) k_backproject(const SliceDesc* __restrict__ dsl, BlockMap map,
+                                                                   const float2* __restrict__ sino,
+                                                                   float2* __restrict__ out, BpEpilogue ep) {
+    int local;
+    const int s = slice_of(map, blockIdx.x, local);
+    backproject_tile<MODE>(dsl[s], local, sino, out, ep, nullptr, 0);
+}
+
+__global__ void __launch_bounds__(64 * kBpMaxGroups) k_backproject_planar(SliceDesc d, const float2* __restrict__ sino,
                                                                           float* __restrict__ out, int nch) {
-    const int nx = d.g.nx, ny = d.g.ny;
-    const int tiles_x = (nx + kBpTile - 1) / kBpTile;
-    const int i = (blockIdx.x % tiles_x) * kBpTile + (threadIdx.x % kBpTile);
-    const int j = (blockIdx.x / tiles_x) * kBpTile + (threadIdx.x / kBpTile);
-    if (i >= nx || j >= ny) return;
-    const float2 acc = gather_pixel(d.g, sino, i, j);
-    const size_t e = (size_t)j * nx + i;
-    out[e] = acc.x;
-    if (nch > 1) out[(size_t)nx * ny + e] = acc.y;
+    BpEpilogue ep{};
+    backproject_tile<BP_PLAIN>(d, blockIdx.x, sino, nullptr, ep, out, nch);
 }
 
 int bp_tiles(int nx, int ny) { return ((nx + kBpTile - 1) / kBpTile) * ((ny + kBpTile - 1) / kBpTile); }
 
+// View groups per tile: the largest G whose grid of `tiles` blocks is resident in one wave; more
+// groups give more threads per tile, and one wave avoids a partly idle tail.
+int bp_groups(int tiles) {
+    static int occ[kBpMaxGroups + 1] = {0};
+    static int sms = 0;
+    if (!sms) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        for (int G = 1; G <= kBpMaxGroups; ++G)
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[G], k_backproject<BP_AP>, 64 * G, 0);
+    }
+    for (int G = kBpMaxGroups; G >= 1; --G)
+        if ((long long)occ[G] * sms >= tiles) return G;
+    return 4;
+}
+
 void launch_backproject(int mode, const SliceDesc* dsl, const BlockMap& map, int nblk, const float2* sino,
-                        float2* out, const BpEpilogue& ep, cudaStream_t st) {
-    const int T = kBpTile * kBpTile;
+                        float2* out, const BpEpilogue& ep, int groups, cudaStream_t st) {
+    const int T = 64 * groups;
     switch (mode) {
         case BP_PLAIN: k_backproject<BP_PLAIN><<<nblk, T, 0, st>>>(dsl, map, sino, out, ep); break;
         case BP_R0: k_backproject<BP_R0><<<nblk, T, 0, st>>>(dsl, map, sino, out, ep); break;
@@ -513,7 +609,8 @@ void backproject_single(const SliceDesc& sd, const float* sino, int nch, float2*
                         cudaStream_t st) {
     const int64_t nr = (int64_t)sd.g.nv * sd.g.nb;
     k_pack_planar<<<(unsigned)((nr + 255) / 256), 256, 0, st>>>(sino, nch, nr, packed);
-    k_backproject_planar<<<bp_tiles(sd.g.nx, sd.g.ny), kBpTile * kBpTile, 0, st>>>(sd, packed, out, nch);
+    const int tiles = bp_tiles(sd.g.nx, sd.g.ny);
+    k_backproject_planar<<<tiles, 64 * bp_groups(tiles), 0, st>>>(sd, packed, out, nch);
 }
 
 int texture_x_blocks(int nx, int ny) { return tx_blocks(nx, ny); }
