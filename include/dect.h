@@ -46,7 +46,7 @@ typedef enum {
 
 typedef enum { DECT_PARALLEL = 0, DECT_FAN_FLAT = 1 } dect_geom_kind;
 
-typedef enum { DECT_F32 = 0 } dect_dtype;
+typedef enum { DECT_F32 = 0, DECT_F64 = 1 } dect_dtype;
 
 /* Per-ray decomposition status codes (uint8 array of dect_decompose_rays). */
 enum { DECT_RAY_ACCEPTED = 0, DECT_RAY_REJECTED = 1, DECT_RAY_NONFINITE = 2 };
@@ -108,8 +108,10 @@ void dect_spectra_destroy(dect_spectra* s);
 
 /* ------------------------------------------------------------------------ */
 /* Forward projection (Eq. 2-3's R): sino_dev[c] = R x_dev[c] for c < n_channels.
- * x_dev: planar [n_channels][ny][nx] float32; sino_dev: planar
- * [n_channels][n_views][n_bins] float32, overwritten. n_channels is 1 or 2.
+ * x_dev: planar [n_channels][ny][nx]; sino_dev: planar [n_channels][n_views][n_bins],
+ * overwritten; both of `dtype` (DECT_F32 or DECT_F64). n_channels is 1 or 2.
+ * DECT_F32 samples positions in 34.30 fixed point (~1e-7 pixel); DECT_F64 uses a
+ * float64 ray table (built on first use) and float64 accumulation.
  * Uses the geometry's workspace (allocated on first use). */
 dect_status dect_project(dect_geom* g, int32_t n_channels, int32_t dtype, const void* x_dev,
                          void* sino_dev, void* stream);
@@ -136,7 +138,7 @@ dect_status dect_project_noalloc(const dect_geom* g, int32_t n_channels, const f
                                  void* stream);
 
 /* Backprojection, the exact adjoint R^T of dect_project (Table 1's R^T):
- * x_dev[c] = R^T sino_dev[c]; same layouts; x_dev is overwritten. It gathers
+ * x_dev[c] = R^T sino_dev[c]; same layouts and dtypes; x_dev is overwritten. It gathers
  * per pixel (no atomics), so the result is deterministic; it evaluates the
  * same per-ray weights as dect_project, so <R x, y> = <x, R^T y> up to float32
  * rounding. */
@@ -159,6 +161,21 @@ dect_status dect_decompose_rays(const dect_spectra* s, int64_t n_rays, const flo
                                 const float* w_h, const float* w_l, const float* v_c, const float* v_p,
                                 double rho_c, double rho_p, int32_t iters, float* a_c, float* a_p,
                                 float* mu, uint8_t* status, void* stream);
+
+/* Forward model of Eq. 3 per ray: f_h, f_l at (a_c, a_p) and, if jac is not
+ * NULL, the Jacobian jac[r] = {df_h/da_c, df_h/da_p, df_l/da_c, df_l/da_p}
+ * ([n_rays][4]). All arrays device memory of `dtype` (DECT_F32: float32
+ * exponentials with compensated sums and float64 logs, as the decomposition;
+ * DECT_F64: float64 throughout). f_h, f_l may be NULL. */
+dect_status dect_forward_model(const dect_spectra* s, int64_t n_rays, int32_t dtype, const void* a_c, const void* a_p,
+                               void* f_h, void* f_l, void* jac, void* stream);
+
+/* Vector-Jacobian product of the forward model (its transpose applied to an
+ * output gradient): grad_c = g_h df_h/da_c + g_l df_l/da_c, grad_p likewise;
+ * the backward pass of the forward model in automatic differentiation. */
+dect_status dect_forward_model_vjp(const dect_spectra* s, int64_t n_rays, int32_t dtype, const void* a_c,
+                                   const void* a_p, const void* g_h, const void* g_l, void* grad_c, void* grad_p,
+                                   void* stream);
 
 /* ------------------------------------------------------------------------ */
 /* ADMM solver state for B >= 1 independent slices (Sec. 3.2-3.3).
@@ -187,6 +204,11 @@ typedef struct {
     int32_t init_pcg_iters;      /* initialisation: CG iterations (10) */
     int32_t precondition;        /* 1: circulant preconditioner, 0: plain CG */
     int32_t use_graph;           /* 1: capture one iteration as a CUDA graph */
+    int32_t bp_view_groups;      /* backprojector view groups per tile, 1..8; 0 = chosen from the
+                                    occupancy so that the grid fills the GPU. It fixes the order of a
+                                    pixel's partial sums: results are bitwise reproducible for a fixed
+                                    value, and a slice solved alone or in a batch gives identical bits
+                                    when the value is the same (it is the one launch-dependent choice). */
 } dect_params;
 
 /* Fills *p with the paper's values and the defaults above. */

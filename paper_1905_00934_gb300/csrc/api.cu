@@ -72,6 +72,7 @@ struct dect_geom {
     float4* ws_tx = nullptr;
     float4* ws_ty = nullptr;
     float2* ws_sino = nullptr;
+    double4* rays64 = nullptr;  // float64 ray table (DECT_F64 calls; built on first use)
 
     int64_t n_rays() const { return (int64_t)desc.n_views * desc.n_bins; }
     int64_t n_pix() const { return (int64_t)desc.nx * desc.ny; }
@@ -113,6 +114,7 @@ struct dect_spectra {
     int ne = 0;
     float4* t1 = nullptr;
     float4* t2 = nullptr;
+    double4* t64 = nullptr;  // {S_h, S_l, f_KN, f_p}, unit-sum spectra
     double abar_low = 1.0;  // sum_E S_l f_KN (unit-sum S_l)
     SpecDev dev() const { return SpecDev{ne, t1, t2}; }
 };
@@ -175,6 +177,7 @@ extern "C" void dect_geometry_destroy(dect_geom* g) {
     cudaFree(g->ws_tx);
     cudaFree(g->ws_ty);
     cudaFree(g->ws_sino);
+    cudaFree(g->rays64);
     delete g;
 }
 
@@ -188,11 +191,26 @@ static dect_status geom_workspace(dect_geom* g) {
     return DECT_OK;
 }
 
+static dect_status geom_table_f64(dect_geom* g) {
+    if (g->rays64) return DECT_OK;
+    CUDA_TRY(dalloc(&g->rays64, (size_t)g->n_rays()));
+    CUDA_TRY(build_ray_table_f64(g->desc, g->rays64, 0));
+    CUDA_TRY(cudaStreamSynchronize(0));
+    return DECT_OK;
+}
+
 extern "C" dect_status dect_project(dect_geom* g, int32_t nch, int32_t dtype, const void* x, void* sino, void* stream) {
     clear_stale_error();
     if (!g || !x || !sino) DECT_FAIL(DECT_EINVAL, "dect_project: null argument");
     if (nch != 1 && nch != 2) DECT_FAIL(DECT_EINVAL, "dect_project: n_channels must be 1 or 2");
-    if (dtype != DECT_F32) DECT_FAIL(DECT_EUNSUPPORTED, "dect_project: only DECT_F32 is supported");
+    if (dtype != DECT_F32 && dtype != DECT_F64) DECT_FAIL(DECT_EUNSUPPORTED, "dect_project: dtype must be DECT_F32 or DECT_F64");
+    if (dtype == DECT_F64) {
+        dect_status s64 = geom_table_f64(g);
+        if (s64 != DECT_OK) return s64;
+        project_single_f64(g->dev(), g->rays64, (const double*)x, nch, (double*)sino, as_stream(stream));
+        CUDA_TRY(cudaGetLastError());
+        return DECT_OK;
+    }
     dect_status st = geom_workspace(g);
     if (st != DECT_OK) return st;
     project_single(g->single(), (const float*)x, nch, g->ws_img, g->ws_tx, g->ws_ty, (float*)sino, as_stream(stream));
@@ -205,7 +223,15 @@ extern "C" dect_status dect_backproject(dect_geom* g, int32_t nch, int32_t dtype
     clear_stale_error();
     if (!g || !x || !sino) DECT_FAIL(DECT_EINVAL, "dect_backproject: null argument");
     if (nch != 1 && nch != 2) DECT_FAIL(DECT_EINVAL, "dect_backproject: n_channels must be 1 or 2");
-    if (dtype != DECT_F32) DECT_FAIL(DECT_EUNSUPPORTED, "dect_backproject: only DECT_F32 is supported");
+    if (dtype != DECT_F32 && dtype != DECT_F64)
+        DECT_FAIL(DECT_EUNSUPPORTED, "dect_backproject: dtype must be DECT_F32 or DECT_F64");
+    if (dtype == DECT_F64) {
+        dect_status s64 = geom_table_f64(g);
+        if (s64 != DECT_OK) return s64;
+        backproject_single_f64(g->dev(), g->rays64, (const double*)sino, nch, (double*)x, as_stream(stream));
+        CUDA_TRY(cudaGetLastError());
+        return DECT_OK;
+    }
     dect_status st = geom_workspace(g);
     if (st != DECT_OK) return st;
     backproject_single(g->single(), (const float*)sino, nch, g->ws_sino, (float*)x, as_stream(stream));
@@ -231,9 +257,11 @@ extern "C" dect_status dect_spectra_create(int32_t ne, const double* S_h, const 
     if (!(th > 0.0) || !(tl > 0.0)) DECT_FAIL(DECT_EINVAL, "dect_spectra_create: spectra must have positive sums");
     const double log2e = 1.4426950408889634;
     std::vector<float4> t1(ne), t2(ne);
+    std::vector<double4> t64(ne);
     double abar = 0.0;
     for (int e = 0; e < ne; ++e) {
         const double sh = S_h[e] / th, sl = S_l[e] / tl;
+        t64[e] = make_double4(sh, sl, f_kn[e], f_p[e]);
         t1[e] = make_float4((float)(f_kn[e] * log2e), (float)(f_p[e] * log2e), (float)sh, (float)sl);
         t2[e] = make_float4((float)(sh * f_kn[e]), (float)(sh * f_p[e]), (float)(sl * f_kn[e]), (float)(sl * f_p[e]));
         abar += sl * f_kn[e];
@@ -245,6 +273,8 @@ extern "C" dect_status dect_spectra_create(int32_t ne, const double* S_h, const 
     if (e == cudaSuccess) e = dalloc(&s->t2, ne);
     if (e == cudaSuccess) e = cudaMemcpy(s->t1, t1.data(), sizeof(float4) * ne, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(s->t2, t2.data(), sizeof(float4) * ne, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = dalloc(&s->t64, ne);
+    if (e == cudaSuccess) e = cudaMemcpy(s->t64, t64.data(), sizeof(double4) * ne, cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {
         dect::set_error(std::string("dect_spectra_create: ") + cudaGetErrorString(e));
         dect_spectra_destroy(s);
@@ -258,6 +288,7 @@ extern "C" void dect_spectra_destroy(dect_spectra* s) {
     if (!s) return;
     cudaFree(s->t1);
     cudaFree(s->t2);
+    cudaFree(s->t64);
     delete s;
 }
 
@@ -280,6 +311,32 @@ extern "C" dect_status dect_decompose_rays(const dect_spectra* s, int64_t n, con
     return DECT_OK;
 }
 
+extern "C" dect_status dect_forward_model(const dect_spectra* s, int64_t n, int32_t dtype, const void* a_c,
+                                          const void* a_p, void* f_h, void* f_l, void* jac, void* stream) {
+    clear_stale_error();
+    if (!s || !a_c || !a_p) DECT_FAIL(DECT_EINVAL, "dect_forward_model: null argument");
+    if (n < 0) DECT_FAIL(DECT_EINVAL, "dect_forward_model: n_rays < 0");
+    if (dtype != DECT_F32 && dtype != DECT_F64) DECT_FAIL(DECT_EUNSUPPORTED, "dect_forward_model: bad dtype");
+    launch_forward_model(s->dev(), s->t64, n, dtype, a_c, a_p, f_h, f_l, jac, nullptr, nullptr, nullptr, nullptr,
+                         as_stream(stream));
+    CUDA_TRY(cudaGetLastError());
+    return DECT_OK;
+}
+
+extern "C" dect_status dect_forward_model_vjp(const dect_spectra* s, int64_t n, int32_t dtype, const void* a_c,
+                                              const void* a_p, const void* g_h, const void* g_l, void* grad_c,
+                                              void* grad_p, void* stream) {
+    clear_stale_error();
+    if (!s || !a_c || !a_p || !g_h || !g_l || !grad_c || !grad_p)
+        DECT_FAIL(DECT_EINVAL, "dect_forward_model_vjp: null argument");
+    if (n < 0) DECT_FAIL(DECT_EINVAL, "dect_forward_model_vjp: n_rays < 0");
+    if (dtype != DECT_F32 && dtype != DECT_F64) DECT_FAIL(DECT_EUNSUPPORTED, "dect_forward_model_vjp: bad dtype");
+    launch_forward_model(s->dev(), s->t64, n, dtype, a_c, a_p, nullptr, nullptr, nullptr, g_h, g_l, grad_c, grad_p,
+                         as_stream(stream));
+    CUDA_TRY(cudaGetLastError());
+    return DECT_OK;
+}
+
 // ----------------------------------------------------------------------------------------------
 extern "C" void dect_params_default(dect_params* p) {
     if (!p) return;
@@ -297,6 +354,7 @@ extern "C" void dect_params_default(dect_params* p) {
     p->init_pcg_iters = 10;
     p->precondition = 1;
     p->use_graph = 1;
+    p->bp_view_groups = 0;
 }
 
 struct MapBuf {
@@ -586,6 +644,8 @@ extern "C" dect_status dect_admm_create(dect_geom* const* geoms, int32_t B, cons
     if (!geoms || !spec || !P || !out) DECT_FAIL(DECT_EINVAL, "dect_admm_create: null argument");
     *out = nullptr;
     if (B < 1 || B > 4096) DECT_FAIL(DECT_EINVAL, "dect_admm_create: n_slices must be in [1, 4096]");
+    if (P->bp_view_groups < 0 || P->bp_view_groups > 8)
+        DECT_FAIL(DECT_EINVAL, "dect_admm_create: bp_view_groups must be in [0, 8]");
     if (P->m_udm < 1 || P->n_pcg < 1 || P->m_udm > 64 || P->n_pcg > 64)
         DECT_FAIL(DECT_EINVAL, "dect_admm_create: m_udm and n_pcg must be in [1, 64]");
     if (P->init_udm_iters < 0 || P->init_pcg_iters < 1 || P->init_udm_iters > 1000 || P->init_pcg_iters > 1000)
@@ -684,7 +744,7 @@ extern "C" dect_status dect_admm_create(dect_geom* const* geoms, int32_t B, cons
     if (e == cudaSuccess) e = dalloc(&A->part_pap, 2 * (size_t)A->bp.h.back());
     for (MapBuf* m : {&A->rays, &A->pix, &A->tx, &A->ty, &A->bp, &A->rows, &A->cols})
         if (e == cudaSuccess) e = upload_map(*m);
-    A->bp_G = bp_groups(A->bp.h.back());
+    A->bp_G = P->bp_view_groups > 0 ? P->bp_view_groups : bp_groups(A->bp.h.back());
     if (e == cudaSuccess) e = cudaMemcpy(A->ds, A->hs.data(), sizeof(SliceDesc) * B, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemset(A->truth, 0, sizeof(float2) * A->n_img);
     if (e == cudaSuccess) e = cudaMemset(A->status, 0, A->n_sino);

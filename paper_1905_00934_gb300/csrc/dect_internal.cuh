@@ -145,6 +145,16 @@ void launch_udm_rays(const SpecDev& sp, int64_t n, const float* mh, const float*
                      const float* wl, const float* vc, const float* vp, double rho_c, double rho_p, int iters,
                      float* ac, float* ap, float* mu, uint8_t* status, cudaStream_t st);
 
+void launch_forward_model(const SpecDev& sp, const double4* t64, int64_t n, int dtype, const void* ac,
+                          const void* ap, void* fh, void* fl, void* jac, const void* gh, const void* gl, void* oc,
+                          void* op, cudaStream_t st);
+
+// projector_f64.cu
+cudaError_t build_ray_table_f64(const dect_geom_desc& d, double4* rays, cudaStream_t st);
+void project_single_f64(const GeomDev& g, const double4* rays, const double* x, int nch, double* out, cudaStream_t st);
+void backproject_single_f64(const GeomDev& g, const double4* rays, const double* sino, int nch, double* out,
+                            cudaStream_t st);
+
 // fft.cu
 const float2* fft_twiddles();   // device table exp(-2 pi i t / kFftMax), t < kFftMax/2 (current device)
 __host__ __device__ int precond_cols_per_block(int py);

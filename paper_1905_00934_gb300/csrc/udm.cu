@@ -262,7 +262,92 @@ __global__ void __launch_bounds__(kRaysPerBlock) k_udm_rays(SpecDev sp, int64_t 
     if (status) status[r] = st.status;
 }
 
+// ---- forward model f (Eq. 3) and its Jacobian-transpose product, per ray ---------------------------
+// float32: the LM kernel's sums (compensated, float32 exponentials), logs and ratios in float64.
+// float64: tables and exponentials in float64 (t64 = {S_h, S_l, f_KN, f_p} per energy, unit-sum S).
+
+__global__ void __launch_bounds__(kRaysPerBlock) k_forward_model_f32(SpecDev sp, int64_t n, const float* __restrict__ ac,
+                                                                     const float* __restrict__ ap, float* __restrict__ fh,
+                                                                     float* __restrict__ fl, float* __restrict__ jac,
+                                                                     const float* __restrict__ gh,
+                                                                     const float* __restrict__ gl, float* __restrict__ oc,
+                                                                     float* __restrict__ op) {
+    extern __shared__ float4 tabs[];
+    float4* t1 = tabs;
+    float4* t2 = tabs + sp.ne;
+    load_tables(sp, t1, t2);
+    const int64_t r = (int64_t)blockIdx.x * kRaysPerBlock + threadIdx.x;
+    if (r >= n) return;
+    float sh, sl, shc, shp, slc, slp;
+    spectral_sums_jac(t1, t2, sp.ne, __ldg(ac + r), __ldg(ap + r), sh, sl, shc, shp, slc, slp);
+    const double ish = 1.0 / (double)sh, isl = 1.0 / (double)sl;
+    const double j0 = shc * ish, j1 = shp * ish, j2 = slc * isl, j3 = slp * isl;
+    if (fh) fh[r] = (float)(-log((double)sh));
+    if (fl) fl[r] = (float)(-log((double)sl));
+    if (jac) {
+        jac[4 * r] = (float)j0;
+        jac[4 * r + 1] = (float)j1;
+        jac[4 * r + 2] = (float)j2;
+        jac[4 * r + 3] = (float)j3;
+    }
+    if (oc) {
+        const double a = __ldg(gh + r), b = __ldg(gl + r);
+        oc[r] = (float)(a * j0 + b * j2);
+        op[r] = (float)(a * j1 + b * j3);
+    }
+}
+
+__global__ void __launch_bounds__(kRaysPerBlock) k_forward_model_f64(int ne, const double4* __restrict__ t64, int64_t n,
+                                                                     const double* __restrict__ ac,
+                                                                     const double* __restrict__ ap, double* __restrict__ fh,
+                                                                     double* __restrict__ fl, double* __restrict__ jac,
+                                                                     const double* __restrict__ gh,
+                                                                     const double* __restrict__ gl,
+                                                                     double* __restrict__ oc, double* __restrict__ op) {
+    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n) return;
+    const double c = ac[r], p = ap[r];
+    double sh = 0, sl = 0, shc = 0, shp = 0, slc = 0, slp = 0;
+    for (int e = 0; e < ne; ++e) {
+        const double4 T = t64[e];  // {S_h, S_l, f_KN, f_p}
+        const double t = exp(-T.z * c - T.w * p);
+        sh += T.x * t;
+        sl += T.y * t;
+        shc += T.x * T.z * t;
+        shp += T.x * T.w * t;
+        slc += T.y * T.z * t;
+        slp += T.y * T.w * t;
+    }
+    const double j0 = shc / sh, j1 = shp / sh, j2 = slc / sl, j3 = slp / sl;
+    if (fh) fh[r] = -log(sh);
+    if (fl) fl[r] = -log(sl);
+    if (jac) {
+        jac[4 * r] = j0;
+        jac[4 * r + 1] = j1;
+        jac[4 * r + 2] = j2;
+        jac[4 * r + 3] = j3;
+    }
+    if (oc) {
+        oc[r] = gh[r] * j0 + gl[r] * j2;
+        op[r] = gh[r] * j1 + gl[r] * j3;
+    }
+}
+
 static size_t tab_bytes(const SpecDev& sp) { return 2 * sizeof(float4) * (size_t)sp.ne; }
+
+void launch_forward_model(const SpecDev& sp, const double4* t64, int64_t n, int dtype, const void* ac,
+                          const void* ap, void* fh, void* fl, void* jac, const void* gh, const void* gl, void* oc,
+                          void* op, cudaStream_t st) {
+    if (n <= 0) return;
+    if (dtype == DECT_F32)
+        k_forward_model_f32<<<(unsigned)((n + kRaysPerBlock - 1) / kRaysPerBlock), kRaysPerBlock, tab_bytes(sp), st>>>(
+            sp, n, (const float*)ac, (const float*)ap, (float*)fh, (float*)fl, (float*)jac, (const float*)gh,
+            (const float*)gl, (float*)oc, (float*)op);
+    else
+        k_forward_model_f64<<<(unsigned)((n + 127) / 128), 128, 0, st>>>(
+            sp.ne, t64, n, (const double*)ac, (const double*)ap, (double*)fh, (double*)fl, (double*)jac,
+            (const double*)gh, (const double*)gl, (double*)oc, (double*)op);
+}
 
 void launch_udm_admm(const SliceDesc* dsl, const BlockMap& map, int nblk, const SpecDev& sp, const float4* meas,
                      const float2* Rx, float2* ua, float2* a, float* mu, uint8_t* status, const SliceScalars* sc,

@@ -19,7 +19,7 @@ LIB_PATH = os.path.join(_HERE, "_build", "libdect.so")
 
 OK, EINVAL, ENOMEM, ECUDA, EUNSUPPORTED, ETIMEOUT, ENOTCONV = range(7)
 PARALLEL, FAN_FLAT = 0, 1
-F32 = 0
+F32, F64 = 0, 1
 RAY_ACCEPTED, RAY_REJECTED, RAY_NONFINITE = 0, 1, 2
 # dect_admm_get array selectors
 X, RX, A, UA, Y, UY, Z, UZ, MU, H = range(10)
@@ -44,7 +44,7 @@ class Params(ctypes.Structure):
                 ("rho0_p", ctypes.c_double), ("m_udm", ctypes.c_int32), ("n_pcg", ctypes.c_int32),
                 ("rho_mu", ctypes.c_double), ("rho_tau", ctypes.c_double), ("lm_mu0", ctypes.c_double),
                 ("kappa", ctypes.c_double), ("init_udm_iters", ctypes.c_int32), ("init_pcg_iters", ctypes.c_int32),
-                ("precondition", ctypes.c_int32), ("use_graph", ctypes.c_int32)]
+                ("precondition", ctypes.c_int32), ("use_graph", ctypes.c_int32), ("bp_view_groups", ctypes.c_int32)]
 
 
 class Stats(ctypes.Structure):
@@ -68,6 +68,8 @@ _SIGS = {
     "dect_project_noalloc": ([_VP, ctypes.c_int32, _VP, _VP, _VP], ctypes.c_int),
     "dect_decompose_rays": ([_VP, ctypes.c_int64, _VP, _VP, _VP, _VP, _VP, _VP, ctypes.c_double, ctypes.c_double,
                              ctypes.c_int32, _VP, _VP, _VP, _VP, _VP], ctypes.c_int),
+    "dect_forward_model": ([_VP, ctypes.c_int64, ctypes.c_int32, _VP, _VP, _VP, _VP, _VP, _VP], ctypes.c_int),
+    "dect_forward_model_vjp": ([_VP, ctypes.c_int64, ctypes.c_int32, _VP, _VP, _VP, _VP, _VP, _VP, _VP], ctypes.c_int),
     "dect_params_default": ([ctypes.POINTER(Params)], None),
     "dect_admm_create": ([_VP, ctypes.c_int32, _VP, ctypes.POINTER(Params), ctypes.POINTER(_VP)], ctypes.c_int),
     "dect_admm_destroy": ([_VP], None),
@@ -164,9 +166,19 @@ def spectra_destroy(h):
 
 # ---- operators ----------------------------------------------------------------------------------
 
+def _dtype(t):
+    import torch
+
+    if t.dtype == torch.float32:
+        return F32
+    if t.dtype == torch.float64:
+        return F64
+    raise TypeError(f"dect supports float32 and float64 tensors, not {t.dtype}")
+
+
 def project(geom, x, out, stream=None):
-    """out[c] = R x[c]; x [nch, ny, nx], out [nch, n_views, n_bins] (CUDA float32)."""
-    _check(lib().dect_project(geom, x.shape[0], F32, _ptr(x), _ptr(out), _stream(stream)))
+    """out[c] = R x[c]; x [nch, ny, nx], out [nch, n_views, n_bins] (CUDA float32 or float64)."""
+    _check(lib().dect_project(geom, x.shape[0], _dtype(x), _ptr(x), _ptr(out), _stream(stream)))
     return out
 
 
@@ -185,7 +197,7 @@ def project_noalloc(geom, x, out, stream=None):
 
 def backproject(geom, sino, out, stream=None):
     """out[c] = R^T sino[c] (exact adjoint of project)."""
-    _check(lib().dect_backproject(geom, sino.shape[0], F32, _ptr(sino), _ptr(out), _stream(stream)))
+    _check(lib().dect_backproject(geom, sino.shape[0], _dtype(sino), _ptr(sino), _ptr(out), _stream(stream)))
     return out
 
 
@@ -195,6 +207,18 @@ def decompose_rays(spec, m_h, m_l, w_h, w_l, v_c, v_p, rho_c, rho_p, iters, a_c,
     _check(lib().dect_decompose_rays(spec, n, _ptr(m_h), _ptr(m_l), _ptr(w_h), _ptr(w_l), _ptr(v_c), _ptr(v_p),
                                      float(rho_c), float(rho_p), int(iters), _ptr(a_c), _ptr(a_p), _ptr(mu),
                                      _ptr(status), _stream(stream)))
+
+
+def forward_model(spec, a_c, a_p, f_h=None, f_l=None, jac=None, stream=None):
+    """Eq. 3 per ray (and its Jacobian [n, 4] if jac is given)."""
+    _check(lib().dect_forward_model(spec, a_c.numel(), _dtype(a_c), _ptr(a_c), _ptr(a_p), _ptr(f_h), _ptr(f_l),
+                                    _ptr(jac), _stream(stream)))
+
+
+def forward_model_vjp(spec, a_c, a_p, g_h, g_l, grad_c, grad_p, stream=None):
+    """Transpose of the forward model's Jacobian applied to (g_h, g_l)."""
+    _check(lib().dect_forward_model_vjp(spec, a_c.numel(), _dtype(a_c), _ptr(a_c), _ptr(a_p), _ptr(g_h), _ptr(g_l),
+                                        _ptr(grad_c), _ptr(grad_p), _stream(stream)))
 
 
 # ---- ADMM solver ----------------------------------------------------------------------------------

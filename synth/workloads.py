@@ -122,3 +122,36 @@ SMALL_KAPPA = 1e-2
 # --- ADMM parameters of the paper's experiments (Sec. 4): lambda = 1e-5, rho0 = 1e-3 for both bases.
 PAPER_LAMBDA = 1e-5
 PAPER_RHO0 = 1e-3
+
+
+def uneven_batch_shapes(n_slices: int = 64, seed: int = BASE_SEED):
+    """Seeded (N, views, bins) of the batched uneven-slice workload: N in 256..1024 step 64,
+    views in 360..1440 step 90, bins in 512..2048 step 128."""
+    rng = np.random.Generator(np.random.PCG64(seed + 7))
+    n = rng.integers(0, (1024 - 256) // 64 + 1, n_slices) * 64 + 256
+    v = rng.integers(0, (1440 - 360) // 90 + 1, n_slices) * 90 + 360
+    b = rng.integers(0, (2048 - 512) // 128 + 1, n_slices) * 128 + 512
+    return [(int(a), int(c), int(d)) for a, c, d in zip(n, v, b)]
+
+
+def quick_fan_case(slice_index: int, n: int, n_views: int, n_bins: int, n_objects: int = 12,
+                   e_ref_kev: float = BAGGAGE_E_REF_KEV, i0: float = 2e5):
+    """A fan-beam slice with a light phantom and no truth image (for large batched runs)."""
+    geom = fan_geometry(n, n_views, n_bins)
+    seed = BASE_SEED + 10_000 + slice_index
+    rng = np.random.Generator(np.random.PCG64(seed))
+    half = 0.5 * geom.nx * geom.pixel_cm
+    rows = []
+    for k in range(n_objects):
+        shape = ELLIPSE if rng.uniform() < 0.5 else RECTANGLE
+        high_z = k == 0
+        a, b = (rng.uniform(0.02, 0.05, 2) if high_z else rng.uniform(0.05, 0.25, 2)) * half
+        c, p = (rng.uniform(1.0, 2.0), rng.uniform(0.1, 0.5)) if high_z else (rng.uniform(0.1, 0.3), rng.uniform(0, 4e-3))
+        r = 0.7 * half * math.sqrt(rng.uniform())
+        t = rng.uniform(0, 2 * math.pi)
+        rows.append([shape, r * math.cos(t), r * math.sin(t), a, b, rng.uniform(0, math.pi), c, p])
+    ph = _phantom_from_rows(rows)
+    spec = SpectralTables(e_ref_kev=e_ref_kev)
+    lc, lp = line_integrals(ph, geom)
+    data = measurements(spec, lc, lp, i0, seed + 1_000_000)
+    return {"geom": geom, "spectra": spec, "phantom": ph, "i0": i0, "seed": seed, **data}

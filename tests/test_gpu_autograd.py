@@ -1,0 +1,166 @@
+"""Differentiable projector and forward model (autograd wrappers over the R / R^T and Jacobian kernels).
+
+Losses on a batch of 16 slices at 512 x 512, 720 views, 1024 bins, float32 and float64:
+  * quadratic: L(x) = 1/2 sum w (R x - l)^2 against the exact line integrals l; central differences
+    (h = 1e-3) are exact up to rounding, so the autograd gradient is held tightly at 32 pixels;
+  * the weighted data fidelity of Eq. 4, L(x) = 1/2 sum_k w_k (f_k(R x_c, R x_p) - m_k)^2, which is
+    not quadratic: the central difference carries an O(h^2) truncation term, bounded against the
+    gradient's scale.
+Also: the adjoint dot-product test through autograd, the float64 gradient against the FP64 oracle's
+R^T (J^T W (f - m)), and the forward model and its Jacobian against the oracle."""
+import numpy as np
+import pytest
+import torch
+
+from conftest import rel_l2
+from oracle import projector as oproj
+from oracle import spectral as ospec
+from synth import spectra as sspec
+from synth.geometry import baggage_fan_geometry
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def setup(cuda_dev):
+    from concurrent.futures import ThreadPoolExecutor
+
+    from paper_1905_00934_gb300 import Geometry, Spectra
+    from synth.workloads import baggage_fan_case
+
+    with ThreadPoolExecutor(max_workers=16) as ex:
+        cases = list(ex.map(lambda b: baggage_fan_case(slice_index=100 + b), range(16)))
+    g = cases[0]["geom"]
+    geo = Geometry(g)
+    spec = Spectra.from_tables(cases[0]["spectra"])
+    rng = np.random.default_rng(3)
+    # evaluation point: the phantom plus a perturbation, so the residuals are not zero
+    x = np.stack([np.stack([c["truth_c"], c["truth_p"]]) for c in cases])
+    x = x + rng.normal(0, 0.01, x.shape) * np.array([1.0, 0.01])[None, :, None, None]
+    data = {k: np.stack([c[k] for c in cases]) for k in ("m_h", "m_l", "w_h", "w_l", "L_c", "L_p")}
+    return cases, geo, spec, x, data
+
+
+def _loss_terms(x, geo, spec, data_t):
+    """Per-ray terms of the weighted data fidelity (float64)."""
+    from paper_1905_00934_gb300 import autograd as ag
+
+    s = ag.project(x, geo)                        # [B, 2, V, Nb]
+    f_h, f_l = ag.forward_model(s[:, 0].contiguous(), s[:, 1].contiguous(), spec)
+    r_h = (f_h - data_t["m_h"]).double()
+    r_l = (f_l - data_t["m_l"]).double()
+    return 0.5 * (data_t["w_h"].double() * r_h * r_h + data_t["w_l"].double() * r_l * r_l)
+
+
+def _loss(x, geo, spec, data_t):
+    return _loss_terms(x, geo, spec, data_t).sum()
+
+
+def _quad_terms(x, geo, spec, data_t):
+    from paper_1905_00934_gb300 import autograd as ag
+
+    s = ag.project(x, geo)
+    rc = (s[:, 0] - data_t["L_c"]).double()
+    rp = (s[:, 1] - data_t["L_p"]).double()
+    return 0.5 * data_t["w_h"].double() * (rc * rc + rp * rp)
+
+
+def _fd_errors(x, loss_terms, geo, spec, data_t, h=1e-3, n=32, seed=4):
+    """(autograd gradient, central difference) at n random pixels."""
+    loss_terms(x, geo, spec, data_t).sum().backward()
+    grad = x.grad.detach()
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(n):
+        b, c = int(rng.integers(x.shape[0])), int(rng.integers(2))
+        j, i = int(rng.integers(100, 412)), int(rng.integers(100, 412))
+        with torch.no_grad():
+            xp = x.detach().clone()
+            xp[b, c, j, i] += h
+            xm = x.detach().clone()
+            xm[b, c, j, i] -= h
+            # rays that miss the pixel give bit-identical terms, so differencing per ray before
+            # summing keeps the sum's rounding out of the difference quotient
+            fd = (loss_terms(xp, geo, spec, data_t) - loss_terms(xm, geo, spec, data_t)).sum().item() / (2 * h)
+        out.append((grad[b, c, j, i].item(), fd))
+    return np.array(out), float(grad.abs().max())
+
+
+@pytest.mark.parametrize("dtype", [torch.float32, torch.float64])
+def test_quadratic_loss_gradient_matches_central_differences(setup, cuda_dev, dtype):
+    cases, geo, spec, x_np, data = setup
+    data_t = {k: torch.tensor(v, dtype=dtype, device=cuda_dev) for k, v in data.items()}
+    x = torch.tensor(x_np, dtype=dtype, device=cuda_dev, requires_grad=True)
+    gf, gmax = _fd_errors(x, _quad_terms, geo, spec, data_t)
+    if dtype == torch.float64:
+        # exact up to rounding
+        err = np.abs(gf[:, 0] - gf[:, 1]) / np.maximum(np.abs(gf[:, 1]), 1e-9 * gmax)
+        assert err.max() < 1e-7, err.max()
+    else:
+        # float32 projections (~10) carry ~1e-6 rounding against a 1e-4 change per ray
+        assert np.all(np.abs(gf[:, 0] - gf[:, 1]) <= 2e-3 * np.abs(gf[:, 1]) + 1e-4 * gmax), gf
+
+
+@pytest.mark.parametrize("dtype", [torch.float32, torch.float64])
+def test_fidelity_loss_gradient_matches_central_differences(setup, cuda_dev, dtype):
+    cases, geo, spec, x_np, data = setup
+    data_t = {k: torch.tensor(v, dtype=dtype, device=cuda_dev) for k, v in data.items()}
+    x = torch.tensor(x_np, dtype=dtype, device=cuda_dev, requires_grad=True)
+    gf, gmax = _fd_errors(x, _loss_terms, geo, spec, data_t)
+    # O(h^2) truncation of the non-quadratic loss is bounded against the gradient scale
+    rel, absl = (3e-3, 1e-4) if dtype == torch.float32 else (1e-4, 1e-6)
+    assert np.all(np.abs(gf[:, 0] - gf[:, 1]) <= rel * np.abs(gf[:, 1]) + absl * gmax), (dtype, gf)
+
+
+def test_autograd_adjoint_dot_product(setup, cuda_dev):
+    from paper_1905_00934_gb300 import autograd as ag
+
+    _, geo, _, _, _ = setup
+    rng = np.random.default_rng(5)
+    for dtype, tol in ((torch.float32, 1e-6), (torch.float64, 1e-12)):
+        x = torch.tensor(rng.normal(size=(3, geo.ny, geo.nx)), dtype=dtype, device=cuda_dev, requires_grad=True)
+        y = torch.tensor(rng.normal(size=(3, geo.n_views, geo.n_bins)), dtype=dtype, device=cuda_dev)
+        s = ag.project(x, geo)
+        (s * y).sum().backward()
+        lhs = (s.detach().double() * y.double()).sum().item()
+        rhs = (x.detach().double() * x.grad.double()).sum().item()
+        assert abs(lhs - rhs) <= tol * torch.linalg.norm(s.double()).item() * torch.linalg.norm(y.double()).item()
+
+
+def test_float64_gradient_matches_oracle(setup, cuda_dev):
+    cases, geo, spec, x_np, data = setup
+    data_t = {k: torch.tensor(v[:2], dtype=torch.float64, device=cuda_dev) for k, v in data.items()}
+    x = torch.tensor(x_np[:2], dtype=torch.float64, device=cuda_dev, requires_grad=True)
+    _loss(x, geo, spec, data_t).backward()
+    g = cases[0]["geom"]
+    t = cases[0]["spectra"]
+    for b in range(2):
+        s = np.stack([oproj.project(g, x_np[b, c]) for c in range(2)])
+        fh, fl, J = ospec.forward_model(t, s[0], s[1], jacobian=True)
+        rh = (fh - data["m_h"][b].ravel()) * data["w_h"][b].ravel()
+        rl = (fl - data["m_l"][b].ravel()) * data["w_l"][b].ravel()
+        gc = (rh * J[:, 0] + rl * J[:, 2]).reshape(g.n_views, g.n_bins)
+        gp = (rh * J[:, 1] + rl * J[:, 3]).reshape(g.n_views, g.n_bins)
+        ref = np.stack([oproj.backproject(g, gc), oproj.backproject(g, gp)])
+        got = x.grad[b].cpu().numpy()
+        assert rel_l2(got[0], ref[0]) < 1e-9 and rel_l2(got[1], ref[1]) < 1e-9
+
+
+@pytest.mark.parametrize("dtype,tol", [(torch.float32, 2e-6), (torch.float64, 1e-13)])
+def test_forward_model_and_jacobian_match_oracle(cuda_dev, dtype, tol):
+    from paper_1905_00934_gb300 import Spectra, dect
+
+    t = sspec.SpectralTables(e_ref_kev=100.0)
+    sp = Spectra.from_tables(t)
+    rng = np.random.default_rng(6)
+    ac, ap = rng.uniform(0, 12, 5000), rng.uniform(0, 2, 5000)
+    if dtype == torch.float32:
+        ac, ap = np.float32(ac).astype(np.float64), np.float32(ap).astype(np.float64)
+    fh, fl, J = ospec.forward_model(t, ac, ap, jacobian=True)
+    a = torch.tensor(ac, dtype=dtype, device=cuda_dev)
+    p = torch.tensor(ap, dtype=dtype, device=cuda_dev)
+    gfh, gfl = torch.empty_like(a), torch.empty_like(a)
+    gJ = torch.empty((5000, 4), dtype=dtype, device=cuda_dev)
+    dect.forward_model(sp.handle, a, p, gfh, gfl, gJ)
+    assert np.max(np.abs(gfh.cpu().numpy() - fh)) < tol * 20 and np.max(np.abs(gfl.cpu().numpy() - fl)) < tol * 20
+    assert np.max(np.abs(gJ.cpu().numpy() - J) / np.abs(J)) < max(tol, 1e-6)

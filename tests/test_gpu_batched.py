@@ -1,0 +1,114 @@
+"""Batched solver over uneven slices (one launch per phase for all slices, block maps per slice).
+
+Each slice of a batch is an independent ADMM problem: the kernels take the same arithmetic path
+per slice and every reduction is per slice in a fixed order. The one launch-dependent choice is
+the backprojector's number of view groups (by default picked from the launch's total tile count),
+which sets the order in which a pixel's view partial sums are added; with the same group count a
+slice in a batch equals the same slice solved alone bit for bit. Small slices are also checked
+against the FP64 oracle."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+from conftest import rel_l2, to_dev
+from oracle import admm as oadmm
+from synth import geometry as G
+from synth.workloads import baggage_phantom, make_case, small_parallel_case, uneven_batch_shapes, quick_fan_case
+
+pytestmark = pytest.mark.gpu
+
+
+def _r32(a):
+    return np.float32(a).astype(np.float64)
+
+
+def _small_cases():
+    c0 = small_parallel_case(e_ref_kev=100.0)
+    g1 = G.Geometry(G.FAN_FLAT, 96, 80, 0.12, 70, 0.3, 2 * math.pi, 130, 0.15, 0.02, 16.0, 27.0)
+    c1 = make_case(g1, lambda g, r: baggage_phantom(g, r, n_objects=8), 2e5, 77, e_ref_kev=100.0)
+    g2 = G.fan_geometry(128, 180, 256)
+    c2 = make_case(g2, lambda g, r: baggage_phantom(g, r, n_objects=10), 2e5, 78, e_ref_kev=100.0)
+    cases = [c0, c1, c2]
+    for c in cases:
+        for k in ("m_h", "m_l", "w_h", "w_l"):
+            c[k] = _r32(c[k])
+    return cases
+
+
+def _solver(cases, dev, x0s, **params):
+    from paper_1905_00934_gb300 import Geometry, Solver, Spectra
+
+    geos = [Geometry(c["geom"]) for c in cases]
+    sp = Spectra.from_tables(cases[0]["spectra"])
+    sol = Solver(geos, sp, **params)
+    for b, c in enumerate(cases):
+        sol.set_data(b, *[to_dev(c[k], dev) for k in ("m_h", "m_l", "w_h", "w_l")],
+                     None if x0s[b] is None else to_dev(x0s[b], dev))
+    sol._keep = geos
+    return sol
+
+
+def test_batched_uneven_matches_single_slices_and_oracle(cuda_dev):
+    from paper_1905_00934_gb300 import dect
+
+    cases = _small_cases()
+    x0s = []
+    refs = []
+    for c in cases:
+        prob = oadmm.Problem(c["geom"], c["spectra"], c["m_h"], c["m_l"], c["w_h"], c["w_l"], oadmm.Params())
+        x0 = _r32(np.stack(oadmm.initial_image(prob)))
+        st = oadmm.state_from_image(prob, x0[0], x0[1])
+        for _ in range(5):
+            st = oadmm.admm_iteration(prob, st)
+        x0s.append(x0)
+        refs.append(st)
+    batched = _solver(cases, cuda_dev, x0s)
+    batched.step(5)
+    for b, c in enumerate(cases):
+        single = _solver([c], cuda_dev, [x0s[b]])
+        single.step(5)
+        xb = batched.get(b, dect.X).cpu().numpy()
+        xs = single.get(0, dect.X).cpu().numpy()
+        assert np.array_equal(xb, xs), f"slice {b}: batched differs from single"
+        assert np.array_equal(batched.get(b, dect.A).cpu().numpy(), single.get(0, dect.A).cpu().numpy())
+        assert batched.stats(b)["rho"] == single.stats(0)["rho"]
+        e_c, e_p = rel_l2(xb[0], refs[b].x[0]), rel_l2(xb[1], refs[b].x[1])
+        assert e_c <= 1e-4 and e_p <= 1e-4, (b, e_c, e_p)
+
+
+def test_batched_initialisation_matches_single(cuda_dev):
+    from paper_1905_00934_gb300 import dect
+
+    cases = _small_cases()
+    batched = _solver(cases, cuda_dev, [None, None, None])
+    batched.reconstruct(2)
+    for b, c in enumerate(cases):
+        single = _solver([c], cuda_dev, [None])
+        single.reconstruct(2)
+        assert np.array_equal(batched.get(b, dect.X).cpu().numpy(), single.get(0, dect.X).cpu().numpy())
+
+
+@pytest.mark.slow
+def test_uneven_64_slice_batch_full_size(cuda_dev):
+    # the batched workload at full size: 64 seeded slices, N 256..1024, 360..1440 views,
+    # 512..2048 bins, in one solver; sampled slices equal their single-slice runs bit for bit
+    from paper_1905_00934_gb300 import dect
+
+    from concurrent.futures import ThreadPoolExecutor
+
+    shapes = uneven_batch_shapes(64)
+    with ThreadPoolExecutor(max_workers=16) as ex:  # numpy releases the GIL in the heavy loops
+        cases = list(ex.map(lambda a: quick_fan_case(a[0], *a[1]), enumerate(shapes)))
+    batched = _solver(cases, cuda_dev, [None] * 64, bp_view_groups=4)
+    batched.reconstruct(2)
+    torch.cuda.synchronize()
+    big = int(np.argmax([n * v * b for n, v, b in shapes]))
+    small = int(np.argmin([n * v * b for n, v, b in shapes]))
+    for b in sorted({0, big, small, 63}):
+        single = _solver([cases[b]], cuda_dev, [None], bp_view_groups=4)
+        single.reconstruct(2)
+        xb = batched.get(b, dect.X).cpu().numpy()
+        assert np.all(np.isfinite(xb))
+        assert np.array_equal(xb, single.get(0, dect.X).cpu().numpy()), f"slice {b} {shapes[b]}"
