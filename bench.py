@@ -209,7 +209,8 @@ def run_dect(args):
         cases = list(ex.map(lambda b: baggage_fan_case(slice_index=rank * B + b), range(B)))
     geo = [Geometry(c["geom"]) for c in cases]
     spec = Spectra.from_tables(cases[0]["spectra"])
-    sol = Solver(geo, spec, kappa=BAGGAGE_KAPPA)
+    storage = {"f32": 0, "f16": 1, "bf16": 2}[args.storage]
+    sol = Solver(geo, spec, kappa=BAGGAGE_KAPPA, storage=storage)
     f32 = lambda a: torch.tensor(np.ascontiguousarray(a), dtype=torch.float32, device=dev)
     dev_data = [[f32(c[k]) for k in ("m_h", "m_l", "w_h", "w_l")] for c in cases]
     for b, c in enumerate(cases):
@@ -334,7 +335,7 @@ def run_dect(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": "fan beam 512x512, 720 views x 1024 bins, 40 objects, I0 2e5, "
                                    "UDM1-PCG1 x 100 iterations + initial image, B slices batched per launch",
-                       "batch_per_gpu": B, "l2": "flushed between steps (512 MB write)",
+                       "batch_per_gpu": B, "l2": "flushed between steps (512 MB write)", "storage": args.storage,
                        "plain_slices_per_s": (ws * B / (plain_ms / 1e3)) if plain_ms else None,
                        "batched_over_plain": (value / (ws * B / (plain_ms / 1e3))) if plain_ms else None,
                        "pe_gate": gate, "phases": phases},
@@ -359,6 +360,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--batch", type=int, default=8)
     ap.add_argument("--impl", default="dect", choices=["dect", "reference"])
+    ap.add_argument("--storage", default="f32", choices=["f32", "f16", "bf16"],
+                    help="storage of the sinogram vectors and projector textures (arithmetic stays f32/f64)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:

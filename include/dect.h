@@ -48,6 +48,11 @@ typedef enum { DECT_PARALLEL = 0, DECT_FAN_FLAT = 1 } dect_geom_kind;
 
 typedef enum { DECT_F32 = 0, DECT_F64 = 1 } dect_dtype;
 
+/* Storage format of the solver's sinogram-domain vectors (a, u^a, R x, the CG
+ * sinogram) and of the projector's pair textures; arithmetic stays float32
+ * (float64 in the decomposition's logs and 2x2 solve) in every format. */
+typedef enum { DECT_STORE_F32 = 0, DECT_STORE_F16 = 1, DECT_STORE_BF16 = 2 } dect_storage;
+
 /* Per-ray decomposition status codes (uint8 array of dect_decompose_rays). */
 enum { DECT_RAY_ACCEPTED = 0, DECT_RAY_REJECTED = 1, DECT_RAY_NONFINITE = 2 };
 
@@ -209,6 +214,8 @@ typedef struct {
                                     pixel's partial sums: results are bitwise reproducible for a fixed
                                     value, and a slice solved alone or in a batch gives identical bits
                                     when the value is the same (it is the one launch-dependent choice). */
+    int32_t storage;             /* dect_storage (DECT_STORE_F32): 16-bit formats halve the bytes of the
+                                    sinogram vectors and textures at the cost of their precision */
 } dect_params;
 
 /* Fills *p with the paper's values and the defaults above. */

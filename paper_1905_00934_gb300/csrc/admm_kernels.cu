@@ -10,6 +10,7 @@
 #include <math.h>
 
 #include "admm_kernels.cuh"
+#include "prec.cuh"
 
 namespace dect {
 
@@ -54,17 +55,18 @@ __device__ void slice_sum(const double* __restrict__ part, const int* __restrict
 // ---- Eq. 12 pieces ------------------------------------------------------------------------------
 
 // b = a + u^a - R x (the sinogram part of the CG residual)
+template <class S2>
 __global__ void __launch_bounds__(256) k_sino_resid(const SliceDesc* __restrict__ dsl, BlockMap map,
-                                                    const float2* __restrict__ a, const float2* __restrict__ ua,
-                                                    const float2* __restrict__ Rx, float2* __restrict__ b) {
+                                                    const S2* __restrict__ a, const S2* __restrict__ ua,
+                                                    const S2* __restrict__ Rx, S2* __restrict__ b) {
     int local;
     const int s = slice_of(map, blockIdx.x, local);
     const SliceDesc& d = dsl[s];
     const int64_t r = (int64_t)local * 256 + threadIdx.x;
     if (r >= (int64_t)d.g.nv * d.g.nb) return;
     const int64_t e = d.sino_off + r;
-    const float2 av = __ldg(a + e), uv = __ldg(ua + e), rv = __ldg(Rx + e);
-    b[e] = make_float2(av.x + uv.x - rv.x, av.y + uv.y - rv.y);
+    const float2 av = ldg2(a + e), uv = ldg2(ua + e), rv = ldg2(Rx + e);
+    st2(b + e, make_float2(av.x + uv.x - rv.x, av.y + uv.y - rv.y));
 }
 
 // rs = <r, M^-1 r> from the preconditioner's row partials; after the first CG step also beta
@@ -96,11 +98,12 @@ __global__ void __launch_bounds__(256) k_alpha(const double* __restrict__ part, 
 }
 
 // x += alpha p, r -= alpha A p (unless last) over the image blocks; R x += alpha q over the ray blocks
+template <class S2>
 __global__ void __launch_bounds__(256) k_cg_update(const SliceDesc* __restrict__ dsl, BlockMap pix, int nblk_pix,
                                                    BlockMap rays, const SliceScalars* __restrict__ sc,
                                                    float2* __restrict__ x, const float2* __restrict__ p,
                                                    float2* __restrict__ r, const float2* __restrict__ Ap,
-                                                   float2* __restrict__ Rx, const float2* __restrict__ q, int last) {
+                                                   S2* __restrict__ Rx, const S2* __restrict__ q, int last) {
     int local;
     if ((int)blockIdx.x < nblk_pix) {
         const int s = slice_of(pix, blockIdx.x, local);
@@ -128,11 +131,11 @@ __global__ void __launch_bounds__(256) k_cg_update(const SliceDesc* __restrict__
         if (k >= (int64_t)d.g.nv * d.g.nb) return;
         const float ac = (float)sc[s].alpha[0], ap = (float)sc[s].alpha[1];
         const int64_t e = d.sino_off + k;
-        const float2 qv = __ldg(q + e);
-        float2 rx = Rx[e];
+        const float2 qv = ldg2(q + e);
+        float2 rx = ld2(Rx + e);
         rx.x = fmaf(ac, qv.x, rx.x);
         rx.y = fmaf(ap, qv.y, rx.y);
-        Rx[e] = rx;
+        st2(Rx + e, rx);
     }
 }
 
@@ -248,10 +251,11 @@ __global__ void __launch_bounds__(256) k_rho_update(const double* __restrict__ p
 }
 
 // scaled duals follow rho: u /= factor (no-op when both factors are 1)
+template <class S2>
 __global__ void __launch_bounds__(256) k_dual_rescale(const SliceDesc* __restrict__ dsl, BlockMap pix, int nblk_pix,
                                                       BlockMap rays, const SliceScalars* __restrict__ sc,
                                                       float4* __restrict__ uy, float2* __restrict__ uz,
-                                                      float2* __restrict__ ua) {
+                                                      S2* __restrict__ ua) {
     int local;
     const bool img = (int)blockIdx.x < nblk_pix;
     const int s = img ? slice_of(pix, blockIdx.x, local) : slice_of(rays, blockIdx.x - nblk_pix, local);
@@ -276,10 +280,10 @@ __global__ void __launch_bounds__(256) k_dual_rescale(const SliceDesc* __restric
     } else {
         if (k >= (int64_t)d.g.nv * d.g.nb) return;
         const int64_t e = d.sino_off + k;
-        float2 u = ua[e];
+        float2 u = ld2(ua + e);
         u.x *= gc;
         u.y *= gp;
-        ua[e] = u;
+        st2(ua + e, u);
     }
 }
 
@@ -340,12 +344,13 @@ __global__ void __launch_bounds__(256) k_init_image(const SliceDesc* __restrict_
 }
 
 // y = D x, u^y = 0, z = x, u^z = 0 (image blocks); a = R x, u^a = 0, mu = mu0 (ray blocks)
+template <class S2>
 __global__ void __launch_bounds__(256) k_state_from_image(const SliceDesc* __restrict__ dsl, BlockMap pix, int nblk_pix,
                                                           BlockMap rays, const float2* __restrict__ x,
                                                           float4* __restrict__ y, float4* __restrict__ uy,
                                                           float2* __restrict__ z, float2* __restrict__ uz,
-                                                          const float2* __restrict__ Rx, float2* __restrict__ a,
-                                                          float2* __restrict__ ua, float* __restrict__ mu, float mu0) {
+                                                          const S2* __restrict__ Rx, S2* __restrict__ a,
+                                                          S2* __restrict__ ua, float* __restrict__ mu, float mu0) {
     int local;
     if ((int)blockIdx.x < nblk_pix) {
         const int s = slice_of(pix, blockIdx.x, local);
@@ -378,8 +383,8 @@ __global__ void __launch_bounds__(256) k_state_from_image(const SliceDesc* __res
         const int64_t k = (int64_t)local * 256 + threadIdx.x;
         if (k >= (int64_t)d.g.nv * d.g.nb) return;
         const int64_t e = d.sino_off + k;
-        a[e] = __ldg(Rx + e);
-        ua[e] = make_float2(0.f, 0.f);
+        a[e] = Rx[e];
+        st2(ua + e, make_float2(0.f, 0.f));
         mu[e] = mu0;
     }
 }
@@ -410,11 +415,12 @@ __global__ void k_interleave(const float* __restrict__ in, int64_t n, float2* __
     out[r] = make_float2(in[r], in[n + r]);
 }
 
-// interleaved float2 [n] -> planar [2][n]
-__global__ void k_deinterleave2(const float2* __restrict__ in, int64_t n, float* __restrict__ out) {
+// interleaved {c, p} [n] -> planar float [2][n]
+template <class S2>
+__global__ void k_deinterleave2(const S2* __restrict__ in, int64_t n, float* __restrict__ out) {
     const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= n) return;
-    const float2 v = in[r];
+    const float2 v = ld2(in + r);
     out[r] = v.x;
     out[n + r] = v.y;
 }
@@ -457,9 +463,24 @@ void launch_identity_precond(const SliceDesc* d, const BlockMap& rows, int nrows
 
 static unsigned nb(int64_t n, int t = 256) { return (unsigned)((n + t - 1) / t); }
 
-void launch_sino_resid(const SliceDesc* d, const BlockMap& rays, int nr, const float2* a, const float2* ua,
-                       const float2* Rx, float2* b, cudaStream_t st) {
-    k_sino_resid<<<nr, 256, 0, st>>>(d, rays, a, ua, Rx, b);
+#define DISPATCH_S2(prec, call)                                                  \
+    do {                                                                          \
+        if ((prec) == PREC_F16) {                                                 \
+            using S2 = __half2;                                                   \
+            call;                                                                 \
+        } else if ((prec) == PREC_BF16) {                                         \
+            using S2 = __nv_bfloat162;                                            \
+            call;                                                                 \
+        } else {                                                                  \
+            using S2 = float2;                                                    \
+            call;                                                                 \
+        }                                                                         \
+    } while (0)
+
+void launch_sino_resid(const SliceDesc* d, const BlockMap& rays, int nr, const void* a, const void* ua,
+                       const void* Rx, void* b, int prec, cudaStream_t st) {
+    DISPATCH_S2(prec, (k_sino_resid<S2><<<nr, 256, 0, st>>>(d, rays, (const S2*)a, (const S2*)ua, (const S2*)Rx,
+                                                            (S2*)b)));
 }
 void launch_rs_reduce(const double* part, const int* rows_prefix, SliceScalars* sc, int B, int first, cudaStream_t st) {
     k_rs_reduce<<<B, 256, 0, st>>>(part, rows_prefix, sc, first);
@@ -468,9 +489,10 @@ void launch_alpha(const double* part, const int* bp_prefix, SliceScalars* sc, in
     k_alpha<<<B, 256, 0, st>>>(part, bp_prefix, sc);
 }
 void launch_cg_update(const SliceDesc* d, const BlockMap& pix, int np, const BlockMap& rays, int nr,
-                      const SliceScalars* sc, float2* x, const float2* p, float2* r, const float2* Ap, float2* Rx,
-                      const float2* q, int last, cudaStream_t st) {
-    k_cg_update<<<np + nr, 256, 0, st>>>(d, pix, np, rays, sc, x, p, r, Ap, Rx, q, last);
+                      const SliceScalars* sc, float2* x, const float2* p, float2* r, const float2* Ap, void* Rx,
+                      const void* q, int last, int prec, cudaStream_t st) {
+    DISPATCH_S2(prec, (k_cg_update<S2><<<np + nr, 256, 0, st>>>(d, pix, np, rays, sc, x, p, r, Ap, (S2*)Rx,
+                                                                 (const S2*)q, last)));
 }
 void launch_cg_p(const SliceDesc* d, const BlockMap& pix, int np, const SliceScalars* sc, const float2* s, float2* p,
                  cudaStream_t st) {
@@ -486,8 +508,8 @@ void launch_rho_update(const double* part_udm, const int* rays_prefix, const dou
     k_rho_update<<<B, 256, 0, st>>>(part_udm, rays_prefix, part_img, pix_prefix, sc, mu_b, tau);
 }
 void launch_dual_rescale(const SliceDesc* d, const BlockMap& pix, int np, const BlockMap& rays, int nr,
-                         const SliceScalars* sc, float4* uy, float2* uz, float2* ua, cudaStream_t st) {
-    k_dual_rescale<<<np + nr, 256, 0, st>>>(d, pix, np, rays, sc, uy, uz, ua);
+                         const SliceScalars* sc, float4* uy, float2* uz, void* ua, int prec, cudaStream_t st) {
+    DISPATCH_S2(prec, (k_dual_rescale<S2><<<np + nr, 256, 0, st>>>(d, pix, np, rays, sc, uy, uz, (S2*)ua)));
 }
 void launch_xi(const SliceDesc* d, const BlockMap& pix, int np, const float2* x, const float2* truth, double* partial,
                SliceScalars* sc, int B, cudaStream_t st) {
@@ -499,9 +521,10 @@ void launch_init_image(const SliceDesc* d, const BlockMap& pix, int np, const in
     k_init_image<<<np, 256, 0, st>>>(d, pix, has_x0, x0, x, kappa);
 }
 void launch_state_from_image(const SliceDesc* d, const BlockMap& pix, int np, const BlockMap& rays, int nr,
-                             const float2* x, float4* y, float4* uy, float2* z, float2* uz, const float2* Rx,
-                             float2* a, float2* ua, float* mu, float mu0, cudaStream_t st) {
-    k_state_from_image<<<np + nr, 256, 0, st>>>(d, pix, np, rays, x, y, uy, z, uz, Rx, a, ua, mu, mu0);
+                             const float2* x, float4* y, float4* uy, float2* z, float2* uz, const void* Rx,
+                             void* a, void* ua, float* mu, float mu0, int prec, cudaStream_t st) {
+    DISPATCH_S2(prec, (k_state_from_image<S2><<<np + nr, 256, 0, st>>>(d, pix, np, rays, x, y, uy, z, uz,
+                                                                        (const S2*)Rx, (S2*)a, (S2*)ua, mu, mu0)));
 }
 void launch_reset_scalars(SliceScalars* sc, int B, double rho_c, double rho_p, cudaStream_t st) {
     k_reset_scalars<<<nb(B, 64), 64, 0, st>>>(sc, B, rho_c, rho_p);
@@ -512,8 +535,8 @@ void launch_pack_meas(const float* staged, int64_t n, float4* meas, cudaStream_t
 void launch_interleave(const float* in, int64_t n, float2* out, cudaStream_t st) {
     k_interleave<<<nb(n), 256, 0, st>>>(in, n, out);
 }
-void launch_deinterleave2(const float2* in, int64_t n, float* out, cudaStream_t st) {
-    k_deinterleave2<<<nb(n), 256, 0, st>>>(in, n, out);
+void launch_deinterleave2(const void* in, int64_t n, float* out, int prec, cudaStream_t st) {
+    DISPATCH_S2(prec, (k_deinterleave2<S2><<<nb(n), 256, 0, st>>>((const S2*)in, n, out)));
 }
 void launch_deinterleave4(const float4* in, int64_t n, float* out, cudaStream_t st) {
     k_deinterleave4<<<nb(n), 256, 0, st>>>(in, n, out);

@@ -5,13 +5,14 @@
 
 namespace dect {
 
-void launch_sino_resid(const SliceDesc* d, const BlockMap& rays, int nr, const float2* a, const float2* ua,
-                       const float2* Rx, float2* b, cudaStream_t st);
+// (prec: storage format of the sinogram-domain vectors a, u^a, R x, q / b; see prec.cuh)
+void launch_sino_resid(const SliceDesc* d, const BlockMap& rays, int nr, const void* a, const void* ua,
+                       const void* Rx, void* b, int prec, cudaStream_t st);
 void launch_rs_reduce(const double* part, const int* rows_prefix, SliceScalars* sc, int B, int first, cudaStream_t st);
 void launch_alpha(const double* part, const int* bp_prefix, SliceScalars* sc, int B, cudaStream_t st);
 void launch_cg_update(const SliceDesc* d, const BlockMap& pix, int np, const BlockMap& rays, int nr,
-                      const SliceScalars* sc, float2* x, const float2* p, float2* r, const float2* Ap, float2* Rx,
-                      const float2* q, int last, cudaStream_t st);
+                      const SliceScalars* sc, float2* x, const float2* p, float2* r, const float2* Ap, void* Rx,
+                      const void* q, int last, int prec, cudaStream_t st);
 void launch_cg_p(const SliceDesc* d, const BlockMap& pix, int np, const SliceScalars* sc, const float2* s, float2* p,
                  cudaStream_t st);
 void launch_image_update(const SliceDesc* d, const BlockMap& pix, int np, const SliceScalars* sc, double lam_c,
@@ -20,18 +21,18 @@ void launch_image_update(const SliceDesc* d, const BlockMap& pix, int np, const 
 void launch_rho_update(const double* part_udm, const int* rays_prefix, const double* part_img, const int* pix_prefix,
                        SliceScalars* sc, int B, double mu_b, double tau, cudaStream_t st);
 void launch_dual_rescale(const SliceDesc* d, const BlockMap& pix, int np, const BlockMap& rays, int nr,
-                         const SliceScalars* sc, float4* uy, float2* uz, float2* ua, cudaStream_t st);
+                         const SliceScalars* sc, float4* uy, float2* uz, void* ua, int prec, cudaStream_t st);
 void launch_xi(const SliceDesc* d, const BlockMap& pix, int np, const float2* x, const float2* truth, double* partial,
                SliceScalars* sc, int B, cudaStream_t st);
 void launch_init_image(const SliceDesc* d, const BlockMap& pix, int np, const int* has_x0, const float2* x0,
                        float2* x, float kappa, cudaStream_t st);
 void launch_state_from_image(const SliceDesc* d, const BlockMap& pix, int np, const BlockMap& rays, int nr,
-                             const float2* x, float4* y, float4* uy, float2* z, float2* uz, const float2* Rx,
-                             float2* a, float2* ua, float* mu, float mu0, cudaStream_t st);
+                             const float2* x, float4* y, float4* uy, float2* z, float2* uz, const void* Rx,
+                             void* a, void* ua, float* mu, float mu0, int prec, cudaStream_t st);
 void launch_reset_scalars(SliceScalars* sc, int B, double rho_c, double rho_p, cudaStream_t st);
 void launch_pack_meas(const float* staged, int64_t n, float4* meas, cudaStream_t st);
 void launch_interleave(const float* in, int64_t n, float2* out, cudaStream_t st);
-void launch_deinterleave2(const float2* in, int64_t n, float* out, cudaStream_t st);
+void launch_deinterleave2(const void* in, int64_t n, float* out, int prec, cudaStream_t st);
 void launch_deinterleave4(const float4* in, int64_t n, float* out, cudaStream_t st);
 
 }  // namespace dect

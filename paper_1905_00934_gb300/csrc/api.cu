@@ -11,6 +11,7 @@
 
 #include "admm_kernels.cuh"
 #include "dect_internal.cuh"
+#include "prec.cuh"
 
 namespace dect {
 static thread_local std::string g_err;
@@ -355,6 +356,7 @@ extern "C" void dect_params_default(dect_params* p) {
     p->precondition = 1;
     p->use_graph = 1;
     p->bp_view_groups = 0;
+    p->storage = DECT_STORE_F32;
 }
 
 struct MapBuf {
@@ -376,8 +378,11 @@ struct dect_admm {
     int max_px = 0, max_py = 0;
     int bp_G = 4;  // view groups per backprojector tile
     float2 *x = nullptr, *r = nullptr, *s = nullptr, *p = nullptr, *Ap = nullptr, *z = nullptr, *uz = nullptr;
-    float2 *x0 = nullptr, *truth = nullptr, *Rx = nullptr, *a = nullptr, *ua = nullptr, *q = nullptr, *Z = nullptr;
-    float4 *y = nullptr, *uy = nullptr, *meas = nullptr, *txb = nullptr, *tyb = nullptr;
+    float2 *x0 = nullptr, *truth = nullptr, *Z = nullptr;
+    void *Rx = nullptr, *a = nullptr, *ua = nullptr, *q = nullptr;  // sinogram vectors, storage format `prec`
+    void *txb = nullptr, *tyb = nullptr;                            // pair textures, storage format `prec`
+    float4 *y = nullptr, *uy = nullptr, *meas = nullptr;
+    int prec = PREC_F32;
     float *mu = nullptr, *H = nullptr, *Hn = nullptr, *stage = nullptr;
     uint8_t* status = nullptr;
     SliceScalars* sc = nullptr;
@@ -441,13 +446,13 @@ static cudaError_t upload_map(MapBuf& m) {
 
 // ---- enqueue helpers ---------------------------------------------------------------------------
 
-static void enq_project(dect_admm* A, const float2* img, float2* out, cudaStream_t st) {
+static void enq_project(dect_admm* A, const float2* img, void* out, cudaStream_t st) {
     const int B = A->B;
     pb(A, st);
-    launch_textures(A->ds, A->tx.map(B), A->tx.total, A->ty.map(B), A->ty.total, img, A->txb, A->tyb, st);
+    launch_textures(A->ds, A->tx.map(B), A->tx.total, A->ty.map(B), A->ty.total, img, A->txb, A->tyb, A->prec, st);
     pe(A, DECT_PHASE_TEXTURE, 2, st);
     pb(A, st);
-    launch_project(A->ds, A->rays.map(B), A->rays.total, A->txb, A->tyb, out, st);
+    launch_project(A->ds, A->rays.map(B), A->rays.total, A->txb, A->tyb, out, A->prec, st);
     pe(A, DECT_PHASE_PROJECT, 1, st);
     if (A->counting) A->cR += 2;
 }
@@ -477,10 +482,11 @@ static void enq_pcg(dect_admm* A, int n, bool with_grad, const float* H, cudaStr
     ep.p = A->p;
     ep.partial = A->part_pap;
     pb(A, st);
-    launch_sino_resid(A->ds, A->rays.map(B), A->rays.total, A->a, A->ua, A->Rx, A->q, st);
+    launch_sino_resid(A->ds, A->rays.map(B), A->rays.total, A->a, A->ua, A->Rx, A->q, A->prec, st);
     pe(A, DECT_PHASE_UPDATE, 1, st);
     pb(A, st);
-    launch_backproject(with_grad ? BP_R0 : BP_R0_NOGRAD, A->ds, A->bp.map(B), A->bp.total, A->q, A->r, ep, A->bp_G, st);
+    launch_backproject(with_grad ? BP_R0 : BP_R0_NOGRAD, A->ds, A->bp.map(B), A->bp.total, A->q, A->r, ep, A->bp_G,
+                       A->prec, st);
     pe(A, DECT_PHASE_BACKPROJECT, 1, st);
     if (A->counting) A->cRT += 2;
     enq_precond(A, H, A->r, A->p, st);
@@ -490,7 +496,8 @@ static void enq_pcg(dect_admm* A, int n, bool with_grad, const float* H, cudaStr
     for (int it = 0; it < n; ++it) {
         enq_project(A, A->p, A->q, st);
         pb(A, st);
-        launch_backproject(with_grad ? BP_AP : BP_AP_NOGRAD, A->ds, A->bp.map(B), A->bp.total, A->q, A->Ap, ep, A->bp_G, st);
+        launch_backproject(with_grad ? BP_AP : BP_AP_NOGRAD, A->ds, A->bp.map(B), A->bp.total, A->q, A->Ap, ep,
+                           A->bp_G, A->prec, st);
         pe(A, DECT_PHASE_BACKPROJECT, 1, st);
         if (A->counting) A->cRT += 2;
         pb(A, st);
@@ -499,7 +506,7 @@ static void enq_pcg(dect_admm* A, int n, bool with_grad, const float* H, cudaStr
         const int last = it == n - 1;
         pb(A, st);
         launch_cg_update(A->ds, A->pix.map(B), A->pix.total, A->rays.map(B), A->rays.total, A->sc, A->x, A->p, A->r,
-                         A->Ap, A->Rx, A->q, last, st);
+                         A->Ap, A->Rx, A->q, last, A->prec, st);
         pe(A, DECT_PHASE_UPDATE, 1, st);
         if (!last) {
             enq_precond(A, H, A->r, A->s, st);
@@ -518,7 +525,7 @@ static void enq_iteration(dect_admm* A, cudaStream_t st) {
     enq_pcg(A, A->P.n_pcg, true, A->H, st);
     pb(A, st);
     launch_udm_admm(A->ds, A->rays.map(B), A->rays.total, A->spec->dev(), A->meas, A->Rx, A->ua, A->a, A->mu,
-                    A->status, A->sc, A->P.m_udm, A->part_udm, st);
+                    A->status, A->sc, A->P.m_udm, A->part_udm, A->prec, st);
     pe(A, DECT_PHASE_UDM, 1, st);
     if (A->counting) A->cF += 4 * A->P.m_udm;
     pb(A, st);
@@ -530,7 +537,7 @@ static void enq_iteration(dect_admm* A, cudaStream_t st) {
     pe(A, DECT_PHASE_REDUCE, 1, st);
     pb(A, st);
     launch_dual_rescale(A->ds, A->pix.map(B), A->pix.total, A->rays.map(B), A->rays.total, A->sc, A->uy, A->uz, A->ua,
-                        st);
+                        A->prec, st);
     pe(A, DECT_PHASE_UPDATE, 1, st);
 }
 
@@ -573,14 +580,14 @@ static dect_status enq_initialize(dect_admm* A, cudaStream_t st) {
     for (int b = 0; b < B; ++b) all_x0 = all_x0 && A->has_x0[b];
     if (!all_x0) {
         CUDA_TRY(cudaMemsetAsync(A->x, 0, sizeof(float2) * A->n_img, st));
-        CUDA_TRY(cudaMemsetAsync(A->Rx, 0, sizeof(float2) * A->n_sino, st));
-        CUDA_TRY(cudaMemsetAsync(A->ua, 0, sizeof(float2) * A->n_sino, st));
+        CUDA_TRY(cudaMemsetAsync(A->Rx, 0, sino_bytes(A->prec) * A->n_sino, st));
+        CUDA_TRY(cudaMemsetAsync(A->ua, 0, sino_bytes(A->prec) * A->n_sino, st));
         CUDA_TRY(cudaMemsetAsync(A->y, 0, sizeof(float4) * A->n_img, st));
         CUDA_TRY(cudaMemsetAsync(A->uy, 0, sizeof(float4) * A->n_img, st));
         CUDA_TRY(cudaMemsetAsync(A->z, 0, sizeof(float2) * A->n_img, st));
         CUDA_TRY(cudaMemsetAsync(A->uz, 0, sizeof(float2) * A->n_img, st));
         launch_udm_init(A->ds, A->rays.map(B), A->rays.total, A->spec->dev(), A->meas, A->a, A->mu, A->P.rho0_p,
-                        A->P.init_udm_iters, (float)A->spec->abar_low, A->P.lm_mu0, st);
+                        A->P.init_udm_iters, (float)A->spec->abar_low, A->P.lm_mu0, A->prec, st);
         A->cF += 4 * A->P.init_udm_iters;
         launch_reset_scalars(A->sc, B, A->P.rho0_c, A->P.rho0_p, st);
         enq_pcg(A, A->P.init_pcg_iters, false, A->Hn, st);
@@ -588,7 +595,7 @@ static dect_status enq_initialize(dect_admm* A, cudaStream_t st) {
     launch_init_image(A->ds, A->pix.map(B), A->pix.total, A->d_has_x0, A->x0, A->x, (float)A->P.kappa, st);
     enq_project(A, A->x, A->Rx, st);
     launch_state_from_image(A->ds, A->pix.map(B), A->pix.total, A->rays.map(B), A->rays.total, A->x, A->y, A->uy,
-                            A->z, A->uz, A->Rx, A->a, A->ua, A->mu, (float)A->P.lm_mu0, st);
+                            A->z, A->uz, A->Rx, A->a, A->ua, A->mu, (float)A->P.lm_mu0, A->prec, st);
     launch_reset_scalars(A->sc, B, A->P.rho0_c, A->P.rho0_p, st);
     CUDA_TRY(cudaGetLastError());
     A->initialized = true;
@@ -609,9 +616,12 @@ static dect_status compute_responses(dect_admm* A) {
         CUDA_TRY(cudaMemcpyAsync(A->stage + c, one, sizeof(float), cudaMemcpyHostToDevice, st));
         CUDA_TRY(cudaMemcpyAsync(A->stage + np + c, one, sizeof(float), cudaMemcpyHostToDevice, st));
         CUDA_TRY(cudaStreamSynchronize(st));
-        project_single(sd, A->stage, 2, A->x + sd.img_off, A->txb + sd.tx_off, A->tyb + sd.ty_off, A->stage + 2 * np,
-                       st);
-        backproject_single(sd, A->stage + 2 * np, 2, A->q + sd.sino_off, A->stage, st);
+        // float32 projector pair through the geometry's own workspace (independent of the storage format)
+        dect_geom* g = A->geoms[b];
+        dect_status ws = geom_workspace(g);
+        if (ws != DECT_OK) return ws;
+        project_single(sd, A->stage, 2, g->ws_img, g->ws_tx, g->ws_ty, A->stage + 2 * np, st);
+        backproject_single(sd, A->stage + 2 * np, 2, g->ws_sino, A->stage, st);
         launch_interleave(A->stage, np, A->r + sd.img_off, st);
         // one-slice descriptor and column map
         SliceDesc one_slice = sd;
@@ -644,6 +654,8 @@ extern "C" dect_status dect_admm_create(dect_geom* const* geoms, int32_t B, cons
     if (!geoms || !spec || !P || !out) DECT_FAIL(DECT_EINVAL, "dect_admm_create: null argument");
     *out = nullptr;
     if (B < 1 || B > 4096) DECT_FAIL(DECT_EINVAL, "dect_admm_create: n_slices must be in [1, 4096]");
+    if (P->storage != DECT_STORE_F32 && P->storage != DECT_STORE_F16 && P->storage != DECT_STORE_BF16)
+        DECT_FAIL(DECT_EINVAL, "dect_admm_create: storage must be DECT_STORE_F32, F16 or BF16");
     if (P->bp_view_groups < 0 || P->bp_view_groups > 8)
         DECT_FAIL(DECT_EINVAL, "dect_admm_create: bp_view_groups must be in [0, 8]");
     if (P->m_udm < 1 || P->n_pcg < 1 || P->m_udm > 64 || P->n_pcg > 64)
@@ -664,6 +676,7 @@ extern "C" dect_status dect_admm_create(dect_geom* const* geoms, int32_t B, cons
 
     dect_admm* A = new dect_admm();
     A->B = B;
+    A->prec = P->storage;
     A->spec = spec;
     A->P = *P;
     A->geoms.assign(geoms, geoms + B);
@@ -721,12 +734,12 @@ extern "C" dect_status dect_admm_create(dect_geom* const* geoms, int32_t B, cons
     } while (0)
     ALLOC(A->ds, B);
     for (float2** pp : {&A->x, &A->r, &A->s, &A->p, &A->Ap, &A->z, &A->uz, &A->x0, &A->truth}) ALLOC(*pp, A->n_img);
-    for (float2** pp : {&A->Rx, &A->a, &A->ua, &A->q}) ALLOC(*pp, A->n_sino);
+    for (void** pp : {&A->Rx, &A->a, &A->ua, &A->q}) ALLOC(*(char**)pp, A->n_sino * sino_bytes(A->prec));
     ALLOC(A->y, A->n_img);
     ALLOC(A->uy, A->n_img);
     ALLOC(A->meas, A->n_sino);
-    ALLOC(A->txb, A->n_tx);
-    ALLOC(A->tyb, A->n_ty);
+    ALLOC(*(char**)&A->txb, A->n_tx * texel_bytes(A->prec));
+    ALLOC(*(char**)&A->tyb, A->n_ty * texel_bytes(A->prec));
     ALLOC(A->mu, A->n_sino);
     ALLOC(A->status, A->n_sino);
     ALLOC(A->Z, A->n_fft);
@@ -916,14 +929,14 @@ extern "C" dect_status dect_admm_get(const dect_admm* A, int32_t b, int32_t whic
     }
     if (dst_bytes < need) DECT_FAIL(DECT_EINVAL, "dect_admm_get: destination too small");
     switch (which) {
-        case 0: launch_deinterleave2(A->x + sd.img_off, np, A->stage, st); break;
-        case 1: launch_deinterleave2(A->Rx + sd.sino_off, nr, A->stage, st); break;
-        case 2: launch_deinterleave2(A->a + sd.sino_off, nr, A->stage, st); break;
-        case 3: launch_deinterleave2(A->ua + sd.sino_off, nr, A->stage, st); break;
+        case 0: launch_deinterleave2(A->x + sd.img_off, np, A->stage, PREC_F32, st); break;
+        case 1: launch_deinterleave2((const char*)A->Rx + sd.sino_off * sino_bytes(A->prec), nr, A->stage, A->prec, st); break;
+        case 2: launch_deinterleave2((const char*)A->a + sd.sino_off * sino_bytes(A->prec), nr, A->stage, A->prec, st); break;
+        case 3: launch_deinterleave2((const char*)A->ua + sd.sino_off * sino_bytes(A->prec), nr, A->stage, A->prec, st); break;
         case 4: launch_deinterleave4(A->y + sd.img_off, np, A->stage, st); break;
         case 5: launch_deinterleave4(A->uy + sd.img_off, np, A->stage, st); break;
-        case 6: launch_deinterleave2(A->z + sd.img_off, np, A->stage, st); break;
-        case 7: launch_deinterleave2(A->uz + sd.img_off, np, A->stage, st); break;
+        case 6: launch_deinterleave2(A->z + sd.img_off, np, A->stage, PREC_F32, st); break;
+        case 7: launch_deinterleave2(A->uz + sd.img_off, np, A->stage, PREC_F32, st); break;
         default: break;
     }
     if (which == 8)

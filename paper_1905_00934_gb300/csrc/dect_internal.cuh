@@ -117,12 +117,13 @@ struct BpEpilogue {
 
 // projector.cu
 cudaError_t build_ray_table(const dect_geom_desc& d, int4* rays, float4* views, cudaStream_t st);
+// (prec: storage format of textures and sinogram vectors, see prec.cuh)
 void launch_textures(const SliceDesc* dsl, const BlockMap& mx, int nbx, const BlockMap& my, int nby,
-                     const float2* img, float4* tx, float4* ty, cudaStream_t st);
-void launch_project(const SliceDesc* dsl, const BlockMap& map, int nblk, const float4* tx, const float4* ty,
-                    float2* out_interleaved, cudaStream_t st);
-void launch_backproject(int mode, const SliceDesc* dsl, const BlockMap& map, int nblk, const float2* sino,
-                        float2* out, const BpEpilogue& ep, int groups, cudaStream_t st);
+                     const float2* img, void* tx, void* ty, int prec, cudaStream_t st);
+void launch_project(const SliceDesc* dsl, const BlockMap& map, int nblk, const void* tx, const void* ty, void* out,
+                    int prec, cudaStream_t st);
+void launch_backproject(int mode, const SliceDesc* dsl, const BlockMap& map, int nblk, const void* sino,
+                        float2* out, const BpEpilogue& ep, int groups, int prec, cudaStream_t st);
 int bp_groups(int tiles);
 void project_single(const SliceDesc& sd, const float* img, int nch, float2* scratch, float4* tx, float4* ty,
                     float* out, cudaStream_t st);
@@ -137,10 +138,10 @@ constexpr int kBpTile = 16;
 
 // udm.cu
 void launch_udm_admm(const SliceDesc* dsl, const BlockMap& map, int nblk, const SpecDev& sp, const float4* meas,
-                     const float2* Rx, float2* ua, float2* a, float* mu, uint8_t* status,
-                     const SliceScalars* sc, int iters, double* partial, cudaStream_t st);
+                     const void* Rx, void* ua, void* a, float* mu, uint8_t* status,
+                     const SliceScalars* sc, int iters, double* partial, int prec, cudaStream_t st);
 void launch_udm_init(const SliceDesc* dsl, const BlockMap& map, int nblk, const SpecDev& sp, const float4* meas,
-                     float2* a, float* mu, double rho_p, int iters, float abar, double mu0, cudaStream_t st);
+                     void* a, float* mu, double rho_p, int iters, float abar, double mu0, int prec, cudaStream_t st);
 void launch_udm_rays(const SpecDev& sp, int64_t n, const float* mh, const float* ml, const float* wh,
                      const float* wl, const float* vc, const float* vp, double rho_c, double rho_p, int iters,
                      float* ac, float* ap, float* mu, uint8_t* status, cudaStream_t st);

@@ -26,6 +26,7 @@
 #include <math.h>
 
 #include "dect_internal.cuh"
+#include "prec.cuh"
 #include "ray_fixed.cuh"
 
 namespace dect {
@@ -96,8 +97,9 @@ __device__ __forceinline__ float2 img_at(const float2* __restrict__ img, int nx,
 }
 
 // TX[i][jj] from a 32 (jj) x 32 (i) tile; rows jj-2 .. jj+29 staged in shared memory.
+template <class TX>
 __global__ void __launch_bounds__(256) k_texture_x(const SliceDesc* __restrict__ dsl, BlockMap map,
-                                                   const float2* __restrict__ img, float4* __restrict__ tx) {
+                                                   const float2* __restrict__ img, TX* __restrict__ tx) {
     __shared__ float2 tile[33][33];
     int local;
     const int s = slice_of(map, blockIdx.x, local);
@@ -112,21 +114,19 @@ __global__ void __launch_bounds__(256) k_texture_x(const SliceDesc* __restrict__
         tile[rr][cc] = img_at(im, nx, ny, jt - 2 + rr, it + cc);
     }
     __syncthreads();
-    float4* out = tx + d.tx_off;
+    TX* out = tx + d.tx_off;
     const int ld = ny + 3;
     for (int e = threadIdx.x; e < 32 * 32; e += blockDim.x) {
         const int ci = e / 32, cj = e % 32;  // consecutive threads walk jj: coalesced stores
         const int i = it + ci, jj = jt + cj;
-        if (i < nx && jj < ld) {
-            const float2 a = tile[cj][ci], b = tile[cj + 1][ci];
-            out[(size_t)i * ld + jj] = make_float4(a.x, a.y, b.x, b.y);
-        }
+        if (i < nx && jj < ld) sttex(out + (size_t)i * ld + jj, tile[cj][ci], tile[cj + 1][ci]);
     }
 }
 
 // TY[j][ii], one entry per thread.
+template <class TX>
 __global__ void __launch_bounds__(256) k_texture_y(const SliceDesc* __restrict__ dsl, BlockMap map,
-                                                   const float2* __restrict__ img, float4* __restrict__ ty) {
+                                                   const float2* __restrict__ img, TX* __restrict__ ty) {
     int local;
     const int s = slice_of(map, blockIdx.x, local);
     const SliceDesc& d = dsl[s];
@@ -135,8 +135,7 @@ __global__ void __launch_bounds__(256) k_texture_y(const SliceDesc* __restrict__
     if (e >= (int64_t)ny * ld) return;
     const int j = (int)(e / ld), ii = (int)(e % ld);
     const float2* im = img + d.img_off;
-    const float2 a = img_at(im, nx, ny, j, ii - 2), b = img_at(im, nx, ny, j, ii - 1);
-    ty[d.ty_off + e] = make_float4(a.x, a.y, b.x, b.y);
+    sttex(ty + d.ty_off + e, img_at(im, nx, ny, j, ii - 2), img_at(im, nx, ny, j, ii - 1));
 }
 
 static int tx_blocks(int nx, int ny) { return ((nx + 31) / 32) * ((ny + 3 + 31) / 32); }
@@ -144,9 +143,17 @@ static int ty_blocks(int nx, int ny) { return (int)(((int64_t)ny * (nx + 3) + 25
 
 // Textures of the batched solver: two maps (TX tiles, TY blocks).
 void launch_textures(const SliceDesc* dsl, const BlockMap& mx, int nbx, const BlockMap& my, int nby,
-                     const float2* img, float4* tx, float4* ty, cudaStream_t st) {
-    k_texture_x<<<nbx, 256, 0, st>>>(dsl, mx, img, tx);
-    k_texture_y<<<nby, 256, 0, st>>>(dsl, my, img, ty);
+                     const float2* img, void* tx, void* ty, int prec, cudaStream_t st) {
+    if (prec == PREC_F16) {
+        k_texture_x<TexH><<<nbx, 256, 0, st>>>(dsl, mx, img, (TexH*)tx);
+        k_texture_y<TexH><<<nby, 256, 0, st>>>(dsl, my, img, (TexH*)ty);
+    } else if (prec == PREC_BF16) {
+        k_texture_x<TexB><<<nbx, 256, 0, st>>>(dsl, mx, img, (TexB*)tx);
+        k_texture_y<TexB><<<nby, 256, 0, st>>>(dsl, my, img, (TexB*)ty);
+    } else {
+        k_texture_x<float4><<<nbx, 256, 0, st>>>(dsl, mx, img, (float4*)tx);
+        k_texture_y<float4><<<nby, 256, 0, st>>>(dsl, my, img, (float4*)ty);
+    }
 }
 
 // planar input (1 or 2 channels) -> interleaved float2 image
@@ -160,31 +167,33 @@ __global__ void k_pack_planar(const float* __restrict__ in, int nch, int64_t n, 
 // forward projector
 
 // Sum over the ray's samples of the interpolated {c, p}; returns unweighted sums.
-__device__ __forceinline__ float2 ray_sum(const int4 P, const GeomDev& g, const float4* __restrict__ tx,
-                                          const float4* __restrict__ ty) {
+template <class TX>
+__device__ __forceinline__ float2 ray_sum(const int4 P, const GeomDev& g, const TX* __restrict__ tx,
+                                          const TX* __restrict__ ty) {
     float ac = 0.f, ap = 0.f;
     const bool ax = ray_axis(P);
     const int n_along = ax ? g.ny : g.nx, n_across = ax ? g.nx : g.ny;
-    const float4* tex = ax ? ty : tx;
+    const TX* tex = ax ? ty : tx;
     const int ld = n_across + 3;
     int lo, hi;
     sample_range(P, n_along, n_across, lo, hi);
     const long long step = ray_step(P);
     long long q = ray_q0(P) + (long long)lo * step;
-    const float4* row = tex + (size_t)lo * ld;
+    const TX* row = tex + (size_t)lo * ld;
     for (int t = lo; t <= hi; ++t, q += step, row += ld) {
         const int jj = min(max(pos_floor(q) + 2, 0), n_across + 2);
         const float f = frac_of(q);
-        const float4 v = __ldg(row + jj);
+        const float4 v = ldtex(row + jj);
         ac += fmaf(f, v.z - v.x, v.x);
         ap += fmaf(f, v.w - v.y, v.y);
     }
     return make_float2(ac, ap);
 }
 
+template <class S2, class TX>
 __global__ void __launch_bounds__(kRaysPerBlock) k_project(const SliceDesc* __restrict__ dsl, BlockMap map,
-                                                           const float4* __restrict__ tx,
-                                                           const float4* __restrict__ ty, float2* __restrict__ out) {
+                                                           const TX* __restrict__ tx, const TX* __restrict__ ty,
+                                                           S2* __restrict__ out) {
     int local;
     const int s = slice_of(map, blockIdx.x, local);
     const SliceDesc& d = dsl[s];
@@ -193,7 +202,7 @@ __global__ void __launch_bounds__(kRaysPerBlock) k_project(const SliceDesc* __re
     const int4 P = __ldg(d.g.rays + r);
     const float2 acc = ray_sum(P, d.g, tx + d.tx_off, ty + d.ty_off);
     const float w = ray_w(P);
-    out[d.sino_off + r] = make_float2(w * acc.x, w * acc.y);
+    st2(out + d.sino_off + r, make_float2(w * acc.x, w * acc.y));
 }
 
 __global__ void __launch_bounds__(kRaysPerBlock) k_project_planar(SliceDesc d, const float4* __restrict__ tx,
@@ -209,9 +218,17 @@ __global__ void __launch_bounds__(kRaysPerBlock) k_project_planar(SliceDesc d, c
     if (nch > 1) out[n + r] = w * acc.y;
 }
 
-void launch_project(const SliceDesc* dsl, const BlockMap& map, int nblk, const float4* tx, const float4* ty,
-                    float2* out, cudaStream_t st) {
-    k_project<<<nblk, kRaysPerBlock, 0, st>>>(dsl, map, tx, ty, out);
+void launch_project(const SliceDesc* dsl, const BlockMap& map, int nblk, const void* tx, const void* ty, void* out,
+                    int prec, cudaStream_t st) {
+    if (prec == PREC_F16)
+        k_project<__half2, TexH><<<nblk, kRaysPerBlock, 0, st>>>(dsl, map, (const TexH*)tx, (const TexH*)ty,
+                                                                  (__half2*)out);
+    else if (prec == PREC_BF16)
+        k_project<__nv_bfloat162, TexB><<<nblk, kRaysPerBlock, 0, st>>>(dsl, map, (const TexB*)tx, (const TexB*)ty,
+                                                                         (__nv_bfloat162*)out);
+    else
+        k_project<float2, float4><<<nblk, kRaysPerBlock, 0, st>>>(dsl, map, (const float4*)tx, (const float4*)ty,
+                                                                   (float2*)out);
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -224,8 +241,8 @@ struct Block2x2 {
 
 // One candidate ray for the block with top-left pixel (i, j). AX: 0 or 1 when the ray's axis is
 // known to the caller, -1 to read it from the entry.
-template <int AX>
-__device__ __forceinline__ void block_ray(const int4 P, const float2* __restrict__ sv, int i, int j, Block2x2& a) {
+template <int AX, class S2>
+__device__ __forceinline__ void block_ray(const int4 P, const S2* __restrict__ sv, int i, int j, Block2x2& a) {
     const bool ax = AX < 0 ? ray_axis(P) : (AX == 1);
     // samples at the block's two columns (axis 0) or rows (axis 1)
     const long long qa = ray_pos(P, ax ? j : i);
@@ -239,7 +256,7 @@ __device__ __forceinline__ void block_ray(const int4 P, const float2* __restrict
     // axis 0: sample s at column i + s, across offset r at row j + r -> pixel (r, s)
     // axis 1: sample s at row j + s, across offset r at column i + r -> pixel (s, r)
     const float w01 = ax ? a1 : b0, w10 = ax ? b0 : a1;
-    const float2 s2 = __ldg(sv);
+    const float2 s2 = ldg2(sv);
     const float wr = ray_w(P);
     const float sc = wr * s2.x, sp = wr * s2.y;
     a.c00 = fmaf(a0, sc, a.c00);
@@ -257,7 +274,8 @@ __device__ __forceinline__ void block_ray(const int4 P, const float2* __restrict
 // geometry check keeps the source at least 4.25 pixels away) and their sampling axis changes at
 // most once, where the direction crosses a diagonal: when the first and last candidate share an
 // axis, every candidate between them does too (specialised loop).
-__device__ __forceinline__ void gather_block(const GeomDev& g, const float2* __restrict__ sino, int i, int j, int v0,
+template <class S2>
+__device__ __forceinline__ void gather_block(const GeomDev& g, const S2* __restrict__ sino, int i, int j, int v0,
                                              int dv, Block2x2& a) {
     const float xc = ((float)i + 0.5f - g.cx) * g.pix, yc = ((float)j + 0.5f - g.cy) * g.pix;
     for (int v = v0; v < g.nv; v += dv) {
@@ -265,16 +283,16 @@ __device__ __forceinline__ void gather_block(const GeomDev& g, const float2* __r
         const CandRange cr = block_candidates<-1>(g, V.x, V.y, xc, yc);
         if (cr.lo > cr.hi) continue;
         const int4* rv = g.rays + (size_t)v * g.nb;
-        const float2* sv = sino + (size_t)v * g.nb;
+        const S2* sv = sino + (size_t)v * g.nb;
         const bool ax_lo = __ldg(&rv[cr.lo].w) < 0, ax_hi = __ldg(&rv[cr.hi].w) < 0;
         if (ax_lo == ax_hi) {
             if (ax_lo) {
-                for (int k = cr.lo; k <= cr.hi; ++k) block_ray<1>(__ldg(rv + k), sv + k, i, j, a);
+                for (int k = cr.lo; k <= cr.hi; ++k) block_ray<1, S2>(__ldg(rv + k), sv + k, i, j, a);
             } else {
-                for (int k = cr.lo; k <= cr.hi; ++k) block_ray<0>(__ldg(rv + k), sv + k, i, j, a);
+                for (int k = cr.lo; k <= cr.hi; ++k) block_ray<0, S2>(__ldg(rv + k), sv + k, i, j, a);
             }
         } else {
-            for (int k = cr.lo; k <= cr.hi; ++k) block_ray<-1>(__ldg(rv + k), sv + k, i, j, a);
+            for (int k = cr.lo; k <= cr.hi; ++k) block_ray<-1, S2>(__ldg(rv + k), sv + k, i, j, a);
         }
     }
 }
@@ -329,8 +347,8 @@ __device__ __forceinline__ float4 grad_of(const float2* __restrict__ p, int nx, 
 // so the result is deterministic.
 constexpr int kBpMaxGroups = 8;
 
-template <int MODE>
-__device__ __forceinline__ void backproject_tile(const SliceDesc& d, int local, const float2* __restrict__ sino,
+template <int MODE, class S2>
+__device__ __forceinline__ void backproject_tile(const SliceDesc& d, int local, const S2* __restrict__ sino,
                                                  float2* __restrict__ out, const BpEpilogue& ep, float* __restrict__ planar,
                                                  int nch) {
     __shared__ float red[kBpMaxGroups][8][64];
@@ -427,19 +445,19 @@ __device__ __forceinline__ void backproject_tile(const SliceDesc& d, int local, 
     }
 }
 
-template <int MODE>
+template <int MODE, class S2>
 __global__ void __launch_bounds__(64 * kBpMaxGroups) k_backproject(const SliceDesc* __restrict__ dsl, BlockMap map,
-                                                                   const float2* __restrict__ sino,
+                                                                   const S2* __restrict__ sino,
                                                                    float2* __restrict__ out, BpEpilogue ep) {
     int local;
     const int s = slice_of(map, blockIdx.x, local);
-    backproject_tile<MODE>(dsl[s], local, sino, out, ep, nullptr, 0);
+    backproject_tile<MODE, S2>(dsl[s], local, sino, out, ep, nullptr, 0);
 }
 
 __global__ void __launch_bounds__(64 * kBpMaxGroups) k_backproject_planar(SliceDesc d, const float2* __restrict__ sino,
                                                                           float* __restrict__ out, int nch) {
     BpEpilogue ep{};
-    backproject_tile<BP_PLAIN>(d, blockIdx.x, sino, nullptr, ep, out, nch);
+    backproject_tile<BP_PLAIN, float2>(d, blockIdx.x, sino, nullptr, ep, out, nch);
 }
 
 int bp_tiles(int nx, int ny) { return ((nx + kBpTile - 1) / kBpTile) * ((ny + kBpTile - 1) / kBpTile); }
@@ -454,24 +472,35 @@ int bp_groups(int tiles) {
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         for (int G = 1; G <= kBpMaxGroups; ++G)
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[G], k_backproject<BP_AP>, 64 * G, 0);
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[G], k_backproject<BP_AP, float2>, 64 * G, 0);
     }
     for (int G = kBpMaxGroups; G >= 1; --G)
         if ((long long)occ[G] * sms >= tiles) return G;
     return 4;
 }
 
-void launch_backproject(int mode, const SliceDesc* dsl, const BlockMap& map, int nblk, const float2* sino,
-                        float2* out, const BpEpilogue& ep, int groups, cudaStream_t st) {
-    const int T = 64 * groups;
+template <class S2>
+static void launch_bp_t(int mode, const SliceDesc* dsl, const BlockMap& map, int nblk, const S2* sino, float2* out,
+                        const BpEpilogue& ep, int T, cudaStream_t st) {
     switch (mode) {
-        case BP_PLAIN: k_backproject<BP_PLAIN><<<nblk, T, 0, st>>>(dsl, map, sino, out, ep); break;
-        case BP_R0: k_backproject<BP_R0><<<nblk, T, 0, st>>>(dsl, map, sino, out, ep); break;
-        case BP_AP: k_backproject<BP_AP><<<nblk, T, 0, st>>>(dsl, map, sino, out, ep); break;
-        case BP_R0_NOGRAD: k_backproject<BP_R0_NOGRAD><<<nblk, T, 0, st>>>(dsl, map, sino, out, ep); break;
-        case BP_AP_NOGRAD: k_backproject<BP_AP_NOGRAD><<<nblk, T, 0, st>>>(dsl, map, sino, out, ep); break;
+        case BP_PLAIN: k_backproject<BP_PLAIN, S2><<<nblk, T, 0, st>>>(dsl, map, sino, out, ep); break;
+        case BP_R0: k_backproject<BP_R0, S2><<<nblk, T, 0, st>>>(dsl, map, sino, out, ep); break;
+        case BP_AP: k_backproject<BP_AP, S2><<<nblk, T, 0, st>>>(dsl, map, sino, out, ep); break;
+        case BP_R0_NOGRAD: k_backproject<BP_R0_NOGRAD, S2><<<nblk, T, 0, st>>>(dsl, map, sino, out, ep); break;
+        case BP_AP_NOGRAD: k_backproject<BP_AP_NOGRAD, S2><<<nblk, T, 0, st>>>(dsl, map, sino, out, ep); break;
         default: break;
     }
+}
+
+void launch_backproject(int mode, const SliceDesc* dsl, const BlockMap& map, int nblk, const void* sino,
+                        float2* out, const BpEpilogue& ep, int groups, int prec, cudaStream_t st) {
+    const int T = 64 * groups;
+    if (prec == PREC_F16)
+        launch_bp_t(mode, dsl, map, nblk, (const __half2*)sino, out, ep, T, st);
+    else if (prec == PREC_BF16)
+        launch_bp_t(mode, dsl, map, nblk, (const __nv_bfloat162*)sino, out, ep, T, st);
+    else
+        launch_bp_t(mode, dsl, map, nblk, (const float2*)sino, out, ep, T, st);
 }
 
 // ---------------------------------------------------------------------------------------------

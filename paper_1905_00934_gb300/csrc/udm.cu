@@ -13,6 +13,7 @@
 #include <math.h>
 
 #include "dect_internal.cuh"
+#include "prec.cuh"
 
 namespace dect {
 
@@ -139,10 +140,11 @@ __device__ __forceinline__ void load_tables(const SpecDev& sp, float4* t1, float
 
 // ADMM a-update fused with the a-block of the dual update (Eq. 11) and the a-block residual sums:
 // partial[4*blk + {0,1}] = sum (a - Rx)^2 (c, p); partial[4*blk + {2,3}] = sum (a - a_old)^2.
+template <class S2>
 __global__ void __launch_bounds__(kRaysPerBlock) k_udm_admm(const SliceDesc* __restrict__ dsl, BlockMap map, SpecDev sp,
                                                             const float4* __restrict__ meas,
-                                                            const float2* __restrict__ Rx, float2* __restrict__ ua,
-                                                            float2* __restrict__ a, float* __restrict__ mu,
+                                                            const S2* __restrict__ Rx, S2* __restrict__ ua,
+                                                            S2* __restrict__ a, float* __restrict__ mu,
                                                             uint8_t* __restrict__ status,
                                                             const SliceScalars* __restrict__ sc, int iters,
                                                             double* __restrict__ partial) {
@@ -159,9 +161,9 @@ __global__ void __launch_bounds__(kRaysPerBlock) k_udm_admm(const SliceDesc* __r
     if (r < n) {
         const int64_t e = d.sino_off + r;
         const float4 m = __ldg(meas + e);
-        const float2 rx = __ldg(Rx + e);
-        float2 u = ua[e];
-        const float2 a_old = a[e];
+        const float2 rx = ldg2(Rx + e);
+        float2 u = ld2(ua + e);
+        const float2 a_old = ld2(a + e);
         RayIn in;
         in.mh = m.x;
         in.ml = m.y;
@@ -173,14 +175,16 @@ __global__ void __launch_bounds__(kRaysPerBlock) k_udm_admm(const SliceDesc* __r
         in.rp = sc[s].rho[1];
         LmState st{a_old.x, a_old.y, mu[e], DECT_RAY_ACCEPTED};
         lm_ray(t1, t2, sp.ne, in, iters, st);
-        a[e] = make_float2(st.ac, st.ap);
+        // the stored (possibly rounded) a is what the dual update and the residuals see
+        st2(a + e, make_float2(st.ac, st.ap));
+        const float2 an = ld2(a + e);
         mu[e] = st.mu;
         if (status) status[e] = st.status;
-        const float rc = st.ac - rx.x, rp = st.ap - rx.y;
+        const float rc = an.x - rx.x, rp = an.y - rx.y;
         u.x += rc;
         u.y += rp;
-        ua[e] = u;
-        const float dc = st.ac - a_old.x, dp = st.ap - a_old.y;
+        st2(ua + e, u);
+        const float dc = an.x - a_old.x, dp = an.y - a_old.y;
         acc[0] = (double)rc * rc;
         acc[1] = (double)rp * rp;
         acc[2] = (double)dc * dc;
@@ -201,8 +205,9 @@ __global__ void __launch_bounds__(kRaysPerBlock) k_udm_admm(const SliceDesc* __r
 }
 
 // Initial decomposition: rho = (0, rho_p), v = 0, from a = (m_l / abar, 0), mu = mu0.
+template <class S2>
 __global__ void __launch_bounds__(kRaysPerBlock) k_udm_init(const SliceDesc* __restrict__ dsl, BlockMap map, SpecDev sp,
-                                                            const float4* __restrict__ meas, float2* __restrict__ a,
+                                                            const float4* __restrict__ meas, S2* __restrict__ a,
                                                             float* __restrict__ mu, double rho_p, int iters,
                                                             float abar, float mu0) {
     extern __shared__ float4 tabs[];
@@ -228,7 +233,7 @@ __global__ void __launch_bounds__(kRaysPerBlock) k_udm_init(const SliceDesc* __r
     in.rp = rho_p;
     LmState st{m.y / abar, 0.0f, mu0, DECT_RAY_ACCEPTED};
     lm_ray(t1, t2, sp.ne, in, iters, st);
-    a[e] = make_float2(st.ac, 0.0f);
+    st2(a + e, make_float2(st.ac, 0.0f));
     mu[e] = mu0;
 }
 
@@ -350,15 +355,31 @@ void launch_forward_model(const SpecDev& sp, const double4* t64, int64_t n, int 
 }
 
 void launch_udm_admm(const SliceDesc* dsl, const BlockMap& map, int nblk, const SpecDev& sp, const float4* meas,
-                     const float2* Rx, float2* ua, float2* a, float* mu, uint8_t* status, const SliceScalars* sc,
-                     int iters, double* partial, cudaStream_t st) {
-    k_udm_admm<<<nblk, kRaysPerBlock, tab_bytes(sp), st>>>(dsl, map, sp, meas, Rx, ua, a, mu, status, sc, iters,
-                                                            partial);
+                     const void* Rx, void* ua, void* a, float* mu, uint8_t* status, const SliceScalars* sc,
+                     int iters, double* partial, int prec, cudaStream_t st) {
+    if (prec == PREC_F16)
+        k_udm_admm<__half2><<<nblk, kRaysPerBlock, tab_bytes(sp), st>>>(
+            dsl, map, sp, meas, (const __half2*)Rx, (__half2*)ua, (__half2*)a, mu, status, sc, iters, partial);
+    else if (prec == PREC_BF16)
+        k_udm_admm<__nv_bfloat162><<<nblk, kRaysPerBlock, tab_bytes(sp), st>>>(
+            dsl, map, sp, meas, (const __nv_bfloat162*)Rx, (__nv_bfloat162*)ua, (__nv_bfloat162*)a, mu, status, sc,
+            iters, partial);
+    else
+        k_udm_admm<float2><<<nblk, kRaysPerBlock, tab_bytes(sp), st>>>(
+            dsl, map, sp, meas, (const float2*)Rx, (float2*)ua, (float2*)a, mu, status, sc, iters, partial);
 }
 
 void launch_udm_init(const SliceDesc* dsl, const BlockMap& map, int nblk, const SpecDev& sp, const float4* meas,
-                     float2* a, float* mu, double rho_p, int iters, float abar, double mu0, cudaStream_t st) {
-    k_udm_init<<<nblk, kRaysPerBlock, tab_bytes(sp), st>>>(dsl, map, sp, meas, a, mu, rho_p, iters, abar, (float)mu0);
+                     void* a, float* mu, double rho_p, int iters, float abar, double mu0, int prec, cudaStream_t st) {
+    if (prec == PREC_F16)
+        k_udm_init<__half2><<<nblk, kRaysPerBlock, tab_bytes(sp), st>>>(dsl, map, sp, meas, (__half2*)a, mu, rho_p,
+                                                                         iters, abar, (float)mu0);
+    else if (prec == PREC_BF16)
+        k_udm_init<__nv_bfloat162><<<nblk, kRaysPerBlock, tab_bytes(sp), st>>>(
+            dsl, map, sp, meas, (__nv_bfloat162*)a, mu, rho_p, iters, abar, (float)mu0);
+    else
+        k_udm_init<float2><<<nblk, kRaysPerBlock, tab_bytes(sp), st>>>(dsl, map, sp, meas, (float2*)a, mu, rho_p,
+                                                                        iters, abar, (float)mu0);
 }
 
 void launch_udm_rays(const SpecDev& sp, int64_t n, const float* mh, const float* ml, const float* wh, const float* wl,

@@ -118,6 +118,8 @@ def baggage_fan_case(slice_index: int = 0, n: int = 512, n_views: int = 720, n_b
 BAGGAGE_E_REF_KEV = 100.0
 BAGGAGE_KAPPA = 0.25
 SMALL_KAPPA = 1e-2
+# seed base of the mixed-precision workload's slices (1024 x 1024, 1440 views, 2048 bins)
+MIXED_SEED_BASE = 5000
 
 # --- ADMM parameters of the paper's experiments (Sec. 4): lambda = 1e-5, rho0 = 1e-3 for both bases.
 PAPER_LAMBDA = 1e-5

@@ -1,0 +1,71 @@
+"""Writes the FP64 oracle reference for the mixed-precision workload (4-slice subset) using oracle/ only.
+
+Workload: fan-beam slices of 1024 x 1024 pixels, 1440 views, 2048 bins (seeded baggage phantoms,
+I0 2e5), UDM1-PCG1 for 100 ADMM iterations from the oracle's initial image. Stored per slice:
+xi_c, xi_p (Eq. 14) every 10 iterations, and the final Compton and PE values at 2048 seeded pixel
+positions each, so the GPU runs (float32 / float16 / bfloat16 storage) can be compared with the
+oracle pixel by pixel without storing whole images.
+
+Usage: python tests/golden/make_golden_mixed.py [--slices 4] [--iters 100]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import sys
+import time
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, os.path.dirname(os.path.dirname(HERE)))
+
+from oracle import _clib, admm  # noqa: E402
+from synth.workloads import BAGGAGE_KAPPA, MIXED_SEED_BASE, baggage_fan_case  # noqa: E402
+
+N, VIEWS, BINS = 1024, 1440, 2048
+SAMPLES = 2048
+
+
+def sample_pixels(slice_index: int):
+    rng = np.random.Generator(np.random.PCG64(MIXED_SEED_BASE + 500 + slice_index))
+    return rng.integers(0, N * N, SAMPLES)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--slices", type=int, default=4)
+    ap.add_argument("--iters", type=int, default=100)
+    ap.add_argument("--out", default=os.path.join(HERE, "mixed_1024_oracle.json"))
+    args = ap.parse_args()
+    out = {"what": "FP64 oracle, UDM1-PCG1, fan beam 1024x1024, 1440 views, 2048 bins, E_ref 100 keV, kappa 0.25; "
+                   "xi every 10 iterations (entry 0 = initial image) and final x at seeded pixels",
+           "iterations": args.iters, "slices": []}
+    for s in range(args.slices):
+        t0 = time.time()
+        c = baggage_fan_case(slice_index=MIXED_SEED_BASE + s, n=N, n_views=VIEWS, n_bins=BINS)
+        prob = admm.Problem(c["geom"], c["spectra"], c["m_h"], c["m_l"], c["w_h"], c["w_l"],
+                            admm.Params(kappa=BAGGAGE_KAPPA))
+        xc0, xp0 = admm.initial_image(prob)
+        st = admm.state_from_image(prob, xc0, xp0)
+        xi = [[admm.xi_db(xc0, c["truth_c"]), admm.xi_db(xp0, c["truth_p"])]]
+        for it in range(args.iters):
+            st = admm.admm_iteration(prob, st)
+            if (it + 1) % 10 == 0:
+                xi.append([admm.xi_db(st.x[0], c["truth_c"]), admm.xi_db(st.x[1], c["truth_p"])])
+                print(s, it + 1, xi[-1], flush=True)
+        idx = sample_pixels(s)
+        out["slices"].append({"slice_index": MIXED_SEED_BASE + s, "xi": xi, "pixels": idx.tolist(),
+                              "x_c": st.x[0].ravel()[idx].tolist(), "x_p": st.x[1].ravel()[idx].tolist(),
+                              "norm_x_c": float(np.linalg.norm(st.x[0])), "norm_x_p": float(np.linalg.norm(st.x[1])),
+                              "seconds": time.time() - t0})
+        with open(args.out, "w") as f:
+            json.dump(out, f)
+    out["oracle_threads"] = _clib.num_threads()
+    with open(args.out, "w") as f:
+        json.dump(out, f)
+
+
+if __name__ == "__main__":
+    main()
