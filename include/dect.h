@@ -209,11 +209,12 @@ typedef struct {
     int32_t init_pcg_iters;      /* initialisation: CG iterations (10) */
     int32_t precondition;        /* 1: circulant preconditioner, 0: plain CG */
     int32_t use_graph;           /* 1: capture one iteration as a CUDA graph */
-    int32_t bp_view_groups;      /* backprojector view groups per tile, 1..8; 0 = chosen from the
-                                    occupancy so that the grid fills the GPU. It fixes the order of a
-                                    pixel's partial sums: results are bitwise reproducible for a fixed
-                                    value, and a slice solved alone or in a batch gives identical bits
-                                    when the value is the same (it is the one launch-dependent choice). */
+    int32_t bp_view_groups;      /* backprojector view groups per image tile, 1..16;
+                                    0 = chosen from the occupancy so that the grid fills the GPU. It fixes
+                                    the order of a pixel's partial sums: results are bitwise reproducible
+                                    for a fixed value, and a slice solved alone or in a batch gives
+                                    identical bits when the value is the same (it is the one
+                                    launch-dependent choice). */
     int32_t storage;             /* dect_storage (DECT_STORE_F32): 16-bit formats halve the bytes of the
                                     sinogram vectors and textures at the cost of their precision */
 } dect_params;

@@ -373,7 +373,9 @@ struct dect_admm {
     dect_params P{};
     std::vector<SliceDesc> hs;
     SliceDesc* ds = nullptr;
-    MapBuf rays, pix, tx, ty, bp, rows, cols;
+    MapBuf rays, pix, tx, ty, bp, rows, cols, sweep;
+    int sweep_C = 1;                 // CTA groups (partial images) per backprojector tile
+    float2* bp_partial = nullptr;    // [sweep_C][n_img] partial images of the backprojector
     int64_t n_img = 0, n_sino = 0, n_tx = 0, n_ty = 0, n_fft = 0, n_h = 0, n_stage = 0;
     int max_px = 0, max_py = 0;
     int bp_G = 4;  // view groups per backprojector tile
@@ -425,7 +427,8 @@ static void pe(dect_admm* A, int phase, int nk, cudaStream_t st) {
 }
 
 static void free_admm(dect_admm* A) {
-    void* ptrs[] = {A->ds, A->rays.d, A->pix.d, A->tx.d, A->ty.d, A->bp.d, A->rows.d, A->cols.d, A->x, A->r, A->s,
+    void* ptrs[] = {A->ds, A->rays.d, A->pix.d, A->tx.d, A->ty.d, A->bp.d, A->rows.d, A->cols.d, A->sweep.d,
+                    A->bp_partial, A->x, A->r, A->s,
                     A->p, A->Ap, A->z, A->uz, A->x0, A->truth, A->Rx, A->a, A->ua, A->q, A->Z, A->y, A->uy,
                     A->meas, A->txb, A->tyb, A->mu, A->H, A->Hn, A->stage, A->status, A->sc, A->part_udm,
                     A->part_img, A->part_rs, A->part_pap, A->part_xi, A->d_has_x0};
@@ -485,9 +488,9 @@ static void enq_pcg(dect_admm* A, int n, bool with_grad, const float* H, cudaStr
     launch_sino_resid(A->ds, A->rays.map(B), A->rays.total, A->a, A->ua, A->Rx, A->q, A->prec, st);
     pe(A, DECT_PHASE_UPDATE, 1, st);
     pb(A, st);
-    launch_backproject(with_grad ? BP_R0 : BP_R0_NOGRAD, A->ds, A->bp.map(B), A->bp.total, A->q, A->r, ep, A->bp_G,
-                       A->prec, st);
-    pe(A, DECT_PHASE_BACKPROJECT, 1, st);
+    launch_backproject_sweep(with_grad ? BP_R0 : BP_R0_NOGRAD, A->ds, A->sweep.map(B), A->sweep.total, A->pix.map(B),
+                             A->pix.total, A->sweep_C, A->q, A->bp_partial, A->n_img, A->r, ep, A->prec, st);
+    pe(A, DECT_PHASE_BACKPROJECT, 2, st);
     if (A->counting) A->cRT += 2;
     enq_precond(A, H, A->r, A->p, st);
     pb(A, st);
@@ -496,12 +499,13 @@ static void enq_pcg(dect_admm* A, int n, bool with_grad, const float* H, cudaStr
     for (int it = 0; it < n; ++it) {
         enq_project(A, A->p, A->q, st);
         pb(A, st);
-        launch_backproject(with_grad ? BP_AP : BP_AP_NOGRAD, A->ds, A->bp.map(B), A->bp.total, A->q, A->Ap, ep,
-                           A->bp_G, A->prec, st);
-        pe(A, DECT_PHASE_BACKPROJECT, 1, st);
+        launch_backproject_sweep(with_grad ? BP_AP : BP_AP_NOGRAD, A->ds, A->sweep.map(B), A->sweep.total,
+                                 A->pix.map(B), A->pix.total, A->sweep_C, A->q, A->bp_partial, A->n_img, A->Ap, ep,
+                                 A->prec, st);
+        pe(A, DECT_PHASE_BACKPROJECT, 2, st);
         if (A->counting) A->cRT += 2;
         pb(A, st);
-        launch_alpha(A->part_pap, A->bp.d, A->sc, B, st);
+        launch_alpha(A->part_pap, A->pix.d, A->sc, B, st);
         pe(A, DECT_PHASE_REDUCE, 1, st);
         const int last = it == n - 1;
         pb(A, st);
@@ -656,8 +660,8 @@ extern "C" dect_status dect_admm_create(dect_geom* const* geoms, int32_t B, cons
     if (B < 1 || B > 4096) DECT_FAIL(DECT_EINVAL, "dect_admm_create: n_slices must be in [1, 4096]");
     if (P->storage != DECT_STORE_F32 && P->storage != DECT_STORE_F16 && P->storage != DECT_STORE_BF16)
         DECT_FAIL(DECT_EINVAL, "dect_admm_create: storage must be DECT_STORE_F32, F16 or BF16");
-    if (P->bp_view_groups < 0 || P->bp_view_groups > 8)
-        DECT_FAIL(DECT_EINVAL, "dect_admm_create: bp_view_groups must be in [0, 8]");
+    if (P->bp_view_groups < 0 || P->bp_view_groups > 16)
+        DECT_FAIL(DECT_EINVAL, "dect_admm_create: bp_view_groups must be in [0, 16]");
     if (P->m_udm < 1 || P->n_pcg < 1 || P->m_udm > 64 || P->n_pcg > 64)
         DECT_FAIL(DECT_EINVAL, "dect_admm_create: m_udm and n_pcg must be in [1, 64]");
     if (P->init_udm_iters < 0 || P->init_pcg_iters < 1 || P->init_udm_iters > 1000 || P->init_pcg_iters > 1000)
@@ -683,7 +687,12 @@ extern "C" dect_status dect_admm_create(dect_geom* const* geoms, int32_t B, cons
     A->has_x0.assign(B, 0);
     A->has_truth.assign(B, 0);
     A->has_data.assign(B, 0);
-    for (auto* m : {&A->rays, &A->pix, &A->tx, &A->ty, &A->bp, &A->rows, &A->cols}) m->h.assign(1, 0);
+    for (auto* m : {&A->rays, &A->pix, &A->tx, &A->ty, &A->bp, &A->rows, &A->cols, &A->sweep}) m->h.assign(1, 0);
+    {
+        int total = 0;
+        for (int b = 0; b < B; ++b) total += sweep_tiles(geoms[b]->desc.nx, geoms[b]->desc.ny);
+        A->sweep_C = P->bp_view_groups > 0 ? sweep_ctas_for_groups(P->bp_view_groups) : sweep_groups(total);
+    }
     int64_t max_np = 0, max_nr = 0;
     for (int b = 0; b < B; ++b) {
         const dect_geom* g = geoms[b];
@@ -717,6 +726,7 @@ extern "C" dect_status dect_admm_create(dect_geom* const* geoms, int32_t B, cons
         A->tx.h.push_back(A->tx.h.back() + texture_x_blocks(nx, ny));
         A->ty.h.push_back(A->ty.h.back() + texture_y_blocks(nx, ny));
         A->bp.h.push_back(A->bp.h.back() + bp_tiles(nx, ny));
+        A->sweep.h.push_back(A->sweep.h.back() + sweep_tiles(nx, ny) * A->sweep_C);
         A->rows.h.push_back(A->rows.h.back() + ny);
         const int C = precond_cols_per_block(sd.py);
         A->cols.h.push_back(A->cols.h.back() + (sd.px + C - 1) / C);
@@ -754,8 +764,9 @@ extern "C" dect_status dect_admm_create(dect_geom* const* geoms, int32_t B, cons
     if (e == cudaSuccess) e = dalloc(&A->part_img, 4 * (size_t)np_blk);
     if (e == cudaSuccess) e = dalloc(&A->part_xi, 4 * (size_t)np_blk);
     if (e == cudaSuccess) e = dalloc(&A->part_rs, 2 * (size_t)A->rows.h.back());
-    if (e == cudaSuccess) e = dalloc(&A->part_pap, 2 * (size_t)A->bp.h.back());
-    for (MapBuf* m : {&A->rays, &A->pix, &A->tx, &A->ty, &A->bp, &A->rows, &A->cols})
+    if (e == cudaSuccess) e = dalloc(&A->part_pap, 2 * (size_t)std::max(A->bp.h.back(), A->pix.h.back()));
+    if (e == cudaSuccess) e = dalloc(&A->bp_partial, (size_t)A->sweep_C * A->n_img);
+    for (MapBuf* m : {&A->rays, &A->pix, &A->tx, &A->ty, &A->bp, &A->rows, &A->cols, &A->sweep})
         if (e == cudaSuccess) e = upload_map(*m);
     A->bp_G = P->bp_view_groups > 0 ? P->bp_view_groups : bp_groups(A->bp.h.back());
     if (e == cudaSuccess) e = cudaMemcpy(A->ds, A->hs.data(), sizeof(SliceDesc) * B, cudaMemcpyHostToDevice);

@@ -1,0 +1,249 @@
+// Column-sweep gathering backprojector R^T of the ADMM solver (Table 1's R^T, with the CG
+// epilogues of Eq. 12).
+//
+// A CTA owns a 32 x 32 pixel tile and a group of views; of its two warps one takes the rays
+// sampled once per column (axis 0), the other the rays sampled once per row (axis 1). For each
+// view a warp stages its rays that can reach the tile (32 at a time) in shared memory, in bin
+// order, and walks them. For an axis-0 ray lane c evaluates the sample at column ti + c with the
+// same fixed-point integers as the forward projector and adds (1 - f) w s and f w s to the two rows
+// it interpolates between; for an axis-1 ray lane r does the same for row tj + r. Each lane thus
+// only touches its own column of the warp's accumulator tile ([row][column] for axis 0,
+// [column][row] for axis 1: both free of bank conflicts), every sample is evaluated exactly once,
+// and no atomics are needed. The two tiles are added in a fixed order into this CTA's partial
+// image, and k_bp_finalize adds the C partials of a pixel in a fixed order and applies the
+// epilogue, so results are deterministic for a given C.
+//
+// Staging turns a ray into {tile-relative position at lane 0, slope, w s}: the position is
+// q0 + t0 * slope - (a0 << 30) for the tile's first sampled index t0 and first across index a0,
+// an exact integer shift, so a lane's floor and fraction equal those of the forward projector at
+// the same sample. The ray loop runs in blocks of kSwUnroll rays (the stage padded with null rays:
+// far position, zero weight): positions and weights of a block are computed before its
+// accumulator updates, and the next chunk's rays are fetched while the current one is processed.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+
+#include "bp_epilogue.cuh"
+#include "dect_internal.cuh"
+#include "prec.cuh"
+#include "ray_fixed.cuh"
+
+namespace dect {
+
+constexpr int kSw = 32;           // tile side
+constexpr int kSwGroups = 1;      // view groups per CTA
+constexpr int kSwWarps = 2 * kSwGroups;  // one warp per view group and ray axis
+constexpr int kSwRows = kSw + 2;  // accumulator rows -1 .. 32 (the two halo rows are discarded)
+constexpr int kSwUnroll = 8;
+
+template <class S2>
+__global__ void __launch_bounds__(32 * kSwWarps) k_bp_sweep(const SliceDesc* __restrict__ dsl, BlockMap map, int C,
+                                                            const S2* __restrict__ sino, float2* __restrict__ partial,
+                                                            int64_t stride) {
+    // [warp][across index + 1][lane]: [row][column] for axis 0, [column][row] for axis 1
+    __shared__ float2 acc[kSwWarps][kSwRows][kSw];
+    __shared__ int4 st_ray[kSwWarps][32];  // {position lo, position hi, slope, w s_c}
+    __shared__ float st_wp[kSwWarps][32];  // w s_p
+    int local;
+    const int s = slice_of(map, blockIdx.x, local);
+    const SliceDesc& d = dsl[s];
+    const GeomDev& g = d.g;
+    const int nx = g.nx, ny = g.ny;
+    const int c = local % C, tile = local / C;
+    const int tiles_x = (nx + kSw - 1) / kSw;
+    const int ti = (tile % tiles_x) * kSw, tj = (tile / tiles_x) * kSw;
+    const int w = threadIdx.x / 32, lane = threadIdx.x % 32;
+    const bool my_axis = w & 1;
+    for (int r = 0; r < kSwRows; ++r) acc[w][r][lane] = make_float2(0.f, 0.f);
+    const int G = C * kSwGroups, grp = c * kSwGroups + (w >> 1);
+    // the tile's pixel centres span ti .. ti+31 (cm below); interpolation reaches one pixel further
+    const float xc = ((float)ti + 15.5f - g.cx) * g.pix, yc = ((float)tj + 15.5f - g.cy) * g.pix;
+    const float hs = 16.5f * g.pix;
+    const S2* sn = sino + d.sino_off;
+    const int t0 = my_axis ? tj : ti, a0 = my_axis ? ti : tj;
+    const long long a0q = (long long)a0 << 30;
+
+    // chunk cursor: view v, first bin k0 of the chunk, last candidate bin khi of the view
+    int v = grp, k0 = 0, khi = -1;
+    auto seek = [&](int vv) {
+        for (v = vv; v < g.nv; v += G) {
+            const float4 V = __ldg(g.views + v);
+            const CandRange cr = rect_candidates(g, V.x, V.y, xc, yc, hs, hs);
+            if (cr.lo <= cr.hi) {
+                k0 = cr.lo;
+                khi = cr.hi;
+                return;
+            }
+        }
+    };
+    seek(grp);
+    int4 P = make_int4(0, 0, 0, 0);
+    float2 sv = make_float2(0.f, 0.f);
+    bool have = false;
+    auto fetch = [&]() {
+        const int k = k0 + lane;
+        have = v < g.nv && k <= khi;
+        if (have) {
+            P = __ldg(g.rays + (size_t)v * g.nb + k);
+            sv = ldg2(sn + (size_t)v * g.nb + k);
+        }
+    };
+    fetch();
+    while (v < g.nv) {
+        // stage this warp's rays of the fetched chunk, compacted in bin order
+        const bool mine = have && ray_axis(P) == my_axis;
+        const unsigned mask = __ballot_sync(0xffffffffu, mine);
+        const int n = __popc(mask);
+        if (mine) {
+            const long long q = ray_pos(P, t0) - a0q;
+            const float wr = ray_w(P);
+            const int at = __popc(mask & ((1u << lane) - 1u));
+            st_ray[w][at] = make_int4((int)(unsigned)(unsigned long long)q, (int)(q >> 32), P.z, __float_as_int(wr * sv.x));
+            st_wp[w][at] = wr * sv.y;
+        }
+        const int nr = (n + kSwUnroll - 1) / kSwUnroll * kSwUnroll;
+        if (lane >= n && lane < nr) {  // null rays pad the stage to a multiple of kSwUnroll
+            st_ray[w][lane] = make_int4(0, -1000 << 2, 0, 0);
+            st_wp[w][lane] = 0.f;
+        }
+        // advance the cursor and fetch the next chunk while this one is processed
+        k0 += 32;
+        if (k0 > khi) seek(v + G);
+        fetch();
+        __syncwarp();
+        for (int r0 = 0; r0 < nr; r0 += kSwUnroll) {
+            int hh[kSwUnroll];
+            float ff[kSwUnroll], wc[kSwUnroll], wp[kSwUnroll];
+#pragma unroll
+            for (int u = 0; u < kSwUnroll; ++u) {
+                const int4 S = st_ray[w][r0 + u];
+                const long long q = ((((long long)S.y) << 32) | (long long)(unsigned)S.x) + (long long)lane * S.z;
+                hh[u] = pos_floor(q);
+                ff[u] = frac_of(q);
+                wc[u] = __int_as_float(S.w);
+                wp[u] = st_wp[w][r0 + u];
+            }
+#pragma unroll
+            for (int u = 0; u < kSwUnroll; ++u) {
+                // rows h, h+1 with h in [-1, 31] are accumulator rows h+1, h+2 (lanes outside skip)
+                if ((unsigned)(hh[u] + 1) < (unsigned)(kSw + 1)) {
+                    float2* a = &acc[w][hh[u] + 1][lane];
+                    float2 x0 = a[0], x1 = a[kSw];
+                    x0.x = fmaf(1.0f - ff[u], wc[u], x0.x);
+                    x0.y = fmaf(1.0f - ff[u], wp[u], x0.y);
+                    x1.x = fmaf(ff[u], wc[u], x1.x);
+                    x1.y = fmaf(ff[u], wp[u], x1.y);
+                    a[0] = x0;
+                    a[kSw] = x1;
+                }
+            }
+        }
+        __syncwarp();  // the stage is rewritten by the next chunk
+    }
+    __syncthreads();
+    for (int px = threadIdx.x; px < kSw * kSw; px += blockDim.x) {
+        const int rr = px / kSw, cc = px % kSw;
+        const int i = ti + cc, j = tj + rr;
+        if (i < nx && j < ny) {
+            float2 sum = make_float2(0.f, 0.f);
+            for (int gi = 0; gi < kSwGroups; ++gi) {
+                const float2 a = acc[2 * gi][rr + 1][cc], b = acc[2 * gi + 1][cc + 1][rr];
+                sum.x += a.x + b.x;
+                sum.y += a.y + b.y;
+            }
+            partial[c * stride + d.img_off + (size_t)j * nx + i] = sum;
+        }
+    }
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(256) k_bp_finalize(const SliceDesc* __restrict__ dsl, BlockMap pix, int C,
+                                                     const float2* __restrict__ partial, int64_t stride,
+                                                     float2* __restrict__ out, BpEpilogue ep) {
+    int local;
+    const int s = slice_of(pix, blockIdx.x, local);
+    const SliceDesc& d = dsl[s];
+    const int64_t k = (int64_t)local * 256 + threadIdx.x;
+    double dot_c = 0.0, dot_p = 0.0;
+    if (k < (int64_t)d.g.nx * d.g.ny) {
+        const int j = (int)(k / d.g.nx), i = (int)(k % d.g.nx);
+        const int64_t e = d.img_off + k;
+        float2 acc = make_float2(0.f, 0.f);
+        for (int c = 0; c < C; ++c) {
+            const float2 v = __ldg(partial + c * stride + e);
+            acc.x += v.x;
+            acc.y += v.y;
+        }
+        bp_pixel_epilogue<MODE>(d, i, j, acc, ep, out, nullptr, 0, dot_c, dot_p);
+    }
+    if (MODE == BP_AP || MODE == BP_AP_NOGRAD) bp_block_dots(dot_c, dot_p, ep.partial);
+}
+
+int sweep_tiles(int nx, int ny) { return ((nx + kSw - 1) / kSw) * ((ny + kSw - 1) / kSw); }
+
+int sweep_ctas_for_groups(int view_groups) { return (view_groups + kSwGroups - 1) / kSwGroups; }
+
+// CTA groups per tile: the smallest C (up to 8) whose grid of tiles * C blocks fills the resident
+// slots best (each CTA holds kSwGroups view groups; C * kSwGroups view groups per tile in total).
+int sweep_groups(int tiles) {
+    static int slots = 0;
+    if (!slots) {
+        int dev = 0, sms = 0, occ = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        // shared memory (34 KB per CTA) limits residency: ask for the largest carve-out
+        cudaFuncSetAttribute(k_bp_sweep<float2>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             cudaSharedmemCarveoutMaxShared);
+        cudaFuncSetAttribute(k_bp_sweep<__half2>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             cudaSharedmemCarveoutMaxShared);
+        cudaFuncSetAttribute(k_bp_sweep<__nv_bfloat162>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             cudaSharedmemCarveoutMaxShared);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_bp_sweep<float2>, 32 * kSwWarps, 0);
+        slots = sms * (occ > 0 ? occ : 1);
+    }
+    int best = 1;
+    double best_fill = 0.0;
+    for (int C = 1; C <= 8; ++C) {
+        const long long blocks = (long long)tiles * C;
+        const long long waves = (blocks + slots - 1) / slots;
+        const double fill = (double)blocks / (double)(waves * slots);
+        if (fill > best_fill + 0.05) {
+            best = C;
+            best_fill = fill;
+        }
+    }
+    return best;
+}
+
+template <class S2>
+static void launch_sweep_t(int mode, const SliceDesc* dsl, const BlockMap& smap, int nsweep, const BlockMap& pix,
+                           int npix, int C, const S2* sino, float2* partial, int64_t stride, float2* out,
+                           const BpEpilogue& ep, cudaStream_t st) {
+    k_bp_sweep<S2><<<nsweep, 32 * kSwWarps, 0, st>>>(dsl, smap, C, sino, partial, stride);
+    switch (mode) {
+        case BP_PLAIN: k_bp_finalize<BP_PLAIN><<<npix, 256, 0, st>>>(dsl, pix, C, partial, stride, out, ep); break;
+        case BP_R0: k_bp_finalize<BP_R0><<<npix, 256, 0, st>>>(dsl, pix, C, partial, stride, out, ep); break;
+        case BP_AP: k_bp_finalize<BP_AP><<<npix, 256, 0, st>>>(dsl, pix, C, partial, stride, out, ep); break;
+        case BP_R0_NOGRAD:
+            k_bp_finalize<BP_R0_NOGRAD><<<npix, 256, 0, st>>>(dsl, pix, C, partial, stride, out, ep);
+            break;
+        case BP_AP_NOGRAD:
+            k_bp_finalize<BP_AP_NOGRAD><<<npix, 256, 0, st>>>(dsl, pix, C, partial, stride, out, ep);
+            break;
+        default: break;
+    }
+}
+
+void launch_backproject_sweep(int mode, const SliceDesc* dsl, const BlockMap& smap, int nsweep, const BlockMap& pix,
+                              int npix, int C, const void* sino, float2* partial, int64_t stride, float2* out,
+                              const BpEpilogue& ep, int prec, cudaStream_t st) {
+    if (prec == PREC_F16)
+        launch_sweep_t(mode, dsl, smap, nsweep, pix, npix, C, (const __half2*)sino, partial, stride, out, ep, st);
+    else if (prec == PREC_BF16)
+        launch_sweep_t(mode, dsl, smap, nsweep, pix, npix, C, (const __nv_bfloat162*)sino, partial, stride, out, ep,
+                       st);
+    else
+        launch_sweep_t(mode, dsl, smap, nsweep, pix, npix, C, (const float2*)sino, partial, stride, out, ep, st);
+}
+
+}  // namespace dect

@@ -125,6 +125,14 @@ void launch_project(const SliceDesc* dsl, const BlockMap& map, int nblk, const v
 void launch_backproject(int mode, const SliceDesc* dsl, const BlockMap& map, int nblk, const void* sino,
                         float2* out, const BpEpilogue& ep, int groups, int prec, cudaStream_t st);
 int bp_groups(int tiles);
+// backproject_sweep.cu: the solver's backprojector (two kernels: sweep into C partial images, then
+// the fixed-order sum of the partials with the epilogue; partial dots over the `pix` blocks)
+int sweep_ctas_for_groups(int view_groups);
+int sweep_tiles(int nx, int ny);
+int sweep_groups(int tiles);
+void launch_backproject_sweep(int mode, const SliceDesc* dsl, const BlockMap& smap, int nsweep, const BlockMap& pix,
+                              int npix, int C, const void* sino, float2* partial, int64_t stride, float2* out,
+                              const BpEpilogue& ep, int prec, cudaStream_t st);
 void project_single(const SliceDesc& sd, const float* img, int nch, float2* scratch, float4* tx, float4* ty,
                     float* out, cudaStream_t st);
 void backproject_single(const SliceDesc& sd, const float* sino, int nch, float2* packed, float* out,

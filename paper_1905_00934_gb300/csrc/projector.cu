@@ -26,6 +26,7 @@
 #include <math.h>
 
 #include "dect_internal.cuh"
+#include "bp_epilogue.cuh"
 #include "prec.cuh"
 #include "ray_fixed.cuh"
 
@@ -297,50 +298,6 @@ __device__ __forceinline__ void gather_block(const GeomDev& g, const S2* __restr
     }
 }
 
-__device__ __forceinline__ float2 f2(const float2* __restrict__ a, int nx, int ny, int j, int i) {
-    return (i < 0 || i >= nx || j < 0 || j >= ny) ? make_float2(0.f, 0.f) : __ldg(a + (size_t)j * nx + i);
-}
-
-// forward differences of a float2 image at (j, i): {dx_c, dy_c, dx_p, dy_p}, 0 at the last column/row
-__device__ __forceinline__ float4 grad_at(const float2* __restrict__ a, int nx, int ny, int j, int i) {
-    const float2 c = __ldg(a + (size_t)j * nx + i);
-    float4 g = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (i < nx - 1) {
-        const float2 r = __ldg(a + (size_t)j * nx + i + 1);
-        g.x = r.x - c.x;
-        g.z = r.y - c.y;
-    }
-    if (j < ny - 1) {
-        const float2 u = __ldg(a + (size_t)(j + 1) * nx + i);
-        g.y = u.x - c.x;
-        g.w = u.y - c.y;
-    }
-    return g;
-}
-
-// (D^T t)(j, i) for a field t given at (j, i), (j, i-1) and (j-1, i): only components whose
-// D row is non-zero (x-component at i < nx-1, y-component at j < ny-1) take part.
-__device__ __forceinline__ float2 div_t(float4 t_ij, float4 t_im, float4 t_jm, int nx, int ny, int j, int i) {
-    float c = 0.f, p = 0.f;
-    if (i < nx - 1) { c -= t_ij.x; p -= t_ij.z; }
-    if (i >= 1) { c += t_im.x; p += t_im.z; }
-    if (j < ny - 1) { c -= t_ij.y; p -= t_ij.w; }
-    if (j >= 1) { c += t_jm.y; p += t_jm.w; }
-    return make_float2(c, p);
-}
-
-__device__ __forceinline__ float4 y_plus_u_minus_grad(const BpEpilogue& ep, int64_t off, int nx, int ny, int j, int i) {
-    const float2* x = ep.x + off;
-    const size_t e = (size_t)j * nx + i;
-    const float4 y = __ldg(ep.y + off + e), u = __ldg(ep.uy + off + e);
-    const float4 g = grad_at(x, nx, ny, j, i);
-    return make_float4(y.x + u.x - g.x, y.y + u.y - g.y, y.z + u.z - g.z, y.w + u.w - g.w);
-}
-
-__device__ __forceinline__ float4 grad_of(const float2* __restrict__ p, int nx, int ny, int j, int i) {
-    return grad_at(p, nx, ny, j, i);
-}
-
 // Backprojector tile: 16 x 16 pixels; 64 threads per view group, each owning a 2x2 pixel block; G
 // view groups (views v = group, group + G, ...) with G chosen by the host so that the grid fills
 // the GPU in one wave where possible. The G partial sums of each pixel are added in a fixed order,
@@ -383,66 +340,9 @@ __device__ __forceinline__ void backproject_tile(const SliceDesc& d, int local, 
             r.x += red[grp][q][b];
             r.y += red[grp][q + 1][b];
         }
-        const int64_t off = d.img_off;
-        const size_t e = (size_t)j * nx + i;
-        if (MODE == BP_R0 || MODE == BP_R0_NOGRAD) {
-            const float2 xc = __ldg(ep.x + off + e), z = __ldg(ep.z + off + e), uz = __ldg(ep.uz + off + e);
-            r.x += z.x + uz.x - xc.x;
-            r.y += z.y + uz.y - xc.y;
-            if (MODE == BP_R0) {
-                const float4 t_ij = y_plus_u_minus_grad(ep, off, nx, ny, j, i);
-                const float4 t_im = i >= 1 ? y_plus_u_minus_grad(ep, off, nx, ny, j, i - 1) : make_float4(0, 0, 0, 0);
-                const float4 t_jm = j >= 1 ? y_plus_u_minus_grad(ep, off, nx, ny, j - 1, i) : make_float4(0, 0, 0, 0);
-                const float2 dt = div_t(t_ij, t_im, t_jm, nx, ny, j, i);
-                r.x += dt.x;
-                r.y += dt.y;
-            }
-        } else if (MODE == BP_AP || MODE == BP_AP_NOGRAD) {
-            const float2* p = ep.p + off;
-            const float2 pc = __ldg(p + e);
-            r.x += pc.x;
-            r.y += pc.y;
-            if (MODE == BP_AP) {
-                const float4 g_ij = grad_of(p, nx, ny, j, i);
-                const float4 g_im = i >= 1 ? grad_of(p, nx, ny, j, i - 1) : make_float4(0, 0, 0, 0);
-                const float4 g_jm = j >= 1 ? grad_of(p, nx, ny, j - 1, i) : make_float4(0, 0, 0, 0);
-                const float2 dt = div_t(g_ij, g_im, g_jm, nx, ny, j, i);
-                r.x += dt.x;
-                r.y += dt.y;
-            }
-            dot_c += (double)pc.x * (double)r.x;
-            dot_p += (double)pc.y * (double)r.y;
-        }
-        if (planar) {
-            planar[e] = r.x;
-            if (nch > 1) planar[(size_t)nx * ny + e] = r.y;
-        } else {
-            out[off + e] = r;
-        }
+        bp_pixel_epilogue<MODE>(d, i, j, r, ep, out, planar, nch, dot_c, dot_p);
     }
-    if (MODE == BP_AP || MODE == BP_AP_NOGRAD) {
-        // deterministic block reduction of the two partial dot products
-        __shared__ double dred[2][kBpMaxGroups * 2];
-        for (int o = 16; o > 0; o >>= 1) {
-            dot_c += __shfl_down_sync(0xffffffffu, dot_c, o);
-            dot_p += __shfl_down_sync(0xffffffffu, dot_p, o);
-        }
-        const int w = threadIdx.x / 32, l = threadIdx.x % 32;
-        if (l == 0) {
-            dred[0][w] = dot_c;
-            dred[1][w] = dot_p;
-        }
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            double sc = 0.0, sp = 0.0;
-            for (int k = 0; k < (int)blockDim.x / 32; ++k) {
-                sc += dred[0][k];
-                sp += dred[1][k];
-            }
-            ep.partial[2 * (size_t)blockIdx.x] = sc;
-            ep.partial[2 * (size_t)blockIdx.x + 1] = sp;
-        }
-    }
+    if (MODE == BP_AP || MODE == BP_AP_NOGRAD) bp_block_dots(dot_c, dot_p, ep.partial);
 }
 
 template <int MODE, class S2>

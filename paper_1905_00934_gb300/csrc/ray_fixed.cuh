@@ -87,6 +87,34 @@ __device__ __forceinline__ CandRange block_candidates(const GeomDev& g, float cs
     return c;
 }
 
+// Bins whose rays can reach the axis-aligned rectangle of half-sides (hx, hy) cm centred at (xc, yc):
+// the projection of its corners (fan) or of its half-width (parallel), widened by eps bins.
+__device__ __forceinline__ CandRange rect_candidates(const GeomDev& g, float cs, float sn, float xc, float yc, float hx,
+                                                     float hy) {
+    const float eps = 0.02f;
+    float kmin, kmax;
+    if (g.kind == DECT_PARALLEL) {
+        const float kc = fmaf(fmaf(xc, cs, yc * sn), g.inv_du, g.k0);
+        const float h = fmaf(hx, fabsf(cs), hy * fabsf(sn)) * g.inv_du;
+        kmin = kc - h;
+        kmax = kc + h;
+    } else {
+        const float num = fmaf(-xc, sn, yc * cs), den = g.sod - fmaf(xc, cs, yc * sn);
+        const float nx_ = -hx * sn, dx_ = -hx * cs;
+        const float ny_ = hy * cs, dy_ = -hy * sn;
+        const float u1 = __fdividef(num + nx_ + ny_, den + dx_ + dy_);
+        const float u2 = __fdividef(num + nx_ - ny_, den + dx_ - dy_);
+        const float u3 = __fdividef(num - nx_ + ny_, den - dx_ + dy_);
+        const float u4 = __fdividef(num - nx_ - ny_, den - dx_ - dy_);
+        kmin = fmaf(g.k1, fminf(fminf(u1, u2), fminf(u3, u4)), g.k0);
+        kmax = fmaf(g.k1, fmaxf(fmaxf(u1, u2), fmaxf(u3, u4)), g.k0);
+    }
+    CandRange c;
+    c.lo = max(0, (int)ceilf(fmaxf(kmin - eps, -1.0f)));
+    c.hi = min(g.nb - 1, (int)floorf(fminf(kmax + eps, (float)g.nb)));
+    return c;
+}
+
 // Interpolation weights of one sample for the two pixels across at offsets 0 and 1 (d = lower
 // neighbour minus the first across index): the lower neighbour gets 1 - f and the upper one f,
 // exactly as the forward interpolation.

@@ -64,10 +64,10 @@ def test_batched_uneven_matches_single_slices_and_oracle(cuda_dev):
             st = oadmm.admm_iteration(prob, st)
         x0s.append(x0)
         refs.append(st)
-    batched = _solver(cases, cuda_dev, x0s)
+    batched = _solver(cases, cuda_dev, x0s, bp_view_groups=4)
     batched.step(5)
     for b, c in enumerate(cases):
-        single = _solver([c], cuda_dev, [x0s[b]])
+        single = _solver([c], cuda_dev, [x0s[b]], bp_view_groups=4)
         single.step(5)
         xb = batched.get(b, dect.X).cpu().numpy()
         xs = single.get(0, dect.X).cpu().numpy()
@@ -82,10 +82,10 @@ def test_batched_initialisation_matches_single(cuda_dev):
     from paper_1905_00934_gb300 import dect
 
     cases = _small_cases()
-    batched = _solver(cases, cuda_dev, [None, None, None])
+    batched = _solver(cases, cuda_dev, [None, None, None], bp_view_groups=4)
     batched.reconstruct(2)
     for b, c in enumerate(cases):
-        single = _solver([c], cuda_dev, [None])
+        single = _solver([c], cuda_dev, [None], bp_view_groups=4)
         single.reconstruct(2)
         assert np.array_equal(batched.get(b, dect.X).cpu().numpy(), single.get(0, dect.X).cpu().numpy())
 
