@@ -116,6 +116,33 @@ def _golden():
         return None
 
 
+def joseph_weight_count(g) -> int:
+    """Non-zero weights of the projection matrix R (one channel) for geometry g: every sample of the
+    Joseph interpolation (Eq. 2-3's R, one sample per column or row along each ray) has up to two
+    in-image neighbours. Counted in float64 from the same ray parameters the projector tabulates;
+    samples landing exactly on a pixel centre (a zero upper weight) are counted too."""
+    px, py, dx, dy = g.rays()
+    total = 0
+    for v0 in range(0, g.n_views, 16):
+        X, Y, DX, DY = (a[v0:v0 + 16].ravel() for a in (px, py, dx, dy))
+        ax0 = np.abs(DX) >= np.abs(DY)
+        for m, (pa, pb, da, db, n_along, n_across) in ((ax0, (X, Y, DX, DY, g.nx, g.ny)),
+                                                        (~ax0, (Y, X, DY, DX, g.ny, g.nx))):
+            if not m.any():
+                continue
+            slope = db[m] / da[m]
+            q0 = (pb[m] - pa[m] * slope) / g.pixel_cm + 0.5 * (n_across - 1) - 0.5 * (n_along - 1) * slope
+            h = np.floor(q0[:, None] + np.arange(n_along)[None, :] * slope[:, None])
+            total += int(((h >= 0) & (h < n_across)).sum() + ((h >= -1) & (h < n_across - 1)).sum())
+    return total
+
+
+# dram bytes per launch of the backprojector sweep at the bench workload (8 slices), from one ncu
+# capture of this kernel (profiles/k_bp_sweep_512x720x1024_b8.txt); None when not measured for the
+# current kernel
+SWEEP_TRAFFIC_B8 = 163.1e6
+
+
 # ------------------------------------------------------------------------------------------------
 # CPU baseline / reference arm: the FP64 oracle as it stands, on a bounded sample of the workload
 
@@ -217,6 +244,12 @@ def run_dect(args):
         sol.set_data(b, *dev_data[b])
         sol.set_truth(b, f32(np.stack([c["truth_c"], c["truth_p"]])))
     stream = torch.cuda.current_stream()
+    if args.profile_run:
+        # one untimed reconstruction of the workload, for profiler captures
+        sol.reconstruct(args.profile_run)
+        torch.cuda.synchronize()
+        print(json.dumps({"profile_run": args.profile_run, "batch": B, "stats": sol.stats(0)}), flush=True)
+        return 0
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # 512 MB > 129 MB L2
 
     def barrier():
@@ -316,16 +349,33 @@ def run_dect(args):
         "texture": B * (8 * Np + 16 * (g.nx * (g.ny + 3) + g.ny * (g.nx + 3))),
         "update": None,
         "reduce": None,
+        "bp_finalize": B * ((8 * 4 + 8) * Np + (56 + 16) / 2 * Np),  # C = 4 partials in, image out, epilogue
     }
     ms_total, n_launch = prof[top]
     avg_ms = ms_total / max(n_launch, 1)
     peak, peak_kind = _peaks()
     roof = None
+    # R and R^T compute their weights on chip: the work is one FMA per weight and channel, against the
+    # FP32 rate of the SMs (no measured figure for it; derived from unit counts and the max SM clock)
+    nnz = joseph_weight_count(g)
+    alg_flops = {"backproject": B * 2 * 2 * nnz, "project": B * 2 * 2 * nnz}
+    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+    fp32_peak = n_sm * 128 * 2 * (clocks.get("sm_max_mhz") or 2070.0) * 1e6 / 1e12
+    hbm = None
     if alg_bytes.get(top):
-        achieved = alg_bytes[top] / (avg_ms / 1e3) / 1e9
-        roof = {"kernel": top, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": None, "peak_kind": peak_kind,
-                "avg_launch_ms": avg_ms, "algorithmic_bytes_per_launch": alg_bytes[top]}
+        gbs = alg_bytes[top] / (avg_ms / 1e3) / 1e9
+        hbm = {"achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak, "peak_kind": peak_kind,
+               "algorithmic_bytes_per_launch": alg_bytes[top]}
+    if alg_flops.get(top):
+        tf = alg_flops[top] / (avg_ms / 1e3) / 1e12
+        roof = {"kernel": top, "bound": "alu", "achieved": tf, "peak": fp32_peak, "unit": "TFLOP/s",
+                "frac": tf / fp32_peak,
+                "traffic": SWEEP_TRAFFIC_B8 if (top == "backproject" and B == 8) else None,
+                "peak_kind": f"derived: {n_sm} SMs x 128 FP32 lanes x 2 flop x max SM clock",
+                "avg_launch_ms": avg_ms, "algorithmic_flops_per_launch": alg_flops[top],
+                "weights_per_slice_channel": nnz, "hbm": hbm}
+    elif hbm is not None:
+        roof = dict(kernel=top, bound="hbm", traffic=None, avg_launch_ms=avg_ms, **hbm)
     phases = {p: {"ms_per_iter": prof[p][0] / 10, "launches_per_iter": prof[p][1] / 10} for p in prof}
 
     if rank == 0:
@@ -363,6 +413,9 @@ def main():
     ap.add_argument("--storage", default="f32", choices=["f32", "f16", "bf16"],
                     help="storage of the sinogram vectors and projector textures (arithmetic stays f32/f64)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile-run", type=int, default=0, metavar="ITERS",
+                    help="set up the workload, run one untimed reconstruction of ITERS iterations and exit "
+                         "(for profiler captures; prints no bench line)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

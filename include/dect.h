@@ -278,12 +278,13 @@ dect_status dect_admm_stats(dect_admm* a, int32_t slice, dect_stats* out, void* 
 enum {
     DECT_PHASE_TEXTURE = 0,      /* pair textures of the image the projector reads */
     DECT_PHASE_PROJECT = 1,      /* R */
-    DECT_PHASE_BACKPROJECT = 2,  /* R^T with the CG epilogues */
+    DECT_PHASE_BACKPROJECT = 2,  /* R^T: the tile sweep writing partial images */
     DECT_PHASE_PRECOND = 3,      /* FFT preconditioner (3 kernels) */
     DECT_PHASE_UDM = 4,          /* Eq. 13 with the a-block dual update */
     DECT_PHASE_UPDATE = 5,       /* element-wise CG, Eq. 9-11 and dual rescaling kernels */
     DECT_PHASE_REDUCE = 6,       /* per-slice scalar reductions (CG alpha/beta, rho) */
-    DECT_NUM_PHASES = 7
+    DECT_PHASE_BP_FINALIZE = 7,  /* R^T: sum of the partial images and the CG epilogues of Eq. 12 */
+    DECT_NUM_PHASES = 8
 };
 
 /* Runs `iters` iterations exactly like dect_admm_step (same kernels, replayed as a

@@ -488,9 +488,12 @@ static void enq_pcg(dect_admm* A, int n, bool with_grad, const float* H, cudaStr
     launch_sino_resid(A->ds, A->rays.map(B), A->rays.total, A->a, A->ua, A->Rx, A->q, A->prec, st);
     pe(A, DECT_PHASE_UPDATE, 1, st);
     pb(A, st);
-    launch_backproject_sweep(with_grad ? BP_R0 : BP_R0_NOGRAD, A->ds, A->sweep.map(B), A->sweep.total, A->pix.map(B),
-                             A->pix.total, A->sweep_C, A->q, A->bp_partial, A->n_img, A->r, ep, A->prec, st);
-    pe(A, DECT_PHASE_BACKPROJECT, 2, st);
+    launch_bp_sweep(A->ds, A->sweep.map(B), A->sweep.total, A->sweep_C, A->q, A->bp_partial, A->n_img, A->prec, st);
+    pe(A, DECT_PHASE_BACKPROJECT, 1, st);
+    pb(A, st);
+    launch_bp_finalize(with_grad ? BP_R0 : BP_R0_NOGRAD, A->ds, A->pix.map(B), A->pix.total, A->sweep_C,
+                       A->bp_partial, A->n_img, A->r, ep, st);
+    pe(A, DECT_PHASE_BP_FINALIZE, 1, st);
     if (A->counting) A->cRT += 2;
     enq_precond(A, H, A->r, A->p, st);
     pb(A, st);
@@ -499,10 +502,13 @@ static void enq_pcg(dect_admm* A, int n, bool with_grad, const float* H, cudaStr
     for (int it = 0; it < n; ++it) {
         enq_project(A, A->p, A->q, st);
         pb(A, st);
-        launch_backproject_sweep(with_grad ? BP_AP : BP_AP_NOGRAD, A->ds, A->sweep.map(B), A->sweep.total,
-                                 A->pix.map(B), A->pix.total, A->sweep_C, A->q, A->bp_partial, A->n_img, A->Ap, ep,
-                                 A->prec, st);
-        pe(A, DECT_PHASE_BACKPROJECT, 2, st);
+        launch_bp_sweep(A->ds, A->sweep.map(B), A->sweep.total, A->sweep_C, A->q, A->bp_partial, A->n_img, A->prec,
+                        st);
+        pe(A, DECT_PHASE_BACKPROJECT, 1, st);
+        pb(A, st);
+        launch_bp_finalize(with_grad ? BP_AP : BP_AP_NOGRAD, A->ds, A->pix.map(B), A->pix.total, A->sweep_C,
+                           A->bp_partial, A->n_img, A->Ap, ep, st);
+        pe(A, DECT_PHASE_BP_FINALIZE, 1, st);
         if (A->counting) A->cRT += 2;
         pb(A, st);
         launch_alpha(A->part_pap, A->pix.d, A->sc, B, st);

@@ -215,11 +215,19 @@ int sweep_groups(int tiles) {
     return best;
 }
 
-template <class S2>
-static void launch_sweep_t(int mode, const SliceDesc* dsl, const BlockMap& smap, int nsweep, const BlockMap& pix,
-                           int npix, int C, const S2* sino, float2* partial, int64_t stride, float2* out,
-                           const BpEpilogue& ep, cudaStream_t st) {
-    k_bp_sweep<S2><<<nsweep, 32 * kSwWarps, 0, st>>>(dsl, smap, C, sino, partial, stride);
+void launch_bp_sweep(const SliceDesc* dsl, const BlockMap& smap, int nsweep, int C, const void* sino,
+                     float2* partial, int64_t stride, int prec, cudaStream_t st) {
+    if (prec == PREC_F16)
+        k_bp_sweep<__half2><<<nsweep, 32 * kSwWarps, 0, st>>>(dsl, smap, C, (const __half2*)sino, partial, stride);
+    else if (prec == PREC_BF16)
+        k_bp_sweep<__nv_bfloat162><<<nsweep, 32 * kSwWarps, 0, st>>>(dsl, smap, C, (const __nv_bfloat162*)sino,
+                                                                      partial, stride);
+    else
+        k_bp_sweep<float2><<<nsweep, 32 * kSwWarps, 0, st>>>(dsl, smap, C, (const float2*)sino, partial, stride);
+}
+
+void launch_bp_finalize(int mode, const SliceDesc* dsl, const BlockMap& pix, int npix, int C, const float2* partial,
+                        int64_t stride, float2* out, const BpEpilogue& ep, cudaStream_t st) {
     switch (mode) {
         case BP_PLAIN: k_bp_finalize<BP_PLAIN><<<npix, 256, 0, st>>>(dsl, pix, C, partial, stride, out, ep); break;
         case BP_R0: k_bp_finalize<BP_R0><<<npix, 256, 0, st>>>(dsl, pix, C, partial, stride, out, ep); break;
@@ -232,18 +240,6 @@ static void launch_sweep_t(int mode, const SliceDesc* dsl, const BlockMap& smap,
             break;
         default: break;
     }
-}
-
-void launch_backproject_sweep(int mode, const SliceDesc* dsl, const BlockMap& smap, int nsweep, const BlockMap& pix,
-                              int npix, int C, const void* sino, float2* partial, int64_t stride, float2* out,
-                              const BpEpilogue& ep, int prec, cudaStream_t st) {
-    if (prec == PREC_F16)
-        launch_sweep_t(mode, dsl, smap, nsweep, pix, npix, C, (const __half2*)sino, partial, stride, out, ep, st);
-    else if (prec == PREC_BF16)
-        launch_sweep_t(mode, dsl, smap, nsweep, pix, npix, C, (const __nv_bfloat162*)sino, partial, stride, out, ep,
-                       st);
-    else
-        launch_sweep_t(mode, dsl, smap, nsweep, pix, npix, C, (const float2*)sino, partial, stride, out, ep, st);
 }
 
 }  // namespace dect

@@ -130,9 +130,10 @@ int bp_groups(int tiles);
 int sweep_ctas_for_groups(int view_groups);
 int sweep_tiles(int nx, int ny);
 int sweep_groups(int tiles);
-void launch_backproject_sweep(int mode, const SliceDesc* dsl, const BlockMap& smap, int nsweep, const BlockMap& pix,
-                              int npix, int C, const void* sino, float2* partial, int64_t stride, float2* out,
-                              const BpEpilogue& ep, int prec, cudaStream_t st);
+void launch_bp_sweep(const SliceDesc* dsl, const BlockMap& smap, int nsweep, int C, const void* sino,
+                     float2* partial, int64_t stride, int prec, cudaStream_t st);
+void launch_bp_finalize(int mode, const SliceDesc* dsl, const BlockMap& pix, int npix, int C, const float2* partial,
+                        int64_t stride, float2* out, const BpEpilogue& ep, cudaStream_t st);
 void project_single(const SliceDesc& sd, const float* img, int nch, float2* scratch, float4* tx, float4* ty,
                     float* out, cudaStream_t st);
 void backproject_single(const SliceDesc& sd, const float* sino, int nch, float2* packed, float* out,

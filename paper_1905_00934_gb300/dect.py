@@ -276,7 +276,7 @@ def admm_stats(h, slice_index, stream=None) -> dict:
             "count_launches": s.count_launches}
 
 
-PHASES = ["texture", "project", "backproject", "precond", "udm", "update", "reduce"]
+PHASES = ["texture", "project", "backproject", "precond", "udm", "update", "reduce", "bp_finalize"]
 
 
 def admm_profile(h, iters, stream=None):

@@ -62,7 +62,7 @@ def test_profile_counts_every_kernel_group(cuda_dev, small100):
     launched = sum(v[1] for v in prof.values())
     assert sol.stats(0)["count_launches"] - l0 == launched
     assert all(v[0] > 0 for k, v in prof.items() if k != "texture" or v[1] > 0)
-    assert prof["backproject"][1] == 3 * 2 * 2 and prof["project"][1] == 3 and prof["udm"][1] == 3
+    assert prof["backproject"][1] == 3 * 2 and prof["bp_finalize"][1] == 3 * 2 and prof["project"][1] == 3 and prof["udm"][1] == 3
 
 
 def test_preconditioner_response_matches_oracle(cuda_dev, small):
