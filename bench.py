@@ -226,14 +226,16 @@ def run_dect(args):
     import __graft_entry__
 
     __graft_entry__.build()
-    from paper_1905_00934_gb300 import Geometry, Solver, Spectra, dect
+    from paper_1905_00934_gb300 import Geometry, Solver, Spectra, dect, shard
     from synth.workloads import BAGGAGE_KAPPA, baggage_fan_case
 
     B = args.batch
     from concurrent.futures import ThreadPoolExecutor
 
     with ThreadPoolExecutor(max_workers=min(B, 16)) as ex:  # numpy releases the GIL in the heavy loops
-        cases = list(ex.map(lambda b: baggage_fan_case(slice_index=rank * B + b), range(B)))
+        # weak scaling: ws * B equal slices, each rank its contiguous share (no data-path collective)
+        mine = list(shard.rank_slices([1.0] * (ws * B), rank, ws))
+        cases = list(ex.map(lambda s: baggage_fan_case(slice_index=s), mine))
     geo = [Geometry(c["geom"]) for c in cases]
     spec = Spectra.from_tables(cases[0]["spectra"])
     storage = {"f32": 0, "f16": 1, "bf16": 2}[args.storage]
@@ -274,11 +276,7 @@ def run_dect(args):
     clocks = clk.summary()
     launches = sol.stats(0)["count_launches"] - launches0
     step_ms = [a.elapsed_time(b) for a, b in ev]
-    total_ms = float(sum(step_ms))
-    if ws > 1:
-        t = torch.tensor([total_ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = shard.max_over_ranks(float(sum(step_ms)), dev)
     value = ws * B * args.steps / (total_ms / 1e3)
 
     # the plain form: the same slices reconstructed one at a time by single-slice solvers
@@ -328,11 +326,7 @@ def run_dect(args):
             dect.admm_get(sol.handle, b, dect.X, host_out[b])
     e1.record(stream)
     barrier()
-    e2e_ms = e0.elapsed_time(e1)
-    if ws > 1:
-        t = torch.tensor([e2e_ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_ms = float(t.item())
+    e2e_ms = shard.max_over_ranks(e0.elapsed_time(e1), dev)
     e2e_value = ws * B * e2e_steps / (e2e_ms / 1e3)
 
     # live per-kernel-group timing of the same iteration (CUDA events around each group)

@@ -143,10 +143,11 @@ dect_status dect_project_noalloc(const dect_geom* g, int32_t n_channels, const f
                                  void* stream);
 
 /* Backprojection, the exact adjoint R^T of dect_project (Table 1's R^T):
- * x_dev[c] = R^T sino_dev[c]; same layouts and dtypes; x_dev is overwritten. It gathers
- * per pixel (no atomics), so the result is deterministic; it evaluates the
- * same per-ray weights as dect_project, so <R x, y> = <x, R^T y> up to float32
- * rounding. */
+ * x_dev[c] = R^T sino_dev[c]; same layouts and dtypes; x_dev is overwritten. Every
+ * pixel is accumulated by one thread (image tiles sweep the rays that reach them,
+ * partial images are added in a fixed order; no atomics), so the result is
+ * deterministic; it evaluates the same per-ray weights as dect_project, so
+ * <R x, y> = <x, R^T y> up to float32 rounding. */
 dect_status dect_backproject(dect_geom* g, int32_t n_channels, int32_t dtype, const void* sino_dev,
                              void* x_dev, void* stream);
 

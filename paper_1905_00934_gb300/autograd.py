@@ -1,6 +1,6 @@
 """torch.autograd wrappers over libdect (marshalling only; the arithmetic is in the CUDA kernels).
 
-* project(x, geometry): R x (Eq. 2-3's projection matrix) with the gathering R^T kernel as its
+* project(x, geometry): R x (Eq. 2-3's projection matrix) with the R^T kernel as its
   backward pass. x has any leading dims [..., ny, nx]; float32 or float64 on the GPU.
 * forward_model(a_c, a_p, spectra): f_h, f_l of Eq. 3 per ray, whose backward is the transpose
   of the per-ray 2x2 Jacobian (the derivative the decomposition step of Eq. 13 linearises).

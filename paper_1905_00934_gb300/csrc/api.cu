@@ -73,6 +73,12 @@ struct dect_geom {
     float4* ws_tx = nullptr;
     float4* ws_ty = nullptr;
     float2* ws_sino = nullptr;
+    // R^T workspace: descriptor with zero offsets, block-map prefixes {0, sweep CTAs, 0, pixel blocks},
+    // ws_C partial images
+    SliceDesc* ws_desc = nullptr;
+    int* ws_maps = nullptr;
+    float2* ws_partial = nullptr;
+    int ws_C = 1;
     double4* rays64 = nullptr;  // float64 ray table (DECT_F64 calls; built on first use)
 
     int64_t n_rays() const { return (int64_t)desc.n_views * desc.n_bins; }
@@ -151,8 +157,8 @@ extern "C" dect_status dect_geometry_create(const dect_geom_desc* d, dect_geom**
             DECT_FAIL(DECT_EINVAL, "geometry: fan beam needs sdd > sod > 0");
         const double r = 0.5 * d->pixel_cm * std::sqrt((double)d->nx * d->nx + (double)d->ny * d->ny) + 2.0 * d->pixel_cm;
         if (r >= 0.98 * d->sod_cm) DECT_FAIL(DECT_EINVAL, "geometry: image must lie well inside the source circle");
-        // the rays through any 3x3-pixel neighbourhood then span less than 60 degrees, which the
-        // backprojector's per-window axis test relies on
+        // the backprojectors project rectangles around image tiles onto the detector, which needs
+        // them in front of the source with a margin
         if (d->sod_cm - r < 4.25 * d->pixel_cm) DECT_FAIL(DECT_EINVAL, "geometry: source too close to the image");
     }
     dect_geom* g = new dect_geom();
@@ -178,6 +184,9 @@ extern "C" void dect_geometry_destroy(dect_geom* g) {
     cudaFree(g->ws_tx);
     cudaFree(g->ws_ty);
     cudaFree(g->ws_sino);
+    cudaFree(g->ws_desc);
+    cudaFree(g->ws_maps);
+    cudaFree(g->ws_partial);
     cudaFree(g->rays64);
     delete g;
 }
@@ -189,6 +198,15 @@ static dect_status geom_workspace(dect_geom* g) {
     CUDA_TRY(dalloc(&g->ws_tx, (size_t)d.nx * (d.ny + 3)));
     CUDA_TRY(dalloc(&g->ws_ty, (size_t)d.ny * (d.nx + 3)));
     CUDA_TRY(dalloc(&g->ws_sino, (size_t)g->n_rays()));
+    const int tiles = sweep_tiles(d.nx, d.ny);
+    g->ws_C = sweep_groups(tiles);
+    CUDA_TRY(dalloc(&g->ws_partial, (size_t)g->ws_C * g->n_pix()));
+    CUDA_TRY(dalloc(&g->ws_desc, 1));
+    CUDA_TRY(dalloc(&g->ws_maps, 4));
+    const SliceDesc sd = g->single();
+    const int maps[4] = {0, tiles * g->ws_C, 0, (int)((g->n_pix() + kPixPerBlock - 1) / kPixPerBlock)};
+    CUDA_TRY(cudaMemcpy(g->ws_desc, &sd, sizeof(SliceDesc), cudaMemcpyHostToDevice));
+    CUDA_TRY(cudaMemcpy(g->ws_maps, maps, sizeof(maps), cudaMemcpyHostToDevice));
     return DECT_OK;
 }
 
@@ -235,7 +253,8 @@ extern "C" dect_status dect_backproject(dect_geom* g, int32_t nch, int32_t dtype
     }
     dect_status st = geom_workspace(g);
     if (st != DECT_OK) return st;
-    backproject_single(g->single(), (const float*)sino, nch, g->ws_sino, (float*)x, as_stream(stream));
+    backproject_single(g->single(), g->ws_desc, g->ws_maps, g->ws_C, (const float*)sino, nch, g->ws_sino,
+                       g->ws_partial, (float*)x, as_stream(stream));
     CUDA_TRY(cudaGetLastError());
     return DECT_OK;
 }
@@ -373,12 +392,11 @@ struct dect_admm {
     dect_params P{};
     std::vector<SliceDesc> hs;
     SliceDesc* ds = nullptr;
-    MapBuf rays, pix, tx, ty, bp, rows, cols, sweep;
+    MapBuf rays, pix, tx, ty, rows, cols, sweep;
     int sweep_C = 1;                 // CTA groups (partial images) per backprojector tile
     float2* bp_partial = nullptr;    // [sweep_C][n_img] partial images of the backprojector
     int64_t n_img = 0, n_sino = 0, n_tx = 0, n_ty = 0, n_fft = 0, n_h = 0, n_stage = 0;
     int max_px = 0, max_py = 0;
-    int bp_G = 4;  // view groups per backprojector tile
     float2 *x = nullptr, *r = nullptr, *s = nullptr, *p = nullptr, *Ap = nullptr, *z = nullptr, *uz = nullptr;
     float2 *x0 = nullptr, *truth = nullptr, *Z = nullptr;
     void *Rx = nullptr, *a = nullptr, *ua = nullptr, *q = nullptr;  // sinogram vectors, storage format `prec`
@@ -427,7 +445,7 @@ static void pe(dect_admm* A, int phase, int nk, cudaStream_t st) {
 }
 
 static void free_admm(dect_admm* A) {
-    void* ptrs[] = {A->ds, A->rays.d, A->pix.d, A->tx.d, A->ty.d, A->bp.d, A->rows.d, A->cols.d, A->sweep.d,
+    void* ptrs[] = {A->ds, A->rays.d, A->pix.d, A->tx.d, A->ty.d, A->rows.d, A->cols.d, A->sweep.d,
                     A->bp_partial, A->x, A->r, A->s,
                     A->p, A->Ap, A->z, A->uz, A->x0, A->truth, A->Rx, A->a, A->ua, A->q, A->Z, A->y, A->uy,
                     A->meas, A->txb, A->tyb, A->mu, A->H, A->Hn, A->stage, A->status, A->sc, A->part_udm,
@@ -631,7 +649,8 @@ static dect_status compute_responses(dect_admm* A) {
         dect_status ws = geom_workspace(g);
         if (ws != DECT_OK) return ws;
         project_single(sd, A->stage, 2, g->ws_img, g->ws_tx, g->ws_ty, A->stage + 2 * np, st);
-        backproject_single(sd, A->stage + 2 * np, 2, g->ws_sino, A->stage, st);
+        backproject_single(sd, g->ws_desc, g->ws_maps, g->ws_C, A->stage + 2 * np, 2, g->ws_sino, g->ws_partial,
+                           A->stage, st);
         launch_interleave(A->stage, np, A->r + sd.img_off, st);
         // one-slice descriptor and column map
         SliceDesc one_slice = sd;
@@ -693,7 +712,7 @@ extern "C" dect_status dect_admm_create(dect_geom* const* geoms, int32_t B, cons
     A->has_x0.assign(B, 0);
     A->has_truth.assign(B, 0);
     A->has_data.assign(B, 0);
-    for (auto* m : {&A->rays, &A->pix, &A->tx, &A->ty, &A->bp, &A->rows, &A->cols, &A->sweep}) m->h.assign(1, 0);
+    for (auto* m : {&A->rays, &A->pix, &A->tx, &A->ty, &A->rows, &A->cols, &A->sweep}) m->h.assign(1, 0);
     {
         int total = 0;
         for (int b = 0; b < B; ++b) total += sweep_tiles(geoms[b]->desc.nx, geoms[b]->desc.ny);
@@ -731,7 +750,6 @@ extern "C" dect_status dect_admm_create(dect_geom* const* geoms, int32_t B, cons
         A->pix.h.push_back(A->pix.h.back() + (int)((np + 255) / 256));
         A->tx.h.push_back(A->tx.h.back() + texture_x_blocks(nx, ny));
         A->ty.h.push_back(A->ty.h.back() + texture_y_blocks(nx, ny));
-        A->bp.h.push_back(A->bp.h.back() + bp_tiles(nx, ny));
         A->sweep.h.push_back(A->sweep.h.back() + sweep_tiles(nx, ny) * A->sweep_C);
         A->rows.h.push_back(A->rows.h.back() + ny);
         const int C = precond_cols_per_block(sd.py);
@@ -770,11 +788,10 @@ extern "C" dect_status dect_admm_create(dect_geom* const* geoms, int32_t B, cons
     if (e == cudaSuccess) e = dalloc(&A->part_img, 4 * (size_t)np_blk);
     if (e == cudaSuccess) e = dalloc(&A->part_xi, 4 * (size_t)np_blk);
     if (e == cudaSuccess) e = dalloc(&A->part_rs, 2 * (size_t)A->rows.h.back());
-    if (e == cudaSuccess) e = dalloc(&A->part_pap, 2 * (size_t)std::max(A->bp.h.back(), A->pix.h.back()));
+    if (e == cudaSuccess) e = dalloc(&A->part_pap, 2 * (size_t)A->pix.h.back());
     if (e == cudaSuccess) e = dalloc(&A->bp_partial, (size_t)A->sweep_C * A->n_img);
-    for (MapBuf* m : {&A->rays, &A->pix, &A->tx, &A->ty, &A->bp, &A->rows, &A->cols, &A->sweep})
+    for (MapBuf* m : {&A->rays, &A->pix, &A->tx, &A->ty, &A->rows, &A->cols, &A->sweep})
         if (e == cudaSuccess) e = upload_map(*m);
-    A->bp_G = P->bp_view_groups > 0 ? P->bp_view_groups : bp_groups(A->bp.h.back());
     if (e == cudaSuccess) e = cudaMemcpy(A->ds, A->hs.data(), sizeof(SliceDesc) * B, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemset(A->truth, 0, sizeof(float2) * A->n_img);
     if (e == cudaSuccess) e = cudaMemset(A->status, 0, A->n_sino);

@@ -56,9 +56,12 @@ __global__ void __launch_bounds__(32 * kSwWarps) k_bp_sweep(const SliceDesc* __r
     const bool my_axis = w & 1;
     for (int r = 0; r < kSwRows; ++r) acc[w][r][lane] = make_float2(0.f, 0.f);
     const int G = C * kSwGroups, grp = c * kSwGroups + (w >> 1);
-    // the tile's pixel centres span ti .. ti+31 (cm below); interpolation reaches one pixel further
-    const float xc = ((float)ti + 15.5f - g.cx) * g.pix, yc = ((float)tj + 15.5f - g.cy) * g.pix;
-    const float hs = 16.5f * g.pix;
+    // rays with a weight at the tile's in-image pixels pass within one pixel of their centres:
+    // columns ti .. ie, rows tj .. je, widened by one pixel (the rectangle stays inside the image's
+    // one-pixel margin, in front of a fan source)
+    const int ie = min(ti + kSw, nx) - 1, je = min(tj + kSw, ny) - 1;
+    const float xc = (0.5f * (float)(ti + ie) - g.cx) * g.pix, yc = (0.5f * (float)(tj + je) - g.cy) * g.pix;
+    const float hx = (0.5f * (float)(ie - ti) + 1.0f) * g.pix, hy = (0.5f * (float)(je - tj) + 1.0f) * g.pix;
     const S2* sn = sino + d.sino_off;
     const int t0 = my_axis ? tj : ti, a0 = my_axis ? ti : tj;
     const long long a0q = (long long)a0 << 30;
@@ -68,7 +71,7 @@ __global__ void __launch_bounds__(32 * kSwWarps) k_bp_sweep(const SliceDesc* __r
     auto seek = [&](int vv) {
         for (v = vv; v < g.nv; v += G) {
             const float4 V = __ldg(g.views + v);
-            const CandRange cr = rect_candidates(g, V.x, V.y, xc, yc, hs, hs);
+            const CandRange cr = rect_candidates(g, V.x, V.y, xc, yc, hx, hy);
             if (cr.lo <= cr.hi) {
                 k0 = cr.lo;
                 khi = cr.hi;
@@ -156,10 +159,12 @@ __global__ void __launch_bounds__(32 * kSwWarps) k_bp_sweep(const SliceDesc* __r
     }
 }
 
+// (planar != nullptr: single slice, written as [nch][ny][nx] instead of interleaved into `out`)
 template <int MODE>
 __global__ void __launch_bounds__(256) k_bp_finalize(const SliceDesc* __restrict__ dsl, BlockMap pix, int C,
                                                      const float2* __restrict__ partial, int64_t stride,
-                                                     float2* __restrict__ out, BpEpilogue ep) {
+                                                     float2* __restrict__ out, BpEpilogue ep,
+                                                     float* __restrict__ planar, int nch) {
     int local;
     const int s = slice_of(pix, blockIdx.x, local);
     const SliceDesc& d = dsl[s];
@@ -174,7 +179,7 @@ __global__ void __launch_bounds__(256) k_bp_finalize(const SliceDesc* __restrict
             acc.x += v.x;
             acc.y += v.y;
         }
-        bp_pixel_epilogue<MODE>(d, i, j, acc, ep, out, nullptr, 0, dot_c, dot_p);
+        bp_pixel_epilogue<MODE>(d, i, j, acc, ep, out, planar, nch, dot_c, dot_p);
     }
     if (MODE == BP_AP || MODE == BP_AP_NOGRAD) bp_block_dots(dot_c, dot_p, ep.partial);
 }
@@ -226,20 +231,33 @@ void launch_bp_sweep(const SliceDesc* dsl, const BlockMap& smap, int nsweep, int
         k_bp_sweep<float2><<<nsweep, 32 * kSwWarps, 0, st>>>(dsl, smap, C, (const float2*)sino, partial, stride);
 }
 
+template <int MODE>
+static void finalize_t(const SliceDesc* dsl, const BlockMap& pix, int npix, int C, const float2* partial,
+                       int64_t stride, float2* out, const BpEpilogue& ep, cudaStream_t st) {
+    k_bp_finalize<MODE><<<npix, 256, 0, st>>>(dsl, pix, C, partial, stride, out, ep, nullptr, 0);
+}
+
 void launch_bp_finalize(int mode, const SliceDesc* dsl, const BlockMap& pix, int npix, int C, const float2* partial,
                         int64_t stride, float2* out, const BpEpilogue& ep, cudaStream_t st) {
     switch (mode) {
-        case BP_PLAIN: k_bp_finalize<BP_PLAIN><<<npix, 256, 0, st>>>(dsl, pix, C, partial, stride, out, ep); break;
-        case BP_R0: k_bp_finalize<BP_R0><<<npix, 256, 0, st>>>(dsl, pix, C, partial, stride, out, ep); break;
-        case BP_AP: k_bp_finalize<BP_AP><<<npix, 256, 0, st>>>(dsl, pix, C, partial, stride, out, ep); break;
-        case BP_R0_NOGRAD:
-            k_bp_finalize<BP_R0_NOGRAD><<<npix, 256, 0, st>>>(dsl, pix, C, partial, stride, out, ep);
-            break;
-        case BP_AP_NOGRAD:
-            k_bp_finalize<BP_AP_NOGRAD><<<npix, 256, 0, st>>>(dsl, pix, C, partial, stride, out, ep);
-            break;
+        case BP_PLAIN: finalize_t<BP_PLAIN>(dsl, pix, npix, C, partial, stride, out, ep, st); break;
+        case BP_R0: finalize_t<BP_R0>(dsl, pix, npix, C, partial, stride, out, ep, st); break;
+        case BP_AP: finalize_t<BP_AP>(dsl, pix, npix, C, partial, stride, out, ep, st); break;
+        case BP_R0_NOGRAD: finalize_t<BP_R0_NOGRAD>(dsl, pix, npix, C, partial, stride, out, ep, st); break;
+        case BP_AP_NOGRAD: finalize_t<BP_AP_NOGRAD>(dsl, pix, npix, C, partial, stride, out, ep, st); break;
         default: break;
     }
+}
+
+void backproject_single(const SliceDesc& sd, const SliceDesc* d_dev, const int* maps, int C, const float* sino,
+                        int nch, float2* packed, float2* partial, float* out, cudaStream_t st) {
+    const int64_t nr = (int64_t)sd.g.nv * sd.g.nb, np = (int64_t)sd.g.nx * sd.g.ny;
+    launch_pack_planar(sino, nch, nr, packed, st);
+    const BlockMap smap{maps, 1}, pmap{maps + 2, 1};
+    k_bp_sweep<float2><<<sweep_tiles(sd.g.nx, sd.g.ny) * C, 32 * kSwWarps, 0, st>>>(d_dev, smap, C, packed, partial,
+                                                                                   np);
+    k_bp_finalize<BP_PLAIN><<<(unsigned)((np + 255) / 256), 256, 0, st>>>(d_dev, pmap, C, partial, np, nullptr,
+                                                                         BpEpilogue{}, out, nch);
 }
 
 }  // namespace dect

@@ -1,4 +1,4 @@
-// Per-pixel epilogues of the gathering backprojector: the CG pieces of Eq. 12 that are computed
+// Per-pixel epilogues of the backprojector: the CG pieces of Eq. 12 that are computed
 // where R^T's result for a pixel is produced (r0 = R^T b + D^T(y + u^y - D x) + (z + u^z - x), and
 // A p = R^T q + D^T D p + p with the partial sums of <p, A p>), shared by the backprojector kernels.
 #pragma once

@@ -94,7 +94,7 @@ struct SpecDev {
     const float4* t2;
 };
 
-// Epilogue modes of the gathering backprojector.
+// Epilogue modes of the backprojector.
 enum BpMode {
     BP_PLAIN = 0,      // out = R^T s
     BP_R0 = 1,         // out = R^T b + D^T(y + u^y - D x) + (z + u^z - x)
@@ -122,9 +122,6 @@ void launch_textures(const SliceDesc* dsl, const BlockMap& mx, int nbx, const Bl
                      const float2* img, void* tx, void* ty, int prec, cudaStream_t st);
 void launch_project(const SliceDesc* dsl, const BlockMap& map, int nblk, const void* tx, const void* ty, void* out,
                     int prec, cudaStream_t st);
-void launch_backproject(int mode, const SliceDesc* dsl, const BlockMap& map, int nblk, const void* sino,
-                        float2* out, const BpEpilogue& ep, int groups, int prec, cudaStream_t st);
-int bp_groups(int tiles);
 // backproject_sweep.cu: the solver's backprojector (two kernels: sweep into C partial images, then
 // the fixed-order sum of the partials with the epilogue; partial dots over the `pix` blocks)
 int sweep_ctas_for_groups(int view_groups);
@@ -134,16 +131,18 @@ void launch_bp_sweep(const SliceDesc* dsl, const BlockMap& smap, int nsweep, int
                      float2* partial, int64_t stride, int prec, cudaStream_t st);
 void launch_bp_finalize(int mode, const SliceDesc* dsl, const BlockMap& pix, int npix, int C, const float2* partial,
                         int64_t stride, float2* out, const BpEpilogue& ep, cudaStream_t st);
+// Single-slice planar R^T (dect_backproject): sino [nch][nv][nb] -> out [nch][ny][nx]. d_dev is the
+// slice's descriptor on the device with zero offsets; maps holds the sweep and pixel-block prefixes
+// {0, sweep_tiles * C, 0, pixel blocks}; packed holds nv*nb float2, partial C*nx*ny float2.
+void backproject_single(const SliceDesc& sd, const SliceDesc* d_dev, const int* maps, int C, const float* sino,
+                        int nch, float2* packed, float2* partial, float* out, cudaStream_t st);
 void project_single(const SliceDesc& sd, const float* img, int nch, float2* scratch, float4* tx, float4* ty,
                     float* out, cudaStream_t st);
-void backproject_single(const SliceDesc& sd, const float* sino, int nch, float2* packed, float* out,
-                        cudaStream_t st);
-int bp_tiles(int nx, int ny);
+void launch_pack_planar(const float* in, int nch, int64_t n, float2* out, cudaStream_t st);
 int texture_x_blocks(int nx, int ny);
 int texture_y_blocks(int nx, int ny);
 constexpr int kRaysPerBlock = 256;
 constexpr int kPixPerBlock = 256;
-constexpr int kBpTile = 16;
 
 // udm.cu
 void launch_udm_admm(const SliceDesc* dsl, const BlockMap& map, int nblk, const SpecDev& sp, const float4* meas,

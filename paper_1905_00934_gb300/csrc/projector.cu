@@ -15,13 +15,9 @@
 // neighbours; the image is read through a pair texture (both neighbours of
 // both bases in one 16-byte load).
 //
-// R^T: one thread per pixel, gathering over views. For each view it bounds
-// the detector interval that can reach the pixel (the projection of the
-// 2-pixel cross around it), then evaluates each candidate ray's position at
-// the pixel's column (row) with the same integers R steps through, so both
-// kernels apply bit-identical interpolation weights and <R x, y> = <x, R^T y>
-// holds to float32 summation rounding. No atomics: the result is
-// deterministic.
+// R^T: the column-sweep kernel of backproject_sweep.cu evaluates the same
+// integers per sample, so <R x, y> = <x, R^T y> holds to float32 summation
+// rounding; no atomics, deterministic.
 #include <cuda_runtime.h>
 #include <math.h>
 
@@ -233,177 +229,6 @@ void launch_project(const SliceDesc* dsl, const BlockMap& map, int nblk, const v
 }
 
 // ---------------------------------------------------------------------------------------------
-// gathering backprojector
-
-// Accumulators of a 2x2 pixel block, both bases: pixel (dy, dx) -> a[dy][dx].
-struct Block2x2 {
-    float c00, c01, c10, c11, p00, p01, p10, p11;
-};
-
-// One candidate ray for the block with top-left pixel (i, j). AX: 0 or 1 when the ray's axis is
-// known to the caller, -1 to read it from the entry.
-template <int AX, class S2>
-__device__ __forceinline__ void block_ray(const int4 P, const S2* __restrict__ sv, int i, int j, Block2x2& a) {
-    const bool ax = AX < 0 ? ray_axis(P) : (AX == 1);
-    // samples at the block's two columns (axis 0) or rows (axis 1)
-    const long long qa = ray_pos(P, ax ? j : i);
-    const long long qb = qa + ray_step(P);
-    const int c0 = ax ? i : j;
-    const int da = pos_floor(qa) - c0, db = pos_floor(qb) - c0;
-    if ((unsigned)(da + 1) > 2u && (unsigned)(db + 1) > 2u) return;  // no weight on the block
-    float a0, a1, b0, b1;
-    across_weights(da, frac_of(qa), a0, a1);
-    across_weights(db, frac_of(qb), b0, b1);
-    // axis 0: sample s at column i + s, across offset r at row j + r -> pixel (r, s)
-    // axis 1: sample s at row j + s, across offset r at column i + r -> pixel (s, r)
-    const float w01 = ax ? a1 : b0, w10 = ax ? b0 : a1;
-    const float2 s2 = ldg2(sv);
-    const float wr = ray_w(P);
-    const float sc = wr * s2.x, sp = wr * s2.y;
-    a.c00 = fmaf(a0, sc, a.c00);
-    a.p00 = fmaf(a0, sp, a.p00);
-    a.c01 = fmaf(w01, sc, a.c01);
-    a.p01 = fmaf(w01, sp, a.p01);
-    a.c10 = fmaf(w10, sc, a.c10);
-    a.p10 = fmaf(w10, sp, a.p10);
-    a.c11 = fmaf(b1, sc, a.c11);
-    a.p11 = fmaf(b1, sp, a.p11);
-}
-
-// Gathers views v0, v0 + dv, ... for the 2x2 block with top-left pixel (i, j). The candidates of one
-// view pass within 1.5 pixels of the block, so their directions span less than 60 degrees (the
-// geometry check keeps the source at least 4.25 pixels away) and their sampling axis changes at
-// most once, where the direction crosses a diagonal: when the first and last candidate share an
-// axis, every candidate between them does too (specialised loop).
-template <class S2>
-__device__ __forceinline__ void gather_block(const GeomDev& g, const S2* __restrict__ sino, int i, int j, int v0,
-                                             int dv, Block2x2& a) {
-    const float xc = ((float)i + 0.5f - g.cx) * g.pix, yc = ((float)j + 0.5f - g.cy) * g.pix;
-    for (int v = v0; v < g.nv; v += dv) {
-        const float4 V = __ldg(g.views + v);
-        const CandRange cr = block_candidates<-1>(g, V.x, V.y, xc, yc);
-        if (cr.lo > cr.hi) continue;
-        const int4* rv = g.rays + (size_t)v * g.nb;
-        const S2* sv = sino + (size_t)v * g.nb;
-        const bool ax_lo = __ldg(&rv[cr.lo].w) < 0, ax_hi = __ldg(&rv[cr.hi].w) < 0;
-        if (ax_lo == ax_hi) {
-            if (ax_lo) {
-                for (int k = cr.lo; k <= cr.hi; ++k) block_ray<1, S2>(__ldg(rv + k), sv + k, i, j, a);
-            } else {
-                for (int k = cr.lo; k <= cr.hi; ++k) block_ray<0, S2>(__ldg(rv + k), sv + k, i, j, a);
-            }
-        } else {
-            for (int k = cr.lo; k <= cr.hi; ++k) block_ray<-1, S2>(__ldg(rv + k), sv + k, i, j, a);
-        }
-    }
-}
-
-// Backprojector tile: 16 x 16 pixels; 64 threads per view group, each owning a 2x2 pixel block; G
-// view groups (views v = group, group + G, ...) with G chosen by the host so that the grid fills
-// the GPU in one wave where possible. The G partial sums of each pixel are added in a fixed order,
-// so the result is deterministic.
-constexpr int kBpMaxGroups = 8;
-
-template <int MODE, class S2>
-__device__ __forceinline__ void backproject_tile(const SliceDesc& d, int local, const S2* __restrict__ sino,
-                                                 float2* __restrict__ out, const BpEpilogue& ep, float* __restrict__ planar,
-                                                 int nch) {
-    __shared__ float red[kBpMaxGroups][8][64];
-    const int G = blockDim.x / 64;
-    const int nx = d.g.nx, ny = d.g.ny;
-    const int tiles_x = (nx + kBpTile - 1) / kBpTile;
-    const int ti = (local % tiles_x) * kBpTile, tj = (local / tiles_x) * kBpTile;
-    {
-        const int grp = threadIdx.x / 64, b = threadIdx.x % 64;
-        const int bi = ti + 2 * (b % 8), bj = tj + 2 * (b / 8);
-        Block2x2 a = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-        if (bi < nx && bj < ny) gather_block(d.g, sino + d.sino_off, bi, bj, grp, G, a);
-        red[grp][0][b] = a.c00;
-        red[grp][1][b] = a.p00;
-        red[grp][2][b] = a.c01;
-        red[grp][3][b] = a.p01;
-        red[grp][4][b] = a.c10;
-        red[grp][5][b] = a.p10;
-        red[grp][6][b] = a.c11;
-        red[grp][7][b] = a.p11;
-    }
-    __syncthreads();
-    // epilogue: the block's threads walk the tile's 256 pixels
-    double dot_c = 0.0, dot_p = 0.0;
-    for (int px = threadIdx.x; px < kBpTile * kBpTile; px += blockDim.x) {
-        const int pi = px % kBpTile, pj = px / kBpTile;
-        const int i = ti + pi, j = tj + pj;
-        if (i >= nx || j >= ny) continue;
-        const int b = (pj / 2) * 8 + (pi / 2), q = 2 * (2 * (pj % 2) + (pi % 2));
-        float2 r = make_float2(0.f, 0.f);
-        for (int grp = 0; grp < G; ++grp) {
-            r.x += red[grp][q][b];
-            r.y += red[grp][q + 1][b];
-        }
-        bp_pixel_epilogue<MODE>(d, i, j, r, ep, out, planar, nch, dot_c, dot_p);
-    }
-    if (MODE == BP_AP || MODE == BP_AP_NOGRAD) bp_block_dots(dot_c, dot_p, ep.partial);
-}
-
-template <int MODE, class S2>
-__global__ void __launch_bounds__(64 * kBpMaxGroups) k_backproject(const SliceDesc* __restrict__ dsl, BlockMap map,
-                                                                   const S2* __restrict__ sino,
-                                                                   float2* __restrict__ out, BpEpilogue ep) {
-    int local;
-    const int s = slice_of(map, blockIdx.x, local);
-    backproject_tile<MODE, S2>(dsl[s], local, sino, out, ep, nullptr, 0);
-}
-
-__global__ void __launch_bounds__(64 * kBpMaxGroups) k_backproject_planar(SliceDesc d, const float2* __restrict__ sino,
-                                                                          float* __restrict__ out, int nch) {
-    BpEpilogue ep{};
-    backproject_tile<BP_PLAIN, float2>(d, blockIdx.x, sino, nullptr, ep, out, nch);
-}
-
-int bp_tiles(int nx, int ny) { return ((nx + kBpTile - 1) / kBpTile) * ((ny + kBpTile - 1) / kBpTile); }
-
-// View groups per tile: the largest G whose grid of `tiles` blocks is resident in one wave; more
-// groups give more threads per tile, and one wave avoids a partly idle tail.
-int bp_groups(int tiles) {
-    static int occ[kBpMaxGroups + 1] = {0};
-    static int sms = 0;
-    if (!sms) {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        for (int G = 1; G <= kBpMaxGroups; ++G)
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[G], k_backproject<BP_AP, float2>, 64 * G, 0);
-    }
-    for (int G = kBpMaxGroups; G >= 1; --G)
-        if ((long long)occ[G] * sms >= tiles) return G;
-    return 4;
-}
-
-template <class S2>
-static void launch_bp_t(int mode, const SliceDesc* dsl, const BlockMap& map, int nblk, const S2* sino, float2* out,
-                        const BpEpilogue& ep, int T, cudaStream_t st) {
-    switch (mode) {
-        case BP_PLAIN: k_backproject<BP_PLAIN, S2><<<nblk, T, 0, st>>>(dsl, map, sino, out, ep); break;
-        case BP_R0: k_backproject<BP_R0, S2><<<nblk, T, 0, st>>>(dsl, map, sino, out, ep); break;
-        case BP_AP: k_backproject<BP_AP, S2><<<nblk, T, 0, st>>>(dsl, map, sino, out, ep); break;
-        case BP_R0_NOGRAD: k_backproject<BP_R0_NOGRAD, S2><<<nblk, T, 0, st>>>(dsl, map, sino, out, ep); break;
-        case BP_AP_NOGRAD: k_backproject<BP_AP_NOGRAD, S2><<<nblk, T, 0, st>>>(dsl, map, sino, out, ep); break;
-        default: break;
-    }
-}
-
-void launch_backproject(int mode, const SliceDesc* dsl, const BlockMap& map, int nblk, const void* sino,
-                        float2* out, const BpEpilogue& ep, int groups, int prec, cudaStream_t st) {
-    const int T = 64 * groups;
-    if (prec == PREC_F16)
-        launch_bp_t(mode, dsl, map, nblk, (const __half2*)sino, out, ep, T, st);
-    else if (prec == PREC_BF16)
-        launch_bp_t(mode, dsl, map, nblk, (const __nv_bfloat162*)sino, out, ep, T, st);
-    else
-        launch_bp_t(mode, dsl, map, nblk, (const float2*)sino, out, ep, T, st);
-}
-
-// ---------------------------------------------------------------------------------------------
 // single-slice planar entry points (dect_project / dect_backproject)
 
 __global__ void k_texture_x_single(SliceDesc d, const float2* __restrict__ img, float4* __restrict__ tx) {
@@ -453,15 +278,8 @@ void project_single(const SliceDesc& sd_in, const float* img, int nch, float2* s
                                                                                                       nch);
 }
 
-// `packed` must hold nv*nb float2
-void backproject_single(const SliceDesc& sd_in, const float* sino, int nch, float2* packed, float* out,
-                        cudaStream_t st) {
-    SliceDesc sd = sd_in;
-    sd.img_off = sd.sino_off = sd.tx_off = sd.ty_off = sd.fft_off = sd.h_off = 0;
-    const int64_t nr = (int64_t)sd.g.nv * sd.g.nb;
-    k_pack_planar<<<(unsigned)((nr + 255) / 256), 256, 0, st>>>(sino, nch, nr, packed);
-    const int tiles = bp_tiles(sd.g.nx, sd.g.ny);
-    k_backproject_planar<<<tiles, 64 * bp_groups(tiles), 0, st>>>(sd, packed, out, nch);
+void launch_pack_planar(const float* in, int nch, int64_t n, float2* out, cudaStream_t st) {
+    k_pack_planar<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(in, nch, n, out);
 }
 
 int texture_x_blocks(int nx, int ny) { return tx_blocks(nx, ny); }

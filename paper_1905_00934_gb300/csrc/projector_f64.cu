@@ -1,4 +1,4 @@
-// Float64 forward projector R and gathering adjoint R^T (Eq. 2-3's projection matrix) for the
+// Float64 forward projector R and adjoint R^T (Eq. 2-3's projection matrix) for the
 // public entry points (dect_project / dect_backproject with DECT_F64), used where a float64 result
 // is wanted, e.g. gradient checks through the autograd wrappers.
 //
@@ -106,13 +106,14 @@ __global__ void k_backproject_f64(GeomDev g, const double4* __restrict__ rays, c
     const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= np) return;
     const int j = (int)(e / g.nx), i = (int)(e % g.nx);
-    // the candidate search of the float32 kernel for the 2x2 block with top-left (i, j) covers (i, j)
+    // rays with a non-zero weight at (i, j) pass within 1 pixel of it: candidates of the square of
+    // half-side 1.5 pixels around the 2x2 block with top-left (i, j)
     const float xc = ((float)i + 0.5f - g.cx) * g.pix, yc = ((float)j + 0.5f - g.cy) * g.pix;
     const int64_t n = (int64_t)g.nv * g.nb;
     double acc0 = 0.0, acc1 = 0.0;
     for (int v = 0; v < g.nv; ++v) {
         const float4 V = __ldg(g.views + v);
-        const CandRange cr = block_candidates<-1>(g, V.x, V.y, xc, yc);
+        const CandRange cr = rect_candidates(g, V.x, V.y, xc, yc, 1.5f * g.pix, 1.5f * g.pix);
         for (int k = cr.lo; k <= cr.hi; ++k) {
             const int64_t r = (int64_t)v * g.nb + k;
             const double4 P = rays[r];

@@ -52,43 +52,10 @@ struct CandRange {
     int lo, hi;
 };
 
-// Bins whose rays can have a non-zero weight at any pixel of a 2x2 block centred at (xc, yc) (cm)
-// in view (cs, sn). The block's interpolation support is, for rays sampled per column (axis 0), the
-// two vertical segments x = xc -+ pix/2, |y - yc| <= 1.5 pix, and for rays sampled per row (axis 1)
-// the transposed pair; AX = -1 bounds both (the square of half-side 1.5 pix). A segment's
-// projection onto the detector is bounded by its end points' projections (fan) or by the projected
-// half-width (parallel). eps absorbs float32 rounding and the rays' fixed-point quantisation (both
-// far below 0.02 bins).
-template <int AX>
-__device__ __forceinline__ CandRange block_candidates(const GeomDev& g, float cs, float sn, float xc, float yc) {
-    const float eps = 0.02f;
-    const float hx = (AX == 0 ? 0.5f : 1.5f) * g.pix, hy = (AX == 1 ? 0.5f : 1.5f) * g.pix;
-    float kmin, kmax;
-    if (g.kind == DECT_PARALLEL) {
-        const float kc = fmaf(fmaf(xc, cs, yc * sn), g.inv_du, g.k0);
-        const float h = fmaf(hx, fabsf(cs), hy * fabsf(sn)) * g.inv_du;
-        kmin = kc - h;
-        kmax = kc + h;
-    } else {
-        // u(P) = sdd (P . e) / (sod - P . n), e = (-sin, cos), n = (cos, sin)
-        const float num = fmaf(-xc, sn, yc * cs), den = g.sod - fmaf(xc, cs, yc * sn);
-        const float nx_ = -hx * sn, dx_ = -hx * cs;  // change of num / den for x += hx
-        const float ny_ = hy * cs, dy_ = -hy * sn;   // change of num / den for y += hy
-        const float u1 = __fdividef(num + nx_ + ny_, den + dx_ + dy_);
-        const float u2 = __fdividef(num + nx_ - ny_, den + dx_ - dy_);
-        const float u3 = __fdividef(num - nx_ + ny_, den - dx_ + dy_);
-        const float u4 = __fdividef(num - nx_ - ny_, den - dx_ - dy_);
-        kmin = fmaf(g.k1, fminf(fminf(u1, u2), fminf(u3, u4)), g.k0);
-        kmax = fmaf(g.k1, fmaxf(fmaxf(u1, u2), fmaxf(u3, u4)), g.k0);
-    }
-    CandRange c;
-    c.lo = max(0, (int)ceilf(fmaxf(kmin - eps, -1.0f)));
-    c.hi = min(g.nb - 1, (int)floorf(fminf(kmax + eps, (float)g.nb)));
-    return c;
-}
-
-// Bins whose rays can reach the axis-aligned rectangle of half-sides (hx, hy) cm centred at (xc, yc):
-// the projection of its corners (fan) or of its half-width (parallel), widened by eps bins.
+// Bins whose rays can reach the axis-aligned rectangle of half-sides (hx, hy) cm centred at (xc, yc)
+// in view (cs, sn): the projection of its corners (fan; the rectangle lies in front of the source)
+// or of its half-width (parallel). eps absorbs float32 rounding and the rays' fixed-point
+// quantisation (both far below 0.02 bins).
 __device__ __forceinline__ CandRange rect_candidates(const GeomDev& g, float cs, float sn, float xc, float yc, float hx,
                                                      float hy) {
     const float eps = 0.02f;
@@ -113,14 +80,6 @@ __device__ __forceinline__ CandRange rect_candidates(const GeomDev& g, float cs,
     c.lo = max(0, (int)ceilf(fmaxf(kmin - eps, -1.0f)));
     c.hi = min(g.nb - 1, (int)floorf(fminf(kmax + eps, (float)g.nb)));
     return c;
-}
-
-// Interpolation weights of one sample for the two pixels across at offsets 0 and 1 (d = lower
-// neighbour minus the first across index): the lower neighbour gets 1 - f and the upper one f,
-// exactly as the forward interpolation.
-__device__ __forceinline__ void across_weights(int d, float f, float& w0, float& w1) {
-    w0 = d == 0 ? 1.0f - f : (d == -1 ? f : 0.0f);
-    w1 = d == 1 ? 1.0f - f : (d == 0 ? f : 0.0f);
 }
 
 }  // namespace dect

@@ -1,0 +1,86 @@
+"""Slice sharding across ranks (one process per GPU).
+
+Slices are independent ADMM problems (Sec. 3.3 per slice), so ranks reconstruct disjoint slices and
+exchange nothing on the data path. Ranks take contiguous slice ranges balanced by a per-slice cost:
+the iteration's work is dominated by R and R^T (Table 1), whose cost grows with the number of
+projection-matrix weights, about n_views * n_bins * max(nx, ny) per basis.
+"""
+from __future__ import annotations
+
+from typing import Sequence
+
+
+def slice_cost(nx: int, ny: int, n_views: int, n_bins: int, iterations: int = 1) -> float:
+    """Relative cost of reconstructing one slice: projector weights x iterations."""
+    return float(n_views) * float(n_bins) * float(max(nx, ny)) * float(iterations)
+
+
+def _fits(costs: Sequence[float], parts: int, cap: float) -> bool:
+    used, load = 1, 0.0
+    for c in costs:
+        if c > cap:
+            return False
+        if load + c > cap:
+            used += 1
+            load = c
+        else:
+            load += c
+    return used <= parts
+
+
+def partition(costs: Sequence[float], parts: int) -> list[tuple[int, int]]:
+    """Splits slices 0..n-1 into `parts` contiguous ranges [lo, hi) minimising the largest range cost.
+
+    Exact over the candidate capacities (the sums of contiguous runs); ranges may be empty when there
+    are fewer slices than parts.
+    """
+    if parts < 1:
+        raise ValueError("parts must be >= 1")
+    n = len(costs)
+    if any(c < 0 for c in costs):
+        raise ValueError("costs must be >= 0")
+    if n == 0:
+        return [(0, 0)] * parts
+    # the optimal bottleneck is the sum of some contiguous run: bisect over the sorted run sums
+    prefix = [0.0]
+    for c in costs:
+        prefix.append(prefix[-1] + c)
+    cands = sorted({prefix[j] - prefix[i] for i in range(n) for j in range(i + 1, n + 1)})
+    lo, hi = 0, len(cands) - 1
+    while lo < hi:
+        mid = (lo + hi) // 2
+        if _fits(costs, parts, cands[mid]):
+            hi = mid
+        else:
+            lo = mid + 1
+    cap = cands[lo]
+    # greedy fill at the optimal capacity, then pad with empty ranges
+    ranges, start, load = [], 0, 0.0
+    for i, c in enumerate(costs):
+        if load + c > cap and i > start:
+            ranges.append((start, i))
+            start, load = i, 0.0
+        load += c
+    ranges.append((start, n))
+    while len(ranges) < parts:
+        ranges.append((n, n))
+    return ranges
+
+
+def rank_slices(costs: Sequence[float], rank: int, world_size: int) -> range:
+    """The slice indices rank `rank` of `world_size` reconstructs."""
+    lo, hi = partition(costs, world_size)[rank]
+    return range(lo, hi)
+
+
+def max_over_ranks(value: float, device=None) -> float:
+    """The largest `value` over all ranks (the job's time is its slowest rank's); `value` itself
+    without an initialised process group."""
+    import torch
+    import torch.distributed as dist
+
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(value)
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())

@@ -6,7 +6,12 @@ xi_c, xi_p (Eq. 14) every 10 iterations, and the final Compton and PE values at 
 positions each, so the GPU runs (float32 / float16 / bfloat16 storage) can be compared with the
 oracle pixel by pixel without storing whole images.
 
-Usage: python tests/golden/make_golden_mixed.py [--slices 4] [--iters 100]
+With --early K it instead writes mixed_1024_early.json: for each slice, the sampled pixels after the
+initial image and after each of the first K iterations, from float32-rounded measurements (the
+values the GPU receives), for a pixel-by-pixel comparison before float32 rounding of the per-ray
+decisions has had time to accumulate.
+
+Usage: python tests/golden/make_golden_mixed.py [--slices 4] [--iters 100] [--early K]
 """
 from __future__ import annotations
 
@@ -37,8 +42,12 @@ def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--slices", type=int, default=4)
     ap.add_argument("--iters", type=int, default=100)
-    ap.add_argument("--out", default=os.path.join(HERE, "mixed_1024_oracle.json"))
+    ap.add_argument("--out", default=None)
+    ap.add_argument("--early", type=int, default=0)
     args = ap.parse_args()
+    if args.early:
+        return early(args)
+    args.out = args.out or os.path.join(HERE, "mixed_1024_oracle.json")
     out = {"what": "FP64 oracle, UDM1-PCG1, fan beam 1024x1024, 1440 views, 2048 bins, E_ref 100 keV, kappa 0.25; "
                    "xi every 10 iterations (entry 0 = initial image) and final x at seeded pixels",
            "iterations": args.iters, "slices": []}
@@ -64,6 +73,28 @@ def main():
             json.dump(out, f)
     out["oracle_threads"] = _clib.num_threads()
     with open(args.out, "w") as f:
+        json.dump(out, f)
+
+
+def early(args):
+    out_path = args.out or os.path.join(HERE, "mixed_1024_early.json")
+    out = {"what": "FP64 oracle from float32-rounded measurements, fan beam 1024x1024, 1440 views, 2048 bins, "
+                   "E_ref 100 keV, kappa 0.25: sampled x after the initial image (entry 0) and after each of the "
+                   "first iterations", "iterations": args.early, "slices": []}
+    for s in range(args.slices):
+        c = baggage_fan_case(slice_index=MIXED_SEED_BASE + s, n=N, n_views=VIEWS, n_bins=BINS)
+        meas = [np.float32(c[k]).astype(np.float64) for k in ("m_h", "m_l", "w_h", "w_l")]
+        prob = admm.Problem(c["geom"], c["spectra"], *meas, admm.Params(kappa=BAGGAGE_KAPPA))
+        xc0, xp0 = admm.initial_image(prob)
+        st = admm.state_from_image(prob, xc0, xp0)
+        idx = sample_pixels(s)
+        xs = [[xc0.ravel()[idx].tolist(), xp0.ravel()[idx].tolist()]]
+        for _ in range(args.early):
+            st = admm.admm_iteration(prob, st)
+            xs.append([st.x[0].ravel()[idx].tolist(), st.x[1].ravel()[idx].tolist()])
+        out["slices"].append({"slice_index": MIXED_SEED_BASE + s, "pixels": idx.tolist(), "x": xs})
+        print(s, "done", flush=True)
+    with open(out_path, "w") as f:
         json.dump(out, f)
 
 

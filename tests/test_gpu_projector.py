@@ -1,4 +1,4 @@
-"""GPU projector R and gathering backprojector R^T against the FP64 oracle (Eq. 2-3's R, Table 1's R^T).
+"""GPU projector R and backprojector R^T against the FP64 oracle (Eq. 2-3's R, Table 1's R^T).
 
 Tolerance: relative L2 <= 1e-5 (float32 accumulation over <= 2N samples per ray / pixel)."""
 import math
@@ -16,13 +16,18 @@ pytestmark = pytest.mark.gpu
 TOL = 1e-5
 
 GEOMS = {
-    # several 16x16 tiles plus ragged tails, non-square, odd sizes, offset detector
+    # several 32x32 backprojector tiles plus ragged tails, non-square, odd sizes, offset detector
     "parallel_ragged": G.Geometry(G.PARALLEL, 53, 37, 0.1, 41, 0.13, math.pi, 77, 0.085, 0.03),
     "parallel_small": G.small_parallel_geometry(),
     "fan_ragged": G.Geometry(G.FAN_FLAT, 45, 61, 0.1, 47, 0.2, 2 * math.pi, 83, 0.13, -0.05, 12.0, 21.0),
     "fan_baggage_128": G.baggage_fan_geometry(128, 180, 256),
     "tiny": G.Geometry(G.PARALLEL, 3, 5, 0.5, 3, 0.3, math.pi, 4, 0.4, 0.0),
     "one_view_one_bin": G.Geometry(G.FAN_FLAT, 9, 9, 0.1, 1, 0.7, 2 * math.pi, 1, 0.2, 0.0, 5.0, 9.0),
+    # image much smaller than one tile, source as close as the geometry check allows (4.25 pixels
+    # beyond the image's bounding circle plus margin): the tile rectangle must be clipped to the image
+    "fan_near_source": G.Geometry(G.FAN_FLAT, 20, 12, 0.1, 64, 0.1, 2 * math.pi, 96, 0.06, 0.0, 1.80, 3.5),
+    # three by two tiles with ragged tails, wide detector
+    "fan_ragged_tiles": G.Geometry(G.FAN_FLAT, 70, 33, 0.1, 90, 1.1, 2 * math.pi, 140, 0.12, 0.3, 9.0, 15.0),
 }
 
 
