@@ -6,9 +6,18 @@
 // evaluates f_h, f_l and their Jacobian at a (one pass over the energies:
 // one exp2 and six FMAs per bin) and f_h, f_l at the trial point a + delta
 // (one exp2 and two FMAs per bin): the 4 evaluations of f of Table 1. Energy
-// sums are float32; the logs of the spectral sums, the cost and the 2x2 solve
-// are float64, where the photoelectric coordinate (whose Jacobian column is
-// orders of magnitude below the Compton one) needs the range.
+// sums are float32 (compensated). Residuals come from the ratio of a spectral
+// sum to the measured transmission t = e^{-m}: f - m = -log(s / t), from
+// log1p of the relative difference when s and t are within a factor 2, which
+// keeps the float32 sum's accuracy without a float64 log; the cost change of
+// the trial step is formed from the residual changes -log(s' / s), so the
+// accept test (cost decreased) does not subtract two large costs. The normal
+// equations, the 2x2 Marquardt solve and the cost change are float64 from
+// float32 inputs: the photoelectric Jacobian column is nearly a multiple of
+// the Compton one at high attenuation, and rounding the three matrix entries
+// separately in float32 breaks the consistency the solve relies on (measured:
+// 10x larger drift from the FP64 oracle at 1024^2). Everything else is float32
+// (float64 throughput is low on this GPU).
 #include <cuda_runtime.h>
 #include <math.h>
 
@@ -17,9 +26,19 @@
 
 namespace dect {
 
+// One ray's inputs; v = (R x - u^a) is carried as an unevaluated sum hi + lo (exact in float32)
 struct RayIn {
-    double mh, ml, wh, wl, vc, vp, rc, rp;
+    float mh, ml, wh, wl;
+    float vc_hi, vc_lo, vp_hi, vp_lo;
+    double rc, rp;
 };
+
+// v = a - b as hi + lo with hi = fl(a - b) and lo its exact rounding error (two-sum)
+__device__ __forceinline__ void split_diff(float a, float b, float& hi, float& lo) {
+    hi = a - b;
+    const float bb = a - hi;
+    lo = (a - (hi + bb)) + (bb - b);
+}
 
 struct LmState {
     float ac, ap, mu;
@@ -78,46 +97,59 @@ __device__ __forceinline__ void spectral_sums(const float4* __restrict__ t1, int
     }
 }
 
-__device__ __forceinline__ double ray_cost(double fh, double fl, double ac, double ap, const RayIn& in) {
-    const double rh = fh - in.mh, rl = fl - in.ml;
-    const double dc = ac - in.vc, dp = ap - in.vp;
-    return 0.5 * (in.wh * rh * rh + in.wl * rl * rl) + 0.5 * (in.rc * dc * dc + in.rp * dp * dp);
+// -log(a / b) for positive a, b: from the relative difference when the ratio is within [1/2, 2] (then
+// a - b is exact and log1p keeps its accuracy), from the ratio itself otherwise (photon-starved
+// rays whose model sum is orders of magnitude off the measurement, large trial steps)
+__device__ __forceinline__ float neg_log_ratio(float a, float b) {
+    const float q = a / b;
+    return (q > 0.5f && q < 2.0f) ? -log1pf((a - b) / b) : -logf(q);
 }
 
 // `iters` LM iterations of Eq. 13 for one ray (tables t1/t2 in shared memory).
 __device__ void lm_ray(const float4* __restrict__ t1, const float4* __restrict__ t2, int ne, const RayIn& in,
                        int iters, LmState& s) {
+    const float tm_h = expf(-in.mh), tm_l = expf(-in.ml);
+    const double wh = in.wh, wl = in.wl, rc = in.rc, rp = in.rp;  // rho exact as the host's float64
     for (int it = 0; it < iters; ++it) {
         float sh, sl, shc, shp, slc, slp;
         spectral_sums_jac(t1, t2, ne, s.ac, s.ap, sh, sl, shc, shp, slc, slp);
-        const double fh = -log((double)sh), fl = -log((double)sl);
-        const double ish = 1.0 / (double)sh, isl = 1.0 / (double)sl;
-        const double j0 = shc * ish, j1 = shp * ish, j2 = slc * isl, j3 = slp * isl;
-        const double rh = fh - in.mh, rl = fl - in.ml;
-        const double g0 = in.wh * rh * j0 + in.wl * rl * j2 + in.rc * ((double)s.ac - in.vc);
-        const double g1 = in.wh * rh * j1 + in.wl * rl * j3 + in.rp * ((double)s.ap - in.vp);
-        const double A00 = in.wh * j0 * j0 + in.wl * j2 * j2 + in.rc;
-        const double A01 = in.wh * j0 * j1 + in.wl * j2 * j3;
-        const double A11 = in.wh * j1 * j1 + in.wl * j3 * j3 + in.rp;
-        const double m1 = 1.0 + (double)s.mu;
-        const double B00 = A00 * m1, B11 = A11 * m1;
-        const double det = B00 * B11 - A01 * A01;
-        const double cost0 = ray_cost(fh, fl, s.ac, s.ap, in);
-        if (!(det > 0.0) || !isfinite(det) || !isfinite(cost0)) {
+        const float rh = neg_log_ratio(sh, tm_h), rl = neg_log_ratio(sl, tm_l);  // f - m = -log(s / t)
+        if (!isfinite(rh) || !isfinite(rl)) {
             s.status = DECT_RAY_NONFINITE;
             break;
         }
-        const double d0 = (-g0 * B11 + g1 * A01) / det;
-        const double d1 = (-g1 * B00 + g0 * A01) / det;
-        const float tc = (float)((double)s.ac + d0), tp = (float)((double)s.ap + d1);
+        // gradient and damped Gauss-Newton matrix of the linearised Eq. 13, float64 from the float32
+        // Jacobian (products of float32 values are exact, so the matrix stays consistent)
+        const double j0 = shc / sh, j1 = shp / sh, j2 = slc / sl, j3 = slp / sl;
+        const double dc = ((double)s.ac - in.vc_hi) - in.vc_lo, dp = ((double)s.ap - in.vp_hi) - in.vp_lo;
+        const double wrh = wh * rh, wrl = wl * rl;
+        const double g0 = wrh * j0 + wrl * j2 + rc * dc;
+        const double g1 = wrh * j1 + wrl * j3 + rp * dp;
+        const double A00 = wh * j0 * j0 + wl * j2 * j2 + rc;
+        const double A01 = wh * j0 * j1 + wl * j2 * j3;
+        const double A11 = wh * j1 * j1 + wl * j3 * j3 + rp;
+        const double m1 = 1.0 + (double)s.mu;
+        const double B00 = A00 * m1, B11 = A11 * m1;
+        const double det = B00 * B11 - A01 * A01;
+        if (!(det > 0.0) || !isfinite(det)) {
+            s.status = DECT_RAY_NONFINITE;
+            break;
+        }
+        const double idet = 1.0 / det;
+        const float tc = (float)((double)s.ac + (g1 * A01 - g0 * B11) * idet);
+        const float tp = (float)((double)s.ap + (g0 * A01 - g1 * B00) * idet);
         float th, tl;
         spectral_sums(t1, ne, tc, tp, th, tl);
-        const double cost1 = ray_cost(-log((double)th), -log((double)tl), tc, tp, in);
+        // cost(trial) - cost(a) = 1/2 sum_k w_k (r1 - r0)(r1 + r0) + 1/2 sum_b rho_b e_b (e_b + 2 (a_b - v_b))
+        const float eh = neg_log_ratio(th, sh), el = neg_log_ratio(tl, sl);  // r1 - r0
+        const double ec = (double)tc - (double)s.ac, ep = (double)tp - (double)s.ap;
+        const double dcost = 0.5 * (wh * eh * (2.0 * rh + eh) + wl * el * (2.0 * rl + el)) +
+                             0.5 * (rc * ec * (ec + 2.0 * dc) + rp * ep * (ep + 2.0 * dp));
         float mu = s.mu;
-        if (!isfinite(cost1)) {
+        if (!isfinite(dcost)) {
             mu *= 10.f;
             s.status = DECT_RAY_NONFINITE;
-        } else if (cost1 < cost0) {
+        } else if (dcost < 0.0) {
             s.ac = tc;
             s.ap = tp;
             mu *= 0.1f;
@@ -169,8 +201,8 @@ __global__ void __launch_bounds__(kRaysPerBlock) k_udm_admm(const SliceDesc* __r
         in.ml = m.y;
         in.wh = m.z;
         in.wl = m.w;
-        in.vc = (double)rx.x - (double)u.x;
-        in.vp = (double)rx.y - (double)u.y;
+        split_diff(rx.x, u.x, in.vc_hi, in.vc_lo);
+        split_diff(rx.y, u.y, in.vp_hi, in.vp_lo);
         in.rc = sc[s].rho[0];
         in.rp = sc[s].rho[1];
         LmState st{a_old.x, a_old.y, mu[e], DECT_RAY_ACCEPTED};
@@ -227,8 +259,7 @@ __global__ void __launch_bounds__(kRaysPerBlock) k_udm_init(const SliceDesc* __r
     in.ml = m.y;
     in.wh = m.z;
     in.wl = m.w;
-    in.vc = 0.0;
-    in.vp = 0.0;
+    in.vc_hi = in.vc_lo = in.vp_hi = in.vp_lo = 0.0f;
     in.rc = 0.0;
     in.rp = rho_p;
     LmState st{m.y / abar, 0.0f, mu0, DECT_RAY_ACCEPTED};
@@ -255,8 +286,9 @@ __global__ void __launch_bounds__(kRaysPerBlock) k_udm_rays(SpecDev sp, int64_t 
     in.ml = __ldg(ml + r);
     in.wh = __ldg(wh + r);
     in.wl = __ldg(wl + r);
-    in.vc = __ldg(vc + r);
-    in.vp = __ldg(vp + r);
+    in.vc_hi = __ldg(vc + r);
+    in.vp_hi = __ldg(vp + r);
+    in.vc_lo = in.vp_lo = 0.0f;
     in.rc = rho_c;
     in.rp = rho_p;
     LmState st{ac[r], ap[r], mu[r], DECT_RAY_ACCEPTED};

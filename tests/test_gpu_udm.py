@@ -85,19 +85,27 @@ def test_one_lm_iteration_matches_oracle(cuda_dev, e_ref, rho):
 
 
 def test_many_iterations_converge_to_oracle_minimiser(cuda_dev):
-    # after enough iterations both sides sit at the same minimiser of Eq. 13
+    # run until both sides have stopped (damping at its clamp): they sit at the same minimiser of
+    # Eq. 13. Photon-starved rays (counts ~10) have flat valleys where the two sides take different
+    # accept sequences for a while (after 30 iterations one such ray was still 1.6e-4 apart, with
+    # different damping); the cost at the GPU's point must match the oracle's minimum.
     n = 5000
     t, d, a0 = _rays(n, 2, 100.0)
     d32 = _f32(d)
     a0 = tuple(np.float32(a).astype(np.float64) for a in a0)
     mu0 = np.full(n, 1e-3)
     rho = (1e-2, 1e-1)
-    gc, gp, _, gst = _run_gpu(cuda_dev, t, d32, a0, mu0, rho, 30)
+    gc, gp, _, gst = _run_gpu(cuda_dev, t, d32, a0, mu0, rho, 60)
     oc, op, _, _ = ospec.udm(t, d32["m_h"], d32["m_l"], d32["w_h"], d32["w_l"], d32["v_c"], d32["v_p"],
-                             rho[0], rho[1], 30, a0[0], a0[1], mu0)
+                             rho[0], rho[1], 60, a0[0], a0[1], mu0)
     assert np.max(np.abs(gc - oc) / np.maximum(np.abs(oc), 1)) < 1e-4
     assert np.linalg.norm(gp - op) / np.linalg.norm(op) < 1e-3
     assert np.all(gst != 2)
+    args = (t, d32["m_h"], d32["m_l"], d32["w_h"], d32["w_l"], d32["v_c"], d32["v_p"], rho[0], rho[1])
+    cg, co = ospec.udm_cost(*args, gc, gp), ospec.udm_cost(*args, oc, op)
+    # float32 resolution: a displacement of 8 ulps of a_c (unit Jacobian) costs about w * (8 ulp)^2
+    ulp_cost = (d32["w_h"] + d32["w_l"]) * (8 * 2.0 ** -24 * np.maximum(1.0, np.abs(oc))) ** 2
+    assert np.all(cg - co <= 1e-6 * co + ulp_cost)
 
 
 def test_edge_cases(cuda_dev):
