@@ -163,26 +163,70 @@ __global__ void k_pack_planar(const float* __restrict__ in, int nch, int64_t n, 
 // ---------------------------------------------------------------------------------------------
 // forward projector
 
+constexpr int kProjBatch = 8;
+
 // Sum over the ray's samples of the interpolated {c, p}; returns unweighted sums.
+//
+// The float estimate of the sample range is trimmed with the exact fixed-point positions at its two
+// ends, so every sample in [lo, hi] has its lower neighbour in [-2, n_across] (positions are linear
+// in t): the texel index (t, floor + 2) then lies inside the padded row [0, n_across + 2] without a
+// per-sample clamp. Trimming only drops samples whose two neighbours are both outside the image.
 template <class TX>
 __device__ __forceinline__ float2 ray_sum(const int4 P, const GeomDev& g, const TX* __restrict__ tx,
                                           const TX* __restrict__ ty) {
-    float ac = 0.f, ap = 0.f;
     const bool ax = ray_axis(P);
     const int n_along = ax ? g.ny : g.nx, n_across = ax ? g.nx : g.ny;
-    const TX* tex = ax ? ty : tx;
+    const TX* __restrict__ tex = ax ? ty : tx;
     const int ld = n_across + 3;
     int lo, hi;
     sample_range(P, n_along, n_across, lo, hi);
-    const long long step = ray_step(P);
-    long long q = ray_q0(P) + (long long)lo * step;
-    const TX* row = tex + (size_t)lo * ld;
-    for (int t = lo; t <= hi; ++t, q += step, row += ld) {
-        const int jj = min(max(pos_floor(q) + 2, 0), n_across + 2);
+    const long long step = ray_step(P), q0 = ray_q0(P);
+    for (int k = 0; k < 4 && lo <= hi; ++k) {
+        const int h = pos_floor(q0 + (long long)lo * step);
+        if (h >= -2 && h <= n_across) break;
+        ++lo;
+    }
+    for (int k = 0; k < 4 && hi >= lo; ++k) {
+        const int h = pos_floor(q0 + (long long)hi * step);
+        if (h >= -2 && h <= n_across) break;
+        --hi;
+    }
+    float ac = 0.f, ap = 0.f;
+    if (lo > hi) return make_float2(ac, ap);
+    {
+        // the trimming loops stop after 4 steps; re-check so that no sample can index outside its row
+        const int h0 = pos_floor(q0 + (long long)lo * step), h1 = pos_floor(q0 + (long long)hi * step);
+        if (h0 < -2 || h0 > n_across || h1 < -2 || h1 > n_across) return make_float2(ac, ap);
+    }
+    long long q = q0 + (long long)lo * step;
+    int base = lo * ld + 2;  // texel (t, floor(q) + 2) is tex[base + floor(q)]
+    int t = lo;
+    // blocks of kProjBatch samples: all texel loads of a block are issued before they are used, so a
+    // warp keeps several L2 requests in flight (the texels of neighbouring rays rarely share L1 lines)
+    for (; t + kProjBatch - 1 <= hi; t += kProjBatch) {
+        float4 v[kProjBatch];
+        float f[kProjBatch];
+#pragma unroll
+        for (int u = 0; u < kProjBatch; ++u) {
+            const long long qu = q + (long long)u * step;
+            v[u] = ldtex(tex + (base + u * ld + pos_floor(qu)));
+            f[u] = frac_of(qu);
+        }
+#pragma unroll
+        for (int u = 0; u < kProjBatch; ++u) {
+            ac += fmaf(f[u], v[u].z - v[u].x, v[u].x);
+            ap += fmaf(f[u], v[u].w - v[u].y, v[u].y);
+        }
+        q += (long long)kProjBatch * step;
+        base += kProjBatch * ld;
+    }
+    for (; t <= hi; ++t) {
+        const float4 v = ldtex(tex + (base + pos_floor(q)));
         const float f = frac_of(q);
-        const float4 v = ldtex(row + jj);
         ac += fmaf(f, v.z - v.x, v.x);
         ap += fmaf(f, v.w - v.y, v.y);
+        q += step;
+        base += ld;
     }
     return make_float2(ac, ap);
 }
