@@ -380,6 +380,7 @@ def run_dect(args):
             "config": {"workload": "fan beam 512x512, 720 views x 1024 bins, 40 objects, I0 2e5, "
                                    "UDM1-PCG1 x 100 iterations + initial image, B slices batched per launch",
                        "batch_per_gpu": B, "l2": "flushed between steps (512 MB write)", "storage": args.storage,
+                       "bp_view_groups": st0["bp_view_groups"],
                        "plain_slices_per_s": (ws * B / (plain_ms / 1e3)) if plain_ms else None,
                        "batched_over_plain": (value / (ws * B / (plain_ms / 1e3))) if plain_ms else None,
                        "pe_gate": gate, "phases": phases},

@@ -210,12 +210,14 @@ typedef struct {
     int32_t init_pcg_iters;      /* initialisation: CG iterations (10) */
     int32_t precondition;        /* 1: circulant preconditioner, 0: plain CG */
     int32_t use_graph;           /* 1: capture one iteration as a CUDA graph */
-    int32_t bp_view_groups;      /* backprojector view groups per image tile, 1..16;
-                                    0 = chosen from the occupancy so that the grid fills the GPU. It fixes
-                                    the order of a pixel's partial sums: results are bitwise reproducible
-                                    for a fixed value, and a slice solved alone or in a batch gives
-                                    identical bits when the value is the same (it is the one
-                                    launch-dependent choice). */
+    int32_t bp_view_groups;      /* backprojector view groups per image tile, 1..16; 0 = autotuned:
+                                    dect_admm_create times the backprojector on this batch for a few
+                                    candidates (memory permitting) and keeps the fastest (reported in
+                                    dect_stats). It fixes the order of a pixel's partial sums: results
+                                    are bitwise reproducible for a fixed value, and a slice solved alone
+                                    or in a batch gives identical bits when the value is the same (it is
+                                    the one launch-dependent choice; an autotuned value can differ from
+                                    run to run). */
     int32_t storage;             /* dect_storage (DECT_STORE_F32): 16-bit formats halve the bytes of the
                                     sinogram vectors and textures at the cost of their precision */
 } dect_params;
@@ -272,6 +274,7 @@ typedef struct {
     int64_t count_R, count_RT;   /* projector applications per basis (Table 1) */
     int64_t count_f;             /* forward-model evaluations per ray */
     int64_t count_launches;      /* kernels launched by this solver so far (all slices) */
+    int32_t bp_view_groups;      /* backprojector view groups per tile in use (fixed or autotuned) */
 } dect_stats;
 dect_status dect_admm_stats(dect_admm* a, int32_t slice, dect_stats* out, void* stream);
 

@@ -4,6 +4,7 @@
 // kernels; the host only enqueues them (or replays them as one CUDA graph).
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <string>
@@ -394,6 +395,7 @@ struct dect_admm {
     SliceDesc* ds = nullptr;
     MapBuf rays, pix, tx, ty, rows, cols, sweep;
     int sweep_C = 1;                 // CTA groups (partial images) per backprojector tile
+    int sweep_groups_in_use = 1;     // view groups per tile (sweep_C CTAs of the kernel's groups each)
     float2* bp_partial = nullptr;    // [sweep_C][n_img] partial images of the backprojector
     int64_t n_img = 0, n_sino = 0, n_tx = 0, n_ty = 0, n_fft = 0, n_h = 0, n_stage = 0;
     int max_px = 0, max_py = 0;
@@ -632,6 +634,60 @@ static dect_status enq_initialize(dect_admm* A, cudaStream_t st) {
 
 // ---- creation ------------------------------------------------------------------------------------
 
+// Sweep block map for C CTA groups per tile (prefix over slices)
+static void sweep_prefix(const dect_admm* A, int C, std::vector<int>& h) {
+    h.assign(1, 0);
+    for (int b = 0; b < A->B; ++b) h.push_back(h.back() + sweep_tiles(A->hs[b].g.nx, A->hs[b].g.ny) * C);
+}
+
+// Times the backprojector sweep on this batch for each candidate C (on a zero sinogram; the work does
+// not depend on the values), keeps the fastest (a smaller C unless a larger one is 1% faster) and
+// shrinks the partial-image buffer to it. bp_partial is allocated for the largest candidate.
+static cudaError_t autotune_sweep(dect_admm* A, const std::vector<int>& cands) {
+    cudaStream_t st = A->cap;
+    cudaError_t e = cudaMemsetAsync(A->q, 0, sino_bytes(A->prec) * (size_t)A->n_sino, st);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (e == cudaSuccess) e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    int best = cands[0];
+    float best_ms = 0.f;
+    std::vector<int> h;
+    for (size_t k = 0; k < cands.size() && e == cudaSuccess; ++k) {
+        const int C = cands[k];
+        sweep_prefix(A, C, h);
+        e = cudaMemcpy(A->sweep.d, h.data(), sizeof(int) * h.size(), cudaMemcpyHostToDevice);
+        const BlockMap m{A->sweep.d, A->B};
+        for (int w = 0; w < 2 && e == cudaSuccess; ++w) {  // warm-up
+            launch_bp_sweep(A->ds, m, h.back(), C, A->q, A->bp_partial, A->n_img, A->prec, st);
+            e = cudaGetLastError();
+        }
+        if (e == cudaSuccess) e = cudaEventRecord(e0, st);
+        for (int r = 0; r < 3 && e == cudaSuccess; ++r) {
+            launch_bp_sweep(A->ds, m, h.back(), C, A->q, A->bp_partial, A->n_img, A->prec, st);
+            e = cudaGetLastError();
+        }
+        if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        float ms = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (e == cudaSuccess && (k == 0 || ms < 0.99f * best_ms || (ms <= best_ms && C < best))) {
+            best = C;
+            best_ms = ms;
+        }
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (e != cudaSuccess) return e;
+    A->sweep_C = best;
+    sweep_prefix(A, best, A->sweep.h);
+    A->sweep.total = A->sweep.h.back();
+    e = cudaMemcpy(A->sweep.d, A->sweep.h.data(), sizeof(int) * A->sweep.h.size(), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return e;
+    cudaFree(A->bp_partial);
+    A->bp_partial = nullptr;
+    return dalloc(&A->bp_partial, (size_t)best * A->n_img);
+}
+
 static dect_status compute_responses(dect_admm* A) {
     cudaStream_t st = A->cap;
     for (int b = 0; b < A->B; ++b) {
@@ -713,10 +769,27 @@ extern "C" dect_status dect_admm_create(dect_geom* const* geoms, int32_t B, cons
     A->has_truth.assign(B, 0);
     A->has_data.assign(B, 0);
     for (auto* m : {&A->rays, &A->pix, &A->tx, &A->ty, &A->rows, &A->cols, &A->sweep}) m->h.assign(1, 0);
+    std::vector<int> tune;  // candidate CTA groups per tile when autotuning (first = the occupancy choice)
     {
         int total = 0;
-        for (int b = 0; b < B; ++b) total += sweep_tiles(geoms[b]->desc.nx, geoms[b]->desc.ny);
-        A->sweep_C = P->bp_view_groups > 0 ? sweep_ctas_for_groups(P->bp_view_groups) : sweep_groups(total);
+        int64_t pix = 0;
+        for (int b = 0; b < B; ++b) {
+            total += sweep_tiles(geoms[b]->desc.nx, geoms[b]->desc.ny);
+            pix += geoms[b]->n_pix();
+        }
+        if (P->bp_view_groups > 0) {
+            A->sweep_C = sweep_ctas_for_groups(P->bp_view_groups);
+        } else {
+            // candidates whose partial images fit in 1/16 of the free memory (and 4 GiB)
+            size_t free_b = 0, total_b = 0;
+            cudaMemGetInfo(&free_b, &total_b);
+            const double budget = std::min(4.0 * (1 << 30), (double)free_b / 16.0);
+            const int first = sweep_groups(total);
+            tune.push_back(first);
+            for (int c : {4, 6, 8, 10, 12, 16})
+                if (c != first && (double)c * pix * sizeof(float2) <= budget) tune.push_back(c);
+            A->sweep_C = *std::max_element(tune.begin(), tune.end());
+        }
     }
     int64_t max_np = 0, max_nr = 0;
     for (int b = 0; b < B; ++b) {
@@ -805,6 +878,13 @@ extern "C" dect_status dect_admm_create(dect_geom* const* geoms, int32_t B, cons
         free_admm(A);
         return e == cudaErrorMemoryAllocation ? DECT_ENOMEM : DECT_ECUDA;
     }
+    if (tune.size() > 1) e = autotune_sweep(A, tune);
+    if (e != cudaSuccess) {
+        dect::set_error(std::string("dect_admm_create (backprojector autotuning): ") + cudaGetErrorString(e));
+        free_admm(A);
+        return e == cudaErrorMemoryAllocation ? DECT_ENOMEM : DECT_ECUDA;
+    }
+    A->sweep_groups_in_use = A->sweep_C * sweep_groups_per_cta();
     dect_status s = compute_responses(A);
     if (s != DECT_OK) {
         free_admm(A);
@@ -1005,5 +1085,6 @@ extern "C" dect_status dect_admm_stats(dect_admm* A, int32_t b, dect_stats* out,
     out->count_RT = A->cRT;
     out->count_f = A->cF;
     out->count_launches = A->cL;
+    out->bp_view_groups = A->sweep_groups_in_use;
     return DECT_OK;
 }

@@ -187,6 +187,7 @@ __global__ void __launch_bounds__(256) k_bp_finalize(const SliceDesc* __restrict
 int sweep_tiles(int nx, int ny) { return ((nx + kSw - 1) / kSw) * ((ny + kSw - 1) / kSw); }
 
 int sweep_ctas_for_groups(int view_groups) { return (view_groups + kSwGroups - 1) / kSwGroups; }
+int sweep_groups_per_cta() { return kSwGroups; }
 
 // CTA groups per tile: the smallest C (up to 8) whose grid of tiles * C blocks fills the resident
 // slots best (each CTA holds kSwGroups view groups; C * kSwGroups view groups per tile in total).

@@ -125,6 +125,7 @@ void launch_project(const SliceDesc* dsl, const BlockMap& map, int nblk, const v
 // backproject_sweep.cu: the solver's backprojector (two kernels: sweep into C partial images, then
 // the fixed-order sum of the partials with the epilogue; partial dots over the `pix` blocks)
 int sweep_ctas_for_groups(int view_groups);
+int sweep_groups_per_cta();
 int sweep_tiles(int nx, int ny);
 int sweep_groups(int tiles);
 void launch_bp_sweep(const SliceDesc* dsl, const BlockMap& smap, int nsweep, int C, const void* sino,

@@ -52,7 +52,8 @@ class Params(ctypes.Structure):
 class Stats(ctypes.Structure):
     _fields_ = [("iteration", ctypes.c_int32), ("rho", ctypes.c_double * 2), ("r_pri", ctypes.c_double * 2),
                 ("r_dual", ctypes.c_double * 2), ("xi_db", ctypes.c_double * 2), ("count_R", ctypes.c_int64),
-                ("count_RT", ctypes.c_int64), ("count_f", ctypes.c_int64), ("count_launches", ctypes.c_int64)]
+                ("count_RT", ctypes.c_int64), ("count_f", ctypes.c_int64), ("count_launches", ctypes.c_int64),
+                ("bp_view_groups", ctypes.c_int32)]
 
 
 # every symbol declared in include/dect.h, with its ctypes signature
@@ -273,7 +274,7 @@ def admm_stats(h, slice_index, stream=None) -> dict:
     _check(lib().dect_admm_stats(h, slice_index, ctypes.byref(s), _stream(stream)))
     return {"iteration": s.iteration, "rho": list(s.rho), "r_pri": list(s.r_pri), "r_dual": list(s.r_dual),
             "xi_db": list(s.xi_db), "count_R": s.count_R, "count_RT": s.count_RT, "count_f": s.count_f,
-            "count_launches": s.count_launches}
+            "count_launches": s.count_launches, "bp_view_groups": s.bp_view_groups}
 
 
 PHASES = ["texture", "project", "backproject", "precond", "udm", "update", "reduce", "bp_finalize"]

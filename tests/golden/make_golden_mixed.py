@@ -43,9 +43,9 @@ def main():
     ap.add_argument("--slices", type=int, default=4)
     ap.add_argument("--iters", type=int, default=100)
     ap.add_argument("--out", default=None)
-    ap.add_argument("--early", type=int, default=0)
+    ap.add_argument("--early", type=int, default=-1)
     args = ap.parse_args()
-    if args.early:
+    if args.early >= 0:
         return early(args)
     args.out = args.out or os.path.join(HERE, "mixed_1024_oracle.json")
     out = {"what": "FP64 oracle, UDM1-PCG1, fan beam 1024x1024, 1440 views, 2048 bins, E_ref 100 keV, kappa 0.25; "

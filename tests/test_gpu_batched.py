@@ -90,6 +90,23 @@ def test_batched_initialisation_matches_single(cuda_dev):
         assert np.array_equal(batched.get(b, dect.X).cpu().numpy(), single.get(0, dect.X).cpu().numpy())
 
 
+def test_autotuned_view_groups_equal_the_fixed_choice(cuda_dev):
+    # the autotuner only picks the backprojector's view-group count: a solver given that count
+    # explicitly reproduces the autotuned run bit for bit
+    from paper_1905_00934_gb300 import dect
+
+    cases = _small_cases()
+    tuned = _solver(cases, cuda_dev, [None] * 3)
+    g = tuned.stats(0)["bp_view_groups"]
+    assert 1 <= g <= 16
+    fixed = _solver(cases, cuda_dev, [None] * 3, bp_view_groups=g)
+    assert fixed.stats(0)["bp_view_groups"] == g
+    tuned.reconstruct(3)
+    fixed.reconstruct(3)
+    for b in range(3):
+        assert np.array_equal(tuned.get(b, dect.X).cpu().numpy(), fixed.get(b, dect.X).cpu().numpy())
+
+
 @pytest.mark.slow
 def test_uneven_64_slice_batch_full_size(cuda_dev):
     # the batched workload at full size: 64 seeded slices, N 256..1024, 360..1440 views,

@@ -75,27 +75,50 @@ def _mixed_solver(cuda_dev, slices, storage, with_truth):
     return sol
 
 
-@pytest.mark.skipif(not os.path.exists(GOLDEN_EARLY), reason="early-iteration oracle pixels for 1024^2 not generated")
-def test_full_size_subset_early_iterations_float32(cuda_dev):
-    # pixel by pixel against the oracle after the initial image and the first iterations, before
-    # float32 rounding of the per-ray decisions can accumulate. The initial image's 10 float32 PCG
-    # iterations on (R^T R + I) x = R^T a_c already amplify the rounding of R / R^T: the full image
-    # differs from the FP64 oracle's by 7e-5 relative, the sampled pixels by 2e-4 (started from the
-    # oracle's own initial image the GPU agrees to 3e-8), so the bar is 5e-4.
+@pytest.mark.skipif(not os.path.exists(GOLDEN_EARLY), reason="initial-image oracle pixels for 1024^2 not generated")
+def test_full_size_initial_image_float32(cuda_dev):
+    # The initial image's 10 float32 PCG iterations on (R^T R + I) x = R^T a_c amplify the rounding of
+    # R / R^T: the full image differs from the FP64 oracle's by 7e-5 relative, the sampled pixels by
+    # 2e-4, so the bar is 5e-4 (iterations from a common starting image are held below).
     from paper_1905_00934_gb300 import dect
 
     ref = json.load(open(GOLDEN_EARLY))
     sl = ref["slices"]
     sol = _mixed_solver(cuda_dev, sl, 0, False)
     sol.reconstruct(0)
-    for it in range(ref["iterations"] + 1):
-        if it:
-            sol.step(1)
-        for b, s in enumerate(sl):
-            x = sol.get(b, dect.X).cpu().numpy().reshape(2, -1)
-            idx = np.array(s["pixels"])
-            e_c, e_p = rel_l2(x[0, idx], s["x"][it][0]), rel_l2(x[1, idx], s["x"][it][1])
-            assert e_c <= 5e-4 and e_p <= 5e-4, (it, b, e_c, e_p)
+    for b, s in enumerate(sl):
+        x = sol.get(b, dect.X).cpu().numpy().reshape(2, -1)
+        idx = np.array(s["pixels"])
+        e_c, e_p = rel_l2(x[0, idx], s["x"][0][0]), rel_l2(x[1, idx], s["x"][0][1])
+        assert e_c <= 5e-4 and e_p <= 5e-4, (b, e_c, e_p)
+
+
+@pytest.mark.slow
+def test_full_size_iterations_from_the_oracle_initial_image(cuda_dev):
+    # 1024 x 1024, 1440 views, 2048 bins: the oracle's initial image and 3 ADMM iterations (computed
+    # here, about a minute on the host cores), the GPU started from that image; the whole images
+    # agree to float32 level (measured 2e-6 after 3 iterations) until float32 rounding flips a
+    # per-ray LM decision, which happens later.
+    from paper_1905_00934_gb300 import Geometry, Solver, Spectra, dect
+    from synth.workloads import BAGGAGE_KAPPA, MIXED_SEED_BASE, baggage_fan_case
+
+    c = baggage_fan_case(slice_index=MIXED_SEED_BASE, n=1024, n_views=1440, n_bins=2048)
+    for k in ("m_h", "m_l", "w_h", "w_l"):
+        c[k] = _r32(c[k])
+    prob = oadmm.Problem(c["geom"], c["spectra"], c["m_h"], c["m_l"], c["w_h"], c["w_l"],
+                         oadmm.Params(kappa=BAGGAGE_KAPPA))
+    x0 = _r32(np.stack(oadmm.initial_image(prob)))
+    st = oadmm.state_from_image(prob, x0[0], x0[1])
+    geo = Geometry(c["geom"])
+    sol = Solver([geo], Spectra.from_tables(c["spectra"]), kappa=BAGGAGE_KAPPA)
+    sol.set_data(0, *[to_dev(c[k], cuda_dev) for k in ("m_h", "m_l", "w_h", "w_l")], to_dev(x0, cuda_dev))
+    sol.reconstruct(0)
+    for it in range(1, 4):
+        st = oadmm.admm_iteration(prob, st)
+        sol.step(1)
+        x = sol.get(0, dect.X).cpu().numpy().astype(np.float64)
+        e_c, e_p = rel_l2(x[0], st.x[0]), rel_l2(x[1], st.x[1])
+        assert e_c <= 5e-5 and e_p <= 5e-5, (it, e_c, e_p)
 
 
 # After 100 iterations float32 rounding has flipped the accept/reject decision of Eq. 13's LM step
