@@ -137,10 +137,10 @@ def joseph_weight_count(g) -> int:
     return total
 
 
-# dram bytes per launch of the backprojector sweep at the bench workload (8 slices), from one ncu
-# capture of this kernel (profiles/k_bp_sweep_512x720x1024_b8.txt); None when not measured for the
-# current kernel
-SWEEP_TRAFFIC_B8 = 163.1e6
+# dram bytes per launch of the backprojector sweep at the bench workload (8 slices) and the view-group
+# count it was captured with (profiles/k_bp_sweep_512x720x1024.txt); reported only when the solver
+# runs that count, since the partial images it writes scale with it
+SWEEP_TRAFFIC_B8 = (217.4e6, 8)
 
 
 # ------------------------------------------------------------------------------------------------
@@ -364,7 +364,8 @@ def run_dect(args):
         tf = alg_flops[top] / (avg_ms / 1e3) / 1e12
         roof = {"kernel": top, "bound": "alu", "achieved": tf, "peak": fp32_peak, "unit": "TFLOP/s",
                 "frac": tf / fp32_peak,
-                "traffic": SWEEP_TRAFFIC_B8 if (top == "backproject" and B == 8) else None,
+                "traffic": SWEEP_TRAFFIC_B8[0] if (top == "backproject" and B == 8
+                                                    and st0["bp_view_groups"] == SWEEP_TRAFFIC_B8[1]) else None,
                 "peak_kind": f"derived: {n_sm} SMs x 128 FP32 lanes x 2 flop x max SM clock",
                 "avg_launch_ms": avg_ms, "algorithmic_flops_per_launch": alg_flops[top],
                 "weights_per_slice_channel": nnz, "hbm": hbm}
