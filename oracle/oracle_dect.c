@@ -124,10 +124,13 @@ static double og_joseph(const og_geom* g, int v, int k, const double* img, doubl
     }
 }
 
+/* Loops over fewer rays than this run on one thread: thread start-up would dominate them. */
+#define OG_PAR_MIN 8192
+
 /* sino[v][k] = (R img)[v][k] for an image [ny][nx]. */
 void og_project(const og_geom* g, const double* img, double* sino) {
     const long nr = (long)g->nv * g->nb;
-#pragma omp parallel for schedule(dynamic, 64)
+#pragma omp parallel for schedule(dynamic, 64) if (nr >= OG_PAR_MIN)
     for (long r = 0; r < nr; r++) {
         int v = (int)(r / g->nb), k = (int)(r % g->nb);
         sino[r] = og_joseph(g, v, k, img, NULL, 0.0, 0);
@@ -148,7 +151,7 @@ void og_backproject(const og_geom* g, const double* sino, double* img) {
     const size_t np = (size_t)g->nx * g->ny;
     int nt = og_num_threads();
     double* part = (double*)calloc((size_t)nt * np, sizeof(double));
-#pragma omp parallel
+#pragma omp parallel if ((long)g->nv * g->nb >= OG_PAR_MIN)
     {
         int t = 0;
 #ifdef _OPENMP
@@ -227,7 +230,7 @@ void og_forward_model(int ne, const double* S_h, const double* S_l, const double
     double* sh = og_normalised(S_h, ne);
     double* sl = og_normalised(S_l, ne);
     og_spec sp = {ne, sh, sl, fkn, fp};
-#pragma omp parallel for schedule(static)
+#pragma omp parallel for schedule(static) if (n >= OG_PAR_MIN)
     for (long r = 0; r < n; r++) og_fwd(&sp, ac[r], ap[r], fh + r, fl + r, jac ? jac + 4 * r : NULL);
     free(sh);
     free(sl);
@@ -258,7 +261,7 @@ void og_udm(int ne, const double* S_h, const double* S_l, const double* fkn, con
     double* sh = og_normalised(S_h, ne);
     double* sl = og_normalised(S_l, ne);
     og_spec sp = {ne, sh, sl, fkn, fp};
-#pragma omp parallel for schedule(static)
+#pragma omp parallel for schedule(static) if (n >= OG_PAR_MIN)
     for (long r = 0; r < n; r++) {
         double a0 = ac[r], a1 = ap[r], m = mu[r];
         uint8_t st = 0;
@@ -304,7 +307,7 @@ void og_udm_cost(int ne, const double* S_h, const double* S_l, const double* fkn
     double* sh = og_normalised(S_h, ne);
     double* sl = og_normalised(S_l, ne);
     og_spec sp = {ne, sh, sl, fkn, fp};
-#pragma omp parallel for schedule(static)
+#pragma omp parallel for schedule(static) if (n >= OG_PAR_MIN)
     for (long r = 0; r < n; r++) {
         double fh, fl;
         og_fwd(&sp, ac[r], ap[r], &fh, &fl, NULL);
