@@ -198,7 +198,23 @@ dect_status dect_forward_model_vjp(const dect_spectra* s, int64_t n_rays, int32_
  *  5. rho by residual balancing (Sec. 3.2): r_pri = ||[a;y;z] - [R;D;I]x||,
  *     r_dual = rho ||[a;y;z] - [a;y;z]_prev||; if r_pri > mu_b r_dual then
  *     rho *= tau, u /= tau; if r_dual > mu_b r_pri then rho /= tau, u *= tau.
- * All scalars (CG alpha/beta, rho, residuals) stay on the device. */
+ * All scalars (CG alpha/beta, rho, residuals) stay on the device.
+ *
+ * With scheme = DECT_SCHEME_LM_CG the iteration is instead the comparison scheme
+ * LM(m) x CG(n) of Sec. 3.2 (Eq. 6-11; Table 1's first row), float32 storage only:
+ *  1. Eq. 7 then Eq. 8: m Levenberg-Marquardt steps on x_c (x_p fixed), then on
+ *     x_p (the new x_c fixed). A step models the data term by Gauss-Newton around
+ *     the current projections and adds the basis' augmented-Lagrangian term
+ *     rho/2 ||[y; z] - [D; I] x + u||^2; its linear system, with the data
+ *     curvature scaled by (1 + mu), is solved by n plain CG iterations from 0;
+ *     the step is kept iff the subproblem objective decreases (mu / 10), else
+ *     dropped (mu * 10); one mu per slice and basis, mu0 = lm_mu0. Per step:
+ *     n R and n + 1 R^T on the basis (R d is carried through CG, so the trial
+ *     point needs no projection; Table 1 counts n + 1 R), 2 f-evaluations.
+ *  2-4. Eq. 9-11 without an a-block; rho by residual balancing on [y; z].
+ * m_udm and n_pcg give m and n. The initial image is the same as above. */
+enum dect_scheme { DECT_SCHEME_UDM_PCG = 0, DECT_SCHEME_LM_CG = 1 };
+
 typedef struct {
     double lambda_c, lambda_p;   /* TV weights (paper: 1e-5) */
     double rho0_c, rho0_p;       /* initial penalties (paper: 1e-3) */
@@ -220,6 +236,7 @@ typedef struct {
                                     run to run). */
     int32_t storage;             /* dect_storage (DECT_STORE_F32): 16-bit formats halve the bytes of the
                                     sinogram vectors and textures at the cost of their precision */
+    int32_t scheme;              /* dect_scheme (DECT_SCHEME_UDM_PCG): the splitting one iteration runs */
 } dect_params;
 
 /* Fills *p with the paper's values and the defaults above. */

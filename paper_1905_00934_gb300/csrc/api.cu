@@ -377,6 +377,7 @@ extern "C" void dect_params_default(dect_params* p) {
     p->use_graph = 1;
     p->bp_view_groups = 0;
     p->storage = DECT_STORE_F32;
+    p->scheme = DECT_SCHEME_UDM_PCG;
 }
 
 struct MapBuf {
@@ -409,6 +410,17 @@ struct dect_admm {
     uint8_t* status = nullptr;
     SliceScalars* sc = nullptr;
     double *part_udm = nullptr, *part_img = nullptr, *part_rs = nullptr, *part_pap = nullptr, *part_xi = nullptr;
+    // comparison scheme LM(m) x CG(n): per-slice scalars, single-channel CG vectors (d, r, p, A p), per-ray
+    // Gauss-Newton weights (e, g), spectral sums at x (s0), R p (q1), carried R d, single-channel textures
+    // and partial images, one partial slot per pixel / ray block
+    LmScalars* ls = nullptr;
+    float* lm_scale = nullptr;
+    float *lm_d = nullptr, *lm_r = nullptr, *lm_p = nullptr, *lm_Ap = nullptr;
+    float *lm_e = nullptr, *lm_g = nullptr, *lm_q = nullptr, *lm_Rd = nullptr;
+    float2* lm_s0 = nullptr;
+    float2 *tx1 = nullptr, *ty1 = nullptr;
+    float* bp_partial1 = nullptr;
+    double *part_lm_pix = nullptr, *part_lm_ray = nullptr;
     int* d_has_x0 = nullptr;
     std::vector<int> has_x0, has_truth, has_data;
     const float2* tw = nullptr;
@@ -417,7 +429,7 @@ struct dect_admm {
     cudaStream_t cap = nullptr;
     cudaGraphExec_t gexec = nullptr;
     int64_t cR = 0, cRT = 0, cF = 0, cL = 0;
-    int64_t launches_per_iter = 0;
+    int64_t launches_per_iter = 0, R_per_iter = 0, RT_per_iter = 0, f_per_iter = 0;
     // profiling: an event pair around every kernel group of the captured iteration
     bool prof_on = false;
     int prof_n = 0;
@@ -451,7 +463,9 @@ static void free_admm(dect_admm* A) {
                     A->bp_partial, A->x, A->r, A->s,
                     A->p, A->Ap, A->z, A->uz, A->x0, A->truth, A->Rx, A->a, A->ua, A->q, A->Z, A->y, A->uy,
                     A->meas, A->txb, A->tyb, A->mu, A->H, A->Hn, A->stage, A->status, A->sc, A->part_udm,
-                    A->part_img, A->part_rs, A->part_pap, A->part_xi, A->d_has_x0};
+                    A->part_img, A->part_rs, A->part_pap, A->part_xi, A->d_has_x0, A->ls, A->lm_scale, A->lm_d,
+                    A->lm_r, A->lm_p, A->lm_Ap, A->lm_e, A->lm_g, A->lm_q, A->lm_Rd, A->lm_s0, A->tx1, A->ty1,
+                    A->bp_partial1, A->part_lm_pix, A->part_lm_ray};
     for (void* q : ptrs) cudaFree(q);
     if (A->gexec) cudaGraphExecDestroy(A->gexec);
     if (A->pgexec) cudaGraphExecDestroy(A->pgexec);
@@ -550,8 +564,116 @@ static void enq_pcg(dect_admm* A, int n, bool with_grad, const float* H, cudaStr
     }
 }
 
+// One LM step on basis b for every slice (Eq. 7 for b = 0, Eq. 8 for b = 1): Gauss-Newton weights, the
+// gradient (one single-channel R^T), n CG iterations (one R and one R^T each; R d carried), the trial's
+// objective change and the accept / damping decision, then x_b and (R x)_b move on accepted slices.
+static void enq_lm_step(dect_admm* A, int b, cudaStream_t st) {
+    const int B = A->B, n = A->P.n_pcg;
+    const BlockMap pix = A->pix.map(B), rays = A->rays.map(B);
+    BpEpilogue ep{};
+    ep.x = A->x;
+    ep.y = A->y;
+    ep.uy = A->uy;
+    ep.z = A->z;
+    ep.uz = A->uz;
+    pb(A, st);
+    launch_lm_rays(A->ds, rays, A->rays.total, A->spec->dev(), A->meas, (const float2*)A->Rx, b, A->lm_e, A->lm_g,
+                   A->lm_s0, A->lm_Rd, st);
+    pe(A, DECT_PHASE_UDM, 1, st);
+    pb(A, st);
+    launch_bp_sweep1(A->ds, A->sweep.map(B), A->sweep.total, A->sweep_C, A->lm_e, nullptr, nullptr, A->bp_partial1,
+                     A->n_img, st);
+    pe(A, DECT_PHASE_BACKPROJECT, 1, st);
+    pb(A, st);
+    launch_lm_grad(A->ds, pix, A->pix.total, A->sweep_C, A->bp_partial1, A->n_img, b, A->sc, ep, A->lm_r, A->lm_p,
+                   A->lm_d, A->part_lm_pix, st);
+    pe(A, DECT_PHASE_BP_FINALIZE, 1, st);
+    pb(A, st);
+    launch_lm_rr(A->part_lm_pix, A->pix.d, A->ls, B, 1, st);
+    pe(A, DECT_PHASE_REDUCE, 1, st);
+    if (A->counting) A->cRT += 1;
+    for (int k = 0; k < n; ++k) {
+        const int last = k == n - 1;
+        pb(A, st);
+        launch_textures1(A->ds, A->tx.map(B), A->tx.total, A->ty.map(B), A->ty.total, A->lm_p, A->tx1, A->ty1, st);
+        pe(A, DECT_PHASE_TEXTURE, 2, st);
+        pb(A, st);
+        launch_project1(A->ds, rays, A->rays.total, A->tx1, A->ty1, A->lm_q, st);
+        pe(A, DECT_PHASE_PROJECT, 1, st);
+        pb(A, st);
+        launch_bp_sweep1(A->ds, A->sweep.map(B), A->sweep.total, A->sweep_C, A->lm_q, A->lm_g, A->lm_scale,
+                         A->bp_partial1, A->n_img, st);
+        pe(A, DECT_PHASE_BACKPROJECT, 1, st);
+        pb(A, st);
+        launch_lm_ap(A->ds, pix, A->pix.total, A->sweep_C, A->bp_partial1, A->n_img, b, A->sc, A->lm_p, A->lm_Ap,
+                     A->part_lm_pix, st);
+        pe(A, DECT_PHASE_BP_FINALIZE, 1, st);
+        pb(A, st);
+        launch_lm_alpha(A->part_lm_pix, A->pix.d, A->ls, B, st);
+        pe(A, DECT_PHASE_REDUCE, 1, st);
+        pb(A, st);
+        launch_lm_cg(A->ds, pix, A->pix.total, rays, A->rays.total, A->ls, A->lm_d, A->lm_p, A->lm_r, A->lm_Ap,
+                     A->lm_Rd, A->lm_q, last, A->part_lm_pix, st);
+        pe(A, DECT_PHASE_UPDATE, 1, st);
+        if (A->counting) {
+            A->cR += 1;
+            A->cRT += 1;
+        }
+        if (!last) {
+            pb(A, st);
+            launch_lm_rr(A->part_lm_pix, A->pix.d, A->ls, B, 0, st);
+            pe(A, DECT_PHASE_REDUCE, 1, st);
+            pb(A, st);
+            launch_lm_p(A->ds, pix, A->pix.total, A->ls, A->lm_r, A->lm_p, st);
+            pe(A, DECT_PHASE_UPDATE, 1, st);
+        }
+    }
+    pb(A, st);
+    launch_lm_trial(A->ds, rays, A->rays.total, A->spec->dev(), A->meas, (const float2*)A->Rx, b, A->lm_Rd, A->lm_s0,
+                    A->part_lm_ray, st);
+    pe(A, DECT_PHASE_UDM, 1, st);
+    pb(A, st);
+    launch_lm_al_delta(A->ds, pix, A->pix.total, b, A->sc, ep, A->lm_d, A->part_lm_pix, st);
+    pe(A, DECT_PHASE_UPDATE, 1, st);
+    pb(A, st);
+    launch_lm_decide(A->part_lm_ray, A->rays.d, A->part_lm_pix, A->pix.d, A->ls, A->lm_scale, B, b, st);
+    pe(A, DECT_PHASE_REDUCE, 1, st);
+    pb(A, st);
+    launch_lm_accept(A->ds, pix, A->pix.total, rays, A->rays.total, A->ls, b, A->x, A->lm_d, (float2*)A->Rx, A->lm_Rd,
+                     st);
+    pe(A, DECT_PHASE_UPDATE, 1, st);
+    if (A->counting) A->cF += 2;
+}
+
+// One ADMM iteration of the comparison scheme: m LM steps on x_c, then on x_p (Eq. 7-8), then Eq. 9-11
+// (no a-block: its residual slots stay zero) and residual-balancing rho.
+static void enq_lmcg_iteration(dect_admm* A, cudaStream_t st) {
+    const int B = A->B;
+    for (int b = 0; b < 2; ++b) {
+        pb(A, st);
+        launch_lm_begin(A->ls, A->lm_scale, B, b, st);
+        pe(A, DECT_PHASE_REDUCE, 1, st);
+        for (int it = 0; it < A->P.m_udm; ++it) enq_lm_step(A, b, st);
+    }
+    pb(A, st);
+    launch_image_update(A->ds, A->pix.map(B), A->pix.total, A->sc, A->P.lambda_c, A->P.lambda_p, A->x, A->y, A->uy,
+                        A->z, A->uz, A->part_img, st);
+    pe(A, DECT_PHASE_UPDATE, 1, st);
+    pb(A, st);
+    launch_rho_update(A->part_udm, A->rays.d, A->part_img, A->pix.d, A->sc, B, A->P.rho_mu, A->P.rho_tau, st);
+    pe(A, DECT_PHASE_REDUCE, 1, st);
+    pb(A, st);
+    launch_dual_rescale(A->ds, A->pix.map(B), A->pix.total, A->rays.map(B), A->rays.total, A->sc, A->uy, A->uz, A->ua,
+                        A->prec, st);
+    pe(A, DECT_PHASE_UPDATE, 1, st);
+}
+
 static void enq_iteration(dect_admm* A, cudaStream_t st) {
     const int B = A->B;
+    if (A->P.scheme == DECT_SCHEME_LM_CG) {
+        enq_lmcg_iteration(A, st);
+        return;
+    }
     enq_pcg(A, A->P.n_pcg, true, A->H, st);
     pb(A, st);
     launch_udm_admm(A->ds, A->rays.map(B), A->rays.total, A->spec->dev(), A->meas, A->Rx, A->ua, A->a, A->mu,
@@ -586,6 +708,9 @@ static dect_status capture_iteration(dect_admm* A, bool profile, cudaGraphExec_t
         const int64_t r0 = A->cR, rt0 = A->cRT, f0 = A->cF;
         enq_iteration(A, A->cap);
         A->launches_per_iter = A->cL - l0;
+        A->R_per_iter = A->cR - r0;
+        A->RT_per_iter = A->cRT - rt0;
+        A->f_per_iter = A->cF - f0;
         A->cL = l0;
         A->cR = r0;
         A->cRT = rt0;
@@ -627,6 +752,7 @@ static dect_status enq_initialize(dect_admm* A, cudaStream_t st) {
     launch_state_from_image(A->ds, A->pix.map(B), A->pix.total, A->rays.map(B), A->rays.total, A->x, A->y, A->uy,
                             A->z, A->uz, A->Rx, A->a, A->ua, A->mu, (float)A->P.lm_mu0, A->prec, st);
     launch_reset_scalars(A->sc, B, A->P.rho0_c, A->P.rho0_p, st);
+    if (A->P.scheme == DECT_SCHEME_LM_CG) launch_lm_reset(A->ls, B, A->P.lm_mu0, st);
     CUDA_TRY(cudaGetLastError());
     A->initialized = true;
     return DECT_OK;
@@ -741,6 +867,10 @@ extern "C" dect_status dect_admm_create(dect_geom* const* geoms, int32_t B, cons
     if (B < 1 || B > 4096) DECT_FAIL(DECT_EINVAL, "dect_admm_create: n_slices must be in [1, 4096]");
     if (P->storage != DECT_STORE_F32 && P->storage != DECT_STORE_F16 && P->storage != DECT_STORE_BF16)
         DECT_FAIL(DECT_EINVAL, "dect_admm_create: storage must be DECT_STORE_F32, F16 or BF16");
+    if (P->scheme != DECT_SCHEME_UDM_PCG && P->scheme != DECT_SCHEME_LM_CG)
+        DECT_FAIL(DECT_EINVAL, "dect_admm_create: scheme must be DECT_SCHEME_UDM_PCG or DECT_SCHEME_LM_CG");
+    if (P->scheme == DECT_SCHEME_LM_CG && P->storage != DECT_STORE_F32)
+        DECT_FAIL(DECT_EUNSUPPORTED, "dect_admm_create: the LM x CG scheme runs with float32 storage only");
     if (P->bp_view_groups < 0 || P->bp_view_groups > 16)
         DECT_FAIL(DECT_EINVAL, "dect_admm_create: bp_view_groups must be in [0, 16]");
     if (P->m_udm < 1 || P->n_pcg < 1 || P->m_udm > 64 || P->n_pcg > 64)
@@ -855,6 +985,15 @@ extern "C" dect_status dect_admm_create(dect_geom* const* geoms, int32_t B, cons
     ALLOC(A->stage, A->n_stage);
     ALLOC(A->sc, B);
     ALLOC(A->d_has_x0, B);
+    if (P->scheme == DECT_SCHEME_LM_CG) {
+        ALLOC(A->ls, B);
+        ALLOC(A->lm_scale, B);
+        for (float** pp : {&A->lm_d, &A->lm_r, &A->lm_p, &A->lm_Ap}) ALLOC(*pp, A->n_img);
+        for (float** pp : {&A->lm_e, &A->lm_g, &A->lm_q, &A->lm_Rd}) ALLOC(*pp, A->n_sino);
+        ALLOC(A->lm_s0, A->n_sino);
+        ALLOC(A->tx1, A->n_tx);
+        ALLOC(A->ty1, A->n_ty);
+    }
 #undef ALLOC
     const int np_blk = A->pix.h.back(), nr_blk = A->rays.h.back();
     cudaError_t e = dalloc(&A->part_udm, 4 * (size_t)nr_blk);
@@ -885,6 +1024,18 @@ extern "C" dect_status dect_admm_create(dect_geom* const* geoms, int32_t B, cons
         return e == cudaErrorMemoryAllocation ? DECT_ENOMEM : DECT_ECUDA;
     }
     A->sweep_groups_in_use = A->sweep_C * sweep_groups_per_cta();
+    if (P->scheme == DECT_SCHEME_LM_CG) {
+        // the comparison scheme has no a-block: its residual slots stay zero for the rho update
+        e = cudaMemset(A->part_udm, 0, sizeof(double) * 4 * (size_t)A->rays.h.back());
+        if (e == cudaSuccess) e = dalloc(&A->part_lm_pix, (size_t)A->pix.h.back());
+        if (e == cudaSuccess) e = dalloc(&A->part_lm_ray, (size_t)A->rays.h.back());
+        if (e == cudaSuccess) e = dalloc(&A->bp_partial1, (size_t)A->sweep_C * A->n_img);
+        if (e != cudaSuccess) {
+            dect::set_error(std::string("dect_admm_create: ") + cudaGetErrorString(e));
+            free_admm(A);
+            return e == cudaErrorMemoryAllocation ? DECT_ENOMEM : DECT_ECUDA;
+        }
+    }
     dect_status s = compute_responses(A);
     if (s != DECT_OK) {
         free_admm(A);
@@ -948,10 +1099,11 @@ extern "C" dect_status dect_admm_set_truth(dect_admm* A, int32_t b, const float*
     return DECT_OK;
 }
 
+// counters of `iters` replays of the captured iteration (its own counts, taken at capture)
 static void count_iterations(dect_admm* A, int iters) {
-    A->cR += (int64_t)iters * 2 * A->P.n_pcg;
-    A->cRT += (int64_t)iters * 2 * (A->P.n_pcg + 1);
-    A->cF += (int64_t)iters * 4 * A->P.m_udm;
+    A->cR += (int64_t)iters * A->R_per_iter;
+    A->cRT += (int64_t)iters * A->RT_per_iter;
+    A->cF += (int64_t)iters * A->f_per_iter;
     A->cL += (int64_t)iters * A->launches_per_iter;
 }
 

@@ -23,6 +23,8 @@
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
+#include <type_traits>
+
 #include "bp_epilogue.cuh"
 #include "dect_internal.cuh"
 #include "prec.cuh"
@@ -36,12 +38,19 @@ constexpr int kSwWarps = 2 * kSwGroups;  // one warp per view group and ray axis
 constexpr int kSwRows = kSw + 2;  // accumulator rows -1 .. 32 (the two halo rows are discarded)
 constexpr int kSwUnroll = 8;
 
-template <class S2>
+// NCH = 2: sinogram S2 pairs {c, p}, float2 accumulators and partial images. NCH = 1: float sinogram,
+// float accumulators (half the shared-memory traffic), optionally multiplied per ray by rw[ray] and per
+// slice by scale[slice] as the rays are staged (the weighted R^T of a Gauss-Newton operator).
+template <class S2, int NCH>
 __global__ void __launch_bounds__(32 * kSwWarps) k_bp_sweep(const SliceDesc* __restrict__ dsl, BlockMap map, int C,
-                                                            const S2* __restrict__ sino, float2* __restrict__ partial,
-                                                            int64_t stride) {
+                                                            const S2* __restrict__ sino,
+                                                            typename std::conditional<NCH == 2, float2, float>::type*
+                                                                __restrict__ partial,
+                                                            int64_t stride, const float* __restrict__ rw,
+                                                            const float* __restrict__ scale) {
+    using Acc = typename std::conditional<NCH == 2, float2, float>::type;
     // [warp][across index + 1][lane]: [row][column] for axis 0, [column][row] for axis 1
-    __shared__ float2 acc[kSwWarps][kSwRows][kSw];
+    __shared__ Acc acc[kSwWarps][kSwRows][kSw];
     __shared__ int4 st_ray[kSwWarps][32];  // {position lo, position hi, slope, w s_c}
     __shared__ float st_wp[kSwWarps][32];  // w s_p
     int local;
@@ -54,7 +63,7 @@ __global__ void __launch_bounds__(32 * kSwWarps) k_bp_sweep(const SliceDesc* __r
     const int ti = (tile % tiles_x) * kSw, tj = (tile / tiles_x) * kSw;
     const int w = threadIdx.x / 32, lane = threadIdx.x % 32;
     const bool my_axis = w & 1;
-    for (int r = 0; r < kSwRows; ++r) acc[w][r][lane] = make_float2(0.f, 0.f);
+    for (int r = 0; r < kSwRows; ++r) acc[w][r][lane] = Acc{};
     const int G = C * kSwGroups, grp = c * kSwGroups + (w >> 1);
     // rays with a weight at the tile's in-image pixels pass within one pixel of their centres:
     // columns ti .. ie, rows tj .. je, widened by one pixel (the rectangle stays inside the image's
@@ -87,11 +96,18 @@ __global__ void __launch_bounds__(32 * kSwWarps) k_bp_sweep(const SliceDesc* __r
         const int k = k0 + lane;
         have = v < g.nv && k <= khi;
         if (have) {
-            P = __ldg(g.rays + (size_t)v * g.nb + k);
-            sv = ldg2(sn + (size_t)v * g.nb + k);
+            const size_t e = (size_t)v * g.nb + k;
+            P = __ldg(g.rays + e);
+            if constexpr (NCH == 2) {
+                sv = ldg2(sn + e);
+            } else {
+                sv.x = __ldg(sn + e);
+                if (rw) sv.x *= __ldg(rw + d.sino_off + e);
+            }
         }
     };
     fetch();
+    const float sscale = (NCH == 1 && scale) ? __ldg(scale + s) : 1.0f;
     while (v < g.nv) {
         // stage this warp's rays of the fetched chunk, compacted in bin order
         const bool mine = have && ray_axis(P) == my_axis;
@@ -99,7 +115,7 @@ __global__ void __launch_bounds__(32 * kSwWarps) k_bp_sweep(const SliceDesc* __r
         const int n = __popc(mask);
         if (mine) {
             const long long q = ray_pos(P, t0) - a0q;
-            const float wr = ray_w(P);
+            const float wr = ray_w(P) * sscale;
             const int at = __popc(mask & ((1u << lane) - 1u));
             st_ray[w][at] = make_int4((int)(unsigned)(unsigned long long)q, (int)(q >> 32), P.z, __float_as_int(wr * sv.x));
             st_wp[w][at] = wr * sv.y;
@@ -130,14 +146,19 @@ __global__ void __launch_bounds__(32 * kSwWarps) k_bp_sweep(const SliceDesc* __r
             for (int u = 0; u < kSwUnroll; ++u) {
                 // rows h, h+1 with h in [-1, 31] are accumulator rows h+1, h+2 (lanes outside skip)
                 if ((unsigned)(hh[u] + 1) < (unsigned)(kSw + 1)) {
-                    float2* a = &acc[w][hh[u] + 1][lane];
-                    float2 x0 = a[0], x1 = a[kSw];
-                    x0.x = fmaf(1.0f - ff[u], wc[u], x0.x);
-                    x0.y = fmaf(1.0f - ff[u], wp[u], x0.y);
-                    x1.x = fmaf(ff[u], wc[u], x1.x);
-                    x1.y = fmaf(ff[u], wp[u], x1.y);
-                    a[0] = x0;
-                    a[kSw] = x1;
+                    Acc* a = &acc[w][hh[u] + 1][lane];
+                    if constexpr (NCH == 2) {
+                        float2 x0 = a[0], x1 = a[kSw];
+                        x0.x = fmaf(1.0f - ff[u], wc[u], x0.x);
+                        x0.y = fmaf(1.0f - ff[u], wp[u], x0.y);
+                        x1.x = fmaf(ff[u], wc[u], x1.x);
+                        x1.y = fmaf(ff[u], wp[u], x1.y);
+                        a[0] = x0;
+                        a[kSw] = x1;
+                    } else {
+                        a[0] = fmaf(1.0f - ff[u], wc[u], a[0]);
+                        a[kSw] = fmaf(ff[u], wc[u], a[kSw]);
+                    }
                 }
             }
         }
@@ -148,11 +169,15 @@ __global__ void __launch_bounds__(32 * kSwWarps) k_bp_sweep(const SliceDesc* __r
         const int rr = px / kSw, cc = px % kSw;
         const int i = ti + cc, j = tj + rr;
         if (i < nx && j < ny) {
-            float2 sum = make_float2(0.f, 0.f);
+            Acc sum{};
             for (int gi = 0; gi < kSwGroups; ++gi) {
-                const float2 a = acc[2 * gi][rr + 1][cc], b = acc[2 * gi + 1][cc + 1][rr];
-                sum.x += a.x + b.x;
-                sum.y += a.y + b.y;
+                const Acc a = acc[2 * gi][rr + 1][cc], b = acc[2 * gi + 1][cc + 1][rr];
+                if constexpr (NCH == 2) {
+                    sum.x += a.x + b.x;
+                    sum.y += a.y + b.y;
+                } else {
+                    sum += a + b;
+                }
             }
             partial[c * stride + d.img_off + (size_t)j * nx + i] = sum;
         }
@@ -198,13 +223,15 @@ int sweep_groups(int tiles) {
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         // shared memory (34 KB per CTA) limits residency: ask for the largest carve-out
-        cudaFuncSetAttribute(k_bp_sweep<float2>, cudaFuncAttributePreferredSharedMemoryCarveout,
+        cudaFuncSetAttribute(k_bp_sweep<float2, 2>, cudaFuncAttributePreferredSharedMemoryCarveout,
                              cudaSharedmemCarveoutMaxShared);
-        cudaFuncSetAttribute(k_bp_sweep<__half2>, cudaFuncAttributePreferredSharedMemoryCarveout,
+        cudaFuncSetAttribute(k_bp_sweep<__half2, 2>, cudaFuncAttributePreferredSharedMemoryCarveout,
                              cudaSharedmemCarveoutMaxShared);
-        cudaFuncSetAttribute(k_bp_sweep<__nv_bfloat162>, cudaFuncAttributePreferredSharedMemoryCarveout,
+        cudaFuncSetAttribute(k_bp_sweep<__nv_bfloat162, 2>, cudaFuncAttributePreferredSharedMemoryCarveout,
                              cudaSharedmemCarveoutMaxShared);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_bp_sweep<float2>, 32 * kSwWarps, 0);
+        cudaFuncSetAttribute(k_bp_sweep<float, 1>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             cudaSharedmemCarveoutMaxShared);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_bp_sweep<float2, 2>, 32 * kSwWarps, 0);
         slots = sms * (occ > 0 ? occ : 1);
     }
     int best = 1;
@@ -224,12 +251,19 @@ int sweep_groups(int tiles) {
 void launch_bp_sweep(const SliceDesc* dsl, const BlockMap& smap, int nsweep, int C, const void* sino,
                      float2* partial, int64_t stride, int prec, cudaStream_t st) {
     if (prec == PREC_F16)
-        k_bp_sweep<__half2><<<nsweep, 32 * kSwWarps, 0, st>>>(dsl, smap, C, (const __half2*)sino, partial, stride);
+        k_bp_sweep<__half2, 2><<<nsweep, 32 * kSwWarps, 0, st>>>(dsl, smap, C, (const __half2*)sino, partial, stride,
+                                                                 nullptr, nullptr);
     else if (prec == PREC_BF16)
-        k_bp_sweep<__nv_bfloat162><<<nsweep, 32 * kSwWarps, 0, st>>>(dsl, smap, C, (const __nv_bfloat162*)sino,
-                                                                      partial, stride);
+        k_bp_sweep<__nv_bfloat162, 2><<<nsweep, 32 * kSwWarps, 0, st>>>(dsl, smap, C, (const __nv_bfloat162*)sino,
+                                                                         partial, stride, nullptr, nullptr);
     else
-        k_bp_sweep<float2><<<nsweep, 32 * kSwWarps, 0, st>>>(dsl, smap, C, (const float2*)sino, partial, stride);
+        k_bp_sweep<float2, 2><<<nsweep, 32 * kSwWarps, 0, st>>>(dsl, smap, C, (const float2*)sino, partial, stride,
+                                                                nullptr, nullptr);
+}
+
+void launch_bp_sweep1(const SliceDesc* dsl, const BlockMap& smap, int nsweep, int C, const float* sino, const float* rw,
+                      const float* scale, float* partial, int64_t stride, cudaStream_t st) {
+    k_bp_sweep<float, 1><<<nsweep, 32 * kSwWarps, 0, st>>>(dsl, smap, C, sino, partial, stride, rw, scale);
 }
 
 template <int MODE>
@@ -255,8 +289,8 @@ void backproject_single(const SliceDesc& sd, const SliceDesc* d_dev, const int* 
     const int64_t nr = (int64_t)sd.g.nv * sd.g.nb, np = (int64_t)sd.g.nx * sd.g.ny;
     launch_pack_planar(sino, nch, nr, packed, st);
     const BlockMap smap{maps, 1}, pmap{maps + 2, 1};
-    k_bp_sweep<float2><<<sweep_tiles(sd.g.nx, sd.g.ny) * C, 32 * kSwWarps, 0, st>>>(d_dev, smap, C, packed, partial,
-                                                                                   np);
+    k_bp_sweep<float2, 2><<<sweep_tiles(sd.g.nx, sd.g.ny) * C, 32 * kSwWarps, 0, st>>>(d_dev, smap, C, packed,
+                                                                                      partial, np, nullptr, nullptr);
     k_bp_finalize<BP_PLAIN><<<(unsigned)((np + 255) / 256), 256, 0, st>>>(d_dev, pmap, C, partial, np, nullptr,
                                                                          BpEpilogue{}, out, nch);
 }

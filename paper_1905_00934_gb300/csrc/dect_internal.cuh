@@ -86,6 +86,17 @@ struct SliceScalars {
     int32_t pad;
 };
 
+// Per-slice scalars of the comparison scheme LM(m) x CG(n) (one LM step on one basis at a time)
+struct LmScalars {
+    double mu[2];    // LM damping per basis (Marquardt scaling of the data curvature)
+    double rr;       // CG: <r, r>
+    double alpha;    // CG step
+    double beta;     // CG direction update
+    double dcost;    // change of the subproblem objective at the last trial point
+    int32_t accept;  // the last trial step was accepted
+    int32_t pad;
+};
+
 // Spectral tables on the device: T1 = {k_kn, k_p, S_h, S_l}, T2 = {S_h f_KN, S_h f_p, S_l f_KN, S_l f_p}
 // with k = f * log2(e) so that exp(-f_KN a_c - f_p a_p) = exp2(-k_kn a_c - k_p a_p).
 struct SpecDev {
@@ -120,6 +131,10 @@ cudaError_t build_ray_table(const dect_geom_desc& d, int4* rays, float4* views, 
 // (prec: storage format of textures and sinogram vectors, see prec.cuh)
 void launch_textures(const SliceDesc* dsl, const BlockMap& mx, int nbx, const BlockMap& my, int nby,
                      const float2* img, void* tx, void* ty, int prec, cudaStream_t st);
+void launch_textures1(const SliceDesc* dsl, const BlockMap& mx, int nbx, const BlockMap& my, int nby,
+                      const float* img, float2* tx, float2* ty, cudaStream_t st);
+void launch_project1(const SliceDesc* dsl, const BlockMap& map, int nblk, const float2* tx, const float2* ty,
+                     float* out, cudaStream_t st);
 void launch_project(const SliceDesc* dsl, const BlockMap& map, int nblk, const void* tx, const void* ty, void* out,
                     int prec, cudaStream_t st);
 // backproject_sweep.cu: the solver's backprojector (two kernels: sweep into C partial images, then
@@ -130,6 +145,9 @@ int sweep_tiles(int nx, int ny);
 int sweep_groups(int tiles);
 void launch_bp_sweep(const SliceDesc* dsl, const BlockMap& smap, int nsweep, int C, const void* sino,
                      float2* partial, int64_t stride, int prec, cudaStream_t st);
+// single-channel sweep (float sinogram, float partial images; rw per ray and scale per slice optional)
+void launch_bp_sweep1(const SliceDesc* dsl, const BlockMap& smap, int nsweep, int C, const float* sino, const float* rw,
+                      const float* scale, float* partial, int64_t stride, cudaStream_t st);
 void launch_bp_finalize(int mode, const SliceDesc* dsl, const BlockMap& pix, int npix, int C, const float2* partial,
                         int64_t stride, float2* out, const BpEpilogue& ep, cudaStream_t st);
 // Single-slice planar R^T (dect_backproject): sino [nch][nv][nb] -> out [nch][ny][nx]. d_dev is the
@@ -154,6 +172,34 @@ void launch_udm_init(const SliceDesc* dsl, const BlockMap& map, int nblk, const 
 void launch_udm_rays(const SpecDev& sp, int64_t n, const float* mh, const float* ml, const float* wh,
                      const float* wl, const float* vc, const float* vp, double rho_c, double rho_p, int iters,
                      float* ac, float* ap, float* mu, uint8_t* status, cudaStream_t st);
+
+void launch_lm_rays(const SliceDesc* dsl, const BlockMap& map, int nblk, const SpecDev& sp, const float4* meas,
+                    const float2* Rx, int b, float* ew, float* gw, float2* s0, float* Rd, cudaStream_t st);
+void launch_lm_trial(const SliceDesc* dsl, const BlockMap& map, int nblk, const SpecDev& sp, const float4* meas,
+                     const float2* Rx, int b, const float* Rd, const float2* s0, double* partial, cudaStream_t st);
+
+// lmcg.cu
+void launch_lm_reset(LmScalars* ls, int B, double mu0, cudaStream_t st);
+void launch_lm_begin(const LmScalars* ls, float* scale, int B, int b, cudaStream_t st);
+void launch_lm_grad(const SliceDesc* dsl, const BlockMap& pix, int npix, int C, const float* partial, int64_t stride,
+                    int b, const SliceScalars* sc, const BpEpilogue& ep, float* r, float* p, float* dlt, double* part,
+                    cudaStream_t st);
+void launch_lm_ap(const SliceDesc* dsl, const BlockMap& pix, int npix, int C, const float* partial, int64_t stride,
+                  int b, const SliceScalars* sc, const float* p, float* Ap, double* part, cudaStream_t st);
+void launch_lm_alpha(const double* part, const int* prefix, LmScalars* ls, int B, cudaStream_t st);
+void launch_lm_rr(const double* part, const int* prefix, LmScalars* ls, int B, int first, cudaStream_t st);
+void launch_lm_cg(const SliceDesc* dsl, const BlockMap& pix, int npix, const BlockMap& rays, int nray,
+                  const LmScalars* ls, float* dlt, const float* p, float* r, const float* Ap, float* Rd, const float* q,
+                  int last, double* part, cudaStream_t st);
+void launch_lm_p(const SliceDesc* dsl, const BlockMap& pix, int npix, const LmScalars* ls, const float* r, float* p,
+                 cudaStream_t st);
+void launch_lm_al_delta(const SliceDesc* dsl, const BlockMap& pix, int npix, int b, const SliceScalars* sc,
+                        const BpEpilogue& ep, const float* dlt, double* part, cudaStream_t st);
+void launch_lm_decide(const double* part_ray, const int* rays_prefix, const double* part_pix, const int* pix_prefix,
+                      LmScalars* ls, float* scale, int B, int b, cudaStream_t st);
+void launch_lm_accept(const SliceDesc* dsl, const BlockMap& pix, int npix, const BlockMap& rays, int nray,
+                      const LmScalars* ls, int b, float2* x, const float* dlt, float2* Rx, const float* Rd,
+                      cudaStream_t st);
 
 void launch_forward_model(const SpecDev& sp, const double4* t64, int64_t n, int dtype, const void* ac,
                           const void* ap, void* fh, void* fl, void* jac, const void* gh, const void* gl, void* oc,

@@ -43,11 +43,16 @@ __device__ __forceinline__ float2 ld2(const float2* p) { return *p; }
 __device__ __forceinline__ float2 ld2(const __half2* p) { return __half22float2(*p); }
 __device__ __forceinline__ float2 ld2(const __nv_bfloat162* p) { return __bfloat1622float2(*p); }
 __device__ __forceinline__ void st2(float2* p, float2 v) { *p = v; }
+__device__ __forceinline__ void st2(float* p, float2 v) { *p = v.x; }  // single-channel vectors keep x
 __device__ __forceinline__ void st2(__half2* p, float2 v) { *p = __float22half2_rn(v); }
 __device__ __forceinline__ void st2(__nv_bfloat162* p, float2 v) { *p = __float22bfloat162_rn(v); }
 
-// pair-texture texels: {c(lo), p(lo), c(hi), p(hi)}
+// pair-texture texels: {c(lo), p(lo), c(hi), p(hi)}; single-channel texels float2 {lo, hi}
 __device__ __forceinline__ float4 ldtex(const float4* p) { return __ldg(p); }
+__device__ __forceinline__ float4 ldtex(const float2* p) {
+    const float2 v = __ldg(p);
+    return make_float4(v.x, 0.f, v.y, 0.f);
+}
 __device__ __forceinline__ float4 ldtex(const TexH* p) {
     const uint2 u = __ldg(reinterpret_cast<const uint2*>(p));
     const float2 a = __half22float2(*reinterpret_cast<const __half2*>(&u.x));
@@ -61,6 +66,7 @@ __device__ __forceinline__ float4 ldtex(const TexB* p) {
     return make_float4(a.x, a.y, b.x, b.y);
 }
 __device__ __forceinline__ void sttex(float4* p, float2 lo, float2 hi) { *p = make_float4(lo.x, lo.y, hi.x, hi.y); }
+__device__ __forceinline__ void sttex(float2* p, float lo, float hi) { *p = make_float2(lo, hi); }
 __device__ __forceinline__ void sttex(TexH* p, float2 lo, float2 hi) {
     TexH t;
     t.lo = __float22half2_rn(lo);

@@ -88,23 +88,25 @@ cudaError_t build_ray_table(const dect_geom_desc& d, int4* rays, float4* views, 
 // ---------------------------------------------------------------------------------------------
 // pair textures
 
-__device__ __forceinline__ float2 img_at(const float2* __restrict__ img, int nx, int ny, int j, int i) {
-    if (j < 0 || j >= ny || i < 0 || i >= nx) return make_float2(0.f, 0.f);
+// image value at (j, i), zero outside; IM = float2 {c, p} or float (single channel)
+template <class IM>
+__device__ __forceinline__ IM img_at(const IM* __restrict__ img, int nx, int ny, int j, int i) {
+    if (j < 0 || j >= ny || i < 0 || i >= nx) return IM{};
     return __ldg(img + (size_t)j * nx + i);
 }
 
 // TX[i][jj] from a 32 (jj) x 32 (i) tile; rows jj-2 .. jj+29 staged in shared memory.
-template <class TX>
+template <class TX, class IM = float2>
 __global__ void __launch_bounds__(256) k_texture_x(const SliceDesc* __restrict__ dsl, BlockMap map,
-                                                   const float2* __restrict__ img, TX* __restrict__ tx) {
-    __shared__ float2 tile[33][33];
+                                                   const IM* __restrict__ img, TX* __restrict__ tx) {
+    __shared__ IM tile[33][33];
     int local;
     const int s = slice_of(map, blockIdx.x, local);
     const SliceDesc& d = dsl[s];
     const int nx = d.g.nx, ny = d.g.ny;
     const int tiles_i = (nx + 31) / 32;
     const int jt = (local / tiles_i) * 32, it = (local % tiles_i) * 32;
-    const float2* im = img + d.img_off;
+    const IM* im = img + d.img_off;
     // stage rows jt-2 .. jt+30 (33 rows), columns it .. it+31
     for (int e = threadIdx.x; e < 33 * 32; e += blockDim.x) {
         const int rr = e / 32, cc = e % 32;
@@ -121,9 +123,9 @@ __global__ void __launch_bounds__(256) k_texture_x(const SliceDesc* __restrict__
 }
 
 // TY[j][ii], one entry per thread.
-template <class TX>
+template <class TX, class IM = float2>
 __global__ void __launch_bounds__(256) k_texture_y(const SliceDesc* __restrict__ dsl, BlockMap map,
-                                                   const float2* __restrict__ img, TX* __restrict__ ty) {
+                                                   const IM* __restrict__ img, TX* __restrict__ ty) {
     int local;
     const int s = slice_of(map, blockIdx.x, local);
     const SliceDesc& d = dsl[s];
@@ -131,7 +133,7 @@ __global__ void __launch_bounds__(256) k_texture_y(const SliceDesc* __restrict__
     const int64_t e = (int64_t)local * blockDim.x + threadIdx.x;
     if (e >= (int64_t)ny * ld) return;
     const int j = (int)(e / ld), ii = (int)(e % ld);
-    const float2* im = img + d.img_off;
+    const IM* im = img + d.img_off;
     sttex(ty + d.ty_off + e, img_at(im, nx, ny, j, ii - 2), img_at(im, nx, ny, j, ii - 1));
 }
 
@@ -151,6 +153,14 @@ void launch_textures(const SliceDesc* dsl, const BlockMap& mx, int nbx, const Bl
         k_texture_x<float4><<<nbx, 256, 0, st>>>(dsl, mx, img, (float4*)tx);
         k_texture_y<float4><<<nby, 256, 0, st>>>(dsl, my, img, (float4*)ty);
     }
+}
+
+// Single-channel textures (float2 texels {x(lo), x(hi)}) of a float image, for the comparison scheme's
+// per-basis projections.
+void launch_textures1(const SliceDesc* dsl, const BlockMap& mx, int nbx, const BlockMap& my, int nby,
+                      const float* img, float2* tx, float2* ty, cudaStream_t st) {
+    k_texture_x<float2, float><<<nbx, 256, 0, st>>>(dsl, mx, img, tx);
+    k_texture_y<float2, float><<<nby, 256, 0, st>>>(dsl, my, img, ty);
 }
 
 // planar input (1 or 2 channels) -> interleaved float2 image
@@ -270,6 +280,12 @@ void launch_project(const SliceDesc* dsl, const BlockMap& map, int nblk, const v
     else
         k_project<float2, float4><<<nblk, kRaysPerBlock, 0, st>>>(dsl, map, (const float4*)tx, (const float4*)ty,
                                                                    (float2*)out);
+}
+
+// single channel: float out, float2 texels
+void launch_project1(const SliceDesc* dsl, const BlockMap& map, int nblk, const float2* tx, const float2* ty,
+                     float* out, cudaStream_t st) {
+    k_project<float, float2><<<nblk, kRaysPerBlock, 0, st>>>(dsl, map, tx, ty, out);
 }
 
 // ---------------------------------------------------------------------------------------------

@@ -23,6 +23,7 @@
 
 #include "dect_internal.cuh"
 #include "prec.cuh"
+#include "reduce.cuh"
 
 namespace dect {
 
@@ -299,6 +300,81 @@ __global__ void __launch_bounds__(kRaysPerBlock) k_udm_rays(SpecDev sp, int64_t 
     if (status) status[r] = st.status;
 }
 
+// ---- comparison scheme LM(m) x CG(n): the per-ray parts of one LM step on basis b --------------------
+
+// Gauss-Newton weights at the current projections: e = w_h r_h J_h,b + w_l r_l J_l,b and
+// g = w_h J_h,b^2 + w_l J_l,b^2 (r = f - m), the spectral sums s0 = {s_h, s_l} for the trial's cost
+// change, and R d cleared.
+__global__ void __launch_bounds__(kRaysPerBlock) k_lm_rays(const SliceDesc* __restrict__ dsl, BlockMap map, SpecDev sp,
+                                                           const float4* __restrict__ meas,
+                                                           const float2* __restrict__ Rx, int b, float* __restrict__ ew,
+                                                           float* __restrict__ gw, float2* __restrict__ s0,
+                                                           float* __restrict__ Rd) {
+    extern __shared__ float4 tabs[];
+    float4* t1 = tabs;
+    float4* t2 = tabs + sp.ne;
+    load_tables(sp, t1, t2);
+    int local;
+    const int s = slice_of(map, blockIdx.x, local);
+    const SliceDesc& d = dsl[s];
+    const int64_t r = (int64_t)local * kRaysPerBlock + threadIdx.x;
+    if (r >= (int64_t)d.g.nv * d.g.nb) return;
+    const int64_t e = d.sino_off + r;
+    const float4 m = __ldg(meas + e);
+    const float2 a = __ldg(Rx + e);
+    float sh, sl, shc, shp, slc, slp;
+    spectral_sums_jac(t1, t2, sp.ne, a.x, a.y, sh, sl, shc, shp, slc, slp);
+    const float rh = neg_log_ratio(sh, expf(-m.x)), rl = neg_log_ratio(sl, expf(-m.y));
+    const float jh = (b ? shp : shc) / sh, jl = (b ? slp : slc) / sl;
+    ew[e] = m.z * rh * jh + m.w * rl * jl;
+    gw[e] = m.z * jh * jh + m.w * jl * jl;
+    s0[e] = make_float2(sh, sl);
+    Rd[e] = 0.f;
+}
+
+// Change of the data term 1/2 sum_k w_k r_k^2 when basis b's projections move by R d:
+// 1/2 sum_k w_k (r1 - r0)(r1 + r0) with r1 - r0 = -log(s1 / s0); partial[blk] = sum.
+__global__ void __launch_bounds__(kRaysPerBlock) k_lm_trial(const SliceDesc* __restrict__ dsl, BlockMap map,
+                                                            SpecDev sp, const float4* __restrict__ meas,
+                                                            const float2* __restrict__ Rx, int b,
+                                                            const float* __restrict__ Rd,
+                                                            const float2* __restrict__ s0,
+                                                            double* __restrict__ partial) {
+    extern __shared__ float4 tabs[];
+    float4* t1 = tabs;
+    float4* t2 = tabs + sp.ne;
+    load_tables(sp, t1, t2);
+    int local;
+    const int s = slice_of(map, blockIdx.x, local);
+    const SliceDesc& d = dsl[s];
+    const int64_t r = (int64_t)local * kRaysPerBlock + threadIdx.x;
+    double acc[1] = {0.0};
+    if (r < (int64_t)d.g.nv * d.g.nb) {
+        const int64_t e = d.sino_off + r;
+        const float4 m = __ldg(meas + e);
+        float2 a = __ldg(Rx + e);
+        if (b) a.y += __ldg(Rd + e); else a.x += __ldg(Rd + e);
+        float sh, sl;
+        spectral_sums(t1, sp.ne, a.x, a.y, sh, sl);
+        const float2 o = __ldg(s0 + e);
+        const float r0h = neg_log_ratio(o.x, expf(-m.x)), r0l = neg_log_ratio(o.y, expf(-m.y));
+        const float eh = neg_log_ratio(sh, o.x), el = neg_log_ratio(sl, o.y);
+        acc[0] = 0.5 * ((double)m.z * eh * (2.0 * r0h + eh) + (double)m.w * el * (2.0 * r0l + el));
+    }
+    block_partials<1>(acc, partial);
+}
+
+static size_t tab_bytes(const SpecDev& sp) { return 2 * sizeof(float4) * (size_t)sp.ne; }
+
+void launch_lm_rays(const SliceDesc* dsl, const BlockMap& map, int nblk, const SpecDev& sp, const float4* meas,
+                    const float2* Rx, int b, float* ew, float* gw, float2* s0, float* Rd, cudaStream_t st) {
+    k_lm_rays<<<nblk, kRaysPerBlock, tab_bytes(sp), st>>>(dsl, map, sp, meas, Rx, b, ew, gw, s0, Rd);
+}
+void launch_lm_trial(const SliceDesc* dsl, const BlockMap& map, int nblk, const SpecDev& sp, const float4* meas,
+                     const float2* Rx, int b, const float* Rd, const float2* s0, double* partial, cudaStream_t st) {
+    k_lm_trial<<<nblk, kRaysPerBlock, tab_bytes(sp), st>>>(dsl, map, sp, meas, Rx, b, Rd, s0, partial);
+}
+
 // ---- forward model f (Eq. 3) and its Jacobian-transpose product, per ray ---------------------------
 // float32: the LM kernel's sums (compensated, float32 exponentials), logs and ratios in float64.
 // float64: tables and exponentials in float64 (t64 = {S_h, S_l, f_KN, f_p} per energy, unit-sum S).
@@ -370,7 +446,6 @@ __global__ void __launch_bounds__(kRaysPerBlock) k_forward_model_f64(int ne, con
     }
 }
 
-static size_t tab_bytes(const SpecDev& sp) { return 2 * sizeof(float4) * (size_t)sp.ne; }
 
 void launch_forward_model(const SpecDev& sp, const double4* t64, int64_t n, int dtype, const void* ac,
                           const void* ap, void* fh, void* fl, void* jac, const void* gh, const void* gl, void* oc,
