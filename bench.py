@@ -309,6 +309,41 @@ def run_dect(args):
         gate.update({"oracle_xi_p_db": target, "oracle_xi_c_db": gold["xi_c"][ITERS],
                      "within_0p5_db": bool(abs(st0["xi_db"][1] - target) <= 0.5)})
 
+    # the paper's comparison (Sec. 4): time to the same PE error for UDM1-PCG1 and the old splitting
+    # LM1 x CG1 on the same slices; slice 0's xi_p checked every 5 iterations against the oracle's
+    # xi_p after the workload's iterations + 0.5 dB, up to twice the workload's iterations
+    comparison = None
+    if gold is not None and rank == 0 and not args.no_comparison:
+        target = gold["xi_p"][ITERS] + 0.5
+        comparison = {"target_xi_p_db": target, "check_every": 5, "cap_iterations": 2 * ITERS,
+                      "timed": "ADMM iterations after the shared initial image, CUDA events"}
+        for name, scheme in (("udm1_pcg1", dect.SCHEME_UDM_PCG), ("lm1_cg1", dect.SCHEME_LM_CG)):
+            s2 = Solver(geo, spec, kappa=BAGGAGE_KAPPA, scheme=scheme)
+            for b, c in enumerate(cases):
+                s2.set_data(b, *dev_data[b])
+                s2.set_truth(b, f32(np.stack([c["truth_c"], c["truth_p"]])))
+            s2.reconstruct(0)
+            s2.step(5)  # graph capture outside the timing
+            s2.reconstruct(0)
+            barrier()
+            t_ms, it, hit, xi_p = 0.0, 0, None, None
+            while it < 2 * ITERS:
+                c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                c0.record(stream)
+                s2.step(5)
+                c1.record(stream)
+                c1.synchronize()
+                t_ms += c0.elapsed_time(c1)
+                it += 5
+                xi_p = s2.stats(0)["xi_db"][1]
+                if xi_p <= target:
+                    hit = it
+                    break
+            comparison[name] = {"iterations_to_target": hit, "ms_to_target": t_ms if hit else None,
+                                "ms_per_iteration": t_ms / it, "xi_p_db_at_stop": xi_p, "iterations_run": it,
+                                "slices": B}
+            del s2
+
     # end to end through the C ABI: pinned host measurements in, image out, every step
     host_in = [[t.cpu().pin_memory() for t in d] for d in dev_data]
     host_out = [torch.empty((2, c["geom"].ny, c["geom"].nx), dtype=torch.float32).pin_memory() for c in cases]
@@ -384,7 +419,7 @@ def run_dect(args):
                        "bp_view_groups": st0["bp_view_groups"],
                        "plain_slices_per_s": (ws * B / (plain_ms / 1e3)) if plain_ms else None,
                        "batched_over_plain": (value / (ws * B / (plain_ms / 1e3))) if plain_ms else None,
-                       "pe_gate": gate, "phases": phases},
+                       "pe_gate": gate, "phases": phases, "scheme_comparison": comparison},
             "clocks": clocks,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                     "steps": e2e_steps},
@@ -409,6 +444,8 @@ def main():
     ap.add_argument("--storage", default="f32", choices=["f32", "f16", "bf16"],
                     help="storage of the sinogram vectors and projector textures (arithmetic stays f32/f64)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-comparison", action="store_true",
+                    help="skip the time-to-target comparison with the LM x CG splitting")
     ap.add_argument("--profile-run", type=int, default=0, metavar="ITERS",
                     help="set up the workload, run one untimed reconstruction of ITERS iterations and exit "
                          "(for profiler captures; prints no bench line)")
