@@ -279,26 +279,32 @@ def run_dect(args):
     total_ms = shard.max_over_ranks(float(sum(step_ms)), dev)
     value = ws * B * args.steps / (total_ms / 1e3)
 
-    # the plain form: the same slices reconstructed one at a time by single-slice solvers
-    plain_ms = None
+    # the plain form: the same slices reconstructed one at a time by single-slice solvers, (a) as the
+    # metric names it -- eager launches, view groups from the occupancy rule -- and (b) with the
+    # graph and the autotuner (the single-slice path at its best)
+    plain_ms = plain_best_ms = None
     if B > 1:
-        singles = []
-        for b, c in enumerate(cases):
-            s1 = Solver([geo[b]], spec, kappa=BAGGAGE_KAPPA)
-            s1.set_data(0, *dev_data[b])
-            singles.append(s1)
-        for s1 in singles:
-            s1.reconstruct(ITERS)  # warm-up (graph capture)
-        barrier()
-        p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        flush.fill_(0.0)
-        p0.record(stream)
-        for s1 in singles:
-            s1.reconstruct(ITERS)
-        p1.record(stream)
-        barrier()
-        plain_ms = p0.elapsed_time(p1)
-        del singles
+        for kind, params in (("plain", dict(use_graph=0, bp_view_groups=-1)), ("best", {})):
+            singles = []
+            for b, c in enumerate(cases):
+                s1 = Solver([geo[b]], spec, kappa=BAGGAGE_KAPPA, **params)
+                s1.set_data(0, *dev_data[b])
+                singles.append(s1)
+            for s1 in singles:
+                s1.reconstruct(ITERS)  # warm-up (graph capture)
+            barrier()
+            p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            flush.fill_(0.0)
+            p0.record(stream)
+            for s1 in singles:
+                s1.reconstruct(ITERS)
+            p1.record(stream)
+            barrier()
+            if kind == "plain":
+                plain_ms = p0.elapsed_time(p1)
+            else:
+                plain_best_ms = p0.elapsed_time(p1)
+            del singles
 
     # quality gate: xi_p of slice 0 after the workload's iterations vs the oracle's
     st0 = sol.stats(0)
@@ -419,6 +425,9 @@ def run_dect(args):
                        "bp_view_groups": st0["bp_view_groups"],
                        "plain_slices_per_s": (ws * B / (plain_ms / 1e3)) if plain_ms else None,
                        "batched_over_plain": (value / (ws * B / (plain_ms / 1e3))) if plain_ms else None,
+                       "plain_graph_autotuned_slices_per_s": (ws * B / (plain_best_ms / 1e3)) if plain_best_ms
+                       else None,
+                       "plain": "single-slice solvers one after another; eager launches, occupancy view groups",
                        "pe_gate": gate, "phases": phases, "scheme_comparison": comparison},
             "clocks": clocks,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
@@ -431,6 +440,59 @@ def run_dect(args):
         print(json.dumps(line), flush=True)
     if ws > 1:
         torch.distributed.destroy_process_group()
+    return 0
+
+
+def run_study(args):
+    """The paper's evaluation protocol on the synthetic workload (Sec. 4, Fig. 2): xi_c, xi_p (Eq. 14,
+    mean over the batch) every 10 iterations and the device time per iteration, for UDM(m)-PCG(n)
+    variants, the same with plain CG (no preconditioner) and the LM(m) x CG(n) splitting."""
+    import torch
+
+    import __graft_entry__
+
+    __graft_entry__.build()
+    from paper_1905_00934_gb300 import Geometry, Solver, Spectra, dect
+    from synth.workloads import BAGGAGE_KAPPA, baggage_fan_case
+    from concurrent.futures import ThreadPoolExecutor
+
+    dev = torch.device("cuda", 0)
+    B = args.batch
+    with ThreadPoolExecutor(max_workers=min(B, 16)) as ex:
+        cases = list(ex.map(lambda b: baggage_fan_case(slice_index=b), range(B)))
+    geo = [Geometry(c["geom"]) for c in cases]
+    spec = Spectra.from_tables(cases[0]["spectra"])
+    f32 = lambda a: torch.tensor(np.ascontiguousarray(a), dtype=torch.float32, device=dev)
+    configs = [("UDM1-PCG1", dict(m_udm=1, n_pcg=1)), ("UDM1-PCG2", dict(m_udm=1, n_pcg=2)),
+               ("UDM2-PCG1", dict(m_udm=2, n_pcg=1)), ("UDM1-PCG5", dict(m_udm=1, n_pcg=5)),
+               ("UDM1-CG1", dict(m_udm=1, n_pcg=1, precondition=0)),
+               ("UDM1-CG5", dict(m_udm=1, n_pcg=5, precondition=0)),
+               ("LM1xCG1", dict(m_udm=1, n_pcg=1, scheme=dect.SCHEME_LM_CG)),
+               ("LM1xCG5", dict(m_udm=1, n_pcg=5, scheme=dect.SCHEME_LM_CG))]
+    iters = args.study_iters
+    rows = {}
+    for name, params in configs:
+        sol = Solver(geo, spec, kappa=BAGGAGE_KAPPA, **params)
+        for b, c in enumerate(cases):
+            sol.set_data(b, *[f32(c[k]) for k in ("m_h", "m_l", "w_h", "w_l")])
+            sol.set_truth(b, f32(np.stack([c["truth_c"], c["truth_p"]])))
+        sol.reconstruct(0)
+        xi0 = np.mean([sol.stats(b)["xi_db"] for b in range(B)], axis=0)
+        traj, t_ms = [(0, 0.0, float(xi0[0]), float(xi0[1]))], 0.0
+        for k in range(iters // 10):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            sol.step(10)
+            e1.record()
+            e1.synchronize()
+            t_ms += e0.elapsed_time(e1)
+            xi = np.mean([sol.stats(b)["xi_db"] for b in range(B)], axis=0)
+            traj.append((10 * (k + 1), round(t_ms, 2), round(float(xi[0]), 4), round(float(xi[1]), 4)))
+        rows[name] = {"ms_per_iteration": t_ms / iters, "params": params,
+                      "xi": traj, "best_xi_p_db": min(r[3] for r in traj)}
+        del sol
+    print(json.dumps({"study": "xi vs iteration and time, mean over the batch", "batch": B,
+                      "workload": "fan beam 512x512, 720 views x 1024 bins", "trajectories": rows}), flush=True)
     return 0
 
 
@@ -449,7 +511,12 @@ def main():
     ap.add_argument("--profile-run", type=int, default=0, metavar="ITERS",
                     help="set up the workload, run one untimed reconstruction of ITERS iterations and exit "
                          "(for profiler captures; prints no bench line)")
+    ap.add_argument("--study", action="store_true",
+                    help="print xi trajectories of UDM-PCG variants, plain CG and LM x CG instead of the bench line")
+    ap.add_argument("--study-iters", type=int, default=200)
     args = ap.parse_args()
+    if args.study:
+        return run_study(args)
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":

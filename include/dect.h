@@ -226,7 +226,8 @@ typedef struct {
     int32_t init_pcg_iters;      /* initialisation: CG iterations (10) */
     int32_t precondition;        /* 1: circulant preconditioner, 0: plain CG */
     int32_t use_graph;           /* 1: capture one iteration as a CUDA graph */
-    int32_t bp_view_groups;      /* backprojector view groups per image tile, 1..16; 0 = autotuned:
+    int32_t bp_view_groups;      /* backprojector view groups per image tile, 1..16; -1 = chosen from the
+                                    occupancy (fill the GPU's resident slots) without timing; 0 = autotuned:
                                     dect_admm_create times the backprojector on this batch for a few
                                     candidates (memory permitting) and keeps the fastest (reported in
                                     dect_stats). It fixes the order of a pixel's partial sums: results

@@ -871,8 +871,8 @@ extern "C" dect_status dect_admm_create(dect_geom* const* geoms, int32_t B, cons
         DECT_FAIL(DECT_EINVAL, "dect_admm_create: scheme must be DECT_SCHEME_UDM_PCG or DECT_SCHEME_LM_CG");
     if (P->scheme == DECT_SCHEME_LM_CG && P->storage != DECT_STORE_F32)
         DECT_FAIL(DECT_EUNSUPPORTED, "dect_admm_create: the LM x CG scheme runs with float32 storage only");
-    if (P->bp_view_groups < 0 || P->bp_view_groups > 16)
-        DECT_FAIL(DECT_EINVAL, "dect_admm_create: bp_view_groups must be in [0, 16]");
+    if (P->bp_view_groups < -1 || P->bp_view_groups > 16)
+        DECT_FAIL(DECT_EINVAL, "dect_admm_create: bp_view_groups must be in [-1, 16]");
     if (P->m_udm < 1 || P->n_pcg < 1 || P->m_udm > 64 || P->n_pcg > 64)
         DECT_FAIL(DECT_EINVAL, "dect_admm_create: m_udm and n_pcg must be in [1, 64]");
     if (P->init_udm_iters < 0 || P->init_pcg_iters < 1 || P->init_udm_iters > 1000 || P->init_pcg_iters > 1000)
@@ -909,6 +909,8 @@ extern "C" dect_status dect_admm_create(dect_geom* const* geoms, int32_t B, cons
         }
         if (P->bp_view_groups > 0) {
             A->sweep_C = sweep_ctas_for_groups(P->bp_view_groups);
+        } else if (P->bp_view_groups < 0) {
+            A->sweep_C = sweep_groups(total);  // occupancy choice, not timed
         } else {
             // candidates whose partial images fit in 1/16 of the free memory (and 4 GiB)
             size_t free_b = 0, total_b = 0;
