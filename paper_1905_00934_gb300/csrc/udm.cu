@@ -11,12 +11,9 @@
 // log1p of the relative difference when s and t are within a factor 2, which
 // keeps the float32 sum's accuracy without a float64 log; the cost change of
 // the trial step is formed from the residual changes -log(s' / s), so the
-// accept test (cost decreased) does not subtract two large costs. The normal
-// equations, the 2x2 Marquardt solve and the cost change are float64 from
-// float32 inputs: the photoelectric Jacobian column is nearly a multiple of
-// the Compton one at high attenuation, and rounding the three matrix entries
-// separately in float32 breaks the consistency the solve relies on (measured:
-// 10x larger drift from the FP64 oracle at 1024^2). Everything else is float32
+// accept test (cost decreased) does not subtract two large costs. The 2x2
+// Marquardt solve is float32 from the Jacobian's minors (see lm_ray), which
+// keeps it consistent with its float32 inputs; no float64 in the LM loop
 // (float64 throughput is low on this GPU).
 #include <cuda_runtime.h>
 #include <math.h>
@@ -106,51 +103,63 @@ __device__ __forceinline__ float neg_log_ratio(float a, float b) {
     return (q > 0.5f && q < 2.0f) ? -log1pf((a - b) / b) : -logf(q);
 }
 
+// a * b - c * d with one rounding of the result (the rounding error of c * d is recovered by an fma)
+__device__ __forceinline__ float diff_of_products(float a, float b, float c, float d) {
+    const float w = c * d;
+    const float e = fmaf(-c, d, w);
+    return fmaf(a, b, -w) + e;
+}
+
 // `iters` LM iterations of Eq. 13 for one ray (tables t1/t2 in shared memory).
+//
+// The Marquardt-damped Gauss-Newton step solves B d = -g with B = J^T W J + diag(e) (W = diag(w_h, w_l),
+// J the 2x2 Jacobian of f, e_b = rho_b + mu (B_bb of the undamped matrix)) and g = J^T W r + q,
+// q = rho (a - v). For a 2x2 J these follow from J's minors (Cauchy-Binet):
+//   det B   = w_h w_l det(J)^2 + e_0 C_11 + e_1 C_00 + e_0 e_1         (C = J^T W J; every term >= 0)
+//   adj(B) g = w_h w_l det(J) adj(J) r + adj(J) diag(w_l, w_h) adj(J)^T q + (e_1 g_0, e_0 g_1)
+// so the cancellations of nearly collinear Compton and photoelectric columns happen only inside
+// det(J) and the adj(J) products, each one fma-compensated difference of products: the float32 solve
+// stays consistent with its float32 Jacobian, like a float64 solve of the same inputs.
 __device__ void lm_ray(const float4* __restrict__ t1, const float4* __restrict__ t2, int ne, const RayIn& in,
                        int iters, LmState& s) {
     const float tm_h = expf(-in.mh), tm_l = expf(-in.ml);
-    const double wh = in.wh, wl = in.wl, rc = in.rc, rp = in.rp;  // rho exact as the host's float64
+    const float wh = in.wh, wl = in.wl, rc = (float)in.rc, rp = (float)in.rp;
     for (int it = 0; it < iters; ++it) {
         float sh, sl, shc, shp, slc, slp;
         spectral_sums_jac(t1, t2, ne, s.ac, s.ap, sh, sl, shc, shp, slc, slp);
         const float rh = neg_log_ratio(sh, tm_h), rl = neg_log_ratio(sl, tm_l);  // f - m = -log(s / t)
-        if (!isfinite(rh) || !isfinite(rl)) {
+        const float j0 = shc / sh, j1 = shp / sh, j2 = slc / sl, j3 = slp / sl;
+        const float dc = (s.ac - in.vc_hi) - in.vc_lo, dp = (s.ap - in.vp_hi) - in.vp_lo;  // a - v
+        const float q0 = rc * dc, q1 = rp * dp;
+        const float C00 = fmaf(wh * j0, j0, wl * j2 * j2), C11 = fmaf(wh * j1, j1, wl * j3 * j3);
+        const float e0 = fmaf(s.mu, C00 + rc, rc), e1 = fmaf(s.mu, C11 + rp, rp);
+        const float dJ = diff_of_products(j0, j3, j1, j2);
+        const float whl = wh * wl;
+        const float det = fmaf(whl * dJ, dJ, fmaf(e0, C11, fmaf(e1, C00, e0 * e1)));
+        if (!(det > 0.0f) || !isfinite(det) || !isfinite(rh) || !isfinite(rl)) {
             s.status = DECT_RAY_NONFINITE;
             break;
         }
-        // gradient and damped Gauss-Newton matrix of the linearised Eq. 13, float64 from the float32
-        // Jacobian (products of float32 values are exact, so the matrix stays consistent)
-        const double j0 = shc / sh, j1 = shp / sh, j2 = slc / sl, j3 = slp / sl;
-        const double dc = ((double)s.ac - in.vc_hi) - in.vc_lo, dp = ((double)s.ap - in.vp_hi) - in.vp_lo;
-        const double wrh = wh * rh, wrl = wl * rl;
-        const double g0 = wrh * j0 + wrl * j2 + rc * dc;
-        const double g1 = wrh * j1 + wrl * j3 + rp * dp;
-        const double A00 = wh * j0 * j0 + wl * j2 * j2 + rc;
-        const double A01 = wh * j0 * j1 + wl * j2 * j3;
-        const double A11 = wh * j1 * j1 + wl * j3 * j3 + rp;
-        const double m1 = 1.0 + (double)s.mu;
-        const double B00 = A00 * m1, B11 = A11 * m1;
-        const double det = B00 * B11 - A01 * A01;
-        if (!(det > 0.0) || !isfinite(det)) {
-            s.status = DECT_RAY_NONFINITE;
-            break;
-        }
-        const double idet = 1.0 / det;
-        const float tc = (float)((double)s.ac + (g1 * A01 - g0 * B11) * idet);
-        const float tp = (float)((double)s.ap + (g0 * A01 - g1 * B00) * idet);
+        const float g0 = fmaf(wh * rh, j0, fmaf(wl * rl, j2, q0));
+        const float g1 = fmaf(wh * rh, j1, fmaf(wl * rl, j3, q1));
+        const float ar0 = diff_of_products(j3, rh, j1, rl), ar1 = diff_of_products(j0, rl, j2, rh);
+        const float u0 = wl * diff_of_products(j3, q0, j2, q1), u1 = wh * diff_of_products(j0, q1, j1, q0);
+        const float aq0 = diff_of_products(j3, u0, j1, u1), aq1 = diff_of_products(j0, u1, j2, u0);
+        const float n0 = fmaf(whl * dJ, ar0, aq0) + e1 * g0;
+        const float n1 = fmaf(whl * dJ, ar1, aq1) + e0 * g1;
+        const float tc = s.ac - n0 / det, tp = s.ap - n1 / det;
         float th, tl;
         spectral_sums(t1, ne, tc, tp, th, tl);
-        // cost(trial) - cost(a) = 1/2 sum_k w_k (r1 - r0)(r1 + r0) + 1/2 sum_b rho_b e_b (e_b + 2 (a_b - v_b))
+        // 2 (cost(trial) - cost(a)) = sum_k w_k (r1 - r0)(r1 + r0) + sum_b rho_b e_b (e_b + 2 (a_b - v_b))
         const float eh = neg_log_ratio(th, sh), el = neg_log_ratio(tl, sl);  // r1 - r0
-        const double ec = (double)tc - (double)s.ac, ep = (double)tp - (double)s.ap;
-        const double dcost = 0.5 * (wh * eh * (2.0 * rh + eh) + wl * el * (2.0 * rl + el)) +
-                             0.5 * (rc * ec * (ec + 2.0 * dc) + rp * ep * (ep + 2.0 * dp));
+        const float ec = tc - s.ac, ep = tp - s.ap;
+        const float dcost = (wh * eh * fmaf(2.0f, rh, eh) + wl * el * fmaf(2.0f, rl, el)) +
+                            (rc * ec * fmaf(2.0f, dc, ec) + rp * ep * fmaf(2.0f, dp, ep));
         float mu = s.mu;
         if (!isfinite(dcost)) {
             mu *= 10.f;
             s.status = DECT_RAY_NONFINITE;
-        } else if (dcost < 0.0) {
+        } else if (dcost < 0.0f) {
             s.ac = tc;
             s.ap = tp;
             mu *= 0.1f;

