@@ -140,7 +140,7 @@ __global__ void __launch_bounds__(256) k_image_update(const SliceDesc* __restric
     const SliceDesc& d = dsl[s];
     const int nx = d.g.nx, ny = d.g.ny;
     const int64_t k = (int64_t)local * 256 + threadIdx.x;
-    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    float acc[4] = {0.f, 0.f, 0.f, 0.f};
     if (k < (int64_t)nx * ny) {
         const int j = (int)(k / nx), i = (int)(k % nx);
         const float2* xs = x + d.img_off;
@@ -175,14 +175,14 @@ __global__ void __launch_bounds__(256) k_image_update(const SliceDesc* __restric
         w.y += zn.y - xc.y;
         z[e] = zn;
         uz[e] = w;
-        const double ryx = yn.x - g.x, ryy = yn.y - g.y, rpx = yn.z - g.z, rpy = yn.w - g.w;
-        const double rzc = zn.x - xc.x, rzp = zn.y - xc.y;
-        acc[0] = ryx * ryx + ryy * ryy + rzc * rzc;
-        acc[1] = rpx * rpx + rpy * rpy + rzp * rzp;
-        const double dyx = yn.x - yo.x, dyy = yn.y - yo.y, dpx = yn.z - yo.z, dpy = yn.w - yo.w;
-        const double dzc = zn.x - zo.x, dzp = zn.y - zo.y;
-        acc[2] = dyx * dyx + dyy * dyy + dzc * dzc;
-        acc[3] = dpx * dpx + dpy * dpy + dzp * dzp;
+        const float ryx = yn.x - g.x, ryy = yn.y - g.y, rpx = yn.z - g.z, rpy = yn.w - g.w;
+        const float rzc = zn.x - xc.x, rzp = zn.y - xc.y;
+        acc[0] = fmaf(ryx, ryx, fmaf(ryy, ryy, rzc * rzc));
+        acc[1] = fmaf(rpx, rpx, fmaf(rpy, rpy, rzp * rzp));
+        const float dyx = yn.x - yo.x, dyy = yn.y - yo.y, dpx = yn.z - yo.z, dpy = yn.w - yo.w;
+        const float dzc = zn.x - zo.x, dzp = zn.y - zo.y;
+        acc[2] = fmaf(dyx, dyx, fmaf(dyy, dyy, dzc * dzc));
+        acc[3] = fmaf(dpx, dpx, fmaf(dpy, dpy, dzp * dzp));
     }
     block_partials<4>(acc, partial);
 }

@@ -194,7 +194,7 @@ __global__ void __launch_bounds__(256) k_bp_finalize(const SliceDesc* __restrict
     const int s = slice_of(pix, blockIdx.x, local);
     const SliceDesc& d = dsl[s];
     const int64_t k = (int64_t)local * 256 + threadIdx.x;
-    double dot_c = 0.0, dot_p = 0.0;
+    float dot_c = 0.f, dot_p = 0.f;
     if (k < (int64_t)d.g.nx * d.g.ny) {
         const int j = (int)(k / d.g.nx), i = (int)(k % d.g.nx);
         const int64_t e = d.img_off + k;

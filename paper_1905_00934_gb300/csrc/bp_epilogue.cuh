@@ -6,6 +6,7 @@
 #include <cuda_runtime.h>
 
 #include "dect_internal.cuh"
+#include "reduce.cuh"
 
 namespace dect {
 
@@ -59,7 +60,7 @@ __device__ __forceinline__ float4 grad_of(const float2* __restrict__ p, int nx, 
 template <int MODE>
 __device__ __forceinline__ void bp_pixel_epilogue(const SliceDesc& d, int i, int j, float2 r, const BpEpilogue& ep,
                                                   float2* __restrict__ out, float* __restrict__ planar, int nch,
-                                                  double& dot_c, double& dot_p) {
+                                                  float& dot_c, float& dot_p) {
     const int nx = d.g.nx, ny = d.g.ny;
     const int64_t off = d.img_off;
     const size_t e = (size_t)j * nx + i;
@@ -88,8 +89,8 @@ __device__ __forceinline__ void bp_pixel_epilogue(const SliceDesc& d, int i, int
             r.x += dt.x;
             r.y += dt.y;
         }
-        dot_c += (double)pc.x * (double)r.x;
-        dot_p += (double)pc.y * (double)r.y;
+        dot_c = fmaf(pc.x, r.x, dot_c);
+        dot_p = fmaf(pc.y, r.y, dot_p);
     }
     if (planar) {
         planar[e] = r.x;
@@ -99,28 +100,11 @@ __device__ __forceinline__ void bp_pixel_epilogue(const SliceDesc& d, int i, int
     }
 }
 
-// Deterministic block reduction of the partial <p, A p> sums into partial[2 * blockIdx.x + {0, 1}].
-__device__ __forceinline__ void bp_block_dots(double dot_c, double dot_p, double* __restrict__ partial) {
-    __shared__ double dred[2][32];
-    for (int o = 16; o > 0; o >>= 1) {
-        dot_c += __shfl_down_sync(0xffffffffu, dot_c, o);
-        dot_p += __shfl_down_sync(0xffffffffu, dot_p, o);
-    }
-    const int w = threadIdx.x / 32, l = threadIdx.x % 32;
-    if (l == 0) {
-        dred[0][w] = dot_c;
-        dred[1][w] = dot_p;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double sc = 0.0, sp = 0.0;
-        for (int k = 0; k < (int)(blockDim.x + 31) / 32; ++k) {
-            sc += dred[0][k];
-            sp += dred[1][k];
-        }
-        partial[2 * (size_t)blockIdx.x] = sc;
-        partial[2 * (size_t)blockIdx.x + 1] = sp;
-    }
+// Deterministic block reduction of the partial <p, A p> sums into partial[2 * blockIdx.x + {0, 1}]
+// (float within a warp, float64 across warps).
+__device__ __forceinline__ void bp_block_dots(float dot_c, float dot_p, double* __restrict__ partial) {
+    float v[2] = {dot_c, dot_p};
+    block_partials<2>(v, partial);
 }
 
 }  // namespace dect

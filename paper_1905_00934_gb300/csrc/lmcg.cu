@@ -10,7 +10,8 @@
 // so the trial point needs no projection. The step is accepted iff the subproblem objective decreases:
 // the change is summed per ray from the residual changes (udm.cu) and per pixel from the
 // augmented-Lagrangian change, so no two large costs are subtracted. mu is per slice and basis.
-// All scalars stay on the device; sums are per-block float64 partials added in a fixed order.
+// All scalars stay on the device; sums are per-block float64 partials added in a fixed order (the CG
+// dot products add in float within a warp; the accept test's changes are float64 throughout).
 #include <cuda_runtime.h>
 #include <math.h>
 
@@ -60,7 +61,7 @@ __global__ void __launch_bounds__(256) k_lm_grad(const SliceDesc* __restrict__ d
     const SliceDesc& d = dsl[s];
     const int nx = d.g.nx, ny = d.g.ny;
     const int64_t k = (int64_t)local * 256 + threadIdx.x;
-    double acc[1] = {0.0};
+    float acc[1] = {0.f};
     if (k < (int64_t)nx * ny) {
         const int j = (int)(k / nx), i = (int)(k % nx);
         const int64_t e = d.img_off + k;
@@ -77,7 +78,7 @@ __global__ void __launch_bounds__(256) k_lm_grad(const SliceDesc* __restrict__ d
         r[e] = -gr;
         p[e] = -gr;
         dlt[e] = 0.f;
-        acc[0] = (double)gr * gr;
+        acc[0] = gr * gr;
     }
     block_partials<1>(acc, part);
 }
@@ -92,7 +93,7 @@ __global__ void __launch_bounds__(256) k_lm_ap(const SliceDesc* __restrict__ dsl
     const SliceDesc& d = dsl[s];
     const int nx = d.g.nx, ny = d.g.ny;
     const int64_t k = (int64_t)local * 256 + threadIdx.x;
-    double acc[1] = {0.0};
+    float acc[1] = {0.f};
     if (k < (int64_t)nx * ny) {
         const int j = (int)(k / nx), i = (int)(k % nx);
         const int64_t e = d.img_off + k;
@@ -102,7 +103,7 @@ __global__ void __launch_bounds__(256) k_lm_ap(const SliceDesc* __restrict__ dsl
         const float pv = __ldg(ps + k);
         const float a = rt + (float)sc[s].rho[b] * (dtd1(ps, nx, ny, j, i) + pv);
         Ap[e] = a;
-        acc[0] = (double)pv * a;
+        acc[0] = pv * a;
     }
     block_partials<1>(acc, part);
 }
@@ -143,14 +144,14 @@ __global__ void __launch_bounds__(256) k_lm_cg(const SliceDesc* __restrict__ dsl
     const float alpha = (float)ls[s].alpha;
     const int64_t k = (int64_t)local * 256 + threadIdx.x;
     if (img) {
-        double acc[1] = {0.0};
+        float acc[1] = {0.f};
         if (k < (int64_t)d.g.nx * d.g.ny) {
             const int64_t e = d.img_off + k;
             dlt[e] = fmaf(alpha, p[e], dlt[e]);
             if (!last) {
                 const float rn = fmaf(-alpha, Ap[e], r[e]);
                 r[e] = rn;
-                acc[0] = (double)rn * rn;
+                acc[0] = rn * rn;
             }
         }
         block_partials<1>(acc, part);

@@ -1,5 +1,6 @@
 // Deterministic reductions: each block writes its partial sums (float64) to a slot indexed by its block
 // number (block_partials), and one block per slice adds that slice's slots in a fixed order (slice_sum).
+// Every order is fixed by the launch shape, so results are bitwise reproducible.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -18,6 +19,25 @@ __device__ __forceinline__ void block_partials(double (&v)[N], double* __restric
     if (threadIdx.x < N) {
         double t = 0.0;
         for (int k = 0; k < (int)blockDim.x / 32; ++k) t += red[threadIdx.x][k];
+        out[N * (size_t)blockIdx.x + threadIdx.x] = t;
+    }
+}
+
+// The same slots from float per-thread values: each warp adds its 32 values in float (a few ulps of the
+// warp sum), the warp sums are added in float64. Keeps float64 work (slow on this GPU) off the
+// per-element path of element-wise kernels.
+template <int N>
+__device__ __forceinline__ void block_partials(float (&v)[N], double* __restrict__ out) {
+    __shared__ double redf[N][32];
+    for (int q = 0; q < N; ++q)
+        for (int o = 16; o > 0; o >>= 1) v[q] += __shfl_down_sync(0xffffffffu, v[q], o);
+    const int w = threadIdx.x / 32;
+    if ((threadIdx.x & 31) == 0)
+        for (int q = 0; q < N; ++q) redf[q][w] = (double)v[q];
+    __syncthreads();
+    if (threadIdx.x < N) {
+        double t = 0.0;
+        for (int k = 0; k < (int)blockDim.x / 32; ++k) t += redf[threadIdx.x][k];
         out[N * (size_t)blockIdx.x + threadIdx.x] = t;
     }
 }

@@ -199,7 +199,7 @@ __global__ void __launch_bounds__(kRaysPerBlock) k_udm_admm(const SliceDesc* __r
     const SliceDesc& d = dsl[s];
     const int64_t n = (int64_t)d.g.nv * d.g.nb;
     const int64_t r = (int64_t)local * kRaysPerBlock + threadIdx.x;
-    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    float acc[4] = {0.f, 0.f, 0.f, 0.f};
     if (r < n) {
         const int64_t e = d.sino_off + r;
         const float4 m = __ldg(meas + e);
@@ -227,23 +227,12 @@ __global__ void __launch_bounds__(kRaysPerBlock) k_udm_admm(const SliceDesc* __r
         u.y += rp;
         st2(ua + e, u);
         const float dc = an.x - a_old.x, dp = an.y - a_old.y;
-        acc[0] = (double)rc * rc;
-        acc[1] = (double)rp * rp;
-        acc[2] = (double)dc * dc;
-        acc[3] = (double)dp * dp;
+        acc[0] = rc * rc;
+        acc[1] = rp * rp;
+        acc[2] = dc * dc;
+        acc[3] = dp * dp;
     }
-    __shared__ double red[4][kRaysPerBlock / 32];
-    for (int q = 0; q < 4; ++q)
-        for (int o = 16; o > 0; o >>= 1) acc[q] += __shfl_down_sync(0xffffffffu, acc[q], o);
-    const int w = threadIdx.x / 32;
-    if ((threadIdx.x & 31) == 0)
-        for (int q = 0; q < 4; ++q) red[q][w] = acc[q];
-    __syncthreads();
-    if (threadIdx.x < 4) {
-        double t = 0.0;
-        for (int k = 0; k < kRaysPerBlock / 32; ++k) t += red[threadIdx.x][k];
-        partial[4 * (size_t)blockIdx.x + threadIdx.x] = t;
-    }
+    block_partials<4>(acc, partial);
 }
 
 // Initial decomposition: rho = (0, rho_p), v = 0, from a = (m_l / abar, 0), mu = mu0.
