@@ -140,7 +140,7 @@ def joseph_weight_count(g) -> int:
 # dram bytes per launch of the backprojector sweep at the bench workload (8 slices) and the view-group
 # count it was captured with (profiles/k_bp_sweep_512x720x1024.txt); reported only when the solver
 # runs that count, since the partial images it writes scale with it
-SWEEP_TRAFFIC_B8 = (217.4e6, 8)
+SWEEP_TRAFFIC_B8 = (216.9e6, 8)
 
 
 # ------------------------------------------------------------------------------------------------
@@ -413,6 +413,19 @@ def run_dect(args):
     elif hbm is not None:
         roof = dict(kernel=top, bound="hbm", traffic=None, avg_launch_ms=avg_ms, **hbm)
     phases = {p: {"ms_per_iter": prof[p][0] / 10, "launches_per_iter": prof[p][1] / 10} for p in prof}
+    # the HBM-bound phases (data read and written once per iteration; 8 slices exceed L2): the four
+    # element-wise kernels of an iteration (b = a + u^a - R x: 32 B/ray; x, R x += alpha p, q: 24 B/pixel
+    # + 24 B/ray; y, z, u^y, u^z of Eq. 9-11 with x: 104 B/pixel; the dual rescale moves nothing when
+    # rho stays) and the two backprojector finalize passes (C partial images of 8 B, plus 64 B/pixel of
+    # epilogue images for r0 and 16 B/pixel for A p)
+    C = st0["bp_view_groups"]
+    hbm_phase_bytes = {"update": B * (56 * M + 128 * Np), "bp_finalize": B * ((16 * C + 80) * Np)}
+    hbm_phases = {}
+    for p_, nbytes in hbm_phase_bytes.items():
+        ms = prof[p_][0] / 10
+        gbs = nbytes / (ms / 1e3) / 1e9
+        hbm_phases[p_] = {"algorithmic_bytes_per_iter": nbytes, "ms_per_iter": ms, "achieved_gbs": gbs,
+                          "peak_gbs": peak, "frac": gbs / peak}
 
     if rank == 0:
         line = {
@@ -428,7 +441,8 @@ def run_dect(args):
                        "plain_graph_autotuned_slices_per_s": (ws * B / (plain_best_ms / 1e3)) if plain_best_ms
                        else None,
                        "plain": "single-slice solvers one after another; eager launches, occupancy view groups",
-                       "pe_gate": gate, "phases": phases, "scheme_comparison": comparison},
+                       "pe_gate": gate, "phases": phases, "hbm_phases": hbm_phases,
+                       "scheme_comparison": comparison},
             "clocks": clocks,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                     "steps": e2e_steps},

@@ -41,6 +41,7 @@ __global__ void __launch_bounds__(256) k_rs_reduce(const double* __restrict__ pa
     if (threadIdx.x == 0) {
         for (int c = 0; c < 2; ++c) {
             if (!first) sc[s].beta[c] = sc[s].rs[c] > 0.0 ? v[c] / sc[s].rs[c] : 0.0;
+            sc[s].beta_f[c] = (float)sc[s].beta[c];
             sc[s].rs[c] = v[c];
         }
     }
@@ -56,6 +57,7 @@ __global__ void __launch_bounds__(256) k_alpha(const double* __restrict__ part, 
         for (int c = 0; c < 2; ++c) {
             sc[s].pAp[c] = v[c];
             sc[s].alpha[c] = v[c] > 0.0 ? sc[s].rs[c] / v[c] : 0.0;
+            sc[s].alpha_f[c] = (float)sc[s].alpha[c];
         }
     }
 }
@@ -68,12 +70,15 @@ __global__ void __launch_bounds__(256) k_cg_update(const SliceDesc* __restrict__
                                                    float2* __restrict__ r, const float2* __restrict__ Ap,
                                                    S2* __restrict__ Rx, const S2* __restrict__ q, int last) {
     int local;
-    if ((int)blockIdx.x < nblk_pix) {
-        const int s = slice_of(pix, blockIdx.x, local);
+    const bool img = (int)blockIdx.x < nblk_pix;
+    const int sb = img ? slice_of(pix, blockIdx.x, local) : slice_of(rays, blockIdx.x - nblk_pix, local);
+    const float2 al = make_float2(sc[sb].alpha_f[0], sc[sb].alpha_f[1]);
+    if (img) {
+        const int s = sb;
         const SliceDesc& d = dsl[s];
         const int64_t k = (int64_t)local * 256 + threadIdx.x;
         if (k >= (int64_t)d.g.nx * d.g.ny) return;
-        const float ac = (float)sc[s].alpha[0], ap = (float)sc[s].alpha[1];
+        const float ac = al.x, ap = al.y;
         const int64_t e = d.img_off + k;
         const float2 pv = __ldg(p + e);
         float2 xv = x[e];
@@ -88,11 +93,11 @@ __global__ void __launch_bounds__(256) k_cg_update(const SliceDesc* __restrict__
             r[e] = rv;
         }
     } else {
-        const int s = slice_of(rays, blockIdx.x - nblk_pix, local);
+        const int s = sb;
         const SliceDesc& d = dsl[s];
         const int64_t k = (int64_t)local * 256 + threadIdx.x;
         if (k >= (int64_t)d.g.nv * d.g.nb) return;
-        const float ac = (float)sc[s].alpha[0], ap = (float)sc[s].alpha[1];
+        const float ac = al.x, ap = al.y;
         const int64_t e = d.sino_off + k;
         const float2 qv = ldg2(q + e);
         float2 rx = ld2(Rx + e);
@@ -108,11 +113,12 @@ __global__ void __launch_bounds__(256) k_cg_p(const SliceDesc* __restrict__ dsl,
                                               float2* __restrict__ p) {
     int local;
     const int s = slice_of(pix, blockIdx.x, local);
+    const float2 be = make_float2(sc[s].beta_f[0], sc[s].beta_f[1]);
     const SliceDesc& d = dsl[s];
     const int64_t k = (int64_t)local * 256 + threadIdx.x;
     if (k >= (int64_t)d.g.nx * d.g.ny) return;
     const int64_t e = d.img_off + k;
-    const float bc = (float)sc[s].beta[0], bp = (float)sc[s].beta[1];
+    const float bc = be.x, bp = be.y;
     const float2 a = __ldg(sv + e);
     float2 pv = p[e];
     pv.x = fmaf(bc, pv.x, a.x);
@@ -141,6 +147,7 @@ __global__ void __launch_bounds__(256) k_image_update(const SliceDesc* __restric
     const int nx = d.g.nx, ny = d.g.ny;
     const int64_t k = (int64_t)local * 256 + threadIdx.x;
     float acc[4] = {0.f, 0.f, 0.f, 0.f};
+    const float2 tau = make_float2((float)lam_c / sc[s].rho_f[0], (float)lam_p / sc[s].rho_f[1]);  // lambda / rho
     if (k < (int64_t)nx * ny) {
         const int j = (int)(k / nx), i = (int)(k % nx);
         const float2* xs = x + d.img_off;
@@ -157,7 +164,7 @@ __global__ void __launch_bounds__(256) k_image_update(const SliceDesc* __restric
             g.y = uu.x - xc.x;
             g.w = uu.y - xc.y;
         }
-        const float tc = (float)(lam_c / sc[s].rho[0]), tp = (float)(lam_p / sc[s].rho[1]);
+        const float tc = tau.x, tp = tau.y;
         const float4 yo = y[e];
         float4 u = uy[e];
         const float4 yn = make_float4(shrink(g.x - u.x, tc), shrink(g.y - u.y, tc), shrink(g.z - u.z, tp),
@@ -208,6 +215,8 @@ __global__ void __launch_bounds__(256) k_rho_update(const double* __restrict__ p
             else if (rd > mu_b * rp) f = 1.0 / tau;
             sc[s].factor[c] = f;
             sc[s].rho[c] *= f;
+            sc[s].rho_f[c] = (float)sc[s].rho[c];
+            sc[s].ifactor_f[c] = (float)(1.0 / f);
         }
         sc[s].iteration += 1;
     }
@@ -222,9 +231,8 @@ __global__ void __launch_bounds__(256) k_dual_rescale(const SliceDesc* __restric
     int local;
     const bool img = (int)blockIdx.x < nblk_pix;
     const int s = img ? slice_of(pix, blockIdx.x, local) : slice_of(rays, blockIdx.x - nblk_pix, local);
-    const double fc = sc[s].factor[0], fp = sc[s].factor[1];
-    if (fc == 1.0 && fp == 1.0) return;
-    const float gc = (float)(1.0 / fc), gp = (float)(1.0 / fp);
+    const float gc = sc[s].ifactor_f[0], gp = sc[s].ifactor_f[1];  // exactly 1, 1/tau or tau
+    if (gc == 1.0f && gp == 1.0f) return;
     const SliceDesc& d = dsl[s];
     const int64_t k = (int64_t)local * 256 + threadIdx.x;
     if (img) {
@@ -359,6 +367,9 @@ __global__ void k_reset_scalars(SliceScalars* __restrict__ sc, int B, double rho
     v.rho[0] = rho_c;
     v.rho[1] = rho_p;
     v.factor[0] = v.factor[1] = 1.0;
+    v.rho_f[0] = (float)rho_c;
+    v.rho_f[1] = (float)rho_p;
+    v.ifactor_f[0] = v.ifactor_f[1] = 1.0f;
     v.xi_num[0] = v.xi_num[1] = nan("");
     v.xi_den[0] = v.xi_den[1] = nan("");
     sc[s] = v;

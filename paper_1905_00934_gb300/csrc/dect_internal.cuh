@@ -82,6 +82,9 @@ struct SliceScalars {
     double r_pri[2];
     double r_dual[2];
     double xi_num[2], xi_den[2];
+    // float32 copies for the element-wise kernels (float64 is slow on this GPU): CG step and direction
+    // scalars, rho, and the factor the scaled duals are divided by this iteration
+    float alpha_f[2], beta_f[2], rho_f[2], ifactor_f[2];
     int32_t iteration;
     int32_t pad;
 };

@@ -74,7 +74,7 @@ __global__ void __launch_bounds__(256) k_lm_grad(const SliceDesc* __restrict__ d
         const float2 dt = div_t(t_ij, t_im, t_jm, nx, ny, j, i);
         const float2 xc = __ldg(ep.x + e), z = __ldg(ep.z + e), uz = __ldg(ep.uz + e);
         const float epi = b ? (z.y + uz.y - xc.y + dt.y) : (z.x + uz.x - xc.x + dt.x);
-        const float gr = rt - (float)sc[s].rho[b] * epi;
+        const float gr = rt - sc[s].rho_f[b] * epi;
         r[e] = -gr;
         p[e] = -gr;
         dlt[e] = 0.f;
@@ -101,7 +101,7 @@ __global__ void __launch_bounds__(256) k_lm_ap(const SliceDesc* __restrict__ dsl
         for (int c = 0; c < C; ++c) rt += __ldg(partial + c * stride + e);
         const float* ps = p + d.img_off;
         const float pv = __ldg(ps + k);
-        const float a = rt + (float)sc[s].rho[b] * (dtd1(ps, nx, ny, j, i) + pv);
+        const float a = rt + sc[s].rho_f[b] * (dtd1(ps, nx, ny, j, i) + pv);
         Ap[e] = a;
         acc[0] = pv * a;
     }

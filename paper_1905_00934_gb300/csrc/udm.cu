@@ -28,7 +28,7 @@ namespace dect {
 struct RayIn {
     float mh, ml, wh, wl;
     float vc_hi, vc_lo, vp_hi, vp_lo;
-    double rc, rp;
+    float rc, rp;
 };
 
 // v = a - b as hi + lo with hi = fl(a - b) and lo its exact rounding error (two-sum)
@@ -123,7 +123,7 @@ __device__ __forceinline__ float diff_of_products(float a, float b, float c, flo
 __device__ void lm_ray(const float4* __restrict__ t1, const float4* __restrict__ t2, int ne, const RayIn& in,
                        int iters, LmState& s) {
     const float tm_h = expf(-in.mh), tm_l = expf(-in.ml);
-    const float wh = in.wh, wl = in.wl, rc = (float)in.rc, rp = (float)in.rp;
+    const float wh = in.wh, wl = in.wl, rc = in.rc, rp = in.rp;
     for (int it = 0; it < iters; ++it) {
         float sh, sl, shc, shp, slc, slp;
         spectral_sums_jac(t1, t2, ne, s.ac, s.ap, sh, sl, shc, shp, slc, slp);
@@ -213,8 +213,8 @@ __global__ void __launch_bounds__(kRaysPerBlock) k_udm_admm(const SliceDesc* __r
         in.wl = m.w;
         split_diff(rx.x, u.x, in.vc_hi, in.vc_lo);
         split_diff(rx.y, u.y, in.vp_hi, in.vp_lo);
-        in.rc = sc[s].rho[0];
-        in.rp = sc[s].rho[1];
+        in.rc = sc[s].rho_f[0];
+        in.rp = sc[s].rho_f[1];
         LmState st{a_old.x, a_old.y, mu[e], DECT_RAY_ACCEPTED};
         lm_ray(t1, t2, sp.ne, in, iters, st);
         // the stored (possibly rounded) a is what the dual update and the residuals see
@@ -259,8 +259,8 @@ __global__ void __launch_bounds__(kRaysPerBlock) k_udm_init(const SliceDesc* __r
     in.wh = m.z;
     in.wl = m.w;
     in.vc_hi = in.vc_lo = in.vp_hi = in.vp_lo = 0.0f;
-    in.rc = 0.0;
-    in.rp = rho_p;
+    in.rc = 0.0f;
+    in.rp = (float)rho_p;
     LmState st{m.y / abar, 0.0f, mu0, DECT_RAY_ACCEPTED};
     lm_ray(t1, t2, sp.ne, in, iters, st);
     st2(a + e, make_float2(st.ac, 0.0f));
@@ -288,8 +288,8 @@ __global__ void __launch_bounds__(kRaysPerBlock) k_udm_rays(SpecDev sp, int64_t 
     in.vc_hi = __ldg(vc + r);
     in.vp_hi = __ldg(vp + r);
     in.vc_lo = in.vp_lo = 0.0f;
-    in.rc = rho_c;
-    in.rp = rho_p;
+    in.rc = (float)rho_c;
+    in.rp = (float)rho_p;
     LmState st{ac[r], ap[r], mu[r], DECT_RAY_ACCEPTED};
     lm_ray(t1, t2, sp.ne, in, iters, st);
     ac[r] = st.ac;
