@@ -80,14 +80,18 @@ __global__ void __launch_bounds__(256) k_cg_update(const SliceDesc* __restrict__
         if (k >= (int64_t)d.g.nx * d.g.ny) return;
         const float ac = al.x, ap = al.y;
         const int64_t e = d.img_off + k;
+        // loads before stores (independent addresses; keeps them all in flight together)
         const float2 pv = __ldg(p + e);
         float2 xv = x[e];
+        float2 av = make_float2(0.f, 0.f), rv = make_float2(0.f, 0.f);
+        if (!last) {
+            av = __ldg(Ap + e);
+            rv = r[e];
+        }
         xv.x = fmaf(ac, pv.x, xv.x);
         xv.y = fmaf(ap, pv.y, xv.y);
         x[e] = xv;
         if (!last) {
-            const float2 av = __ldg(Ap + e);
-            float2 rv = r[e];
             rv.x = fmaf(-ac, av.x, rv.x);
             rv.y = fmaf(-ap, av.y, rv.y);
             r[e] = rv;
@@ -152,21 +156,16 @@ __global__ void __launch_bounds__(256) k_image_update(const SliceDesc* __restric
         const int j = (int)(k / nx), i = (int)(k % nx);
         const float2* xs = x + d.img_off;
         const int64_t e = d.img_off + k;
+        // every load first (they are independent), then the arithmetic and the stores
         const float2 xc = __ldg(xs + k);
-        float4 g = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (i < nx - 1) {
-            const float2 rr = __ldg(xs + k + 1);
-            g.x = rr.x - xc.x;
-            g.z = rr.y - xc.y;
-        }
-        if (j < ny - 1) {
-            const float2 uu = __ldg(xs + k + nx);
-            g.y = uu.x - xc.x;
-            g.w = uu.y - xc.y;
-        }
-        const float tc = tau.x, tp = tau.y;
+        const float2 rr = i < nx - 1 ? __ldg(xs + k + 1) : xc;
+        const float2 uu = j < ny - 1 ? __ldg(xs + k + nx) : xc;
         const float4 yo = y[e];
         float4 u = uy[e];
+        const float2 zo = z[e];
+        float2 w = uz[e];
+        const float4 g = make_float4(rr.x - xc.x, uu.x - xc.x, rr.y - xc.y, uu.y - xc.y);
+        const float tc = tau.x, tp = tau.y;
         const float4 yn = make_float4(shrink(g.x - u.x, tc), shrink(g.y - u.y, tc), shrink(g.z - u.z, tp),
                                       shrink(g.w - u.w, tp));
         u.x += yn.x - g.x;
@@ -175,8 +174,6 @@ __global__ void __launch_bounds__(256) k_image_update(const SliceDesc* __restric
         u.w += yn.w - g.w;
         y[e] = yn;
         uy[e] = u;
-        const float2 zo = z[e];
-        float2 w = uz[e];
         const float2 zn = make_float2(fmaxf(0.f, xc.x - w.x), fmaxf(0.f, xc.y - w.y));
         w.x += zn.x - xc.x;
         w.y += zn.y - xc.y;
@@ -239,12 +236,12 @@ __global__ void __launch_bounds__(256) k_dual_rescale(const SliceDesc* __restric
         if (k >= (int64_t)d.g.nx * d.g.ny) return;
         const int64_t e = d.img_off + k;
         float4 u = uy[e];
+        float2 w = uz[e];
         u.x *= gc;
         u.y *= gc;
         u.z *= gp;
         u.w *= gp;
         uy[e] = u;
-        float2 w = uz[e];
         w.x *= gc;
         w.y *= gp;
         uz[e] = w;

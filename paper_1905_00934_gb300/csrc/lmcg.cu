@@ -147,9 +147,11 @@ __global__ void __launch_bounds__(256) k_lm_cg(const SliceDesc* __restrict__ dsl
         float acc[1] = {0.f};
         if (k < (int64_t)d.g.nx * d.g.ny) {
             const int64_t e = d.img_off + k;
-            dlt[e] = fmaf(alpha, p[e], dlt[e]);
+            const float pv = p[e], dv = dlt[e];
+            const float av = last ? 0.f : Ap[e], rv = last ? 0.f : r[e];  // loads before stores
+            dlt[e] = fmaf(alpha, pv, dv);
             if (!last) {
-                const float rn = fmaf(-alpha, Ap[e], r[e]);
+                const float rn = fmaf(-alpha, av, rv);
                 r[e] = rn;
                 acc[0] = rn * rn;
             }
