@@ -141,6 +141,9 @@ def joseph_weight_count(g) -> int:
 # count it was captured with (profiles/k_bp_sweep_512x720x1024.txt); reported only when the solver
 # runs that count, since the partial images it writes scale with it
 SWEEP_TRAFFIC_B8 = (216.9e6, 8)
+# what bounds the sweep on chip, from its full-set capture (profiles/k_bp_sweep_512x720x1024.txt)
+SWEEP_LIMITER = {"resource": "shared-memory throughput and issue", "l1tex_throughput_pct": 82.7,
+                 "issue_active_pct": 66.3, "shared_wavefronts_per_slice": 9.66e7}
 
 
 # ------------------------------------------------------------------------------------------------
@@ -409,7 +412,8 @@ def run_dect(args):
                                                     and st0["bp_view_groups"] == SWEEP_TRAFFIC_B8[1]) else None,
                 "peak_kind": f"derived: {n_sm} SMs x 128 FP32 lanes x 2 flop x max SM clock",
                 "avg_launch_ms": avg_ms, "algorithmic_flops_per_launch": alg_flops[top],
-                "weights_per_slice_channel": nnz, "hbm": hbm}
+                "weights_per_slice_channel": nnz, "hbm": hbm,
+                "limiter": SWEEP_LIMITER if top == "backproject" else None}
     elif hbm is not None:
         roof = dict(kernel=top, bound="hbm", traffic=None, avg_launch_ms=avg_ms, **hbm)
     phases = {p: {"ms_per_iter": prof[p][0] / 10, "launches_per_iter": prof[p][1] / 10} for p in prof}
