@@ -228,7 +228,13 @@ def run_dect(args):
 
     import __graft_entry__
 
-    __graft_entry__.build()
+    # one build per node: local rank 0 compiles while the other ranks wait, then every rank loads it
+    if ws == 1 or local == 0:
+        __graft_entry__.build()
+    if ws > 1:
+        torch.distributed.barrier()
+        if local != 0:
+            __graft_entry__.build()  # up to date: only checks and loads
     from paper_1905_00934_gb300 import Geometry, Solver, Spectra, dect, shard
     from synth.workloads import BAGGAGE_KAPPA, baggage_fan_case
 
