@@ -17,7 +17,8 @@ Readings where the paper is silent (each listed in the design notes):
     Eq. 12 operator R^T R + D^T D + I, H = 1 / (Re F[R^T R delta] + |F[D]|^2 + 1)
     on a zero-padded grid (power of two >= 2N per axis), F[R^T R delta] the DFT
     of the point response at the centre pixel (clamped >= 0). At low frequency
-    R^T R ~ 1/|w|, so H behaves as the ramp filter the paper names.
+    R^T R ~ 1/|w|, so H behaves as the ramp filter the paper names. The plain ramp filter
+    1 / (K/|w| + 1) is the alternative (PRECOND_RAMP), for the preconditioner comparison.
   * adaptive rho (Boyd et al. 2011, Sec. 3.4.1): mu_b = 10, tau = 2, per basis,
     r_pri = ||[a; y; z] - [R; D; I] x||, r_dual = rho ||[a; y; z]_new - [a; y; z]_old||;
     when rho changes the scaled duals are divided by the same factor.
@@ -69,6 +70,9 @@ def xi_db(x: np.ndarray, truth: np.ndarray) -> float:
 # ----------------------------------------------------------------------------
 # preconditioner (Sec. 3.3)
 
+PRECOND_NONE, PRECOND_CIRCULANT, PRECOND_RAMP = 0, 1, 2
+
+
 def pad_size(n: int) -> int:
     p = 1
     while p < 2 * n:
@@ -83,19 +87,42 @@ def point_response(geom) -> np.ndarray:
     return projector.backproject(geom, projector.project(geom, d))
 
 
-def precond_response(geom, with_grad: bool = True) -> np.ndarray:
-    """H on the [Py][Px] padded frequency grid (real, > 0)."""
+def point_response_dft(geom) -> np.ndarray:
+    """Re F[R^T R delta] on the [Py][Px] padded grid, the point response centred at grid index
+    (0, 0) (wrapped), clamped >= 0."""
     py, px = pad_size(geom.ny), pad_size(geom.nx)
     psf = point_response(geom)
     grid = np.zeros((py, px))
     jj = (np.arange(geom.ny) - geom.ny // 2) % py
     ii = (np.arange(geom.nx) - geom.nx // 2) % px
     grid[np.ix_(jj, ii)] = psf
-    phat = np.maximum(np.fft.fft2(grid).real, 0.0)
+    return np.maximum(np.fft.fft2(grid).real, 0.0)
+
+
+def precond_response(geom, with_grad: bool = True) -> np.ndarray:
+    """H on the [Py][Px] padded frequency grid (real, > 0)."""
+    phat = point_response_dft(geom)
+    py, px = phat.shape
     wy = 2.0 * np.pi * np.arange(py) / py
     wx = 2.0 * np.pi * np.arange(px) / px
     dhat = 4.0 * np.sin(wy / 2.0)[:, None] ** 2 + 4.0 * np.sin(wx / 2.0)[None, :] ** 2
     return 1.0 / (phat + (dhat if with_grad else 0.0) + 1.0)
+
+
+def ramp_response(geom) -> np.ndarray:
+    """The plain ramp filter as the preconditioner (Sec. 3.3 names a ramp / high-pass filter):
+    R^T R replaced by its asymptotic form K / |w| and D^T D dropped, H = 1 / (K / |w| + 1) =
+    |w| / (K + |w|). |w| is the wrapped radial frequency in radians per pixel, floored at the
+    first non-zero grid frequency 2 pi / max(Px, Py) so that H(0) > 0. K is read off the point
+    response at w = (0, pi/4): K = (pi/4) Re F[R^T R delta](0, Px/8)."""
+    phat = point_response_dft(geom)
+    py, px = phat.shape
+    K = phat[0, px // 8] * (np.pi / 4.0)
+    ky, kx = np.arange(py), np.arange(px)
+    wy = 2.0 * np.pi * np.minimum(ky, py - ky) / py
+    wx = 2.0 * np.pi * np.minimum(kx, px - kx) / px
+    w = np.maximum(np.hypot(wy[:, None], wx[None, :]), 2.0 * np.pi / max(px, py))
+    return 1.0 / (K / w + 1.0)
 
 
 def apply_precond(H: np.ndarray, r: np.ndarray) -> np.ndarray:
@@ -119,7 +146,7 @@ class Params:
     tau: float = 2.0                   # residual-balancing factor
     lm_mu0: float = 1e-3               # initial LM damping
     adapt_rho: bool = True
-    precondition: bool = True
+    precondition: int = 1              # PRECOND_NONE (plain CG), PRECOND_CIRCULANT or PRECOND_RAMP
     # initialisation
     kappa: float = 1e-2                # x_p0 = kappa * x_c0
     init_udm_iters: int = 10
@@ -143,8 +170,14 @@ class Problem:
         self.w_h = np.asarray(w_h, dtype=np.float64).reshape(geom.n_views, geom.n_bins)
         self.w_l = np.asarray(w_l, dtype=np.float64).reshape(geom.n_views, geom.n_bins)
         self.params = params
-        self.H = precond_response(geom, True) if params.precondition else None
-        self.H_init = precond_response(geom, False) if params.precondition else None
+        mode = int(params.precondition)
+        if mode not in (PRECOND_NONE, PRECOND_CIRCULANT, PRECOND_RAMP):
+            raise ValueError(f"precondition must be 0, 1 or 2, got {params.precondition}")
+        self.H = self.H_init = None
+        if mode == PRECOND_CIRCULANT:
+            self.H, self.H_init = precond_response(geom, True), precond_response(geom, False)
+        elif mode == PRECOND_RAMP:
+            self.H = self.H_init = ramp_response(geom)
         self.count = Counters()
 
     # operators on both bases, with Table 1 counting

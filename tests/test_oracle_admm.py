@@ -86,7 +86,7 @@ def _eq12_dense(g):
     return Rm, Dm, Rm.T @ Rm + Dm.T @ Dm + np.eye(g.n_pixels)
 
 
-@pytest.mark.parametrize("precondition", [False, True])
+@pytest.mark.parametrize("precondition", [admm.PRECOND_NONE, admm.PRECOND_CIRCULANT, admm.PRECOND_RAMP])
 def test_pcg_converges_to_dense_cholesky_solution(precondition):
     g = G.parallel_geometry(8, 9, 12, 0.1, 0.1, angle0_rad=0.05)
     Rm, Dm, A = _eq12_dense(g)
@@ -214,3 +214,70 @@ def test_small_case_objective_and_residuals_trend():
     assert np.all(st.r_pri < r0)
     # the Compton estimate improves on the initial image over the first iterations
     assert admm.xi_db(st.x[0], c["truth_c"]) < admm.xi_db(xc0, c["truth_c"]) + 3.0
+
+
+@pytest.mark.parametrize("nx,nv,nb,dx,du", [(48, 96, 72, 0.1, 0.1), (64, 90, 96, 0.1, 0.1),
+                                           (40, 60, 64, 0.1, 0.15), (32, 120, 80, 0.05, 0.04)])
+def test_point_response_follows_the_continuous_parallel_beam_constant(nx, nv, nb, dx, du):
+    # continuous parallel beam, V views over pi, pixel dx, bin pitch du: the backprojection of the
+    # projection of a point is (V / pi) (dx^4 / du) / r at distance r (the angular integral of
+    # delta(r cos phi) over [0, pi) is 1 / r), whose 2D Fourier transform on the pixel grid is
+    # 2 V dx^3 / (du |w|). The discrete point response at w = pi/4 (the ramp constant K) carries
+    # that constant up to the Joseph interpolation footprint (a few per cent at pi/4).
+    g = G.parallel_geometry(nx, nv, nb, dx, du)
+    phat = admm.point_response_dft(g)
+    K = phat[0, phat.shape[1] // 8] * np.pi / 4
+    assert K == pytest.approx(2 * nv * dx**3 / du, rel=0.12)
+    # same constant along y (the operator is isotropic)
+    assert phat[phat.shape[0] // 8, 0] == pytest.approx(phat[0, phat.shape[1] // 8], rel=1e-9)
+
+
+def test_ramp_response_shape():
+    g = G.parallel_geometry(32, 120, 80, 0.05, 0.04)
+    H = admm.ramp_response(g)
+    py, px = H.shape
+    assert (py, px) == (64, 64)
+    assert np.all(H > 0) and np.all(H < 1)
+    # real and even in frequency, and radial: equal wherever |w| is equal
+    assert np.allclose(H, np.roll(H[::-1, ::-1], 1, axis=(0, 1)))
+    assert np.allclose(H, H.T)
+    assert H[3, 4] == pytest.approx(H[0, 5]) and H[60, 3] == pytest.approx(H[5, 0])
+    # increasing with |w| along the axis up to Nyquist; DC takes the first non-zero frequency
+    assert np.all(np.diff(H[0, 1 : px // 2 + 1]) > 0)
+    assert H[0, 0] == H[0, 1]
+    # at the calibration frequency (0, pi/4) it equals the circulant model without D^T D
+    phat = admm.point_response_dft(g)
+    assert H[0, px // 8] == pytest.approx(1.0 / (phat[0, px // 8] + 1.0), rel=1e-12)
+    assert H[0, px // 8] == pytest.approx(admm.precond_response(g, False)[0, px // 8], rel=1e-12)
+    # H = |w| / (K + |w|) at a diagonal frequency, with |w| written out
+    K = phat[0, px // 8] * np.pi / 4
+    w = np.hypot(2 * np.pi * 5 / py, 2 * np.pi * 7 / px)
+    assert H[5, px - 7] == pytest.approx(w / (K + w), rel=1e-12)
+
+
+def test_ramp_preconditioner_ranks_between_none_and_circulant():
+    # R^T R-dominated operator (many views): the plain ramp speeds CG up over no preconditioner,
+    # the full circulant model (which also carries D^T D) more
+    g = G.parallel_geometry(32, 360, 48, 0.1, 0.1)
+    rng = np.random.default_rng(2)
+    xt = rng.uniform(size=(32, 32))
+    errs = {}
+    for pc in (admm.PRECOND_NONE, admm.PRECOND_CIRCULANT, admm.PRECOND_RAMP):
+        P = admm.Params(precondition=pc)
+        z = np.zeros((360, 48))
+        prob = admm.Problem(g, spectra.SpectralTables(), z, z, z + 1, z + 1, P)
+        st = admm.state_from_image(prob, np.zeros((32, 32)), np.zeros((32, 32)))
+        st.a = np.stack([projector.project(g, xt)] * 2)
+        ref = st.copy()
+        admm.pcg_x_update(prob, ref, 400, True, prob.H)
+        admm.pcg_x_update(prob, st, 8, True, prob.H)
+        errs[pc] = np.linalg.norm(st.x - ref.x) / np.linalg.norm(ref.x)
+    assert errs[admm.PRECOND_CIRCULANT] < 0.1 * errs[admm.PRECOND_RAMP]
+    assert errs[admm.PRECOND_RAMP] < 0.2 * errs[admm.PRECOND_NONE]
+
+
+def test_precondition_mode_is_validated():
+    g = G.parallel_geometry(8, 9, 12, 0.1, 0.1)
+    z = np.zeros((9, 12))
+    with pytest.raises(ValueError):
+        admm.Problem(g, spectra.SpectralTables(), z, z, z + 1, z + 1, admm.Params(precondition=3))
