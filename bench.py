@@ -470,7 +470,8 @@ def run_dect(args):
 def run_study(args):
     """The paper's evaluation protocol on the synthetic workload (Sec. 4, Fig. 2): xi_c, xi_p (Eq. 14,
     mean over the batch) every 10 iterations and the device time per iteration, for UDM(m)-PCG(n)
-    variants, the same with plain CG (no preconditioner) and the LM(m) x CG(n) splitting."""
+    variants (circulant preconditioner), with the plain ramp-filter preconditioner, with plain CG (no
+    preconditioner) and the LM(m) x CG(n) splitting."""
     import torch
 
     import __graft_entry__
@@ -489,6 +490,8 @@ def run_study(args):
     f32 = lambda a: torch.tensor(np.ascontiguousarray(a), dtype=torch.float32, device=dev)
     configs = [("UDM1-PCG1", dict(m_udm=1, n_pcg=1)), ("UDM1-PCG2", dict(m_udm=1, n_pcg=2)),
                ("UDM2-PCG1", dict(m_udm=2, n_pcg=1)), ("UDM1-PCG5", dict(m_udm=1, n_pcg=5)),
+               ("UDM1-PCG1 ramp", dict(m_udm=1, n_pcg=1, precondition=dect.PRECOND_RAMP)),
+               ("UDM1-PCG5 ramp", dict(m_udm=1, n_pcg=5, precondition=dect.PRECOND_RAMP)),
                ("UDM1-CG1", dict(m_udm=1, n_pcg=1, precondition=0)),
                ("UDM1-CG5", dict(m_udm=1, n_pcg=5, precondition=0)),
                ("LM1xCG1", dict(m_udm=1, n_pcg=1, scheme=dect.SCHEME_LM_CG)),

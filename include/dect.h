@@ -190,8 +190,11 @@ dect_status dect_forward_model_vjp(const dect_spectra* s, int64_t n_rays, int32_
  *     = R^T(a+u^a) + D^T(y+u^y) + (z+u^z), warm-started from x_beta, with
  *     R x carried (R x += alpha R p): 2n R and 2(n+1) R^T (Table 1).
  *     D: forward differences along x and y, zero at the last column/row.
- *     Preconditioner: the circulant model 1/(F[R^T R delta] + |F[D]|^2 + 1)
- *     of the operator on a zero-padded grid ("high-passing filter", Sec. 3.3).
+ *     Preconditioner (dect_precond): the circulant model 1/(F[R^T R delta] + |F[D]|^2 + 1)
+ *     of the operator on a zero-padded grid (the high-pass filter of Sec. 3.3); or the plain
+ *     ramp filter 1/(K/|w| + 1) = |w|/(K + |w|), |w| the radial frequency in radians per
+ *     pixel floored at the first non-zero grid frequency, K = (pi/4) F[R^T R delta](0, pi/4);
+ *     or none (plain CG).
  *  2. Eq. 13: m LM iterations per ray with v = R x - u^a (as dect_decompose_rays).
  *  3. Eq. 9-10: y = shrinkage(D x - u^y, lambda/rho), z = max(0, x - u^z).
  *  4. Eq. 11 with the a-block: u^a += a - R x, u^y += y - D x, u^z += z - x.
@@ -214,6 +217,7 @@ dect_status dect_forward_model_vjp(const dect_spectra* s, int64_t n_rays, int32_
  *  2-4. Eq. 9-11 without an a-block; rho by residual balancing on [y; z].
  * m_udm and n_pcg give m and n. The initial image is the same as above. */
 enum dect_scheme { DECT_SCHEME_UDM_PCG = 0, DECT_SCHEME_LM_CG = 1 };
+enum dect_precond { DECT_PRECOND_NONE = 0, DECT_PRECOND_CIRCULANT = 1, DECT_PRECOND_RAMP = 2 };
 
 typedef struct {
     double lambda_c, lambda_p;   /* TV weights (paper: 1e-5) */
@@ -224,7 +228,8 @@ typedef struct {
     double kappa;                /* initial PE image = kappa * Compton image */
     int32_t init_udm_iters;      /* initialisation: LM iterations (10) */
     int32_t init_pcg_iters;      /* initialisation: CG iterations (10) */
-    int32_t precondition;        /* 1: circulant preconditioner, 0: plain CG */
+    int32_t precondition;        /* enum dect_precond: 1 circulant model (default), 2 ramp filter,
+                                    0 plain CG; other values: DECT_EINVAL */
     int32_t use_graph;           /* 1: capture one iteration as a CUDA graph */
     int32_t bp_view_groups;      /* backprojector view groups per image tile, 1..16; -1 = chosen from the
                                     occupancy (fill the GPU's resident slots) without timing; 0 = autotuned:

@@ -373,7 +373,7 @@ extern "C" void dect_params_default(dect_params* p) {
     p->kappa = 1e-2;
     p->init_udm_iters = 10;
     p->init_pcg_iters = 10;
-    p->precondition = 1;
+    p->precondition = DECT_PRECOND_CIRCULANT;
     p->use_graph = 1;
     p->bp_view_groups = 0;
     p->storage = DECT_STORE_F32;
@@ -848,7 +848,8 @@ static dect_status compute_responses(dect_admm* A) {
         CUDA_TRY(cudaMemcpyAsync(dd, &one_slice, sizeof(SliceDesc), cudaMemcpyHostToDevice, st));
         CUDA_TRY(cudaMemcpyAsync(pre, hp, sizeof(hp), cudaMemcpyHostToDevice, st));
         launch_psf_to_response(dd, one_slice, BlockMap{pre, 1}, ncols, A->r + sd.img_off, A->Z + sd.fft_off,
-                               A->H + sd.h_off, A->Hn + sd.h_off, A->tw, st);
+                               A->H + sd.h_off, A->Hn + sd.h_off, A->tw, A->P.precondition == DECT_PRECOND_RAMP,
+                               st);
         cudaError_t e = cudaStreamSynchronize(st);
         cudaFree(dd);
         cudaFree(pre);
@@ -869,6 +870,9 @@ extern "C" dect_status dect_admm_create(dect_geom* const* geoms, int32_t B, cons
         DECT_FAIL(DECT_EINVAL, "dect_admm_create: storage must be DECT_STORE_F32, F16 or BF16");
     if (P->scheme != DECT_SCHEME_UDM_PCG && P->scheme != DECT_SCHEME_LM_CG)
         DECT_FAIL(DECT_EINVAL, "dect_admm_create: scheme must be DECT_SCHEME_UDM_PCG or DECT_SCHEME_LM_CG");
+    if (P->precondition != DECT_PRECOND_NONE && P->precondition != DECT_PRECOND_CIRCULANT &&
+        P->precondition != DECT_PRECOND_RAMP)
+        DECT_FAIL(DECT_EINVAL, "dect_admm_create: precondition must be DECT_PRECOND_NONE, CIRCULANT or RAMP");
     if (P->scheme == DECT_SCHEME_LM_CG && P->storage != DECT_STORE_F32)
         DECT_FAIL(DECT_EUNSUPPORTED, "dect_admm_create: the LM x CG scheme runs with float32 storage only");
     if (P->bp_view_groups < -1 || P->bp_view_groups > 16)

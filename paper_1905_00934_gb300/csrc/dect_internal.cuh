@@ -224,7 +224,7 @@ void launch_precond(const SliceDesc* dsl, const BlockMap& rows_map, int nrows_bl
 // H (and the variant without the D^T D term) from R^T R applied to a centred impulse (one slice)
 // (d_dev: the slice's descriptor on the device with fft_off = h_off = 0; cols_map: its column groups)
 void launch_psf_to_response(const SliceDesc* d_dev, const SliceDesc& d, const BlockMap& cols_map, int ncols,
-                            const float2* psf, float2* Z, float* H, float* H_nograd, const float2* tw,
+                            const float2* psf, float2* Z, float* H, float* H_nograd, const float2* tw, bool ramp,
                             cudaStream_t st);
 cudaError_t fft_init_attributes();
 

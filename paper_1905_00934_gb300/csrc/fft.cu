@@ -239,12 +239,24 @@ __global__ void __launch_bounds__(256) k_fft_rows_full(SliceDesc d, float2* __re
     for (int t = threadIdx.x; t < px; t += blockDim.x) zr[t] = buf[t];
 }
 
+// circulant model: H = 1 / (P(w) + |F[D]|^2 + 1) and, for the initialisation without D, 1 / (P(w) + 1).
+// ramp filter: H = 1 / (K / |w| + 1) for both, K = (pi/4) P(0, pi/4), |w| the wrapped radial frequency
+// floored at the first non-zero grid frequency.
 __global__ void k_response(SliceDesc d, const float2* __restrict__ Z, float* __restrict__ H,
-                           float* __restrict__ Hn) {
+                           float* __restrict__ Hn, bool ramp) {
     const int64_t n = (int64_t)d.px * d.py;
     const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= n) return;
     const int k = (int)(e / d.px), l = (int)(e % d.px);
+    if (ramp) {
+        const double K = fmax((double)Z[d.px / 8].x, 0.0) * (0.25 * M_PI);
+        const double wy = 2.0 * M_PI * min(k, d.py - k) / d.py, wx = 2.0 * M_PI * min(l, d.px - l) / d.px;
+        const double w = fmax(sqrt(wx * wx + wy * wy), 2.0 * M_PI / max(d.px, d.py));
+        const float h = (float)(1.0 / (K / w + 1.0));
+        H[e] = h;
+        Hn[e] = h;
+        return;
+    }
     const double wy = 2.0 * M_PI * k / d.py, wx = 2.0 * M_PI * l / d.px;
     const double sy = sin(0.5 * wy), sx = sin(0.5 * wx);
     const double dhat = 4.0 * sy * sy + 4.0 * sx * sx;
@@ -254,13 +266,13 @@ __global__ void k_response(SliceDesc d, const float2* __restrict__ Z, float* __r
 }
 
 void launch_psf_to_response(const SliceDesc* d_dev, const SliceDesc& d, const BlockMap& cols_map, int ncols,
-                            const float2* psf, float2* Z, float* H, float* H_nograd, const float2* tw,
+                            const float2* psf, float2* Z, float* H, float* H_nograd, const float2* tw, bool ramp,
                             cudaStream_t st) {
     const int64_t n = (int64_t)d.px * d.py;
     k_embed_psf<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(d, psf, Z);
     k_fft_rows_full<<<d.py, 256, sizeof(float2) * d.px, st>>>(d, Z, tw);
     k_fft_cols<<<ncols, 256, sizeof(float2) * 8192, st>>>(d_dev, cols_map, Z, nullptr, 1, 1, tw);
-    k_response<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(d, Z, H, H_nograd);
+    k_response<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(d, Z, H, H_nograd, ramp);
 }
 
 cudaError_t fft_init_attributes() {

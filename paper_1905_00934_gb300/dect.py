@@ -22,6 +22,7 @@ PARALLEL, FAN_FLAT = 0, 1
 F32, F64 = 0, 1
 STORE_F32, STORE_F16, STORE_BF16 = 0, 1, 2
 SCHEME_UDM_PCG, SCHEME_LM_CG = 0, 1
+PRECOND_NONE, PRECOND_CIRCULANT, PRECOND_RAMP = 0, 1, 2
 RAY_ACCEPTED, RAY_REJECTED, RAY_NONFINITE = 0, 1, 2
 # dect_admm_get array selectors
 X, RX, A, UA, Y, UY, Z, UZ, MU, H = range(10)

@@ -72,6 +72,17 @@ def test_preconditioner_response_matches_oracle(cuda_dev, small):
     sol = _solver(c, cuda_dev, x0)
     H = sol.get(0, dect.H).cpu().numpy()
     assert rel_l2(H, prob.H) <= 1e-5
+    ramp = _solver(c, cuda_dev, x0, precondition=dect.PRECOND_RAMP)
+    H = ramp.get(0, dect.H).cpu().numpy()
+    assert rel_l2(H, oadmm.ramp_response(c["geom"])) <= 1e-5
+
+
+def test_precondition_mode_is_validated(cuda_dev, small):
+    from paper_1905_00934_gb300 import dect
+
+    c, _, x0 = small
+    with pytest.raises(Exception, match="precondition"):
+        _solver(c, cuda_dev, x0, precondition=3)
 
 
 def test_initial_image_matches_oracle(cuda_dev, small):
@@ -160,16 +171,17 @@ def test_graph_and_eager_are_bitwise_equal_and_deterministic(cuda_dev, small100)
     assert np.array_equal(outs[0], outs[1]) and np.array_equal(outs[0], outs[2])
 
 
-def test_unpreconditioned_cg_matches_oracle(cuda_dev, small100):
+@pytest.mark.parametrize("mode", [0, 2])
+def test_plain_cg_and_ramp_pcg_match_oracle(cuda_dev, small100, mode):
     from paper_1905_00934_gb300 import dect
 
     c, _, x0 = small100
-    P = oadmm.Params(precondition=False, n_pcg=2)
+    P = oadmm.Params(precondition=mode, n_pcg=2)
     prob = oadmm.Problem(c["geom"], c["spectra"], c["m_h"], c["m_l"], c["w_h"], c["w_l"], P)
     st = oadmm.state_from_image(prob, x0[0], x0[1])
     for _ in range(3):
         st = oadmm.admm_iteration(prob, st)
-    sol = _solver(c, cuda_dev, x0, precondition=0, n_pcg=2)
+    sol = _solver(c, cuda_dev, x0, precondition=mode, n_pcg=2)
     sol.step(3)
     x = sol.get(0, dect.X).cpu().numpy()
     assert rel_l2(x[0], st.x[0]) <= 1e-4 and rel_l2(x[1], st.x[1]) <= 1e-4
