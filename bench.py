@@ -213,6 +213,9 @@ def run_reference(args):
 
 # ------------------------------------------------------------------------------------------------
 
+CDM_ITERS = 20  # LM iterations of the CDM decomposition (the same LM as UDM, rho = 0)
+
+
 def run_dect(args):
     import torch
 
@@ -358,6 +361,21 @@ def run_dect(args):
                                 "ms_per_iteration": t_ms / it, "xi_p_db_at_stop": xi_p, "iterations_run": it,
                                 "slices": B}
             del s2
+        # the paper's baseline (i), CDM-FBP (per-ray decomposition with rho = 0, a >= 0, FBP of each
+        # basis): device time per slice and the xi of slice 0, against the same target
+        from paper_1905_00934_gb300 import cdm_fbp
+
+        cdm_fbp(geo[0], spec, *dev_data[0][:4], iters=CDM_ITERS)  # one-time per-geometry tables
+        c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        c0.record(stream)
+        xs = [cdm_fbp(geo[b], spec, *dev_data[b][:4], iters=CDM_ITERS) for b in range(B)]
+        c1.record(stream)
+        c1.synchronize()
+        x0 = xs[0].cpu().numpy().astype(np.float64)
+        xi = [float(20.0 * np.log10(np.linalg.norm(x0[k] - t) / np.linalg.norm(t)))
+              for k, t in enumerate((cases[0]["truth_c"], cases[0]["truth_p"]))]
+        comparison["cdm_fbp"] = {"ms_per_slice": c0.elapsed_time(c1) / B, "decomposition_iterations": CDM_ITERS,
+                                 "xi_c_db": xi[0], "xi_p_db": xi[1], "reaches_target": bool(xi[1] <= target)}
 
     # end to end through the C ABI: pinned host measurements in, image out, every step
     host_in = [[t.cpu().pin_memory() for t in d] for d in dev_data]
@@ -471,7 +489,7 @@ def run_study(args):
     """The paper's evaluation protocol on the synthetic workload (Sec. 4, Fig. 2): xi_c, xi_p (Eq. 14,
     mean over the batch) every 10 iterations and the device time per iteration, for UDM(m)-PCG(n)
     variants (circulant preconditioner), with the plain ramp-filter preconditioner, with plain CG (no
-    preconditioner) and the LM(m) x CG(n) splitting."""
+    preconditioner) and the LM(m) x CG(n) splitting; and the one-pass CDM-FBP baseline."""
     import torch
 
     import __graft_entry__
@@ -518,6 +536,20 @@ def run_study(args):
         rows[name] = {"ms_per_iteration": t_ms / iters, "params": params,
                       "xi": traj, "best_xi_p_db": min(r[3] for r in traj)}
         del sol
+    # the paper's baseline (i), CDM-FBP: one pass, no iterations
+    from paper_1905_00934_gb300 import cdm_fbp
+
+    data = [[f32(c[k]) for k in ("m_h", "m_l", "w_h", "w_l")] for c in cases]
+    cdm_fbp(geo[0], spec, *data[0], iters=CDM_ITERS)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    xs = [cdm_fbp(geo[b], spec, *data[b], iters=CDM_ITERS) for b in range(B)]
+    e1.record()
+    e1.synchronize()
+    xi = np.mean([[20.0 * np.log10(np.linalg.norm(xs[b][k].cpu().numpy().astype(np.float64) - t) / np.linalg.norm(t))
+                   for k, t in enumerate((cases[b]["truth_c"], cases[b]["truth_p"]))] for b in range(B)], axis=0)
+    rows["CDM-FBP"] = {"ms_per_slice": e0.elapsed_time(e1) / B, "decomposition_iterations": CDM_ITERS,
+                       "xi_c_db": float(xi[0]), "xi_p_db": float(xi[1])}
     print(json.dumps({"study": "xi vs iteration and time, mean over the batch", "batch": B,
                       "workload": "fan beam 512x512, 720 views x 1024 bins", "trajectories": rows}), flush=True)
     return 0

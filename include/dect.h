@@ -161,12 +161,46 @@ dect_status dect_backproject(dect_geom* g, int32_t n_channels, int32_t dtype, co
  * [1e-10, 1e10]; 4 evaluations of f per iteration (Table 1).
  * All arrays are device float32 of length n_rays except status (uint8,
  * nullable). a_c, a_p, mu are read and overwritten. rho = 0 gives the plain
- * maximum-likelihood decomposition. Sums over energy in float32, log of the
- * spectral sums and the 2x2 solve in float64. */
+ * maximum-likelihood decomposition. Float32 throughout: compensated sums over
+ * energy, residuals as -log of the ratio of the spectral sum to the measured
+ * transmission, the 2x2 Marquardt solve from the Jacobian's minors. */
 dect_status dect_decompose_rays(const dect_spectra* s, int64_t n_rays, const float* m_h, const float* m_l,
                                 const float* w_h, const float* w_l, const float* v_c, const float* v_p,
                                 double rho_c, double rho_p, int32_t iters, float* a_c, float* a_p,
                                 float* mu, uint8_t* status, void* stream);
+
+/* ------------------------------------------------------------------------ */
+/* Filtered backprojection, the reconstruction half of the CDM-FBP comparison
+ * method (Sec. 2, Sec. 4): the band-limited ramp filter h(0) = 1/(4 a^2),
+ * h(m a) = -1/(pi^2 m^2 a^2) for odd m, 0 for even m != 0, applied along each
+ * view (linear convolution, no wrap-around), then backprojection with linear
+ * interpolation between bins (zero beyond the first and last bin).
+ *   parallel beam, views over pi or 2 pi (a = du): x = (pi/V) sum_v Q_v(t),
+ *     t = P . (cos, sin)(theta_v);
+ *   flat-detector fan beam, views over 2 pi: the detector rescaled to the
+ *     isocentre (s = u SOD/SDD, a = du SOD/SDD), pre-weight SOD/sqrt(SOD^2+s^2),
+ *     half the ramp, x = (2 pi/V) sum_v Q_v(s(P)) / U^2 with
+ *     U = (SOD - P . n_v)/SOD, s(P) = (P . e_v)/U (n_v towards the source,
+ *     e_v the detector axis, as in dect_geom_desc).
+ * sino_dev: float32 [n_channels][n_views][n_bins]; x_dev: float32
+ * [n_channels][ny][nx], overwritten; both device memory owned by the caller.
+ * clamp_nonneg != 0 replaces negative sinogram values by 0 first (the CDM
+ * constraint). n_channels is 1 or 2. Other angular spans (short scans) return
+ * DECT_EUNSUPPORTED. The filtered rows live in a per-geometry workspace
+ * (allocated on the first call), so calls on one geometry must be ordered. */
+dect_status dect_fbp(dect_geom* g, int32_t n_channels, const float* sino_dev, float* x_dev, int32_t clamp_nonneg,
+                     void* stream);
+
+/* CDM-FBP, the comparison method of Sec. 4: per ray the decomposition of
+ * dect_decompose_rays with rho_c = rho_p = 0 (the weighted least-squares fit of
+ * f(a) to (m_h, m_l)) by `iters` LM iterations from a_c = m_l / sum_E S_l f_KN,
+ * a_p = 0, mu = 1e-3; then a >= 0 per basis and dect_fbp of both bases.
+ * m_h, m_l, w_h, w_l: float32 [n_views][n_bins] device. x_dev: float32
+ * [2][ny][nx] (Compton, PE), overwritten. work_dev: NULL (the call allocates
+ * and frees stream-ordered scratch) or 4 n_views n_bins floats of device memory,
+ * which then hold a_c, a_p (before the clamp), mu and zeros on return. */
+dect_status dect_cdm_fbp(dect_geom* g, const dect_spectra* s, const float* m_h, const float* m_l, const float* w_h,
+                         const float* w_l, int32_t iters, float* work_dev, float* x_dev, void* stream);
 
 /* Forward model of Eq. 3 per ray: f_h, f_l at (a_c, a_p) and, if jac is not
  * NULL, the Jacobian jac[r] = {df_h/da_c, df_h/da_p, df_l/da_c, df_l/da_p}

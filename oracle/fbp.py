@@ -1,11 +1,11 @@
 """Filtered backprojection and the CDM-FBP comparison method (Sec. 2, Sec. 4), FP64.
 
-TEST INFRASTRUCTURE ONLY (with bench.py's CPU baseline): plain numpy, one view at a time.
+TEST INFRASTRUCTURE ONLY: plain numpy, one view at a time.
 
 The paper's baseline (i) decomposes each ray's dual-energy measurements into Compton and PE line
-integrals (the constrained decomposition method, CDM, of a reference that restates it) and then
+integrals (the constrained decomposition method, CDM, from a cited reference) and then
 reconstructs each basis by filtered backprojection (FBP); its Compton image also starts the ADMM.
-Neither is restated in the paper, so both follow these readings:
+The paper restates neither, so both follow these readings:
 
   * CDM: Eq. 13 with rho_c = rho_p = 0, i.e. the weighted least-squares fit of the forward model
     f(a) to (m_h, m_l) per ray, by `iters` Levenberg-Marquardt iterations (the same LM as UDM)
@@ -98,8 +98,8 @@ def fbp(geom, sino: np.ndarray) -> np.ndarray:
     raise ValueError(f"unknown geometry kind {g.kind}")
 
 
-def cdm(spec, m_h, m_l, w_h, w_l, iters: int = 20, mu0: float = 1e-3):
-    """(a_c, a_p) [V][Nb]: per-ray decomposition with rho = 0, then a >= 0."""
+def cdm_fit(spec, m_h, m_l, w_h, w_l, iters: int = 20, mu0: float = 1e-3):
+    """(a_c, a_p) [V][Nb]: the per-ray decomposition with rho = 0, before the constraint."""
     m_h = np.asarray(m_h, dtype=np.float64)
     shape = m_h.shape
     m_l = np.asarray(m_l, dtype=np.float64).reshape(shape)
@@ -110,7 +110,13 @@ def cdm(spec, m_h, m_l, w_h, w_l, iters: int = 20, mu0: float = 1e-3):
     ac, ap, _, _ = spectral.udm(spec, m_h, m_l, np.asarray(w_h, np.float64).reshape(shape),
                                 np.asarray(w_l, np.float64).reshape(shape), zeros, zeros, 0.0, 0.0, iters,
                                 a_c0, zeros, mu)
-    return np.maximum(ac.reshape(shape), 0.0), np.maximum(ap.reshape(shape), 0.0)
+    return ac.reshape(shape), ap.reshape(shape)
+
+
+def cdm(spec, m_h, m_l, w_h, w_l, iters: int = 20, mu0: float = 1e-3):
+    """(a_c, a_p) [V][Nb]: per-ray decomposition with rho = 0, then a >= 0."""
+    ac, ap = cdm_fit(spec, m_h, m_l, w_h, w_l, iters, mu0)
+    return np.maximum(ac, 0.0), np.maximum(ap, 0.0)
 
 
 def cdm_fbp(geom, spec, m_h, m_l, w_h, w_l, iters: int = 20):

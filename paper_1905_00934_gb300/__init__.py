@@ -2,4 +2,4 @@
 dual-energy CT reconstruction (Li et al., Sec. 3), with a C ABI (include/dect.h)
 and this thin ctypes binding (`dect`)."""
 from . import dect  # noqa: F401
-from .solver import Geometry, Spectra, Solver  # noqa: F401
+from .solver import Geometry, Spectra, Solver, cdm_fbp  # noqa: F401

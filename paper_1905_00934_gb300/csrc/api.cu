@@ -81,6 +81,10 @@ struct dect_geom {
     float2* ws_partial = nullptr;
     int ws_C = 1;
     double4* rays64 = nullptr;  // float64 ray table (DECT_F64 calls; built on first use)
+    // dect_fbp: per-view constants, fan pre-weights, filtered sinograms [2][V][Nb] (built on first use)
+    float4* fbp_tab = nullptr;
+    float* fbp_prew = nullptr;
+    float* fbp_q = nullptr;
 
     int64_t n_rays() const { return (int64_t)desc.n_views * desc.n_bins; }
     int64_t n_pix() const { return (int64_t)desc.nx * desc.ny; }
@@ -189,6 +193,9 @@ extern "C" void dect_geometry_destroy(dect_geom* g) {
     cudaFree(g->ws_maps);
     cudaFree(g->ws_partial);
     cudaFree(g->rays64);
+    cudaFree(g->fbp_tab);
+    cudaFree(g->fbp_prew);
+    cudaFree(g->fbp_q);
     delete g;
 }
 
@@ -329,6 +336,118 @@ extern "C" dect_status dect_decompose_rays(const dect_spectra* s, int64_t n, con
     launch_udm_rays(s->dev(), n, m_h, m_l, w_h, w_l, v_c, v_p, rho_c, rho_p, iters, a_c, a_p, mu, status,
                     as_stream(stream));
     CUDA_TRY(cudaGetLastError());
+    return DECT_OK;
+}
+
+// ---- FBP and CDM-FBP ---------------------------------------------------------------------------
+
+static bool span_is(double span, double target) { return std::fabs(span - target) <= 1e-6 * target; }
+
+static dect_status fbp_prepare(dect_geom* g, FbpDev& f) {
+    const auto& d = g->desc;
+    const bool fan = d.kind == DECT_FAN_FLAT;
+    if (fan ? !span_is(d.angle_span_rad, 2.0 * M_PI)
+            : !(span_is(d.angle_span_rad, M_PI) || span_is(d.angle_span_rad, 2.0 * M_PI)))
+        DECT_FAIL(DECT_EUNSUPPORTED, "dect_fbp: views must cover 2 pi (fan) or pi / 2 pi (parallel); short scans "
+                                     "are not supported");
+    const double k0 = 0.5 * (d.n_bins - 1) - d.bin_offset_cm / d.bin_pitch_cm;
+    if (!g->fbp_tab) {
+        static bool attr = false;
+        if (!attr) {
+            CUDA_TRY(fbp_init_attributes());
+            attr = true;
+        }
+        std::vector<float4> tab(d.n_views);
+        for (int v = 0; v < d.n_views; ++v) {
+            const double th = d.angle0_rad + v * (d.angle_span_rad / d.n_views);
+            const double c = std::cos(th), sn = std::sin(th);
+            tab[v] = fan ? make_float4((float)c, (float)sn, 0.f, 0.f)
+                         : make_float4((float)(c / d.bin_pitch_cm), (float)(sn / d.bin_pitch_cm), (float)k0, 0.f);
+        }
+        float4* dt = nullptr;
+        CUDA_TRY(dalloc(&dt, tab.size()));
+        cudaError_t e = cudaMemcpy(dt, tab.data(), sizeof(float4) * tab.size(), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) {
+            cudaFree(dt);
+            CUDA_TRY(e);
+        }
+        float* pw = nullptr;
+        if (fan) {
+            std::vector<float> w(d.n_bins);
+            for (int k = 0; k < d.n_bins; ++k) {
+                const double u = (k - 0.5 * (d.n_bins - 1)) * d.bin_pitch_cm + d.bin_offset_cm;
+                const double s = u * d.sod_cm / d.sdd_cm;
+                w[k] = (float)(d.sod_cm / std::sqrt(d.sod_cm * d.sod_cm + s * s));
+            }
+            e = dalloc(&pw, w.size());
+            if (e == cudaSuccess) e = cudaMemcpy(pw, w.data(), sizeof(float) * w.size(), cudaMemcpyHostToDevice);
+        }
+        float* q = nullptr;
+        if (e == cudaSuccess) e = dalloc(&q, (size_t)2 * g->n_rays());
+        if (e != cudaSuccess) {
+            cudaFree(dt);
+            cudaFree(pw);
+            cudaFree(q);
+            CUDA_TRY(e);
+        }
+        g->fbp_tab = dt;
+        g->fbp_prew = pw;
+        g->fbp_q = q;
+    }
+    f.nx = d.nx;
+    f.ny = d.ny;
+    f.nv = d.n_views;
+    f.nb = d.n_bins;
+    f.fan = fan ? 1 : 0;
+    f.pix = (float)d.pixel_cm;
+    f.cx = 0.5f * (float)(d.nx - 1);
+    f.cy = 0.5f * (float)(d.ny - 1);
+    f.sod = (float)d.sod_cm;
+    f.k0 = (float)k0;
+    f.k1 = fan ? (float)(d.sdd_cm / d.bin_pitch_cm) : 0.f;
+    f.gain = fan ? (float)(0.5 * d.sdd_cm / (d.bin_pitch_cm * d.sod_cm)) : (float)(1.0 / d.bin_pitch_cm);
+    f.scale = (float)((fan ? 2.0 * M_PI : M_PI) / d.n_views);
+    f.tab = g->fbp_tab;
+    f.prew = g->fbp_prew;
+    return DECT_OK;
+}
+
+extern "C" dect_status dect_fbp(dect_geom* g, int32_t n_channels, const float* sino_dev, float* x_dev,
+                                int32_t clamp_nonneg, void* stream) {
+    clear_stale_error();
+    if (!g || !sino_dev || !x_dev) DECT_FAIL(DECT_EINVAL, "dect_fbp: null argument");
+    if (n_channels != 1 && n_channels != 2) DECT_FAIL(DECT_EINVAL, "dect_fbp: n_channels must be 1 or 2");
+    FbpDev f{};
+    const dect_status s = fbp_prepare(g, f);
+    if (s != DECT_OK) return s;
+    launch_fbp(f, n_channels, sino_dev, g->fbp_q, x_dev, clamp_nonneg != 0, as_stream(stream));
+    CUDA_TRY(cudaGetLastError());
+    return DECT_OK;
+}
+
+extern "C" dect_status dect_cdm_fbp(dect_geom* g, const dect_spectra* sp, const float* m_h, const float* m_l,
+                                    const float* w_h, const float* w_l, int32_t iters, float* work_dev, float* x_dev,
+                                    void* stream) {
+    clear_stale_error();
+    if (!g || !sp || !m_h || !m_l || !w_h || !w_l || !x_dev) DECT_FAIL(DECT_EINVAL, "dect_cdm_fbp: null argument");
+    if (iters < 0) DECT_FAIL(DECT_EINVAL, "dect_cdm_fbp: iters < 0");
+    FbpDev f{};
+    const dect_status s = fbp_prepare(g, f);
+    if (s != DECT_OK) return s;
+    cudaStream_t st = as_stream(stream);
+    const int64_t n = g->n_rays();
+    float* w = work_dev;
+    if (!w) CUDA_TRY(cudaMallocAsync((void**)&w, sizeof(float) * 4 * (size_t)n, st));
+    float *a_c = w, *a_p = w + n, *mu = w + 2 * n, *zero = w + 3 * n;
+    launch_cdm_start(n, m_l, (float)(1.0 / sp->abar_low), 1e-3f, a_c, a_p, mu, zero, st);
+    launch_udm_rays(sp->dev(), n, m_h, m_l, w_h, w_l, zero, zero, 0.0, 0.0, iters, a_c, a_p, mu, nullptr, st);
+    launch_fbp(f, 2, a_c, g->fbp_q, x_dev, true, st);
+    cudaError_t e = cudaGetLastError();
+    if (!work_dev) {
+        cudaError_t fe = cudaFreeAsync(w, st);
+        if (e == cudaSuccess) e = fe;
+    }
+    CUDA_TRY(e);
     return DECT_OK;
 }
 

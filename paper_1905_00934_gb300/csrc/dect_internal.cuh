@@ -228,6 +228,20 @@ void launch_psf_to_response(const SliceDesc* d_dev, const SliceDesc& d, const Bl
                             cudaStream_t st);
 cudaError_t fft_init_attributes();
 
+// ---- filtered backprojection and CDM-FBP (fbp.cu) ----
+struct FbpDev {
+    int nx, ny, nv, nb, fan;
+    float pix, cx, cy;   // pixel pitch, image centre (pixels)
+    float sod, k0, k1;   // fan: source distance; fractional bin k = k1 * (P.e) / den + k0 (k0 also in tab.z)
+    float gain, scale;   // filter gain (1/du, or 1/(2 du SOD/SDD)); backprojection factor (pi/V, 2 pi/V)
+    const float4* tab;   // [nv]: parallel {c/du, s/du, k0, 0}; fan {c, s, 0, 0}
+    const float* prew;   // [nb] fan pre-weight SOD / sqrt(SOD^2 + s^2), or null
+};
+void launch_fbp(const FbpDev& f, int nch, const float* sino, float* q, float* x, bool clamp, cudaStream_t st);
+void launch_cdm_start(int64_t n, const float* m_l, float inv_abar, float mu0, float* a_c, float* a_p, float* mu,
+                      float* zero, cudaStream_t st);
+cudaError_t fbp_init_attributes();
+
 // admm.cu helpers are local to that file.
 
 // ---- error handling ----------------------------------------------------------------------

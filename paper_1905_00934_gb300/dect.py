@@ -73,6 +73,8 @@ _SIGS = {
     "dect_project_noalloc": ([_VP, ctypes.c_int32, _VP, _VP, _VP], ctypes.c_int),
     "dect_decompose_rays": ([_VP, ctypes.c_int64, _VP, _VP, _VP, _VP, _VP, _VP, ctypes.c_double, ctypes.c_double,
                              ctypes.c_int32, _VP, _VP, _VP, _VP, _VP], ctypes.c_int),
+    "dect_fbp": ([_VP, ctypes.c_int32, _VP, _VP, ctypes.c_int32, _VP], ctypes.c_int),
+    "dect_cdm_fbp": ([_VP, _VP, _VP, _VP, _VP, _VP, ctypes.c_int32, _VP, _VP, _VP], ctypes.c_int),
     "dect_forward_model": ([_VP, ctypes.c_int64, ctypes.c_int32, _VP, _VP, _VP, _VP, _VP, _VP], ctypes.c_int),
     "dect_forward_model_vjp": ([_VP, ctypes.c_int64, ctypes.c_int32, _VP, _VP, _VP, _VP, _VP, _VP, _VP], ctypes.c_int),
     "dect_params_default": ([ctypes.POINTER(Params)], None),
@@ -212,6 +214,19 @@ def decompose_rays(spec, m_h, m_l, w_h, w_l, v_c, v_p, rho_c, rho_p, iters, a_c,
     _check(lib().dect_decompose_rays(spec, n, _ptr(m_h), _ptr(m_l), _ptr(w_h), _ptr(w_l), _ptr(v_c), _ptr(v_p),
                                      float(rho_c), float(rho_p), int(iters), _ptr(a_c), _ptr(a_p), _ptr(mu),
                                      _ptr(status), _stream(stream)))
+
+
+def fbp(geom, sino, out, clamp_nonneg=False, stream=None):
+    """out[c] = filtered backprojection of sino[c] (float32 [nch, V, Nb] -> [nch, ny, nx])."""
+    _check(lib().dect_fbp(geom, sino.shape[0], _ptr(sino), _ptr(out), 1 if clamp_nonneg else 0, _stream(stream)))
+    return out
+
+
+def cdm_fbp(geom, spec, m_h, m_l, w_h, w_l, iters, out, work=None, stream=None):
+    """CDM-FBP: per-ray decomposition with rho = 0, a >= 0, FBP of both bases into out [2, ny, nx]."""
+    _check(lib().dect_cdm_fbp(geom, spec, _ptr(m_h), _ptr(m_l), _ptr(w_h), _ptr(w_l), int(iters), _ptr(work),
+                              _ptr(out), _stream(stream)))
+    return out
 
 
 def forward_model(spec, a_c, a_p, f_h=None, f_l=None, jac=None, stream=None):

@@ -30,11 +30,29 @@ class Geometry:
         dect.backproject(self.handle, s, out, stream)
         return out[0] if squeeze else out
 
+    def fbp(self, s: torch.Tensor, out: torch.Tensor | None = None, clamp_nonneg: bool = False,
+            stream=None) -> torch.Tensor:
+        """Filtered backprojection of float32 sinograms [nch, V, Nb] (or [V, Nb])."""
+        squeeze = s.dim() == 2
+        s = s.reshape(-1, self.n_views, self.n_bins)
+        if out is None:
+            out = torch.empty((s.shape[0], self.ny, self.nx), device=s.device, dtype=torch.float32)
+        dect.fbp(self.handle, s, out, clamp_nonneg, stream)
+        return out[0] if squeeze else out
+
     def __del__(self):
         h = getattr(self, "handle", None)
         if h is not None and dect._lib is not None:
             dect.geometry_destroy(h)
             self.handle = None
+
+
+def cdm_fbp(geo: Geometry, spec: "Spectra", m_h, m_l, w_h, w_l, iters: int = 20, work=None, stream=None):
+    """The CDM-FBP comparison method: [2, ny, nx] (Compton, PE). work, if given, is a float32 device
+    tensor of 4 V Nb elements and holds the per-ray line integrals (a_c, a_p) on return."""
+    out = torch.empty((2, geo.ny, geo.nx), device=m_h.device, dtype=torch.float32)
+    dect.cdm_fbp(geo.handle, spec.handle, m_h, m_l, w_h, w_l, iters, out, work, stream)
+    return out
 
 
 class Spectra:

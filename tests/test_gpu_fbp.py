@@ -1,0 +1,148 @@
+"""GPU filtered backprojection and CDM-FBP (the comparison method of Sec. 2 / Sec. 4) against the
+FP64 oracle (oracle/fbp.py), on the same float32-rounded inputs.
+
+FBP is linear and sums float32 products in a fixed order: images within 1e-5 relative L2 of the
+oracle. CDM-FBP adds the per-ray decomposition with rho = 0 in float32 (as dect_decompose_rays);
+its line integrals and images are compared with the tolerances stated at each test."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+from conftest import rel_l2, to_dev
+from oracle import fbp as ofbp
+from oracle import spectral as ospec
+from synth import geometry as G
+from synth import phantom as P
+from synth.workloads import baggage_fan_case, baggage_phantom, make_case, small_parallel_case
+
+pytestmark = pytest.mark.gpu
+
+# float32 interpolation positions carry ~1e-4 bins of rounding (the fan's division included); at the
+# sharpest sinogram edges (metal inserts) that is ~1e-4 of a sample, ~1e-5 in the image after the
+# view sum; the image-level bound of the method's reconstructions is 1e-4
+FBP_TOL = 3e-5
+
+
+def _r32(a):
+    return np.float32(a).astype(np.float64)
+
+
+def _geoms():
+    return {
+        "parallel_pi": G.parallel_geometry(64, 90, 96, 0.1, 0.1),
+        "parallel_2pi_offset": G.Geometry(G.PARALLEL, 70, 58, 0.1, 120, 0.3, 2 * math.pi, 101, 0.09, 0.04),
+        "fan_ragged": G.Geometry(G.FAN_FLAT, 70, 58, 0.12, 90, 0.3, 2 * math.pi, 130, 0.15, 0.02, 16.0, 27.0),
+        "fan_512": G.baggage_fan_geometry(),
+    }
+
+
+@pytest.fixture(scope="module")
+def sinos():
+    out = {}
+    for name, g in _geoms().items():
+        rng = np.random.default_rng(7)
+        ph = baggage_phantom(g, rng, n_objects=12)[0] if g.kind == G.FAN_FLAT else None
+        if ph is None:
+            one = lambda *v: np.array(v, dtype=np.float64)
+            ph = P.Phantom(shape=np.array([P.ELLIPSE, P.RECTANGLE]), cx=one(0.3, -0.8), cy=one(-0.2, 0.6),
+                           a=one(2.2, 0.7), b=one(1.8, 0.4), phi=one(0.3, 1.1), compton=one(0.2, 0.5),
+                           pe=one(0.002, 0.04))
+        lc, lp = P.line_integrals(ph, g)
+        out[name] = (g, _r32(lc), _r32(lp))
+    return out
+
+
+@pytest.mark.parametrize("name", list(_geoms().keys()))
+def test_fbp_matches_oracle(cuda_dev, sinos, name):
+    from paper_1905_00934_gb300 import Geometry
+
+    g, lc, lp = sinos[name]
+    geo = Geometry(g)
+    x = geo.fbp(to_dev(np.stack([lc, lp]), cuda_dev)).cpu().numpy()
+    ref_c, ref_p = ofbp.fbp(g, lc), ofbp.fbp(g, lp)
+    e_c, e_p = rel_l2(x[0], ref_c), rel_l2(x[1], ref_p)
+    print(f"{name}: FBP rel-L2 Compton {e_c:.2e}, PE {e_p:.2e}")
+    assert e_c <= FBP_TOL and e_p <= FBP_TOL
+
+
+def test_fbp_channels_and_clamp_are_consistent(cuda_dev, sinos):
+    from paper_1905_00934_gb300 import Geometry
+
+    g, lc, lp = sinos["fan_ragged"]
+    geo = Geometry(g)
+    s = to_dev(np.stack([lc - 0.5 * lc.mean(), lp]), cuda_dev)
+    both = geo.fbp(s)
+    assert torch.equal(both[0], geo.fbp(s[0]))
+    assert torch.equal(both[1], geo.fbp(s[1]))
+    assert torch.equal(geo.fbp(s, clamp_nonneg=True), geo.fbp(torch.clamp(s, min=0.0)))
+
+
+def test_short_scans_are_rejected(cuda_dev):
+    from paper_1905_00934_gb300 import Geometry, dect
+
+    geo = Geometry(G.parallel_geometry(16, 30, 24, 0.1, 0.1, span_rad=0.75 * math.pi))
+    with pytest.raises(dect.DectError) as ei:
+        geo.fbp(torch.zeros((30, 24), device=cuda_dev))
+    assert ei.value.status == dect.EUNSUPPORTED
+
+
+def _cdm_pair(c, dev, iters):
+    """Oracle and GPU CDM-FBP on the same float32-rounded data: (data, a_ref, a_gpu, x_ref, x_gpu), a before
+    the constraint a >= 0, [2][V][Nb]; images [2][ny][nx]."""
+    from paper_1905_00934_gb300 import Geometry, Spectra, cdm_fbp
+
+    m = {k: _r32(c[k]) for k in ("m_h", "m_l", "w_h", "w_l")}
+    g = c["geom"]
+    a_ref = np.stack(ofbp.cdm_fit(c["spectra"], m["m_h"], m["m_l"], m["w_h"], m["w_l"], iters))
+    x_ref = np.stack([ofbp.fbp(g, np.maximum(a_ref[b], 0.0)) for b in (0, 1)])
+    geo, spec = Geometry(g), Spectra.from_tables(c["spectra"])
+    n = g.n_views * g.n_bins
+    work = torch.empty(4 * n, device=dev)
+    x = cdm_fbp(geo, spec, *[to_dev(m[k], dev) for k in ("m_h", "m_l", "w_h", "w_l")], iters=iters, work=work)
+    a_gpu = work[: 2 * n].reshape(2, g.n_views, g.n_bins).cpu().numpy().astype(np.float64)
+    # the same call without a work buffer gives the same image
+    x2 = cdm_fbp(geo, spec, *[to_dev(m[k], dev) for k in ("m_h", "m_l", "w_h", "w_l")], iters=iters)
+    assert torch.equal(x, x2)
+    return m, a_ref, a_gpu, x_ref, x.cpu().numpy()
+
+
+def _check_cdm(c, dev, iters, img_tol):
+    m, a_ref, a_gpu, x_ref, x = _cdm_pair(c, dev, iters)
+    counts = np.minimum(m["w_h"], m["w_l"])  # the weights are the photon counts (clamped >= 1)
+    good = counts >= 10
+    d = np.abs(a_gpu - a_ref)
+    off = d[0] > 1e-4 * np.abs(a_ref[0]) + 1e-6
+    errs = [rel_l2(a_gpu[b][good], a_ref[b][good]) for b in (0, 1)] + [rel_l2(x[b], x_ref[b]) for b in (0, 1)]
+    args = (c["spectra"], m["m_h"], m["m_l"], m["w_h"], m["w_l"], np.zeros_like(m["m_h"]), np.zeros_like(m["m_h"]),
+            0.0, 0.0)
+    starved = ~good
+    cg = ospec.udm_cost(*args, a_gpu[0], a_gpu[1]).reshape(good.shape)
+    co = ospec.udm_cost(*args, a_ref[0], a_ref[1]).reshape(good.shape)
+    viol = cg - co - (1e-4 * co + 1e-6)
+    print(f"{c['geom'].nx}^2 CDM-FBP, {iters} LM iterations: rays with >= 10 counts: a rel-L2 {errs[0]:.2e} / "
+          f"{errs[1]:.2e}, Compton off by > 1e-4: {int((off & good).sum())} of {int(good.sum())}; starved rays "
+          f"{int(starved.sum())}, Compton off {int((off & starved).sum())}; cost above the oracle's by more than "
+          f"1e-4 relative: {int((viol > 0).sum())} rays (max {viol.max():.2e}); images rel-L2 {errs[2]:.2e} / "
+          f"{errs[3]:.2e}")
+    # the LM accept test compares two float32 costs on the GPU and two float64 costs in the oracle; on
+    # rays with few counts the fit is flat along the valley where the PE and Compton columns are nearly
+    # parallel, a near-tie can go either way and the two stop at different points of it. Unique part:
+    # all but a 1e-4 fraction of the rays with >= 10 counts agree to 1e-4 and both bases to 1e-4 in L2;
+    # the rest is valid: on every ray the GPU's point fits the data as well as the oracle's
+    assert (off & good).sum() <= 1e-4 * good.sum()
+    assert errs[0] <= 1e-4 and errs[1] <= 1e-4
+    assert np.all(viol <= 0)
+    # images: FBP's ramp turns a one-ray difference into a streak, so the differing rays set the bound
+    assert errs[2] <= img_tol and errs[3] <= img_tol
+
+
+def test_cdm_fbp_small_parallel_matches_oracle(cuda_dev):
+    # 64 x 64 parallel beam, Poisson data (I0 1e5), PE referred to 100 keV
+    _check_cdm(small_parallel_case(e_ref_kev=100.0), cuda_dev, 20, 1e-4)
+
+
+def test_cdm_fbp_full_size_fan_matches_oracle(cuda_dev):
+    # 512 x 512, 720 views x 1024 bins fan beam, the benchmark's slice 0 (metal inserts: starved rays)
+    _check_cdm(baggage_fan_case(slice_index=0), cuda_dev, 20, 1e-3)
