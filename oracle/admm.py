@@ -33,7 +33,7 @@ import dataclasses
 
 import numpy as np
 
-from . import projector, spectral
+from . import fbp, projector, spectral
 
 
 # ----------------------------------------------------------------------------
@@ -71,6 +71,7 @@ def xi_db(x: np.ndarray, truth: np.ndarray) -> float:
 # preconditioner (Sec. 3.3)
 
 PRECOND_NONE, PRECOND_CIRCULANT, PRECOND_RAMP = 0, 1, 2
+INIT_PCG, INIT_CDM_FBP = 0, 1
 
 
 def pad_size(n: int) -> int:
@@ -151,6 +152,7 @@ class Params:
     kappa: float = 1e-2                # x_p0 = kappa * x_c0
     init_udm_iters: int = 10
     init_pcg_iters: int = 10
+    init: int = 0                      # INIT_PCG (the stand-in below) or INIT_CDM_FBP (the paper's start)
 
 
 @dataclasses.dataclass
@@ -332,13 +334,20 @@ def initial_image(prob: Problem):
     """x0 = (x_c0, kappa * x_c0).
 
     The paper starts from a CDM decomposition + FBP Compton image and a scaled
-    copy for PE. Stand-in: a0 = per-ray decomposition (Eq. 13) with rho_c = 0,
+    copy for PE (params.init = INIT_CDM_FBP). Default stand-in (INIT_PCG, chosen
+    before CDM-FBP existed here and kept as the default): a0 = per-ray decomposition (Eq. 13) with rho_c = 0,
     rho_p = rho0_p, v = 0, from a_c = m_l / sum_E S_l f_KN, a_p = 0; then
     x_c0 = max(0, PCG iterations on (R^T R + I) x = R^T a_c0 from 0).
     """
     P = prob.params
     g = prob.geom
     spec = prob.spec
+    if P.init == INIT_CDM_FBP:
+        # the paper's start: the Compton image of CDM-FBP (oracle.fbp), clamped, and a scaled copy
+        ac, _ = fbp.cdm(spec, prob.m_h, prob.m_l, prob.w_h, prob.w_l, P.init_udm_iters, P.lm_mu0)
+        prob.count.f += 4 * P.init_udm_iters
+        xc = np.maximum(fbp.fbp(g, ac), 0.0)
+        return xc, P.kappa * xc
     sl = spec.s_low / spec.s_low.sum()
     a_c0 = prob.m_l / float(np.dot(sl, spec.f_kn))
     zeros = np.zeros_like(prob.m_l)

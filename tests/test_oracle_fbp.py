@@ -143,3 +143,25 @@ def test_cdm_fbp_of_noise_free_polychromatic_data():
     insert = r1 < 0.6
     assert abs(xc[body].mean() - 0.2) < 2e-3 and abs(xc[insert].mean() - 0.5) < 5e-3
     assert abs(xp[body].mean() - 0.002) < 1e-4 and abs(xp[insert].mean() - 0.032) < 5e-4
+
+
+def test_cdm_fbp_start_of_the_admm():
+    # the paper's initial image (Sec. 4): CDM-FBP Compton, clamped, and kappa times it for PE
+    from oracle import admm
+
+    g = G.parallel_geometry(64, 180, 128, 0.1, 0.1)
+    one = lambda *v: np.array(v, dtype=np.float64)
+    ph = P.Phantom(shape=np.array([P.ELLIPSE, P.ELLIPSE]), cx=one(0.0, 0.8), cy=one(0.0, 0.5),
+                   a=one(2.5, 0.8), b=one(2.5, 0.8), phi=one(0.0, 0.0), compton=one(0.2, 0.3), pe=one(0.002, 0.03))
+    t = spectra.SpectralTables(e_ref_kev=100.0)
+    lc, lp = P.line_integrals(ph, g)
+    d = P.noise_free_measurements(t, lc, lp)
+    w = np.full(lc.shape, 1e5)
+    prob = admm.Problem(g, t, d["m_h"], d["m_l"], w, w, admm.Params(init=admm.INIT_CDM_FBP, init_udm_iters=40,
+                                                                       kappa=0.25))
+    xc, xp = admm.initial_image(prob)
+    assert prob.count.f == 4 * 40
+    assert np.all(xc >= 0) and np.array_equal(xp, 0.25 * xc)
+    r0, r1 = _radius_map(g, 0.0, 0.0), _radius_map(g, 0.8, 0.5)
+    body, insert = (r0 < 2.0) & (r1 > 1.1), r1 < 0.6
+    assert abs(xc[body].mean() - 0.2) < 2e-3 and abs(xc[insert].mean() - 0.5) < 5e-3
