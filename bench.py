@@ -508,6 +508,7 @@ def run_study(args):
     f32 = lambda a: torch.tensor(np.ascontiguousarray(a), dtype=torch.float32, device=dev)
     configs = [("UDM1-PCG1", dict(m_udm=1, n_pcg=1)), ("UDM1-PCG2", dict(m_udm=1, n_pcg=2)),
                ("UDM2-PCG1", dict(m_udm=2, n_pcg=1)), ("UDM1-PCG5", dict(m_udm=1, n_pcg=5)),
+               ("UDM1-PCG1 CDM-FBP start", dict(m_udm=1, n_pcg=1, init=dect.INIT_CDM_FBP)),
                ("UDM1-PCG1 ramp", dict(m_udm=1, n_pcg=1, precondition=dect.PRECOND_RAMP)),
                ("UDM1-PCG5 ramp", dict(m_udm=1, n_pcg=5, precondition=dect.PRECOND_RAMP)),
                ("UDM1-CG1", dict(m_udm=1, n_pcg=1, precondition=0)),

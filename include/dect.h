@@ -252,6 +252,12 @@ dect_status dect_forward_model_vjp(const dect_spectra* s, int64_t n_rays, int32_
  * m_udm and n_pcg give m and n. The initial image is the same as above. */
 enum dect_scheme { DECT_SCHEME_UDM_PCG = 0, DECT_SCHEME_LM_CG = 1 };
 enum dect_precond { DECT_PRECOND_NONE = 0, DECT_PRECOND_CIRCULANT = 1, DECT_PRECOND_RAMP = 2 };
+/* Initial image when a slice has no x0 (both: x_p0 = kappa x_c0, x_c0 >= 0):
+ * DECT_INIT_PCG      per-ray decomposition (init_udm_iters LM iterations, rho_c = 0, rho_p = rho0_p,
+ *                    v = 0) and init_pcg_iters CG iterations on (R^T R + I) x_c = R^T a_c from 0;
+ * DECT_INIT_CDM_FBP  the paper's start (Sec. 4): the Compton image of CDM-FBP (dect_cdm_fbp with
+ *                    init_udm_iters LM iterations and mu0 = lm_mu0); needs full scans. */
+enum dect_init { DECT_INIT_PCG = 0, DECT_INIT_CDM_FBP = 1 };
 
 typedef struct {
     double lambda_c, lambda_p;   /* TV weights (paper: 1e-5) */
@@ -277,6 +283,7 @@ typedef struct {
     int32_t storage;             /* dect_storage (DECT_STORE_F32): 16-bit formats halve the bytes of the
                                     sinogram vectors and textures at the cost of their precision */
     int32_t scheme;              /* dect_scheme (DECT_SCHEME_UDM_PCG): the splitting one iteration runs */
+    int32_t init;                /* dect_init (DECT_INIT_PCG): the initial image of slices without x0 */
 } dect_params;
 
 /* Fills *p with the paper's values and the defaults above. */

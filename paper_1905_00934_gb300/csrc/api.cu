@@ -497,6 +497,7 @@ extern "C" void dect_params_default(dect_params* p) {
     p->bp_view_groups = 0;
     p->storage = DECT_STORE_F32;
     p->scheme = DECT_SCHEME_UDM_PCG;
+    p->init = DECT_INIT_PCG;
 }
 
 struct MapBuf {
@@ -845,6 +846,44 @@ static dect_status capture_iteration(dect_admm* A, bool profile, cudaGraphExec_t
     return DECT_OK;
 }
 
+// The paper's start (Sec. 4): x_c of the slices without x0 = the Compton image of CDM-FBP (per-ray
+// decomposition with rho = 0, a >= 0, FBP); k_init_image then clamps it and sets x_p = kappa x_c.
+static dect_status enq_cdm_fbp_start(dect_admm* A, cudaStream_t st) {
+    int64_t max_nr = 0;
+    for (int b = 0; b < A->B; ++b) max_nr = std::max(max_nr, (int64_t)A->hs[b].g.nv * A->hs[b].g.nb);
+    float* work = nullptr;  // a_c, a_p, mu, zeros of one slice
+    CUDA_TRY(cudaMallocAsync((void**)&work, sizeof(float) * 4 * (size_t)max_nr, st));
+    dect_status status = DECT_OK;
+    for (int b = 0; b < A->B && status == DECT_OK; ++b) {
+        if (A->has_x0[b]) continue;
+        const SliceDesc& sd = A->hs[b];
+        const int64_t nr = (int64_t)sd.g.nv * sd.g.nb, np = (int64_t)sd.g.nx * sd.g.ny;
+        FbpDev f{};
+        status = fbp_prepare(A->geoms[b], f);
+        if (status != DECT_OK) break;
+        float* m = A->stage;          // planar m_h, m_l, w_h, w_l
+        float* img = A->stage + 4 * nr;  // planar [2][ny][nx]: Compton, then zeros
+        launch_unpack_meas(nr, A->meas + sd.sino_off, m, st);
+        launch_cdm_start(nr, m + nr, (float)(1.0 / A->spec->abar_low), (float)A->P.lm_mu0, work, work + nr,
+                         work + 2 * nr, work + 3 * nr, st);
+        launch_udm_rays(A->spec->dev(), nr, m, m + nr, m + 2 * nr, m + 3 * nr, work + 3 * nr, work + 3 * nr, 0.0,
+                        0.0, A->P.init_udm_iters, work, work + nr, work + 2 * nr, nullptr, st);
+        launch_fbp(f, 1, work, A->geoms[b]->fbp_q, img, true, st);
+        cudaError_t e = cudaMemsetAsync(img + np, 0, sizeof(float) * np, st);
+        if (e != cudaSuccess) {
+            status = DECT_ECUDA;
+            dect::set_error(std::string("dect_admm init: ") + cudaGetErrorString(e));
+            break;
+        }
+        launch_interleave(img, np, A->x + sd.img_off, st);
+    }
+    A->cF += 4 * A->P.init_udm_iters;
+    cudaError_t fe = cudaFreeAsync(work, st);
+    if (status != DECT_OK) return status;
+    CUDA_TRY(fe);
+    return DECT_OK;
+}
+
 static dect_status enq_initialize(dect_admm* A, cudaStream_t st) {
     const int B = A->B;
     for (int b = 0; b < B; ++b)
@@ -860,11 +899,16 @@ static dect_status enq_initialize(dect_admm* A, cudaStream_t st) {
         CUDA_TRY(cudaMemsetAsync(A->uy, 0, sizeof(float4) * A->n_img, st));
         CUDA_TRY(cudaMemsetAsync(A->z, 0, sizeof(float2) * A->n_img, st));
         CUDA_TRY(cudaMemsetAsync(A->uz, 0, sizeof(float2) * A->n_img, st));
-        launch_udm_init(A->ds, A->rays.map(B), A->rays.total, A->spec->dev(), A->meas, A->a, A->mu, A->P.rho0_p,
-                        A->P.init_udm_iters, (float)A->spec->abar_low, A->P.lm_mu0, A->prec, st);
-        A->cF += 4 * A->P.init_udm_iters;
-        launch_reset_scalars(A->sc, B, A->P.rho0_c, A->P.rho0_p, st);
-        enq_pcg(A, A->P.init_pcg_iters, false, A->Hn, st);
+        if (A->P.init == DECT_INIT_CDM_FBP) {
+            const dect_status s = enq_cdm_fbp_start(A, st);
+            if (s != DECT_OK) return s;
+        } else {
+            launch_udm_init(A->ds, A->rays.map(B), A->rays.total, A->spec->dev(), A->meas, A->a, A->mu,
+                            A->P.rho0_p, A->P.init_udm_iters, (float)A->spec->abar_low, A->P.lm_mu0, A->prec, st);
+            A->cF += 4 * A->P.init_udm_iters;
+            launch_reset_scalars(A->sc, B, A->P.rho0_c, A->P.rho0_p, st);
+            enq_pcg(A, A->P.init_pcg_iters, false, A->Hn, st);
+        }
     }
     launch_init_image(A->ds, A->pix.map(B), A->pix.total, A->d_has_x0, A->x0, A->x, (float)A->P.kappa, st);
     enq_project(A, A->x, A->Rx, st);
@@ -996,6 +1040,16 @@ extern "C" dect_status dect_admm_create(dect_geom* const* geoms, int32_t B, cons
         DECT_FAIL(DECT_EUNSUPPORTED, "dect_admm_create: the LM x CG scheme runs with float32 storage only");
     if (P->bp_view_groups < -1 || P->bp_view_groups > 16)
         DECT_FAIL(DECT_EINVAL, "dect_admm_create: bp_view_groups must be in [-1, 16]");
+    if (P->init != DECT_INIT_PCG && P->init != DECT_INIT_CDM_FBP)
+        DECT_FAIL(DECT_EINVAL, "dect_admm_create: init must be DECT_INIT_PCG or DECT_INIT_CDM_FBP");
+    if (P->init == DECT_INIT_CDM_FBP)
+        for (int b = 0; b < B; ++b) {
+            if (!geoms[b]) break;  // reported below
+            const auto& gd = geoms[b]->desc;
+            if (gd.kind == DECT_FAN_FLAT ? !span_is(gd.angle_span_rad, 2.0 * M_PI)
+                                         : !(span_is(gd.angle_span_rad, M_PI) || span_is(gd.angle_span_rad, 2.0 * M_PI)))
+                DECT_FAIL(DECT_EUNSUPPORTED, "dect_admm_create: the CDM-FBP start needs full scans (FBP)");
+        }
     if (P->m_udm < 1 || P->n_pcg < 1 || P->m_udm > 64 || P->n_pcg > 64)
         DECT_FAIL(DECT_EINVAL, "dect_admm_create: m_udm and n_pcg must be in [1, 64]");
     if (P->init_udm_iters < 0 || P->init_pcg_iters < 1 || P->init_udm_iters > 1000 || P->init_pcg_iters > 1000)

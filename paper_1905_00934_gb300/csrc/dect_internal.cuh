@@ -240,6 +240,7 @@ struct FbpDev {
 void launch_fbp(const FbpDev& f, int nch, const float* sino, float* q, float* x, bool clamp, cudaStream_t st);
 void launch_cdm_start(int64_t n, const float* m_l, float inv_abar, float mu0, float* a_c, float* a_p, float* mu,
                       float* zero, cudaStream_t st);
+void launch_unpack_meas(int64_t n, const float4* meas, float* planar, cudaStream_t st);
 cudaError_t fbp_init_attributes();
 
 // admm.cu helpers are local to that file.

@@ -120,6 +120,21 @@ __global__ void k_cdm_start(int64_t n, const float* __restrict__ m_l, float inv_
     zero[r] = 0.0f;
 }
 
+// planar copies of a slice's measurements {m_h, m_l, w_h, w_l} (the solver keeps them interleaved)
+__global__ void k_unpack_meas(int64_t n, const float4* __restrict__ meas, float* __restrict__ planar) {
+    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n) return;
+    const float4 m = __ldg(meas + r);
+    planar[r] = m.x;
+    planar[n + r] = m.y;
+    planar[2 * n + r] = m.z;
+    planar[3 * n + r] = m.w;
+}
+
+void launch_unpack_meas(int64_t n, const float4* meas, float* planar, cudaStream_t st) {
+    k_unpack_meas<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, meas, planar);
+}
+
 void launch_fbp(const FbpDev& f, int nch, const float* sino, float* q, float* x, bool clamp, cudaStream_t st) {
     const size_t smem = sizeof(float) * (f.nb + (f.nb + 1) / 2);
     k_fbp_filter<<<dim3((unsigned)f.nv, (unsigned)nch), kFbpFilterThreads, smem, st>>>(f, sino, q, clamp ? 1 : 0);

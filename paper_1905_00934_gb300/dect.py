@@ -23,6 +23,7 @@ F32, F64 = 0, 1
 STORE_F32, STORE_F16, STORE_BF16 = 0, 1, 2
 SCHEME_UDM_PCG, SCHEME_LM_CG = 0, 1
 PRECOND_NONE, PRECOND_CIRCULANT, PRECOND_RAMP = 0, 1, 2
+INIT_PCG, INIT_CDM_FBP = 0, 1
 RAY_ACCEPTED, RAY_REJECTED, RAY_NONFINITE = 0, 1, 2
 # dect_admm_get array selectors
 X, RX, A, UA, Y, UY, Z, UZ, MU, H = range(10)
@@ -48,7 +49,7 @@ class Params(ctypes.Structure):
                 ("rho_mu", ctypes.c_double), ("rho_tau", ctypes.c_double), ("lm_mu0", ctypes.c_double),
                 ("kappa", ctypes.c_double), ("init_udm_iters", ctypes.c_int32), ("init_pcg_iters", ctypes.c_int32),
                 ("precondition", ctypes.c_int32), ("use_graph", ctypes.c_int32), ("bp_view_groups", ctypes.c_int32),
-                ("storage", ctypes.c_int32), ("scheme", ctypes.c_int32)]
+                ("storage", ctypes.c_int32), ("scheme", ctypes.c_int32), ("init", ctypes.c_int32)]
 
 
 class Stats(ctypes.Structure):

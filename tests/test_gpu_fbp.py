@@ -146,3 +146,55 @@ def test_cdm_fbp_small_parallel_matches_oracle(cuda_dev):
 def test_cdm_fbp_full_size_fan_matches_oracle(cuda_dev):
     # 512 x 512, 720 views x 1024 bins fan beam, the benchmark's slice 0 (metal inserts: starved rays)
     _check_cdm(baggage_fan_case(slice_index=0), cuda_dev, 20, 1e-3)
+
+
+def test_solver_cdm_fbp_start_matches_oracle(cuda_dev):
+    # the paper's initial image (Sec. 4) in the solver: CDM-FBP Compton, clamped, x_p = kappa x_c;
+    # then 3 UDM1-PCG1 iterations from it
+    from oracle import admm as oadmm
+    from paper_1905_00934_gb300 import Geometry, Solver, Spectra, dect
+
+    c = small_parallel_case(e_ref_kev=100.0)
+    for k in ("m_h", "m_l", "w_h", "w_l"):
+        c[k] = _r32(c[k])
+    prob = oadmm.Problem(c["geom"], c["spectra"], c["m_h"], c["m_l"], c["w_h"], c["w_l"],
+                         oadmm.Params(init=oadmm.INIT_CDM_FBP))
+    x0 = np.stack(oadmm.initial_image(prob))
+    st = oadmm.state_from_image(prob, x0[0], x0[1])
+    geo = Geometry(c["geom"])
+    sol = Solver([geo], Spectra.from_tables(c["spectra"]), init=dect.INIT_CDM_FBP)
+    sol.set_data(0, *[to_dev(c[k], cuda_dev) for k in ("m_h", "m_l", "w_h", "w_l")])
+    sol.reconstruct(0)
+    x = sol.get(0, dect.X).cpu().numpy()
+    e0 = (rel_l2(x[0], x0[0]), rel_l2(x[1], x0[1]))
+    for _ in range(3):
+        st = oadmm.admm_iteration(prob, st)
+    sol.step(3)
+    x = sol.get(0, dect.X).cpu().numpy()
+    e3 = (rel_l2(x[0], st.x[0]), rel_l2(x[1], st.x[1]))
+    print(f"CDM-FBP start: rel-L2 {e0[0]:.2e} / {e0[1]:.2e}; after 3 iterations {e3[0]:.2e} / {e3[1]:.2e}")
+    assert max(e0) <= 1e-4 and max(e3) <= 1e-4
+
+
+def test_solver_cdm_fbp_start_batched_equals_single(cuda_dev, sinos):
+    from paper_1905_00934_gb300 import Geometry, Solver, Spectra, dect
+
+    cases = [small_parallel_case(e_ref_kev=100.0),
+             make_case(_geoms()["fan_ragged"], lambda gg, r: baggage_phantom(gg, r, n_objects=8), 2e5, 91,
+                       e_ref_kev=100.0)]
+    spec = Spectra.from_tables(cases[0]["spectra"])
+    geos = [Geometry(cc["geom"]) for cc in cases]
+    data = [[to_dev(cc[k], cuda_dev) for k in ("m_h", "m_l", "w_h", "w_l")] for cc in cases]
+    both = Solver(geos, spec, init=dect.INIT_CDM_FBP, bp_view_groups=4)
+    for b in range(2):
+        both.set_data(b, *data[b])
+    both.reconstruct(2)
+    for b in range(2):
+        one = Solver([geos[b]], spec, init=dect.INIT_CDM_FBP, bp_view_groups=4)
+        one.set_data(0, *data[b])
+        one.reconstruct(2)
+        assert torch.equal(one.get(0, dect.X), both.get(b, dect.X))
+    # a short scan cannot start from FBP
+    with pytest.raises(dect.DectError):
+        Solver([Geometry(G.parallel_geometry(16, 30, 24, 0.1, 0.1, span_rad=0.75 * math.pi))], spec,
+               init=dect.INIT_CDM_FBP)
