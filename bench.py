@@ -556,6 +556,63 @@ def run_study(args):
     return 0
 
 
+def run_uneven(args):
+    """Batching on the uneven-slice workload: one batched solver against the plain form (single-slice
+    solvers one after another, eager launches, occupancy view groups) and single-slice solvers with
+    graph and autotuner, as device time per ADMM iteration (after the initial image, CUDA events)."""
+    import torch
+
+    import __graft_entry__
+
+    __graft_entry__.build()
+    from paper_1905_00934_gb300 import Geometry, Solver, Spectra
+    from synth.workloads import BAGGAGE_KAPPA, quick_fan_case, uneven_batch_shapes
+    from concurrent.futures import ThreadPoolExecutor
+
+    dev = torch.device("cuda", 0)
+    shapes = uneven_batch_shapes(args.uneven)
+    with ThreadPoolExecutor(max_workers=16) as ex:
+        cases = list(ex.map(lambda b: quick_fan_case(b, *shapes[b]), range(len(shapes))))
+    spec = Spectra.from_tables(cases[0]["spectra"])
+    geo = [Geometry(c["geom"]) for c in cases]
+    data = [[torch.tensor(np.ascontiguousarray(c[k]), dtype=torch.float32, device=dev)
+             for k in ("m_h", "m_l", "w_h", "w_l")] for c in cases]
+    iters = 10
+
+    def timed(solvers):
+        for s in solvers:
+            s.reconstruct(0)
+            s.step(2)  # graph capture outside the timing
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for s in solvers:
+            s.step(iters)
+        e1.record()
+        e1.synchronize()
+        return e0.elapsed_time(e1) / iters
+
+    out = {}
+    batched = Solver(geo, spec, kappa=BAGGAGE_KAPPA)
+    for b in range(len(cases)):
+        batched.set_data(b, *data[b])
+    out["batched_ms_per_iteration"] = timed([batched])
+    del batched
+    for name, params in (("plain", dict(use_graph=0, bp_view_groups=-1)), ("plain_graph_autotuned", {})):
+        singles = []
+        for b in range(len(cases)):
+            s1 = Solver([geo[b]], spec, kappa=BAGGAGE_KAPPA, **params)
+            s1.set_data(0, *data[b])
+            singles.append(s1)
+        out[name + "_ms_per_iteration"] = timed(singles)
+        del singles
+    out["batched_over_plain"] = out["plain_ms_per_iteration"] / out["batched_ms_per_iteration"]
+    out["batched_over_plain_graph_autotuned"] = (out["plain_graph_autotuned_ms_per_iteration"]
+                                                 / out["batched_ms_per_iteration"])
+    print(json.dumps({"uneven_batch": {"slices": len(cases), "shapes_n_views_bins": shapes, "iterations_timed": iters,
+                                       **out}}), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -574,9 +631,14 @@ def main():
     ap.add_argument("--study", action="store_true",
                     help="print xi trajectories of UDM-PCG variants, plain CG and LM x CG instead of the bench line")
     ap.add_argument("--study-iters", type=int, default=200)
+    ap.add_argument("--uneven", type=int, default=0, metavar="SLICES",
+                    help="batched vs plain on SLICES seeded uneven fan slices (256..1024 px, 360..1440 views, "
+                         "512..2048 bins), per ADMM iteration")
     args = ap.parse_args()
     if args.study:
         return run_study(args)
+    if args.uneven:
+        return run_uneven(args)
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
