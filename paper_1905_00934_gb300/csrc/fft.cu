@@ -90,6 +90,81 @@ __device__ void bitrev_permute(float2* buf, int logn, int lane, int nlanes) {
 
 __host__ __device__ int precond_cols_per_block(int py) { return py >= 4096 ? 2 : (py >= 2048 ? 4 : 8); }
 
+// The same radix-2 DIT FFT (same butterflies, twiddles and operation order, so the same results) held
+// in registers by one warp, for lengths 2^LOG with 5 <= LOG <= 10: lane t holds elements 32 m + t of the
+// bit-reversed sequence in v[m]. Stages with half < 32 pair lanes t and t ^ half (shuffles); stages with
+// half >= 32 pair slots m and m + half/32 of the same lane. No shared memory, no barriers.
+template <int LOG>
+__device__ __forceinline__ void fft_warp_regs(float2 (&v)[1 << (LOG - 5)], int lane, bool inverse,
+                                              const float2* __restrict__ tw) {
+    constexpr int M = 1 << (LOG - 5);
+#pragma unroll
+    for (int s = 0; s < 5; ++s) {
+        const int half = 1 << s;
+        float2 w = __ldg(tw + (lane & (half - 1)) * (kFftMax >> (s + 1)));
+        if (inverse) w.y = -w.y;
+        const bool upper = (lane & half) != 0;
+#pragma unroll
+        for (int m = 0; m < M; ++m) {
+            const float2 o = make_float2(__shfl_xor_sync(0xffffffffu, v[m].x, half),
+                                         __shfl_xor_sync(0xffffffffu, v[m].y, half));
+            const float2 x0 = upper ? o : v[m];
+            const float2 t = cmul(w, upper ? v[m] : o);
+            v[m] = upper ? make_float2(x0.x - t.x, x0.y - t.y) : make_float2(x0.x + t.x, x0.y + t.y);
+        }
+    }
+#pragma unroll
+    for (int s = 5; s < LOG; ++s) {
+        const int hs = 1 << (s - 5);
+#pragma unroll
+        for (int m = 0; m < M; ++m) {
+            if (m & hs) continue;
+            float2 w = __ldg(tw + (((m & (hs - 1)) << 5) + lane) * (kFftMax >> (s + 1)));
+            if (inverse) w.y = -w.y;
+            const float2 x0 = v[m];
+            const float2 t = cmul(w, v[m + hs]);
+            v[m] = make_float2(x0.x + t.x, x0.y + t.y);
+            v[m + hs] = make_float2(x0.x - t.x, x0.y - t.y);
+        }
+    }
+}
+
+// Column group of k_fft_cols on the register path: 8 columns, warp c owns column c (blockDim 256).
+// buf holds the group's columns in bit-reversed order on entry; on return, rows in natural order.
+template <int LOG>
+__device__ void cols_regs(float2* buf, const float* __restrict__ hs, int px, int k0,
+                          const float2* __restrict__ tw) {
+    constexpr int M = 1 << (LOG - 5), py = 1 << LOG, C = 8;
+    const int c = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    float2* col = buf + c * py;
+    float2 v[M];
+#pragma unroll
+    for (int m = 0; m < M; ++m) v[m] = col[(m << 5) + lane];
+    fft_warp_regs<LOG>(v, lane, false, tw);
+    if (hs) {
+#pragma unroll
+        for (int m = 0; m < M; ++m) col[(m << 5) + lane] = v[m];
+        __syncthreads();
+        for (int e = threadIdx.x; e < C * py; e += blockDim.x) {
+            const int cc = e % C, j = e / C;
+            const int k = k0 + cc;
+            const float h = k < px ? __ldg(hs + (size_t)j * px + k) : 0.f;
+            float2& x = buf[cc * py + j];
+            x.x *= h;
+            x.y *= h;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int m = 0; m < M; ++m) v[m] = col[bitrev((m << 5) + lane, LOG)];
+        fft_warp_regs<LOG>(v, lane, true, tw);
+    }
+    // every lane has passed the shuffles above, so all reads of this column are done
+#pragma unroll
+    for (int m = 0; m < M; ++m) col[(m << 5) + lane] = v[m];
+}
+
+
+
 // forward row FFTs of the image rows (Compton + i PE), zero-padded to px
 __global__ void __launch_bounds__(256) k_prec_rows_fwd(const SliceDesc* __restrict__ dsl, BlockMap map,
                                                        const float2* __restrict__ r, float2* __restrict__ Z,
@@ -132,23 +207,34 @@ __global__ void __launch_bounds__(256) k_fft_cols(const SliceDesc* __restrict__ 
         buf[c * py + bitrev(j, lp)] = v;
     }
     __syncthreads();
-    const int lanes = blockDim.x / C;
-    const int c = threadIdx.x / lanes, lane = threadIdx.x % lanes;
-    fft_stages(buf + c * py, lp, false, tw, lane, lanes);
-    if (H) {
-        const float* hs = H + d.h_off;
-        for (int e = threadIdx.x; e < C * py; e += blockDim.x) {
-            const int cc = e % C, j = e / C;
-            const int k = k0 + cc;
-            const float h = k < px ? __ldg(hs + (size_t)j * px + k) : 0.f;
-            float2& v = buf[cc * py + j];
-            v.x *= h;
-            v.y *= h;
+    const float* hs = H ? H + d.h_off : nullptr;
+    switch (lp) {  // one slice per block, so the branch is uniform
+        case 5: cols_regs<5>(buf, hs, px, k0, tw); break;
+        case 6: cols_regs<6>(buf, hs, px, k0, tw); break;
+        case 7: cols_regs<7>(buf, hs, px, k0, tw); break;
+        case 8: cols_regs<8>(buf, hs, px, k0, tw); break;
+        case 9: cols_regs<9>(buf, hs, px, k0, tw); break;
+        case 10: cols_regs<10>(buf, hs, px, k0, tw); break;
+        default: {  // py < 32 or py >= 2048: shared-memory stages, C columns of blockDim/C threads each
+            const int lanes = blockDim.x / C;
+            const int c = threadIdx.x / lanes, lane = threadIdx.x % lanes;
+            fft_stages(buf + c * py, lp, false, tw, lane, lanes);
+            if (hs) {
+                for (int e = threadIdx.x; e < C * py; e += blockDim.x) {
+                    const int cc = e % C, j = e / C;
+                    const int k = k0 + cc;
+                    const float h = k < px ? __ldg(hs + (size_t)j * px + k) : 0.f;
+                    float2& v = buf[cc * py + j];
+                    v.x *= h;
+                    v.y *= h;
+                }
+                __syncthreads();
+                bitrev_permute(buf + c * py, lp, lane, lanes);
+                fft_stages(buf + c * py, lp, true, tw, lane, lanes);
+            }
         }
-        __syncthreads();
-        bitrev_permute(buf + c * py, lp, lane, lanes);
-        fft_stages(buf + c * py, lp, true, tw, lane, lanes);
     }
+    __syncthreads();
     for (int e = threadIdx.x; e < C * rows_out; e += blockDim.x) {
         const int cc = e % C, j = e / C;
         const int k = k0 + cc;
