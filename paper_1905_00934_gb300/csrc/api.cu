@@ -519,7 +519,7 @@ struct dect_admm {
     int sweep_groups_in_use = 1;     // view groups per tile (sweep_C CTAs of the kernel's groups each)
     float2* bp_partial = nullptr;    // [sweep_C][n_img] partial images of the backprojector
     int64_t n_img = 0, n_sino = 0, n_tx = 0, n_ty = 0, n_fft = 0, n_h = 0, n_stage = 0;
-    int max_px = 0, max_py = 0;
+    int max_px = 0, max_py = 0, min_px = 1 << 30;
     float2 *x = nullptr, *r = nullptr, *s = nullptr, *p = nullptr, *Ap = nullptr, *z = nullptr, *uz = nullptr;
     float2 *x0 = nullptr, *truth = nullptr, *Z = nullptr;
     void *Rx = nullptr, *a = nullptr, *ua = nullptr, *q = nullptr;  // sinogram vectors, storage format `prec`
@@ -619,7 +619,7 @@ static void enq_precond(dect_admm* A, const float* H, const float2* r, float2* s
     pb(A, st);
     if (A->P.precondition) {
         launch_precond(A->ds, A->rows.map(B), A->rows.total, A->cols.map(B), A->cols.total, H, r, s, A->Z, A->part_rs,
-                       A->tw, A->max_px, A->max_py, st);
+                       A->tw, A->max_px, A->min_px, st);
         pe(A, DECT_PHASE_PRECOND, 3, st);
     } else {
         launch_identity_precond(A->ds, A->rows.map(B), A->rows.total, r, s, A->part_rs, st);
@@ -1125,6 +1125,7 @@ extern "C" dect_status dect_admm_create(dect_geom* const* geoms, int32_t B, cons
         A->n_h += (int64_t)sd.px * sd.py;
         A->max_px = std::max(A->max_px, sd.px);
         A->max_py = std::max(A->max_py, sd.py);
+        A->min_px = std::min(A->min_px, sd.px);
         max_np = std::max(max_np, np);
         max_nr = std::max(max_nr, nr);
         A->hs.push_back(sd);

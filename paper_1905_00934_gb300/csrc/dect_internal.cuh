@@ -220,7 +220,7 @@ __host__ __device__ int precond_cols_per_block(int py);
 // s = M^-1 r per slice and partial[2*blk] = <r, s> per channel over the row blocks
 void launch_precond(const SliceDesc* dsl, const BlockMap& rows_map, int nrows_blk, const BlockMap& cols_map,
                     int ncols_blk, const float* H, const float2* r, float2* s, float2* Z, double* partial_rs,
-                    const float2* tw, int max_px, int max_py, cudaStream_t st);
+                    const float2* tw, int max_px, int min_px, cudaStream_t st);
 // H (and the variant without the D^T D term) from R^T R applied to a centred impulse (one slice)
 // (d_dev: the slice's descriptor on the device with fft_off = h_off = 0; cols_map: its column groups)
 void launch_psf_to_response(const SliceDesc* d_dev, const SliceDesc& d, const BlockMap& cols_map, int ncols,

@@ -287,14 +287,110 @@ __global__ void __launch_bounds__(256) k_prec_rows_inv(const SliceDesc* __restri
     }
 }
 
+// Row passes on the register path (every slice's padded row length in 32..1024): one warp per row,
+// blockDim 32, the row staged in shared memory only for the bit-reversal.
+template <int LOG>
+__device__ void row_fwd_regs(const float2* __restrict__ row, int nx, float2* __restrict__ zr, float2* buf,
+                             const float2* __restrict__ tw) {
+    constexpr int M = 1 << (LOG - 5), n = 1 << LOG;
+    const int lane = threadIdx.x;
+    for (int t = lane; t < n; t += 32) buf[bitrev(t, LOG)] = t < nx ? __ldg(row + t) : make_float2(0.f, 0.f);
+    __syncwarp();
+    float2 v[M];
+#pragma unroll
+    for (int m = 0; m < M; ++m) v[m] = buf[(m << 5) + lane];
+    fft_warp_regs<LOG>(v, lane, false, tw);
+#pragma unroll
+    for (int m = 0; m < M; ++m) zr[(m << 5) + lane] = v[m];
+}
+
+template <int LOG>
+__device__ void row_inv_regs(const float2* __restrict__ zr, float2* buf, const float2* __restrict__ tw, float scale,
+                             const float2* __restrict__ r, float2* __restrict__ s_out, int nx, double& dc, double& dp) {
+    constexpr int M = 1 << (LOG - 5), n = 1 << LOG;
+    const int lane = threadIdx.x;
+    for (int t = lane; t < n; t += 32) buf[bitrev(t, LOG)] = zr[t];
+    __syncwarp();
+    float2 v[M];
+#pragma unroll
+    for (int m = 0; m < M; ++m) v[m] = buf[(m << 5) + lane];
+    fft_warp_regs<LOG>(v, lane, true, tw);
+#pragma unroll
+    for (int m = 0; m < M; ++m) {
+        const int t = (m << 5) + lane;
+        if (t < nx) {
+            const float2 x = make_float2(v[m].x * scale, v[m].y * scale);
+            s_out[t] = x;
+            const float2 rv = __ldg(r + t);
+            dc += (double)rv.x * x.x;
+            dp += (double)rv.y * x.y;
+        }
+    }
+}
+
+__global__ void __launch_bounds__(32) k_prec_rows_fwd_w(const SliceDesc* __restrict__ dsl, BlockMap map,
+                                                        const float2* __restrict__ r, float2* __restrict__ Z,
+                                                        const float2* __restrict__ tw) {
+    extern __shared__ float2 buf[];
+    int j;
+    const int s = slice_of(map, blockIdx.x, j);
+    const SliceDesc& d = dsl[s];
+    const float2* row = r + d.img_off + (size_t)j * d.g.nx;
+    float2* zr = Z + d.fft_off + (size_t)j * d.px;
+    switch (d.lpx) {
+        case 5: row_fwd_regs<5>(row, d.g.nx, zr, buf, tw); break;
+        case 6: row_fwd_regs<6>(row, d.g.nx, zr, buf, tw); break;
+        case 7: row_fwd_regs<7>(row, d.g.nx, zr, buf, tw); break;
+        case 8: row_fwd_regs<8>(row, d.g.nx, zr, buf, tw); break;
+        case 9: row_fwd_regs<9>(row, d.g.nx, zr, buf, tw); break;
+        default: row_fwd_regs<10>(row, d.g.nx, zr, buf, tw); break;
+    }
+}
+
+__global__ void __launch_bounds__(32) k_prec_rows_inv_w(const SliceDesc* __restrict__ dsl, BlockMap map,
+                                                        const float2* __restrict__ Z, const float2* __restrict__ r,
+                                                        float2* __restrict__ s_out, double* __restrict__ partial,
+                                                        const float2* __restrict__ tw) {
+    extern __shared__ float2 buf[];
+    int j;
+    const int s = slice_of(map, blockIdx.x, j);
+    const SliceDesc& d = dsl[s];
+    const float2* zr = Z + d.fft_off + (size_t)j * d.px;
+    const size_t row = d.img_off + (size_t)j * d.g.nx;
+    const float scale = 1.0f / ((float)d.px * (float)d.py);
+    double dc = 0.0, dp = 0.0;
+    switch (d.lpx) {
+        case 5: row_inv_regs<5>(zr, buf, tw, scale, r + row, s_out + row, d.g.nx, dc, dp); break;
+        case 6: row_inv_regs<6>(zr, buf, tw, scale, r + row, s_out + row, d.g.nx, dc, dp); break;
+        case 7: row_inv_regs<7>(zr, buf, tw, scale, r + row, s_out + row, d.g.nx, dc, dp); break;
+        case 8: row_inv_regs<8>(zr, buf, tw, scale, r + row, s_out + row, d.g.nx, dc, dp); break;
+        case 9: row_inv_regs<9>(zr, buf, tw, scale, r + row, s_out + row, d.g.nx, dc, dp); break;
+        default: row_inv_regs<10>(zr, buf, tw, scale, r + row, s_out + row, d.g.nx, dc, dp); break;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        dc += __shfl_down_sync(0xffffffffu, dc, o);
+        dp += __shfl_down_sync(0xffffffffu, dp, o);
+    }
+    if (threadIdx.x == 0) {
+        partial[2 * (size_t)blockIdx.x] = dc;
+        partial[2 * (size_t)blockIdx.x + 1] = dp;
+    }
+}
+
 void launch_precond(const SliceDesc* dsl, const BlockMap& rows_map, int nrows_blk, const BlockMap& cols_map,
                     int ncols_blk, const float* H, const float2* r, float2* s, float2* Z, double* partial_rs,
-                    const float2* tw, int max_px, int max_py, cudaStream_t st) {
-    k_prec_rows_fwd<<<nrows_blk, 256, sizeof(float2) * max_px, st>>>(dsl, rows_map, r, Z, tw);
-    (void)max_py;
+                    const float2* tw, int max_px, int min_px, cudaStream_t st) {
+    const bool warp_rows = min_px >= 32 && max_px <= 1024;
+    if (warp_rows)
+        k_prec_rows_fwd_w<<<nrows_blk, 32, sizeof(float2) * max_px, st>>>(dsl, rows_map, r, Z, tw);
+    else
+        k_prec_rows_fwd<<<nrows_blk, 256, sizeof(float2) * max_px, st>>>(dsl, rows_map, r, Z, tw);
     // C(py) * py <= 8192 complex entries for every py <= 4096
     k_fft_cols<<<ncols_blk, 256, sizeof(float2) * 8192, st>>>(dsl, cols_map, Z, H, 0, 0, tw);
-    k_prec_rows_inv<<<nrows_blk, 256, sizeof(float2) * max_px, st>>>(dsl, rows_map, Z, r, s, partial_rs, tw);
+    if (warp_rows)
+        k_prec_rows_inv_w<<<nrows_blk, 32, sizeof(float2) * max_px, st>>>(dsl, rows_map, Z, r, s, partial_rs, tw);
+    else
+        k_prec_rows_inv<<<nrows_blk, 256, sizeof(float2) * max_px, st>>>(dsl, rows_map, Z, r, s, partial_rs, tw);
 }
 
 // ---- response H from the point response of R^T R ---------------------------------------------
