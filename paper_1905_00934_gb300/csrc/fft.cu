@@ -257,33 +257,27 @@ __global__ void __launch_bounds__(256) k_prec_rows_inv(const SliceDesc* __restri
     __syncthreads();
     fft_stages(buf, lp, true, tw, threadIdx.x, blockDim.x);
     const float scale = 1.0f / ((float)px * (float)d.py);
-    double dc = 0.0, dp = 0.0;
     const size_t row = d.img_off + (size_t)j * nx;
-    for (int t = threadIdx.x; t < nx; t += blockDim.x) {
-        const float2 v = make_float2(buf[t].x * scale, buf[t].y * scale);
-        s_out[row + t] = v;
-        const float2 rv = __ldg(r + row + t);
-        dc += (double)rv.x * v.x;
-        dp += (double)rv.y * v.y;
-    }
-    __shared__ double red[2][8];
-    for (int o = 16; o > 0; o >>= 1) {
-        dc += __shfl_down_sync(0xffffffffu, dc, o);
-        dp += __shfl_down_sync(0xffffffffu, dp, o);
-    }
-    if ((threadIdx.x & 31) == 0) {
-        red[0][threadIdx.x / 32] = dc;
-        red[1][threadIdx.x / 32] = dp;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double a = 0.0, b = 0.0;
-        for (int w = 0; w < (int)blockDim.x / 32; ++w) {
-            a += red[0][w];
-            b += red[1][w];
+    for (int t = threadIdx.x; t < nx; t += blockDim.x)
+        s_out[row + t] = make_float2(buf[t].x * scale, buf[t].y * scale);
+    // <r, s> of the row in the order of the register path (lane l takes t = l, l + 32, ..., then a
+    // shuffle tree), so a slice gets the same partials whichever row kernel a batch launches
+    if (threadIdx.x < 32) {
+        double dc = 0.0, dp = 0.0;
+        for (int t = threadIdx.x; t < nx; t += 32) {
+            const float2 v = make_float2(buf[t].x * scale, buf[t].y * scale);
+            const float2 rv = __ldg(r + row + t);
+            dc = fma((double)rv.x, (double)v.x, dc);
+            dp = fma((double)rv.y, (double)v.y, dp);
         }
-        partial[2 * (size_t)blockIdx.x] = a;
-        partial[2 * (size_t)blockIdx.x + 1] = b;
+        for (int o = 16; o > 0; o >>= 1) {
+            dc += __shfl_down_sync(0xffffffffu, dc, o);
+            dp += __shfl_down_sync(0xffffffffu, dp, o);
+        }
+        if (threadIdx.x == 0) {
+            partial[2 * (size_t)blockIdx.x] = dc;
+            partial[2 * (size_t)blockIdx.x + 1] = dp;
+        }
     }
 }
 
@@ -322,8 +316,8 @@ __device__ void row_inv_regs(const float2* __restrict__ zr, float2* buf, const f
             const float2 x = make_float2(v[m].x * scale, v[m].y * scale);
             s_out[t] = x;
             const float2 rv = __ldg(r + t);
-            dc += (double)rv.x * x.x;
-            dp += (double)rv.y * x.y;
+            dc = fma((double)rv.x, (double)x.x, dc);
+            dp = fma((double)rv.y, (double)x.y, dp);
         }
     }
 }
