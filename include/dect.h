@@ -50,7 +50,7 @@ typedef enum { DECT_F32 = 0, DECT_F64 = 1 } dect_dtype;
 
 /* Storage format of the solver's sinogram-domain vectors (a, u^a, R x, the CG
  * sinogram) and of the projector's pair textures; arithmetic stays float32
- * (float64 in the decomposition's logs and 2x2 solve) in every format. */
+ * (the decomposition included) in every format. */
 typedef enum { DECT_STORE_F32 = 0, DECT_STORE_F16 = 1, DECT_STORE_BF16 = 2 } dect_storage;
 
 /* Per-ray decomposition status codes (uint8 array of dect_decompose_rays). */
@@ -205,8 +205,8 @@ dect_status dect_cdm_fbp(dect_geom* g, const dect_spectra* s, const float* m_h, 
 /* Forward model of Eq. 3 per ray: f_h, f_l at (a_c, a_p) and, if jac is not
  * NULL, the Jacobian jac[r] = {df_h/da_c, df_h/da_p, df_l/da_c, df_l/da_p}
  * ([n_rays][4]). All arrays device memory of `dtype` (DECT_F32: float32
- * exponentials with compensated sums and float64 logs, as the decomposition;
- * DECT_F64: float64 throughout). f_h, f_l may be NULL. */
+ * exponentials with compensated sums, float64 logs of the sums; DECT_F64:
+ * float64 throughout). f_h, f_l may be NULL. */
 dect_status dect_forward_model(const dect_spectra* s, int64_t n_rays, int32_t dtype, const void* a_c, const void* a_p,
                                void* f_h, void* f_l, void* jac, void* stream);
 
