@@ -9,7 +9,6 @@ amplifies rounding by w J_p / rho ~ 500 and flips LM accept/reject decisions, so
 the Compton image is held to 1e-4 and the PE deviation is reported (bounded loosely)."""
 import numpy as np
 import pytest
-import torch
 
 from conftest import rel_l2, to_dev
 from oracle import admm as oadmm

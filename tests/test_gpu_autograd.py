@@ -16,7 +16,6 @@ from conftest import rel_l2
 from oracle import projector as oproj
 from oracle import spectral as ospec
 from synth import spectra as sspec
-from synth.geometry import baggage_fan_geometry
 
 pytestmark = pytest.mark.gpu
 

@@ -12,7 +12,6 @@ import os
 
 import numpy as np
 import pytest
-import torch
 
 from conftest import rel_l2, to_dev
 from oracle import admm as oadmm

@@ -1,6 +1,5 @@
 """Pins for the oracle's ADMM pieces: D, shrinkage, preconditioner, PCG (Eq. 12), the
 iteration (Eq. 9-13), its operation counts (Table 1) and its convergence."""
-import math
 
 import numpy as np
 import pytest

@@ -4,7 +4,7 @@ import math
 import numpy as np
 import pytest
 
-from oracle import fbp, spectral
+from oracle import fbp
 from synth import geometry as G
 from synth import phantom as P
 from synth import spectra
