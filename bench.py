@@ -168,12 +168,36 @@ def _oracle_sample(n_iters: int, case=None):
     return t_init, times, _clib.num_threads(), (prob, st)
 
 
+def _oracle_phases(prob, st):
+    """Seconds of one application of each phase of an iteration in the oracle, on its current state:
+    R and R^T of both bases, the preconditioner on both bases, one LM iteration of every ray (Eq. 13)."""
+    from oracle import spectral
+
+    out = {}
+    t = time.perf_counter()
+    prob.R(st.x)
+    out["R_both_bases"] = time.perf_counter() - t
+    t = time.perf_counter()
+    prob.RT(st.a)
+    out["RT_both_bases"] = time.perf_counter() - t
+    t = time.perf_counter()
+    prob.M(st.x, prob.H)
+    out["preconditioner_both_bases"] = time.perf_counter() - t
+    v = st.Rx - st.ua
+    t = time.perf_counter()
+    spectral.udm(prob.spec, prob.m_h, prob.m_l, prob.w_h, prob.w_l, v[0], v[1], st.rho[0], st.rho[1], 1,
+                 st.a[0], st.a[1], st.mu.copy())
+    out["udm_one_lm_iteration"] = time.perf_counter() - t
+    return {k: round(v, 4) for k, v in out.items()}
+
+
 def cpu_baseline():
-    t_init, times, cores, _ = _oracle_sample(2)
+    t_init, times, cores, (prob, st) = _oracle_sample(2)
     per_slice = t_init + ITERS * float(np.mean(times))
     return {"value": 1.0 / per_slice, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"FP64 oracle on one 512^2 slice: set-up + initial image ({t_init:.1f} s) and 2 of the "
-                      f"{ITERS} ADMM iterations ({np.mean(times):.2f} s each), iterations scaled x{ITERS // 2}"}
+                      f"{ITERS} ADMM iterations ({np.mean(times):.2f} s each), iterations scaled x{ITERS // 2}",
+            "phases_s": _oracle_phases(prob, st)}
 
 
 def run_reference(args):
