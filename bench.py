@@ -34,6 +34,7 @@ METRIC = "slices/s to fixed PE error (UDM1-PCG1, 100 ADMM iterations), 512^2 x 7
 UNIT = "slices/s"
 ITERS = 100
 GOLDEN = os.path.join(ROOT, "tests", "golden", "baggage_fan_512_xi.json")
+GOLDEN_CDM_FBP = os.path.join(ROOT, "tests", "golden", "baggage_fan_512_cdm_fbp.json")
 
 
 def _peaks():
@@ -107,9 +108,9 @@ def _dist():
     return ws, rank, local
 
 
-def _golden():
+def _golden(path=None):
     try:
-        with open(GOLDEN) as f:
+        with open(path or GOLDEN) as f:
             return json.load(f)
     except Exception:
         return None
@@ -399,6 +400,9 @@ def run_dect(args):
               for k, t in enumerate((cases[0]["truth_c"], cases[0]["truth_p"]))]
         comparison["cdm_fbp"] = {"ms_per_slice": c0.elapsed_time(c1) / B, "decomposition_iterations": CDM_ITERS,
                                  "xi_c_db": xi[0], "xi_p_db": xi[1], "reaches_target": bool(xi[1] <= target)}
+        gold_cdm = _golden(GOLDEN_CDM_FBP)
+        if gold_cdm is not None and gold_cdm.get("decomposition_iterations") == CDM_ITERS:
+            comparison["cdm_fbp"].update({"oracle_xi_c_db": gold_cdm["xi_c"], "oracle_xi_p_db": gold_cdm["xi_p"]})
 
     # end to end through the C ABI: pinned host measurements in, image out, every step
     host_in = [[t.cpu().pin_memory() for t in d] for d in dev_data]
