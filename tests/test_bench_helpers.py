@@ -25,3 +25,14 @@ def test_weight_count_grows_with_the_workload():
     large = G.fan_geometry(128, 180, 256)
     ratio = bench.joseph_weight_count(large) / bench.joseph_weight_count(small)
     assert 7.0 < ratio < 9.0  # views x bins x samples per ray: ~2 x 2 x 2
+
+
+def test_stored_oracle_values_load():
+    # the quality gate and the CDM-FBP comparison read these files written by tests/golden scripts
+    import bench
+
+    gold = bench._golden()
+    assert gold is not None and len(gold["xi_p"]) == bench.ITERS + 1
+    cdm = bench._golden(bench.GOLDEN_CDM_FBP)
+    assert cdm is not None and cdm["decomposition_iterations"] == bench.CDM_ITERS
+    assert set(cdm) >= {"xi_c", "xi_p"}
