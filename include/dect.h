@@ -342,6 +342,26 @@ typedef struct {
 } dect_stats;
 dect_status dect_admm_stats(dect_admm* a, int32_t slice, dect_stats* out, void* stream);
 
+/* Checkpoint and resume of a solver. The state image holds, for every slice, the
+ * iterate of Sec. 3.2-3.3 (x, R x, a, y, z and the scaled duals u^a, u^y, u^z),
+ * rho and the per-slice scalars, the LM damping and status per ray, the CG
+ * vectors, the comparison scheme's vectors and scalars, the measurements, x0 and
+ * the truth, and the host-side counters; not the geometry, spectra or
+ * parameters, nor what is derived from them (textures, preconditioner).
+ * dect_admm_state_bytes: the image's size in bytes.
+ * dect_admm_save: writes the image to host memory dst_host (capacity `bytes`,
+ * at least the size; caller-owned) after the work already queued on `stream`,
+ * and synchronises `stream`.
+ * dect_admm_load: restores an image into a solver created with the same slice
+ * shapes (nx, ny, n_views, n_bins per slice, in order), storage and scheme;
+ * anything else, or a wrong size or header, returns DECT_EINVAL without
+ * touching the solver's state. With the same parameters, dect_admm_step then
+ * continues exactly (bit for bit) as the saved solver would have. Synchronises
+ * `stream`. */
+dect_status dect_admm_state_bytes(const dect_admm* a, size_t* bytes);
+dect_status dect_admm_save(dect_admm* a, void* dst_host, size_t bytes, void* stream);
+dect_status dect_admm_load(dect_admm* a, const void* src_host, size_t bytes, void* stream);
+
 /* Kernel groups timed by dect_admm_profile. */
 enum {
     DECT_PHASE_TEXTURE = 0,      /* pair textures of the image the projector reads */

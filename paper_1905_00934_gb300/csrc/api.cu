@@ -1395,6 +1395,148 @@ extern "C" dect_status dect_admm_get(const dect_admm* A, int32_t b, int32_t whic
     return DECT_OK;
 }
 
+// ---- checkpoint / resume ----------------------------------------------------------------------
+
+namespace {
+struct Segment {
+    void* p;
+    size_t bytes;
+};
+
+struct CkptHeader {
+    char magic[8];
+    int32_t version, B, storage, scheme, initialized, n_segments;
+    int64_t n_img, n_sino, cR, cRT, cF, cL;
+};
+
+constexpr char kCkptMagic[8] = {'D', 'E', 'C', 'T', 'C', 'K', 'P', 'T'};
+constexpr int32_t kCkptVersion = 1;
+}  // namespace
+
+// The device arrays that carry state from one iteration to the next (and the data), with the byte
+// counts of their allocations in dect_admm_create.
+static std::vector<Segment> state_segments(const dect_admm* A) {
+    std::vector<Segment> v;
+    auto add = [&](const void* p, size_t bytes) {
+        if (p && bytes) v.push_back(Segment{const_cast<void*>(p), bytes});
+    };
+    const size_t ni = (size_t)A->n_img, ns = (size_t)A->n_sino, B = (size_t)A->B;
+    for (const float2* p : {A->x, A->r, A->s, A->p, A->Ap, A->z, A->uz, A->x0, A->truth}) add(p, sizeof(float2) * ni);
+    for (const void* p : {A->Rx, A->a, A->ua, A->q}) add(p, ns * sino_bytes(A->prec));
+    add(A->y, sizeof(float4) * ni);
+    add(A->uy, sizeof(float4) * ni);
+    add(A->meas, sizeof(float4) * ns);
+    add(A->mu, sizeof(float) * ns);
+    add(A->status, sizeof(uint8_t) * ns);
+    add(A->sc, sizeof(SliceScalars) * B);
+    add(A->d_has_x0, sizeof(int) * B);
+    if (A->P.scheme == DECT_SCHEME_LM_CG) {
+        add(A->ls, sizeof(LmScalars) * B);
+        add(A->lm_scale, sizeof(float) * B);
+        for (const float* p : {A->lm_d, A->lm_r, A->lm_p, A->lm_Ap}) add(p, sizeof(float) * ni);
+        for (const float* p : {A->lm_e, A->lm_g, A->lm_q, A->lm_Rd}) add(p, sizeof(float) * ns);
+        add(A->lm_s0, sizeof(float2) * ns);
+    }
+    return v;
+}
+
+// header, then per slice {nx, ny, n_views, n_bins, has_x0, has_truth, has_data}, then the segments
+static size_t ckpt_bytes(const dect_admm* A, const std::vector<Segment>& segs) {
+    size_t n = sizeof(CkptHeader) + sizeof(int32_t) * 7 * (size_t)A->B;
+    for (const Segment& g : segs) n += g.bytes;
+    return n;
+}
+
+extern "C" dect_status dect_admm_state_bytes(const dect_admm* A, size_t* bytes) {
+    clear_stale_error();
+    if (!A || !bytes) DECT_FAIL(DECT_EINVAL, "dect_admm_state_bytes: null argument");
+    *bytes = ckpt_bytes(A, state_segments(A));
+    return DECT_OK;
+}
+
+extern "C" dect_status dect_admm_save(dect_admm* A, void* dst_host, size_t bytes, void* stream) {
+    clear_stale_error();
+    if (!A || !dst_host) DECT_FAIL(DECT_EINVAL, "dect_admm_save: null argument");
+    const std::vector<Segment> segs = state_segments(A);
+    const size_t need = ckpt_bytes(A, segs);
+    if (bytes < need) DECT_FAIL(DECT_EINVAL, "dect_admm_save: buffer smaller than dect_admm_state_bytes");
+    char* out = (char*)dst_host;
+    CkptHeader h{};
+    std::memcpy(h.magic, kCkptMagic, sizeof(kCkptMagic));
+    h.version = kCkptVersion;
+    h.B = A->B;
+    h.storage = A->P.storage;
+    h.scheme = A->P.scheme;
+    h.initialized = A->initialized ? 1 : 0;
+    h.n_segments = (int32_t)segs.size();
+    h.n_img = A->n_img;
+    h.n_sino = A->n_sino;
+    h.cR = A->cR;
+    h.cRT = A->cRT;
+    h.cF = A->cF;
+    h.cL = A->cL;
+    std::memcpy(out, &h, sizeof(h));
+    size_t off = sizeof(h);
+    for (int b = 0; b < A->B; ++b) {
+        const GeomDev& g = A->hs[b].g;
+        const int32_t rec[7] = {g.nx, g.ny, g.nv, g.nb, A->has_x0[b], A->has_truth[b], A->has_data[b]};
+        std::memcpy(out + off, rec, sizeof(rec));
+        off += sizeof(rec);
+    }
+    cudaStream_t st = as_stream(stream);
+    for (const Segment& g : segs) {
+        CUDA_TRY(cudaMemcpyAsync(out + off, g.p, g.bytes, cudaMemcpyDeviceToHost, st));
+        off += g.bytes;
+    }
+    CUDA_TRY(cudaStreamSynchronize(st));
+    return DECT_OK;
+}
+
+extern "C" dect_status dect_admm_load(dect_admm* A, const void* src_host, size_t bytes, void* stream) {
+    clear_stale_error();
+    if (!A || !src_host) DECT_FAIL(DECT_EINVAL, "dect_admm_load: null argument");
+    const std::vector<Segment> segs = state_segments(A);
+    const size_t need = ckpt_bytes(A, segs);
+    const char* in = (const char*)src_host;
+    CkptHeader h{};
+    if (bytes < sizeof(h)) DECT_FAIL(DECT_EINVAL, "dect_admm_load: image too small");
+    std::memcpy(&h, in, sizeof(h));
+    if (std::memcmp(h.magic, kCkptMagic, sizeof(kCkptMagic)) != 0 || h.version != kCkptVersion)
+        DECT_FAIL(DECT_EINVAL, "dect_admm_load: not a dect solver state image");
+    if (h.B != A->B || h.storage != A->P.storage || h.scheme != A->P.scheme || h.n_img != A->n_img ||
+        h.n_sino != A->n_sino || h.n_segments != (int32_t)segs.size())
+        DECT_FAIL(DECT_EINVAL, "dect_admm_load: the image is of a solver with other slices, storage or scheme");
+    if (bytes != need) DECT_FAIL(DECT_EINVAL, "dect_admm_load: image size does not match this solver");
+    size_t off = sizeof(h);
+    std::vector<int32_t> flags(3 * (size_t)A->B);
+    for (int b = 0; b < A->B; ++b) {
+        int32_t rec[7];
+        std::memcpy(rec, in + off, sizeof(rec));
+        off += sizeof(rec);
+        const GeomDev& g = A->hs[b].g;
+        if (rec[0] != g.nx || rec[1] != g.ny || rec[2] != g.nv || rec[3] != g.nb)
+            DECT_FAIL(DECT_EINVAL, "dect_admm_load: slice " + std::to_string(b) + " has another shape");
+        for (int k = 0; k < 3; ++k) flags[3 * (size_t)b + k] = rec[4 + k];
+    }
+    cudaStream_t st = as_stream(stream);
+    for (const Segment& g : segs) {
+        CUDA_TRY(cudaMemcpyAsync(g.p, in + off, g.bytes, cudaMemcpyHostToDevice, st));
+        off += g.bytes;
+    }
+    CUDA_TRY(cudaStreamSynchronize(st));
+    for (int b = 0; b < A->B; ++b) {
+        A->has_x0[b] = flags[3 * (size_t)b];
+        A->has_truth[b] = flags[3 * (size_t)b + 1];
+        A->has_data[b] = flags[3 * (size_t)b + 2];
+    }
+    A->initialized = h.initialized != 0;
+    A->cR = h.cR;
+    A->cRT = h.cRT;
+    A->cF = h.cF;
+    A->cL = h.cL;
+    return DECT_OK;
+}
+
 extern "C" dect_status dect_admm_stats(dect_admm* A, int32_t b, dect_stats* out, void* stream) {
     clear_stale_error();
     dect_status cs = check_slice(A, b);

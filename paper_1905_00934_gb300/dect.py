@@ -88,6 +88,9 @@ _SIGS = {
     "dect_admm_get": ([_VP, ctypes.c_int32, ctypes.c_int32, _VP, ctypes.c_size_t, _VP], ctypes.c_int),
     "dect_admm_stats": ([_VP, ctypes.c_int32, ctypes.POINTER(Stats), _VP], ctypes.c_int),
     "dect_admm_profile": ([_VP, ctypes.c_int32, _VP, _VP, _VP], ctypes.c_int),
+    "dect_admm_state_bytes": ([_VP, ctypes.POINTER(ctypes.c_size_t)], ctypes.c_int),
+    "dect_admm_save": ([_VP, _VP, ctypes.c_size_t, _VP], ctypes.c_int),
+    "dect_admm_load": ([_VP, _VP, ctypes.c_size_t, _VP], ctypes.c_int),
 }
 
 _lib = None
@@ -293,6 +296,22 @@ def admm_stats(h, slice_index, stream=None) -> dict:
     return {"iteration": s.iteration, "rho": list(s.rho), "r_pri": list(s.r_pri), "r_dual": list(s.r_dual),
             "xi_db": list(s.xi_db), "count_R": s.count_R, "count_RT": s.count_RT, "count_f": s.count_f,
             "count_launches": s.count_launches, "bp_view_groups": s.bp_view_groups}
+
+
+def admm_save(h, stream=None) -> np.ndarray:
+    """The solver's state image (checkpoint) as a host uint8 array."""
+    n = ctypes.c_size_t()
+    _check(lib().dect_admm_state_bytes(h, ctypes.byref(n)))
+    buf = np.empty(n.value, dtype=np.uint8)
+    _check(lib().dect_admm_save(h, buf.ctypes.data, buf.nbytes, _stream(stream)))
+    return buf
+
+
+def admm_load(h, image, stream=None):
+    """Restores a state image written by admm_save (host bytes-like or uint8 array)."""
+    buf = np.ascontiguousarray(np.frombuffer(image, dtype=np.uint8) if not isinstance(image, np.ndarray) else image,
+                               dtype=np.uint8)
+    _check(lib().dect_admm_load(h, buf.ctypes.data, buf.nbytes, _stream(stream)))
 
 
 PHASES = ["texture", "project", "backproject", "precond", "udm", "update", "reduce", "bp_finalize"]

@@ -122,6 +122,14 @@ class Solver:
     def stats(self, b=0, stream=None) -> dict:
         return dect.admm_stats(self.handle, b, stream)
 
+    def save(self, stream=None):
+        """Checkpoint: the solver's state as a host uint8 array (numpy)."""
+        return dect.admm_save(self.handle, stream)
+
+    def load(self, image, stream=None):
+        """Resume from a checkpoint of a solver with the same slice shapes, storage and scheme."""
+        dect.admm_load(self.handle, image, stream)
+
     def __del__(self):
         h = getattr(self, "handle", None)
         if h is not None and dect._lib is not None:
