@@ -352,11 +352,7 @@ static dect_status fbp_prepare(dect_geom* g, FbpDev& f) {
                                      "are not supported");
     const double k0 = 0.5 * (d.n_bins - 1) - d.bin_offset_cm / d.bin_pitch_cm;
     if (!g->fbp_tab) {
-        static bool attr = false;
-        if (!attr) {
-            CUDA_TRY(fbp_init_attributes());
-            attr = true;
-        }
+        CUDA_TRY(fbp_init_attributes());  // per device: the geometry's device is the current one
         std::vector<float4> tab(d.n_views);
         for (int v = 0; v < d.n_views; ++v) {
             const double th = d.angle0_rad + v * (d.angle_span_rad / d.n_views);

@@ -23,7 +23,9 @@
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
+#include <mutex>
 #include <type_traits>
+#include <vector>
 
 #include "bp_epilogue.cuh"
 #include "dect_internal.cuh"
@@ -216,11 +218,16 @@ int sweep_groups_per_cta() { return kSwGroups; }
 
 // CTA groups per tile: the smallest C (up to 8) whose grid of tiles * C blocks fills the resident
 // slots best (each CTA holds kSwGroups view groups; C * kSwGroups view groups per tile in total).
+static std::mutex g_slots_mu;
+static std::vector<int> g_slots;  // resident CTA slots of k_bp_sweep, per device
+
 int sweep_groups(int tiles) {
-    static int slots = 0;
-    if (!slots) {
-        int dev = 0, sms = 0, occ = 0;
-        cudaGetDevice(&dev);
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::unique_lock<std::mutex> lk(g_slots_mu);
+    if ((int)g_slots.size() <= dev) g_slots.resize(dev + 1, 0);
+    if (!g_slots[dev]) {
+        int sms = 0, occ = 0;
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         // shared memory (34 KB per CTA) limits residency: ask for the largest carve-out
         cudaFuncSetAttribute(k_bp_sweep<float2, 2>, cudaFuncAttributePreferredSharedMemoryCarveout,
@@ -232,8 +239,10 @@ int sweep_groups(int tiles) {
         cudaFuncSetAttribute(k_bp_sweep<float, 1>, cudaFuncAttributePreferredSharedMemoryCarveout,
                              cudaSharedmemCarveoutMaxShared);
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_bp_sweep<float2, 2>, 32 * kSwWarps, 0);
-        slots = sms * (occ > 0 ? occ : 1);
+        g_slots[dev] = sms * (occ > 0 ? occ : 1);
     }
+    const int slots = g_slots[dev];
+    lk.unlock();
     int best = 1;
     double best_fill = 0.0;
     for (int C = 1; C <= 8; ++C) {
