@@ -272,6 +272,42 @@ def pcg_x_update(prob: Problem, st: State, n: int, with_grad: bool = True, H=Non
 
 
 # ----------------------------------------------------------------------------
+# residual balancing (Sec. 3.2, following Boyd et al. 2011, Sec. 3.4.1)
+
+def residual_balance(st: State, P: Params, a_old, y_old, z_old, Dx, a_block: bool = True) -> None:
+    """Residuals and the adaptive penalty, in place on the state after the dual update.
+
+    Per basis b: r_pri = ||[a; y; z] - [R x; D x; x]||, r_dual = rho ||[a; y; z] - [a; y; z]_old||
+    (the surrogate without the C^T factor). If r_pri > mu_b r_dual, rho grows by tau; else if
+    r_dual > mu_b r_pri it shrinks by tau. The scaled duals u = y_dual / rho follow: they are
+    divided by the factor rho was multiplied by, so the unscaled duals stay put.
+    a_block=False drops the a terms and leaves u^a alone (the LM x CG splitting has no a-block).
+    """
+    r_pri = np.zeros(2)
+    r_dual = np.zeros(2)
+    for b in (0, 1):
+        pri_a = np.sum((st.a[b] - st.Rx[b]) ** 2) if a_block else 0.0
+        dual_a = np.sum((st.a[b] - a_old[b]) ** 2) if a_block else 0.0
+        r_pri[b] = np.sqrt(pri_a + np.sum((st.y[b] - Dx[b]) ** 2) + np.sum((st.z[b] - st.x[b]) ** 2))
+        r_dual[b] = st.rho[b] * np.sqrt(dual_a + np.sum((st.y[b] - y_old[b]) ** 2)
+                                        + np.sum((st.z[b] - z_old[b]) ** 2))
+    st.r_pri, st.r_dual = r_pri, r_dual
+    if P.adapt_rho:
+        for b in (0, 1):
+            factor = 1.0
+            if r_pri[b] > P.mu_b * r_dual[b]:
+                factor = P.tau
+            elif r_dual[b] > P.mu_b * r_pri[b]:
+                factor = 1.0 / P.tau
+            if factor != 1.0:
+                st.rho[b] *= factor
+                if a_block:
+                    st.ua[b] /= factor
+                st.uy[b] /= factor
+                st.uz[b] /= factor
+
+
+# ----------------------------------------------------------------------------
 # one ADMM iteration (Sec. 3.3)
 
 def admm_iteration(prob: Problem, st: State) -> State:
@@ -303,26 +339,7 @@ def admm_iteration(prob: Problem, st: State) -> State:
     st.uz = st.uz + st.z - st.x
 
     # residuals and adaptive rho
-    r_pri = np.zeros(2)
-    r_dual = np.zeros(2)
-    for b in (0, 1):
-        r_pri[b] = np.sqrt(np.sum((st.a[b] - st.Rx[b]) ** 2) + np.sum((st.y[b] - Dx[b]) ** 2)
-                           + np.sum((st.z[b] - st.x[b]) ** 2))
-        r_dual[b] = st.rho[b] * np.sqrt(np.sum((st.a[b] - a_old[b]) ** 2) + np.sum((st.y[b] - y_old[b]) ** 2)
-                                        + np.sum((st.z[b] - z_old[b]) ** 2))
-    st.r_pri, st.r_dual = r_pri, r_dual
-    if P.adapt_rho:
-        for b in (0, 1):
-            factor = 1.0
-            if r_pri[b] > P.mu_b * r_dual[b]:
-                factor = P.tau
-            elif r_dual[b] > P.mu_b * r_pri[b]:
-                factor = 1.0 / P.tau
-            if factor != 1.0:
-                st.rho[b] *= factor
-                st.ua[b] /= factor
-                st.uy[b] /= factor
-                st.uz[b] /= factor
+    residual_balance(st, P, a_old, y_old, z_old, Dx)
     st.iteration += 1
     return st
 

@@ -29,7 +29,7 @@ from __future__ import annotations
 import numpy as np
 
 from . import projector, spectral
-from .admm import Problem, State, grad, grad_t, shrinkage, state_from_image
+from .admm import Problem, State, grad, grad_t, residual_balance, shrinkage, state_from_image
 
 
 def _data_terms(prob: Problem, Rx: np.ndarray, jacobian: bool):
@@ -136,23 +136,7 @@ def lmcg_iteration(prob: Problem, st: State, m: int = 1, n: int = 1) -> State:
     st.uy = st.uy + st.y - Dx
     st.uz = st.uz + st.z - st.x
 
-    r_pri = np.zeros(2)
-    r_dual = np.zeros(2)
-    for b in (0, 1):
-        r_pri[b] = np.sqrt(np.sum((st.y[b] - Dx[b]) ** 2) + np.sum((st.z[b] - st.x[b]) ** 2))
-        r_dual[b] = st.rho[b] * np.sqrt(np.sum((st.y[b] - y_old[b]) ** 2) + np.sum((st.z[b] - z_old[b]) ** 2))
-    st.r_pri, st.r_dual = r_pri, r_dual
-    if P.adapt_rho:
-        for b in (0, 1):
-            factor = 1.0
-            if r_pri[b] > P.mu_b * r_dual[b]:
-                factor = P.tau
-            elif r_dual[b] > P.mu_b * r_pri[b]:
-                factor = 1.0 / P.tau
-            if factor != 1.0:
-                st.rho[b] *= factor
-                st.uy[b] /= factor
-                st.uz[b] /= factor
+    residual_balance(st, P, None, y_old, z_old, Dx, a_block=False)
     st.a = st.Rx.copy()
     st.iteration += 1
     return st

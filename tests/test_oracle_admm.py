@@ -280,3 +280,78 @@ def test_precondition_mode_is_validated():
     z = np.zeros((9, 12))
     with pytest.raises(ValueError):
         admm.Problem(g, spectra.SpectralTables(), z, z, z + 1, z + 1, admm.Params(precondition=3))
+
+
+# ---- residual balancing (Sec. 3.2, Boyd et al. Sec. 3.4.1): the rho rule and the dual rescale ----
+
+def _balance_state(rho):
+    """A hand-made state after the dual update: one non-zero entry per block, so that per basis
+    ||a - R x||, ||y - D x||, ||z - x|| = 6, 2, 3 (r_pri = 7) and ||a - a_old||, ||y - y_old||,
+    ||z - z_old|| = 2, 1, 2 (r_dual = 3 rho); every scaled dual entry is 1 + its index."""
+    V, Nb, ny, nx = 1, 3, 2, 2
+    z4 = lambda *s: np.zeros(s)
+    st = admm.State(x=z4(2, ny, nx), Rx=z4(2, V, Nb), a=z4(2, V, Nb), ua=z4(2, V, Nb), y=z4(2, 2, ny, nx),
+                    uy=z4(2, 2, ny, nx), z=z4(2, ny, nx), uz=z4(2, ny, nx), rho=np.array(rho, dtype=np.float64),
+                    mu=z4(V, Nb), status=np.zeros((V, Nb), np.uint8))
+    for u in (st.ua, st.uy, st.uz):
+        u[...] = 1.0 + np.arange(u.size).reshape(u.shape)
+    Dx = z4(2, 2, ny, nx)
+    a_old, y_old, z_old = z4(2, V, Nb), z4(2, 2, ny, nx), z4(2, ny, nx)
+    for b in (0, 1):
+        st.a[b, 0, 1] = 6.0           # a - R x
+        a_old[b, 0, 1] = 4.0          # a - a_old = 2
+        st.y[b, 1, 0, 1] = 2.0        # y - D x (D x = 0)
+        y_old[b, 1, 0, 1] = 1.0       # y - y_old = 1
+        st.z[b, 1, 1] = 3.0           # z - x (x = 0)
+        z_old[b, 1, 1] = 1.0          # z - z_old = 2
+    return st, a_old, y_old, z_old, Dx
+
+
+@pytest.mark.parametrize("rho,expect", [
+    ((0.2, 25.0), (2.0, 0.5)),    # r_pri 7 > 10 * 0.6: grow; r_dual 75 > 10 * 7: shrink
+    ((20.0, 1.0), (1.0, 1.0)),    # 60 and 3 against 7: neither rule fires
+])
+def test_residual_balance_rule_and_dual_rescale(rho, expect):
+    P = admm.Params(mu_b=10.0, tau=2.0)
+    st, a_old, y_old, z_old, Dx = _balance_state(rho)
+    before = st.copy()
+    admm.residual_balance(st, P, a_old, y_old, z_old, Dx)
+    for b in (0, 1):
+        # residuals by hand: sqrt(6^2 + 2^2 + 3^2) and rho sqrt(2^2 + 1^2 + 2^2)
+        assert st.r_pri[b] == pytest.approx(7.0, rel=1e-15)
+        assert st.r_dual[b] == pytest.approx(3.0 * rho[b], rel=1e-15)
+        f = expect[b]
+        assert st.rho[b] == rho[b] * f
+        # scaled duals divided by the factor rho was multiplied by (exact: f is a power of two)
+        for name in ("ua", "uy", "uz"):
+            assert np.array_equal(getattr(st, name)[b], getattr(before, name)[b] / f), (name, b)
+        # the primal blocks are untouched
+        for name in ("x", "a", "Rx", "y", "z"):
+            assert np.array_equal(getattr(st, name)[b], getattr(before, name)[b])
+
+
+def test_residual_balance_counts_the_a_block():
+    """Without the a-block the same state balances differently: rho 0.2 would stay (r_pri sqrt(13)
+    < 10 * 0.2 sqrt(5)) and rho 20 would shrink (20 sqrt(5) > 10 sqrt(13)). With it, 0.2 grows and
+    20 stays, and u^a is rescaled only when the a-block takes part."""
+    P = admm.Params(mu_b=10.0, tau=2.0)
+    st, a_old, y_old, z_old, Dx = _balance_state((0.2, 20.0))
+    admm.residual_balance(st, P, a_old, y_old, z_old, Dx)
+    assert list(st.rho) == [0.4, 20.0]
+    st, a_old, y_old, z_old, Dx = _balance_state((0.2, 20.0))
+    ua = st.ua.copy()
+    admm.residual_balance(st, P, None, y_old, z_old, Dx, a_block=False)
+    assert list(st.rho) == [0.2, 10.0]
+    assert st.r_pri[0] == pytest.approx(np.sqrt(13.0), rel=1e-15)
+    assert st.r_dual[1] == pytest.approx(20.0 * np.sqrt(5.0), rel=1e-15)
+    assert np.array_equal(st.ua, ua)
+    assert np.array_equal(st.uy[1], _balance_state((0.2, 20.0))[0].uy[1] * 2.0)
+
+
+def test_residual_balance_off_keeps_rho():
+    P = admm.Params(mu_b=10.0, tau=2.0, adapt_rho=False)
+    st, a_old, y_old, z_old, Dx = _balance_state((0.2, 25.0))
+    before = st.copy()
+    admm.residual_balance(st, P, a_old, y_old, z_old, Dx)
+    assert np.array_equal(st.rho, before.rho) and np.array_equal(st.ua, before.ua)
+    assert st.r_pri[0] == pytest.approx(7.0, rel=1e-15)
