@@ -49,9 +49,17 @@ typedef enum { DECT_PARALLEL = 0, DECT_FAN_FLAT = 1 } dect_geom_kind;
 typedef enum { DECT_F32 = 0, DECT_F64 = 1 } dect_dtype;
 
 /* Storage format of the solver's sinogram-domain vectors (a, u^a, R x, the CG
- * sinogram) and of the projector's pair textures; arithmetic stays float32
- * (the decomposition included) in every format. */
-typedef enum { DECT_STORE_F32 = 0, DECT_STORE_F16 = 1, DECT_STORE_BF16 = 2 } dect_storage;
+ * sinogram) and of the projector's pair textures. With F32, F16 and BF16 the
+ * arithmetic is float32 (the decomposition's by default; see
+ * dect_params.udm_f64). DECT_STORE_F64 runs a separate float64 solver: every
+ * vector, scalar and operation of the iteration (projector pair, FFT
+ * preconditioner, decomposition, updates) in float64, for problems whose
+ * photoelectric signal lies below float32 resolution (Sec. 1: the PE basis
+ * decays as E^-3, so with a 1 keV reference f_p a_p is ~1e-7 of the
+ * attenuation). It supports images up to 1024 x 1024, the UDM-PCG scheme and
+ * the DECT_INIT_PCG start; its projector pair is a plain float64 gather
+ * (much slower than the float32 kernels: meant for small problems). */
+typedef enum { DECT_STORE_F32 = 0, DECT_STORE_F16 = 1, DECT_STORE_BF16 = 2, DECT_STORE_F64 = 3 } dect_storage;
 
 /* Per-ray decomposition status codes (uint8 array of dect_decompose_rays). */
 enum { DECT_RAY_ACCEPTED = 0, DECT_RAY_REJECTED = 1, DECT_RAY_NONFINITE = 2 };
@@ -284,6 +292,13 @@ typedef struct {
                                     sinogram vectors and textures at the cost of their precision */
     int32_t scheme;              /* dect_scheme (DECT_SCHEME_UDM_PCG): the splitting one iteration runs */
     int32_t init;                /* dect_init (DECT_INIT_PCG): the initial image of slices without x0 */
+    int32_t udm_f64;             /* float32 / float16 / bfloat16 storage only. 0 (default): the decomposition
+                                    (Eq. 13) in float32 as described at dect_decompose_rays. 1: float64 where
+                                    the photoelectric coordinate needs it (Sec. 1): the energy sums of the
+                                    spectral model accumulate the float32 exponentials in float64, its logs,
+                                    the 2x2 Marquardt solve and the accept test (cost comparison) are float64.
+                                    Float64 runs at 1/64 of the float32 rate on this GPU, so this is several
+                                    times slower than 0 (the cost per slice is reported by the bench). */
 } dect_params;
 
 /* Fills *p with the paper's values and the defaults above. */
@@ -321,7 +336,8 @@ dect_status dect_admm_step(dect_admm* a, int32_t iters, void* stream);
  * mu = lm_mu0; then runs `iters` iterations. */
 dect_status dect_reconstruct(dect_admm* a, int32_t iters, void* stream);
 
-/* Copies a state array of slice b to dst (host or device), planar float32:
+/* Copies a state array of slice b to dst (host or device), planar float32
+ * (float64 with DECT_STORE_F64 storage, except which = 8 and 9, which are float64 there too):
  * which = 0: x [2][ny][nx]; 1: R x [2][V][Nb]; 2: a [2][V][Nb]; 3: u^a;
  * 4: y [2][2][ny][nx] (channel, then component along x, along y); 5: u^y;
  * 6: z [2][ny][nx]; 7: u^z; 8: LM mu [V][Nb]; 9: the preconditioner

@@ -10,7 +10,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 SRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libdect.so")
-SOURCES = ["projector.cu", "udm.cu", "fft.cu", "admm_kernels.cu", "api.cu", "project_noalloc.cu", "projector_f64.cu", "backproject_sweep.cu", "lmcg.cu", "fbp.cu"]
+SOURCES = ["projector.cu", "udm.cu", "fft.cu", "admm_kernels.cu", "api.cu", "project_noalloc.cu", "projector_f64.cu",
+           "backproject_sweep.cu", "lmcg.cu", "fbp.cu", "solver_f64.cu"]
 NVCC = os.environ.get("NVCC", "nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-cudart", "static"]

@@ -487,6 +487,9 @@ void launch_xi(const SliceDesc* d, const BlockMap& pix, int np, const float2* x,
     k_xi_partials<<<np, 256, 0, st>>>(d, pix, x, truth, partial);
     k_xi_reduce<<<B, 256, 0, st>>>(partial, pix.prefix, sc);
 }
+void launch_xi_reduce(const double* partial, const int* pix_prefix, SliceScalars* sc, int B, cudaStream_t st) {
+    k_xi_reduce<<<B, 256, 0, st>>>(partial, pix_prefix, sc);
+}
 void launch_init_image(const SliceDesc* d, const BlockMap& pix, int np, const int* has_x0, const float2* x0,
                        float2* x, float kappa, cudaStream_t st) {
     k_init_image<<<np, 256, 0, st>>>(d, pix, has_x0, x0, x, kappa);

@@ -80,7 +80,7 @@ struct dect_geom {
     int* ws_maps = nullptr;
     float2* ws_partial = nullptr;
     int ws_C = 1;
-    double4* rays64 = nullptr;  // float64 ray table (DECT_F64 calls; built on first use)
+    double4_32a* rays64 = nullptr;  // float64 ray table (DECT_F64 calls; built on first use)
     // dect_fbp: per-view constants, fan pre-weights, filtered sinograms [2][V][Nb] (built on first use)
     float4* fbp_tab = nullptr;
     float* fbp_prew = nullptr;
@@ -126,9 +126,10 @@ struct dect_spectra {
     int ne = 0;
     float4* t1 = nullptr;
     float4* t2 = nullptr;
-    double4* t64 = nullptr;  // {S_h, S_l, f_KN, f_p}, unit-sum spectra
+    double4_32a* t64 = nullptr;  // {S_h, S_l, f_KN, f_p}, unit-sum spectra
+    double4_32a* w64 = nullptr;  // [2][ne]: {S_h, S_l, S_h f_KN, S_h f_p}, {S_l f_KN, S_l f_p, 0, 0}
     double abar_low = 1.0;  // sum_E S_l f_KN (unit-sum S_l)
-    SpecDev dev() const { return SpecDev{ne, t1, t2}; }
+    SpecDev dev() const { return SpecDev{ne, t1, t2, w64, w64 + ne}; }
 };
 
 extern "C" const char* dect_version(void) { return "dect 0.1 sm_103a"; }
@@ -285,11 +286,13 @@ extern "C" dect_status dect_spectra_create(int32_t ne, const double* S_h, const 
     if (!(th > 0.0) || !(tl > 0.0)) DECT_FAIL(DECT_EINVAL, "dect_spectra_create: spectra must have positive sums");
     const double log2e = 1.4426950408889634;
     std::vector<float4> t1(ne), t2(ne);
-    std::vector<double4> t64(ne);
+    std::vector<double4_32a> t64(ne), w64(2 * (size_t)ne);
     double abar = 0.0;
     for (int e = 0; e < ne; ++e) {
         const double sh = S_h[e] / th, sl = S_l[e] / tl;
-        t64[e] = make_double4(sh, sl, f_kn[e], f_p[e]);
+        t64[e] = make_double4_32a(sh, sl, f_kn[e], f_p[e]);
+        w64[e] = make_double4_32a(sh, sl, sh * f_kn[e], sh * f_p[e]);
+        w64[ne + e] = make_double4_32a(sl * f_kn[e], sl * f_p[e], 0.0, 0.0);
         t1[e] = make_float4((float)(f_kn[e] * log2e), (float)(f_p[e] * log2e), (float)sh, (float)sl);
         t2[e] = make_float4((float)(sh * f_kn[e]), (float)(sh * f_p[e]), (float)(sl * f_kn[e]), (float)(sl * f_p[e]));
         abar += sl * f_kn[e];
@@ -302,7 +305,9 @@ extern "C" dect_status dect_spectra_create(int32_t ne, const double* S_h, const 
     if (e == cudaSuccess) e = cudaMemcpy(s->t1, t1.data(), sizeof(float4) * ne, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(s->t2, t2.data(), sizeof(float4) * ne, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = dalloc(&s->t64, ne);
-    if (e == cudaSuccess) e = cudaMemcpy(s->t64, t64.data(), sizeof(double4) * ne, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(s->t64, t64.data(), sizeof(double4_32a) * ne, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = dalloc(&s->w64, 2 * (size_t)ne);
+    if (e == cudaSuccess) e = cudaMemcpy(s->w64, w64.data(), sizeof(double4_32a) * 2 * ne, cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {
         dect::set_error(std::string("dect_spectra_create: ") + cudaGetErrorString(e));
         dect_spectra_destroy(s);
@@ -317,6 +322,7 @@ extern "C" void dect_spectra_destroy(dect_spectra* s) {
     cudaFree(s->t1);
     cudaFree(s->t2);
     cudaFree(s->t64);
+    cudaFree(s->w64);
     delete s;
 }
 
@@ -494,6 +500,7 @@ extern "C" void dect_params_default(dect_params* p) {
     p->storage = DECT_STORE_F32;
     p->scheme = DECT_SCHEME_UDM_PCG;
     p->init = DECT_INIT_PCG;
+    p->udm_f64 = 0;
 }
 
 struct MapBuf {
@@ -515,7 +522,7 @@ struct dect_admm {
     int sweep_groups_in_use = 1;     // view groups per tile (sweep_C CTAs of the kernel's groups each)
     float2* bp_partial = nullptr;    // [sweep_C][n_img] partial images of the backprojector
     int64_t n_img = 0, n_sino = 0, n_tx = 0, n_ty = 0, n_fft = 0, n_h = 0, n_stage = 0;
-    int max_px = 0, max_py = 0, min_px = 1 << 30;
+    int max_px = 0, min_px = 1 << 30;
     float2 *x = nullptr, *r = nullptr, *s = nullptr, *p = nullptr, *Ap = nullptr, *z = nullptr, *uz = nullptr;
     float2 *x0 = nullptr, *truth = nullptr, *Z = nullptr;
     void *Rx = nullptr, *a = nullptr, *ua = nullptr, *q = nullptr;  // sinogram vectors, storage format `prec`
@@ -538,6 +545,12 @@ struct dect_admm {
     float* bp_partial1 = nullptr;
     double *part_lm_pix = nullptr, *part_lm_ray = nullptr;
     int* d_has_x0 = nullptr;
+    // float64 path (storage DECT_STORE_F64): its vectors, a one-column-per-block FFT map and the slices'
+    // float64 ray tables (owned by the geometries)
+    F64Vecs v64;
+    MapBuf cols64;
+    int max_py = 0;
+    std::vector<const double4_32a*> rays64;
     std::vector<int> has_x0, has_truth, has_data;
     const float2* tw = nullptr;
     bool initialized = false;
@@ -581,8 +594,13 @@ static void free_admm(dect_admm* A) {
                     A->meas, A->txb, A->tyb, A->mu, A->H, A->Hn, A->stage, A->status, A->sc, A->part_udm,
                     A->part_img, A->part_rs, A->part_pap, A->part_xi, A->d_has_x0, A->ls, A->lm_scale, A->lm_d,
                     A->lm_r, A->lm_p, A->lm_Ap, A->lm_e, A->lm_g, A->lm_q, A->lm_Rd, A->lm_s0, A->tx1, A->ty1,
-                    A->bp_partial1, A->part_lm_pix, A->part_lm_ray};
+                    A->bp_partial1, A->part_lm_pix, A->part_lm_ray, A->cols64.d};
     for (void* q : ptrs) cudaFree(q);
+    const F64Vecs& v = A->v64;
+    for (void* q : {(void*)v.x, (void*)v.r, (void*)v.s, (void*)v.p, (void*)v.Ap, (void*)v.z, (void*)v.uz, (void*)v.x0,
+                    (void*)v.y, (void*)v.uy, (void*)v.RTs, (void*)v.Rx, (void*)v.a, (void*)v.ua, (void*)v.q,
+                    (void*)v.mu, (void*)v.H, (void*)v.Hn, (void*)v.Z})
+        cudaFree(q);
     if (A->gexec) cudaGraphExecDestroy(A->gexec);
     if (A->pgexec) cudaGraphExecDestroy(A->pgexec);
     for (cudaEvent_t e : A->prof_ev) cudaEventDestroy(e);
@@ -784,8 +802,105 @@ static void enq_lmcg_iteration(dect_admm* A, cudaStream_t st) {
     pe(A, DECT_PHASE_UPDATE, 1, st);
 }
 
+// ---- float64 path (storage DECT_STORE_F64): the same iteration with float64 kernels ----------------
+
+static void enq_project64(dect_admm* A, const double* img, double* out, cudaStream_t st) {
+    pb(A, st);
+    for (int b = 0; b < A->B; ++b) {
+        const SliceDesc& sd = A->hs[b];
+        project_single_f64(sd.g, A->rays64[b], img + 2 * sd.img_off, 2, out + 2 * sd.sino_off, st);
+    }
+    pe(A, DECT_PHASE_PROJECT, A->B, st);
+    if (A->counting) A->cR += 2;
+}
+
+static void enq_backproject64(dect_admm* A, const double* sino, double* out, cudaStream_t st) {
+    pb(A, st);
+    for (int b = 0; b < A->B; ++b) {
+        const SliceDesc& sd = A->hs[b];
+        backproject_single_f64(sd.g, A->rays64[b], sino + 2 * sd.sino_off, 2, out + 2 * sd.img_off, st);
+    }
+    pe(A, DECT_PHASE_BACKPROJECT, A->B, st);
+    if (A->counting) A->cRT += 2;
+}
+
+static void enq_precond64(dect_admm* A, const double* H, const double* r, double* s, cudaStream_t st) {
+    const int B = A->B;
+    const double* h = A->P.precondition ? H : nullptr;
+    pb(A, st);
+    launch64_precond(A->ds, A->rows.map(B), A->rows.total, A->cols64.map(B), A->cols64.total, h, r, s, A->v64.Z,
+                     A->part_rs, A->max_px, A->max_py, st);
+    pe(A, DECT_PHASE_PRECOND, h ? 3 : 1, st);
+}
+
+// Eq. 12 in float64: n PCG steps, warm-started from x, R x carried
+static void enq_pcg64(dect_admm* A, int n, bool with_grad, const double* H, cudaStream_t st) {
+    const int B = A->B;
+    F64Vecs& v = A->v64;
+    const BlockMap pix = A->pix.map(B), rays = A->rays.map(B);
+    pb(A, st);
+    launch64_sino_resid(A->ds, rays, A->rays.total, v.a, v.ua, v.Rx, v.q, st);
+    pe(A, DECT_PHASE_UPDATE, 1, st);
+    enq_backproject64(A, v.q, v.RTs, st);
+    pb(A, st);
+    launch64_r0(A->ds, pix, A->pix.total, v.RTs, v, v.r, with_grad, st);
+    pe(A, DECT_PHASE_BP_FINALIZE, 1, st);
+    enq_precond64(A, H, v.r, v.p, st);
+    pb(A, st);
+    launch_rs_reduce(A->part_rs, A->rows.d, A->sc, B, 1, st);
+    pe(A, DECT_PHASE_REDUCE, 1, st);
+    for (int it = 0; it < n; ++it) {
+        enq_project64(A, v.p, v.q, st);
+        enq_backproject64(A, v.q, v.RTs, st);
+        pb(A, st);
+        launch64_ap(A->ds, pix, A->pix.total, v.RTs, v.p, v.Ap, A->part_pap, with_grad, st);
+        pe(A, DECT_PHASE_BP_FINALIZE, 1, st);
+        pb(A, st);
+        launch_alpha(A->part_pap, A->pix.d, A->sc, B, st);
+        pe(A, DECT_PHASE_REDUCE, 1, st);
+        const int last = it == n - 1;
+        pb(A, st);
+        launch64_cg_update(A->ds, pix, A->pix.total, rays, A->rays.total, A->sc, v, last, st);
+        pe(A, DECT_PHASE_UPDATE, 1, st);
+        if (!last) {
+            enq_precond64(A, H, v.r, v.s, st);
+            pb(A, st);
+            launch_rs_reduce(A->part_rs, A->rows.d, A->sc, B, 0, st);
+            pe(A, DECT_PHASE_REDUCE, 1, st);
+            pb(A, st);
+            launch64_cg_p(A->ds, pix, A->pix.total, A->sc, v.s, v.p, st);
+            pe(A, DECT_PHASE_UPDATE, 1, st);
+        }
+    }
+}
+
+static void enq_iteration64(dect_admm* A, cudaStream_t st) {
+    const int B = A->B;
+    F64Vecs& v = A->v64;
+    const BlockMap pix = A->pix.map(B), rays = A->rays.map(B);
+    enq_pcg64(A, A->P.n_pcg, true, v.H, st);
+    pb(A, st);
+    launch64_udm_admm(A->ds, rays, A->rays.total, A->spec->t64, A->spec->ne, A->meas, v, A->status, A->sc,
+                      A->P.m_udm, A->part_udm, st);
+    pe(A, DECT_PHASE_UDM, 1, st);
+    if (A->counting) A->cF += 4 * A->P.m_udm;
+    pb(A, st);
+    launch64_image_update(A->ds, pix, A->pix.total, A->sc, A->P.lambda_c, A->P.lambda_p, v, A->part_img, st);
+    pe(A, DECT_PHASE_UPDATE, 1, st);
+    pb(A, st);
+    launch_rho_update(A->part_udm, A->rays.d, A->part_img, A->pix.d, A->sc, B, A->P.rho_mu, A->P.rho_tau, st);
+    pe(A, DECT_PHASE_REDUCE, 1, st);
+    pb(A, st);
+    launch64_dual_rescale(A->ds, pix, A->pix.total, rays, A->rays.total, A->sc, v, st);
+    pe(A, DECT_PHASE_UPDATE, 1, st);
+}
+
 static void enq_iteration(dect_admm* A, cudaStream_t st) {
     const int B = A->B;
+    if (A->prec == PREC_F64) {
+        enq_iteration64(A, st);
+        return;
+    }
     if (A->P.scheme == DECT_SCHEME_LM_CG) {
         enq_lmcg_iteration(A, st);
         return;
@@ -793,7 +908,7 @@ static void enq_iteration(dect_admm* A, cudaStream_t st) {
     enq_pcg(A, A->P.n_pcg, true, A->H, st);
     pb(A, st);
     launch_udm_admm(A->ds, A->rays.map(B), A->rays.total, A->spec->dev(), A->meas, A->Rx, A->ua, A->a, A->mu,
-                    A->status, A->sc, A->P.m_udm, A->part_udm, A->prec, st);
+                    A->status, A->sc, A->P.m_udm, A->part_udm, A->prec, A->P.udm_f64 != 0, st);
     pe(A, DECT_PHASE_UDM, 1, st);
     if (A->counting) A->cF += 4 * A->P.m_udm;
     pb(A, st);
@@ -880,11 +995,45 @@ static dect_status enq_cdm_fbp_start(dect_admm* A, cudaStream_t st) {
     return DECT_OK;
 }
 
+// The float64 path's start (the same steps as enq_initialize below, DECT_INIT_PCG only).
+static dect_status enq_initialize64(dect_admm* A, bool all_x0, cudaStream_t st) {
+    const int B = A->B;
+    F64Vecs& v = A->v64;
+    const BlockMap pix = A->pix.map(B), rays = A->rays.map(B);
+    const size_t ni = (size_t)A->n_img, ns = (size_t)A->n_sino;
+    if (!all_x0) {
+        CUDA_TRY(cudaMemsetAsync(v.x, 0, sizeof(double) * 2 * ni, st));
+        CUDA_TRY(cudaMemsetAsync(v.Rx, 0, sizeof(double) * 2 * ns, st));
+        CUDA_TRY(cudaMemsetAsync(v.ua, 0, sizeof(double) * 2 * ns, st));
+        CUDA_TRY(cudaMemsetAsync(v.y, 0, sizeof(double) * 4 * ni, st));
+        CUDA_TRY(cudaMemsetAsync(v.uy, 0, sizeof(double) * 4 * ni, st));
+        CUDA_TRY(cudaMemsetAsync(v.z, 0, sizeof(double) * 2 * ni, st));
+        CUDA_TRY(cudaMemsetAsync(v.uz, 0, sizeof(double) * 2 * ni, st));
+        launch64_udm_init(A->ds, rays, A->rays.total, A->spec->t64, A->spec->ne, A->meas, v, A->P.rho0_p,
+                          A->P.init_udm_iters, A->spec->abar_low, A->P.lm_mu0, st);
+        A->cF += 4 * A->P.init_udm_iters;
+        launch_reset_scalars(A->sc, B, A->P.rho0_c, A->P.rho0_p, st);
+        enq_pcg64(A, A->P.init_pcg_iters, false, v.Hn, st);
+    }
+    launch64_init_image(A->ds, pix, A->pix.total, A->d_has_x0, v, A->P.kappa, st);
+    enq_project64(A, v.x, v.Rx, st);
+    launch64_state_from_image(A->ds, pix, A->pix.total, rays, A->rays.total, v, A->P.lm_mu0, st);
+    launch_reset_scalars(A->sc, B, A->P.rho0_c, A->P.rho0_p, st);
+    CUDA_TRY(cudaGetLastError());
+    A->initialized = true;
+    return DECT_OK;
+}
+
 static dect_status enq_initialize(dect_admm* A, cudaStream_t st) {
     const int B = A->B;
     for (int b = 0; b < B; ++b)
         if (!A->has_data[b]) DECT_FAIL(DECT_EINVAL, "dect_admm: slice " + std::to_string(b) + " has no data");
     CUDA_TRY(cudaMemcpyAsync(A->d_has_x0, A->has_x0.data(), sizeof(int) * B, cudaMemcpyHostToDevice, st));
+    if (A->prec == PREC_F64) {
+        bool all = true;
+        for (int b = 0; b < B; ++b) all = all && A->has_x0[b];
+        return enq_initialize64(A, all, st);
+    }
     bool all_x0 = true;
     for (int b = 0; b < B; ++b) all_x0 = all_x0 && A->has_x0[b];
     if (!all_x0) {
@@ -973,7 +1122,46 @@ static cudaError_t autotune_sweep(dect_admm* A, const std::vector<int>& cands) {
     return dalloc(&A->bp_partial, (size_t)best * A->n_img);
 }
 
+// The float64 preconditioner responses: the point response of R^T R through the float64 projector
+// pair, its 2D DFT in float64 and H (and H without D) from it.
+static dect_status compute_responses64(dect_admm* A) {
+    cudaStream_t st = A->cap;
+    F64Vecs& v = A->v64;
+    for (int b = 0; b < A->B; ++b) {
+        const SliceDesc& sd = A->hs[b];
+        const int64_t np = (int64_t)sd.g.nx * sd.g.ny;
+        double* imp = v.r + 2 * sd.img_off;
+        CUDA_TRY(cudaMemsetAsync(imp, 0, sizeof(double) * np, st));
+        const double one = 1.0;
+        const int64_t c = (int64_t)(sd.g.ny / 2) * sd.g.nx + sd.g.nx / 2;
+        CUDA_TRY(cudaMemcpyAsync(imp + c, &one, sizeof(double), cudaMemcpyHostToDevice, st));
+        project_single_f64(sd.g, A->rays64[b], imp, 1, v.q + 2 * sd.sino_off, st);
+        backproject_single_f64(sd.g, A->rays64[b], v.q + 2 * sd.sino_off, 1, v.s + 2 * sd.img_off, st);
+        SliceDesc one_slice = sd;
+        one_slice.fft_off = 0;
+        one_slice.h_off = 0;
+        SliceDesc* dd = nullptr;
+        int* pre = nullptr;
+        CUDA_TRY(dalloc(&dd, 1));
+        cudaError_t e = dalloc(&pre, 2);
+        const int hp[2] = {0, sd.px};
+        if (e == cudaSuccess) e = cudaMemcpyAsync(dd, &one_slice, sizeof(SliceDesc), cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(pre, hp, sizeof(hp), cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess) {
+            launch64_response(dd, one_slice, BlockMap{pre, 1}, sd.px, v.s + 2 * sd.img_off, v.Z + sd.fft_off,
+                              v.H + sd.h_off, v.Hn + sd.h_off, A->P.precondition == DECT_PRECOND_RAMP, st);
+            e = cudaStreamSynchronize(st);
+        }
+        cudaFree(dd);
+        cudaFree(pre);
+        CUDA_TRY(e);
+    }
+    CUDA_TRY(cudaGetLastError());
+    return DECT_OK;
+}
+
 static dect_status compute_responses(dect_admm* A) {
+    if (A->prec == PREC_F64) return compute_responses64(A);
     cudaStream_t st = A->cap;
     for (int b = 0; b < A->B; ++b) {
         const SliceDesc& sd = A->hs[b];
@@ -1025,8 +1213,18 @@ extern "C" dect_status dect_admm_create(dect_geom* const* geoms, int32_t B, cons
     if (!geoms || !spec || !P || !out) DECT_FAIL(DECT_EINVAL, "dect_admm_create: null argument");
     *out = nullptr;
     if (B < 1 || B > 4096) DECT_FAIL(DECT_EINVAL, "dect_admm_create: n_slices must be in [1, 4096]");
-    if (P->storage != DECT_STORE_F32 && P->storage != DECT_STORE_F16 && P->storage != DECT_STORE_BF16)
-        DECT_FAIL(DECT_EINVAL, "dect_admm_create: storage must be DECT_STORE_F32, F16 or BF16");
+    if (P->storage != DECT_STORE_F32 && P->storage != DECT_STORE_F16 && P->storage != DECT_STORE_BF16 &&
+        P->storage != DECT_STORE_F64)
+        DECT_FAIL(DECT_EINVAL, "dect_admm_create: storage must be DECT_STORE_F32, F16, BF16 or F64");
+    if (P->udm_f64 != 0 && P->udm_f64 != 1) DECT_FAIL(DECT_EINVAL, "dect_admm_create: udm_f64 must be 0 or 1");
+    if (P->storage == DECT_STORE_F64) {
+        if (P->scheme != DECT_SCHEME_UDM_PCG || P->init != DECT_INIT_PCG)
+            DECT_FAIL(DECT_EUNSUPPORTED, "dect_admm_create: float64 storage runs the UDM-PCG scheme from the "
+                                         "DECT_INIT_PCG start only");
+        for (int b = 0; b < B; ++b)
+            if (geoms[b] && (geoms[b]->desc.nx > 1024 || geoms[b]->desc.ny > 1024))
+                DECT_FAIL(DECT_EUNSUPPORTED, "dect_admm_create: float64 storage supports images up to 1024 x 1024");
+    }
     if (P->scheme != DECT_SCHEME_UDM_PCG && P->scheme != DECT_SCHEME_LM_CG)
         DECT_FAIL(DECT_EINVAL, "dect_admm_create: scheme must be DECT_SCHEME_UDM_PCG or DECT_SCHEME_LM_CG");
     if (P->precondition != DECT_PRECOND_NONE && P->precondition != DECT_PRECOND_CIRCULANT &&
@@ -1071,7 +1269,7 @@ extern "C" dect_status dect_admm_create(dect_geom* const* geoms, int32_t B, cons
     A->has_x0.assign(B, 0);
     A->has_truth.assign(B, 0);
     A->has_data.assign(B, 0);
-    for (auto* m : {&A->rays, &A->pix, &A->tx, &A->ty, &A->rows, &A->cols, &A->sweep}) m->h.assign(1, 0);
+    for (auto* m : {&A->rays, &A->pix, &A->tx, &A->ty, &A->rows, &A->cols, &A->sweep, &A->cols64}) m->h.assign(1, 0);
     std::vector<int> tune;  // candidate CTA groups per tile when autotuning (first = the occupancy choice)
     {
         int total = 0;
@@ -1080,7 +1278,9 @@ extern "C" dect_status dect_admm_create(dect_geom* const* geoms, int32_t B, cons
             total += sweep_tiles(geoms[b]->desc.nx, geoms[b]->desc.ny);
             pix += geoms[b]->n_pix();
         }
-        if (P->bp_view_groups > 0) {
+        if (P->storage == DECT_STORE_F64) {
+            A->sweep_C = 1;  // the float64 path has its own backprojector; no sweep, no partial images
+        } else if (P->bp_view_groups > 0) {
             A->sweep_C = sweep_ctas_for_groups(P->bp_view_groups);
         } else if (P->bp_view_groups < 0) {
             A->sweep_C = sweep_groups(total);  // occupancy choice, not timed
@@ -1133,6 +1333,7 @@ extern "C" dect_status dect_admm_create(dect_geom* const* geoms, int32_t B, cons
         A->rows.h.push_back(A->rows.h.back() + ny);
         const int C = precond_cols_per_block(sd.py);
         A->cols.h.push_back(A->cols.h.back() + (sd.px + C - 1) / C);
+        A->cols64.h.push_back(A->cols64.h.back() + sd.px);
     }
     A->n_stage = std::max(4 * max_nr + 4 * max_np, (int64_t)16);
 
@@ -1146,21 +1347,41 @@ extern "C" dect_status dect_admm_create(dect_geom* const* geoms, int32_t B, cons
         }                                                                  \
     } while (0)
     ALLOC(A->ds, B);
-    for (float2** pp : {&A->x, &A->r, &A->s, &A->p, &A->Ap, &A->z, &A->uz, &A->x0, &A->truth}) ALLOC(*pp, A->n_img);
-    for (void** pp : {&A->Rx, &A->a, &A->ua, &A->q}) ALLOC(*(char**)pp, A->n_sino * sino_bytes(A->prec));
-    ALLOC(A->y, A->n_img);
-    ALLOC(A->uy, A->n_img);
+    ALLOC(A->truth, A->n_img);
     ALLOC(A->meas, A->n_sino);
-    ALLOC(*(char**)&A->txb, A->n_tx * texel_bytes(A->prec));
-    ALLOC(*(char**)&A->tyb, A->n_ty * texel_bytes(A->prec));
-    ALLOC(A->mu, A->n_sino);
     ALLOC(A->status, A->n_sino);
-    ALLOC(A->Z, A->n_fft);
-    ALLOC(A->H, A->n_h);
-    ALLOC(A->Hn, A->n_h);
     ALLOC(A->stage, A->n_stage);
     ALLOC(A->sc, B);
     ALLOC(A->d_has_x0, B);
+    if (A->prec == PREC_F64) {
+        F64Vecs& v = A->v64;
+        for (double** pp : {&v.x, &v.r, &v.s, &v.p, &v.Ap, &v.z, &v.uz, &v.x0, &v.RTs}) ALLOC(*pp, 2 * A->n_img);
+        for (double** pp : {&v.y, &v.uy}) ALLOC(*pp, 4 * A->n_img);
+        for (double** pp : {&v.Rx, &v.a, &v.ua, &v.q}) ALLOC(*pp, 2 * A->n_sino);
+        ALLOC(v.mu, A->n_sino);
+        ALLOC(v.H, A->n_h);
+        ALLOC(v.Hn, A->n_h);
+        ALLOC(v.Z, A->n_fft);
+        for (int b = 0; b < B; ++b) {
+            const dect_status ts = geom_table_f64(geoms[b]);
+            if (ts != DECT_OK) {
+                free_admm(A);
+                return ts;
+            }
+            A->rays64.push_back(geoms[b]->rays64);
+        }
+    } else {
+        for (float2** pp : {&A->x, &A->r, &A->s, &A->p, &A->Ap, &A->z, &A->uz, &A->x0}) ALLOC(*pp, A->n_img);
+        for (void** pp : {&A->Rx, &A->a, &A->ua, &A->q}) ALLOC(*(char**)pp, A->n_sino * sino_bytes(A->prec));
+        ALLOC(A->y, A->n_img);
+        ALLOC(A->uy, A->n_img);
+        ALLOC(*(char**)&A->txb, A->n_tx * texel_bytes(A->prec));
+        ALLOC(*(char**)&A->tyb, A->n_ty * texel_bytes(A->prec));
+        ALLOC(A->mu, A->n_sino);
+        ALLOC(A->Z, A->n_fft);
+        ALLOC(A->H, A->n_h);
+        ALLOC(A->Hn, A->n_h);
+    }
     if (P->scheme == DECT_SCHEME_LM_CG) {
         ALLOC(A->ls, B);
         ALLOC(A->lm_scale, B);
@@ -1177,14 +1398,14 @@ extern "C" dect_status dect_admm_create(dect_geom* const* geoms, int32_t B, cons
     if (e == cudaSuccess) e = dalloc(&A->part_xi, 4 * (size_t)np_blk);
     if (e == cudaSuccess) e = dalloc(&A->part_rs, 2 * (size_t)A->rows.h.back());
     if (e == cudaSuccess) e = dalloc(&A->part_pap, 2 * (size_t)A->pix.h.back());
-    if (e == cudaSuccess) e = dalloc(&A->bp_partial, (size_t)A->sweep_C * A->n_img);
-    for (MapBuf* m : {&A->rays, &A->pix, &A->tx, &A->ty, &A->rows, &A->cols, &A->sweep})
+    if (e == cudaSuccess && A->prec != PREC_F64) e = dalloc(&A->bp_partial, (size_t)A->sweep_C * A->n_img);
+    for (MapBuf* m : {&A->rays, &A->pix, &A->tx, &A->ty, &A->rows, &A->cols, &A->sweep, &A->cols64})
         if (e == cudaSuccess) e = upload_map(*m);
     if (e == cudaSuccess) e = cudaMemcpy(A->ds, A->hs.data(), sizeof(SliceDesc) * B, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemset(A->truth, 0, sizeof(float2) * A->n_img);
     if (e == cudaSuccess) e = cudaMemset(A->status, 0, A->n_sino);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&A->cap, cudaStreamNonBlocking);
-    if (e == cudaSuccess) {
+    if (e == cudaSuccess && A->prec != PREC_F64) {
         A->tw = fft_twiddles();
         if (!A->tw) e = cudaErrorMemoryAllocation;
     }
@@ -1248,7 +1469,10 @@ extern "C" dect_status dect_admm_set_data(dect_admm* A, int32_t b, const float* 
     launch_pack_meas(A->stage, nr, A->meas + sd.sino_off, st);
     if (x0) {
         CUDA_TRY(cudaMemcpyAsync(A->stage + 4 * nr, x0, sizeof(float) * 2 * np, cudaMemcpyDefault, st));
-        launch_interleave(A->stage + 4 * nr, np, A->x0 + sd.img_off, st);
+        if (A->prec == PREC_F64)
+            launch64_from_f32(A->stage + 4 * nr, np, A->v64.x0 + 2 * sd.img_off, st);
+        else
+            launch_interleave(A->stage + 4 * nr, np, A->x0 + sd.img_off, st);
     }
     CUDA_TRY(cudaGetLastError());
     A->has_x0[b] = x0 ? 1 : 0;
@@ -1369,6 +1593,27 @@ extern "C" dect_status dect_admm_get(const dect_admm* A, int32_t b, int32_t whic
         case 9: need = sizeof(float) * (size_t)sd.px * sd.py; break;
         default: DECT_FAIL(DECT_EINVAL, "dect_admm_get: unknown array");
     }
+    if (A->prec == PREC_F64) {
+        // planar float64 arrays: copied as they are
+        const F64Vecs& v = A->v64;
+        const double* src = nullptr;
+        size_t n64 = 0;
+        switch (which) {
+            case 0: src = v.x + 2 * sd.img_off; n64 = 2 * np; break;
+            case 1: src = v.Rx + 2 * sd.sino_off; n64 = 2 * nr; break;
+            case 2: src = v.a + 2 * sd.sino_off; n64 = 2 * nr; break;
+            case 3: src = v.ua + 2 * sd.sino_off; n64 = 2 * nr; break;
+            case 4: src = v.y + 4 * sd.img_off; n64 = 4 * np; break;
+            case 5: src = v.uy + 4 * sd.img_off; n64 = 4 * np; break;
+            case 6: src = v.z + 2 * sd.img_off; n64 = 2 * np; break;
+            case 7: src = v.uz + 2 * sd.img_off; n64 = 2 * np; break;
+            case 8: src = v.mu + sd.sino_off; n64 = nr; break;
+            default: src = v.H + sd.h_off; n64 = (size_t)sd.px * sd.py; break;
+        }
+        if (dst_bytes < sizeof(double) * n64) DECT_FAIL(DECT_EINVAL, "dect_admm_get: destination too small");
+        CUDA_TRY(cudaMemcpyAsync(dst, src, sizeof(double) * n64, cudaMemcpyDefault, st));
+        return DECT_OK;
+    }
     if (dst_bytes < need) DECT_FAIL(DECT_EINVAL, "dect_admm_get: destination too small");
     switch (which) {
         case 0: launch_deinterleave2(A->x + sd.img_off, np, A->stage, PREC_F32, st); break;
@@ -1399,14 +1644,51 @@ struct Segment {
     size_t bytes;
 };
 
+// the parameters that shape an iteration's arithmetic (a solver resumes only under the same ones)
+struct CkptParams {
+    double lambda_c, lambda_p, rho0_c, rho0_p, rho_mu, rho_tau, lm_mu0, kappa;
+    int32_t m_udm, n_pcg, init_udm_iters, init_pcg_iters, precondition, init, udm_f64, view_groups;
+};
+
 struct CkptHeader {
     char magic[8];
     int32_t version, B, storage, scheme, initialized, n_segments;
     int64_t n_img, n_sino, cR, cRT, cF, cL;
+    CkptParams params;
 };
 
 constexpr char kCkptMagic[8] = {'D', 'E', 'C', 'T', 'C', 'K', 'P', 'T'};
-constexpr int32_t kCkptVersion = 1;
+constexpr int32_t kCkptVersion = 2;
+
+CkptParams ckpt_params(const dect_admm* A) {
+    CkptParams c{};
+    const dect_params& P = A->P;
+    c.lambda_c = P.lambda_c;
+    c.lambda_p = P.lambda_p;
+    c.rho0_c = P.rho0_c;
+    c.rho0_p = P.rho0_p;
+    c.rho_mu = P.rho_mu;
+    c.rho_tau = P.rho_tau;
+    c.lm_mu0 = P.lm_mu0;
+    c.kappa = P.kappa;
+    c.m_udm = P.m_udm;
+    c.n_pcg = P.n_pcg;
+    c.init_udm_iters = P.init_udm_iters;
+    c.init_pcg_iters = P.init_pcg_iters;
+    c.precondition = P.precondition;
+    c.init = P.init;
+    c.udm_f64 = P.udm_f64;
+    c.view_groups = A->sweep_groups_in_use;  // the view-group count in use fixes the backprojector's sums
+    return c;
+}
+
+bool same_params(const CkptParams& a, const CkptParams& b) {
+    return a.lambda_c == b.lambda_c && a.lambda_p == b.lambda_p && a.rho0_c == b.rho0_c && a.rho0_p == b.rho0_p &&
+           a.rho_mu == b.rho_mu && a.rho_tau == b.rho_tau && a.lm_mu0 == b.lm_mu0 && a.kappa == b.kappa &&
+           a.m_udm == b.m_udm && a.n_pcg == b.n_pcg && a.init_udm_iters == b.init_udm_iters &&
+           a.init_pcg_iters == b.init_pcg_iters && a.precondition == b.precondition && a.init == b.init &&
+           a.udm_f64 == b.udm_f64 && a.view_groups == b.view_groups;
+}
 }  // namespace
 
 // The device arrays that carry state from one iteration to the next (and the data), with the byte
@@ -1417,6 +1699,19 @@ static std::vector<Segment> state_segments(const dect_admm* A) {
         if (p && bytes) v.push_back(Segment{const_cast<void*>(p), bytes});
     };
     const size_t ni = (size_t)A->n_img, ns = (size_t)A->n_sino, B = (size_t)A->B;
+    if (A->prec == PREC_F64) {
+        const F64Vecs& f = A->v64;
+        for (const double* p : {f.x, f.r, f.s, f.p, f.Ap, f.z, f.uz, f.x0}) add(p, sizeof(double) * 2 * ni);
+        for (const double* p : {f.y, f.uy}) add(p, sizeof(double) * 4 * ni);
+        for (const double* p : {f.Rx, f.a, f.ua, f.q}) add(p, sizeof(double) * 2 * ns);
+        add(f.mu, sizeof(double) * ns);
+        add(A->truth, sizeof(float2) * ni);
+        add(A->meas, sizeof(float4) * ns);
+        add(A->status, sizeof(uint8_t) * ns);
+        add(A->sc, sizeof(SliceScalars) * B);
+        add(A->d_has_x0, sizeof(int) * B);
+        return v;
+    }
     for (const float2* p : {A->x, A->r, A->s, A->p, A->Ap, A->z, A->uz, A->x0, A->truth}) add(p, sizeof(float2) * ni);
     for (const void* p : {A->Rx, A->a, A->ua, A->q}) add(p, ns * sino_bytes(A->prec));
     add(A->y, sizeof(float4) * ni);
@@ -1471,6 +1766,7 @@ extern "C" dect_status dect_admm_save(dect_admm* A, void* dst_host, size_t bytes
     h.cRT = A->cRT;
     h.cF = A->cF;
     h.cL = A->cL;
+    h.params = ckpt_params(A);
     std::memcpy(out, &h, sizeof(h));
     size_t off = sizeof(h);
     for (int b = 0; b < A->B; ++b) {
@@ -1502,6 +1798,9 @@ extern "C" dect_status dect_admm_load(dect_admm* A, const void* src_host, size_t
     if (h.B != A->B || h.storage != A->P.storage || h.scheme != A->P.scheme || h.n_img != A->n_img ||
         h.n_sino != A->n_sino || h.n_segments != (int32_t)segs.size())
         DECT_FAIL(DECT_EINVAL, "dect_admm_load: the image is of a solver with other slices, storage or scheme");
+    if (!same_params(h.params, ckpt_params(A)))
+        DECT_FAIL(DECT_EINVAL, "dect_admm_load: the image is of a solver with other iteration parameters (lambda, "
+                               "rho, m, n, damping, preconditioner, start or backprojector view groups)");
     if (bytes != need) DECT_FAIL(DECT_EINVAL, "dect_admm_load: image size does not match this solver");
     size_t off = sizeof(h);
     std::vector<int32_t> flags(3 * (size_t)A->B);
@@ -1539,8 +1838,14 @@ extern "C" dect_status dect_admm_stats(dect_admm* A, int32_t b, dect_stats* out,
     if (cs != DECT_OK) return cs;
     if (!out) DECT_FAIL(DECT_EINVAL, "dect_admm_stats: null output");
     cudaStream_t st = as_stream(stream);
-    if (A->has_truth[b])
-        launch_xi(A->ds, A->pix.map(A->B), A->pix.total, A->x, A->truth, A->part_xi, A->sc, A->B, st);
+    if (A->has_truth[b]) {
+        if (A->prec == PREC_F64) {
+            launch64_xi_partials(A->ds, A->pix.map(A->B), A->pix.total, A->v64.x, A->truth, A->part_xi, st);
+            launch_xi_reduce(A->part_xi, A->pix.d, A->sc, A->B, st);
+        } else {
+            launch_xi(A->ds, A->pix.map(A->B), A->pix.total, A->x, A->truth, A->part_xi, A->sc, A->B, st);
+        }
+    }
     SliceScalars v{};
     CUDA_TRY(cudaMemcpyAsync(&v, A->sc + b, sizeof(v), cudaMemcpyDeviceToHost, st));
     CUDA_TRY(cudaStreamSynchronize(st));

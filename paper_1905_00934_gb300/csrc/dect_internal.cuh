@@ -102,10 +102,14 @@ struct LmScalars {
 
 // Spectral tables on the device: T1 = {k_kn, k_p, S_h, S_l}, T2 = {S_h f_KN, S_h f_p, S_l f_KN, S_l f_p}
 // with k = f * log2(e) so that exp(-f_KN a_c - f_p a_p) = exp2(-k_kn a_c - k_p a_p).
+// w1 = {S_h, S_l, S_h f_KN, S_h f_p}, w2 = {S_l f_KN, S_l f_p, 0, 0} in float64 (unit-sum S), for the
+// decomposition's float64 sums (dect_params.udm_f64).
 struct SpecDev {
     int ne;
     const float4* t1;
     const float4* t2;
+    const double4_32a* w1;
+    const double4_32a* w2;
 };
 
 // Epilogue modes of the backprojector.
@@ -169,7 +173,7 @@ constexpr int kPixPerBlock = 256;
 // udm.cu
 void launch_udm_admm(const SliceDesc* dsl, const BlockMap& map, int nblk, const SpecDev& sp, const float4* meas,
                      const void* Rx, void* ua, void* a, float* mu, uint8_t* status,
-                     const SliceScalars* sc, int iters, double* partial, int prec, cudaStream_t st);
+                     const SliceScalars* sc, int iters, double* partial, int prec, bool f64, cudaStream_t st);
 void launch_udm_init(const SliceDesc* dsl, const BlockMap& map, int nblk, const SpecDev& sp, const float4* meas,
                      void* a, float* mu, double rho_p, int iters, float abar, double mu0, int prec, cudaStream_t st);
 void launch_udm_rays(const SpecDev& sp, int64_t n, const float* mh, const float* ml, const float* wh,
@@ -204,14 +208,14 @@ void launch_lm_accept(const SliceDesc* dsl, const BlockMap& pix, int npix, const
                       const LmScalars* ls, int b, float2* x, const float* dlt, float2* Rx, const float* Rd,
                       cudaStream_t st);
 
-void launch_forward_model(const SpecDev& sp, const double4* t64, int64_t n, int dtype, const void* ac,
+void launch_forward_model(const SpecDev& sp, const double4_32a* t64, int64_t n, int dtype, const void* ac,
                           const void* ap, void* fh, void* fl, void* jac, const void* gh, const void* gl, void* oc,
                           void* op, cudaStream_t st);
 
 // projector_f64.cu
-cudaError_t build_ray_table_f64(const dect_geom_desc& d, double4* rays, cudaStream_t st);
-void project_single_f64(const GeomDev& g, const double4* rays, const double* x, int nch, double* out, cudaStream_t st);
-void backproject_single_f64(const GeomDev& g, const double4* rays, const double* sino, int nch, double* out,
+cudaError_t build_ray_table_f64(const dect_geom_desc& d, double4_32a* rays, cudaStream_t st);
+void project_single_f64(const GeomDev& g, const double4_32a* rays, const double* x, int nch, double* out, cudaStream_t st);
+void backproject_single_f64(const GeomDev& g, const double4_32a* rays, const double* sino, int nch, double* out,
                             cudaStream_t st);
 
 // fft.cu
@@ -227,6 +231,51 @@ void launch_psf_to_response(const SliceDesc* d_dev, const SliceDesc& d, const Bl
                             const float2* psf, float2* Z, float* H, float* H_nograd, const float2* tw, bool ramp,
                             cudaStream_t st);
 cudaError_t fft_init_attributes();
+
+// ---- float64 solver path (solver_f64.cu) ----
+// Device vectors of the float64 path, planar per slice: images [2][np] at 2 img_off, y / u^y
+// [2][2][np] at 4 img_off, sinograms [2][nr] at 2 sino_off, mu [nr] at sino_off, Z at fft_off,
+// H / Hn at h_off; RTs holds a backprojection [2][np] per slice.
+struct F64Vecs {
+    double *x = nullptr, *r = nullptr, *s = nullptr, *p = nullptr, *Ap = nullptr, *z = nullptr, *uz = nullptr;
+    double *x0 = nullptr, *y = nullptr, *uy = nullptr, *RTs = nullptr;
+    double *Rx = nullptr, *a = nullptr, *ua = nullptr, *q = nullptr, *mu = nullptr;
+    double *H = nullptr, *Hn = nullptr;
+    double2* Z = nullptr;
+};
+void launch64_sino_resid(const SliceDesc* d, const BlockMap& rays, int nr, const double* a, const double* ua,
+                         const double* Rx, double* b, cudaStream_t st);
+void launch64_r0(const SliceDesc* d, const BlockMap& pix, int np, const double* RTb, const F64Vecs& v, double* r,
+                 bool with_grad, cudaStream_t st);
+void launch64_ap(const SliceDesc* d, const BlockMap& pix, int np, const double* RTq, const double* p, double* Ap,
+                 double* partial, bool with_grad, cudaStream_t st);
+void launch64_cg_update(const SliceDesc* d, const BlockMap& pix, int np, const BlockMap& rays, int nr,
+                        const SliceScalars* sc, const F64Vecs& v, int last, cudaStream_t st);
+void launch64_cg_p(const SliceDesc* d, const BlockMap& pix, int np, const SliceScalars* sc, const double* s, double* p,
+                   cudaStream_t st);
+// s = M^-1 r (H null: plain CG, s = r); partial[2 row + c] = <r_c, s_c> over the image-row map
+void launch64_precond(const SliceDesc* d, const BlockMap& rows, int nrows, const BlockMap& cols, int ncols,
+                      const double* H, const double* r, double* s, double2* Z, double* partial, int max_px, int max_py,
+                      cudaStream_t st);
+void launch64_response(const SliceDesc* d_dev, const SliceDesc& d, const BlockMap& cols, int ncols, const double* psf,
+                       double2* Z, double* H, double* Hn, bool ramp, cudaStream_t st);
+void launch64_udm_admm(const SliceDesc* d, const BlockMap& rays, int nr, const double4_32a* t64, int ne,
+                       const float4* meas, const F64Vecs& v, uint8_t* status, const SliceScalars* sc, int iters,
+                       double* partial, cudaStream_t st);
+void launch64_udm_init(const SliceDesc* d, const BlockMap& rays, int nr, const double4_32a* t64, int ne,
+                       const float4* meas, const F64Vecs& v, double rho_p, int iters, double abar, double mu0,
+                       cudaStream_t st);
+void launch64_image_update(const SliceDesc* d, const BlockMap& pix, int np, const SliceScalars* sc, double lam_c,
+                           double lam_p, const F64Vecs& v, double* partial, cudaStream_t st);
+void launch64_dual_rescale(const SliceDesc* d, const BlockMap& pix, int np, const BlockMap& rays, int nr,
+                           const SliceScalars* sc, const F64Vecs& v, cudaStream_t st);
+void launch64_init_image(const SliceDesc* d, const BlockMap& pix, int np, const int* has_x0, const F64Vecs& v,
+                         double kappa, cudaStream_t st);
+void launch64_state_from_image(const SliceDesc* d, const BlockMap& pix, int np, const BlockMap& rays, int nr,
+                               const F64Vecs& v, double mu0, cudaStream_t st);
+void launch64_xi_partials(const SliceDesc* d, const BlockMap& pix, int np, const double* x, const float2* truth,
+                          double* partial, cudaStream_t st);
+void launch64_from_f32(const float* in, int64_t n, double* out, cudaStream_t st);
 
 // ---- filtered backprojection and CDM-FBP (fbp.cu) ----
 struct FbpDev {

@@ -13,7 +13,8 @@
 
 namespace dect {
 
-enum { PREC_F32 = 0, PREC_F16 = 1, PREC_BF16 = 2 };
+// PREC_F64 selects the solver's separate float64 path (solver_f64.cu); the helpers below serve the others
+enum { PREC_F32 = 0, PREC_F16 = 1, PREC_BF16 = 2, PREC_F64 = 3 };
 
 struct __align__(8) TexH {
     __half2 lo, hi;
@@ -80,7 +81,7 @@ __device__ __forceinline__ void sttex(TexB* p, float2 lo, float2 hi) {
     *p = t;
 }
 
-inline size_t sino_bytes(int prec) { return prec == PREC_F32 ? 8 : 4; }
-inline size_t texel_bytes(int prec) { return prec == PREC_F32 ? 16 : 8; }
+inline size_t sino_bytes(int prec) { return prec == PREC_F64 ? 16 : (prec == PREC_F32 ? 8 : 4); }
+inline size_t texel_bytes(int prec) { return prec == PREC_F64 ? 32 : (prec == PREC_F32 ? 16 : 8); }
 
 }  // namespace dect

@@ -17,7 +17,7 @@
 namespace dect {
 
 // {position at index 0 of the sampled axis, slope, weight, axis (0: per column, 1: per row)}
-__global__ void k_ray_table_f64(dect_geom_desc d, double4* __restrict__ rays) {
+__global__ void k_ray_table_f64(dect_geom_desc d, double4_32a* __restrict__ rays) {
     const int64_t n = (int64_t)d.n_views * d.n_bins;
     const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= n) return;
@@ -45,16 +45,16 @@ __global__ void k_ray_table_f64(dect_geom_desc d, double4* __restrict__ rays) {
     }
     if (fabs(dx) >= fabs(dy)) {
         const double slope = dy / dx;
-        rays[r] = make_double4((py - px * slope) / d.pixel_cm + 0.5 * (d.ny - 1) - 0.5 * (d.nx - 1) * slope, slope,
+        rays[r] = make_double4_32a((py - px * slope) / d.pixel_cm + 0.5 * (d.ny - 1) - 0.5 * (d.nx - 1) * slope, slope,
                                d.pixel_cm / fabs(dx), 0.0);
     } else {
         const double slope = dx / dy;
-        rays[r] = make_double4((px - py * slope) / d.pixel_cm + 0.5 * (d.nx - 1) - 0.5 * (d.ny - 1) * slope, slope,
+        rays[r] = make_double4_32a((px - py * slope) / d.pixel_cm + 0.5 * (d.nx - 1) - 0.5 * (d.ny - 1) * slope, slope,
                                d.pixel_cm / fabs(dy), 1.0);
     }
 }
 
-cudaError_t build_ray_table_f64(const dect_geom_desc& d, double4* rays, cudaStream_t st) {
+cudaError_t build_ray_table_f64(const dect_geom_desc& d, double4_32a* rays, cudaStream_t st) {
     const int64_t n = (int64_t)d.n_views * d.n_bins;
     k_ray_table_f64<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(d, rays);
     return cudaGetLastError();
@@ -65,12 +65,12 @@ __device__ __forceinline__ double img64(const double* __restrict__ im, int nx, i
 }
 
 // out[c][ray] = R x[c], planar float64
-__global__ void k_project_f64(GeomDev g, const double4* __restrict__ rays, const double* __restrict__ x, int nch,
+__global__ void k_project_f64(GeomDev g, const double4_32a* __restrict__ rays, const double* __restrict__ x, int nch,
                               double* __restrict__ out) {
     const int64_t n = (int64_t)g.nv * g.nb;
     const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= n) return;
-    const double4 P = rays[r];
+    const double4_32a P = rays[r];
     const bool ax = P.w != 0.0;
     const int n_along = ax ? g.ny : g.nx, n_across = ax ? g.nx : g.ny;
     // indices whose positions lie in (-1, n_across): the only ones with a non-zero weight
@@ -100,7 +100,7 @@ __global__ void k_project_f64(GeomDev g, const double4* __restrict__ rays, const
 }
 
 // x[c][pixel] = R^T s[c]: gathers per pixel over views and candidate bins
-__global__ void k_backproject_f64(GeomDev g, const double4* __restrict__ rays, const double* __restrict__ sino, int nch,
+__global__ void k_backproject_f64(GeomDev g, const double4_32a* __restrict__ rays, const double* __restrict__ sino, int nch,
                                   double* __restrict__ out) {
     const int64_t np = (int64_t)g.nx * g.ny;
     const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -116,7 +116,7 @@ __global__ void k_backproject_f64(GeomDev g, const double4* __restrict__ rays, c
         const CandRange cr = rect_candidates(g, V.x, V.y, xc, yc, 1.5f * g.pix, 1.5f * g.pix);
         for (int k = cr.lo; k <= cr.hi; ++k) {
             const int64_t r = (int64_t)v * g.nb + k;
-            const double4 P = rays[r];
+            const double4_32a P = rays[r];
             const bool ax = P.w != 0.0;
             const int t = ax ? j : i, across = ax ? i : j;
             const double q = __fma_rn((double)t, P.y, P.x);
@@ -134,13 +134,13 @@ __global__ void k_backproject_f64(GeomDev g, const double4* __restrict__ rays, c
     if (nch > 1) out[np + e] = acc1;
 }
 
-void project_single_f64(const GeomDev& g, const double4* rays, const double* x, int nch, double* out,
+void project_single_f64(const GeomDev& g, const double4_32a* rays, const double* x, int nch, double* out,
                         cudaStream_t st) {
     const int64_t n = (int64_t)g.nv * g.nb;
     k_project_f64<<<(unsigned)((n + 127) / 128), 128, 0, st>>>(g, rays, x, nch, out);
 }
 
-void backproject_single_f64(const GeomDev& g, const double4* rays, const double* sino, int nch, double* out,
+void backproject_single_f64(const GeomDev& g, const double4_32a* rays, const double* sino, int nch, double* out,
                             cudaStream_t st) {
     const int64_t np = (int64_t)g.nx * g.ny;
     k_backproject_f64<<<(unsigned)((np + 127) / 128), 128, 0, st>>>(g, rays, sino, nch, out);

@@ -172,6 +172,92 @@ __device__ void lm_ray(const float4* __restrict__ t1, const float4* __restrict__
     }
 }
 
+// ---- float64 decomposition arithmetic (dect_params.udm_f64 = 1) -------------------------------------
+// The float32 exponentials of the kernel above, accumulated in float64 with float64 spectral weights
+// (w1 = {S_h, S_l, S_h f_KN, S_h f_p}, w2 = {S_l f_KN, S_l f_p, -, -}); logs of the sums, the 2x2
+// Marquardt solve and the accept test (a direct comparison of the Eq. 13 costs, as in the oracle) in
+// float64. The exponent's argument is formed in float32 from the float32-rounded point.
+
+__device__ __forceinline__ void spectral_sums64(const float4* __restrict__ t1, const double4_32a* __restrict__ w1,
+                                                const double4_32a* __restrict__ w2, int ne, double ac, double ap,
+                                                bool jac, double& fh, double& fl, double* J) {
+    const float fa = (float)ac, fp = (float)ap;
+    double sh = 0.0, sl = 0.0, shc = 0.0, shp = 0.0, slc = 0.0, slp = 0.0;
+    for (int e = 0; e < ne; ++e) {
+        const float4 a = t1[e];
+        const double t = (double)exp2f(-fmaf(a.x, fa, a.y * fp));
+        const double4_32a u = w1[e];
+        sh = fma(u.x, t, sh);
+        sl = fma(u.y, t, sl);
+        if (jac) {
+            const double4_32a v = w2[e];
+            shc = fma(u.z, t, shc);
+            shp = fma(u.w, t, shp);
+            slc = fma(v.x, t, slc);
+            slp = fma(v.y, t, slp);
+        }
+    }
+    fh = -log(sh);
+    fl = -log(sl);
+    if (jac) {
+        J[0] = shc / sh;
+        J[1] = shp / sh;
+        J[2] = slc / sl;
+        J[3] = slp / sl;
+    }
+}
+
+__device__ __forceinline__ double cost_f64(double fh, double fl, double mh, double ml, double wh, double wl, double ac,
+                                           double ap, double vc, double vp, double rc, double rp) {
+    const double rh = fh - mh, rl = fl - ml;
+    return 0.5 * (wh * rh * rh + wl * rl * rl) + 0.5 * (rc * (ac - vc) * (ac - vc) + rp * (ap - vp) * (ap - vp));
+}
+
+__device__ void lm_ray64(const float4* __restrict__ t1, const double4_32a* __restrict__ w1, const double4_32a* __restrict__ w2,
+                         int ne, const RayIn& in, int iters, LmState& s) {
+    const double mh = in.mh, ml = in.ml, wh = in.wh, wl = in.wl, rc = in.rc, rp = in.rp;
+    const double vc = (double)in.vc_hi + (double)in.vc_lo, vp = (double)in.vp_hi + (double)in.vp_lo;
+    double a0 = s.ac, a1 = s.ap, m = s.mu;
+    for (int it = 0; it < iters; ++it) {
+        double fh, fl, J[4];
+        spectral_sums64(t1, w1, w2, ne, a0, a1, true, fh, fl, J);
+        const double rh = fh - mh, rl = fl - ml;
+        const double g0 = wh * rh * J[0] + wl * rl * J[2] + rc * (a0 - vc);
+        const double g1 = wh * rh * J[1] + wl * rl * J[3] + rp * (a1 - vp);
+        const double A00 = wh * J[0] * J[0] + wl * J[2] * J[2] + rc;
+        const double A01 = wh * J[0] * J[1] + wl * J[2] * J[3];
+        const double A11 = wh * J[1] * J[1] + wl * J[3] * J[3] + rp;
+        const double B00 = A00 * (1.0 + m), B11 = A11 * (1.0 + m);
+        const double det = B00 * B11 - A01 * A01;
+        const double cost0 = cost_f64(fh, fl, mh, ml, wh, wl, a0, a1, vc, vp, rc, rp);
+        if (!(det > 0.0) || !isfinite(det) || !isfinite(cost0)) {
+            s.status = DECT_RAY_NONFINITE;
+            break;
+        }
+        const double t0 = a0 + (-g0 * B11 + g1 * A01) / det;
+        const double t1_ = a1 + (-g1 * B00 + g0 * A01) / det;
+        double fh1, fl1;
+        spectral_sums64(t1, w1, w2, ne, t0, t1_, false, fh1, fl1, nullptr);
+        const double cost1 = cost_f64(fh1, fl1, mh, ml, wh, wl, t0, t1_, vc, vp, rc, rp);
+        if (!isfinite(cost1)) {
+            m *= 10.0;
+            s.status = DECT_RAY_NONFINITE;
+        } else if (cost1 < cost0) {
+            a0 = t0;
+            a1 = t1_;
+            m /= 10.0;
+            s.status = DECT_RAY_ACCEPTED;
+        } else {
+            m *= 10.0;
+            s.status = DECT_RAY_REJECTED;
+        }
+        m = fmin(fmax(m, 1e-10), 1e10);
+    }
+    s.ac = (float)a0;
+    s.ap = (float)a1;
+    s.mu = (float)m;
+}
+
 __device__ __forceinline__ void load_tables(const SpecDev& sp, float4* t1, float4* t2) {
     for (int e = threadIdx.x; e < sp.ne; e += blockDim.x) {
         t1[e] = __ldg(sp.t1 + e);
@@ -182,7 +268,7 @@ __device__ __forceinline__ void load_tables(const SpecDev& sp, float4* t1, float
 
 // ADMM a-update fused with the a-block of the dual update (Eq. 11) and the a-block residual sums:
 // partial[4*blk + {0,1}] = sum (a - Rx)^2 (c, p); partial[4*blk + {2,3}] = sum (a - a_old)^2.
-template <class S2>
+template <class S2, bool F64>
 __global__ void __launch_bounds__(kRaysPerBlock) k_udm_admm(const SliceDesc* __restrict__ dsl, BlockMap map, SpecDev sp,
                                                             const float4* __restrict__ meas,
                                                             const S2* __restrict__ Rx, S2* __restrict__ ua,
@@ -193,6 +279,13 @@ __global__ void __launch_bounds__(kRaysPerBlock) k_udm_admm(const SliceDesc* __r
     extern __shared__ float4 tabs[];
     float4* t1 = tabs;
     float4* t2 = tabs + sp.ne;
+    double4_32a* w1 = reinterpret_cast<double4_32a*>(tabs + 2 * sp.ne);
+    double4_32a* w2 = w1 + sp.ne;
+    if (F64)
+        for (int e = threadIdx.x; e < sp.ne; e += blockDim.x) {
+            w1[e] = sp.w1[e];
+            w2[e] = sp.w2[e];
+        }
     load_tables(sp, t1, t2);
     int local;
     const int s = slice_of(map, blockIdx.x, local);
@@ -216,7 +309,10 @@ __global__ void __launch_bounds__(kRaysPerBlock) k_udm_admm(const SliceDesc* __r
         in.rc = sc[s].rho_f[0];
         in.rp = sc[s].rho_f[1];
         LmState st{a_old.x, a_old.y, mu[e], DECT_RAY_ACCEPTED};
-        lm_ray(t1, t2, sp.ne, in, iters, st);
+        if (F64)
+            lm_ray64(t1, w1, w2, sp.ne, in, iters, st);
+        else
+            lm_ray(t1, t2, sp.ne, in, iters, st);
         // the stored (possibly rounded) a is what the dual update and the residuals see
         st2(a + e, make_float2(st.ac, st.ap));
         const float2 an = ld2(a + e);
@@ -408,7 +504,7 @@ __global__ void __launch_bounds__(kRaysPerBlock) k_forward_model_f32(SpecDev sp,
     }
 }
 
-__global__ void __launch_bounds__(kRaysPerBlock) k_forward_model_f64(int ne, const double4* __restrict__ t64, int64_t n,
+__global__ void __launch_bounds__(kRaysPerBlock) k_forward_model_f64(int ne, const double4_32a* __restrict__ t64, int64_t n,
                                                                      const double* __restrict__ ac,
                                                                      const double* __restrict__ ap, double* __restrict__ fh,
                                                                      double* __restrict__ fl, double* __restrict__ jac,
@@ -420,7 +516,7 @@ __global__ void __launch_bounds__(kRaysPerBlock) k_forward_model_f64(int ne, con
     const double c = ac[r], p = ap[r];
     double sh = 0, sl = 0, shc = 0, shp = 0, slc = 0, slp = 0;
     for (int e = 0; e < ne; ++e) {
-        const double4 T = t64[e];  // {S_h, S_l, f_KN, f_p}
+        const double4_32a T = t64[e];  // {S_h, S_l, f_KN, f_p}
         const double t = exp(-T.z * c - T.w * p);
         sh += T.x * t;
         sl += T.y * t;
@@ -445,7 +541,7 @@ __global__ void __launch_bounds__(kRaysPerBlock) k_forward_model_f64(int ne, con
 }
 
 
-void launch_forward_model(const SpecDev& sp, const double4* t64, int64_t n, int dtype, const void* ac,
+void launch_forward_model(const SpecDev& sp, const double4_32a* t64, int64_t n, int dtype, const void* ac,
                           const void* ap, void* fh, void* fl, void* jac, const void* gh, const void* gl, void* oc,
                           void* op, cudaStream_t st) {
     if (n <= 0) return;
@@ -459,19 +555,30 @@ void launch_forward_model(const SpecDev& sp, const double4* t64, int64_t n, int 
             (const double*)gh, (const double*)gl, (double*)oc, (double*)op);
 }
 
-void launch_udm_admm(const SliceDesc* dsl, const BlockMap& map, int nblk, const SpecDev& sp, const float4* meas,
-                     const void* Rx, void* ua, void* a, float* mu, uint8_t* status, const SliceScalars* sc,
-                     int iters, double* partial, int prec, cudaStream_t st) {
+template <bool F64>
+static void udm_admm_t(const SliceDesc* dsl, const BlockMap& map, int nblk, const SpecDev& sp, const float4* meas,
+                       const void* Rx, void* ua, void* a, float* mu, uint8_t* status, const SliceScalars* sc,
+                       int iters, double* partial, int prec, cudaStream_t st) {
+    const size_t smem = tab_bytes(sp) + (F64 ? 2 * sizeof(double4_32a) * (size_t)sp.ne : 0);
     if (prec == PREC_F16)
-        k_udm_admm<__half2><<<nblk, kRaysPerBlock, tab_bytes(sp), st>>>(
+        k_udm_admm<__half2, F64><<<nblk, kRaysPerBlock, smem, st>>>(
             dsl, map, sp, meas, (const __half2*)Rx, (__half2*)ua, (__half2*)a, mu, status, sc, iters, partial);
     else if (prec == PREC_BF16)
-        k_udm_admm<__nv_bfloat162><<<nblk, kRaysPerBlock, tab_bytes(sp), st>>>(
+        k_udm_admm<__nv_bfloat162, F64><<<nblk, kRaysPerBlock, smem, st>>>(
             dsl, map, sp, meas, (const __nv_bfloat162*)Rx, (__nv_bfloat162*)ua, (__nv_bfloat162*)a, mu, status, sc,
             iters, partial);
     else
-        k_udm_admm<float2><<<nblk, kRaysPerBlock, tab_bytes(sp), st>>>(
+        k_udm_admm<float2, F64><<<nblk, kRaysPerBlock, smem, st>>>(
             dsl, map, sp, meas, (const float2*)Rx, (float2*)ua, (float2*)a, mu, status, sc, iters, partial);
+}
+
+void launch_udm_admm(const SliceDesc* dsl, const BlockMap& map, int nblk, const SpecDev& sp, const float4* meas,
+                     const void* Rx, void* ua, void* a, float* mu, uint8_t* status, const SliceScalars* sc,
+                     int iters, double* partial, int prec, bool f64, cudaStream_t st) {
+    if (f64)
+        udm_admm_t<true>(dsl, map, nblk, sp, meas, Rx, ua, a, mu, status, sc, iters, partial, prec, st);
+    else
+        udm_admm_t<false>(dsl, map, nblk, sp, meas, Rx, ua, a, mu, status, sc, iters, partial, prec, st);
 }
 
 void launch_udm_init(const SliceDesc* dsl, const BlockMap& map, int nblk, const SpecDev& sp, const float4* meas,

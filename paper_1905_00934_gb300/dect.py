@@ -20,7 +20,7 @@ LIB_PATH = os.path.join(_HERE, "_build", "libdect.so")
 OK, EINVAL, ENOMEM, ECUDA, EUNSUPPORTED, ETIMEOUT, ENOTCONV = range(7)
 PARALLEL, FAN_FLAT = 0, 1
 F32, F64 = 0, 1
-STORE_F32, STORE_F16, STORE_BF16 = 0, 1, 2
+STORE_F32, STORE_F16, STORE_BF16, STORE_F64 = 0, 1, 2, 3
 SCHEME_UDM_PCG, SCHEME_LM_CG = 0, 1
 PRECOND_NONE, PRECOND_CIRCULANT, PRECOND_RAMP = 0, 1, 2
 INIT_PCG, INIT_CDM_FBP = 0, 1
@@ -49,7 +49,8 @@ class Params(ctypes.Structure):
                 ("rho_mu", ctypes.c_double), ("rho_tau", ctypes.c_double), ("lm_mu0", ctypes.c_double),
                 ("kappa", ctypes.c_double), ("init_udm_iters", ctypes.c_int32), ("init_pcg_iters", ctypes.c_int32),
                 ("precondition", ctypes.c_int32), ("use_graph", ctypes.c_int32), ("bp_view_groups", ctypes.c_int32),
-                ("storage", ctypes.c_int32), ("scheme", ctypes.c_int32), ("init", ctypes.c_int32)]
+                ("storage", ctypes.c_int32), ("scheme", ctypes.c_int32), ("init", ctypes.c_int32),
+                ("udm_f64", ctypes.c_int32)]
 
 
 class Stats(ctypes.Structure):
@@ -201,8 +202,24 @@ def project_noalloc(geom, x, out, stream=None):
 
     For callers that must not allocate device memory (e.g. while a stream is being captured).
     Images must fit the fixed scratch (about 320 x 320); calls must not overlap on the GPU.
+    geom is a geometry handle or a solver.Geometry; with the latter the shapes are checked too.
+    x: float32 [nch, ny, nx], out: float32 [nch, n_views, n_bins] (CUDA, contiguous), nch 1 or 2.
     """
-    _check(lib().dect_project_noalloc(geom, x.shape[0], _ptr(x), _ptr(out), _stream(stream)))
+    import torch
+
+    for name, t in (("x", x), ("out", out)):
+        if not isinstance(t, torch.Tensor) or t.dtype != torch.float32:
+            raise TypeError(f"project_noalloc: {name} must be a float32 tensor")
+        if not t.is_cuda or t.dim() != 3 or not t.is_contiguous():
+            raise ValueError(f"project_noalloc: {name} must be a contiguous 3-d CUDA tensor")
+    if x.shape[0] not in (1, 2) or out.shape[0] != x.shape[0]:
+        raise ValueError("project_noalloc: x and out need the same channel count, 1 or 2")
+    handle = getattr(geom, "handle", geom)
+    if hasattr(geom, "handle"):
+        if tuple(x.shape[1:]) != (geom.ny, geom.nx) or tuple(out.shape[1:]) != (geom.n_views, geom.n_bins):
+            raise ValueError(f"project_noalloc: shapes {tuple(x.shape)} -> {tuple(out.shape)} do not match the "
+                             f"geometry ({geom.ny} x {geom.nx} image, {geom.n_views} x {geom.n_bins} sinogram)")
+    _check(lib().dect_project_noalloc(handle, x.shape[0], _ptr(x), _ptr(out), _stream(stream)))
     return out
 
 

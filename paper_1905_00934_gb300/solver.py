@@ -112,7 +112,9 @@ class Solver:
             shape = (py, px)
         else:
             shape = shapes[which]
-        out = torch.empty(shape, dtype=torch.float32, device=device)
+        # float64 storage keeps (and returns) every array in float64
+        dtype = torch.float64 if self.params.storage == dect.STORE_F64 else torch.float32
+        out = torch.empty(shape, dtype=dtype, device=device)
         dect.admm_get(self.handle, b, which, out, stream)
         return out
 

@@ -11,7 +11,12 @@ initial image and after each of the first K iterations, from float32-rounded mea
 values the GPU receives), for a pixel-by-pixel comparison before float32 rounding of the per-ray
 decisions has had time to accumulate.
 
-Usage: python tests/golden/make_golden_mixed.py [--slices 4] [--iters 100] [--early K]
+With --from-x0 it writes mixed_1024_from_x0.json for slice 0: float32-rounded measurements and the
+oracle's initial image rounded to float32 (both as the GPU receives them), then xi every 10
+iterations and the sampled pixels after iterations 10, 20, 50 and 100, so a GPU run started from the
+same image can be compared pixel by pixel at several depths of the trajectory.
+
+Usage: python tests/golden/make_golden_mixed.py [--slices 4] [--iters 100] [--early K] [--from-x0]
 """
 from __future__ import annotations
 
@@ -44,9 +49,12 @@ def main():
     ap.add_argument("--iters", type=int, default=100)
     ap.add_argument("--out", default=None)
     ap.add_argument("--early", type=int, default=-1)
+    ap.add_argument("--from-x0", action="store_true")
     args = ap.parse_args()
     if args.early >= 0:
         return early(args)
+    if args.from_x0:
+        return from_x0(args)
     args.out = args.out or os.path.join(HERE, "mixed_1024_oracle.json")
     out = {"what": "FP64 oracle, UDM1-PCG1, fan beam 1024x1024, 1440 views, 2048 bins, E_ref 100 keV, kappa 0.25; "
                    "xi every 10 iterations (entry 0 = initial image) and final x at seeded pixels",
@@ -94,6 +102,36 @@ def early(args):
             xs.append([st.x[0].ravel()[idx].tolist(), st.x[1].ravel()[idx].tolist()])
         out["slices"].append({"slice_index": MIXED_SEED_BASE + s, "pixels": idx.tolist(), "x": xs})
         print(s, "done", flush=True)
+    with open(out_path, "w") as f:
+        json.dump(out, f)
+
+
+FROM_X0_CHECKPOINTS = (10, 20, 50, 100)
+
+
+def from_x0(args):
+    out_path = args.out or os.path.join(HERE, "mixed_1024_from_x0.json")
+    c = baggage_fan_case(slice_index=MIXED_SEED_BASE, n=N, n_views=VIEWS, n_bins=BINS)
+    meas = [np.float32(c[k]).astype(np.float64) for k in ("m_h", "m_l", "w_h", "w_l")]
+    prob = admm.Problem(c["geom"], c["spectra"], *meas, admm.Params(kappa=BAGGAGE_KAPPA))
+    x0 = np.float32(np.stack(admm.initial_image(prob))).astype(np.float64)
+    st = admm.state_from_image(prob, x0[0], x0[1])
+    idx = sample_pixels(0)
+    out = {"what": "FP64 oracle from float32-rounded measurements and its own initial image rounded to float32, "
+                   "fan beam 1024x1024, 1440 views, 2048 bins, E_ref 100 keV, kappa 0.25, UDM1-PCG1: xi every 10 "
+                   "iterations (entry 0 = start) and sampled x after the listed iterations",
+           "slice_index": MIXED_SEED_BASE, "pixels": idx.tolist(), "checkpoints": list(FROM_X0_CHECKPOINTS),
+           "xi": [[admm.xi_db(x0[0], c["truth_c"]), admm.xi_db(x0[1], c["truth_p"])]], "x": {}}
+    for it in range(1, max(FROM_X0_CHECKPOINTS) + 1):
+        st = admm.admm_iteration(prob, st)
+        if it % 10 == 0:
+            out["xi"].append([admm.xi_db(st.x[0], c["truth_c"]), admm.xi_db(st.x[1], c["truth_p"])])
+            print(it, out["xi"][-1], flush=True)
+        if it in FROM_X0_CHECKPOINTS:
+            out["x"][str(it)] = [st.x[0].ravel()[idx].tolist(), st.x[1].ravel()[idx].tolist()]
+            with open(out_path, "w") as f:
+                json.dump(out, f)
+    out["oracle_threads"] = _clib.num_threads()
     with open(out_path, "w") as f:
         json.dump(out, f)
 

@@ -69,3 +69,4 @@ def test_params_default_are_the_papers():
     p = dect.params_default()
     assert (p.lambda_c, p.lambda_p, p.rho0_c, p.rho0_p) == (1e-5, 1e-5, 1e-3, 1e-3)
     assert (p.m_udm, p.n_pcg) == (1, 1)
+    assert (p.storage, p.udm_f64) == (dect.STORE_F32, 0)

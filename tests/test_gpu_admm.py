@@ -1,12 +1,13 @@
-"""GPU ADMM iteration UDM(m)-PCG(n) (Sec. 3.3) against the FP64 oracle.
+"""GPU ADMM iteration UDM(m)-PCG(n) (Sec. 3.3) against the FP64 oracle, float32 storage.
 
 Both sides get the same float32-rounded measurements and the same starting image.
 Compton / PE images: relative L2 <= 1e-4 after the fixed iteration count, PE reported
-separately. With the photoelectric basis referred to 100 keV both bases meet it. With the
-literal 1 keV reference of the small workload the PE signal (f_p a_p ~ 1e-8 of the Compton
-attenuation) is below float32 resolution of the measurements; the per-ray PE update then
-amplifies rounding by w J_p / rho ~ 500 and flips LM accept/reject decisions, so there only
-the Compton image is held to 1e-4 and the PE deviation is reported (bounded loosely)."""
+separately. With the photoelectric basis referred to 100 keV both bases meet it. The small
+workload read literally (1 keV reference) puts the PE signal f_p a_p at ~1e-7 of the attenuation
+(Sec. 1: the PE basis decays as E^-3), below float32 resolution; that workload's parity is held by
+the float64 path (test_gpu_f64.py). Here the float32 path on it is characterised: Compton to 1e-4,
+the PE deviation reported with a regression guard.
+"""
 import numpy as np
 import pytest
 
@@ -95,11 +96,11 @@ def test_initial_image_matches_oracle(cuda_dev, small):
     assert rel_l2(x[1], x0[1]) <= 1e-4
 
 
-def _run_pair(c, x0, dev, iters, m=1, n=1):
+def _run_pair(c, x0, dev, iters, m=1, n=1, **params):
     P = oadmm.Params(m_udm=m, n_pcg=n)
     prob = oadmm.Problem(c["geom"], c["spectra"], c["m_h"], c["m_l"], c["w_h"], c["w_l"], P)
     st = oadmm.state_from_image(prob, x0[0], x0[1])
-    sol = _solver(c, dev, x0, m_udm=m, n_pcg=n)
+    sol = _solver(c, dev, x0, m_udm=m, n_pcg=n, **params)
     hist = []
     for it in range(iters):
         st = oadmm.admm_iteration(prob, st)
@@ -109,18 +110,19 @@ def _run_pair(c, x0, dev, iters, m=1, n=1):
     return st, sol, hist
 
 
-@pytest.mark.parametrize("m,n,iters", [(1, 1, 20), (2, 3, 6)])
-def test_iterations_match_oracle(cuda_dev, small100, m, n, iters):
+@pytest.mark.parametrize("m,n,iters,udm_f64", [(1, 1, 20, 0), (2, 3, 6, 0), (1, 1, 20, 1)])
+def test_iterations_match_oracle(cuda_dev, small100, m, n, iters, udm_f64):
     from paper_1905_00934_gb300 import dect
 
     c, _, x0 = small100
-    st, sol, hist = _run_pair(c, x0, cuda_dev, iters, m, n)
+    st, sol, hist = _run_pair(c, x0, cuda_dev, iters, m, n, udm_f64=udm_f64)
     for it, (rho_o, rho_g, rp_o, rp_g) in enumerate(hist):
         assert np.array_equal(rho_o, rho_g), f"rho decision differs at iteration {it + 1}"
         assert np.allclose(rp_g, rp_o, rtol=1e-3)
     x = sol.get(0, dect.X).cpu().numpy()
     e_c, e_p = rel_l2(x[0], st.x[0]), rel_l2(x[1], st.x[1])
-    print(f"E_ref 100 keV, m={m} n={n} iters={iters}: Compton rel-L2 {e_c:.2e}, PE rel-L2 {e_p:.2e}")
+    print(f"E_ref 100 keV, m={m} n={n} iters={iters} udm_f64={udm_f64}: Compton rel-L2 {e_c:.2e}, "
+          f"PE rel-L2 {e_p:.2e}")
     assert e_c <= 1e-4 and e_p <= 1e-4
     a = sol.get(0, dect.A).cpu().numpy()
     assert rel_l2(a[0], st.a[0]) <= 1e-4 and rel_l2(a[1], st.a[1]) <= 1e-4
@@ -129,19 +131,27 @@ def test_iterations_match_oracle(cuda_dev, small100, m, n, iters):
     assert abs(xi[1] - oadmm.xi_db(st.x[1], c["truth_p"])) < 0.01
 
 
-def test_iterations_literal_pe_reference(cuda_dev, small):
+@pytest.mark.parametrize("udm_f64", [0, 1])
+def test_float32_storage_on_the_literal_pe_reference(cuda_dev, small, udm_f64):
+    # Every float32 rounding of a Compton quantity (a_c ~ 1.3 carries ~7e-8) shifts the model f by
+    # about as much, and the PE coordinate of Eq. 13 answers with the gain w J_p / rho_p ~ 150, so the
+    # float32 path cannot hold 1e-4 on this PE image; the float64 path does (test_gpu_f64.py). With
+    # the float64 decomposition (udm_f64) the spectral weights and the accept test stop adding their
+    # own rounding: measured PE rel-L2 after 20 iterations 2.5e-2 (float32) and 1.3e-3 (float64
+    # decomposition). The PE bounds below are regression guards at twice those values, not parity.
     from paper_1905_00934_gb300 import dect
 
     c, _, x0 = small
-    st, sol, hist = _run_pair(c, x0, cuda_dev, 20)
+    st, sol, hist = _run_pair(c, x0, cuda_dev, 20, udm_f64=udm_f64)
     for it, (rho_o, rho_g, rp_o, rp_g) in enumerate(hist):
         assert rho_o[0] == rho_g[0], f"Compton rho decision differs at iteration {it + 1}"
         assert rp_g[0] == pytest.approx(rp_o[0], rel=1e-3)
     x = sol.get(0, dect.X).cpu().numpy()
     e_c, e_p = rel_l2(x[0], st.x[0]), rel_l2(x[1], st.x[1])
-    print(f"E_ref 1 keV, 20 iterations: Compton rel-L2 {e_c:.2e}, PE rel-L2 {e_p:.2e} (PE reported)")
+    print(f"E_ref 1 keV, float32 storage, udm_f64={udm_f64}, 20 iterations: Compton rel-L2 {e_c:.2e}, "
+          f"PE rel-L2 {e_p:.2e} (PE reported)")
     assert e_c <= 1e-4
-    assert e_p <= 0.25
+    assert e_p <= (5e-2 if udm_f64 == 0 else 3e-3)
 
 
 def test_table1_counts(cuda_dev, small100):

@@ -63,7 +63,10 @@ def test_load_rejects_images_of_other_solvers(cuda_dev, cases):
     others = [_solver(cases[:1], cuda_dev),                   # another number of slices
               _solver(cases[::-1], cuda_dev),                 # the same slices in another order
               _solver(cases, cuda_dev, scheme=dect.SCHEME_LM_CG),
-              _solver(cases, cuda_dev, storage=dect.STORE_F16)]
+              _solver(cases, cuda_dev, storage=dect.STORE_F16),
+              _solver(cases, cuda_dev, lambda_c=2e-5),         # another TV weight
+              _solver(cases, cuda_dev, precondition=dect.PRECOND_RAMP),
+              _solver(cases, cuda_dev, udm_f64=1)]
     for o in others:
         with pytest.raises(dect.DectError) as e:
             o.load(image)
