@@ -299,6 +299,13 @@ typedef struct {
                                     the 2x2 Marquardt solve and the accept test (cost comparison) are float64.
                                     Float64 runs at 1/64 of the float32 rate on this GPU, so this is several
                                     times slower than 0 (the cost per slice is reported by the bench). */
+    int32_t objective_every;     /* k > 0: after every k-th iteration (counted from the last dect_reconstruct
+                                    or initialisation) the solver evaluates the MAP objective of Eq. 4 at the
+                                    current images, 1/2 ||f(R x) - m||^2_Sigma + sum_b lambda_b ||D x_b||_1
+                                    (R x projected afresh, f and the residuals as in the decomposition; with
+                                    16-bit storage R x carries the storage's rounding), reported by
+                                    dect_admm_stats. One projection and one f-evaluation per ray each time,
+                                    outside Table 1's counts. 0 (default): never. */
 } dect_params;
 
 /* Fills *p with the paper's values and the defaults above. */
@@ -355,6 +362,8 @@ typedef struct {
     int64_t count_f;             /* forward-model evaluations per ray */
     int64_t count_launches;      /* kernels launched by this solver so far (all slices) */
     int32_t bp_view_groups;      /* backprojector view groups per tile in use (fixed or autotuned) */
+    double objective;            /* Eq. 4 after iteration objective_iteration (NaN if never evaluated) */
+    int32_t objective_iteration; /* see dect_params.objective_every; -1 if never evaluated */
 } dect_stats;
 dect_status dect_admm_stats(dect_admm* a, int32_t slice, dect_stats* out, void* stream);
 
@@ -369,9 +378,11 @@ dect_status dect_admm_stats(dect_admm* a, int32_t slice, dect_stats* out, void* 
  * at least the size; caller-owned) after the work already queued on `stream`,
  * and synchronises `stream`.
  * dect_admm_load: restores an image into a solver created with the same slice
- * shapes (nx, ny, n_views, n_bins per slice, in order), storage and scheme;
- * anything else, or a wrong size or header, returns DECT_EINVAL without
- * touching the solver's state. With the same parameters, dect_admm_step then
+ * shapes (nx, ny, n_views, n_bins per slice, in order), storage, scheme and
+ * iteration parameters (lambda, rho0, m, n, residual balancing, LM damping,
+ * kappa, the start's iteration counts, preconditioner, start, udm_f64 and the
+ * backprojector view groups in use); anything else, or a wrong size or header,
+ * returns DECT_EINVAL without touching the solver's state. With the same parameters, dect_admm_step then
  * continues exactly (bit for bit) as the saved solver would have. Synchronises
  * `stream`. */
 dect_status dect_admm_state_bytes(const dect_admm* a, size_t* bytes);

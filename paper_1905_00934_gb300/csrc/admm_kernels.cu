@@ -291,6 +291,51 @@ __global__ void __launch_bounds__(256) k_xi_reduce(const double* __restrict__ pa
     }
 }
 
+// Eq. 4's regulariser per pixel block: partial[blk] = sum lambda_c |D x_c|_1 + lambda_p |D x_p|_1
+__global__ void __launch_bounds__(256) k_objective_tv(const SliceDesc* __restrict__ dsl, BlockMap pix,
+                                                      const float2* __restrict__ x, double lam_c, double lam_p,
+                                                      double* __restrict__ partial) {
+    int local;
+    const SliceDesc& d = dsl[slice_of(pix, blockIdx.x, local)];
+    const int nx = d.g.nx, ny = d.g.ny;
+    const int64_t k = (int64_t)local * 256 + threadIdx.x;
+    double acc[1] = {0.0};
+    if (k < (int64_t)nx * ny) {
+        const int j = (int)(k / nx), i = (int)(k % nx);
+        const float2* xs = x + d.img_off;
+        const float2 c = __ldg(xs + k);
+        double tc = 0.0, tp = 0.0;
+        if (i < nx - 1) {
+            const float2 r = __ldg(xs + k + 1);
+            tc += fabs((double)r.x - c.x);
+            tp += fabs((double)r.y - c.y);
+        }
+        if (j < ny - 1) {
+            const float2 u = __ldg(xs + k + nx);
+            tc += fabs((double)u.x - c.x);
+            tp += fabs((double)u.y - c.y);
+        }
+        acc[0] = lam_c * tc + lam_p * tp;
+    }
+    block_partials<1>(acc, partial);
+}
+
+// objective = sum of the slice's ray partials + pixel partials (one block per slice)
+__global__ void __launch_bounds__(256) k_objective_reduce(const double* __restrict__ part_rays,
+                                                          const int* __restrict__ rays_prefix,
+                                                          const double* __restrict__ part_pix,
+                                                          const int* __restrict__ pix_prefix,
+                                                          SliceScalars* __restrict__ sc) {
+    const int s = blockIdx.x;
+    double a[1], b[1];
+    slice_sum<1>(part_rays, rays_prefix, s, a);
+    slice_sum<1>(part_pix, pix_prefix, s, b);
+    if (threadIdx.x == 0) {
+        sc[s].objective = a[0] + b[0];
+        sc[s].objective_iter = sc[s].iteration;
+    }
+}
+
 // ---- state set-up -------------------------------------------------------------------------------
 
 // x_c = max(0, x_c), x_p = kappa x_c, for slices without a given start; slices with one copy x0
@@ -369,6 +414,8 @@ __global__ void k_reset_scalars(SliceScalars* __restrict__ sc, int B, double rho
     v.ifactor_f[0] = v.ifactor_f[1] = 1.0f;
     v.xi_num[0] = v.xi_num[1] = nan("");
     v.xi_den[0] = v.xi_den[1] = nan("");
+    v.objective = nan("");
+    v.objective_iter = -1;
     sc[s] = v;
 }
 
@@ -486,6 +533,14 @@ void launch_xi(const SliceDesc* d, const BlockMap& pix, int np, const float2* x,
                SliceScalars* sc, int B, cudaStream_t st) {
     k_xi_partials<<<np, 256, 0, st>>>(d, pix, x, truth, partial);
     k_xi_reduce<<<B, 256, 0, st>>>(partial, pix.prefix, sc);
+}
+void launch_objective_tv(const SliceDesc* d, const BlockMap& pix, int np, const float2* x, double lam_c, double lam_p,
+                         double* partial, cudaStream_t st) {
+    k_objective_tv<<<np, 256, 0, st>>>(d, pix, x, lam_c, lam_p, partial);
+}
+void launch_objective_reduce(const double* part_rays, const int* rays_prefix, const double* part_pix,
+                             const int* pix_prefix, SliceScalars* sc, int B, cudaStream_t st) {
+    k_objective_reduce<<<B, 256, 0, st>>>(part_rays, rays_prefix, part_pix, pix_prefix, sc);
 }
 void launch_xi_reduce(const double* partial, const int* pix_prefix, SliceScalars* sc, int B, cudaStream_t st) {
     k_xi_reduce<<<B, 256, 0, st>>>(partial, pix_prefix, sc);

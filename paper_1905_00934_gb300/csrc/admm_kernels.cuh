@@ -24,6 +24,11 @@ void launch_dual_rescale(const SliceDesc* d, const BlockMap& pix, int np, const 
                          const SliceScalars* sc, float4* uy, float2* uz, void* ua, int prec, cudaStream_t st);
 void launch_xi(const SliceDesc* d, const BlockMap& pix, int np, const float2* x, const float2* truth, double* partial,
                SliceScalars* sc, int B, cudaStream_t st);
+// Eq. 4's objective: TV partials per pixel block, then ray + pixel partials summed per slice into sc
+void launch_objective_tv(const SliceDesc* d, const BlockMap& pix, int np, const float2* x, double lam_c, double lam_p,
+                         double* partial, cudaStream_t st);
+void launch_objective_reduce(const double* part_rays, const int* rays_prefix, const double* part_pix,
+                             const int* pix_prefix, SliceScalars* sc, int B, cudaStream_t st);
 // xi sums of the slices from per-pixel-block partials (4 per block) written by any xi partial kernel
 void launch_xi_reduce(const double* partial, const int* pix_prefix, SliceScalars* sc, int B, cudaStream_t st);
 void launch_init_image(const SliceDesc* d, const BlockMap& pix, int np, const int* has_x0, const float2* x0,

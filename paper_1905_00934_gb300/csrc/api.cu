@@ -129,7 +129,8 @@ struct dect_spectra {
     double4_32a* t64 = nullptr;  // {S_h, S_l, f_KN, f_p}, unit-sum spectra
     double4_32a* w64 = nullptr;  // [2][ne]: {S_h, S_l, S_h f_KN, S_h f_p}, {S_l f_KN, S_l f_p, 0, 0}
     double abar_low = 1.0;  // sum_E S_l f_KN (unit-sum S_l)
-    SpecDev dev() const { return SpecDev{ne, t1, t2, w64, w64 + ne}; }
+    int n_both = 0, n_end = 0, tail_high = 1;  // supports of the spectra (see SpecDev)
+    SpecDev dev() const { return SpecDev{ne, t1, t2, w64, w64 + ne, n_both, n_end, tail_high}; }
 };
 
 extern "C" const char* dect_version(void) { return "dect 0.1 sm_103a"; }
@@ -300,6 +301,14 @@ extern "C" dect_status dect_spectra_create(int32_t ne, const double* S_h, const 
     dect_spectra* s = new dect_spectra();
     s->ne = ne;
     s->abar_low = abar;
+    int last_h = 0, last_l = 0;  // one past the last non-zero bin of each spectrum
+    for (int e = 0; e < ne; ++e) {
+        if (S_h[e] > 0.0) last_h = e + 1;
+        if (S_l[e] > 0.0) last_l = e + 1;
+    }
+    s->n_both = std::min(last_h, last_l);
+    s->n_end = std::max(last_h, last_l);
+    s->tail_high = last_h >= last_l ? 1 : 0;
     cudaError_t e = dalloc(&s->t1, ne);
     if (e == cudaSuccess) e = dalloc(&s->t2, ne);
     if (e == cudaSuccess) e = cudaMemcpy(s->t1, t1.data(), sizeof(float4) * ne, cudaMemcpyHostToDevice);
@@ -501,6 +510,7 @@ extern "C" void dect_params_default(dect_params* p) {
     p->scheme = DECT_SCHEME_UDM_PCG;
     p->init = DECT_INIT_PCG;
     p->udm_f64 = 0;
+    p->objective_every = 0;
 }
 
 struct MapBuf {
@@ -517,7 +527,7 @@ struct dect_admm {
     dect_params P{};
     std::vector<SliceDesc> hs;
     SliceDesc* ds = nullptr;
-    MapBuf rays, pix, tx, ty, rows, cols, sweep;
+    MapBuf rays, pix, tx, ty, rows, cols, sweep, ptile;  // ptile: the projector's (views x bins) tiles
     int sweep_C = 1;                 // CTA groups (partial images) per backprojector tile
     int sweep_groups_in_use = 1;     // view groups per tile (sweep_C CTAs of the kernel's groups each)
     float2* bp_partial = nullptr;    // [sweep_C][n_img] partial images of the backprojector
@@ -558,6 +568,8 @@ struct dect_admm {
     cudaStream_t cap = nullptr;
     cudaGraphExec_t gexec = nullptr;
     int64_t cR = 0, cRT = 0, cF = 0, cL = 0;
+    int64_t iters_done = 0;                            // iterations since the last (re)initialisation
+    double *part_obj_rays = nullptr, *part_obj_pix = nullptr;  // Eq. 4 partials (one per ray / pixel block)
     int64_t launches_per_iter = 0, R_per_iter = 0, RT_per_iter = 0, f_per_iter = 0;
     // profiling: an event pair around every kernel group of the captured iteration
     bool prof_on = false;
@@ -588,13 +600,14 @@ static void pe(dect_admm* A, int phase, int nk, cudaStream_t st) {
 }
 
 static void free_admm(dect_admm* A) {
-    void* ptrs[] = {A->ds, A->rays.d, A->pix.d, A->tx.d, A->ty.d, A->rows.d, A->cols.d, A->sweep.d,
+    void* ptrs[] = {A->ds, A->rays.d, A->pix.d, A->tx.d, A->ty.d, A->rows.d, A->cols.d, A->sweep.d, A->ptile.d,
                     A->bp_partial, A->x, A->r, A->s,
                     A->p, A->Ap, A->z, A->uz, A->x0, A->truth, A->Rx, A->a, A->ua, A->q, A->Z, A->y, A->uy,
                     A->meas, A->txb, A->tyb, A->mu, A->H, A->Hn, A->stage, A->status, A->sc, A->part_udm,
                     A->part_img, A->part_rs, A->part_pap, A->part_xi, A->d_has_x0, A->ls, A->lm_scale, A->lm_d,
                     A->lm_r, A->lm_p, A->lm_Ap, A->lm_e, A->lm_g, A->lm_q, A->lm_Rd, A->lm_s0, A->tx1, A->ty1,
-                    A->bp_partial1, A->part_lm_pix, A->part_lm_ray, A->cols64.d};
+                    A->bp_partial1, A->part_lm_pix, A->part_lm_ray, A->cols64.d, A->part_obj_rays,
+                    A->part_obj_pix};
     for (void* q : ptrs) cudaFree(q);
     const F64Vecs& v = A->v64;
     for (void* q : {(void*)v.x, (void*)v.r, (void*)v.s, (void*)v.p, (void*)v.Ap, (void*)v.z, (void*)v.uz, (void*)v.x0,
@@ -623,7 +636,7 @@ static void enq_project(dect_admm* A, const float2* img, void* out, cudaStream_t
     launch_textures(A->ds, A->tx.map(B), A->tx.total, A->ty.map(B), A->ty.total, img, A->txb, A->tyb, A->prec, st);
     pe(A, DECT_PHASE_TEXTURE, 2, st);
     pb(A, st);
-    launch_project(A->ds, A->rays.map(B), A->rays.total, A->txb, A->tyb, out, A->prec, st);
+    launch_project(A->ds, A->ptile.map(B), A->ptile.total, A->txb, A->tyb, out, A->prec, st);
     pe(A, DECT_PHASE_PROJECT, 1, st);
     if (A->counting) A->cR += 2;
 }
@@ -732,7 +745,7 @@ static void enq_lm_step(dect_admm* A, int b, cudaStream_t st) {
         launch_textures1(A->ds, A->tx.map(B), A->tx.total, A->ty.map(B), A->ty.total, A->lm_p, A->tx1, A->ty1, st);
         pe(A, DECT_PHASE_TEXTURE, 2, st);
         pb(A, st);
-        launch_project1(A->ds, rays, A->rays.total, A->tx1, A->ty1, A->lm_q, st);
+        launch_project1(A->ds, A->ptile.map(B), A->ptile.total, A->tx1, A->ty1, A->lm_q, st);
         pe(A, DECT_PHASE_PROJECT, 1, st);
         pb(A, st);
         launch_bp_sweep1(A->ds, A->sweep.map(B), A->sweep.total, A->sweep_C, A->lm_q, A->lm_g, A->lm_scale,
@@ -924,6 +937,28 @@ static void enq_iteration(dect_admm* A, cudaStream_t st) {
     pe(A, DECT_PHASE_UPDATE, 1, st);
 }
 
+// Eq. 4 at the current x of every slice: a fresh projection R x, the data term per ray and the TV
+// term per pixel, summed per slice into the scalars (objective, and the iteration it belongs to).
+// A monitor: its projection is not one of Table 1's applications (cR is left as it was).
+static void enq_objective(dect_admm* A, cudaStream_t st) {
+    const int B = A->B;
+    const BlockMap pix = A->pix.map(B), rays = A->rays.map(B);
+    const int64_t r0 = A->cR;
+    if (A->prec == PREC_F64) {
+        enq_project64(A, A->v64.x, A->v64.q, st);
+        launch64_objective(A->ds, rays, A->rays.total, pix, A->pix.total, A->spec->t64, A->spec->ne, A->meas,
+                           A->v64.q, A->v64.x, A->P.lambda_c, A->P.lambda_p, A->part_obj_rays, A->part_obj_pix, st);
+    } else {
+        enq_project(A, A->x, A->q, st);
+        launch_objective_rays(A->ds, rays, A->rays.total, A->spec->dev(), A->meas, A->q, A->part_obj_rays, A->prec,
+                              st);
+        launch_objective_tv(A->ds, pix, A->pix.total, A->x, A->P.lambda_c, A->P.lambda_p, A->part_obj_pix, st);
+    }
+    launch_objective_reduce(A->part_obj_rays, A->rays.d, A->part_obj_pix, A->pix.d, A->sc, B, st);
+    A->cR = r0;
+    A->cL += 3;
+}
+
 // Captures one iteration into a graph (with event pairs when profiling).
 static dect_status capture_iteration(dect_admm* A, bool profile, cudaGraphExec_t* out) {
     cudaGraph_t graph = nullptr;
@@ -1020,6 +1055,7 @@ static dect_status enq_initialize64(dect_admm* A, bool all_x0, cudaStream_t st) 
     launch64_state_from_image(A->ds, pix, A->pix.total, rays, A->rays.total, v, A->P.lm_mu0, st);
     launch_reset_scalars(A->sc, B, A->P.rho0_c, A->P.rho0_p, st);
     CUDA_TRY(cudaGetLastError());
+    A->iters_done = 0;
     A->initialized = true;
     return DECT_OK;
 }
@@ -1062,6 +1098,7 @@ static dect_status enq_initialize(dect_admm* A, cudaStream_t st) {
     launch_reset_scalars(A->sc, B, A->P.rho0_c, A->P.rho0_p, st);
     if (A->P.scheme == DECT_SCHEME_LM_CG) launch_lm_reset(A->ls, B, A->P.lm_mu0, st);
     CUDA_TRY(cudaGetLastError());
+    A->iters_done = 0;
     A->initialized = true;
     return DECT_OK;
 }
@@ -1217,6 +1254,7 @@ extern "C" dect_status dect_admm_create(dect_geom* const* geoms, int32_t B, cons
         P->storage != DECT_STORE_F64)
         DECT_FAIL(DECT_EINVAL, "dect_admm_create: storage must be DECT_STORE_F32, F16, BF16 or F64");
     if (P->udm_f64 != 0 && P->udm_f64 != 1) DECT_FAIL(DECT_EINVAL, "dect_admm_create: udm_f64 must be 0 or 1");
+    if (P->objective_every < 0) DECT_FAIL(DECT_EINVAL, "dect_admm_create: objective_every must be >= 0");
     if (P->storage == DECT_STORE_F64) {
         if (P->scheme != DECT_SCHEME_UDM_PCG || P->init != DECT_INIT_PCG)
             DECT_FAIL(DECT_EUNSUPPORTED, "dect_admm_create: float64 storage runs the UDM-PCG scheme from the "
@@ -1269,7 +1307,8 @@ extern "C" dect_status dect_admm_create(dect_geom* const* geoms, int32_t B, cons
     A->has_x0.assign(B, 0);
     A->has_truth.assign(B, 0);
     A->has_data.assign(B, 0);
-    for (auto* m : {&A->rays, &A->pix, &A->tx, &A->ty, &A->rows, &A->cols, &A->sweep, &A->cols64}) m->h.assign(1, 0);
+    for (auto* m : {&A->rays, &A->pix, &A->tx, &A->ty, &A->rows, &A->cols, &A->sweep, &A->cols64, &A->ptile})
+        m->h.assign(1, 0);
     std::vector<int> tune;  // candidate CTA groups per tile when autotuning (first = the occupancy choice)
     {
         int total = 0;
@@ -1326,6 +1365,7 @@ extern "C" dect_status dect_admm_create(dect_geom* const* geoms, int32_t B, cons
         max_nr = std::max(max_nr, nr);
         A->hs.push_back(sd);
         A->rays.h.push_back(A->rays.h.back() + (int)((nr + kRaysPerBlock - 1) / kRaysPerBlock));
+        A->ptile.h.push_back(A->ptile.h.back() + proj_tiles(g->desc.n_views, g->desc.n_bins));
         A->pix.h.push_back(A->pix.h.back() + (int)((np + 255) / 256));
         A->tx.h.push_back(A->tx.h.back() + texture_x_blocks(nx, ny));
         A->ty.h.push_back(A->ty.h.back() + texture_y_blocks(nx, ny));
@@ -1398,8 +1438,10 @@ extern "C" dect_status dect_admm_create(dect_geom* const* geoms, int32_t B, cons
     if (e == cudaSuccess) e = dalloc(&A->part_xi, 4 * (size_t)np_blk);
     if (e == cudaSuccess) e = dalloc(&A->part_rs, 2 * (size_t)A->rows.h.back());
     if (e == cudaSuccess) e = dalloc(&A->part_pap, 2 * (size_t)A->pix.h.back());
+    if (e == cudaSuccess) e = dalloc(&A->part_obj_rays, (size_t)nr_blk);
+    if (e == cudaSuccess) e = dalloc(&A->part_obj_pix, (size_t)np_blk);
     if (e == cudaSuccess && A->prec != PREC_F64) e = dalloc(&A->bp_partial, (size_t)A->sweep_C * A->n_img);
-    for (MapBuf* m : {&A->rays, &A->pix, &A->tx, &A->ty, &A->rows, &A->cols, &A->sweep, &A->cols64})
+    for (MapBuf* m : {&A->rays, &A->pix, &A->tx, &A->ty, &A->rows, &A->cols, &A->sweep, &A->cols64, &A->ptile})
         if (e == cudaSuccess) e = upload_map(*m);
     if (e == cudaSuccess) e = cudaMemcpy(A->ds, A->hs.data(), sizeof(SliceDesc) * B, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemset(A->truth, 0, sizeof(float2) * A->n_img);
@@ -1508,15 +1550,23 @@ static void count_iterations(dect_admm* A, int iters) {
 }
 
 static dect_status run_iterations(dect_admm* A, int iters, cudaStream_t st) {
-    if (A->P.use_graph) {
-        if (!A->gexec) {
-            dect_status s = capture_iteration(A, false, &A->gexec);
-            if (s != DECT_OK) return s;
+    if (A->P.use_graph && !A->gexec) {
+        dect_status s = capture_iteration(A, false, &A->gexec);
+        if (s != DECT_OK) return s;
+    }
+    const int k = A->P.objective_every;
+    for (int i = 0; i < iters;) {
+        // run up to the next iteration whose objective is wanted
+        const int n = k > 0 ? std::min(iters - i, (int)(k - A->iters_done % k)) : iters - i;
+        if (A->P.use_graph) {
+            for (int j = 0; j < n; ++j) CUDA_TRY(cudaGraphLaunch(A->gexec, st));
+            count_iterations(A, n);
+        } else {
+            for (int j = 0; j < n; ++j) enq_iteration(A, st);
         }
-        for (int i = 0; i < iters; ++i) CUDA_TRY(cudaGraphLaunch(A->gexec, st));
-        count_iterations(A, iters);
-    } else {
-        for (int i = 0; i < iters; ++i) enq_iteration(A, st);
+        A->iters_done += n;
+        i += n;
+        if (k > 0 && A->iters_done % k == 0) enq_objective(A, st);
     }
     CUDA_TRY(cudaGetLastError());
     return DECT_OK;
@@ -1539,6 +1589,7 @@ extern "C" dect_status dect_admm_profile(dect_admm* A, int32_t iters, void* stre
         dect_status s = capture_iteration(A, true, &A->pgexec);
         if (s != DECT_OK) return s;
     }
+    A->iters_done += iters;
     for (int i = 0; i < iters; ++i) {
         CUDA_TRY(cudaGraphLaunch(A->pgexec, st));
         CUDA_TRY(cudaStreamSynchronize(st));
@@ -1653,7 +1704,7 @@ struct CkptParams {
 struct CkptHeader {
     char magic[8];
     int32_t version, B, storage, scheme, initialized, n_segments;
-    int64_t n_img, n_sino, cR, cRT, cF, cL;
+    int64_t n_img, n_sino, cR, cRT, cF, cL, iters_done;
     CkptParams params;
 };
 
@@ -1766,6 +1817,7 @@ extern "C" dect_status dect_admm_save(dect_admm* A, void* dst_host, size_t bytes
     h.cRT = A->cRT;
     h.cF = A->cF;
     h.cL = A->cL;
+    h.iters_done = A->iters_done;
     h.params = ckpt_params(A);
     std::memcpy(out, &h, sizeof(h));
     size_t off = sizeof(h);
@@ -1829,6 +1881,7 @@ extern "C" dect_status dect_admm_load(dect_admm* A, const void* src_host, size_t
     A->cRT = h.cRT;
     A->cF = h.cF;
     A->cL = h.cL;
+    A->iters_done = h.iters_done;
     return DECT_OK;
 }
 
@@ -1861,5 +1914,7 @@ extern "C" dect_status dect_admm_stats(dect_admm* A, int32_t b, dect_stats* out,
     out->count_f = A->cF;
     out->count_launches = A->cL;
     out->bp_view_groups = A->sweep_groups_in_use;
+    out->objective = v.objective_iter >= 0 ? v.objective : NAN;
+    out->objective_iteration = v.objective_iter;
     return DECT_OK;
 }

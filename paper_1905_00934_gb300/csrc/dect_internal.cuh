@@ -86,7 +86,8 @@ struct SliceScalars {
     // scalars, rho, and the factor the scaled duals are divided by this iteration
     float alpha_f[2], beta_f[2], rho_f[2], ifactor_f[2];
     int32_t iteration;
-    int32_t pad;
+    int32_t objective_iter;  // the iteration the objective below was evaluated after (-1: never)
+    double objective;        // Eq. 4 at that iteration's x
 };
 
 // Per-slice scalars of the comparison scheme LM(m) x CG(n) (one LM step on one basis at a time)
@@ -104,12 +105,16 @@ struct LmScalars {
 // with k = f * log2(e) so that exp(-f_KN a_c - f_p a_p) = exp2(-k_kn a_c - k_p a_p).
 // w1 = {S_h, S_l, S_h f_KN, S_h f_p}, w2 = {S_l f_KN, S_l f_p, 0, 0} in float64 (unit-sum S), for the
 // decomposition's float64 sums (dect_params.udm_f64).
+// n_both, n_end, tail_high: the supports of the spectra (bins past a spectrum's last non-zero entry
+// contribute exact zeros to its sums): both may be non-zero below n_both, only the high spectrum
+// (tail_high) or only the low one in [n_both, n_end), neither from n_end on.
 struct SpecDev {
     int ne;
     const float4* t1;
     const float4* t2;
     const double4_32a* w1;
     const double4_32a* w2;
+    int n_both, n_end, tail_high;
 };
 
 // Epilogue modes of the backprojector.
@@ -140,6 +145,8 @@ void launch_textures(const SliceDesc* dsl, const BlockMap& mx, int nbx, const Bl
                      const float2* img, void* tx, void* ty, int prec, cudaStream_t st);
 void launch_textures1(const SliceDesc* dsl, const BlockMap& mx, int nbx, const BlockMap& my, int nby,
                       const float* img, float2* tx, float2* ty, cudaStream_t st);
+// projector CTAs (tiles of views x bins) of a slice; the projector's block maps count these
+int proj_tiles(int nv, int nb);
 void launch_project1(const SliceDesc* dsl, const BlockMap& map, int nblk, const float2* tx, const float2* ty,
                      float* out, cudaStream_t st);
 void launch_project(const SliceDesc* dsl, const BlockMap& map, int nblk, const void* tx, const void* ty, void* out,
@@ -174,6 +181,9 @@ constexpr int kPixPerBlock = 256;
 void launch_udm_admm(const SliceDesc* dsl, const BlockMap& map, int nblk, const SpecDev& sp, const float4* meas,
                      const void* Rx, void* ua, void* a, float* mu, uint8_t* status,
                      const SliceScalars* sc, int iters, double* partial, int prec, bool f64, cudaStream_t st);
+// Eq. 4's data term: partial[blk] = sum 1/2 (w_h r_h^2 + w_l r_l^2) over the block's rays, r = f(q) - m
+void launch_objective_rays(const SliceDesc* dsl, const BlockMap& map, int nblk, const SpecDev& sp, const float4* meas,
+                           const void* q, double* partial, int prec, cudaStream_t st);
 void launch_udm_init(const SliceDesc* dsl, const BlockMap& map, int nblk, const SpecDev& sp, const float4* meas,
                      void* a, float* mu, double rho_p, int iters, float abar, double mu0, int prec, cudaStream_t st);
 void launch_udm_rays(const SpecDev& sp, int64_t n, const float* mh, const float* ml, const float* wh,
@@ -276,6 +286,10 @@ void launch64_state_from_image(const SliceDesc* d, const BlockMap& pix, int np, 
 void launch64_xi_partials(const SliceDesc* d, const BlockMap& pix, int np, const double* x, const float2* truth,
                           double* partial, cudaStream_t st);
 void launch64_from_f32(const float* in, int64_t n, double* out, cudaStream_t st);
+// Eq. 4's partials: data term per ray block at q = R x (part_rays), TV per pixel block (part_pix)
+void launch64_objective(const SliceDesc* d, const BlockMap& rays, int nr, const BlockMap& pix, int np,
+                        const double4_32a* t64, int ne, const float4* meas, const double* q, const double* x,
+                        double lam_c, double lam_p, double* part_rays, double* part_pix, cudaStream_t st);
 
 // ---- filtered backprojection and CDM-FBP (fbp.cu) ----
 struct FbpDev {

@@ -11,9 +11,10 @@
 // Positions carry ~1e-7 pixel error against the exact geometry (float32
 // positions would carry ~3e-5 near |q| = 512).
 //
-// R: one thread per ray; Joseph's linear interpolation between the two
-// neighbours; the image is read through a pair texture (both neighbours of
-// both bases in one 16-byte load).
+// R: one thread per ray, a warp per view and 32 neighbouring bins stepping
+// through the sampled columns (rows) in lock step, a CTA per tile of views x
+// bins; Joseph's linear interpolation between the two neighbours; the image is
+// read through a pair texture (both neighbours of both bases in one 16-byte load).
 //
 // R^T: the column-sweep kernel of backproject_sweep.cu evaluates the same
 // integers per sample, so <R x, y> = <x, R^T y> holds to float32 summation
@@ -173,22 +174,32 @@ __global__ void k_pack_planar(const float* __restrict__ in, int nch, int64_t n, 
 // ---------------------------------------------------------------------------------------------
 // forward projector
 
-constexpr int kProjBatch = 8;
+// Launch shape of the forward projector (compile-time; the defaults are the measured best on GB300):
+// samples whose texel loads are issued together per lane, views (warps) per CTA, the CTAs per SM the
+// register allocation must allow, and whether positions advance incrementally or are recomputed from
+// the index at every sample (both give the same integers, so the same results).
+#ifndef DECT_PROJ_BATCH
+#define DECT_PROJ_BATCH 8
+#endif
+#ifndef DECT_PROJ_VIEWS
+#define DECT_PROJ_VIEWS 8
+#endif
+#ifndef DECT_PROJ_MINB
+#define DECT_PROJ_MINB 1
+#endif
+#ifndef DECT_PROJ_INCR
+#define DECT_PROJ_INCR 0
+#endif
+constexpr int kProjBatch = DECT_PROJ_BATCH;
 
-// Sum over the ray's samples of the interpolated {c, p}; returns unweighted sums.
-//
-// The float estimate of the sample range is trimmed with the exact fixed-point positions at its two
+// The float estimate of a ray's sample range, trimmed with the exact fixed-point positions at its two
 // ends, so every sample in [lo, hi] has its lower neighbour in [-2, n_across] (positions are linear
 // in t): the texel index (t, floor + 2) then lies inside the padded row [0, n_across + 2] without a
 // per-sample clamp. Trimming only drops samples whose two neighbours are both outside the image.
-template <class TX>
-__device__ __forceinline__ float2 ray_sum(const int4 P, const GeomDev& g, const TX* __restrict__ tx,
-                                          const TX* __restrict__ ty) {
+// An empty range comes back as lo > hi.
+__device__ __forceinline__ void trimmed_range(const int4 P, const GeomDev& g, int& lo, int& hi) {
     const bool ax = ray_axis(P);
     const int n_along = ax ? g.ny : g.nx, n_across = ax ? g.nx : g.ny;
-    const TX* __restrict__ tex = ax ? ty : tx;
-    const int ld = n_across + 3;
-    int lo, hi;
     sample_range(P, n_along, n_across, lo, hi);
     const long long step = ray_step(P), q0 = ray_q0(P);
     for (int k = 0; k < 4 && lo <= hi; ++k) {
@@ -201,25 +212,74 @@ __device__ __forceinline__ float2 ray_sum(const int4 P, const GeomDev& g, const 
         if (h >= -2 && h <= n_across) break;
         --hi;
     }
-    float ac = 0.f, ap = 0.f;
-    if (lo > hi) return make_float2(ac, ap);
-    {
+    if (lo <= hi) {
         // the trimming loops stop after 4 steps; re-check so that no sample can index outside its row
         const int h0 = pos_floor(q0 + (long long)lo * step), h1 = pos_floor(q0 + (long long)hi * step);
-        if (h0 < -2 || h0 > n_across || h1 < -2 || h1 > n_across) return make_float2(ac, ap);
+        if (h0 < -2 || h0 > n_across || h1 < -2 || h1 > n_across) hi = lo - 1;
     }
-    long long q = q0 + (long long)lo * step;
-    int base = lo * ld + 2;  // texel (t, floor(q) + 2) is tex[base + floor(q)]
-    int t = lo;
-    // blocks of kProjBatch samples: all texel loads of a block are issued before they are used, so a
-    // warp keeps several L2 requests in flight (the texels of neighbouring rays rarely share L1 lines)
-    for (; t + kProjBatch - 1 <= hi; t += kProjBatch) {
+}
+
+// Sum over a ray's samples of the interpolated {c, p} (unweighted), with the warp stepping in lock
+// step: every lane visits the same sampled index t, from the warp's lowest first index to its highest
+// last one, so at each step the lanes (neighbouring rays) read neighbouring texels of one texture row
+// and their loads coalesce. A lane outside its own [lo, hi] reads texel 0 of its texture, which is
+// always zero padding (the pair of rows or columns -2, -1 of column or row 0), and adds an exact zero,
+// so each ray's sum takes the same terms in the same order as a walk over its own range alone.
+// Every lane of the warp must call this (valid = false for lanes without a ray).
+template <class TX>
+__device__ __forceinline__ float2 ray_sum_sync(const int4 P, bool valid, const GeomDev& g, const TX* __restrict__ tx,
+                                               const TX* __restrict__ ty) {
+    const bool ax = ray_axis(P);
+    const int n_across = ax ? g.nx : g.ny;
+    const TX* __restrict__ tex = ax ? ty : tx;
+    const int ld = n_across + 3;
+    int lo = 1, hi = 0;
+    if (valid) trimmed_range(P, g, lo, hi);
+    const bool any = lo <= hi;
+    const int t0 = __reduce_min_sync(0xffffffffu, any ? lo : 0x7fffffff);
+    const int t1 = __reduce_max_sync(0xffffffffu, any ? hi : -1);
+    float ac = 0.f, ap = 0.f;
+    if (t0 > t1) return make_float2(ac, ap);  // no lane of the warp samples the image (warp-uniform)
+    // from here 0 <= t0 <= t1 < max(nx, ny): the bounds below cannot overflow
+    const long long step = ray_step(P), q0 = ray_q0(P);
+    int t = t0;
+#if DECT_PROJ_INCR
+    // positions and texel rows advance by exact integer steps; a lane samples while (t - lo), modulo 2^32
+    // (it wraps through 0 exactly when t reaches lo), is <= hi - lo. A lane without samples starts at
+    // 2^31 with len 0: its rel stays in [2^31, 2^31 + 4104) over at most 4096 + 8 steps, never <= 0.
+    long long q = q0 + (long long)t0 * step;
+    int base = t0 * ld + 2;  // texel (t, floor + 2) is tex[base + floor(q)]
+    unsigned rel = any ? (unsigned)(t0 - lo) : 0x80000000u;
+    const unsigned len = any ? (unsigned)(hi - lo) : 0u;
+    for (; t <= t1 - (kProjBatch - 1); t += kProjBatch) {
         float4 v[kProjBatch];
         float f[kProjBatch];
 #pragma unroll
         for (int u = 0; u < kProjBatch; ++u) {
-            const long long qu = q + (long long)u * step;
-            v[u] = ldtex(tex + (base + u * ld + pos_floor(qu)));
+            v[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (rel + (unsigned)u <= len) v[u] = ldtex(tex + (base + pos_floor(q)));
+            f[u] = frac_of(q);
+            q += step;
+            base += ld;
+        }
+        rel += kProjBatch;
+#pragma unroll
+        for (int u = 0; u < kProjBatch; ++u) {
+            ac += fmaf(f[u], v[u].z - v[u].x, v[u].x);
+            ap += fmaf(f[u], v[u].w - v[u].y, v[u].y);
+        }
+    }
+#else
+    for (; t <= t1 - (kProjBatch - 1); t += kProjBatch) {
+        float4 v[kProjBatch];
+        float f[kProjBatch];
+#pragma unroll
+        for (int u = 0; u < kProjBatch; ++u) {
+            const int tt = t + u;
+            const long long qu = q0 + (long long)tt * step;
+            // a lane outside its range reads texel 0, which is zero padding (rows or columns -2 and -1)
+            const int idx = (tt >= lo && tt <= hi) ? tt * ld + 2 + pos_floor(qu) : 0;
+            v[u] = ldtex(tex + idx);
             f[u] = frac_of(qu);
         }
 #pragma unroll
@@ -227,65 +287,82 @@ __device__ __forceinline__ float2 ray_sum(const int4 P, const GeomDev& g, const 
             ac += fmaf(f[u], v[u].z - v[u].x, v[u].x);
             ap += fmaf(f[u], v[u].w - v[u].y, v[u].y);
         }
-        q += (long long)kProjBatch * step;
-        base += kProjBatch * ld;
     }
-    for (; t <= hi; ++t) {
-        const float4 v = ldtex(tex + (base + pos_floor(q)));
-        const float f = frac_of(q);
+#endif
+    for (; t <= t1; ++t) {
+        const long long q1 = q0 + (long long)t * step;
+        const float4 v = ldtex(tex + ((t >= lo && t <= hi) ? t * ld + 2 + pos_floor(q1) : 0));
+        const float f = frac_of(q1);
         ac += fmaf(f, v.z - v.x, v.x);
         ap += fmaf(f, v.w - v.y, v.y);
-        q += step;
-        base += ld;
     }
     return make_float2(ac, ap);
 }
 
+// A CTA takes a tile of kProjViews consecutive views x 32 consecutive bins, one warp per view: the
+// rays of neighbouring views through the same bins cross nearly the same texels, so the tile's warps
+// share them in L1.
+constexpr int kProjViews = DECT_PROJ_VIEWS;
+
+__host__ __device__ __forceinline__ int proj_bin_tiles(int nb) { return (nb + 31) / 32; }
+
+int proj_tiles(int nv, int nb) { return ((nv + kProjViews - 1) / kProjViews) * proj_bin_tiles(nb); }
+
+// (view, bin) of this thread in tile `local` of a slice with nv views and nb bins
+__device__ __forceinline__ bool proj_ray(int local, int nv, int nb, int& v, int& k) {
+    const int nbt = proj_bin_tiles(nb);
+    v = (local / nbt) * kProjViews + (int)(threadIdx.x >> 5);
+    k = (local % nbt) * 32 + (int)(threadIdx.x & 31);
+    return v < nv && k < nb;
+}
+
 template <class S2, class TX>
-__global__ void __launch_bounds__(kRaysPerBlock) k_project(const SliceDesc* __restrict__ dsl, BlockMap map,
-                                                           const TX* __restrict__ tx, const TX* __restrict__ ty,
-                                                           S2* __restrict__ out) {
+__global__ void __launch_bounds__(32 * kProjViews, DECT_PROJ_MINB) k_project(const SliceDesc* __restrict__ dsl, BlockMap map,
+                                                             const TX* __restrict__ tx, const TX* __restrict__ ty,
+                                                             S2* __restrict__ out) {
     int local;
     const int s = slice_of(map, blockIdx.x, local);
     const SliceDesc& d = dsl[s];
-    const int64_t r = (int64_t)local * kRaysPerBlock + threadIdx.x;
-    if (r >= (int64_t)d.g.nv * d.g.nb) return;
-    const int4 P = __ldg(d.g.rays + r);
-    const float2 acc = ray_sum(P, d.g, tx + d.tx_off, ty + d.ty_off);
+    int v, k;
+    const bool valid = proj_ray(local, d.g.nv, d.g.nb, v, k);
+    const int64_t r = (int64_t)v * d.g.nb + k;
+    const int4 P = valid ? __ldg(d.g.rays + r) : make_int4(0, 0, 0, 0);
+    const float2 acc = ray_sum_sync(P, valid, d.g, tx + d.tx_off, ty + d.ty_off);
     const float w = ray_w(P);
-    st2(out + d.sino_off + r, make_float2(w * acc.x, w * acc.y));
+    if (valid) st2(out + d.sino_off + r, make_float2(w * acc.x, w * acc.y));
 }
 
-__global__ void __launch_bounds__(kRaysPerBlock) k_project_planar(SliceDesc d, const float4* __restrict__ tx,
-                                                                  const float4* __restrict__ ty,
-                                                                  float* __restrict__ out, int nch) {
+__global__ void __launch_bounds__(32 * kProjViews, DECT_PROJ_MINB) k_project_planar(SliceDesc d, const float4* __restrict__ tx,
+                                                                    const float4* __restrict__ ty,
+                                                                    float* __restrict__ out, int nch) {
     const int64_t n = (int64_t)d.g.nv * d.g.nb;
-    const int64_t r = (int64_t)blockIdx.x * kRaysPerBlock + threadIdx.x;
-    if (r >= n) return;
-    const int4 P = __ldg(d.g.rays + r);
-    const float2 acc = ray_sum(P, d.g, tx, ty);
+    int v, k;
+    const bool valid = proj_ray(blockIdx.x, d.g.nv, d.g.nb, v, k);
+    const int64_t r = (int64_t)v * d.g.nb + k;
+    const int4 P = valid ? __ldg(d.g.rays + r) : make_int4(0, 0, 0, 0);
+    const float2 acc = ray_sum_sync(P, valid, d.g, tx, ty);
     const float w = ray_w(P);
+    if (!valid) return;
     out[r] = w * acc.x;
     if (nch > 1) out[n + r] = w * acc.y;
 }
 
 void launch_project(const SliceDesc* dsl, const BlockMap& map, int nblk, const void* tx, const void* ty, void* out,
                     int prec, cudaStream_t st) {
+    constexpr int T = 32 * kProjViews;
     if (prec == PREC_F16)
-        k_project<__half2, TexH><<<nblk, kRaysPerBlock, 0, st>>>(dsl, map, (const TexH*)tx, (const TexH*)ty,
-                                                                  (__half2*)out);
+        k_project<__half2, TexH><<<nblk, T, 0, st>>>(dsl, map, (const TexH*)tx, (const TexH*)ty, (__half2*)out);
     else if (prec == PREC_BF16)
-        k_project<__nv_bfloat162, TexB><<<nblk, kRaysPerBlock, 0, st>>>(dsl, map, (const TexB*)tx, (const TexB*)ty,
-                                                                         (__nv_bfloat162*)out);
+        k_project<__nv_bfloat162, TexB><<<nblk, T, 0, st>>>(dsl, map, (const TexB*)tx, (const TexB*)ty,
+                                                             (__nv_bfloat162*)out);
     else
-        k_project<float2, float4><<<nblk, kRaysPerBlock, 0, st>>>(dsl, map, (const float4*)tx, (const float4*)ty,
-                                                                   (float2*)out);
+        k_project<float2, float4><<<nblk, T, 0, st>>>(dsl, map, (const float4*)tx, (const float4*)ty, (float2*)out);
 }
 
 // single channel: float out, float2 texels
 void launch_project1(const SliceDesc* dsl, const BlockMap& map, int nblk, const float2* tx, const float2* ty,
                      float* out, cudaStream_t st) {
-    k_project<float, float2><<<nblk, kRaysPerBlock, 0, st>>>(dsl, map, tx, ty, out);
+    k_project<float, float2><<<nblk, 32 * kProjViews, 0, st>>>(dsl, map, tx, ty, out);
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -333,9 +410,7 @@ void project_single(const SliceDesc& sd_in, const float* img, int nch, float2* s
     k_pack_planar<<<(unsigned)((np + 255) / 256), 256, 0, st>>>(img, nch, np, scratch);
     k_texture_x_single<<<tx_blocks(sd.g.nx, sd.g.ny), 256, 0, st>>>(sd, scratch, tx);
     k_texture_y_single<<<ty_blocks(sd.g.nx, sd.g.ny), 256, 0, st>>>(sd, scratch, ty);
-    const int64_t nr = (int64_t)sd.g.nv * sd.g.nb;
-    k_project_planar<<<(unsigned)((nr + kRaysPerBlock - 1) / kRaysPerBlock), kRaysPerBlock, 0, st>>>(sd, tx, ty, out,
-                                                                                                      nch);
+    k_project_planar<<<proj_tiles(sd.g.nv, sd.g.nb), 32 * kProjViews, 0, st>>>(sd, tx, ty, out, nch);
 }
 
 void launch_pack_planar(const float* in, int nch, int64_t n, float2* out, cudaStream_t st) {

@@ -498,6 +498,44 @@ __global__ void __launch_bounds__(256) k64_udm_init(const SliceDesc* __restrict_
     mu[d.sino_off + k] = mu0;
 }
 
+// Eq. 4's data term at the projections q = R x: partial[blk] = sum 1/2 (w_h r_h^2 + w_l r_l^2)
+__global__ void __launch_bounds__(256) k64_objective_rays(const SliceDesc* __restrict__ dsl, BlockMap rays,
+                                                          const double4_32a* __restrict__ t64, int ne,
+                                                          const float4* __restrict__ meas,
+                                                          const double* __restrict__ q, double* __restrict__ partial) {
+    extern __shared__ double4_32a tab64[];
+    const double4_32a* T = load_tables64(t64, ne, tab64);
+    int local;
+    const SliceDesc& d = dsl[slice_of(rays, blockIdx.x, local)];
+    const int64_t nr = nr_of(d), k = (int64_t)local * 256 + threadIdx.x;
+    double acc[1] = {0.0};
+    if (k < nr) {
+        const float4 m4 = meas[d.sino_off + k];
+        double fh, fl;
+        fwd64(T, ne, q[2 * d.sino_off + k], q[2 * d.sino_off + nr + k], fh, fl, nullptr);
+        const double rh = fh - m4.x, rl = fl - m4.y;
+        acc[0] = 0.5 * (m4.z * rh * rh + m4.w * rl * rl);
+    }
+    block_partials<1>(acc, partial);
+}
+
+// Eq. 4's regulariser: partial[blk] = sum lambda_c |D x_c|_1 + lambda_p |D x_p|_1
+__global__ void __launch_bounds__(256) k64_objective_tv(const SliceDesc* __restrict__ dsl, BlockMap pix,
+                                                        const double* __restrict__ x, double lam_c, double lam_p,
+                                                        double* __restrict__ partial) {
+    int local;
+    const SliceDesc& d = dsl[slice_of(pix, blockIdx.x, local)];
+    const int nx = d.g.nx, ny = d.g.ny;
+    const int64_t np = np_of(d), k = (int64_t)local * 256 + threadIdx.x;
+    double acc[1] = {0.0};
+    if (k < np) {
+        const int j = (int)(k / nx), i = (int)(k % nx);
+        const double2 gc = grad64(x + 2 * d.img_off, nx, ny, j, i), gp = grad64(x + 2 * d.img_off + np, nx, ny, j, i);
+        acc[0] = lam_c * (fabs(gc.x) + fabs(gc.y)) + lam_p * (fabs(gp.x) + fabs(gp.y));
+    }
+    block_partials<1>(acc, partial);
+}
+
 // ---- Eq. 9-11 on the image side, residual sums ----------------------------------------------------
 
 // y = shrinkage(D x - u^y, lambda / rho), z = max(0, x - u^z), u^y += y - D x, u^z += z - x;
@@ -734,6 +772,12 @@ void launch64_state_from_image(const SliceDesc* d, const BlockMap& pix, int np, 
 void launch64_xi_partials(const SliceDesc* d, const BlockMap& pix, int np, const double* x, const float2* truth,
                           double* partial, cudaStream_t st) {
     k64_xi_partials<<<np, 256, 0, st>>>(d, pix, x, truth, partial);
+}
+void launch64_objective(const SliceDesc* d, const BlockMap& rays, int nr, const BlockMap& pix, int np,
+                        const double4_32a* t64, int ne, const float4* meas, const double* q, const double* x,
+                        double lam_c, double lam_p, double* part_rays, double* part_pix, cudaStream_t st) {
+    k64_objective_rays<<<nr, 256, sizeof(double4_32a) * ne, st>>>(d, rays, t64, ne, meas, q, part_rays);
+    k64_objective_tv<<<np, 256, 0, st>>>(d, pix, x, lam_c, lam_p, part_pix);
 }
 void launch64_from_f32(const float* in, int64_t n, double* out, cudaStream_t st) {
     if (n > 0) k64_from_f32<<<nblocks(2 * n), 256, 0, st>>>(in, n, out);

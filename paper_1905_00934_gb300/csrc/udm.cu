@@ -52,43 +52,130 @@ __device__ __forceinline__ void kahan_add(float& sum, float& comp, float v) {
     sum = t;
 }
 
+// Energy bins by the spectra's supports (SpecDev): both spectra may be non-zero below n_both, only the
+// longer one (the high spectrum if tail_high) in [n_both, n_end), neither from n_end on. Zero-weight
+// terms are exact zeros, so skipping them leaves every sum bit for bit as it was; the compensated
+// additions still run once per block of 8 bins over all ne bins, so the blocking is unchanged too.
+// Blocks that lie wholly in one range run an unrolled body without per-bin tests.
+
+// one bin's terms: W = 3 both spectra, 1 the high one only, 2 the low one only
+template <int W>
+__device__ __forceinline__ void bin_jac(const float4* __restrict__ t1, const float4* __restrict__ t2, int e, float ac,
+                                        float ap, float& bh, float& bl, float& shc, float& shp, float& slc,
+                                        float& slp) {
+    const float4 a = t1[e];
+    const float4 b = t2[e];
+    const float t = exp2f(-fmaf(a.x, ac, a.y * ap));
+    if (W & 1) {
+        bh = fmaf(a.z, t, bh);
+        shc = fmaf(b.x, t, shc);
+        shp = fmaf(b.y, t, shp);
+    }
+    if (W & 2) {
+        bl = fmaf(a.w, t, bl);
+        slc = fmaf(b.z, t, slc);
+        slp = fmaf(b.w, t, slp);
+    }
+}
+
+// 2^x with rounding errors that average out: x = n + r, n = rint(x), r in [-1/2, 1/2] (exact), 2^r =
+// e^(r ln 2) by its Taylor series to degree 8 (truncation below 2e-10 relative, under 0.01 of float32's
+// half ulp) evaluated by Horner's rule with fused multiply-adds, then scaled by 2^n (ldexpf: exact,
+// down to subnormals and zero). Round-to-nearest errors of the Horner steps carry no sign preference,
+// whereas a fast exponential with a consistent half-ulp bias shifts every f(a) by ~3e-8; that bias is
+// harmless in the decomposition but not in a sum of many squared residuals whose mean is non-zero
+// (the objective of Eq. 4), which is where this one is used.
+__device__ __forceinline__ float exp2_series(float x) {
+    constexpr double L = 0.69314718055994530942;  // ln 2
+    constexpr float c1 = (float)L, c2 = (float)(L * L / 2.0), c3 = (float)(L * L * L / 6.0),
+                    c4 = (float)(L * L * L * L / 24.0), c5 = (float)(L * L * L * L * L / 120.0),
+                    c6 = (float)(L * L * L * L * L * L / 720.0), c7 = (float)(L * L * L * L * L * L * L / 5040.0),
+                    c8 = (float)(L * L * L * L * L * L * L * L / 40320.0);
+    const float n = rintf(x);
+    const float r = x - n;
+    float p = fmaf(c8, r, c7);
+    p = fmaf(p, r, c6);
+    p = fmaf(p, r, c5);
+    p = fmaf(p, r, c4);
+    p = fmaf(p, r, c3);
+    p = fmaf(p, r, c2);
+    p = fmaf(p, r, c1);
+    p = fmaf(p, r, 1.0f);
+    return ldexpf(p, (int)fmaxf(n, -200.0f));
+}
+
+template <int W, bool SERIES = false>
+__device__ __forceinline__ void bin_val(const float4* __restrict__ t1, int e, float ac, float ap, float& bh, float& bl) {
+    const float4 a = t1[e];
+    const float x = -fmaf(a.x, ac, a.y * ap);
+    const float t = SERIES ? exp2_series(x) : exp2f(x);
+    if (W & 1) bh = fmaf(a.z, t, bh);
+    if (W & 2) bl = fmaf(a.w, t, bl);
+}
+
 // s_h, s_l (compensated, in blocks of 8 energies) and the four Jacobian numerators at (ac, ap).
-__device__ __forceinline__ void spectral_sums_jac(const float4* __restrict__ t1, const float4* __restrict__ t2, int ne,
-                                                  float ac, float ap, float& sh, float& sl, float& shc, float& shp,
-                                                  float& slc, float& slp) {
+__device__ __forceinline__ void spectral_sums_jac(const float4* __restrict__ t1, const float4* __restrict__ t2,
+                                                  const SpecDev& sp, float ac, float ap, float& sh, float& sl,
+                                                  float& shc, float& shp, float& slc, float& slp) {
     float ch = 0.f, cl = 0.f;
     sh = sl = shc = shp = slc = slp = 0.f;
-    for (int e0 = 0; e0 < ne; e0 += 8) {
+    for (int e0 = 0; e0 < sp.ne; e0 += 8) {
         float bh = 0.f, bl = 0.f;
-        const int e1 = min(e0 + 8, ne);
-        for (int e = e0; e < e1; ++e) {
-            const float4 a = t1[e];
-            const float4 b = t2[e];
-            const float t = exp2f(-fmaf(a.x, ac, a.y * ap));
-            bh = fmaf(a.z, t, bh);
-            bl = fmaf(a.w, t, bl);
-            shc = fmaf(b.x, t, shc);
-            shp = fmaf(b.y, t, shp);
-            slc = fmaf(b.z, t, slc);
-            slp = fmaf(b.w, t, slp);
+        if (e0 + 8 <= sp.n_both) {
+#pragma unroll
+            for (int u = 0; u < 8; ++u) bin_jac<3>(t1, t2, e0 + u, ac, ap, bh, bl, shc, shp, slc, slp);
+        } else if (e0 >= sp.n_both && e0 + 8 <= sp.n_end) {
+            if (sp.tail_high) {
+#pragma unroll
+                for (int u = 0; u < 8; ++u) bin_jac<1>(t1, t2, e0 + u, ac, ap, bh, bl, shc, shp, slc, slp);
+            } else {
+#pragma unroll
+                for (int u = 0; u < 8; ++u) bin_jac<2>(t1, t2, e0 + u, ac, ap, bh, bl, shc, shp, slc, slp);
+            }
+        } else {
+            const int e1 = min(e0 + 8, sp.n_end);
+            for (int e = e0; e < e1; ++e) {
+                if (e < sp.n_both)
+                    bin_jac<3>(t1, t2, e, ac, ap, bh, bl, shc, shp, slc, slp);
+                else if (sp.tail_high)
+                    bin_jac<1>(t1, t2, e, ac, ap, bh, bl, shc, shp, slc, slp);
+                else
+                    bin_jac<2>(t1, t2, e, ac, ap, bh, bl, shc, shp, slc, slp);
+            }
         }
         kahan_add(sh, ch, bh);
         kahan_add(sl, cl, bl);
     }
 }
 
-__device__ __forceinline__ void spectral_sums(const float4* __restrict__ t1, int ne, float ac, float ap, float& sh,
-                                              float& sl) {
+template <bool SERIES = false>
+__device__ __forceinline__ void spectral_sums(const float4* __restrict__ t1, const SpecDev& sp, float ac, float ap,
+                                              float& sh, float& sl) {
     float ch = 0.f, cl = 0.f;
     sh = sl = 0.f;
-    for (int e0 = 0; e0 < ne; e0 += 8) {
+    for (int e0 = 0; e0 < sp.ne; e0 += 8) {
         float bh = 0.f, bl = 0.f;
-        const int e1 = min(e0 + 8, ne);
-        for (int e = e0; e < e1; ++e) {
-            const float4 a = t1[e];
-            const float t = exp2f(-fmaf(a.x, ac, a.y * ap));
-            bh = fmaf(a.z, t, bh);
-            bl = fmaf(a.w, t, bl);
+        if (e0 + 8 <= sp.n_both) {
+#pragma unroll
+            for (int u = 0; u < 8; ++u) bin_val<3, SERIES>(t1, e0 + u, ac, ap, bh, bl);
+        } else if (e0 >= sp.n_both && e0 + 8 <= sp.n_end) {
+            if (sp.tail_high) {
+#pragma unroll
+                for (int u = 0; u < 8; ++u) bin_val<1, SERIES>(t1, e0 + u, ac, ap, bh, bl);
+            } else {
+#pragma unroll
+                for (int u = 0; u < 8; ++u) bin_val<2, SERIES>(t1, e0 + u, ac, ap, bh, bl);
+            }
+        } else {
+            const int e1 = min(e0 + 8, sp.n_end);
+            for (int e = e0; e < e1; ++e) {
+                if (e < sp.n_both)
+                    bin_val<3, SERIES>(t1, e, ac, ap, bh, bl);
+                else if (sp.tail_high)
+                    bin_val<1, SERIES>(t1, e, ac, ap, bh, bl);
+                else
+                    bin_val<2, SERIES>(t1, e, ac, ap, bh, bl);
+            }
         }
         kahan_add(sh, ch, bh);
         kahan_add(sl, cl, bl);
@@ -120,13 +207,13 @@ __device__ __forceinline__ float diff_of_products(float a, float b, float c, flo
 // so the cancellations of nearly collinear Compton and photoelectric columns happen only inside
 // det(J) and the adj(J) products, each one fma-compensated difference of products: the float32 solve
 // stays consistent with its float32 Jacobian, like a float64 solve of the same inputs.
-__device__ void lm_ray(const float4* __restrict__ t1, const float4* __restrict__ t2, int ne, const RayIn& in,
-                       int iters, LmState& s) {
+__device__ void lm_ray(const float4* __restrict__ t1, const float4* __restrict__ t2, const SpecDev& sp,
+                       const RayIn& in, int iters, LmState& s) {
     const float tm_h = expf(-in.mh), tm_l = expf(-in.ml);
     const float wh = in.wh, wl = in.wl, rc = in.rc, rp = in.rp;
     for (int it = 0; it < iters; ++it) {
         float sh, sl, shc, shp, slc, slp;
-        spectral_sums_jac(t1, t2, ne, s.ac, s.ap, sh, sl, shc, shp, slc, slp);
+        spectral_sums_jac(t1, t2, sp, s.ac, s.ap, sh, sl, shc, shp, slc, slp);
         const float rh = neg_log_ratio(sh, tm_h), rl = neg_log_ratio(sl, tm_l);  // f - m = -log(s / t)
         const float j0 = shc / sh, j1 = shp / sh, j2 = slc / sl, j3 = slp / sl;
         const float dc = (s.ac - in.vc_hi) - in.vc_lo, dp = (s.ap - in.vp_hi) - in.vp_lo;  // a - v
@@ -149,7 +236,7 @@ __device__ void lm_ray(const float4* __restrict__ t1, const float4* __restrict__
         const float n1 = fmaf(whl * dJ, ar1, aq1) + e0 * g1;
         const float tc = s.ac - n0 / det, tp = s.ap - n1 / det;
         float th, tl;
-        spectral_sums(t1, ne, tc, tp, th, tl);
+        spectral_sums(t1, sp, tc, tp, th, tl);
         // 2 (cost(trial) - cost(a)) = sum_k w_k (r1 - r0)(r1 + r0) + sum_b rho_b e_b (e_b + 2 (a_b - v_b))
         const float eh = neg_log_ratio(th, sh), el = neg_log_ratio(tl, sl);  // r1 - r0
         const float ec = tc - s.ac, ep = tp - s.ap;
@@ -312,7 +399,7 @@ __global__ void __launch_bounds__(kRaysPerBlock) k_udm_admm(const SliceDesc* __r
         if (F64)
             lm_ray64(t1, w1, w2, sp.ne, in, iters, st);
         else
-            lm_ray(t1, t2, sp.ne, in, iters, st);
+            lm_ray(t1, t2, sp, in, iters, st);
         // the stored (possibly rounded) a is what the dual update and the residuals see
         st2(a + e, make_float2(st.ac, st.ap));
         const float2 an = ld2(a + e);
@@ -358,7 +445,7 @@ __global__ void __launch_bounds__(kRaysPerBlock) k_udm_init(const SliceDesc* __r
     in.rc = 0.0f;
     in.rp = (float)rho_p;
     LmState st{m.y / abar, 0.0f, mu0, DECT_RAY_ACCEPTED};
-    lm_ray(t1, t2, sp.ne, in, iters, st);
+    lm_ray(t1, t2, sp, in, iters, st);
     st2(a + e, make_float2(st.ac, 0.0f));
     mu[e] = mu0;
 }
@@ -387,7 +474,7 @@ __global__ void __launch_bounds__(kRaysPerBlock) k_udm_rays(SpecDev sp, int64_t 
     in.rc = (float)rho_c;
     in.rp = (float)rho_p;
     LmState st{ac[r], ap[r], mu[r], DECT_RAY_ACCEPTED};
-    lm_ray(t1, t2, sp.ne, in, iters, st);
+    lm_ray(t1, t2, sp, in, iters, st);
     ac[r] = st.ac;
     ap[r] = st.ap;
     mu[r] = st.mu;
@@ -417,7 +504,7 @@ __global__ void __launch_bounds__(kRaysPerBlock) k_lm_rays(const SliceDesc* __re
     const float4 m = __ldg(meas + e);
     const float2 a = __ldg(Rx + e);
     float sh, sl, shc, shp, slc, slp;
-    spectral_sums_jac(t1, t2, sp.ne, a.x, a.y, sh, sl, shc, shp, slc, slp);
+    spectral_sums_jac(t1, t2, sp, a.x, a.y, sh, sl, shc, shp, slc, slp);
     const float rh = neg_log_ratio(sh, expf(-m.x)), rl = neg_log_ratio(sl, expf(-m.y));
     const float jh = (b ? shp : shc) / sh, jl = (b ? slp : slc) / sl;
     ew[e] = m.z * rh * jh + m.w * rl * jl;
@@ -449,7 +536,7 @@ __global__ void __launch_bounds__(kRaysPerBlock) k_lm_trial(const SliceDesc* __r
         float2 a = __ldg(Rx + e);
         if (b) a.y += __ldg(Rd + e); else a.x += __ldg(Rd + e);
         float sh, sl;
-        spectral_sums(t1, sp.ne, a.x, a.y, sh, sl);
+        spectral_sums(t1, sp, a.x, a.y, sh, sl);
         const float2 o = __ldg(s0 + e);
         const float r0h = neg_log_ratio(o.x, expf(-m.x)), r0l = neg_log_ratio(o.y, expf(-m.y));
         const float eh = neg_log_ratio(sh, o.x), el = neg_log_ratio(sl, o.y);
@@ -459,6 +546,37 @@ __global__ void __launch_bounds__(kRaysPerBlock) k_lm_trial(const SliceDesc* __r
 }
 
 static size_t tab_bytes(const SpecDev& sp) { return 2 * sizeof(float4) * (size_t)sp.ne; }
+// ---- Eq. 4's data term, per ray -------------------------------------------------------------------
+
+// partial[blk] = sum over the block's rays of 1/2 (w_h r_h^2 + w_l r_l^2), r = f(q) - m at the
+// projections q = R x (stored in S2), with the spectral sums and residuals of the decomposition.
+template <class S2>
+__global__ void __launch_bounds__(kRaysPerBlock) k_objective_rays(const SliceDesc* __restrict__ dsl, BlockMap map,
+                                                                  SpecDev sp, const float4* __restrict__ meas,
+                                                                  const S2* __restrict__ q,
+                                                                  double* __restrict__ partial) {
+    extern __shared__ float4 tabs[];
+    float4* t1 = tabs;
+    float4* t2 = tabs + sp.ne;
+    load_tables(sp, t1, t2);
+    int local;
+    const SliceDesc& d = dsl[slice_of(map, blockIdx.x, local)];
+    const int64_t r = (int64_t)local * kRaysPerBlock + threadIdx.x;
+    double acc[1] = {0.0};
+    if (r < (int64_t)d.g.nv * d.g.nb) {
+        const int64_t e = d.sino_off + r;
+        const float4 m = __ldg(meas + e);
+        const float2 a = ldg2(q + e);
+        float sh, sl;
+        spectral_sums<true>(t1, sp, a.x, a.y, sh, sl);
+        // r = f - m = -log(s) - m in float64 from the float32 sum (the sum carries ~1 ulp, without bias)
+        const double rh = -log((double)sh) - (double)m.x, rl = -log((double)sl) - (double)m.y;
+        acc[0] = 0.5 * ((double)m.z * rh * rh + (double)m.w * rl * rl);
+    }
+    block_partials<1>(acc, partial);
+}
+
+
 
 void launch_lm_rays(const SliceDesc* dsl, const BlockMap& map, int nblk, const SpecDev& sp, const float4* meas,
                     const float2* Rx, int b, float* ew, float* gw, float2* s0, float* Rd, cudaStream_t st) {
@@ -486,7 +604,7 @@ __global__ void __launch_bounds__(kRaysPerBlock) k_forward_model_f32(SpecDev sp,
     const int64_t r = (int64_t)blockIdx.x * kRaysPerBlock + threadIdx.x;
     if (r >= n) return;
     float sh, sl, shc, shp, slc, slp;
-    spectral_sums_jac(t1, t2, sp.ne, __ldg(ac + r), __ldg(ap + r), sh, sl, shc, shp, slc, slp);
+    spectral_sums_jac(t1, t2, sp, __ldg(ac + r), __ldg(ap + r), sh, sl, shc, shp, slc, slp);
     const double ish = 1.0 / (double)sh, isl = 1.0 / (double)sl;
     const double j0 = shc * ish, j1 = shp * ish, j2 = slc * isl, j3 = slp * isl;
     if (fh) fh[r] = (float)(-log((double)sh));
@@ -579,6 +697,19 @@ void launch_udm_admm(const SliceDesc* dsl, const BlockMap& map, int nblk, const 
         udm_admm_t<true>(dsl, map, nblk, sp, meas, Rx, ua, a, mu, status, sc, iters, partial, prec, st);
     else
         udm_admm_t<false>(dsl, map, nblk, sp, meas, Rx, ua, a, mu, status, sc, iters, partial, prec, st);
+}
+
+void launch_objective_rays(const SliceDesc* dsl, const BlockMap& map, int nblk, const SpecDev& sp, const float4* meas,
+                           const void* q, double* partial, int prec, cudaStream_t st) {
+    if (prec == PREC_F16)
+        k_objective_rays<__half2><<<nblk, kRaysPerBlock, tab_bytes(sp), st>>>(dsl, map, sp, meas, (const __half2*)q,
+                                                                                partial);
+    else if (prec == PREC_BF16)
+        k_objective_rays<__nv_bfloat162><<<nblk, kRaysPerBlock, tab_bytes(sp), st>>>(
+            dsl, map, sp, meas, (const __nv_bfloat162*)q, partial);
+    else
+        k_objective_rays<float2><<<nblk, kRaysPerBlock, tab_bytes(sp), st>>>(dsl, map, sp, meas, (const float2*)q,
+                                                                               partial);
 }
 
 void launch_udm_init(const SliceDesc* dsl, const BlockMap& map, int nblk, const SpecDev& sp, const float4* meas,

@@ -50,14 +50,15 @@ class Params(ctypes.Structure):
                 ("kappa", ctypes.c_double), ("init_udm_iters", ctypes.c_int32), ("init_pcg_iters", ctypes.c_int32),
                 ("precondition", ctypes.c_int32), ("use_graph", ctypes.c_int32), ("bp_view_groups", ctypes.c_int32),
                 ("storage", ctypes.c_int32), ("scheme", ctypes.c_int32), ("init", ctypes.c_int32),
-                ("udm_f64", ctypes.c_int32)]
+                ("udm_f64", ctypes.c_int32), ("objective_every", ctypes.c_int32)]
 
 
 class Stats(ctypes.Structure):
     _fields_ = [("iteration", ctypes.c_int32), ("rho", ctypes.c_double * 2), ("r_pri", ctypes.c_double * 2),
                 ("r_dual", ctypes.c_double * 2), ("xi_db", ctypes.c_double * 2), ("count_R", ctypes.c_int64),
                 ("count_RT", ctypes.c_int64), ("count_f", ctypes.c_int64), ("count_launches", ctypes.c_int64),
-                ("bp_view_groups", ctypes.c_int32)]
+                ("bp_view_groups", ctypes.c_int32), ("objective", ctypes.c_double),
+                ("objective_iteration", ctypes.c_int32)]
 
 
 # every symbol declared in include/dect.h, with its ctypes signature
@@ -312,7 +313,8 @@ def admm_stats(h, slice_index, stream=None) -> dict:
     _check(lib().dect_admm_stats(h, slice_index, ctypes.byref(s), _stream(stream)))
     return {"iteration": s.iteration, "rho": list(s.rho), "r_pri": list(s.r_pri), "r_dual": list(s.r_dual),
             "xi_db": list(s.xi_db), "count_R": s.count_R, "count_RT": s.count_RT, "count_f": s.count_f,
-            "count_launches": s.count_launches, "bp_view_groups": s.bp_view_groups}
+            "count_launches": s.count_launches, "bp_view_groups": s.bp_view_groups, "objective": s.objective,
+            "objective_iteration": s.objective_iteration}
 
 
 def admm_save(h, stream=None) -> np.ndarray:
