@@ -137,13 +137,10 @@ def joseph_weight_count(g) -> int:
     return total
 
 
-# dram bytes per launch of the backprojector sweep at the bench workload (8 slices) and the view-group
-# count it was captured with (profiles/k_bp_sweep_512x720x1024.txt); reported only when the solver
-# runs that count, since the partial images it writes scale with it
-SWEEP_TRAFFIC_B8 = (216.9e6, 8)
-# what bounds the sweep on chip, from its full-set capture (profiles/k_bp_sweep_512x720x1024.txt)
-SWEEP_LIMITER = {"resource": "shared-memory throughput and issue", "l1tex_throughput_pct": 82.7,
-                 "issue_active_pct": 66.3, "shared_wavefronts_per_slice": 9.66e7}
+# DRAM bytes per launch of the backprojector sweep at the bench workload (8 slices), keyed by the launch
+# shape they were captured with (slices, view groups, tile side, cluster form); from the counter capture
+# in profiles/k_bp_sweep_512x720x1024.txt. Reported only when the run uses that shape.
+SWEEP_TRAFFIC = {(8, 8, 32, 0): 134.0e6}
 
 
 # ------------------------------------------------------------------------------------------------
@@ -240,6 +237,51 @@ def run_reference(args):
 CDM_ITERS = 20  # LM iterations of the CDM decomposition (the same LM as UDM, rho = 0)
 
 
+def _timed_reconstruct(sol, steps, warmup, stream, flush, barrier=None):
+    """Device ms per step of reconstruct(ITERS) (L2 flushed between steps, outside the events)."""
+    import torch
+
+    for _ in range(warmup):
+        sol.reconstruct(ITERS)
+    (barrier or torch.cuda.synchronize)()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for k in range(steps):
+        flush.fill_(float(k))
+        ev[k][0].record(stream)
+        sol.reconstruct(ITERS)
+        ev[k][1].record(stream)
+    (barrier or torch.cuda.synchronize)()
+    return [a.elapsed_time(b) for a, b in ev]
+
+
+def _plain_ms(make_single, n, stream, flush, iters=ITERS):
+    """Device ms for the slices reconstructed one after another by single-slice solvers."""
+    import torch
+
+    singles = [make_single(b) for b in range(n)]
+    for s1 in singles:
+        s1.reconstruct(iters)  # warm-up (graph capture)
+    torch.cuda.synchronize()
+    p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    flush.fill_(0.0)
+    p0.record(stream)
+    for s1 in singles:
+        s1.reconstruct(iters)
+    p1.record(stream)
+    torch.cuda.synchronize()
+    del singles
+    return p0.elapsed_time(p1)
+
+
+# a plain single-slice solver: eager launches, backprojector view groups from the occupancy rule
+PLAIN = dict(use_graph=0, bp_view_groups=-1, bp_tile=32, bp_cluster=-1)
+
+
+def _phase_ms(sol, iters=5):
+    prof = sol.profile(iters)
+    return {p: prof[p][0] / iters for p in prof}
+
+
 def run_dect(args):
     import torch
 
@@ -278,9 +320,10 @@ def run_dect(args):
     sol = Solver(geo, spec, kappa=BAGGAGE_KAPPA, storage=storage)
     f32 = lambda a: torch.tensor(np.ascontiguousarray(a), dtype=torch.float32, device=dev)
     dev_data = [[f32(c[k]) for k in ("m_h", "m_l", "w_h", "w_l")] for c in cases]
-    for b, c in enumerate(cases):
+    truths = [f32(np.stack([c["truth_c"], c["truth_p"]])) for c in cases]
+    for b in range(B):
         sol.set_data(b, *dev_data[b])
-        sol.set_truth(b, f32(np.stack([c["truth_c"], c["truth_p"]])))
+        sol.set_truth(b, truths[b])
     stream = torch.cuda.current_stream()
     if args.profile_run:
         # one untimed reconstruction of the workload, for profiler captures
@@ -295,121 +338,16 @@ def run_dect(args):
             torch.distributed.barrier()
         torch.cuda.synchronize()
 
-    for _ in range(args.warmup):
-        sol.reconstruct(ITERS)
-    barrier()
-
+    # ---- the headline: B slices batched per launch, reconstruct to the workload's iteration count ----
     launches0 = sol.stats(0)["count_launches"]
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     with ClockSampler(torch.cuda.current_device()) as clk:
-        barrier()
-        for k in range(args.steps):
-            flush.fill_(float(k))  # evict L2 between steps (outside the events)
-            ev[k][0].record(stream)
-            sol.reconstruct(ITERS)
-            ev[k][1].record(stream)
-        barrier()
+        step_ms = _timed_reconstruct(sol, args.steps, args.warmup, stream, flush, barrier)
     clocks = clk.summary()
-    launches = sol.stats(0)["count_launches"] - launches0
-    step_ms = [a.elapsed_time(b) for a, b in ev]
+    # every step launches the same kernels: the timed steps' share of the warm-up and timed launches
+    launches = (sol.stats(0)["count_launches"] - launches0) * args.steps // (args.steps + args.warmup)
     total_ms = shard.max_over_ranks(float(sum(step_ms)), dev)
     value = ws * B * args.steps / (total_ms / 1e3)
-
-    # the plain form: the same slices reconstructed one at a time by single-slice solvers, (a) as the
-    # metric names it -- eager launches, view groups from the occupancy rule -- and (b) with the
-    # graph and the autotuner (the single-slice path at its best)
-    plain_ms = plain_best_ms = None
-    if B > 1:
-        for kind, params in (("plain", dict(use_graph=0, bp_view_groups=-1)), ("best", {})):
-            singles = []
-            for b, c in enumerate(cases):
-                s1 = Solver([geo[b]], spec, kappa=BAGGAGE_KAPPA, **params)
-                s1.set_data(0, *dev_data[b])
-                singles.append(s1)
-            for s1 in singles:
-                s1.reconstruct(ITERS)  # warm-up (graph capture)
-            barrier()
-            p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            flush.fill_(0.0)
-            p0.record(stream)
-            for s1 in singles:
-                s1.reconstruct(ITERS)
-            p1.record(stream)
-            barrier()
-            if kind == "plain":
-                plain_ms = p0.elapsed_time(p1)
-            else:
-                plain_best_ms = p0.elapsed_time(p1)
-            del singles
-
-    # quality gate: xi_p of slice 0 after the workload's iterations vs the oracle's
     st0 = sol.stats(0)
-    gold = _golden()
-    gate = {"xi_p_db": st0["xi_db"][1], "xi_c_db": st0["xi_db"][0]}
-    if gold is not None and rank == 0:
-        target = gold["xi_p"][ITERS]
-        gate.update({"oracle_xi_p_db": target, "oracle_xi_c_db": gold["xi_c"][ITERS],
-                     "within_0p5_db": bool(abs(st0["xi_db"][1] - target) <= 0.5)})
-
-    # the paper's comparison (Sec. 4): time to the same PE error for UDM1-PCG1 and the old splitting
-    # LM1 x CG1 on the same slices; slice 0's xi_p checked every 5 iterations against the oracle's
-    # xi_p after the workload's iterations + 0.5 dB, up to twice the workload's iterations
-    def scheme_comparison():
-        target = gold["xi_p"][ITERS] + 0.5
-        comp = {"target_xi_p_db": target, "check_every": 5, "cap_iterations": 2 * ITERS,
-                "timed": "ADMM iterations after the shared initial image, CUDA events"}
-        for name, scheme in (("udm1_pcg1", dect.SCHEME_UDM_PCG), ("lm1_cg1", dect.SCHEME_LM_CG)):
-            s2 = Solver(geo, spec, kappa=BAGGAGE_KAPPA, scheme=scheme)
-            for b, c in enumerate(cases):
-                s2.set_data(b, *dev_data[b])
-                s2.set_truth(b, f32(np.stack([c["truth_c"], c["truth_p"]])))
-            s2.reconstruct(0)
-            s2.step(5)  # graph capture outside the timing
-            s2.reconstruct(0)
-            torch.cuda.synchronize()
-            t_ms, it, hit, xi_p = 0.0, 0, None, None
-            while it < 2 * ITERS:
-                c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                c0.record(stream)
-                s2.step(5)
-                c1.record(stream)
-                c1.synchronize()
-                t_ms += c0.elapsed_time(c1)
-                it += 5
-                xi_p = s2.stats(0)["xi_db"][1]
-                if xi_p <= target:
-                    hit = it
-                    break
-            comp[name] = {"iterations_to_target": hit, "ms_to_target": t_ms if hit else None,
-                          "ms_per_iteration": t_ms / it, "xi_p_db_at_stop": xi_p, "iterations_run": it,
-                          "slices": B}
-            del s2
-        # the paper's baseline (i), CDM-FBP (per-ray decomposition with rho = 0, a >= 0, FBP of each
-        # basis): device time per slice and the xi of slice 0, against the same target
-        from paper_1905_00934_gb300 import cdm_fbp
-
-        cdm_fbp(geo[0], spec, *dev_data[0][:4], iters=CDM_ITERS)  # one-time per-geometry tables
-        c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        c0.record(stream)
-        xs = [cdm_fbp(geo[b], spec, *dev_data[b][:4], iters=CDM_ITERS) for b in range(B)]
-        c1.record(stream)
-        c1.synchronize()
-        x0 = xs[0].cpu().numpy().astype(np.float64)
-        xi = [float(20.0 * np.log10(np.linalg.norm(x0[k] - t) / np.linalg.norm(t)))
-              for k, t in enumerate((cases[0]["truth_c"], cases[0]["truth_p"]))]
-        comp["cdm_fbp"] = {"ms_per_slice": c0.elapsed_time(c1) / B, "decomposition_iterations": CDM_ITERS,
-                           "xi_c_db": xi[0], "xi_p_db": xi[1], "reaches_target": bool(xi[1] <= target)}
-        gold_cdm = _golden(GOLDEN_CDM_FBP)
-        if gold_cdm is not None and gold_cdm.get("decomposition_iterations") == CDM_ITERS:
-            comp["cdm_fbp"].update({"oracle_xi_c_db": gold_cdm["xi_c"], "oracle_xi_p_db": gold_cdm["xi_p"]})
-        return comp
-
-    comparison = None
-    if gold is not None and rank == 0 and not args.no_comparison:
-        try:
-            comparison = scheme_comparison()
-        except Exception as exc:  # an optional measurement must not cost the bench line
-            comparison = {"error": f"{type(exc).__name__}: {exc}"}
 
     # end to end through the C ABI: pinned host measurements in, image out, every step
     host_in = [[t.cpu().pin_memory() for t in d] for d in dev_data]
@@ -430,96 +368,320 @@ def run_dect(args):
     barrier()
     e2e_ms = shard.max_over_ranks(e0.elapsed_time(e1), dev)
     e2e_value = ws * B * e2e_steps / (e2e_ms / 1e3)
+    for b in range(B):  # back to the device-resident data
+        sol.set_data(b, *dev_data[b])
+    if ws > 1:
+        torch.distributed.destroy_process_group()  # the rank-0 legs below use no collective
+    if rank != 0:
+        return 0
 
-    # live per-kernel-group timing of the same iteration (CUDA events around each group)
+    cfg = {"workload": "fan 512x512, 720 views x 1024 bins, 40 objects, I0 2e5, UDM1-PCG1 x 100 + init",
+           "iterations_fixed": ITERS, "batch_per_gpu": B, "l2": "flushed between steps (512 MB write)",
+           "storage": args.storage, "bp_view_groups": st0["bp_view_groups"], "bp_tile": st0["bp_tile"],
+           "bp_cluster": st0["bp_cluster"]}
+    phases = _phase_ms(sol, 10)
+    for p_, ms in phases.items():
+        cfg[f"{args.storage}_ms_{p_}"] = round(ms, 4)
+    cfg[f"{args.storage}_ms_iteration"] = round(sum(phases.values()), 4)
+
+    # ---- the plain form of the metric and the batched mixed-precision arms ----
+    extras = not args.no_extras
+    if B > 1 and extras:
+        def single(params):
+            def make(b):
+                s1 = Solver([geo[b]], spec, kappa=BAGGAGE_KAPPA, **params)
+                s1.set_data(0, *dev_data[b])
+                return s1
+            return make
+
+        plain_ms = _plain_ms(single(PLAIN), B, stream, flush)
+        best_ms = _plain_ms(single({}), B, stream, flush)
+        plain = B / (plain_ms / 1e3)
+        cfg.update({"plain": "single-slice solvers in turn: eager, occupancy view groups, FP32",
+                    "plain_slices_per_s": plain, "batched_over_plain": value / plain,
+                    "plain_graph_autotuned_slices_per_s": B / (best_ms / 1e3),
+                    "batched_over_plain_graph_autotuned": value / (B / (best_ms / 1e3))})
+        for name, code in (("f16", 1), ("bf16", 2)):
+            if name == args.storage:
+                continue
+            try:
+                s16 = Solver(geo, spec, kappa=BAGGAGE_KAPPA, storage=code)
+                for b in range(B):
+                    s16.set_data(b, *dev_data[b])
+                    s16.set_truth(b, truths[b])
+                ms16 = _timed_reconstruct(s16, 2, 1, stream, flush)
+                v16 = B * 2 / (sum(ms16) / 1e3)
+                cfg[f"batched_{name}_slices_per_s"] = v16
+                cfg[f"batched_{name}_over_plain"] = v16 / plain
+                cfg[f"batched_{name}_xi_p_db"] = s16.stats(0)["xi_db"][1]
+                ph = _phase_ms(s16, 5)
+                for p_, ms in ph.items():
+                    cfg[f"{name}_ms_{p_}"] = round(ms, 4)
+                cfg[f"{name}_ms_iteration"] = round(sum(ph.values()), 4)
+                del s16
+            except Exception as exc:
+                cfg[f"batched_{name}_error"] = f"{type(exc).__name__}: {exc}"[:90]
+        # the float64 decomposition option: its cost per slice-iteration next to the default's
+        try:
+            s64 = Solver(geo, spec, kappa=BAGGAGE_KAPPA, udm_f64=1)
+            for b in range(B):
+                s64.set_data(b, *dev_data[b])
+            s64.reconstruct(1)
+            cfg["udm_us_per_slice"] = round(1e3 * phases["udm"] / B, 2)
+            cfg["udm_f64_us_per_slice"] = round(1e3 * _phase_ms(s64, 3)["udm"] / B, 2)
+            del s64
+        except Exception as exc:
+            cfg["udm_f64_error"] = f"{type(exc).__name__}: {exc}"[:90]
+
+    # ---- quality gate: xi_p of slice 0 after the workload's iterations vs the FP64 oracle's ----
+    gold = _golden()
+    cfg["pe_gate_xi_p_db"] = st0["xi_db"][1]
+    cfg["pe_gate_xi_c_db"] = st0["xi_db"][0]
+    if gold is not None:
+        target = gold["xi_p"][ITERS]
+        cfg["pe_gate_oracle_xi_p_db"] = target
+        cfg["pe_gate_ok"] = bool(abs(st0["xi_db"][1] - target) <= 0.5)
+
+    # ---- roofline of the dominant kernel group (live events of one captured iteration) ----
     prof = sol.profile(10)
-    top = max(prof, key=lambda p: prof[p][0])
+    top = max(prof, key=lambda p_: prof[p_][0])
     g = cases[0]["geom"]
     M, Np = g.n_views * g.n_bins, g.nx * g.ny
-    # algorithmic bytes per launch of each group (float32, both bases, per slice x B)
-    alg_bytes = {
-        "backproject": B * (8 * M + 8 * Np + (56 + 16) / 2 * Np),   # sinogram in, image out, epilogue images
-        "project": B * (16 * (g.nx * (g.ny + 3) + g.ny * (g.nx + 3)) / 2 + 8 * M),  # one texture read, sinogram out
-        "udm": B * (16 + 8 + 8 + 8 + 4 + 8 + 8 + 4 + 1) * M,
-        "precond": B * (8 * Np + 4 * 8 * Np + 2 * 8 * (2 * g.nx) * (2 * g.ny) + 8 * Np),
-        "texture": B * (8 * Np + 16 * (g.nx * (g.ny + 3) + g.ny * (g.nx + 3))),
-        "update": None,
-        "reduce": None,
-        "bp_finalize": B * ((8 * 4 + 8) * Np + (56 + 16) / 2 * Np),  # C = 4 partials in, image out, epilogue
-    }
-    ms_total, n_launch = prof[top]
-    avg_ms = ms_total / max(n_launch, 1)
     peak, peak_kind = _peaks()
-    roof = None
-    # R and R^T compute their weights on chip: the work is one FMA per weight and channel, against the
-    # FP32 rate of the SMs (no measured figure for it; derived from unit counts and the max SM clock)
     nnz = joseph_weight_count(g)
-    alg_flops = {"backproject": B * 2 * 2 * nnz, "project": B * 2 * 2 * nnz}
     n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
     fp32_peak = n_sm * 128 * 2 * (clocks.get("sm_max_mhz") or 2070.0) * 1e6 / 1e12
-    hbm = None
-    if alg_bytes.get(top):
-        gbs = alg_bytes[top] / (avg_ms / 1e3) / 1e9
-        hbm = {"achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak, "peak_kind": peak_kind,
-               "algorithmic_bytes_per_launch": alg_bytes[top]}
-    if alg_flops.get(top):
-        tf = alg_flops[top] / (avg_ms / 1e3) / 1e12
-        roof = {"kernel": top, "bound": "alu", "achieved": tf, "peak": fp32_peak, "unit": "TFLOP/s",
-                "frac": tf / fp32_peak,
-                "traffic": SWEEP_TRAFFIC_B8[0] if (top == "backproject" and B == 8
-                                                    and st0["bp_view_groups"] == SWEEP_TRAFFIC_B8[1]) else None,
-                "peak_kind": f"derived: {n_sm} SMs x 128 FP32 lanes x 2 flop x max SM clock",
-                "avg_launch_ms": avg_ms, "algorithmic_flops_per_launch": alg_flops[top],
-                "weights_per_slice_channel": nnz, "hbm": hbm,
-                "limiter": SWEEP_LIMITER if top == "backproject" else None}
-    elif hbm is not None:
-        roof = dict(kernel=top, bound="hbm", traffic=None, avg_launch_ms=avg_ms, **hbm)
-    phases = {p: {"ms_per_iter": prof[p][0] / 10, "launches_per_iter": prof[p][1] / 10} for p in prof}
+
+    def kernel_roof(name, launches_per_iter):
+        ms_total, n_launch = prof[name]
+        avg_ms = ms_total / max(n_launch, 1)
+        tf = B * 2 * 2 * nnz / (avg_ms / 1e3) / 1e12
+        # algorithmic bytes: R reads the image once and writes the sinogram (both bases, FP32); R^T reads
+        # the sinogram and writes the image
+        nbytes = B * 8 * (M + Np)
+        gbs = nbytes / (avg_ms / 1e3) / 1e9
+        return avg_ms, tf, gbs, nbytes
+
+    bp_ms, bp_tf, bp_gbs, bp_bytes = kernel_roof("backproject", 2)
+    pr_ms, pr_tf, pr_gbs, pr_bytes = kernel_roof("project", 1)
+    cfg.update({"project_tflops": pr_tf, "project_tflops_frac": pr_tf / fp32_peak, "project_hbm_gbs": pr_gbs,
+                "project_hbm_frac": pr_gbs / peak, "backproject_hbm_frac": bp_gbs / peak})
+    traffic = SWEEP_TRAFFIC.get((B, st0["bp_view_groups"], st0["bp_tile"], st0["bp_cluster"]))
+    roof = {"kernel": "backproject" if top == "backproject" else top, "bound": "alu", "achieved": bp_tf,
+            "peak": fp32_peak, "unit": "TFLOP/s", "frac": bp_tf / fp32_peak,
+            "traffic": traffic, "traffic_source": "stored ncu capture of this kernel and launch shape "
+                                                  "(profiles/k_bp_sweep_512x720x1024.txt)" if traffic else None,
+            "peak_kind": f"derived: {n_sm} SMs x 128 FP32 lanes x 2 flop x max SM clock",
+            "avg_launch_ms": bp_ms, "algorithmic_flops_per_launch": B * 4 * nnz,
+            "algorithmic_bytes_per_launch": bp_bytes, "hbm_achieved_gbs": bp_gbs, "hbm_peak_gbs": peak,
+            "hbm_frac": bp_gbs / peak, "hbm_peak_kind": peak_kind}
     # the HBM-bound phases (data read and written once per iteration; 8 slices exceed L2): the four
     # element-wise kernels of an iteration (b = a + u^a - R x: 32 B/ray; x, R x += alpha p, q: 24 B/pixel
     # + 24 B/ray; y, z, u^y, u^z of Eq. 9-11 with x: 104 B/pixel; the dual rescale moves nothing when
-    # rho stays) and the two backprojector finalize passes (C partial images of 8 B, plus 64 B/pixel of
+    # rho stays) and the two backprojector finalize passes (partial images of 8 B, plus 64 B/pixel of
     # epilogue images for r0 and 16 B/pixel for A p)
-    C = st0["bp_view_groups"]
-    hbm_phase_bytes = {"update": B * (56 * M + 128 * Np), "bp_finalize": B * ((16 * C + 80) * Np)}
-    hbm_phases = {}
-    for p_, nbytes in hbm_phase_bytes.items():
+    parts = 1 if st0["bp_cluster"] else st0["bp_view_groups"]
+    for p_, nbytes in (("update", B * (56 * M + 128 * Np)), ("bp_finalize", B * ((16 * parts + 80) * Np))):
         ms = prof[p_][0] / 10
-        gbs = nbytes / (ms / 1e3) / 1e9
-        hbm_phases[p_] = {"algorithmic_bytes_per_iter": nbytes, "ms_per_iter": ms, "achieved_gbs": gbs,
-                          "peak_gbs": peak, "frac": gbs / peak}
+        cfg[f"{p_}_hbm_frac"] = nbytes / (ms / 1e3) / 1e9 / peak
 
-    if rank == 0:
-        line = {
-            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": "fan beam 512x512, 720 views x 1024 bins, 40 objects, I0 2e5, "
-                                   "UDM1-PCG1 x 100 iterations + initial image, B slices batched per launch",
-                       "batch_per_gpu": B, "l2": "flushed between steps (512 MB write)", "storage": args.storage,
-                       "bp_view_groups": st0["bp_view_groups"],
-                       "plain_slices_per_s": (ws * B / (plain_ms / 1e3)) if plain_ms else None,
-                       "batched_over_plain": (value / (ws * B / (plain_ms / 1e3))) if plain_ms else None,
-                       "plain_graph_autotuned_slices_per_s": (ws * B / (plain_best_ms / 1e3)) if plain_best_ms
-                       else None,
-                       "plain": "single-slice solvers one after another; eager launches, occupancy view groups",
-                       "pe_gate": gate, "phases": phases, "hbm_phases": hbm_phases,
-                       "scheme_comparison": comparison},
-            "clocks": clocks,
-            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-                    "steps": e2e_steps},
-            "gpu_launches": int(launches),
-            "roofline": roof,
-        }
-        if ws == 1 and not args.no_cpu_baseline:
+    # ---- batching on other workloads: slice-size scan, and the 64 uneven slices ----
+    if extras:
+        try:
+            cfg.update(size_scan(args, stream, flush))
+        except Exception as exc:
+            cfg["size_scan_error"] = f"{type(exc).__name__}: {exc}"[:90]
+        if args.uneven_slices:
             try:
-                line["cpu_baseline"] = cpu_baseline()
-            except Exception as exc:  # the oracle leg is a reported baseline, not the measurement
-                line["cpu_baseline"] = {"error": f"{type(exc).__name__}: {exc}"}
-        print(json.dumps(line), flush=True)
-    if ws > 1:
-        torch.distributed.destroy_process_group()
+                cfg.update(uneven_leg(args.uneven_slices, stream))
+            except Exception as exc:
+                cfg["uneven_error"] = f"{type(exc).__name__}: {exc}"[:90]
+
+    # ---- the paper's comparison (Sec. 4): time to the same PE error, new splitting vs LM x CG ----
+    if gold is not None and not args.no_comparison:
+        try:
+            cfg.update(scheme_comparison(geo, spec, cases, dev_data, truths, gold, B, stream))
+        except Exception as exc:  # an optional measurement must not cost the bench line
+            cfg["comparison_error"] = f"{type(exc).__name__}: {exc}"[:90]
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32" if args.storage == "f32" else args.storage,
+        "data": "synthetic", "config": cfg, "clocks": clocks,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                "steps": e2e_steps},
+        "gpu_launches": int(launches),
+        "roofline": roof,
+    }
+    if ws == 1 and not args.no_cpu_baseline:
+        try:
+            line["cpu_baseline"] = cpu_baseline()
+        except Exception as exc:  # the oracle leg is a reported baseline, not the measurement
+            line["cpu_baseline"] = {"error": f"{type(exc).__name__}: {exc}"}
+    print(json.dumps(line), flush=True)
     return 0
+
+
+def size_scan(args, stream, flush):
+    """Batched vs the plain single-slice loop for 8 fan slices at smaller sizes (per ADMM iteration after
+    the initial image, device time): where batching pays beyond launch overheads."""
+    import torch
+
+    from paper_1905_00934_gb300 import Geometry, Solver, Spectra
+    from synth.workloads import BAGGAGE_KAPPA, quick_fan_case
+
+    dev = torch.device("cuda", torch.cuda.current_device())
+    out = {}
+    for n, v, nb in ((128, 180, 256), (256, 360, 512)):
+        cases = [quick_fan_case(s, n, v, nb) for s in range(8)]
+        spec = Spectra.from_tables(cases[0]["spectra"])
+        geo = [Geometry(c["geom"]) for c in cases]
+        data = [[torch.tensor(np.ascontiguousarray(c[k]), dtype=torch.float32, device=dev)
+                 for k in ("m_h", "m_l", "w_h", "w_l")] for c in cases]
+
+        def per_iter(solvers, iters=10):
+            for s1 in solvers:
+                s1.reconstruct(0)
+                s1.step(2)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for s1 in solvers:
+                s1.step(iters)
+            e1.record(stream)
+            e1.synchronize()
+            return e0.elapsed_time(e1) / iters
+
+        bt = Solver(geo, spec, kappa=BAGGAGE_KAPPA)
+        for b in range(8):
+            bt.set_data(b, *data[b])
+        t_b = per_iter([bt])
+        singles = []
+        for b in range(8):
+            s1 = Solver([geo[b]], spec, kappa=BAGGAGE_KAPPA, **PLAIN)
+            s1.set_data(0, *data[b])
+            singles.append(s1)
+        t_p = per_iter(singles)
+        out[f"scan{n}_batched_over_plain"] = t_p / t_b
+        out[f"scan{n}_batched_ms_per_iter"] = t_b
+    return out
+
+
+def uneven_leg(n_slices, stream):
+    """The uneven-batch workload (seeded 256..1024 px, 360..1440 views, 512..2048 bins): one batched
+    solver (graph, autotuned backprojector) against single-slice solvers in turn, plain (eager,
+    occupancy view groups) and with graph and autotuner; device ms per ADMM iteration after the
+    initial image."""
+    import torch
+
+    from paper_1905_00934_gb300 import Geometry, Solver, Spectra
+    from synth.workloads import BAGGAGE_KAPPA, quick_fan_case, uneven_batch_shapes
+    from concurrent.futures import ThreadPoolExecutor
+
+    dev = torch.device("cuda", torch.cuda.current_device())
+    shapes = uneven_batch_shapes(n_slices)
+    with ThreadPoolExecutor(max_workers=16) as ex:
+        cases = list(ex.map(lambda b: quick_fan_case(b, *shapes[b]), range(len(shapes))))
+    spec = Spectra.from_tables(cases[0]["spectra"])
+    geo = [Geometry(c["geom"]) for c in cases]
+    data = [[torch.tensor(np.ascontiguousarray(c[k]), dtype=torch.float32, device=dev)
+             for k in ("m_h", "m_l", "w_h", "w_l")] for c in cases]
+    del cases
+    iters = 5
+
+    def timed(make_solvers):
+        solvers = make_solvers()
+        for s1 in solvers:
+            s1.reconstruct(0)
+            s1.step(1)  # graph capture outside the timing
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for s1 in solvers:
+            s1.step(iters)
+        e1.record(stream)
+        e1.synchronize()
+        del solvers
+        return e0.elapsed_time(e1) / iters
+
+    def batched():
+        s = Solver(geo, spec, kappa=BAGGAGE_KAPPA)
+        for b in range(len(geo)):
+            s.set_data(b, *data[b])
+        return [s]
+
+    def singles(params):
+        def make():
+            out = []
+            for b in range(len(geo)):
+                s1 = Solver([geo[b]], spec, kappa=BAGGAGE_KAPPA, **params)
+                s1.set_data(0, *data[b])
+                out.append(s1)
+            return out
+        return make
+
+    t_b = timed(batched)
+    t_p = timed(singles(PLAIN))
+    t_g = timed(singles({"bp_tile": 32, "bp_cluster": -1}))
+    return {"uneven_slices": len(geo), "uneven_batched_ms_per_iter": t_b, "uneven_plain_ms_per_iter": t_p,
+            "uneven_plain_graph_autotuned_ms_per_iter": t_g, "uneven_batched_over_plain": t_p / t_b,
+            "uneven_batched_over_plain_graph_autotuned": t_g / t_b}
+
+
+def scheme_comparison(geo, spec, cases, dev_data, truths, gold, B, stream):
+    """Time to the same PE error (slice 0's xi_p, checked every 5 iterations, against the oracle's value
+    after the workload's iterations + 0.5 dB, up to twice the workload's iterations) for UDM1-PCG1 and
+    the old splitting LM1 x CG1 on the same slices; and the one-pass CDM-FBP baseline."""
+    import torch
+
+    from paper_1905_00934_gb300 import Solver, cdm_fbp, dect
+    from synth.workloads import BAGGAGE_KAPPA
+
+    target = gold["xi_p"][ITERS] + 0.5
+    out = {"cmp_target_xi_p_db": target}
+    for name, scheme in (("udm", dect.SCHEME_UDM_PCG), ("lmcg", dect.SCHEME_LM_CG)):
+        s2 = Solver(geo, spec, kappa=BAGGAGE_KAPPA, scheme=scheme)
+        for b in range(B):
+            s2.set_data(b, *dev_data[b])
+            s2.set_truth(b, truths[b])
+        s2.reconstruct(0)
+        s2.step(5)  # graph capture outside the timing
+        s2.reconstruct(0)
+        torch.cuda.synchronize()
+        t_ms, it, hit, xi_p = 0.0, 0, None, None
+        while it < 2 * ITERS:
+            c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            c0.record(stream)
+            s2.step(5)
+            c1.record(stream)
+            c1.synchronize()
+            t_ms += c0.elapsed_time(c1)
+            it += 5
+            xi_p = s2.stats(0)["xi_db"][1]
+            if xi_p <= target:
+                hit = it
+                break
+        out[f"cmp_{name}_iters_to_target"] = hit
+        out[f"cmp_{name}_ms_to_target"] = t_ms if hit else None
+        out[f"cmp_{name}_ms_per_iter"] = t_ms / it
+        out[f"cmp_{name}_xi_p_db_at_stop"] = xi_p
+        del s2
+    cdm_fbp(geo[0], spec, *dev_data[0][:4], iters=CDM_ITERS)  # one-time per-geometry tables
+    c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    c0.record(stream)
+    xs = [cdm_fbp(geo[b], spec, *dev_data[b][:4], iters=CDM_ITERS) for b in range(B)]
+    c1.record(stream)
+    c1.synchronize()
+    x0 = xs[0].cpu().numpy().astype(np.float64)
+    xi = [float(20.0 * np.log10(np.linalg.norm(x0[k] - t) / np.linalg.norm(t)))
+          for k, t in enumerate((cases[0]["truth_c"], cases[0]["truth_p"]))]
+    out.update({"cmp_cdm_fbp_ms_per_slice": c0.elapsed_time(c1) / B, "cmp_cdm_fbp_xi_c_db": xi[0],
+                "cmp_cdm_fbp_xi_p_db": xi[1]})
+    gold_cdm = _golden(GOLDEN_CDM_FBP)
+    if gold_cdm is not None and gold_cdm.get("decomposition_iterations") == CDM_ITERS:
+        out["cmp_cdm_fbp_oracle_xi_p_db"] = gold_cdm["xi_p"]
+    return out
 
 
 def run_study(args):
@@ -662,6 +824,10 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-comparison", action="store_true",
                     help="skip the time-to-target comparison with the LM x CG splitting")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the plain forms, the 16-bit arms, the slice-size scan and the uneven batch")
+    ap.add_argument("--uneven-slices", type=int, default=64,
+                    help="slices of the uneven-batch leg of the bench line (0 skips it)")
     ap.add_argument("--profile-run", type=int, default=0, metavar="ITERS",
                     help="set up the workload, run one untimed reconstruction of ITERS iterations and exit "
                          "(for profiler captures; prints no bench line)")

@@ -306,6 +306,16 @@ typedef struct {
                                     16-bit storage R x carries the storage's rounding), reported by
                                     dect_admm_stats. One projection and one f-evaluation per ray each time,
                                     outside Table 1's counts. 0 (default): never. */
+    int32_t bp_tile;             /* backprojector tile side in pixels, 32 or 64 (its CTA's warps take bands of
+                                    32 columns or rows of the tile); 0 (default) = chosen by the autotuner
+                                    with bp_view_groups (timed on this batch; with bp_view_groups fixed, the
+                                    two sides are timed at that count; with -1, 64). The side does not change
+                                    results (every pixel receives the same contributions in the same order). */
+    int32_t bp_cluster;          /* the backprojector's view groups of a tile as one thread-block cluster that
+                                    adds their accumulators on chip (distributed shared memory, in rank order)
+                                    into one partial image, instead of C partial images through L2 / DRAM:
+                                    1 on (2 <= view groups <= 16), -1 off, 0 (default) timed by the autotuner
+                                    against the plain form. Both forms give the same bits. */
 } dect_params;
 
 /* Fills *p with the paper's values and the defaults above. */
@@ -364,6 +374,8 @@ typedef struct {
     int32_t bp_view_groups;      /* backprojector view groups per tile in use (fixed or autotuned) */
     double objective;            /* Eq. 4 after iteration objective_iteration (NaN if never evaluated) */
     int32_t objective_iteration; /* see dect_params.objective_every; -1 if never evaluated */
+    int32_t bp_tile;             /* backprojector tile side in use (0 for float64 storage) */
+    int32_t bp_cluster;          /* 1 if the backprojector's view groups reduce on chip (see bp_cluster) */
 } dect_stats;
 dect_status dect_admm_stats(dect_admm* a, int32_t slice, dect_stats* out, void* stream);
 

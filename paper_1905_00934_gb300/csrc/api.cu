@@ -20,8 +20,6 @@ void set_error(const std::string& m) { g_err = m; }
 
 void project_single(const SliceDesc& sd, const float* img, int nch, float2* scratch, float4* tx, float4* ty,
                     float* out, cudaStream_t st);
-void backproject_single(const SliceDesc& sd, const float* sino, int nch, float2* packed, float* out,
-                        cudaStream_t st);
 void launch_identity_precond(const SliceDesc* d, const BlockMap& rows, int nrows, const float2* r, float2* s,
                              double* partial, cudaStream_t st);
 }  // namespace dect
@@ -144,6 +142,13 @@ extern "C" dect_status dect_sync(void* stream) {
 
 static bool finite_pos(double v) { return std::isfinite(v) && v > 0.0; }
 
+static bool same_geometry(const dect_geom_desc& a, const dect_geom_desc& b) {
+    return a.kind == b.kind && a.nx == b.nx && a.ny == b.ny && a.n_views == b.n_views && a.n_bins == b.n_bins &&
+           a.pixel_cm == b.pixel_cm && a.angle0_rad == b.angle0_rad && a.angle_span_rad == b.angle_span_rad &&
+           a.bin_pitch_cm == b.bin_pitch_cm && a.bin_offset_cm == b.bin_offset_cm && a.sod_cm == b.sod_cm &&
+           a.sdd_cm == b.sdd_cm;
+}
+
 // Launch errors are read back with cudaGetLastError; clear any error left by an unrelated earlier
 // runtime call so that it is not reported against this call.
 static void clear_stale_error() { (void)cudaGetLastError(); }
@@ -208,8 +213,9 @@ static dect_status geom_workspace(dect_geom* g) {
     CUDA_TRY(dalloc(&g->ws_tx, (size_t)d.nx * (d.ny + 3)));
     CUDA_TRY(dalloc(&g->ws_ty, (size_t)d.ny * (d.nx + 3)));
     CUDA_TRY(dalloc(&g->ws_sino, (size_t)g->n_rays()));
-    const int tiles = sweep_tiles(d.nx, d.ny);
-    g->ws_C = sweep_groups(tiles);
+    CUDA_TRY(sweep_init_attributes());  // per device: the geometry's device is the current one
+    const int tiles = sweep_tiles(d.nx, d.ny, kSweepTileDefault);
+    g->ws_C = sweep_groups(tiles, kSweepTileDefault);
     CUDA_TRY(dalloc(&g->ws_partial, (size_t)g->ws_C * g->n_pix()));
     CUDA_TRY(dalloc(&g->ws_desc, 1));
     CUDA_TRY(dalloc(&g->ws_maps, 4));
@@ -263,8 +269,8 @@ extern "C" dect_status dect_backproject(dect_geom* g, int32_t nch, int32_t dtype
     }
     dect_status st = geom_workspace(g);
     if (st != DECT_OK) return st;
-    backproject_single(g->single(), g->ws_desc, g->ws_maps, g->ws_C, (const float*)sino, nch, g->ws_sino,
-                       g->ws_partial, (float*)x, as_stream(stream));
+    backproject_single(g->single(), g->ws_desc, g->ws_maps, g->ws_C, kSweepTileDefault, (const float*)sino, nch,
+                       g->ws_sino, g->ws_partial, (float*)x, as_stream(stream));
     CUDA_TRY(cudaGetLastError());
     return DECT_OK;
 }
@@ -511,6 +517,8 @@ extern "C" void dect_params_default(dect_params* p) {
     p->init = DECT_INIT_PCG;
     p->udm_f64 = 0;
     p->objective_every = 0;
+    p->bp_tile = 0;
+    p->bp_cluster = 0;
 }
 
 struct MapBuf {
@@ -529,6 +537,10 @@ struct dect_admm {
     SliceDesc* ds = nullptr;
     MapBuf rays, pix, tx, ty, rows, cols, sweep, ptile;  // ptile: the projector's (views x bins) tiles
     int sweep_C = 1;                 // CTA groups (partial images) per backprojector tile
+    int sweep_tile = kSweepTileDefault;  // backprojector tile side (32 or 64; does not change results)
+    bool sweep_cluster = false;      // the view groups of a tile reduce on chip into one partial image
+    std::vector<int> cluster_cands;  // cluster forms the autotuner may time (0 off, 1 on)
+    int bp_parts() const { return sweep_cluster ? 1 : sweep_C; }  // partial images the finalize pass reads
     int sweep_groups_in_use = 1;     // view groups per tile (sweep_C CTAs of the kernel's groups each)
     float2* bp_partial = nullptr;    // [sweep_C][n_img] partial images of the backprojector
     int64_t n_img = 0, n_sino = 0, n_tx = 0, n_ty = 0, n_fft = 0, n_h = 0, n_stage = 0;
@@ -669,10 +681,10 @@ static void enq_pcg(dect_admm* A, int n, bool with_grad, const float* H, cudaStr
     launch_sino_resid(A->ds, A->rays.map(B), A->rays.total, A->a, A->ua, A->Rx, A->q, A->prec, st);
     pe(A, DECT_PHASE_UPDATE, 1, st);
     pb(A, st);
-    launch_bp_sweep(A->ds, A->sweep.map(B), A->sweep.total, A->sweep_C, A->q, A->bp_partial, A->n_img, A->prec, st);
+    launch_bp_sweep(A->ds, A->sweep.map(B), A->sweep.total, A->sweep_C, A->sweep_tile, A->sweep_cluster, A->q, A->bp_partial, A->n_img, A->prec, st);
     pe(A, DECT_PHASE_BACKPROJECT, 1, st);
     pb(A, st);
-    launch_bp_finalize(with_grad ? BP_R0 : BP_R0_NOGRAD, A->ds, A->pix.map(B), A->pix.total, A->sweep_C,
+    launch_bp_finalize(with_grad ? BP_R0 : BP_R0_NOGRAD, A->ds, A->pix.map(B), A->pix.total, A->bp_parts(),
                        A->bp_partial, A->n_img, A->r, ep, st);
     pe(A, DECT_PHASE_BP_FINALIZE, 1, st);
     if (A->counting) A->cRT += 2;
@@ -683,11 +695,11 @@ static void enq_pcg(dect_admm* A, int n, bool with_grad, const float* H, cudaStr
     for (int it = 0; it < n; ++it) {
         enq_project(A, A->p, A->q, st);
         pb(A, st);
-        launch_bp_sweep(A->ds, A->sweep.map(B), A->sweep.total, A->sweep_C, A->q, A->bp_partial, A->n_img, A->prec,
+        launch_bp_sweep(A->ds, A->sweep.map(B), A->sweep.total, A->sweep_C, A->sweep_tile, A->sweep_cluster, A->q, A->bp_partial, A->n_img, A->prec,
                         st);
         pe(A, DECT_PHASE_BACKPROJECT, 1, st);
         pb(A, st);
-        launch_bp_finalize(with_grad ? BP_AP : BP_AP_NOGRAD, A->ds, A->pix.map(B), A->pix.total, A->sweep_C,
+        launch_bp_finalize(with_grad ? BP_AP : BP_AP_NOGRAD, A->ds, A->pix.map(B), A->pix.total, A->bp_parts(),
                            A->bp_partial, A->n_img, A->Ap, ep, st);
         pe(A, DECT_PHASE_BP_FINALIZE, 1, st);
         if (A->counting) A->cRT += 2;
@@ -728,11 +740,12 @@ static void enq_lm_step(dect_admm* A, int b, cudaStream_t st) {
                    A->lm_s0, A->lm_Rd, st);
     pe(A, DECT_PHASE_UDM, 1, st);
     pb(A, st);
-    launch_bp_sweep1(A->ds, A->sweep.map(B), A->sweep.total, A->sweep_C, A->lm_e, nullptr, nullptr, A->bp_partial1,
+    launch_bp_sweep1(A->ds, A->sweep.map(B), A->sweep.total, A->sweep_C, A->sweep_tile, A->sweep_cluster, A->lm_e,
+                     nullptr, nullptr, A->bp_partial1,
                      A->n_img, st);
     pe(A, DECT_PHASE_BACKPROJECT, 1, st);
     pb(A, st);
-    launch_lm_grad(A->ds, pix, A->pix.total, A->sweep_C, A->bp_partial1, A->n_img, b, A->sc, ep, A->lm_r, A->lm_p,
+    launch_lm_grad(A->ds, pix, A->pix.total, A->bp_parts(), A->bp_partial1, A->n_img, b, A->sc, ep, A->lm_r, A->lm_p,
                    A->lm_d, A->part_lm_pix, st);
     pe(A, DECT_PHASE_BP_FINALIZE, 1, st);
     pb(A, st);
@@ -748,11 +761,12 @@ static void enq_lm_step(dect_admm* A, int b, cudaStream_t st) {
         launch_project1(A->ds, A->ptile.map(B), A->ptile.total, A->tx1, A->ty1, A->lm_q, st);
         pe(A, DECT_PHASE_PROJECT, 1, st);
         pb(A, st);
-        launch_bp_sweep1(A->ds, A->sweep.map(B), A->sweep.total, A->sweep_C, A->lm_q, A->lm_g, A->lm_scale,
+        launch_bp_sweep1(A->ds, A->sweep.map(B), A->sweep.total, A->sweep_C, A->sweep_tile, A->sweep_cluster, A->lm_q,
+                         A->lm_g, A->lm_scale,
                          A->bp_partial1, A->n_img, st);
         pe(A, DECT_PHASE_BACKPROJECT, 1, st);
         pb(A, st);
-        launch_lm_ap(A->ds, pix, A->pix.total, A->sweep_C, A->bp_partial1, A->n_img, b, A->sc, A->lm_p, A->lm_Ap,
+        launch_lm_ap(A->ds, pix, A->pix.total, A->bp_parts(), A->bp_partial1, A->n_img, b, A->sc, A->lm_p, A->lm_Ap,
                      A->part_lm_pix, st);
         pe(A, DECT_PHASE_BP_FINALIZE, 1, st);
         pb(A, st);
@@ -1105,58 +1119,75 @@ static dect_status enq_initialize(dect_admm* A, cudaStream_t st) {
 
 // ---- creation ------------------------------------------------------------------------------------
 
-// Sweep block map for C CTA groups per tile (prefix over slices)
-static void sweep_prefix(const dect_admm* A, int C, std::vector<int>& h) {
+// Sweep block map for C CTA groups per TILE x TILE tile (prefix over slices)
+static void sweep_prefix(const dect_admm* A, int C, int tile, std::vector<int>& h) {
     h.assign(1, 0);
-    for (int b = 0; b < A->B; ++b) h.push_back(h.back() + sweep_tiles(A->hs[b].g.nx, A->hs[b].g.ny) * C);
+    for (int b = 0; b < A->B; ++b) h.push_back(h.back() + sweep_tiles(A->hs[b].g.nx, A->hs[b].g.ny, tile) * C);
 }
 
-// Times the backprojector sweep on this batch for each candidate C (on a zero sinogram; the work does
-// not depend on the values), keeps the fastest (a smaller C unless a larger one is 1% faster) and
-// shrinks the partial-image buffer to it. bp_partial is allocated for the largest candidate.
-static cudaError_t autotune_sweep(dect_admm* A, const std::vector<int>& cands) {
+// Times the backprojector sweep on this batch for each candidate (tile side, C) (on a zero sinogram; the
+// work does not depend on the values), keeps the fastest (fewer view groups unless more are 1% faster)
+// and shrinks the partial-image buffer to it. bp_partial is allocated for the largest candidate C.
+// The tile side does not change results; C fixes the order of a pixel's partial sums.
+static cudaError_t autotune_sweep(dect_admm* A, const std::vector<int>& cands, const std::vector<int>& tiles) {
     cudaStream_t st = A->cap;
     cudaError_t e = cudaMemsetAsync(A->q, 0, sino_bytes(A->prec) * (size_t)A->n_sino, st);
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (e == cudaSuccess) e = cudaEventCreate(&e0);
     if (e == cudaSuccess) e = cudaEventCreate(&e1);
-    int best = cands[0];
+    int best = cands[0], best_tile = tiles[0];
+    bool best_cluster = false;
     float best_ms = 0.f;
+    bool first = true;
     std::vector<int> h;
-    for (size_t k = 0; k < cands.size() && e == cudaSuccess; ++k) {
-        const int C = cands[k];
-        sweep_prefix(A, C, h);
-        e = cudaMemcpy(A->sweep.d, h.data(), sizeof(int) * h.size(), cudaMemcpyHostToDevice);
-        const BlockMap m{A->sweep.d, A->B};
-        for (int w = 0; w < 2 && e == cudaSuccess; ++w) {  // warm-up
-            launch_bp_sweep(A->ds, m, h.back(), C, A->q, A->bp_partial, A->n_img, A->prec, st);
-            e = cudaGetLastError();
-        }
-        if (e == cudaSuccess) e = cudaEventRecord(e0, st);
-        for (int r = 0; r < 3 && e == cudaSuccess; ++r) {
-            launch_bp_sweep(A->ds, m, h.back(), C, A->q, A->bp_partial, A->n_img, A->prec, st);
-            e = cudaGetLastError();
-        }
-        if (e == cudaSuccess) e = cudaEventRecord(e1, st);
-        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
-        float ms = 0.f;
-        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
-        if (e == cudaSuccess && (k == 0 || ms < 0.99f * best_ms || (ms <= best_ms && C < best))) {
-            best = C;
-            best_ms = ms;
-        }
-    }
+    for (int tile : tiles)
+        for (size_t k = 0; k < cands.size() && e == cudaSuccess; ++k)
+            for (int cl : A->cluster_cands) {
+                if (e != cudaSuccess) break;
+                const int C = cands[k];
+                const bool cluster = cl == 1;
+                if (cluster && (C < 2 || C > 16)) continue;
+                sweep_prefix(A, C, tile, h);
+                e = cudaMemcpy(A->sweep.d, h.data(), sizeof(int) * h.size(), cudaMemcpyHostToDevice);
+                const BlockMap m{A->sweep.d, A->B};
+                // a cluster shape the device cannot schedule is reported at launch: skip that candidate
+                launch_bp_sweep(A->ds, m, h.back(), C, tile, cluster, A->q, A->bp_partial, A->n_img, A->prec, st);
+                if (cluster && cudaGetLastError() != cudaSuccess) continue;
+                for (int w = 0; w < 1 && e == cudaSuccess; ++w) {  // warm-up
+                    launch_bp_sweep(A->ds, m, h.back(), C, tile, cluster, A->q, A->bp_partial, A->n_img, A->prec, st);
+                    e = cudaGetLastError();
+                }
+                if (e == cudaSuccess) e = cudaEventRecord(e0, st);
+                for (int r = 0; r < 3 && e == cudaSuccess; ++r) {
+                    launch_bp_sweep(A->ds, m, h.back(), C, tile, cluster, A->q, A->bp_partial, A->n_img, A->prec, st);
+                    e = cudaGetLastError();
+                }
+                if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+                if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+                float ms = 0.f;
+                if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+                if (e == cudaSuccess && (first || ms < 0.99f * best_ms || (ms <= best_ms && C < best))) {
+                    best = C;
+                    best_tile = tile;
+                    best_cluster = cluster;
+                    best_ms = ms;
+                    first = false;
+                }
+            }
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
     if (e != cudaSuccess) return e;
     A->sweep_C = best;
-    sweep_prefix(A, best, A->sweep.h);
+    A->sweep_tile = best_tile;
+    A->sweep_cluster = best_cluster;
+    sweep_prefix(A, best, best_tile, A->sweep.h);
     A->sweep.total = A->sweep.h.back();
     e = cudaMemcpy(A->sweep.d, A->sweep.h.data(), sizeof(int) * A->sweep.h.size(), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return e;
     cudaFree(A->bp_partial);
     A->bp_partial = nullptr;
-    return dalloc(&A->bp_partial, (size_t)best * A->n_img);
+    e = dalloc(&A->bp_partial, (size_t)A->bp_parts() * A->n_img);
+    return e;
 }
 
 // The float64 preconditioner responses: the point response of R^T R through the float64 projector
@@ -1215,8 +1246,8 @@ static dect_status compute_responses(dect_admm* A) {
         dect_status ws = geom_workspace(g);
         if (ws != DECT_OK) return ws;
         project_single(sd, A->stage, 2, g->ws_img, g->ws_tx, g->ws_ty, A->stage + 2 * np, st);
-        backproject_single(sd, g->ws_desc, g->ws_maps, g->ws_C, A->stage + 2 * np, 2, g->ws_sino, g->ws_partial,
-                           A->stage, st);
+        backproject_single(sd, g->ws_desc, g->ws_maps, g->ws_C, kSweepTileDefault, A->stage + 2 * np, 2, g->ws_sino,
+                           g->ws_partial, A->stage, st);
         launch_interleave(A->stage, np, A->r + sd.img_off, st);
         // one-slice descriptor and column map
         SliceDesc one_slice = sd;
@@ -1272,6 +1303,10 @@ extern "C" dect_status dect_admm_create(dect_geom* const* geoms, int32_t B, cons
         DECT_FAIL(DECT_EUNSUPPORTED, "dect_admm_create: the LM x CG scheme runs with float32 storage only");
     if (P->bp_view_groups < -1 || P->bp_view_groups > 16)
         DECT_FAIL(DECT_EINVAL, "dect_admm_create: bp_view_groups must be in [-1, 16]");
+    if (P->bp_tile != 0 && P->bp_tile != 32 && P->bp_tile != 64)
+        DECT_FAIL(DECT_EINVAL, "dect_admm_create: bp_tile must be 0 (autotuned), 32 or 64");
+    if (P->bp_cluster < -1 || P->bp_cluster > 1)
+        DECT_FAIL(DECT_EINVAL, "dect_admm_create: bp_cluster must be -1 (off), 0 (autotuned) or 1 (on)");
     if (P->init != DECT_INIT_PCG && P->init != DECT_INIT_CDM_FBP)
         DECT_FAIL(DECT_EINVAL, "dect_admm_create: init must be DECT_INIT_PCG or DECT_INIT_CDM_FBP");
     if (P->init == DECT_INIT_CDM_FBP)
@@ -1310,25 +1345,35 @@ extern "C" dect_status dect_admm_create(dect_geom* const* geoms, int32_t B, cons
     for (auto* m : {&A->rays, &A->pix, &A->tx, &A->ty, &A->rows, &A->cols, &A->sweep, &A->cols64, &A->ptile})
         m->h.assign(1, 0);
     std::vector<int> tune;  // candidate CTA groups per tile when autotuning (first = the occupancy choice)
+    std::vector<int> tune_tiles;  // candidate tile sides when autotuning
     {
+        cudaError_t ae = sweep_init_attributes();
+        if (ae != cudaSuccess) DECT_FAIL(DECT_ECUDA, std::string("dect_admm_create: ") + cudaGetErrorString(ae));
+        const int tile0 = P->bp_tile ? P->bp_tile : kSweepTileDefault;
+        if (P->bp_tile) tune_tiles.push_back(P->bp_tile);
+        else tune_tiles = {64, 32};
         int total = 0;
         int64_t pix = 0;
         for (int b = 0; b < B; ++b) {
-            total += sweep_tiles(geoms[b]->desc.nx, geoms[b]->desc.ny);
+            total += sweep_tiles(geoms[b]->desc.nx, geoms[b]->desc.ny, tile0);
             pix += geoms[b]->n_pix();
         }
+        A->sweep_tile = tile0;
+        if (P->bp_cluster == 0) A->cluster_cands = {0, 1};
+        else A->cluster_cands = {P->bp_cluster > 0 ? 1 : 0};
         if (P->storage == DECT_STORE_F64) {
             A->sweep_C = 1;  // the float64 path has its own backprojector; no sweep, no partial images
         } else if (P->bp_view_groups > 0) {
             A->sweep_C = sweep_ctas_for_groups(P->bp_view_groups);
+            tune.push_back(A->sweep_C);  // the tile sides and the cluster form may still be timed at this C
         } else if (P->bp_view_groups < 0) {
-            A->sweep_C = sweep_groups(total);  // occupancy choice, not timed
+            A->sweep_C = sweep_groups(total, tile0);  // occupancy choice, not timed
         } else {
             // candidates whose partial images fit in 1/16 of the free memory (and 4 GiB)
             size_t free_b = 0, total_b = 0;
             cudaMemGetInfo(&free_b, &total_b);
             const double budget = std::min(4.0 * (1 << 30), (double)free_b / 16.0);
-            const int first = sweep_groups(total);
+            const int first = sweep_groups(total, tile0);
             tune.push_back(first);
             for (int c : {4, 6, 8, 10, 12, 16})
                 if (c != first && (double)c * pix * sizeof(float2) <= budget) tune.push_back(c);
@@ -1340,6 +1385,14 @@ extern "C" dect_status dect_admm_create(dect_geom* const* geoms, int32_t B, cons
         const dect_geom* g = geoms[b];
         SliceDesc sd{};
         sd.g = g->dev();
+        // slices with the same geometry (every slice of one scan) read one shared ray table: the tables of
+        // identical descriptors are identical, and sharing keeps one copy in L2 for the whole batch
+        for (int b2 = 0; b2 < b; ++b2)
+            if (same_geometry(geoms[b2]->desc, g->desc)) {
+                sd.g.rays = geoms[b2]->rays;
+                sd.g.views = geoms[b2]->views;
+                break;
+            }
         const int nx = g->desc.nx, ny = g->desc.ny;
         const int64_t np = g->n_pix(), nr = g->n_rays();
         sd.img_off = A->n_img;
@@ -1369,7 +1422,7 @@ extern "C" dect_status dect_admm_create(dect_geom* const* geoms, int32_t B, cons
         A->pix.h.push_back(A->pix.h.back() + (int)((np + 255) / 256));
         A->tx.h.push_back(A->tx.h.back() + texture_x_blocks(nx, ny));
         A->ty.h.push_back(A->ty.h.back() + texture_y_blocks(nx, ny));
-        A->sweep.h.push_back(A->sweep.h.back() + sweep_tiles(nx, ny) * A->sweep_C);
+        A->sweep.h.push_back(A->sweep.h.back() + sweep_tiles(nx, ny, A->sweep_tile) * A->sweep_C);
         A->rows.h.push_back(A->rows.h.back() + ny);
         const int C = precond_cols_per_block(sd.py);
         A->cols.h.push_back(A->cols.h.back() + (sd.px + C - 1) / C);
@@ -1456,7 +1509,11 @@ extern "C" dect_status dect_admm_create(dect_geom* const* geoms, int32_t B, cons
         free_admm(A);
         return e == cudaErrorMemoryAllocation ? DECT_ENOMEM : DECT_ECUDA;
     }
-    if (tune.size() > 1) e = autotune_sweep(A, tune);
+    if (A->prec != PREC_F64 && !tune.empty() &&
+        (tune.size() > 1 || tune_tiles.size() > 1 || (A->cluster_cands.size() > 1 && tune[0] >= 2)))
+        e = autotune_sweep(A, tune, tune_tiles);
+    else if (A->prec != PREC_F64)
+        A->sweep_cluster = P->bp_cluster > 0 && A->sweep_C >= 2 && A->sweep_C <= 16;
     if (e != cudaSuccess) {
         dect::set_error(std::string("dect_admm_create (backprojector autotuning): ") + cudaGetErrorString(e));
         free_admm(A);
@@ -1468,7 +1525,7 @@ extern "C" dect_status dect_admm_create(dect_geom* const* geoms, int32_t B, cons
         e = cudaMemset(A->part_udm, 0, sizeof(double) * 4 * (size_t)A->rays.h.back());
         if (e == cudaSuccess) e = dalloc(&A->part_lm_pix, (size_t)A->pix.h.back());
         if (e == cudaSuccess) e = dalloc(&A->part_lm_ray, (size_t)A->rays.h.back());
-        if (e == cudaSuccess) e = dalloc(&A->bp_partial1, (size_t)A->sweep_C * A->n_img);
+        if (e == cudaSuccess) e = dalloc(&A->bp_partial1, (size_t)A->bp_parts() * A->n_img);
         if (e != cudaSuccess) {
             dect::set_error(std::string("dect_admm_create: ") + cudaGetErrorString(e));
             free_admm(A);
@@ -1916,5 +1973,7 @@ extern "C" dect_status dect_admm_stats(dect_admm* A, int32_t b, dect_stats* out,
     out->bp_view_groups = A->sweep_groups_in_use;
     out->objective = v.objective_iter >= 0 ? v.objective : NAN;
     out->objective_iteration = v.objective_iter;
+    out->bp_tile = A->prec == PREC_F64 ? 0 : A->sweep_tile;
+    out->bp_cluster = A->sweep_cluster ? 1 : 0;
     return DECT_OK;
 }

@@ -1,8 +1,8 @@
 // Column-sweep gathering backprojector R^T of the ADMM solver (Table 1's R^T, with the CG
 // epilogues of Eq. 12).
 //
-// A CTA owns a 32 x 32 pixel tile and a group of views; of its two warps one takes the rays
-// sampled once per column (axis 0), the other the rays sampled once per row (axis 1). For each
+// A CTA owns a pixel tile (32 x 32 or 64 x 64, see SweepShape) and a group of views; its warps take
+// the rays sampled once per column (axis 0) or once per row (axis 1) over bands of the tile. For each
 // view a warp stages its rays that can reach the tile (32 at a time) in shared memory, in bin
 // order, and walks them. For an axis-0 ray lane c evaluates the sample at column ti + c with the
 // same fixed-point integers as the forward projector and adds (1 - f) w s and f w s to the two rows
@@ -19,6 +19,7 @@
 // the same sample. The ray loop runs in blocks of kSwUnroll rays (the stage padded with null rays:
 // far position, zero weight): positions and weights of a block are computed before its
 // accumulator updates, and the next chunk's rays are fetched while the current one is processed.
+#include <cooperative_groups.h>
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
@@ -34,51 +35,77 @@
 
 namespace dect {
 
-constexpr int kSw = 32;           // tile side
-constexpr int kSwGroups = 1;      // view groups per CTA
-constexpr int kSwWarps = 2 * kSwGroups;  // one warp per view group and ray axis
-constexpr int kSwRows = kSw + 2;  // accumulator rows -1 .. 32 (the two halo rows are discarded)
+// A tile is TILE x TILE pixels (TILE = 32 or 64) and its CTA has 2 * TILE / 32 warps: the first
+// TILE / 32 take the rays sampled once per column (axis 0), each for a band of 32 columns x TILE
+// rows, the others the rays sampled once per row (axis 1), each for a band of TILE columns x 32 rows.
+// A taller band leaves fewer lanes idle on rays that clip a corner of it (a CPU model of the 512^2
+// fan workload: 72 % of a staged ray's lanes sample the band at 32 rows, 83 % at 64), at the price of
+// twice the accumulator per warp. Both shapes evaluate every sample once, in the same order per
+// pixel within a view group, and the autotuner of the solver picks one by timing.
 constexpr int kSwUnroll = 8;
+
+template <int TILE>
+struct SweepShape {
+    static constexpr int kBands = TILE / 32;      // bands per axis
+    static constexpr int kWarps = 2 * kBands;     // one warp per band and axis
+    static constexpr int kRows = TILE + 2;        // accumulator rows (across index -1 .. TILE; halo discarded)
+    static constexpr int kThreads = 32 * kWarps;
+};
+
+// shared-memory bytes of a CTA's accumulators (dynamic shared memory)
+template <int TILE, int NCH>
+constexpr size_t sweep_acc_bytes() {
+    return (size_t)SweepShape<TILE>::kWarps * SweepShape<TILE>::kRows * 32 * (NCH == 2 ? sizeof(float2) : sizeof(float));
+}
 
 // NCH = 2: sinogram S2 pairs {c, p}, float2 accumulators and partial images. NCH = 1: float sinogram,
 // float accumulators (half the shared-memory traffic), optionally multiplied per ray by rw[ray] and per
 // slice by scale[slice] as the rays are staged (the weighted R^T of a Gauss-Newton operator).
-template <class S2, int NCH>
-__global__ void __launch_bounds__(32 * kSwWarps) k_bp_sweep(const SliceDesc* __restrict__ dsl, BlockMap map, int C,
-                                                            const S2* __restrict__ sino,
-                                                            typename std::conditional<NCH == 2, float2, float>::type*
-                                                                __restrict__ partial,
-                                                            int64_t stride, const float* __restrict__ rw,
-                                                            const float* __restrict__ scale) {
+// CLUSTER: the C CTAs of a tile (consecutive blocks) form a thread-block cluster and add their
+// accumulators through distributed shared memory, in rank order, into one partial image (image 0);
+// the sum per pixel is the one the finalize pass forms from C partial images (0 + p_0 + p_1 + ...),
+// so both launch forms give the same bits, and only one image per tile goes through L2 and DRAM.
+template <class S2, int NCH, int TILE, bool CLUSTER = false>
+__global__ void __launch_bounds__(SweepShape<TILE>::kThreads) k_bp_sweep(
+    const SliceDesc* __restrict__ dsl, BlockMap map, int C, const S2* __restrict__ sino,
+    typename std::conditional<NCH == 2, float2, float>::type* __restrict__ partial, int64_t stride,
+    const float* __restrict__ rw, const float* __restrict__ scale) {
     using Acc = typename std::conditional<NCH == 2, float2, float>::type;
+    using Sh = SweepShape<TILE>;
     // [warp][across index + 1][lane]: [row][column] for axis 0, [column][row] for axis 1
-    __shared__ Acc acc[kSwWarps][kSwRows][kSw];
-    __shared__ int4 st_ray[kSwWarps][32];  // {position lo, position hi, slope, w s_c}
-    __shared__ float st_wp[kSwWarps][32];  // w s_p
+    extern __shared__ __align__(16) unsigned char sweep_smem[];
+    Acc(*acc)[Sh::kRows][32] = reinterpret_cast<Acc(*)[Sh::kRows][32]>(sweep_smem);
+    __shared__ int4 st_ray[Sh::kWarps][32];                 // {position lo, position hi, slope, w s_c}
+    __shared__ __align__(16) float st_wp[Sh::kWarps][32];   // w s_p
     int local;
     const int s = slice_of(map, blockIdx.x, local);
     const SliceDesc& d = dsl[s];
     const GeomDev& g = d.g;
     const int nx = g.nx, ny = g.ny;
     const int c = local % C, tile = local / C;
-    const int tiles_x = (nx + kSw - 1) / kSw;
-    const int ti = (tile % tiles_x) * kSw, tj = (tile / tiles_x) * kSw;
+    const int tiles_x = (nx + TILE - 1) / TILE;
+    const int ti = (tile % tiles_x) * TILE, tj = (tile / tiles_x) * TILE;
     const int w = threadIdx.x / 32, lane = threadIdx.x % 32;
-    const bool my_axis = w & 1;
-    for (int r = 0; r < kSwRows; ++r) acc[w][r][lane] = Acc{};
-    const int G = C * kSwGroups, grp = c * kSwGroups + (w >> 1);
-    // rays with a weight at the tile's in-image pixels pass within one pixel of their centres:
-    // columns ti .. ie, rows tj .. je, widened by one pixel (the rectangle stays inside the image's
-    // one-pixel margin, in front of a fan source)
-    const int ie = min(ti + kSw, nx) - 1, je = min(tj + kSw, ny) - 1;
-    const float xc = (0.5f * (float)(ti + ie) - g.cx) * g.pix, yc = (0.5f * (float)(tj + je) - g.cy) * g.pix;
-    const float hx = (0.5f * (float)(ie - ti) + 1.0f) * g.pix, hy = (0.5f * (float)(je - tj) + 1.0f) * g.pix;
+    const bool my_axis = w >= Sh::kBands;
+    const int band = w % Sh::kBands;
+    for (int r = 0; r < Sh::kRows; ++r) acc[w][r][lane] = Acc{};
+    const int G = C, grp = c;
+    // this warp's band: 32 sampled indices from bi (columns for axis 0, rows for axis 1) by the tile's
+    // TILE across indices from ba; rays with a weight at its in-image pixels pass within one pixel of
+    // their centres, so candidates come from the band's rectangle widened by one pixel (inside the
+    // image's one-pixel margin, in front of a fan source)
+    const int bi = (my_axis ? tj : ti) + 32 * band, ba = my_axis ? ti : tj;
+    const int n_along = my_axis ? ny : nx, n_across = my_axis ? nx : ny;
+    const int be = min(bi + 32, n_along) - 1, ae = min(ba + TILE, n_across) - 1;
+    const bool empty = bi >= n_along;  // a band past the image's last column / row (ragged tiles)
+    const int i0 = my_axis ? ba : bi, i1 = my_axis ? ae : be, j0 = my_axis ? bi : ba, j1 = my_axis ? be : ae;
+    const float xc = (0.5f * (float)(i0 + i1) - g.cx) * g.pix, yc = (0.5f * (float)(j0 + j1) - g.cy) * g.pix;
+    const float hx = (0.5f * (float)(i1 - i0) + 1.0f) * g.pix, hy = (0.5f * (float)(j1 - j0) + 1.0f) * g.pix;
     const S2* sn = sino + d.sino_off;
-    const int t0 = my_axis ? tj : ti, a0 = my_axis ? ti : tj;
-    const long long a0q = (long long)a0 << 30;
+    const long long a0q = (long long)ba << 30;
 
     // chunk cursor: view v, first bin k0 of the chunk, last candidate bin khi of the view
-    int v = grp, k0 = 0, khi = -1;
+    int v = empty ? g.nv : grp, k0 = 0, khi = -1;
     auto seek = [&](int vv) {
         for (v = vv; v < g.nv; v += G) {
             const float4 V = __ldg(g.views + v);
@@ -90,7 +117,7 @@ __global__ void __launch_bounds__(32 * kSwWarps) k_bp_sweep(const SliceDesc* __r
             }
         }
     };
-    seek(grp);
+    if (!empty) seek(grp);
     int4 P = make_int4(0, 0, 0, 0);
     float2 sv = make_float2(0.f, 0.f);
     bool have = false;
@@ -116,7 +143,7 @@ __global__ void __launch_bounds__(32 * kSwWarps) k_bp_sweep(const SliceDesc* __r
         const unsigned mask = __ballot_sync(0xffffffffu, mine);
         const int n = __popc(mask);
         if (mine) {
-            const long long q = ray_pos(P, t0) - a0q;
+            const long long q = ray_pos(P, bi) - a0q;
             const float wr = ray_w(P) * sscale;
             const int at = __popc(mask & ((1u << lane) - 1u));
             st_ray[w][at] = make_int4((int)(unsigned)(unsigned long long)q, (int)(q >> 32), P.z, __float_as_int(wr * sv.x));
@@ -135,6 +162,12 @@ __global__ void __launch_bounds__(32 * kSwWarps) k_bp_sweep(const SliceDesc* __r
         for (int r0 = 0; r0 < nr; r0 += kSwUnroll) {
             int hh[kSwUnroll];
             float ff[kSwUnroll], wc[kSwUnroll], wp[kSwUnroll];
+            if constexpr (NCH == 2) {  // w s_p of the block's rays: two broadcast 16-byte loads
+                const float4 p0 = *reinterpret_cast<const float4*>(&st_wp[w][r0]);
+                const float4 p1 = *reinterpret_cast<const float4*>(&st_wp[w][r0 + 4]);
+                wp[0] = p0.x; wp[1] = p0.y; wp[2] = p0.z; wp[3] = p0.w;
+                wp[4] = p1.x; wp[5] = p1.y; wp[6] = p1.z; wp[7] = p1.w;
+            }
 #pragma unroll
             for (int u = 0; u < kSwUnroll; ++u) {
                 const int4 S = st_ray[w][r0 + u];
@@ -142,24 +175,23 @@ __global__ void __launch_bounds__(32 * kSwWarps) k_bp_sweep(const SliceDesc* __r
                 hh[u] = pos_floor(q);
                 ff[u] = frac_of(q);
                 wc[u] = __int_as_float(S.w);
-                wp[u] = st_wp[w][r0 + u];
             }
 #pragma unroll
             for (int u = 0; u < kSwUnroll; ++u) {
-                // rows h, h+1 with h in [-1, 31] are accumulator rows h+1, h+2 (lanes outside skip)
-                if ((unsigned)(hh[u] + 1) < (unsigned)(kSw + 1)) {
+                // rows h, h+1 with h in [-1, TILE - 1] are accumulator rows h+1, h+2 (lanes outside skip)
+                if ((unsigned)(hh[u] + 1) < (unsigned)(TILE + 1)) {
                     Acc* a = &acc[w][hh[u] + 1][lane];
                     if constexpr (NCH == 2) {
-                        float2 x0 = a[0], x1 = a[kSw];
+                        float2 x0 = a[0], x1 = a[32];
                         x0.x = fmaf(1.0f - ff[u], wc[u], x0.x);
                         x0.y = fmaf(1.0f - ff[u], wp[u], x0.y);
                         x1.x = fmaf(ff[u], wc[u], x1.x);
                         x1.y = fmaf(ff[u], wp[u], x1.y);
                         a[0] = x0;
-                        a[kSw] = x1;
+                        a[32] = x1;
                     } else {
                         a[0] = fmaf(1.0f - ff[u], wc[u], a[0]);
-                        a[kSw] = fmaf(ff[u], wc[u], a[kSw]);
+                        a[32] = fmaf(ff[u], wc[u], a[32]);
                     }
                 }
             }
@@ -167,21 +199,45 @@ __global__ void __launch_bounds__(32 * kSwWarps) k_bp_sweep(const SliceDesc* __r
         __syncwarp();  // the stage is rewritten by the next chunk
     }
     __syncthreads();
-    for (int px = threadIdx.x; px < kSw * kSw; px += blockDim.x) {
-        const int rr = px / kSw, cc = px % kSw;
-        const int i = ti + cc, j = tj + rr;
-        if (i < nx && j < ny) {
-            Acc sum{};
-            for (int gi = 0; gi < kSwGroups; ++gi) {
-                const Acc a = acc[2 * gi][rr + 1][cc], b = acc[2 * gi + 1][cc + 1][rr];
+    if constexpr (CLUSTER) {
+        namespace cg = cooperative_groups;
+        cg::cluster_group cl = cg::this_cluster();
+        cl.sync();  // every view group of the tile has finished its accumulators
+        const int rank = (int)cl.block_rank(), nrank = (int)cl.num_blocks();
+        for (int px = rank * (int)blockDim.x + (int)threadIdx.x; px < TILE * TILE; px += nrank * (int)blockDim.x) {
+            const int rr = px / TILE, cc = px % TILE;
+            const int i = ti + cc, j = tj + rr;
+            if (i < nx && j < ny) {
+                Acc sum{};
+                for (int k = 0; k < nrank; ++k) {
+                    Acc(*peer)[Sh::kRows][32] = cl.map_shared_rank(acc, k);
+                    const Acc a = peer[cc / 32][rr + 1][cc % 32], b = peer[Sh::kBands + rr / 32][cc + 1][rr % 32];
+                    if constexpr (NCH == 2) {
+                        sum.x += a.x + b.x;
+                        sum.y += a.y + b.y;
+                    } else {
+                        sum += a + b;
+                    }
+                }
+                partial[d.img_off + (size_t)j * nx + i] = sum;
+            }
+        }
+        cl.sync();  // the peers' shared memory stays valid until every rank has read it
+    } else {
+        for (int px = threadIdx.x; px < TILE * TILE; px += blockDim.x) {
+            const int rr = px / TILE, cc = px % TILE;
+            const int i = ti + cc, j = tj + rr;
+            if (i < nx && j < ny) {
+                const Acc a = acc[cc / 32][rr + 1][cc % 32], b = acc[Sh::kBands + rr / 32][cc + 1][rr % 32];
+                Acc sum{};
                 if constexpr (NCH == 2) {
                     sum.x += a.x + b.x;
                     sum.y += a.y + b.y;
                 } else {
                     sum += a + b;
                 }
+                partial[c * stride + d.img_off + (size_t)j * nx + i] = sum;
             }
-            partial[c * stride + d.img_off + (size_t)j * nx + i] = sum;
         }
     }
 }
@@ -211,37 +267,61 @@ __global__ void __launch_bounds__(256) k_bp_finalize(const SliceDesc* __restrict
     if (MODE == BP_AP || MODE == BP_AP_NOGRAD) bp_block_dots(dot_c, dot_p, ep.partial);
 }
 
-int sweep_tiles(int nx, int ny) { return ((nx + kSw - 1) / kSw) * ((ny + kSw - 1) / kSw); }
+int sweep_tiles(int nx, int ny, int tile) { return ((nx + tile - 1) / tile) * ((ny + tile - 1) / tile); }
 
-int sweep_ctas_for_groups(int view_groups) { return (view_groups + kSwGroups - 1) / kSwGroups; }
-int sweep_groups_per_cta() { return kSwGroups; }
+int sweep_ctas_for_groups(int view_groups) { return view_groups; }
+int sweep_groups_per_cta() { return 1; }
 
-// CTA groups per tile: the smallest C (up to 8) whose grid of tiles * C blocks fills the resident
-// slots best (each CTA holds kSwGroups view groups; C * kSwGroups view groups per tile in total).
+// the kernels' dynamic shared memory may exceed the default 48 KB (TILE 64); the attribute is per device
 static std::mutex g_slots_mu;
-static std::vector<int> g_slots;  // resident CTA slots of k_bp_sweep, per device
+static std::vector<int> g_slots[2];  // resident CTA slots of k_bp_sweep per device, TILE 32 and 64
 
-int sweep_groups(int tiles) {
+template <class S2, int NCH, int TILE, bool CLUSTER>
+static cudaError_t sweep_attr1() {
+    auto* k = k_bp_sweep<S2, NCH, TILE, CLUSTER>;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sweep_acc_bytes<TILE, NCH>());
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
+    if (e == cudaSuccess && CLUSTER) e = cudaFuncSetAttribute(k, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    return e;
+}
+
+template <class S2, int NCH, int TILE>
+static cudaError_t sweep_attr() {
+    cudaError_t e = sweep_attr1<S2, NCH, TILE, false>();
+    if (e == cudaSuccess) e = sweep_attr1<S2, NCH, TILE, true>();
+    return e;
+}
+
+cudaError_t sweep_init_attributes() {
+    cudaError_t e = cudaSuccess;
+    for (cudaError_t r : {sweep_attr<float2, 2, 32>(), sweep_attr<__half2, 2, 32>(), sweep_attr<__nv_bfloat162, 2, 32>(),
+                          sweep_attr<float, 1, 32>(), sweep_attr<float2, 2, 64>(), sweep_attr<__half2, 2, 64>(),
+                          sweep_attr<__nv_bfloat162, 2, 64>(), sweep_attr<float, 1, 64>()})
+        if (e == cudaSuccess) e = r;
+    return e;
+}
+
+// CTA groups (view groups) per tile: the smallest C (up to 8) whose grid of tiles * C blocks fills the
+// resident slots best.
+int sweep_groups(int tiles, int tile) {
     int dev = 0;
     cudaGetDevice(&dev);
+    const int which = tile == 64 ? 1 : 0;
     std::unique_lock<std::mutex> lk(g_slots_mu);
-    if ((int)g_slots.size() <= dev) g_slots.resize(dev + 1, 0);
-    if (!g_slots[dev]) {
+    if ((int)g_slots[which].size() <= dev) g_slots[which].resize(dev + 1, 0);
+    if (!g_slots[which][dev]) {
         int sms = 0, occ = 0;
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        // shared memory (34 KB per CTA) limits residency: ask for the largest carve-out
-        cudaFuncSetAttribute(k_bp_sweep<float2, 2>, cudaFuncAttributePreferredSharedMemoryCarveout,
-                             cudaSharedmemCarveoutMaxShared);
-        cudaFuncSetAttribute(k_bp_sweep<__half2, 2>, cudaFuncAttributePreferredSharedMemoryCarveout,
-                             cudaSharedmemCarveoutMaxShared);
-        cudaFuncSetAttribute(k_bp_sweep<__nv_bfloat162, 2>, cudaFuncAttributePreferredSharedMemoryCarveout,
-                             cudaSharedmemCarveoutMaxShared);
-        cudaFuncSetAttribute(k_bp_sweep<float, 1>, cudaFuncAttributePreferredSharedMemoryCarveout,
-                             cudaSharedmemCarveoutMaxShared);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_bp_sweep<float2, 2>, 32 * kSwWarps, 0);
-        g_slots[dev] = sms * (occ > 0 ? occ : 1);
+        sweep_init_attributes();
+        if (which)
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_bp_sweep<float2, 2, 64>, SweepShape<64>::kThreads,
+                                                          sweep_acc_bytes<64, 2>());
+        else
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_bp_sweep<float2, 2, 32>, SweepShape<32>::kThreads,
+                                                          sweep_acc_bytes<32, 2>());
+        g_slots[which][dev] = sms * (occ > 0 ? occ : 1);
     }
-    const int slots = g_slots[dev];
+    const int slots = g_slots[which][dev];
     lk.unlock();
     int best = 1;
     double best_fill = 0.0;
@@ -257,22 +337,61 @@ int sweep_groups(int tiles) {
     return best;
 }
 
-void launch_bp_sweep(const SliceDesc* dsl, const BlockMap& smap, int nsweep, int C, const void* sino,
-                     float2* partial, int64_t stride, int prec, cudaStream_t st) {
-    if (prec == PREC_F16)
-        k_bp_sweep<__half2, 2><<<nsweep, 32 * kSwWarps, 0, st>>>(dsl, smap, C, (const __half2*)sino, partial, stride,
-                                                                 nullptr, nullptr);
-    else if (prec == PREC_BF16)
-        k_bp_sweep<__nv_bfloat162, 2><<<nsweep, 32 * kSwWarps, 0, st>>>(dsl, smap, C, (const __nv_bfloat162*)sino,
-                                                                         partial, stride, nullptr, nullptr);
-    else
-        k_bp_sweep<float2, 2><<<nsweep, 32 * kSwWarps, 0, st>>>(dsl, smap, C, (const float2*)sino, partial, stride,
-                                                                nullptr, nullptr);
+template <class S2, int NCH, int TILE>
+static void sweep_t(const SliceDesc* dsl, const BlockMap& smap, int nsweep, int C, bool cluster, const S2* sino,
+                    typename std::conditional<NCH == 2, float2, float>::type* partial, int64_t stride,
+                    const float* rw, const float* scale, cudaStream_t st) {
+    if (!cluster || C == 1) {
+        k_bp_sweep<S2, NCH, TILE><<<nsweep, SweepShape<TILE>::kThreads, sweep_acc_bytes<TILE, NCH>(), st>>>(
+            dsl, smap, C, sino, partial, stride, rw, scale);
+        return;
+    }
+    // the C CTAs of a tile are consecutive blocks and every slice's block range is a multiple of C,
+    // so a cluster of C blocks is exactly one tile's view groups
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)nsweep);
+    cfg.blockDim = dim3(SweepShape<TILE>::kThreads);
+    cfg.dynamicSmemBytes = sweep_acc_bytes<TILE, NCH>();
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = (unsigned)C;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, k_bp_sweep<S2, NCH, TILE, true>, dsl, smap, C, sino, partial, stride, rw, scale);
 }
 
-void launch_bp_sweep1(const SliceDesc* dsl, const BlockMap& smap, int nsweep, int C, const float* sino, const float* rw,
-                      const float* scale, float* partial, int64_t stride, cudaStream_t st) {
-    k_bp_sweep<float, 1><<<nsweep, 32 * kSwWarps, 0, st>>>(dsl, smap, C, sino, partial, stride, rw, scale);
+void launch_bp_sweep(const SliceDesc* dsl, const BlockMap& smap, int nsweep, int C, int tile, bool cluster,
+                     const void* sino, float2* partial, int64_t stride, int prec, cudaStream_t st) {
+    const bool k = cluster;
+    if (tile == 64) {
+        if (prec == PREC_F16)
+            sweep_t<__half2, 2, 64>(dsl, smap, nsweep, C, k, (const __half2*)sino, partial, stride, nullptr, nullptr, st);
+        else if (prec == PREC_BF16)
+            sweep_t<__nv_bfloat162, 2, 64>(dsl, smap, nsweep, C, k, (const __nv_bfloat162*)sino, partial, stride,
+                                           nullptr, nullptr, st);
+        else
+            sweep_t<float2, 2, 64>(dsl, smap, nsweep, C, k, (const float2*)sino, partial, stride, nullptr, nullptr, st);
+    } else {
+        if (prec == PREC_F16)
+            sweep_t<__half2, 2, 32>(dsl, smap, nsweep, C, k, (const __half2*)sino, partial, stride, nullptr, nullptr, st);
+        else if (prec == PREC_BF16)
+            sweep_t<__nv_bfloat162, 2, 32>(dsl, smap, nsweep, C, k, (const __nv_bfloat162*)sino, partial, stride,
+                                           nullptr, nullptr, st);
+        else
+            sweep_t<float2, 2, 32>(dsl, smap, nsweep, C, k, (const float2*)sino, partial, stride, nullptr, nullptr, st);
+    }
+}
+
+void launch_bp_sweep1(const SliceDesc* dsl, const BlockMap& smap, int nsweep, int C, int tile, bool cluster,
+                      const float* sino, const float* rw, const float* scale, float* partial, int64_t stride,
+                      cudaStream_t st) {
+    if (tile == 64)
+        sweep_t<float, 1, 64>(dsl, smap, nsweep, C, cluster, sino, partial, stride, rw, scale, st);
+    else
+        sweep_t<float, 1, 32>(dsl, smap, nsweep, C, cluster, sino, partial, stride, rw, scale, st);
 }
 
 template <int MODE>
@@ -293,13 +412,13 @@ void launch_bp_finalize(int mode, const SliceDesc* dsl, const BlockMap& pix, int
     }
 }
 
-void backproject_single(const SliceDesc& sd, const SliceDesc* d_dev, const int* maps, int C, const float* sino,
+void backproject_single(const SliceDesc& sd, const SliceDesc* d_dev, const int* maps, int C, int tile, const float* sino,
                         int nch, float2* packed, float2* partial, float* out, cudaStream_t st) {
     const int64_t nr = (int64_t)sd.g.nv * sd.g.nb, np = (int64_t)sd.g.nx * sd.g.ny;
     launch_pack_planar(sino, nch, nr, packed, st);
     const BlockMap smap{maps, 1}, pmap{maps + 2, 1};
-    k_bp_sweep<float2, 2><<<sweep_tiles(sd.g.nx, sd.g.ny) * C, 32 * kSwWarps, 0, st>>>(d_dev, smap, C, packed,
-                                                                                      partial, np, nullptr, nullptr);
+    launch_bp_sweep(d_dev, smap, sweep_tiles(sd.g.nx, sd.g.ny, tile) * C, C, tile, false, packed, partial, np, PREC_F32,
+                    st);
     k_bp_finalize<BP_PLAIN><<<(unsigned)((np + 255) / 256), 256, 0, st>>>(d_dev, pmap, C, partial, np, nullptr,
                                                                          BpEpilogue{}, out, nch);
 }

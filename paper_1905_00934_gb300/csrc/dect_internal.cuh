@@ -155,19 +155,25 @@ void launch_project(const SliceDesc* dsl, const BlockMap& map, int nblk, const v
 // the fixed-order sum of the partials with the epilogue; partial dots over the `pix` blocks)
 int sweep_ctas_for_groups(int view_groups);
 int sweep_groups_per_cta();
-int sweep_tiles(int nx, int ny);
-int sweep_groups(int tiles);
-void launch_bp_sweep(const SliceDesc* dsl, const BlockMap& smap, int nsweep, int C, const void* sino,
-                     float2* partial, int64_t stride, int prec, cudaStream_t st);
+// image tiles of the sweep for a TILE x TILE tile (32 or 64); the occupancy choice of view groups
+int sweep_tiles(int nx, int ny, int tile);
+int sweep_groups(int tiles, int tile);
+cudaError_t sweep_init_attributes();  // per device: dynamic shared memory of the 64-pixel tiles
+constexpr int kSweepTileDefault = 32;
+// cluster: the C view groups of a tile reduce on chip (thread-block cluster, distributed shared memory)
+// into partial image 0 (the finalize pass then reads one image, C = 1); otherwise C partial images
+void launch_bp_sweep(const SliceDesc* dsl, const BlockMap& smap, int nsweep, int C, int tile, bool cluster,
+                     const void* sino, float2* partial, int64_t stride, int prec, cudaStream_t st);
 // single-channel sweep (float sinogram, float partial images; rw per ray and scale per slice optional)
-void launch_bp_sweep1(const SliceDesc* dsl, const BlockMap& smap, int nsweep, int C, const float* sino, const float* rw,
-                      const float* scale, float* partial, int64_t stride, cudaStream_t st);
+void launch_bp_sweep1(const SliceDesc* dsl, const BlockMap& smap, int nsweep, int C, int tile, bool cluster,
+                      const float* sino, const float* rw, const float* scale, float* partial, int64_t stride,
+                      cudaStream_t st);
 void launch_bp_finalize(int mode, const SliceDesc* dsl, const BlockMap& pix, int npix, int C, const float2* partial,
                         int64_t stride, float2* out, const BpEpilogue& ep, cudaStream_t st);
 // Single-slice planar R^T (dect_backproject): sino [nch][nv][nb] -> out [nch][ny][nx]. d_dev is the
 // slice's descriptor on the device with zero offsets; maps holds the sweep and pixel-block prefixes
 // {0, sweep_tiles * C, 0, pixel blocks}; packed holds nv*nb float2, partial C*nx*ny float2.
-void backproject_single(const SliceDesc& sd, const SliceDesc* d_dev, const int* maps, int C, const float* sino,
+void backproject_single(const SliceDesc& sd, const SliceDesc* d_dev, const int* maps, int C, int tile, const float* sino,
                         int nch, float2* packed, float2* partial, float* out, cudaStream_t st);
 void project_single(const SliceDesc& sd, const float* img, int nch, float2* scratch, float4* tx, float4* ty,
                     float* out, cudaStream_t st);

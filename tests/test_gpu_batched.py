@@ -107,6 +107,42 @@ def test_autotuned_view_groups_equal_the_fixed_choice(cuda_dev):
         assert np.array_equal(tuned.get(b, dect.X).cpu().numpy(), fixed.get(b, dect.X).cpu().numpy())
 
 
+def test_backprojector_tile_side_does_not_change_results(cuda_dev):
+    # a pixel receives the same contributions in the same order from 32- and 64-pixel tiles (the
+    # bands differ only in which rays they stage, and a staged ray adds nothing to pixels it misses),
+    # so the autotuner's tile choice is free; the fixed choice of either reproduces the other
+    from paper_1905_00934_gb300 import dect
+
+    cases = _small_cases()
+    outs = []
+    for tile in (32, 64):
+        sol = _solver(cases, cuda_dev, [None] * 3, bp_view_groups=4, bp_tile=tile)
+        assert sol.stats(0)["bp_tile"] == tile
+        sol.reconstruct(3)
+        outs.append([sol.get(b, dect.X).cpu().numpy() for b in range(3)])
+    for b in range(3):
+        assert np.array_equal(outs[0][b], outs[1][b])
+
+
+@pytest.mark.parametrize("scheme", [0, 1])
+@pytest.mark.parametrize("groups", [4, 8])
+def test_cluster_reduction_of_view_groups_gives_the_same_bits(cuda_dev, scheme, groups):
+    # the view groups of a tile adding their accumulators on chip in rank order (one thread-block
+    # cluster) form each pixel's sum exactly as the finalize pass does from C partial images
+    from paper_1905_00934_gb300 import dect
+
+    cases = _small_cases()
+    outs = []
+    for cluster in (-1, 1):
+        sol = _solver(cases, cuda_dev, [None] * 3, bp_view_groups=groups, bp_tile=32, bp_cluster=cluster,
+                      scheme=scheme)
+        assert sol.stats(0)["bp_cluster"] == (1 if cluster > 0 else 0)
+        sol.reconstruct(3)
+        outs.append([sol.get(b, dect.X).cpu().numpy() for b in range(3)])
+    for b in range(3):
+        assert np.array_equal(outs[0][b], outs[1][b])
+
+
 @pytest.mark.slow
 def test_uneven_64_slice_batch_full_size(cuda_dev):
     # the batched workload at full size: 64 seeded slices, N 256..1024, 360..1440 views,
