@@ -76,9 +76,11 @@ def _mixed_solver(cuda_dev, slices, storage, with_truth):
 
 @pytest.mark.skipif(not os.path.exists(GOLDEN_EARLY), reason="initial-image oracle pixels for 1024^2 not generated")
 def test_full_size_initial_image_float32(cuda_dev):
-    # The initial image's 10 float32 PCG iterations on (R^T R + I) x = R^T a_c amplify the rounding of
-    # R / R^T: the full image differs from the FP64 oracle's by 7e-5 relative, the sampled pixels by
-    # 2e-4, so the bar is 5e-4 (iterations from a common starting image are held below).
+    # The start decomposes every ray with rho_c = 0 (Eq. 13 without its Compton penalty), where the
+    # 2x2 system is ill-conditioned (the Compton and PE columns are nearly parallel, Sec. 1), and its 10
+    # float32 PCG iterations on (R^T R + I) x = R^T a_c add the rounding of R / R^T: the full image
+    # differs from the FP64 oracle's by 7e-5 relative, the sampled pixels by 2e-4, so the bar is 5e-4
+    # (iterations from a common starting image are held below, and from the oracle's start above).
     from paper_1905_00934_gb300 import dect
 
     ref = json.load(open(GOLDEN_EARLY))
@@ -92,13 +94,10 @@ def test_full_size_initial_image_float32(cuda_dev):
         assert e_c <= 5e-4 and e_p <= 5e-4, (b, e_c, e_p)
 
 
-@pytest.mark.slow
-def test_full_size_iterations_from_the_oracle_initial_image(cuda_dev):
-    # 1024 x 1024, 1440 views, 2048 bins: the oracle's initial image and 3 ADMM iterations (computed
-    # here, about a minute on the host cores), the GPU started from that image; the whole images
-    # agree to float32 level (measured 2e-6 after 3 iterations) until float32 rounding flips a
-    # per-ray LM decision, which happens later.
-    from paper_1905_00934_gb300 import Geometry, Solver, Spectra, dect
+@pytest.fixture(scope="module")
+def start_1024():
+    """Slice 0 of the 1024 x 1024, 1440-view, 2048-bin workload with float32-rounded measurements, the
+    oracle's problem and its initial image rounded to float32 (about a minute on the host cores)."""
     from synth.workloads import BAGGAGE_KAPPA, MIXED_SEED_BASE, baggage_fan_case
 
     c = baggage_fan_case(slice_index=MIXED_SEED_BASE, n=1024, n_views=1440, n_bins=2048)
@@ -107,6 +106,18 @@ def test_full_size_iterations_from_the_oracle_initial_image(cuda_dev):
     prob = oadmm.Problem(c["geom"], c["spectra"], c["m_h"], c["m_l"], c["w_h"], c["w_l"],
                          oadmm.Params(kappa=BAGGAGE_KAPPA))
     x0 = _r32(np.stack(oadmm.initial_image(prob)))
+    return c, prob, x0
+
+
+@pytest.mark.slow
+def test_full_size_iterations_from_the_oracle_initial_image(cuda_dev, start_1024):
+    # 1024 x 1024, 1440 views, 2048 bins: the oracle's initial image and 3 ADMM iterations (computed
+    # here), the GPU started from that image; the whole images agree to float32 level (measured 2e-6
+    # after 3 iterations) until float32 rounding flips a per-ray LM decision, which happens later.
+    from paper_1905_00934_gb300 import Geometry, Solver, Spectra, dect
+    from synth.workloads import BAGGAGE_KAPPA
+
+    c, prob, x0 = start_1024
     st = oadmm.state_from_image(prob, x0[0], x0[1])
     geo = Geometry(c["geom"])
     sol = Solver([geo], Spectra.from_tables(c["spectra"]), kappa=BAGGAGE_KAPPA)
@@ -125,11 +136,14 @@ def test_full_size_iterations_from_the_oracle_initial_image(cuda_dev):
 # perturbations accumulate: with float32 storage the sampled pixels of slice 0 differ from the
 # FP64 oracle by 4.3 % (Compton) and 9.0 % (PE) relative L2 while xi (Eq. 14), the quantity the
 # workload's error target is set on, tracks the oracle to 0.002 dB at every 10th iteration and
-# the rho decisions are identical. So the trajectory is held on xi; the pixel bound is a
-# regression guard. 16-bit storage rounds the stored line integrals (11 / 8 significant bits):
-# measured xi drift over the 4 reference slices up to 0.017 dB (float16) and 1.16 dB (bfloat16, slice
-# 3 at iteration 90): bfloat16 storage does not hold the workload's 0.5 dB PE-error target on every
-# slice, float16 does.
+# the rho decisions are identical. The same divergence appears from the oracle's own start and with
+# the float64 decomposition (test_full_size_trajectory_from_the_oracle_start: 3.9 % / 7.6 % at 100
+# iterations), so it is the float32 state's sensitivity, not the start or the decomposition's
+# precision: the trajectory is held on xi and the pixel bound is a regression guard. 16-bit storage
+# rounds the stored line integrals (11 / 8 significant bits): measured xi drift over the 4 reference
+# slices up to 0.017 dB (float16) and 1.16 dB (bfloat16, slice 3 at iteration 90): bfloat16 storage
+# does not hold the workload's 0.5 dB PE-error target on every slice (its bound is a regression
+# guard on a format documented as unfit for it), float16 does.
 XI_TOL_DB = {0: 0.02, 1: 0.05, 2: 1.5}
 PIX_TOL = {0: 0.15, 1: 0.3, 2: 1.0}
 
@@ -159,3 +173,54 @@ def test_full_size_subset_against_oracle(cuda_dev, storage):
     print(f"storage {['f32', 'f16', 'bf16'][storage]}, 1024^2 subset: worst xi difference {worst:.4f} dB, "
           f"sampled-pixel rel-L2 after {ref['iterations']} iterations {errs}")
     assert all(e_c <= PIX_TOL[storage] and e_p <= PIX_TOL[storage] for e_c, e_p in errs)
+
+
+GOLDEN_FROM_X0 = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "mixed_1024_from_x0.json")
+
+
+@pytest.mark.slow
+@pytest.mark.skipif(not os.path.exists(GOLDEN_FROM_X0), reason="oracle trajectory from x0 for 1024^2 not generated")
+@pytest.mark.parametrize("udm_f64", [0, 1])
+def test_full_size_trajectory_from_the_oracle_start(cuda_dev, start_1024, udm_f64):
+    """Float32 storage from the oracle's start: sampled pixels after 10, 20, 50 and 100 iterations and
+    xi every 10 iterations against the stored FP64 oracle trajectory (tests/golden/mixed_1024_from_x0.json),
+    with the float32 decomposition and with the float64 one (udm_f64)."""
+    from paper_1905_00934_gb300 import Geometry, Solver, Spectra, dect
+    from synth.workloads import BAGGAGE_KAPPA
+
+    c, _, x0 = start_1024
+    ref = json.load(open(GOLDEN_FROM_X0))
+    idx = np.array(ref["pixels"])
+    geo = Geometry(c["geom"])
+    sol = Solver([geo], Spectra.from_tables(c["spectra"]), kappa=BAGGAGE_KAPPA, udm_f64=udm_f64)
+    sol.set_data(0, *[to_dev(c[k], cuda_dev) for k in ("m_h", "m_l", "w_h", "w_l")], to_dev(x0, cuda_dev))
+    sol.set_truth(0, to_dev(np.stack([c["truth_c"], c["truth_p"]]), cuda_dev))
+    sol.reconstruct(0)
+    errs, xi_worst, done = {}, 0.0, 0
+    for k in range(1, 11):
+        sol.step(10 * k - done)
+        done = 10 * k
+        xi = sol.stats(0)["xi_db"]
+        xi_worst = max(xi_worst, abs(xi[0] - ref["xi"][k][0]), abs(xi[1] - ref["xi"][k][1]))
+        if str(done) in ref["x"]:
+            x = sol.get(0, dect.X).cpu().numpy().reshape(2, -1)
+            r = ref["x"][str(done)]
+            errs[done] = (rel_l2(x[0, idx], r[0]), rel_l2(x[1, idx], r[1]))
+    print(f"1024^2 from the oracle start, float32 storage, udm_f64={udm_f64}: sampled-pixel rel-L2 "
+          f"(Compton, PE) {errs}; worst xi difference {xi_worst:.4f} dB")
+    bounds = TRAJ_PIX_TOL[udm_f64]
+    for it, (e_c, e_p) in errs.items():
+        assert e_c <= bounds[it] and e_p <= bounds[it], (it, e_c, e_p)
+    assert xi_worst <= XI_TOL_DB[0]
+
+
+# Sampled-pixel bounds per checkpoint (iterations -> relative L2): regression guards at about twice the
+# values measured on GB300 from the oracle's own start (float32 decomposition / float64 decomposition):
+#   10 its 7.7e-4, 7.1e-4 / 3.4e-4, 3.8e-4;   20 its 7.8e-3, 4.9e-3 / 5.5e-3, 3.7e-3;
+#   50 its 2.0e-2, 1.5e-2 / 1.6e-2, 8.8e-3;  100 its 4.0e-2, 8.2e-2 / 3.9e-2, 7.6e-2
+# (Compton, PE), xi within 0.0052 / 0.0046 dB of the oracle at every 10th iteration. The float64
+# decomposition halves the early difference but leaves the 100-iteration one: what grows is the float32
+# rounding of the carried state (R x, a, u^a, the images) that Eq. 13's accept test turns into whole-step
+# moves of near-tied rays, and those perturbations compound over the iterations (Sec. 3.3's LM step is a
+# discrete decision per ray). The workload's error target is set on xi, which both hold to 0.005 dB.
+TRAJ_PIX_TOL = {0: {10: 2e-3, 20: 2e-2, 50: 5e-2, 100: 0.15}, 1: {10: 1e-3, 20: 1.5e-2, 50: 4e-2, 100: 0.15}}
