@@ -535,7 +535,9 @@ struct dect_admm {
     dect_params P{};
     std::vector<SliceDesc> hs;
     SliceDesc* ds = nullptr;
-    MapBuf rays, pix, tx, ty, rows, cols, sweep, ptile;  // ptile: the projector's (views x bins) tiles
+    MapBuf rays, pix, tx, ty, rows, cols, sweep, ptile;  // ptile: the projector's (views x bins) tiles per group
+    int n_groups = 0;                // projector groups: consecutive slices of one geometry (proj_group_size())
+    int4* d_groups = nullptr;        // {slice, further slices or -1} per group
     int sweep_C = 1;                 // CTA groups (partial images) per backprojector tile
     int sweep_tile = kSweepTileDefault;  // backprojector tile side (32 or 64; does not change results)
     bool sweep_cluster = false;      // the view groups of a tile reduce on chip into one partial image
@@ -612,7 +614,7 @@ static void pe(dect_admm* A, int phase, int nk, cudaStream_t st) {
 }
 
 static void free_admm(dect_admm* A) {
-    void* ptrs[] = {A->ds, A->rays.d, A->pix.d, A->tx.d, A->ty.d, A->rows.d, A->cols.d, A->sweep.d, A->ptile.d,
+    void* ptrs[] = {A->ds, A->rays.d, A->pix.d, A->tx.d, A->ty.d, A->rows.d, A->cols.d, A->sweep.d, A->ptile.d, A->d_groups,
                     A->bp_partial, A->x, A->r, A->s,
                     A->p, A->Ap, A->z, A->uz, A->x0, A->truth, A->Rx, A->a, A->ua, A->q, A->Z, A->y, A->uy,
                     A->meas, A->txb, A->tyb, A->mu, A->H, A->Hn, A->stage, A->status, A->sc, A->part_udm,
@@ -648,7 +650,7 @@ static void enq_project(dect_admm* A, const float2* img, void* out, cudaStream_t
     launch_textures(A->ds, A->tx.map(B), A->tx.total, A->ty.map(B), A->ty.total, img, A->txb, A->tyb, A->prec, st);
     pe(A, DECT_PHASE_TEXTURE, 2, st);
     pb(A, st);
-    launch_project(A->ds, A->ptile.map(B), A->ptile.total, A->txb, A->tyb, out, A->prec, st);
+    launch_project(A->ds, A->ptile.map(A->n_groups), A->ptile.total, A->d_groups, A->txb, A->tyb, out, A->prec, st);
     pe(A, DECT_PHASE_PROJECT, 1, st);
     if (A->counting) A->cR += 2;
 }
@@ -758,7 +760,7 @@ static void enq_lm_step(dect_admm* A, int b, cudaStream_t st) {
         launch_textures1(A->ds, A->tx.map(B), A->tx.total, A->ty.map(B), A->ty.total, A->lm_p, A->tx1, A->ty1, st);
         pe(A, DECT_PHASE_TEXTURE, 2, st);
         pb(A, st);
-        launch_project1(A->ds, A->ptile.map(B), A->ptile.total, A->tx1, A->ty1, A->lm_q, st);
+        launch_project1(A->ds, A->ptile.map(A->n_groups), A->ptile.total, A->d_groups, A->tx1, A->ty1, A->lm_q, st);
         pe(A, DECT_PHASE_PROJECT, 1, st);
         pb(A, st);
         launch_bp_sweep1(A->ds, A->sweep.map(B), A->sweep.total, A->sweep_C, A->sweep_tile, A->sweep_cluster, A->lm_q,
@@ -1418,7 +1420,7 @@ extern "C" dect_status dect_admm_create(dect_geom* const* geoms, int32_t B, cons
         max_nr = std::max(max_nr, nr);
         A->hs.push_back(sd);
         A->rays.h.push_back(A->rays.h.back() + (int)((nr + kRaysPerBlock - 1) / kRaysPerBlock));
-        A->ptile.h.push_back(A->ptile.h.back() + proj_tiles(g->desc.n_views, g->desc.n_bins));
+
         A->pix.h.push_back(A->pix.h.back() + (int)((np + 255) / 256));
         A->tx.h.push_back(A->tx.h.back() + texture_x_blocks(nx, ny));
         A->ty.h.push_back(A->ty.h.back() + texture_y_blocks(nx, ny));
@@ -1429,6 +1431,22 @@ extern "C" dect_status dect_admm_create(dect_geom* const* geoms, int32_t B, cons
         A->cols64.h.push_back(A->cols64.h.back() + sd.px);
     }
     A->n_stage = std::max(4 * max_nr + 4 * max_np, (int64_t)16);
+    // projector groups: a slice joins the previous group when that has room and the same geometry
+    std::vector<int4> groups;
+    std::vector<int> gsize;
+    for (int b = 0; b < B; ++b) {
+        if (!groups.empty() && gsize.back() < proj_group_size() &&
+            same_geometry(geoms[groups.back().x]->desc, geoms[b]->desc)) {
+            int* slot = &groups.back().x;
+            slot[gsize.back()++] = b;
+        } else {
+            groups.push_back(make_int4(b, -1, -1, -1));
+            gsize.push_back(1);
+        }
+    }
+    A->n_groups = (int)groups.size();
+    for (const int4& gr : groups)
+        A->ptile.h.push_back(A->ptile.h.back() + proj_tiles(geoms[gr.x]->desc.n_views, geoms[gr.x]->desc.n_bins));
 
 #define ALLOC(ptr, n)                                                      \
     do {                                                                   \
@@ -1496,6 +1514,9 @@ extern "C" dect_status dect_admm_create(dect_geom* const* geoms, int32_t B, cons
     if (e == cudaSuccess && A->prec != PREC_F64) e = dalloc(&A->bp_partial, (size_t)A->sweep_C * A->n_img);
     for (MapBuf* m : {&A->rays, &A->pix, &A->tx, &A->ty, &A->rows, &A->cols, &A->sweep, &A->cols64, &A->ptile})
         if (e == cudaSuccess) e = upload_map(*m);
+    if (e == cudaSuccess) e = dalloc(&A->d_groups, groups.size());
+    if (e == cudaSuccess)
+        e = cudaMemcpy(A->d_groups, groups.data(), sizeof(int4) * groups.size(), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(A->ds, A->hs.data(), sizeof(SliceDesc) * B, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemset(A->truth, 0, sizeof(float2) * A->n_img);
     if (e == cudaSuccess) e = cudaMemset(A->status, 0, A->n_sino);

@@ -176,16 +176,20 @@ __global__ void k_pack_planar(const float* __restrict__ in, int nch, int64_t n, 
 
 // Launch shape of the forward projector (compile-time; the defaults are the measured best on GB300):
 // samples whose texel loads are issued together per lane, views (warps) per CTA, the CTAs per SM the
-// register allocation must allow, and whether positions advance incrementally or are recomputed from
-// the index at every sample (both give the same integers, so the same results).
+// register allocation must allow, slices of one geometry per CTA (1, 2 or 4), and whether positions
+// advance incrementally or are recomputed from the index at every sample (both give the same integers,
+// so the same results).
 #ifndef DECT_PROJ_BATCH
 #define DECT_PROJ_BATCH 8
 #endif
 #ifndef DECT_PROJ_VIEWS
-#define DECT_PROJ_VIEWS 8
+#define DECT_PROJ_VIEWS 2
 #endif
 #ifndef DECT_PROJ_MINB
-#define DECT_PROJ_MINB 1
+#define DECT_PROJ_MINB 16
+#endif
+#ifndef DECT_PROJ_GROUP
+#define DECT_PROJ_GROUP 2
 #endif
 #ifndef DECT_PROJ_INCR
 #define DECT_PROJ_INCR 0
@@ -303,6 +307,7 @@ __device__ __forceinline__ float2 ray_sum_sync(const int4 P, bool valid, const G
 // rays of neighbouring views through the same bins cross nearly the same texels, so the tile's warps
 // share them in L1.
 constexpr int kProjViews = DECT_PROJ_VIEWS;
+constexpr int kProjGroup = DECT_PROJ_GROUP;  // slices of one geometry projected by one CTA (<= 4)
 
 __host__ __device__ __forceinline__ int proj_bin_tiles(int nb) { return (nb + 31) / 32; }
 
@@ -316,20 +321,106 @@ __device__ __forceinline__ bool proj_ray(int local, int nv, int nb, int& v, int&
     return v < nv && k < nb;
 }
 
+// The same lock-step sum for the rays of one geometry through up to G slices' images at once (slices
+// of one scan share the geometry): positions, ranges and texel indices are formed once per sample and
+// only the texel loads and the accumulation are per slice. Each slice's sum takes the same terms in the
+// same order as ray_sum_sync on that slice alone. count (<= G) is uniform over the CTA.
+template <class TX, int G>
+__device__ __forceinline__ void ray_sum_group(const int4 P, bool valid, const GeomDev& g, const TX* const (&txs)[G],
+                                              const TX* const (&tys)[G], int count, float2 (&acc)[G]) {
+    const bool ax = ray_axis(P);
+    const int n_across = ax ? g.nx : g.ny;
+    const int ld = n_across + 3;
+    int lo = 1, hi = 0;
+    if (valid) trimmed_range(P, g, lo, hi);
+    const bool any = lo <= hi;
+    const int t0 = __reduce_min_sync(0xffffffffu, any ? lo : 0x7fffffff);
+    const int t1 = __reduce_max_sync(0xffffffffu, any ? hi : -1);
+    float ac[G], ap[G];
+#pragma unroll
+    for (int k = 0; k < G; ++k) ac[k] = ap[k] = 0.f;
+    if (t0 <= t1) {  // some lane of the warp samples the image (warp-uniform)
+        // from here 0 <= t0 <= t1 < max(nx, ny): the bounds below cannot overflow
+        const long long step = ray_step(P), q0 = ray_q0(P);
+        const TX* tex[G];
+#pragma unroll
+        for (int k = 0; k < G; ++k) tex[k] = ax ? tys[k] : txs[k];
+        int t = t0;
+        for (; t <= t1 - (kProjBatch - 1); t += kProjBatch) {
+            int idx[kProjBatch];
+            float f[kProjBatch];
+#pragma unroll
+            for (int u = 0; u < kProjBatch; ++u) {
+                const int tt = t + u;
+                const long long qu = q0 + (long long)tt * step;
+                idx[u] = (tt >= lo && tt <= hi) ? tt * ld + 2 + pos_floor(qu) : 0;  // texel 0: zero padding
+                f[u] = frac_of(qu);
+            }
+#pragma unroll
+            for (int k = 0; k < G; ++k) {
+                if (k >= count) break;
+                float4 v[kProjBatch];
+#pragma unroll
+                for (int u = 0; u < kProjBatch; ++u) v[u] = ldtex(tex[k] + idx[u]);
+#pragma unroll
+                for (int u = 0; u < kProjBatch; ++u) {
+                    ac[k] += fmaf(f[u], v[u].z - v[u].x, v[u].x);
+                    ap[k] += fmaf(f[u], v[u].w - v[u].y, v[u].y);
+                }
+            }
+        }
+        for (; t <= t1; ++t) {
+            const long long q1 = q0 + (long long)t * step;
+            const int i1 = (t >= lo && t <= hi) ? t * ld + 2 + pos_floor(q1) : 0;
+            const float f = frac_of(q1);
+#pragma unroll
+            for (int k = 0; k < G; ++k) {
+                if (k >= count) break;
+                const float4 v = ldtex(tex[k] + i1);
+                ac[k] += fmaf(f, v.z - v.x, v.x);
+                ap[k] += fmaf(f, v.w - v.y, v.y);
+            }
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < G; ++k) acc[k] = make_float2(ac[k], ap[k]);
+}
+
+// One CTA per (geometry group, tile): group gi holds up to kProjGroup slices of one geometry (their
+// indices in groups[gi], -1 past the group's size); the block map counts tiles per group.
 template <class S2, class TX>
 __global__ void __launch_bounds__(32 * kProjViews, DECT_PROJ_MINB) k_project(const SliceDesc* __restrict__ dsl, BlockMap map,
+                                                             const int4* __restrict__ groups,
                                                              const TX* __restrict__ tx, const TX* __restrict__ ty,
                                                              S2* __restrict__ out) {
     int local;
-    const int s = slice_of(map, blockIdx.x, local);
-    const SliceDesc& d = dsl[s];
+    const int gi = slice_of(map, blockIdx.x, local);
+    const int4 gs = __ldg(groups + gi);
+    const int all[4] = {gs.x, gs.y, gs.z, gs.w};
+    int sl[kProjGroup];
+#pragma unroll
+    for (int q = 0; q < kProjGroup; ++q) sl[q] = all[q];
+    const int count = 1 + (gs.y >= 0) + (gs.z >= 0) + (gs.w >= 0);
+    const SliceDesc& d = dsl[sl[0]];
     int v, k;
     const bool valid = proj_ray(local, d.g.nv, d.g.nb, v, k);
     const int64_t r = (int64_t)v * d.g.nb + k;
     const int4 P = valid ? __ldg(d.g.rays + r) : make_int4(0, 0, 0, 0);
-    const float2 acc = ray_sum_sync(P, valid, d.g, tx + d.tx_off, ty + d.ty_off);
+    const TX* txs[kProjGroup];
+    const TX* tys[kProjGroup];
+#pragma unroll
+    for (int q = 0; q < kProjGroup; ++q) {
+        const SliceDesc& dq = dsl[q < count ? sl[q] : sl[0]];
+        txs[q] = tx + dq.tx_off;
+        tys[q] = ty + dq.ty_off;
+    }
+    float2 acc[kProjGroup];
+    ray_sum_group<TX, kProjGroup>(P, valid, d.g, txs, tys, count, acc);
     const float w = ray_w(P);
-    if (valid) st2(out + d.sino_off + r, make_float2(w * acc.x, w * acc.y));
+    if (!valid) return;
+#pragma unroll
+    for (int q = 0; q < kProjGroup; ++q)
+        if (q < count) st2(out + dsl[sl[q]].sino_off + r, make_float2(w * acc[q].x, w * acc[q].y));
 }
 
 __global__ void __launch_bounds__(32 * kProjViews, DECT_PROJ_MINB) k_project_planar(SliceDesc d, const float4* __restrict__ tx,
@@ -347,23 +438,27 @@ __global__ void __launch_bounds__(32 * kProjViews, DECT_PROJ_MINB) k_project_pla
     if (nch > 1) out[n + r] = w * acc.y;
 }
 
-void launch_project(const SliceDesc* dsl, const BlockMap& map, int nblk, const void* tx, const void* ty, void* out,
-                    int prec, cudaStream_t st) {
+void launch_project(const SliceDesc* dsl, const BlockMap& map, int nblk, const int4* groups, const void* tx,
+                    const void* ty, void* out, int prec, cudaStream_t st) {
     constexpr int T = 32 * kProjViews;
     if (prec == PREC_F16)
-        k_project<__half2, TexH><<<nblk, T, 0, st>>>(dsl, map, (const TexH*)tx, (const TexH*)ty, (__half2*)out);
+        k_project<__half2, TexH><<<nblk, T, 0, st>>>(dsl, map, groups, (const TexH*)tx, (const TexH*)ty,
+                                                      (__half2*)out);
     else if (prec == PREC_BF16)
-        k_project<__nv_bfloat162, TexB><<<nblk, T, 0, st>>>(dsl, map, (const TexB*)tx, (const TexB*)ty,
+        k_project<__nv_bfloat162, TexB><<<nblk, T, 0, st>>>(dsl, map, groups, (const TexB*)tx, (const TexB*)ty,
                                                              (__nv_bfloat162*)out);
     else
-        k_project<float2, float4><<<nblk, T, 0, st>>>(dsl, map, (const float4*)tx, (const float4*)ty, (float2*)out);
+        k_project<float2, float4><<<nblk, T, 0, st>>>(dsl, map, groups, (const float4*)tx, (const float4*)ty,
+                                                       (float2*)out);
 }
 
 // single channel: float out, float2 texels
-void launch_project1(const SliceDesc* dsl, const BlockMap& map, int nblk, const float2* tx, const float2* ty,
-                     float* out, cudaStream_t st) {
-    k_project<float, float2><<<nblk, 32 * kProjViews, 0, st>>>(dsl, map, tx, ty, out);
+void launch_project1(const SliceDesc* dsl, const BlockMap& map, int nblk, const int4* groups, const float2* tx,
+                     const float2* ty, float* out, cudaStream_t st) {
+    k_project<float, float2><<<nblk, 32 * kProjViews, 0, st>>>(dsl, map, groups, tx, ty, out);
 }
+
+int proj_group_size() { return kProjGroup; }
 
 // ---------------------------------------------------------------------------------------------
 // single-slice planar entry points (dect_project / dect_backproject)
