@@ -138,9 +138,10 @@ def joseph_weight_count(g) -> int:
 
 
 # DRAM bytes per launch of the backprojector sweep at the bench workload (8 slices), keyed by the launch
-# shape they were captured with (slices, view groups, tile side, cluster form); from the counter capture
+# shape they were captured with (slices, view groups, tile side, cluster form, slices per CTA); from the
+# counter capture
 # in profiles/k_bp_sweep_512x720x1024.txt. Reported only when the run uses that shape.
-SWEEP_TRAFFIC = {(8, 8, 32, 0): 134.0e6}
+SWEEP_TRAFFIC = {(8, 8, 32, 0, 1): 134.0e6}
 
 
 # ------------------------------------------------------------------------------------------------
@@ -378,7 +379,7 @@ def run_dect(args):
     cfg = {"workload": "fan 512x512, 720 views x 1024 bins, 40 objects, I0 2e5, UDM1-PCG1 x 100 + init",
            "iterations_fixed": ITERS, "batch_per_gpu": B, "l2": "flushed between steps (512 MB write)",
            "storage": args.storage, "bp_view_groups": st0["bp_view_groups"], "bp_tile": st0["bp_tile"],
-           "bp_cluster": st0["bp_cluster"]}
+           "bp_cluster": st0["bp_cluster"], "bp_slices": st0["bp_slices"]}
     phases = _phase_ms(sol, 10)
     for p_, ms in phases.items():
         cfg[f"{args.storage}_ms_{p_}"] = round(ms, 4)
@@ -466,7 +467,7 @@ def run_dect(args):
     pr_ms, pr_tf, pr_gbs, pr_bytes = kernel_roof("project", 1)
     cfg.update({"project_tflops": pr_tf, "project_tflops_frac": pr_tf / fp32_peak, "project_hbm_gbs": pr_gbs,
                 "project_hbm_frac": pr_gbs / peak, "backproject_hbm_frac": bp_gbs / peak})
-    traffic = SWEEP_TRAFFIC.get((B, st0["bp_view_groups"], st0["bp_tile"], st0["bp_cluster"]))
+    traffic = SWEEP_TRAFFIC.get((B, st0["bp_view_groups"], st0["bp_tile"], st0["bp_cluster"], st0["bp_slices"]))
     roof = {"kernel": "backproject" if top == "backproject" else top, "bound": "alu", "achieved": bp_tf,
             "peak": fp32_peak, "unit": "TFLOP/s", "frac": bp_tf / fp32_peak,
             "traffic": traffic, "traffic_source": "stored ncu capture of this kernel and launch shape "

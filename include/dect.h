@@ -316,6 +316,10 @@ typedef struct {
                                     into one partial image, instead of C partial images through L2 / DRAM:
                                     1 on (2 <= view groups <= 16), -1 off, 0 (default) timed by the autotuner
                                     against the plain form. Both forms give the same bits. */
+    int32_t bp_slices;           /* slices per backprojector CTA: 2 backprojects the same rays into two
+                                    consecutive slices of one geometry at once (shared staging and sample
+                                    positions, one accumulator per slice; UDM-PCG scheme), 1 one slice,
+                                    0 (default) timed by the autotuner. Same bits either way. */
 } dect_params;
 
 /* Fills *p with the paper's values and the defaults above. */
@@ -376,6 +380,7 @@ typedef struct {
     int32_t objective_iteration; /* see dect_params.objective_every; -1 if never evaluated */
     int32_t bp_tile;             /* backprojector tile side in use (0 for float64 storage) */
     int32_t bp_cluster;          /* 1 if the backprojector's view groups reduce on chip (see bp_cluster) */
+    int32_t bp_slices;           /* slices per backprojector CTA in use (see bp_slices; 0 for float64) */
 } dect_stats;
 dect_status dect_admm_stats(dect_admm* a, int32_t slice, dect_stats* out, void* stream);
 

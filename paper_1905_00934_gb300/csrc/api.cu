@@ -519,6 +519,7 @@ extern "C" void dect_params_default(dect_params* p) {
     p->objective_every = 0;
     p->bp_tile = 0;
     p->bp_cluster = 0;
+    p->bp_slices = 0;
 }
 
 struct MapBuf {
@@ -542,6 +543,11 @@ struct dect_admm {
     int sweep_tile = kSweepTileDefault;  // backprojector tile side (32 or 64; does not change results)
     bool sweep_cluster = false;      // the view groups of a tile reduce on chip into one partial image
     std::vector<int> cluster_cands;  // cluster forms the autotuner may time (0 off, 1 on)
+    int sweep_sg = 1;                // slices per sweep CTA (2: pairs of consecutive slices of one geometry)
+    std::vector<int> sg_cands;       // slices per CTA the autotuner may time
+    std::vector<int4> sgroups;       // the pairs (second -1 for a slice without a partner)
+    int4* d_sgroups = nullptr;
+    int sweep_units() const { return sweep_sg == 2 ? (int)sgroups.size() : B; }
     int bp_parts() const { return sweep_cluster ? 1 : sweep_C; }  // partial images the finalize pass reads
     int sweep_groups_in_use = 1;     // view groups per tile (sweep_C CTAs of the kernel's groups each)
     float2* bp_partial = nullptr;    // [sweep_C][n_img] partial images of the backprojector
@@ -615,6 +621,7 @@ static void pe(dect_admm* A, int phase, int nk, cudaStream_t st) {
 
 static void free_admm(dect_admm* A) {
     void* ptrs[] = {A->ds, A->rays.d, A->pix.d, A->tx.d, A->ty.d, A->rows.d, A->cols.d, A->sweep.d, A->ptile.d, A->d_groups,
+                    A->d_sgroups,
                     A->bp_partial, A->x, A->r, A->s,
                     A->p, A->Ap, A->z, A->uz, A->x0, A->truth, A->Rx, A->a, A->ua, A->q, A->Z, A->y, A->uy,
                     A->meas, A->txb, A->tyb, A->mu, A->H, A->Hn, A->stage, A->status, A->sc, A->part_udm,
@@ -683,7 +690,8 @@ static void enq_pcg(dect_admm* A, int n, bool with_grad, const float* H, cudaStr
     launch_sino_resid(A->ds, A->rays.map(B), A->rays.total, A->a, A->ua, A->Rx, A->q, A->prec, st);
     pe(A, DECT_PHASE_UPDATE, 1, st);
     pb(A, st);
-    launch_bp_sweep(A->ds, A->sweep.map(B), A->sweep.total, A->sweep_C, A->sweep_tile, A->sweep_cluster, A->q, A->bp_partial, A->n_img, A->prec, st);
+    launch_bp_sweep(A->ds, A->sweep.map(A->sweep_units()), A->sweep.total, A->sweep_C, A->sweep_tile, A->sweep_cluster,
+                    A->sweep_sg, A->d_sgroups, A->q, A->bp_partial, A->n_img, A->prec, st);
     pe(A, DECT_PHASE_BACKPROJECT, 1, st);
     pb(A, st);
     launch_bp_finalize(with_grad ? BP_R0 : BP_R0_NOGRAD, A->ds, A->pix.map(B), A->pix.total, A->bp_parts(),
@@ -697,7 +705,8 @@ static void enq_pcg(dect_admm* A, int n, bool with_grad, const float* H, cudaStr
     for (int it = 0; it < n; ++it) {
         enq_project(A, A->p, A->q, st);
         pb(A, st);
-        launch_bp_sweep(A->ds, A->sweep.map(B), A->sweep.total, A->sweep_C, A->sweep_tile, A->sweep_cluster, A->q, A->bp_partial, A->n_img, A->prec,
+        launch_bp_sweep(A->ds, A->sweep.map(A->sweep_units()), A->sweep.total, A->sweep_C, A->sweep_tile, A->sweep_cluster,
+                    A->sweep_sg, A->d_sgroups, A->q, A->bp_partial, A->n_img, A->prec,
                         st);
         pe(A, DECT_PHASE_BACKPROJECT, 1, st);
         pb(A, st);
@@ -1121,10 +1130,14 @@ static dect_status enq_initialize(dect_admm* A, cudaStream_t st) {
 
 // ---- creation ------------------------------------------------------------------------------------
 
-// Sweep block map for C CTA groups per TILE x TILE tile (prefix over slices)
-static void sweep_prefix(const dect_admm* A, int C, int tile, std::vector<int>& h) {
+// Sweep block map for C CTA groups per TILE x TILE tile (prefix over slices, or over slice pairs for sg = 2)
+static void sweep_prefix(const dect_admm* A, int C, int tile, int sg, std::vector<int>& h) {
     h.assign(1, 0);
-    for (int b = 0; b < A->B; ++b) h.push_back(h.back() + sweep_tiles(A->hs[b].g.nx, A->hs[b].g.ny, tile) * C);
+    if (sg == 2)
+        for (const int4& p : A->sgroups)
+            h.push_back(h.back() + sweep_tiles(A->hs[p.x].g.nx, A->hs[p.x].g.ny, tile) * C);
+    else
+        for (int b = 0; b < A->B; ++b) h.push_back(h.back() + sweep_tiles(A->hs[b].g.nx, A->hs[b].g.ny, tile) * C);
 }
 
 // Times the backprojector sweep on this batch for each candidate (tile side, C) (on a zero sinogram; the
@@ -1137,52 +1150,57 @@ static cudaError_t autotune_sweep(dect_admm* A, const std::vector<int>& cands, c
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (e == cudaSuccess) e = cudaEventCreate(&e0);
     if (e == cudaSuccess) e = cudaEventCreate(&e1);
-    int best = cands[0], best_tile = tiles[0];
+    int best = cands[0], best_tile = tiles[0], best_sg = 1;
     bool best_cluster = false;
     float best_ms = 0.f;
     bool first = true;
     std::vector<int> h;
-    for (int tile : tiles)
-        for (size_t k = 0; k < cands.size() && e == cudaSuccess; ++k)
-            for (int cl : A->cluster_cands) {
-                if (e != cudaSuccess) break;
-                const int C = cands[k];
-                const bool cluster = cl == 1;
-                if (cluster && (C < 2 || C > 16)) continue;
-                sweep_prefix(A, C, tile, h);
-                e = cudaMemcpy(A->sweep.d, h.data(), sizeof(int) * h.size(), cudaMemcpyHostToDevice);
-                const BlockMap m{A->sweep.d, A->B};
-                // a cluster shape the device cannot schedule is reported at launch: skip that candidate
-                launch_bp_sweep(A->ds, m, h.back(), C, tile, cluster, A->q, A->bp_partial, A->n_img, A->prec, st);
-                if (cluster && cudaGetLastError() != cudaSuccess) continue;
-                for (int w = 0; w < 1 && e == cudaSuccess; ++w) {  // warm-up
-                    launch_bp_sweep(A->ds, m, h.back(), C, tile, cluster, A->q, A->bp_partial, A->n_img, A->prec, st);
+    for (int sg : A->sg_cands)
+        for (int tile : tiles)
+            for (size_t k = 0; k < cands.size() && e == cudaSuccess; ++k)
+                for (int cl : A->cluster_cands) {
+                    if (e != cudaSuccess) break;
+                    const int C = cands[k];
+                    const bool cluster = cl == 1;
+                    if (cluster && (C < 2 || C > 16 || sg != 1)) continue;
+                    sweep_prefix(A, C, tile, sg, h);
+                    e = cudaMemcpy(A->sweep.d, h.data(), sizeof(int) * h.size(), cudaMemcpyHostToDevice);
+                    const BlockMap m{A->sweep.d, sg == 2 ? (int)A->sgroups.size() : A->B};
+                    auto run = [&]() {
+                        launch_bp_sweep(A->ds, m, h.back(), C, tile, cluster, sg, A->d_sgroups, A->q, A->bp_partial,
+                                        A->n_img, A->prec, st);
+                    };
+                    // a cluster shape the device cannot schedule is reported at launch: skip that candidate
+                    run();
+                    if (cluster && cudaGetLastError() != cudaSuccess) continue;
+                    run();  // warm-up
                     e = cudaGetLastError();
+                    if (e == cudaSuccess) e = cudaEventRecord(e0, st);
+                    for (int r = 0; r < 3 && e == cudaSuccess; ++r) {
+                        run();
+                        e = cudaGetLastError();
+                    }
+                    if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+                    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+                    float ms = 0.f;
+                    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+                    if (e == cudaSuccess && (first || ms < 0.99f * best_ms || (ms <= best_ms && C < best))) {
+                        best = C;
+                        best_tile = tile;
+                        best_cluster = cluster;
+                        best_sg = sg;
+                        best_ms = ms;
+                        first = false;
+                    }
                 }
-                if (e == cudaSuccess) e = cudaEventRecord(e0, st);
-                for (int r = 0; r < 3 && e == cudaSuccess; ++r) {
-                    launch_bp_sweep(A->ds, m, h.back(), C, tile, cluster, A->q, A->bp_partial, A->n_img, A->prec, st);
-                    e = cudaGetLastError();
-                }
-                if (e == cudaSuccess) e = cudaEventRecord(e1, st);
-                if (e == cudaSuccess) e = cudaEventSynchronize(e1);
-                float ms = 0.f;
-                if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
-                if (e == cudaSuccess && (first || ms < 0.99f * best_ms || (ms <= best_ms && C < best))) {
-                    best = C;
-                    best_tile = tile;
-                    best_cluster = cluster;
-                    best_ms = ms;
-                    first = false;
-                }
-            }
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
     if (e != cudaSuccess) return e;
     A->sweep_C = best;
     A->sweep_tile = best_tile;
     A->sweep_cluster = best_cluster;
-    sweep_prefix(A, best, best_tile, A->sweep.h);
+    A->sweep_sg = best_sg;
+    sweep_prefix(A, best, best_tile, best_sg, A->sweep.h);
     A->sweep.total = A->sweep.h.back();
     e = cudaMemcpy(A->sweep.d, A->sweep.h.data(), sizeof(int) * A->sweep.h.size(), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return e;
@@ -1309,6 +1327,8 @@ extern "C" dect_status dect_admm_create(dect_geom* const* geoms, int32_t B, cons
         DECT_FAIL(DECT_EINVAL, "dect_admm_create: bp_tile must be 0 (autotuned), 32 or 64");
     if (P->bp_cluster < -1 || P->bp_cluster > 1)
         DECT_FAIL(DECT_EINVAL, "dect_admm_create: bp_cluster must be -1 (off), 0 (autotuned) or 1 (on)");
+    if (P->bp_slices < 0 || P->bp_slices > 2)
+        DECT_FAIL(DECT_EINVAL, "dect_admm_create: bp_slices must be 0 (autotuned), 1 or 2");
     if (P->init != DECT_INIT_PCG && P->init != DECT_INIT_CDM_FBP)
         DECT_FAIL(DECT_EINVAL, "dect_admm_create: init must be DECT_INIT_PCG or DECT_INIT_CDM_FBP");
     if (P->init == DECT_INIT_CDM_FBP)
@@ -1363,6 +1383,23 @@ extern "C" dect_status dect_admm_create(dect_geom* const* geoms, int32_t B, cons
         A->sweep_tile = tile0;
         if (P->bp_cluster == 0) A->cluster_cands = {0, 1};
         else A->cluster_cands = {P->bp_cluster > 0 ? 1 : 0};
+        // pairs of consecutive slices of one geometry for the two-slice sweep (UDM-PCG only: the comparison
+        // scheme backprojects one basis with its own weights)
+        bool pairs = false;
+        for (int b = 0; b < B; ++b) {
+            if (!A->sgroups.empty() && A->sgroups.back().y < 0 &&
+                same_geometry(geoms[A->sgroups.back().x]->desc, geoms[b]->desc)) {
+                A->sgroups.back().y = b;
+                pairs = true;
+            } else {
+                A->sgroups.push_back(make_int4(b, -1, -1, -1));
+            }
+        }
+        const bool sg_ok = pairs && P->scheme == DECT_SCHEME_UDM_PCG && P->storage != DECT_STORE_F64;
+        if (P->bp_slices == 2 && sg_ok) A->sg_cands = {2};
+        else if (P->bp_slices == 0 && sg_ok) A->sg_cands = {1, 2};
+        else A->sg_cands = {1};
+        A->sweep_sg = A->sg_cands.size() == 1 ? A->sg_cands[0] : 1;
         if (P->storage == DECT_STORE_F64) {
             A->sweep_C = 1;  // the float64 path has its own backprojector; no sweep, no partial images
         } else if (P->bp_view_groups > 0) {
@@ -1424,13 +1461,14 @@ extern "C" dect_status dect_admm_create(dect_geom* const* geoms, int32_t B, cons
         A->pix.h.push_back(A->pix.h.back() + (int)((np + 255) / 256));
         A->tx.h.push_back(A->tx.h.back() + texture_x_blocks(nx, ny));
         A->ty.h.push_back(A->ty.h.back() + texture_y_blocks(nx, ny));
-        A->sweep.h.push_back(A->sweep.h.back() + sweep_tiles(nx, ny, A->sweep_tile) * A->sweep_C);
+
         A->rows.h.push_back(A->rows.h.back() + ny);
         const int C = precond_cols_per_block(sd.py);
         A->cols.h.push_back(A->cols.h.back() + (sd.px + C - 1) / C);
         A->cols64.h.push_back(A->cols64.h.back() + sd.px);
     }
     A->n_stage = std::max(4 * max_nr + 4 * max_np, (int64_t)16);
+    sweep_prefix(A, A->sweep_C, A->sweep_tile, A->sweep_sg, A->sweep.h);
     // projector groups: a slice joins the previous group when that has room and the same geometry
     std::vector<int4> groups;
     std::vector<int> gsize;
@@ -1515,6 +1553,9 @@ extern "C" dect_status dect_admm_create(dect_geom* const* geoms, int32_t B, cons
     for (MapBuf* m : {&A->rays, &A->pix, &A->tx, &A->ty, &A->rows, &A->cols, &A->sweep, &A->cols64, &A->ptile})
         if (e == cudaSuccess) e = upload_map(*m);
     if (e == cudaSuccess) e = dalloc(&A->d_groups, groups.size());
+    if (e == cudaSuccess) e = dalloc(&A->d_sgroups, A->sgroups.size());
+    if (e == cudaSuccess)
+        e = cudaMemcpy(A->d_sgroups, A->sgroups.data(), sizeof(int4) * A->sgroups.size(), cudaMemcpyHostToDevice);
     if (e == cudaSuccess)
         e = cudaMemcpy(A->d_groups, groups.data(), sizeof(int4) * groups.size(), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(A->ds, A->hs.data(), sizeof(SliceDesc) * B, cudaMemcpyHostToDevice);
@@ -1531,7 +1572,8 @@ extern "C" dect_status dect_admm_create(dect_geom* const* geoms, int32_t B, cons
         return e == cudaErrorMemoryAllocation ? DECT_ENOMEM : DECT_ECUDA;
     }
     if (A->prec != PREC_F64 && !tune.empty() &&
-        (tune.size() > 1 || tune_tiles.size() > 1 || (A->cluster_cands.size() > 1 && tune[0] >= 2)))
+        (tune.size() > 1 || tune_tiles.size() > 1 || A->sg_cands.size() > 1 ||
+         (A->cluster_cands.size() > 1 && tune[0] >= 2)))
         e = autotune_sweep(A, tune, tune_tiles);
     else if (A->prec != PREC_F64)
         A->sweep_cluster = P->bp_cluster > 0 && A->sweep_C >= 2 && A->sweep_C <= 16;
@@ -1996,5 +2038,6 @@ extern "C" dect_status dect_admm_stats(dect_admm* A, int32_t b, dect_stats* out,
     out->objective_iteration = v.objective_iter;
     out->bp_tile = A->prec == PREC_F64 ? 0 : A->sweep_tile;
     out->bp_cluster = A->sweep_cluster ? 1 : 0;
+    out->bp_slices = A->prec == PREC_F64 ? 0 : A->sweep_sg;
     return DECT_OK;
 }

@@ -52,10 +52,11 @@ struct SweepShape {
     static constexpr int kThreads = 32 * kWarps;
 };
 
-// shared-memory bytes of a CTA's accumulators (dynamic shared memory)
-template <int TILE, int NCH>
+// shared-memory bytes of a CTA's accumulators (dynamic shared memory), SG slices per CTA
+template <int TILE, int NCH, int SG = 1>
 constexpr size_t sweep_acc_bytes() {
-    return (size_t)SweepShape<TILE>::kWarps * SweepShape<TILE>::kRows * 32 * (NCH == 2 ? sizeof(float2) : sizeof(float));
+    return (size_t)SG * SweepShape<TILE>::kWarps * SweepShape<TILE>::kRows * 32 *
+           (NCH == 2 ? sizeof(float2) : sizeof(float));
 }
 
 // NCH = 2: sinogram S2 pairs {c, p}, float2 accumulators and partial images. NCH = 1: float sinogram,
@@ -65,20 +66,38 @@ constexpr size_t sweep_acc_bytes() {
 // accumulators through distributed shared memory, in rank order, into one partial image (image 0);
 // the sum per pixel is the one the finalize pass forms from C partial images (0 + p_0 + p_1 + ...),
 // so both launch forms give the same bits, and only one image per tile goes through L2 and DRAM.
-template <class S2, int NCH, int TILE, bool CLUSTER = false>
+// SG = 2: a CTA backprojects the same rays into two slices of one geometry (their indices in
+// groups[unit], the second -1 if the group has one slice): staging, candidate search and sample
+// positions are done once, each slice has its own accumulators, and each slice's pixels receive the
+// same contributions in the same order as with SG = 1 (the same bits). NCH = 2, plain form only.
+template <class S2, int NCH, int TILE, bool CLUSTER = false, int SG = 1>
 __global__ void __launch_bounds__(SweepShape<TILE>::kThreads) k_bp_sweep(
-    const SliceDesc* __restrict__ dsl, BlockMap map, int C, const S2* __restrict__ sino,
-    typename std::conditional<NCH == 2, float2, float>::type* __restrict__ partial, int64_t stride,
-    const float* __restrict__ rw, const float* __restrict__ scale) {
+    const SliceDesc* __restrict__ dsl, BlockMap map, int C, const int4* __restrict__ groups,
+    const S2* __restrict__ sino, typename std::conditional<NCH == 2, float2, float>::type* __restrict__ partial,
+    int64_t stride, const float* __restrict__ rw, const float* __restrict__ scale) {
+    static_assert(SG == 1 || (SG == 2 && NCH == 2 && !CLUSTER), "two slices per CTA: two channels, plain form");
     using Acc = typename std::conditional<NCH == 2, float2, float>::type;
     using Sh = SweepShape<TILE>;
-    // [warp][across index + 1][lane]: [row][column] for axis 0, [column][row] for axis 1
+    // [slice][warp][across index + 1][lane]: [row][column] for axis 0, [column][row] for axis 1
     extern __shared__ __align__(16) unsigned char sweep_smem[];
-    Acc(*acc)[Sh::kRows][32] = reinterpret_cast<Acc(*)[Sh::kRows][32]>(sweep_smem);
+    Acc(*acc_all)[Sh::kWarps][Sh::kRows][32] = reinterpret_cast<Acc(*)[Sh::kWarps][Sh::kRows][32]>(sweep_smem);
+    Acc(*acc)[Sh::kRows][32] = acc_all[0];
     __shared__ int4 st_ray[Sh::kWarps][32];                 // {position lo, position hi, slope, w s_c}
-    __shared__ __align__(16) float st_wp[Sh::kWarps][32];   // w s_p
+    __shared__ __align__(16) float st_wp[Sh::kWarps][32];   // w s_p (SG = 1)
+    __shared__ float4 st_w2[SG == 2 ? Sh::kWarps : 1][32];   // {w s_p, w s_c, w s_p of the second slice} (SG = 2)
     int local;
-    const int s = slice_of(map, blockIdx.x, local);
+    const int unit = slice_of(map, blockIdx.x, local);
+    int sl[SG];
+    int count = 1;
+    if constexpr (SG == 1) {
+        sl[0] = unit;
+    } else {
+        const int4 gs = __ldg(groups + unit);
+        sl[0] = gs.x;
+        sl[1] = gs.y >= 0 ? gs.y : gs.x;
+        count = gs.y >= 0 ? 2 : 1;
+    }
+    const int s = sl[0];
     const SliceDesc& d = dsl[s];
     const GeomDev& g = d.g;
     const int nx = g.nx, ny = g.ny;
@@ -88,7 +107,9 @@ __global__ void __launch_bounds__(SweepShape<TILE>::kThreads) k_bp_sweep(
     const int w = threadIdx.x / 32, lane = threadIdx.x % 32;
     const bool my_axis = w >= Sh::kBands;
     const int band = w % Sh::kBands;
-    for (int r = 0; r < Sh::kRows; ++r) acc[w][r][lane] = Acc{};
+#pragma unroll
+    for (int q = 0; q < SG; ++q)
+        for (int r = 0; r < Sh::kRows; ++r) acc_all[q][w][r][lane] = Acc{};
     const int G = C, grp = c;
     // this warp's band: 32 sampled indices from bi (columns for axis 0, rows for axis 1) by the tile's
     // TILE across indices from ba; rays with a weight at its in-image pixels pass within one pixel of
@@ -102,6 +123,7 @@ __global__ void __launch_bounds__(SweepShape<TILE>::kThreads) k_bp_sweep(
     const float xc = (0.5f * (float)(i0 + i1) - g.cx) * g.pix, yc = (0.5f * (float)(j0 + j1) - g.cy) * g.pix;
     const float hx = (0.5f * (float)(i1 - i0) + 1.0f) * g.pix, hy = (0.5f * (float)(j1 - j0) + 1.0f) * g.pix;
     const S2* sn = sino + d.sino_off;
+    const S2* sn1 = sino + dsl[sl[SG - 1]].sino_off;  // the second slice's sinogram (SG = 2)
     const long long a0q = (long long)ba << 30;
 
     // chunk cursor: view v, first bin k0 of the chunk, last candidate bin khi of the view
@@ -119,7 +141,7 @@ __global__ void __launch_bounds__(SweepShape<TILE>::kThreads) k_bp_sweep(
     };
     if (!empty) seek(grp);
     int4 P = make_int4(0, 0, 0, 0);
-    float2 sv = make_float2(0.f, 0.f);
+    float2 sv = make_float2(0.f, 0.f), sv1 = make_float2(0.f, 0.f);
     bool have = false;
     auto fetch = [&]() {
         const int k = k0 + lane;
@@ -129,6 +151,7 @@ __global__ void __launch_bounds__(SweepShape<TILE>::kThreads) k_bp_sweep(
             P = __ldg(g.rays + e);
             if constexpr (NCH == 2) {
                 sv = ldg2(sn + e);
+                if constexpr (SG == 2) sv1 = count > 1 ? ldg2(sn1 + e) : make_float2(0.f, 0.f);
             } else {
                 sv.x = __ldg(sn + e);
                 if (rw) sv.x *= __ldg(rw + d.sino_off + e);
@@ -147,12 +170,18 @@ __global__ void __launch_bounds__(SweepShape<TILE>::kThreads) k_bp_sweep(
             const float wr = ray_w(P) * sscale;
             const int at = __popc(mask & ((1u << lane) - 1u));
             st_ray[w][at] = make_int4((int)(unsigned)(unsigned long long)q, (int)(q >> 32), P.z, __float_as_int(wr * sv.x));
-            st_wp[w][at] = wr * sv.y;
+            if constexpr (SG == 1)
+                st_wp[w][at] = wr * sv.y;
+            else
+                st_w2[w][at] = make_float4(wr * sv.y, wr * sv1.x, wr * sv1.y, 0.f);
         }
         const int nr = (n + kSwUnroll - 1) / kSwUnroll * kSwUnroll;
         if (lane >= n && lane < nr) {  // null rays pad the stage to a multiple of kSwUnroll
             st_ray[w][lane] = make_int4(0, -1000 << 2, 0, 0);
-            st_wp[w][lane] = 0.f;
+            if constexpr (SG == 1)
+                st_wp[w][lane] = 0.f;
+            else
+                st_w2[w][lane] = make_float4(0.f, 0.f, 0.f, 0.f);
         }
         // advance the cursor and fetch the next chunk while this one is processed
         k0 += 32;
@@ -162,7 +191,7 @@ __global__ void __launch_bounds__(SweepShape<TILE>::kThreads) k_bp_sweep(
         for (int r0 = 0; r0 < nr; r0 += kSwUnroll) {
             int hh[kSwUnroll];
             float ff[kSwUnroll], wc[kSwUnroll], wp[kSwUnroll];
-            if constexpr (NCH == 2) {  // w s_p of the block's rays: two broadcast 16-byte loads
+            if constexpr (NCH == 2 && SG == 1) {  // w s_p of the block's rays: two broadcast 16-byte loads
                 const float4 p0 = *reinterpret_cast<const float4*>(&st_wp[w][r0]);
                 const float4 p1 = *reinterpret_cast<const float4*>(&st_wp[w][r0 + 4]);
                 wp[0] = p0.x; wp[1] = p0.y; wp[2] = p0.z; wp[3] = p0.w;
@@ -175,6 +204,34 @@ __global__ void __launch_bounds__(SweepShape<TILE>::kThreads) k_bp_sweep(
                 hh[u] = pos_floor(q);
                 ff[u] = frac_of(q);
                 wc[u] = __int_as_float(S.w);
+            }
+            if constexpr (SG == 2) {
+                // the second slice: its weights per ray; both slices' updates of a ray are independent
+#pragma unroll
+                for (int u = 0; u < kSwUnroll; ++u) {
+                    const float4 x = st_w2[w][r0 + u];
+                    const float wc1 = x.y, wp1 = x.z;
+                    wp[u] = x.x;
+                    if ((unsigned)(hh[u] + 1) < (unsigned)(TILE + 1)) {
+                        float2* a = &acc_all[0][w][hh[u] + 1][lane];
+                        float2* b = &acc_all[1][w][hh[u] + 1][lane];
+                        float2 x0 = a[0], x1 = a[32];
+                        float2 y0 = b[0], y1 = b[32];
+                        x0.x = fmaf(1.0f - ff[u], wc[u], x0.x);
+                        x0.y = fmaf(1.0f - ff[u], wp[u], x0.y);
+                        x1.x = fmaf(ff[u], wc[u], x1.x);
+                        x1.y = fmaf(ff[u], wp[u], x1.y);
+                        y0.x = fmaf(1.0f - ff[u], wc1, y0.x);
+                        y0.y = fmaf(1.0f - ff[u], wp1, y0.y);
+                        y1.x = fmaf(ff[u], wc1, y1.x);
+                        y1.y = fmaf(ff[u], wp1, y1.y);
+                        a[0] = x0;
+                        a[32] = x1;
+                        b[0] = y0;
+                        b[32] = y1;
+                    }
+                }
+                continue;
             }
 #pragma unroll
             for (int u = 0; u < kSwUnroll; ++u) {
@@ -224,19 +281,23 @@ __global__ void __launch_bounds__(SweepShape<TILE>::kThreads) k_bp_sweep(
         }
         cl.sync();  // the peers' shared memory stays valid until every rank has read it
     } else {
-        for (int px = threadIdx.x; px < TILE * TILE; px += blockDim.x) {
-            const int rr = px / TILE, cc = px % TILE;
-            const int i = ti + cc, j = tj + rr;
-            if (i < nx && j < ny) {
-                const Acc a = acc[cc / 32][rr + 1][cc % 32], b = acc[Sh::kBands + rr / 32][cc + 1][rr % 32];
-                Acc sum{};
-                if constexpr (NCH == 2) {
-                    sum.x += a.x + b.x;
-                    sum.y += a.y + b.y;
-                } else {
-                    sum += a + b;
+        for (int q = 0; q < count; ++q) {
+            Acc(*aq)[Sh::kRows][32] = acc_all[q];
+            const int64_t off = c * stride + dsl[sl[q]].img_off;
+            for (int px = threadIdx.x; px < TILE * TILE; px += blockDim.x) {
+                const int rr = px / TILE, cc = px % TILE;
+                const int i = ti + cc, j = tj + rr;
+                if (i < nx && j < ny) {
+                    const Acc a = aq[cc / 32][rr + 1][cc % 32], b = aq[Sh::kBands + rr / 32][cc + 1][rr % 32];
+                    Acc sum{};
+                    if constexpr (NCH == 2) {
+                        sum.x += a.x + b.x;
+                        sum.y += a.y + b.y;
+                    } else {
+                        sum += a + b;
+                    }
+                    partial[off + (size_t)j * nx + i] = sum;
                 }
-                partial[c * stride + d.img_off + (size_t)j * nx + i] = sum;
             }
         }
     }
@@ -276,10 +337,11 @@ int sweep_groups_per_cta() { return 1; }
 static std::mutex g_slots_mu;
 static std::vector<int> g_slots[2];  // resident CTA slots of k_bp_sweep per device, TILE 32 and 64
 
-template <class S2, int NCH, int TILE, bool CLUSTER>
+template <class S2, int NCH, int TILE, bool CLUSTER, int SG>
 static cudaError_t sweep_attr1() {
-    auto* k = k_bp_sweep<S2, NCH, TILE, CLUSTER>;
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sweep_acc_bytes<TILE, NCH>());
+    auto* k = k_bp_sweep<S2, NCH, TILE, CLUSTER, SG>;
+    cudaError_t e =
+        cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sweep_acc_bytes<TILE, NCH, SG>());
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
     if (e == cudaSuccess && CLUSTER) e = cudaFuncSetAttribute(k, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
     return e;
@@ -287,8 +349,10 @@ static cudaError_t sweep_attr1() {
 
 template <class S2, int NCH, int TILE>
 static cudaError_t sweep_attr() {
-    cudaError_t e = sweep_attr1<S2, NCH, TILE, false>();
-    if (e == cudaSuccess) e = sweep_attr1<S2, NCH, TILE, true>();
+    cudaError_t e = sweep_attr1<S2, NCH, TILE, false, 1>();
+    if (e == cudaSuccess) e = sweep_attr1<S2, NCH, TILE, true, 1>();
+    if constexpr (NCH == 2)
+        if (e == cudaSuccess) e = sweep_attr1<S2, NCH, TILE, false, 2>();
     return e;
 }
 
@@ -338,12 +402,19 @@ int sweep_groups(int tiles, int tile) {
 }
 
 template <class S2, int NCH, int TILE>
-static void sweep_t(const SliceDesc* dsl, const BlockMap& smap, int nsweep, int C, bool cluster, const S2* sino,
-                    typename std::conditional<NCH == 2, float2, float>::type* partial, int64_t stride,
-                    const float* rw, const float* scale, cudaStream_t st) {
+static void sweep_t(const SliceDesc* dsl, const BlockMap& smap, int nsweep, int C, bool cluster, int sg,
+                    const int4* groups, const S2* sino, typename std::conditional<NCH == 2, float2, float>::type* partial,
+                    int64_t stride, const float* rw, const float* scale, cudaStream_t st) {
+    if constexpr (NCH == 2) {
+        if (sg == 2) {
+            k_bp_sweep<S2, NCH, TILE, false, 2><<<nsweep, SweepShape<TILE>::kThreads, sweep_acc_bytes<TILE, NCH, 2>(), st>>>(
+                dsl, smap, C, groups, sino, partial, stride, rw, scale);
+            return;
+        }
+    }
     if (!cluster || C == 1) {
         k_bp_sweep<S2, NCH, TILE><<<nsweep, SweepShape<TILE>::kThreads, sweep_acc_bytes<TILE, NCH>(), st>>>(
-            dsl, smap, C, sino, partial, stride, rw, scale);
+            dsl, smap, C, nullptr, sino, partial, stride, rw, scale);
         return;
     }
     // the C CTAs of a tile are consecutive blocks and every slice's block range is a multiple of C,
@@ -360,28 +431,34 @@ static void sweep_t(const SliceDesc* dsl, const BlockMap& smap, int nsweep, int 
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    cudaLaunchKernelEx(&cfg, k_bp_sweep<S2, NCH, TILE, true>, dsl, smap, C, sino, partial, stride, rw, scale);
+    const int4* no_groups = nullptr;
+    cudaLaunchKernelEx(&cfg, k_bp_sweep<S2, NCH, TILE, true>, dsl, smap, C, no_groups, sino, partial, stride, rw,
+                       scale);
 }
 
-void launch_bp_sweep(const SliceDesc* dsl, const BlockMap& smap, int nsweep, int C, int tile, bool cluster,
-                     const void* sino, float2* partial, int64_t stride, int prec, cudaStream_t st) {
+void launch_bp_sweep(const SliceDesc* dsl, const BlockMap& smap, int nsweep, int C, int tile, bool cluster, int sg,
+                     const int4* groups, const void* sino, float2* partial, int64_t stride, int prec, cudaStream_t st) {
     const bool k = cluster;
     if (tile == 64) {
         if (prec == PREC_F16)
-            sweep_t<__half2, 2, 64>(dsl, smap, nsweep, C, k, (const __half2*)sino, partial, stride, nullptr, nullptr, st);
+            sweep_t<__half2, 2, 64>(dsl, smap, nsweep, C, k, sg, groups, (const __half2*)sino, partial, stride, nullptr,
+                                    nullptr, st);
         else if (prec == PREC_BF16)
-            sweep_t<__nv_bfloat162, 2, 64>(dsl, smap, nsweep, C, k, (const __nv_bfloat162*)sino, partial, stride,
-                                           nullptr, nullptr, st);
+            sweep_t<__nv_bfloat162, 2, 64>(dsl, smap, nsweep, C, k, sg, groups, (const __nv_bfloat162*)sino, partial,
+                                           stride, nullptr, nullptr, st);
         else
-            sweep_t<float2, 2, 64>(dsl, smap, nsweep, C, k, (const float2*)sino, partial, stride, nullptr, nullptr, st);
+            sweep_t<float2, 2, 64>(dsl, smap, nsweep, C, k, sg, groups, (const float2*)sino, partial, stride, nullptr,
+                                   nullptr, st);
     } else {
         if (prec == PREC_F16)
-            sweep_t<__half2, 2, 32>(dsl, smap, nsweep, C, k, (const __half2*)sino, partial, stride, nullptr, nullptr, st);
+            sweep_t<__half2, 2, 32>(dsl, smap, nsweep, C, k, sg, groups, (const __half2*)sino, partial, stride, nullptr,
+                                    nullptr, st);
         else if (prec == PREC_BF16)
-            sweep_t<__nv_bfloat162, 2, 32>(dsl, smap, nsweep, C, k, (const __nv_bfloat162*)sino, partial, stride,
-                                           nullptr, nullptr, st);
+            sweep_t<__nv_bfloat162, 2, 32>(dsl, smap, nsweep, C, k, sg, groups, (const __nv_bfloat162*)sino, partial,
+                                           stride, nullptr, nullptr, st);
         else
-            sweep_t<float2, 2, 32>(dsl, smap, nsweep, C, k, (const float2*)sino, partial, stride, nullptr, nullptr, st);
+            sweep_t<float2, 2, 32>(dsl, smap, nsweep, C, k, sg, groups, (const float2*)sino, partial, stride, nullptr,
+                                   nullptr, st);
     }
 }
 
@@ -389,9 +466,9 @@ void launch_bp_sweep1(const SliceDesc* dsl, const BlockMap& smap, int nsweep, in
                       const float* sino, const float* rw, const float* scale, float* partial, int64_t stride,
                       cudaStream_t st) {
     if (tile == 64)
-        sweep_t<float, 1, 64>(dsl, smap, nsweep, C, cluster, sino, partial, stride, rw, scale, st);
+        sweep_t<float, 1, 64>(dsl, smap, nsweep, C, cluster, 1, nullptr, sino, partial, stride, rw, scale, st);
     else
-        sweep_t<float, 1, 32>(dsl, smap, nsweep, C, cluster, sino, partial, stride, rw, scale, st);
+        sweep_t<float, 1, 32>(dsl, smap, nsweep, C, cluster, 1, nullptr, sino, partial, stride, rw, scale, st);
 }
 
 template <int MODE>
@@ -417,8 +494,8 @@ void backproject_single(const SliceDesc& sd, const SliceDesc* d_dev, const int* 
     const int64_t nr = (int64_t)sd.g.nv * sd.g.nb, np = (int64_t)sd.g.nx * sd.g.ny;
     launch_pack_planar(sino, nch, nr, packed, st);
     const BlockMap smap{maps, 1}, pmap{maps + 2, 1};
-    launch_bp_sweep(d_dev, smap, sweep_tiles(sd.g.nx, sd.g.ny, tile) * C, C, tile, false, packed, partial, np, PREC_F32,
-                    st);
+    launch_bp_sweep(d_dev, smap, sweep_tiles(sd.g.nx, sd.g.ny, tile) * C, C, tile, false, 1, nullptr, packed, partial,
+                    np, PREC_F32, st);
     k_bp_finalize<BP_PLAIN><<<(unsigned)((np + 255) / 256), 256, 0, st>>>(d_dev, pmap, C, partial, np, nullptr,
                                                                          BpEpilogue{}, out, nch);
 }

@@ -163,9 +163,11 @@ int sweep_groups(int tiles, int tile);
 cudaError_t sweep_init_attributes();  // per device: dynamic shared memory of the 64-pixel tiles
 constexpr int kSweepTileDefault = 32;
 // cluster: the C view groups of a tile reduce on chip (thread-block cluster, distributed shared memory)
-// into partial image 0 (the finalize pass then reads one image, C = 1); otherwise C partial images
-void launch_bp_sweep(const SliceDesc* dsl, const BlockMap& smap, int nsweep, int C, int tile, bool cluster,
-                     const void* sino, float2* partial, int64_t stride, int prec, cudaStream_t st);
+// into partial image 0 (the finalize pass then reads one image, C = 1); otherwise C partial images.
+// sg = 2: the block map counts tiles of slice groups (groups: {slice, second slice or -1, -, -}) and a
+// CTA backprojects into both slices of its group (plain form only); sg = 1: the map counts slices.
+void launch_bp_sweep(const SliceDesc* dsl, const BlockMap& smap, int nsweep, int C, int tile, bool cluster, int sg,
+                     const int4* groups, const void* sino, float2* partial, int64_t stride, int prec, cudaStream_t st);
 // single-channel sweep (float sinogram, float partial images; rw per ray and scale per slice optional)
 void launch_bp_sweep1(const SliceDesc* dsl, const BlockMap& smap, int nsweep, int C, int tile, bool cluster,
                       const float* sino, const float* rw, const float* scale, float* partial, int64_t stride,

@@ -51,7 +51,7 @@ class Params(ctypes.Structure):
                 ("precondition", ctypes.c_int32), ("use_graph", ctypes.c_int32), ("bp_view_groups", ctypes.c_int32),
                 ("storage", ctypes.c_int32), ("scheme", ctypes.c_int32), ("init", ctypes.c_int32),
                 ("udm_f64", ctypes.c_int32), ("objective_every", ctypes.c_int32), ("bp_tile", ctypes.c_int32),
-                ("bp_cluster", ctypes.c_int32)]
+                ("bp_cluster", ctypes.c_int32), ("bp_slices", ctypes.c_int32)]
 
 
 class Stats(ctypes.Structure):
@@ -59,7 +59,8 @@ class Stats(ctypes.Structure):
                 ("r_dual", ctypes.c_double * 2), ("xi_db", ctypes.c_double * 2), ("count_R", ctypes.c_int64),
                 ("count_RT", ctypes.c_int64), ("count_f", ctypes.c_int64), ("count_launches", ctypes.c_int64),
                 ("bp_view_groups", ctypes.c_int32), ("objective", ctypes.c_double),
-                ("objective_iteration", ctypes.c_int32), ("bp_tile", ctypes.c_int32), ("bp_cluster", ctypes.c_int32)]
+                ("objective_iteration", ctypes.c_int32), ("bp_tile", ctypes.c_int32), ("bp_cluster", ctypes.c_int32),
+                ("bp_slices", ctypes.c_int32)]
 
 
 # every symbol declared in include/dect.h, with its ctypes signature
@@ -315,7 +316,8 @@ def admm_stats(h, slice_index, stream=None) -> dict:
     return {"iteration": s.iteration, "rho": list(s.rho), "r_pri": list(s.r_pri), "r_dual": list(s.r_dual),
             "xi_db": list(s.xi_db), "count_R": s.count_R, "count_RT": s.count_RT, "count_f": s.count_f,
             "count_launches": s.count_launches, "bp_view_groups": s.bp_view_groups, "objective": s.objective,
-            "objective_iteration": s.objective_iteration, "bp_tile": s.bp_tile, "bp_cluster": s.bp_cluster}
+            "objective_iteration": s.objective_iteration, "bp_tile": s.bp_tile, "bp_cluster": s.bp_cluster,
+            "bp_slices": s.bp_slices}
 
 
 def admm_save(h, stream=None) -> np.ndarray:

@@ -124,6 +124,36 @@ def test_backprojector_tile_side_does_not_change_results(cuda_dev):
         assert np.array_equal(outs[0][b], outs[1][b])
 
 
+def _same_geometry_cases():
+    g = G.fan_geometry(128, 180, 256)
+    cases = [make_case(g, lambda gg, r: baggage_phantom(gg, r, n_objects=10), 2e5, 80 + k, e_ref_kev=100.0)
+             for k in range(3)]
+    for c in cases:
+        for k in ("m_h", "m_l", "w_h", "w_l"):
+            c[k] = _r32(c[k])
+    return cases
+
+
+def test_slices_of_one_geometry_share_projector_and_backprojector_ctas_with_the_same_bits(cuda_dev):
+    # three slices of one geometry: the first two form a pair (one CTA projects and backprojects both),
+    # the third stays alone; every slice equals its single-slice solve bit for bit, and the two-slice
+    # backprojector equals the one-slice form
+    from paper_1905_00934_gb300 import dect
+
+    cases = _same_geometry_cases()
+    outs = {}
+    for sl in (1, 2):
+        sol = _solver(cases, cuda_dev, [None] * 3, bp_view_groups=4, bp_tile=32, bp_cluster=-1, bp_slices=sl)
+        assert sol.stats(0)["bp_slices"] == sl
+        sol.reconstruct(3)
+        outs[sl] = [sol.get(b, dect.X).cpu().numpy() for b in range(3)]
+    for b, c in enumerate(cases):
+        one = _solver([c], cuda_dev, [None], bp_view_groups=4, bp_tile=32, bp_cluster=-1)
+        one.reconstruct(3)
+        x = one.get(0, dect.X).cpu().numpy()
+        assert np.array_equal(outs[1][b], x) and np.array_equal(outs[2][b], x), b
+
+
 @pytest.mark.parametrize("scheme", [0, 1])
 @pytest.mark.parametrize("groups", [4, 8])
 def test_cluster_reduction_of_view_groups_gives_the_same_bits(cuda_dev, scheme, groups):
