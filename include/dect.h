@@ -309,7 +309,7 @@ typedef struct {
     int32_t bp_tile;             /* backprojector tile side in pixels, 32 or 64 (its CTA's warps take bands of
                                     32 columns or rows of the tile); 0 (default) = chosen by the autotuner
                                     with bp_view_groups (timed on this batch; with bp_view_groups fixed, the
-                                    two sides are timed at that count; with -1, 64). The side does not change
+                                    two sides are timed at that count; with -1, 32). The side does not change
                                     results (every pixel receives the same contributions in the same order). */
     int32_t bp_cluster;          /* the backprojector's view groups of a tile as one thread-block cluster that
                                     adds their accumulators on chip (distributed shared memory, in rank order)
