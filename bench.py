@@ -137,11 +137,12 @@ def joseph_weight_count(g) -> int:
     return total
 
 
-# DRAM bytes per launch of the backprojector sweep at the bench workload (8 slices), keyed by the launch
-# shape they were captured with (slices, view groups, tile side, cluster form, slices per CTA); from the
-# counter capture
-# in profiles/k_bp_sweep_512x720x1024.txt. Reported only when the run uses that shape.
-SWEEP_TRAFFIC = {(8, 8, 32, 0, 1): 134.0e6}
+# DRAM bytes (read + write) per launch of the backprojector sweep at the bench workload (8 slices),
+# keyed by the launch shape they were captured with (slices, view groups, tile side, cluster form,
+# slices per CTA, reduced form); from the counter captures in profiles/k_bp_sweep_512x720x1024.txt.
+# Reported only when the run uses one of these shapes.
+SWEEP_TRAFFIC = {(8, 8, 32, 0, 1, 0): 134.0e6, (8, 6, 32, 0, 2, 0): 105.2e6, (8, 8, 32, 0, 2, 0): 134.9e6,
+                 (8, 6, 32, 0, 2, 1): 56.9e6}
 
 
 # ------------------------------------------------------------------------------------------------
@@ -318,7 +319,10 @@ def run_dect(args):
     geo = [Geometry(c["geom"]) for c in cases]
     spec = Spectra.from_tables(cases[0]["spectra"])
     storage = {"f32": 0, "f16": 1, "bf16": 2}[args.storage]
-    sol = Solver(geo, spec, kappa=BAGGAGE_KAPPA, storage=storage)
+    # the backprojector's launch shape: autotuned at creation unless fixed on the command line
+    shape = dict(bp_view_groups=args.bp_view_groups, bp_tile=args.bp_tile, bp_cluster=args.bp_cluster,
+                 bp_slices=args.bp_slices, bp_reduce=args.bp_reduce)
+    sol = Solver(geo, spec, kappa=BAGGAGE_KAPPA, storage=storage, **shape)
     f32 = lambda a: torch.tensor(np.ascontiguousarray(a), dtype=torch.float32, device=dev)
     dev_data = [[f32(c[k]) for k in ("m_h", "m_l", "w_h", "w_l")] for c in cases]
     truths = [f32(np.stack([c["truth_c"], c["truth_p"]])) for c in cases]
@@ -379,7 +383,7 @@ def run_dect(args):
     cfg = {"workload": "fan 512x512, 720 views x 1024 bins, 40 objects, I0 2e5, UDM1-PCG1 x 100 + init",
            "iterations_fixed": ITERS, "batch_per_gpu": B, "l2": "flushed between steps (512 MB write)",
            "storage": args.storage, "bp_view_groups": st0["bp_view_groups"], "bp_tile": st0["bp_tile"],
-           "bp_cluster": st0["bp_cluster"], "bp_slices": st0["bp_slices"]}
+           "bp_cluster": st0["bp_cluster"], "bp_slices": st0["bp_slices"], "bp_reduce": st0["bp_reduce"]}
     phases = _phase_ms(sol, 10)
     for p_, ms in phases.items():
         cfg[f"{args.storage}_ms_{p_}"] = round(ms, 4)
@@ -406,7 +410,7 @@ def run_dect(args):
             if name == args.storage:
                 continue
             try:
-                s16 = Solver(geo, spec, kappa=BAGGAGE_KAPPA, storage=code)
+                s16 = Solver(geo, spec, kappa=BAGGAGE_KAPPA, storage=code, **shape)
                 for b in range(B):
                     s16.set_data(b, *dev_data[b])
                     s16.set_truth(b, truths[b])
@@ -424,7 +428,7 @@ def run_dect(args):
                 cfg[f"batched_{name}_error"] = f"{type(exc).__name__}: {exc}"[:90]
         # the float64 decomposition option: its cost per slice-iteration next to the default's
         try:
-            s64 = Solver(geo, spec, kappa=BAGGAGE_KAPPA, udm_f64=1)
+            s64 = Solver(geo, spec, kappa=BAGGAGE_KAPPA, udm_f64=1, **shape)
             for b in range(B):
                 s64.set_data(b, *dev_data[b])
             s64.reconstruct(1)
@@ -467,7 +471,8 @@ def run_dect(args):
     pr_ms, pr_tf, pr_gbs, pr_bytes = kernel_roof("project", 1)
     cfg.update({"project_tflops": pr_tf, "project_tflops_frac": pr_tf / fp32_peak, "project_hbm_gbs": pr_gbs,
                 "project_hbm_frac": pr_gbs / peak, "backproject_hbm_frac": bp_gbs / peak})
-    traffic = SWEEP_TRAFFIC.get((B, st0["bp_view_groups"], st0["bp_tile"], st0["bp_cluster"], st0["bp_slices"]))
+    traffic = SWEEP_TRAFFIC.get((B, st0["bp_view_groups"], st0["bp_tile"], st0["bp_cluster"], st0["bp_slices"],
+                                 st0["bp_reduce"]))
     roof = {"kernel": "backproject" if top == "backproject" else top, "bound": "alu", "achieved": bp_tf,
             "peak": fp32_peak, "unit": "TFLOP/s", "frac": bp_tf / fp32_peak,
             "traffic": traffic, "traffic_source": "stored ncu capture of this kernel and launch shape "
@@ -481,7 +486,7 @@ def run_dect(args):
     # + 24 B/ray; y, z, u^y, u^z of Eq. 9-11 with x: 104 B/pixel; the dual rescale moves nothing when
     # rho stays) and the two backprojector finalize passes (partial images of 8 B, plus 64 B/pixel of
     # epilogue images for r0 and 16 B/pixel for A p)
-    parts = 1 if st0["bp_cluster"] else st0["bp_view_groups"]
+    parts = 1 if st0["bp_cluster"] or st0["bp_reduce"] else st0["bp_view_groups"]
     for p_, nbytes in (("update", B * (56 * M + 128 * Np)), ("bp_finalize", B * ((16 * parts + 80) * Np))):
         ms = prof[p_][0] / 10
         cfg[f"{p_}_hbm_frac"] = nbytes / (ms / 1e3) / 1e9 / peak
@@ -829,6 +834,13 @@ def main():
                     help="skip the plain forms, the 16-bit arms, the slice-size scan and the uneven batch")
     ap.add_argument("--uneven-slices", type=int, default=64,
                     help="slices of the uneven-batch leg of the bench line (0 skips it)")
+    ap.add_argument("--bp-view-groups", type=int, default=0,
+                    help="backprojector view groups per tile (0: autotuned, -1: occupancy rule)")
+    ap.add_argument("--bp-tile", type=int, default=0, help="backprojector tile side, 32 or 64 (0: autotuned)")
+    ap.add_argument("--bp-cluster", type=int, default=0, help="1 cluster form, -1 plain form, 0 autotuned")
+    ap.add_argument("--bp-slices", type=int, default=0, help="slices per backprojector CTA, 1 or 2 (0: autotuned)")
+    ap.add_argument("--bp-reduce", type=int, default=0,
+                    help="-1: the finalize pass sums the view groups' partial images; 0/1: the last CTA of a tile does")
     ap.add_argument("--profile-run", type=int, default=0, metavar="ITERS",
                     help="set up the workload, run one untimed reconstruction of ITERS iterations and exit "
                          "(for profiler captures; prints no bench line)")

@@ -320,6 +320,12 @@ typedef struct {
                                     consecutive slices of one geometry at once (shared staging and sample
                                     positions, one accumulator per slice; UDM-PCG scheme), 1 one slice,
                                     0 (default) timed by the autotuner. Same bits either way. */
+    int32_t bp_reduce;           /* plain (non-cluster) backprojector with C >= 2 view groups: the last CTA of a
+                                    tile to finish sums the tile's C partial images (in view-group order, the
+                                    finalize pass's order) into partial image 0 while they are in L2 and drops
+                                    the other partials' L2 lines, so they are not written back to DRAM; the
+                                    finalize pass reads one image. 0 (default) or 1 on, -1 off (the finalize
+                                    pass reads the C partials). Same bits either way. */
 } dect_params;
 
 /* Fills *p with the paper's values and the defaults above. */
@@ -381,6 +387,7 @@ typedef struct {
     int32_t bp_tile;             /* backprojector tile side in use (0 for float64 storage) */
     int32_t bp_cluster;          /* 1 if the backprojector's view groups reduce on chip (see bp_cluster) */
     int32_t bp_slices;           /* slices per backprojector CTA in use (see bp_slices; 0 for float64) */
+    int32_t bp_reduce;           /* 1 if the backprojector's view groups are summed by its last CTA per tile */
 } dect_stats;
 dect_status dect_admm_stats(dect_admm* a, int32_t slice, dect_stats* out, void* stream);
 

@@ -520,6 +520,7 @@ extern "C" void dect_params_default(dect_params* p) {
     p->bp_tile = 0;
     p->bp_cluster = 0;
     p->bp_slices = 0;
+    p->bp_reduce = 0;
 }
 
 struct MapBuf {
@@ -548,7 +549,12 @@ struct dect_admm {
     std::vector<int4> sgroups;       // the pairs (second -1 for a slice without a partner)
     int4* d_sgroups = nullptr;
     int sweep_units() const { return sweep_sg == 2 ? (int)sgroups.size() : B; }
-    int bp_parts() const { return sweep_cluster ? 1 : sweep_C; }  // partial images the finalize pass reads
+    bool sweep_reduce = false;       // the last CTA of a tile sums its C partials into image 0 (reduced form)
+    int* tile_count = nullptr;       // the reduced form's arrival counters, one per tile (zero between launches)
+    int n_tile_count = 0;            // counters: the batch's tiles at the smallest tile side
+    int* reduce_count() const { return sweep_reduce && !sweep_cluster ? tile_count : nullptr; }
+    int bp_slots() const { return sweep_cluster ? 1 : sweep_C; }  // partial images the sweep writes
+    int bp_parts() const { return sweep_cluster || (sweep_reduce && sweep_C > 1) ? 1 : sweep_C; }  // the finalize reads
     int sweep_groups_in_use = 1;     // view groups per tile (sweep_C CTAs of the kernel's groups each)
     float2* bp_partial = nullptr;    // [sweep_C][n_img] partial images of the backprojector
     int64_t n_img = 0, n_sino = 0, n_tx = 0, n_ty = 0, n_fft = 0, n_h = 0, n_stage = 0;
@@ -628,7 +634,7 @@ static void free_admm(dect_admm* A) {
                     A->part_img, A->part_rs, A->part_pap, A->part_xi, A->d_has_x0, A->ls, A->lm_scale, A->lm_d,
                     A->lm_r, A->lm_p, A->lm_Ap, A->lm_e, A->lm_g, A->lm_q, A->lm_Rd, A->lm_s0, A->tx1, A->ty1,
                     A->bp_partial1, A->part_lm_pix, A->part_lm_ray, A->cols64.d, A->part_obj_rays,
-                    A->part_obj_pix};
+                    A->part_obj_pix, A->tile_count};
     for (void* q : ptrs) cudaFree(q);
     const F64Vecs& v = A->v64;
     for (void* q : {(void*)v.x, (void*)v.r, (void*)v.s, (void*)v.p, (void*)v.Ap, (void*)v.z, (void*)v.uz, (void*)v.x0,
@@ -691,7 +697,7 @@ static void enq_pcg(dect_admm* A, int n, bool with_grad, const float* H, cudaStr
     pe(A, DECT_PHASE_UPDATE, 1, st);
     pb(A, st);
     launch_bp_sweep(A->ds, A->sweep.map(A->sweep_units()), A->sweep.total, A->sweep_C, A->sweep_tile, A->sweep_cluster,
-                    A->sweep_sg, A->d_sgroups, A->q, A->bp_partial, A->n_img, A->prec, st);
+                    A->sweep_sg, A->d_sgroups, A->q, A->bp_partial, A->n_img, A->prec, A->reduce_count(), st);
     pe(A, DECT_PHASE_BACKPROJECT, 1, st);
     pb(A, st);
     launch_bp_finalize(with_grad ? BP_R0 : BP_R0_NOGRAD, A->ds, A->pix.map(B), A->pix.total, A->bp_parts(),
@@ -706,8 +712,7 @@ static void enq_pcg(dect_admm* A, int n, bool with_grad, const float* H, cudaStr
         enq_project(A, A->p, A->q, st);
         pb(A, st);
         launch_bp_sweep(A->ds, A->sweep.map(A->sweep_units()), A->sweep.total, A->sweep_C, A->sweep_tile, A->sweep_cluster,
-                    A->sweep_sg, A->d_sgroups, A->q, A->bp_partial, A->n_img, A->prec,
-                        st);
+                        A->sweep_sg, A->d_sgroups, A->q, A->bp_partial, A->n_img, A->prec, A->reduce_count(), st);
         pe(A, DECT_PHASE_BACKPROJECT, 1, st);
         pb(A, st);
         launch_bp_finalize(with_grad ? BP_AP : BP_AP_NOGRAD, A->ds, A->pix.map(B), A->pix.total, A->bp_parts(),
@@ -752,8 +757,7 @@ static void enq_lm_step(dect_admm* A, int b, cudaStream_t st) {
     pe(A, DECT_PHASE_UDM, 1, st);
     pb(A, st);
     launch_bp_sweep1(A->ds, A->sweep.map(B), A->sweep.total, A->sweep_C, A->sweep_tile, A->sweep_cluster, A->lm_e,
-                     nullptr, nullptr, A->bp_partial1,
-                     A->n_img, st);
+                     nullptr, nullptr, A->bp_partial1, A->n_img, A->reduce_count(), st);
     pe(A, DECT_PHASE_BACKPROJECT, 1, st);
     pb(A, st);
     launch_lm_grad(A->ds, pix, A->pix.total, A->bp_parts(), A->bp_partial1, A->n_img, b, A->sc, ep, A->lm_r, A->lm_p,
@@ -773,8 +777,7 @@ static void enq_lm_step(dect_admm* A, int b, cudaStream_t st) {
         pe(A, DECT_PHASE_PROJECT, 1, st);
         pb(A, st);
         launch_bp_sweep1(A->ds, A->sweep.map(B), A->sweep.total, A->sweep_C, A->sweep_tile, A->sweep_cluster, A->lm_q,
-                         A->lm_g, A->lm_scale,
-                         A->bp_partial1, A->n_img, st);
+                         A->lm_g, A->lm_scale, A->bp_partial1, A->n_img, A->reduce_count(), st);
         pe(A, DECT_PHASE_BACKPROJECT, 1, st);
         pb(A, st);
         launch_lm_ap(A->ds, pix, A->pix.total, A->bp_parts(), A->bp_partial1, A->n_img, b, A->sc, A->lm_p, A->lm_Ap,
@@ -1140,59 +1143,66 @@ static void sweep_prefix(const dect_admm* A, int C, int tile, int sg, std::vecto
         for (int b = 0; b < A->B; ++b) h.push_back(h.back() + sweep_tiles(A->hs[b].g.nx, A->hs[b].g.ny, tile) * C);
 }
 
-// Times the backprojector sweep on this batch for each candidate (tile side, C) (on a zero sinogram; the
-// work does not depend on the values), keeps the fastest (fewer view groups unless more are 1% faster)
-// and shrinks the partial-image buffer to it. bp_partial is allocated for the largest candidate C.
-// The tile side does not change results; C fixes the order of a pixel's partial sums.
+// Times the backprojector sweep on this batch (on a zero sinogram; the work does not depend on the
+// values) and keeps the fastest shape (fewer view groups unless more are 1% faster), in three stages:
+// slices per CTA x view groups C at the default tile side, then the other tile sides at the best of
+// those, then the cluster form there. Shrinks the partial-image buffer to the choice (bp_partial is
+// allocated for the largest candidate C). The tile side, the slices per CTA and the cluster form do
+// not change results; C fixes the order of a pixel's partial sums.
 static cudaError_t autotune_sweep(dect_admm* A, const std::vector<int>& cands, const std::vector<int>& tiles) {
     cudaStream_t st = A->cap;
     cudaError_t e = cudaMemsetAsync(A->q, 0, sino_bytes(A->prec) * (size_t)A->n_sino, st);
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (e == cudaSuccess) e = cudaEventCreate(&e0);
     if (e == cudaSuccess) e = cudaEventCreate(&e1);
-    int best = cands[0], best_tile = tiles[0], best_sg = 1;
+    const int tile0 =
+        std::find(tiles.begin(), tiles.end(), kSweepTileDefault) != tiles.end() ? kSweepTileDefault : tiles[0];
+    const bool cl0 = A->cluster_cands.size() == 1 && A->cluster_cands[0] == 1;  // cluster form required
+    int best = cands[0], best_tile = tile0, best_sg = 1;
     bool best_cluster = false;
     float best_ms = 0.f;
     bool first = true;
     std::vector<int> h;
+    auto trial = [&](int sg, int tile, int C, bool cluster) {
+        if (e != cudaSuccess || (cluster && (C < 2 || C > 16 || sg != 1))) return;
+        sweep_prefix(A, C, tile, sg, h);
+        e = cudaMemcpy(A->sweep.d, h.data(), sizeof(int) * h.size(), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) return;
+        const BlockMap m{A->sweep.d, sg == 2 ? (int)A->sgroups.size() : A->B};
+        auto run = [&]() {
+            launch_bp_sweep(A->ds, m, h.back(), C, tile, cluster, sg, A->d_sgroups, A->q, A->bp_partial, A->n_img,
+                            A->prec, A->sweep_reduce ? A->tile_count : nullptr, st);
+        };
+        // a cluster shape the device cannot schedule is reported at launch: skip that candidate
+        run();
+        if (cluster && cudaGetLastError() != cudaSuccess) return;
+        run();  // warm-up
+        e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaEventRecord(e0, st);
+        for (int r = 0; r < 3 && e == cudaSuccess; ++r) {
+            run();
+            e = cudaGetLastError();
+        }
+        if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        float ms = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (e == cudaSuccess && (first || ms < 0.99f * best_ms || (ms <= best_ms && C < best))) {
+            best = C;
+            best_tile = tile;
+            best_cluster = cluster;
+            best_sg = sg;
+            best_ms = ms;
+            first = false;
+        }
+    };
     for (int sg : A->sg_cands)
-        for (int tile : tiles)
-            for (size_t k = 0; k < cands.size() && e == cudaSuccess; ++k)
-                for (int cl : A->cluster_cands) {
-                    if (e != cudaSuccess) break;
-                    const int C = cands[k];
-                    const bool cluster = cl == 1;
-                    if (cluster && (C < 2 || C > 16 || sg != 1)) continue;
-                    sweep_prefix(A, C, tile, sg, h);
-                    e = cudaMemcpy(A->sweep.d, h.data(), sizeof(int) * h.size(), cudaMemcpyHostToDevice);
-                    const BlockMap m{A->sweep.d, sg == 2 ? (int)A->sgroups.size() : A->B};
-                    auto run = [&]() {
-                        launch_bp_sweep(A->ds, m, h.back(), C, tile, cluster, sg, A->d_sgroups, A->q, A->bp_partial,
-                                        A->n_img, A->prec, st);
-                    };
-                    // a cluster shape the device cannot schedule is reported at launch: skip that candidate
-                    run();
-                    if (cluster && cudaGetLastError() != cudaSuccess) continue;
-                    run();  // warm-up
-                    e = cudaGetLastError();
-                    if (e == cudaSuccess) e = cudaEventRecord(e0, st);
-                    for (int r = 0; r < 3 && e == cudaSuccess; ++r) {
-                        run();
-                        e = cudaGetLastError();
-                    }
-                    if (e == cudaSuccess) e = cudaEventRecord(e1, st);
-                    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
-                    float ms = 0.f;
-                    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
-                    if (e == cudaSuccess && (first || ms < 0.99f * best_ms || (ms <= best_ms && C < best))) {
-                        best = C;
-                        best_tile = tile;
-                        best_cluster = cluster;
-                        best_sg = sg;
-                        best_ms = ms;
-                        first = false;
-                    }
-                }
+        for (int C : cands) trial(sg, tile0, C, cl0);
+    const int C1 = best, sg1 = best_sg;
+    const bool cl1 = best_cluster;
+    for (int tile : tiles)
+        if (tile != tile0) trial(sg1, tile, C1, cl1);
+    if (A->cluster_cands.size() > 1) trial(1, best_tile, C1, true);
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
     if (e != cudaSuccess) return e;
@@ -1206,7 +1216,7 @@ static cudaError_t autotune_sweep(dect_admm* A, const std::vector<int>& cands, c
     if (e != cudaSuccess) return e;
     cudaFree(A->bp_partial);
     A->bp_partial = nullptr;
-    e = dalloc(&A->bp_partial, (size_t)A->bp_parts() * A->n_img);
+    e = dalloc(&A->bp_partial, (size_t)A->bp_slots() * A->n_img);
     return e;
 }
 
@@ -1329,6 +1339,8 @@ extern "C" dect_status dect_admm_create(dect_geom* const* geoms, int32_t B, cons
         DECT_FAIL(DECT_EINVAL, "dect_admm_create: bp_cluster must be -1 (off), 0 (autotuned) or 1 (on)");
     if (P->bp_slices < 0 || P->bp_slices > 2)
         DECT_FAIL(DECT_EINVAL, "dect_admm_create: bp_slices must be 0 (autotuned), 1 or 2");
+    if (P->bp_reduce < -1 || P->bp_reduce > 1)
+        DECT_FAIL(DECT_EINVAL, "dect_admm_create: bp_reduce must be -1 (off), 0 (default: on) or 1 (on)");
     if (P->init != DECT_INIT_PCG && P->init != DECT_INIT_CDM_FBP)
         DECT_FAIL(DECT_EINVAL, "dect_admm_create: init must be DECT_INIT_PCG or DECT_INIT_CDM_FBP");
     if (P->init == DECT_INIT_CDM_FBP)
@@ -1381,6 +1393,8 @@ extern "C" dect_status dect_admm_create(dect_geom* const* geoms, int32_t B, cons
             pix += geoms[b]->n_pix();
         }
         A->sweep_tile = tile0;
+        A->sweep_reduce = P->bp_reduce >= 0;
+        for (int b = 0; b < B; ++b) A->n_tile_count += sweep_tiles(geoms[b]->desc.nx, geoms[b]->desc.ny, 32);
         if (P->bp_cluster == 0) A->cluster_cands = {0, 1};
         else A->cluster_cands = {P->bp_cluster > 0 ? 1 : 0};
         // pairs of consecutive slices of one geometry for the two-slice sweep (UDM-PCG only: the comparison
@@ -1550,6 +1564,8 @@ extern "C" dect_status dect_admm_create(dect_geom* const* geoms, int32_t B, cons
     if (e == cudaSuccess) e = dalloc(&A->part_obj_rays, (size_t)nr_blk);
     if (e == cudaSuccess) e = dalloc(&A->part_obj_pix, (size_t)np_blk);
     if (e == cudaSuccess && A->prec != PREC_F64) e = dalloc(&A->bp_partial, (size_t)A->sweep_C * A->n_img);
+    if (e == cudaSuccess && A->prec != PREC_F64) e = dalloc(&A->tile_count, (size_t)A->n_tile_count);
+    if (e == cudaSuccess && A->prec != PREC_F64) e = cudaMemset(A->tile_count, 0, sizeof(int) * A->n_tile_count);
     for (MapBuf* m : {&A->rays, &A->pix, &A->tx, &A->ty, &A->rows, &A->cols, &A->sweep, &A->cols64, &A->ptile})
         if (e == cudaSuccess) e = upload_map(*m);
     if (e == cudaSuccess) e = dalloc(&A->d_groups, groups.size());
@@ -1588,7 +1604,7 @@ extern "C" dect_status dect_admm_create(dect_geom* const* geoms, int32_t B, cons
         e = cudaMemset(A->part_udm, 0, sizeof(double) * 4 * (size_t)A->rays.h.back());
         if (e == cudaSuccess) e = dalloc(&A->part_lm_pix, (size_t)A->pix.h.back());
         if (e == cudaSuccess) e = dalloc(&A->part_lm_ray, (size_t)A->rays.h.back());
-        if (e == cudaSuccess) e = dalloc(&A->bp_partial1, (size_t)A->bp_parts() * A->n_img);
+        if (e == cudaSuccess) e = dalloc(&A->bp_partial1, (size_t)A->bp_slots() * A->n_img);
         if (e != cudaSuccess) {
             dect::set_error(std::string("dect_admm_create: ") + cudaGetErrorString(e));
             free_admm(A);
@@ -2039,5 +2055,6 @@ extern "C" dect_status dect_admm_stats(dect_admm* A, int32_t b, dect_stats* out,
     out->bp_tile = A->prec == PREC_F64 ? 0 : A->sweep_tile;
     out->bp_cluster = A->sweep_cluster ? 1 : 0;
     out->bp_slices = A->prec == PREC_F64 ? 0 : A->sweep_sg;
+    out->bp_reduce = A->bp_parts() == 1 && !A->sweep_cluster && A->sweep_C > 1 ? 1 : 0;
     return DECT_OK;
 }

@@ -11,7 +11,10 @@
 // [column][row] for axis 1: both free of bank conflicts), every sample is evaluated exactly once,
 // and no atomics are needed. The two tiles are added in a fixed order into this CTA's partial
 // image, and k_bp_finalize adds the C partials of a pixel in a fixed order and applies the
-// epilogue, so results are deterministic for a given C.
+// epilogue, so results are deterministic for a given C. In the reduced form the last of a tile's C
+// CTAs to finish (a per-tile arrival counter) forms that same sum while the partials are still in L2,
+// writes it to partial image 0 (the finalize pass then reads one image) and drops the L2 lines of the
+// other partials it consumed, so they are never written back to DRAM.
 //
 // Staging turns a ray into {tile-relative position at lane 0, slope, w s}: the position is
 // q0 + t0 * slope - (a0 << 30) for the tile's first sampled index t0 and first across index a0,
@@ -44,6 +47,14 @@ namespace dect {
 // pixel within a view group, and the autotuner of the solver picks one by timing.
 constexpr int kSwUnroll = 8;
 
+// Drop the L2 lines that lie wholly inside [lo, hi) without writing them back (discard.global.L2,
+// 128-byte lines; their contents become undefined). The caller owns every byte of the range.
+__device__ __forceinline__ void discard_l2_range(const void* lo, const void* hi) {
+    size_t a = (__cvta_generic_to_global(lo) + 127) & ~(size_t)127;
+    const size_t e = __cvta_generic_to_global(hi);
+    for (; a + 128 <= e; a += 128) asm volatile("discard.global.L2 [%0], 128;" ::"l"(a) : "memory");
+}
+
 template <int TILE>
 struct SweepShape {
     static constexpr int kBands = TILE / 32;      // bands per axis
@@ -70,11 +81,14 @@ constexpr size_t sweep_acc_bytes() {
 // groups[unit], the second -1 if the group has one slice): staging, candidate search and sample
 // positions are done once, each slice has its own accumulators, and each slice's pixels receive the
 // same contributions in the same order as with SG = 1 (the same bits). NCH = 2, plain form only.
+// tile_count != nullptr (plain form): the reduced form. One counter per tile of the launch (block /
+// C), zero on entry; the tile's last CTA adds 0 + p_0 + ... + p_{C-1} per pixel, the finalize pass's
+// sum, into image 0 and sets the counter back to zero.
 template <class S2, int NCH, int TILE, bool CLUSTER = false, int SG = 1>
 __global__ void __launch_bounds__(SweepShape<TILE>::kThreads) k_bp_sweep(
     const SliceDesc* __restrict__ dsl, BlockMap map, int C, const int4* __restrict__ groups,
     const S2* __restrict__ sino, typename std::conditional<NCH == 2, float2, float>::type* __restrict__ partial,
-    int64_t stride, const float* __restrict__ rw, const float* __restrict__ scale) {
+    int64_t stride, const float* __restrict__ rw, const float* __restrict__ scale, int* __restrict__ tile_count) {
     static_assert(SG == 1 || (SG == 2 && NCH == 2 && !CLUSTER), "two slices per CTA: two channels, plain form");
     using Acc = typename std::conditional<NCH == 2, float2, float>::type;
     using Sh = SweepShape<TILE>;
@@ -300,6 +314,45 @@ __global__ void __launch_bounds__(SweepShape<TILE>::kThreads) k_bp_sweep(
                 }
             }
         }
+        if (tile_count == nullptr || C == 1) return;
+        // reduced form: the CTA that completes the tile's count sees every other CTA's partial (each
+        // fenced its stores before its increment)
+        __shared__ int last;
+        __threadfence();
+        __syncthreads();
+        if (threadIdx.x == 0) last = atomicAdd(tile_count + blockIdx.x / C, 1) == C - 1;
+        __syncthreads();
+        if (!last) return;
+        __threadfence();
+        const int iw = min(TILE, nx - ti), jh = min(TILE, ny - tj);
+        for (int q = 0; q < count; ++q) {
+            Acc* img = partial + dsl[sl[q]].img_off;
+            for (int px = threadIdx.x; px < TILE * TILE; px += blockDim.x) {
+                const int rr = px / TILE, cc = px % TILE;
+                if (cc < iw && rr < jh) {
+                    const size_t e = (size_t)(tj + rr) * nx + ti + cc;
+                    Acc sum{};
+#pragma unroll 4
+                    for (int k = 0; k < C; ++k) {
+                        const Acc a = __ldcg(img + k * stride + e);
+                        if constexpr (NCH == 2) {
+                            sum.x += a.x;
+                            sum.y += a.y;
+                        } else {
+                            sum += a;
+                        }
+                    }
+                    img[e] = sum;
+                }
+            }
+        }
+        __syncthreads();  // every partial of the tile has been read
+        for (int t = threadIdx.x; t < count * (C - 1) * jh; t += blockDim.x) {
+            const int rr = t % jh, k = 1 + (t / jh) % (C - 1), q = t / (jh * (C - 1));
+            const Acc* row = partial + dsl[sl[q]].img_off + k * stride + (size_t)(tj + rr) * nx + ti;
+            discard_l2_range(row, row + iw);
+        }
+        if (threadIdx.x == 0) tile_count[blockIdx.x / C] = 0;
     }
 }
 
@@ -404,17 +457,17 @@ int sweep_groups(int tiles, int tile) {
 template <class S2, int NCH, int TILE>
 static void sweep_t(const SliceDesc* dsl, const BlockMap& smap, int nsweep, int C, bool cluster, int sg,
                     const int4* groups, const S2* sino, typename std::conditional<NCH == 2, float2, float>::type* partial,
-                    int64_t stride, const float* rw, const float* scale, cudaStream_t st) {
+                    int64_t stride, const float* rw, const float* scale, int* tile_count, cudaStream_t st) {
     if constexpr (NCH == 2) {
         if (sg == 2) {
             k_bp_sweep<S2, NCH, TILE, false, 2><<<nsweep, SweepShape<TILE>::kThreads, sweep_acc_bytes<TILE, NCH, 2>(), st>>>(
-                dsl, smap, C, groups, sino, partial, stride, rw, scale);
+                dsl, smap, C, groups, sino, partial, stride, rw, scale, tile_count);
             return;
         }
     }
     if (!cluster || C == 1) {
         k_bp_sweep<S2, NCH, TILE><<<nsweep, SweepShape<TILE>::kThreads, sweep_acc_bytes<TILE, NCH>(), st>>>(
-            dsl, smap, C, nullptr, sino, partial, stride, rw, scale);
+            dsl, smap, C, nullptr, sino, partial, stride, rw, scale, tile_count);
         return;
     }
     // the C CTAs of a tile are consecutive blocks and every slice's block range is a multiple of C,
@@ -432,43 +485,47 @@ static void sweep_t(const SliceDesc* dsl, const BlockMap& smap, int nsweep, int 
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     const int4* no_groups = nullptr;
+    int* no_count = nullptr;
     cudaLaunchKernelEx(&cfg, k_bp_sweep<S2, NCH, TILE, true>, dsl, smap, C, no_groups, sino, partial, stride, rw,
-                       scale);
+                       scale, no_count);
 }
 
 void launch_bp_sweep(const SliceDesc* dsl, const BlockMap& smap, int nsweep, int C, int tile, bool cluster, int sg,
-                     const int4* groups, const void* sino, float2* partial, int64_t stride, int prec, cudaStream_t st) {
+                     const int4* groups, const void* sino, float2* partial, int64_t stride, int prec, int* tile_count,
+                     cudaStream_t st) {
     const bool k = cluster;
+    int* tc = cluster ? nullptr : tile_count;
     if (tile == 64) {
         if (prec == PREC_F16)
             sweep_t<__half2, 2, 64>(dsl, smap, nsweep, C, k, sg, groups, (const __half2*)sino, partial, stride, nullptr,
-                                    nullptr, st);
+                                    nullptr, tc, st);
         else if (prec == PREC_BF16)
             sweep_t<__nv_bfloat162, 2, 64>(dsl, smap, nsweep, C, k, sg, groups, (const __nv_bfloat162*)sino, partial,
-                                           stride, nullptr, nullptr, st);
+                                           stride, nullptr, nullptr, tc, st);
         else
             sweep_t<float2, 2, 64>(dsl, smap, nsweep, C, k, sg, groups, (const float2*)sino, partial, stride, nullptr,
-                                   nullptr, st);
+                                   nullptr, tc, st);
     } else {
         if (prec == PREC_F16)
             sweep_t<__half2, 2, 32>(dsl, smap, nsweep, C, k, sg, groups, (const __half2*)sino, partial, stride, nullptr,
-                                    nullptr, st);
+                                    nullptr, tc, st);
         else if (prec == PREC_BF16)
             sweep_t<__nv_bfloat162, 2, 32>(dsl, smap, nsweep, C, k, sg, groups, (const __nv_bfloat162*)sino, partial,
-                                           stride, nullptr, nullptr, st);
+                                           stride, nullptr, nullptr, tc, st);
         else
             sweep_t<float2, 2, 32>(dsl, smap, nsweep, C, k, sg, groups, (const float2*)sino, partial, stride, nullptr,
-                                   nullptr, st);
+                                   nullptr, tc, st);
     }
 }
 
 void launch_bp_sweep1(const SliceDesc* dsl, const BlockMap& smap, int nsweep, int C, int tile, bool cluster,
                       const float* sino, const float* rw, const float* scale, float* partial, int64_t stride,
-                      cudaStream_t st) {
+                      int* tile_count, cudaStream_t st) {
+    int* tc = cluster ? nullptr : tile_count;
     if (tile == 64)
-        sweep_t<float, 1, 64>(dsl, smap, nsweep, C, cluster, 1, nullptr, sino, partial, stride, rw, scale, st);
+        sweep_t<float, 1, 64>(dsl, smap, nsweep, C, cluster, 1, nullptr, sino, partial, stride, rw, scale, tc, st);
     else
-        sweep_t<float, 1, 32>(dsl, smap, nsweep, C, cluster, 1, nullptr, sino, partial, stride, rw, scale, st);
+        sweep_t<float, 1, 32>(dsl, smap, nsweep, C, cluster, 1, nullptr, sino, partial, stride, rw, scale, tc, st);
 }
 
 template <int MODE>
@@ -495,7 +552,7 @@ void backproject_single(const SliceDesc& sd, const SliceDesc* d_dev, const int* 
     launch_pack_planar(sino, nch, nr, packed, st);
     const BlockMap smap{maps, 1}, pmap{maps + 2, 1};
     launch_bp_sweep(d_dev, smap, sweep_tiles(sd.g.nx, sd.g.ny, tile) * C, C, tile, false, 1, nullptr, packed, partial,
-                    np, PREC_F32, st);
+                    np, PREC_F32, nullptr, st);
     k_bp_finalize<BP_PLAIN><<<(unsigned)((np + 255) / 256), 256, 0, st>>>(d_dev, pmap, C, partial, np, nullptr,
                                                                          BpEpilogue{}, out, nch);
 }

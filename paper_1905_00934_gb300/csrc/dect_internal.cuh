@@ -166,12 +166,16 @@ constexpr int kSweepTileDefault = 32;
 // into partial image 0 (the finalize pass then reads one image, C = 1); otherwise C partial images.
 // sg = 2: the block map counts tiles of slice groups (groups: {slice, second slice or -1, -, -}) and a
 // CTA backprojects into both slices of its group (plain form only); sg = 1: the map counts slices.
+// tile_count (plain form, C >= 2; nullptr otherwise): one zeroed counter per tile of the launch
+// (nsweep / C of them); the tile's last CTA sums the C partials into image 0 (the finalize pass then
+// reads one image, C = 1) and zeroes the counter again.
 void launch_bp_sweep(const SliceDesc* dsl, const BlockMap& smap, int nsweep, int C, int tile, bool cluster, int sg,
-                     const int4* groups, const void* sino, float2* partial, int64_t stride, int prec, cudaStream_t st);
+                     const int4* groups, const void* sino, float2* partial, int64_t stride, int prec, int* tile_count,
+                     cudaStream_t st);
 // single-channel sweep (float sinogram, float partial images; rw per ray and scale per slice optional)
 void launch_bp_sweep1(const SliceDesc* dsl, const BlockMap& smap, int nsweep, int C, int tile, bool cluster,
                       const float* sino, const float* rw, const float* scale, float* partial, int64_t stride,
-                      cudaStream_t st);
+                      int* tile_count, cudaStream_t st);
 void launch_bp_finalize(int mode, const SliceDesc* dsl, const BlockMap& pix, int npix, int C, const float2* partial,
                         int64_t stride, float2* out, const BpEpilogue& ep, cudaStream_t st);
 // Single-slice planar R^T (dect_backproject): sino [nch][nv][nb] -> out [nch][ny][nx]. d_dev is the

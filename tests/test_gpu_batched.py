@@ -173,6 +173,28 @@ def test_cluster_reduction_of_view_groups_gives_the_same_bits(cuda_dev, scheme, 
         assert np.array_equal(outs[0][b], outs[1][b])
 
 
+@pytest.mark.parametrize("scheme,slices", [(0, 1), (0, 2), (1, 1)])
+@pytest.mark.parametrize("groups,tile", [(3, 64), (8, 32)])
+def test_last_cta_reduction_of_view_groups_gives_the_same_bits(cuda_dev, scheme, slices, groups, tile):
+    # the last CTA of a tile to finish sums the tile's C partial images in view-group order, the
+    # finalize pass's order, so the reduced form gives the same bits; its arrival counters reset
+    # themselves, so every launch of the captured iterations finds them at zero. Three slices of one
+    # geometry (a pair and a single for the two-slice sweep) and two ragged slices of other sizes.
+    from paper_1905_00934_gb300 import dect
+
+    cases = _same_geometry_cases() + _small_cases()[:2]
+    outs = []
+    for reduce in (-1, 1):
+        sol = _solver(cases, cuda_dev, [None] * 5, bp_view_groups=groups, bp_tile=tile, bp_cluster=-1,
+                      bp_slices=slices, bp_reduce=reduce, scheme=scheme)
+        assert sol.stats(0)["bp_reduce"] == (1 if reduce > 0 else 0)
+        assert sol.stats(0)["bp_slices"] == slices
+        sol.reconstruct(4)
+        outs.append([sol.get(b, dect.X).cpu().numpy() for b in range(5)])
+    for b in range(5):
+        assert np.array_equal(outs[0][b], outs[1][b]), b
+
+
 @pytest.mark.slow
 def test_uneven_64_slice_batch_full_size(cuda_dev):
     # the batched workload at full size: 64 seeded slices, N 256..1024, 360..1440 views,
