@@ -142,7 +142,8 @@ def joseph_weight_count(g) -> int:
 # slices per CTA, reduced form); from the counter captures in profiles/k_bp_sweep_512x720x1024.txt.
 # Reported only when the run uses one of these shapes.
 SWEEP_TRAFFIC = {(8, 8, 32, 0, 1, 0): 134.0e6, (8, 6, 32, 0, 2, 0): 105.2e6, (8, 8, 32, 0, 2, 0): 134.9e6,
-                 (8, 6, 32, 0, 2, 1): 56.9e6}
+                 (8, 6, 32, 0, 2, 1): 56.9e6, (8, 8, 32, 0, 2, 1): 57.8e6, (8, 10, 32, 0, 2, 1): 59.2e6,
+                 (8, 12, 32, 0, 2, 1): 60.2e6}
 
 
 # ------------------------------------------------------------------------------------------------
