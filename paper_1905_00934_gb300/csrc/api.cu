@@ -538,6 +538,9 @@ struct dect_admm {
     std::vector<SliceDesc> hs;
     SliceDesc* ds = nullptr;
     MapBuf rays, pix, tx, ty, rows, cols, sweep, ptile;  // ptile: the projector's (views x bins) tiles per group
+    MapBuf prows, pcols;  // the preconditioner apply's row and column blocks (split or staged, per slice)
+    // row-block prefix of the <r, s> partials the float32 preconditioner wrote
+    const int* rs_prefix() const { return P.precondition ? prows.d : rows.d; }
     int n_groups = 0;                // projector groups: consecutive slices of one geometry (proj_group_size())
     int4* d_groups = nullptr;        // {slice, further slices or -1} per group
     int sweep_C = 1;                 // CTA groups (partial images) per backprojector tile
@@ -558,7 +561,7 @@ struct dect_admm {
     int sweep_groups_in_use = 1;     // view groups per tile (sweep_C CTAs of the kernel's groups each)
     float2* bp_partial = nullptr;    // [sweep_C][n_img] partial images of the backprojector
     int64_t n_img = 0, n_sino = 0, n_tx = 0, n_ty = 0, n_fft = 0, n_h = 0, n_stage = 0;
-    int max_px = 0, min_px = 1 << 30;
+    int max_px = 0, min_px = 1 << 30, min_py = 1 << 30;
     float2 *x = nullptr, *r = nullptr, *s = nullptr, *p = nullptr, *Ap = nullptr, *z = nullptr, *uz = nullptr;
     float2 *x0 = nullptr, *truth = nullptr, *Z = nullptr;
     void *Rx = nullptr, *a = nullptr, *ua = nullptr, *q = nullptr;  // sinogram vectors, storage format `prec`
@@ -566,6 +569,7 @@ struct dect_admm {
     float4 *y = nullptr, *uy = nullptr, *meas = nullptr;
     int prec = PREC_F32;
     float *mu = nullptr, *H = nullptr, *Hn = nullptr, *stage = nullptr;
+    float *Hp = nullptr, *Hnp = nullptr;  // H and Hn permuted for the split column pass
     uint8_t* status = nullptr;
     SliceScalars* sc = nullptr;
     double *part_udm = nullptr, *part_img = nullptr, *part_rs = nullptr, *part_pap = nullptr, *part_xi = nullptr;
@@ -634,7 +638,7 @@ static void free_admm(dect_admm* A) {
                     A->part_img, A->part_rs, A->part_pap, A->part_xi, A->d_has_x0, A->ls, A->lm_scale, A->lm_d,
                     A->lm_r, A->lm_p, A->lm_Ap, A->lm_e, A->lm_g, A->lm_q, A->lm_Rd, A->lm_s0, A->tx1, A->ty1,
                     A->bp_partial1, A->part_lm_pix, A->part_lm_ray, A->cols64.d, A->part_obj_rays,
-                    A->part_obj_pix, A->tile_count};
+                    A->part_obj_pix, A->tile_count, A->prows.d, A->pcols.d, A->Hp, A->Hnp};
     for (void* q : ptrs) cudaFree(q);
     const F64Vecs& v = A->v64;
     for (void* q : {(void*)v.x, (void*)v.r, (void*)v.s, (void*)v.p, (void*)v.Ap, (void*)v.z, (void*)v.uz, (void*)v.x0,
@@ -672,8 +676,9 @@ static void enq_precond(dect_admm* A, const float* H, const float2* r, float2* s
     const int B = A->B;
     pb(A, st);
     if (A->P.precondition) {
-        launch_precond(A->ds, A->rows.map(B), A->rows.total, A->cols.map(B), A->cols.total, H, r, s, A->Z, A->part_rs,
-                       A->tw, A->max_px, A->min_px, st);
+        launch_precond(A->ds, A->prows.map(B), A->prows.total, A->pcols.map(B), A->pcols.total, H,
+                       H == A->H ? A->Hp : A->Hnp, r, s, A->Z, A->part_rs, A->tw, A->max_px, A->min_px, A->max_py,
+                       A->min_py, st);
         pe(A, DECT_PHASE_PRECOND, 3, st);
     } else {
         launch_identity_precond(A->ds, A->rows.map(B), A->rows.total, r, s, A->part_rs, st);
@@ -706,7 +711,7 @@ static void enq_pcg(dect_admm* A, int n, bool with_grad, const float* H, cudaStr
     if (A->counting) A->cRT += 2;
     enq_precond(A, H, A->r, A->p, st);
     pb(A, st);
-    launch_rs_reduce(A->part_rs, A->rows.d, A->sc, B, 1, st);
+    launch_rs_reduce(A->part_rs, A->rs_prefix(), A->sc, B, 1, st);
     pe(A, DECT_PHASE_REDUCE, 1, st);
     for (int it = 0; it < n; ++it) {
         enq_project(A, A->p, A->q, st);
@@ -730,7 +735,7 @@ static void enq_pcg(dect_admm* A, int n, bool with_grad, const float* H, cudaStr
         if (!last) {
             enq_precond(A, H, A->r, A->s, st);
             pb(A, st);
-            launch_rs_reduce(A->part_rs, A->rows.d, A->sc, B, 0, st);
+            launch_rs_reduce(A->part_rs, A->rs_prefix(), A->sc, B, 0, st);
             pe(A, DECT_PHASE_REDUCE, 1, st);
             pb(A, st);
             launch_cg_p(A->ds, A->pix.map(B), A->pix.total, A->sc, A->s, A->p, st);
@@ -1295,6 +1300,8 @@ static dect_status compute_responses(dect_admm* A) {
         launch_psf_to_response(dd, one_slice, BlockMap{pre, 1}, ncols, A->r + sd.img_off, A->Z + sd.fft_off,
                                A->H + sd.h_off, A->Hn + sd.h_off, A->tw, A->P.precondition == DECT_PRECOND_RAMP,
                                st);
+        launch_permute_response(sd, A->H, A->Hp, st);
+        launch_permute_response(sd, A->Hn, A->Hnp, st);
         cudaError_t e = cudaStreamSynchronize(st);
         cudaFree(dd);
         cudaFree(pre);
@@ -1376,7 +1383,8 @@ extern "C" dect_status dect_admm_create(dect_geom* const* geoms, int32_t B, cons
     A->has_x0.assign(B, 0);
     A->has_truth.assign(B, 0);
     A->has_data.assign(B, 0);
-    for (auto* m : {&A->rays, &A->pix, &A->tx, &A->ty, &A->rows, &A->cols, &A->sweep, &A->cols64, &A->ptile})
+    for (auto* m : {&A->rays, &A->pix, &A->tx, &A->ty, &A->rows, &A->cols, &A->sweep, &A->cols64, &A->ptile,
+                    &A->prows, &A->pcols})
         m->h.assign(1, 0);
     std::vector<int> tune;  // candidate CTA groups per tile when autotuning (first = the occupancy choice)
     std::vector<int> tune_tiles;  // candidate tile sides when autotuning
@@ -1467,6 +1475,7 @@ extern "C" dect_status dect_admm_create(dect_geom* const* geoms, int32_t B, cons
         A->max_px = std::max(A->max_px, sd.px);
         A->max_py = std::max(A->max_py, sd.py);
         A->min_px = std::min(A->min_px, sd.px);
+        A->min_py = std::min(A->min_py, sd.py);
         max_np = std::max(max_np, np);
         max_nr = std::max(max_nr, nr);
         A->hs.push_back(sd);
@@ -1479,6 +1488,9 @@ extern "C" dect_status dect_admm_create(dect_geom* const* geoms, int32_t B, cons
         A->rows.h.push_back(A->rows.h.back() + ny);
         const int C = precond_cols_per_block(sd.py);
         A->cols.h.push_back(A->cols.h.back() + (sd.px + C - 1) / C);
+        const int pr = precond_rows_per_block(sd.px), pc = precond_apply_cols_per_block(sd.py);
+        A->prows.h.push_back(A->prows.h.back() + (ny + pr - 1) / pr);
+        A->pcols.h.push_back(A->pcols.h.back() + (sd.px + pc - 1) / pc);
         A->cols64.h.push_back(A->cols64.h.back() + sd.px);
     }
     A->n_stage = std::max(4 * max_nr + 4 * max_np, (int64_t)16);
@@ -1544,6 +1556,8 @@ extern "C" dect_status dect_admm_create(dect_geom* const* geoms, int32_t B, cons
         ALLOC(A->Z, A->n_fft);
         ALLOC(A->H, A->n_h);
         ALLOC(A->Hn, A->n_h);
+        ALLOC(A->Hp, A->n_h);
+        ALLOC(A->Hnp, A->n_h);
     }
     if (P->scheme == DECT_SCHEME_LM_CG) {
         ALLOC(A->ls, B);
@@ -1566,7 +1580,8 @@ extern "C" dect_status dect_admm_create(dect_geom* const* geoms, int32_t B, cons
     if (e == cudaSuccess && A->prec != PREC_F64) e = dalloc(&A->bp_partial, (size_t)A->sweep_C * A->n_img);
     if (e == cudaSuccess && A->prec != PREC_F64) e = dalloc(&A->tile_count, (size_t)A->n_tile_count);
     if (e == cudaSuccess && A->prec != PREC_F64) e = cudaMemset(A->tile_count, 0, sizeof(int) * A->n_tile_count);
-    for (MapBuf* m : {&A->rays, &A->pix, &A->tx, &A->ty, &A->rows, &A->cols, &A->sweep, &A->cols64, &A->ptile})
+    for (MapBuf* m : {&A->rays, &A->pix, &A->tx, &A->ty, &A->rows, &A->cols, &A->sweep, &A->cols64, &A->ptile,
+                      &A->prows, &A->pcols})
         if (e == cudaSuccess) e = upload_map(*m);
     if (e == cudaSuccess) e = dalloc(&A->d_groups, groups.size());
     if (e == cudaSuccess) e = dalloc(&A->d_sgroups, A->sgroups.size());

@@ -245,10 +245,21 @@ void backproject_single_f64(const GeomDev& g, const double4_32a* rays, const dou
 // fft.cu
 const float2* fft_twiddles();   // device table exp(-2 pi i t / kFftMax), t < kFftMax/2 (current device)
 __host__ __device__ int precond_cols_per_block(int py);
+// The preconditioner's apply splits an axis of padded length p in 64..2048 into two half-length register
+// FFTs (a pair of warps per row or column, 4 pairs per 256-thread block); other lengths take the staged
+// path (one row, or precond_cols_per_block(py) columns, per block). The choice depends on the slice only.
+__host__ __device__ inline bool precond_split(int p) { return p >= 64 && p <= 2048; }
+inline int precond_rows_per_block(int px) { return precond_split(px) ? 4 : 1; }
+inline int precond_apply_cols_per_block(int py) { return precond_split(py) ? 4 : precond_cols_per_block(py); }
 // s = M^-1 r per slice and partial[2*blk] = <r, s> per channel over the row blocks
+// (rows_map / cols_map: precond_rows_per_block / precond_apply_cols_per_block blocks; Hp: the response
+// permuted for the split column pass, launch_permute_response)
 void launch_precond(const SliceDesc* dsl, const BlockMap& rows_map, int nrows_blk, const BlockMap& cols_map,
-                    int ncols_blk, const float* H, const float2* r, float2* s, float2* Z, double* partial_rs,
-                    const float2* tw, int max_px, int min_px, cudaStream_t st);
+                    int ncols_blk, const float* H, const float* Hp, const float2* r, float2* s, float2* Z,
+                    double* partial_rs, const float2* tw, int max_px, int min_px, int max_py, int min_py,
+                    cudaStream_t st);
+// Hp[k][h py/2 + t] = H[2 bitrev(t) + h][frequency of storage column k], for a slice whose columns split
+void launch_permute_response(const SliceDesc& d, const float* H, float* Hp, cudaStream_t st);
 // H (and the variant without the D^T D term) from R^T R applied to a centred impulse (one slice)
 // (d_dev: the slice's descriptor on the device with fft_off = h_off = 0; cols_map: its column groups)
 void launch_psf_to_response(const SliceDesc* d_dev, const SliceDesc& d, const BlockMap& cols_map, int ncols,

@@ -48,6 +48,14 @@ const float2* fft_twiddles() {
 
 __device__ __forceinline__ int bitrev(int t, int logn) { return (int)(__brev((unsigned)t) >> (32 - logn)); }
 
+// Shared staging of the register-path FFTs: one float2 of padding after every 32, and columns S(py)
+// apart, so the bit-reversed scatters and gathers spread over the banks (8-byte accesses: 2 to 4
+// wavefronts per warp instead of up to 32). The layout moves data only; the arithmetic is unchanged.
+__host__ __device__ __forceinline__ int spad(int p) { return p + (p >> 5); }
+__host__ __device__ constexpr int col_stride(int py) { return py + py / 32 + 2; }
+constexpr int kColsSmem = 8 * col_stride(1024);  // float2 entries: 8 padded columns of up to 1024 rows
+static_assert(kColsSmem >= 8192, "the shared-memory path stages C(py) * py <= 8192 entries");
+
 __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
     return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
 }
@@ -90,6 +98,33 @@ __device__ void bitrev_permute(float2* buf, int logn, int lane, int nlanes) {
 
 __host__ __device__ int precond_cols_per_block(int py) { return py >= 4096 ? 2 : (py >= 2048 ? 4 : 8); }
 
+// ---- column frequencies of the row pass's output -------------------------------------------------
+// The split row pass (px in 64..2048) stores a row's spectrum half by half, each half in bit-reversed
+// order: storage column k holds frequency 2 * bitrev(k mod px/2) + (k >= px/2). Otherwise storage column
+// k holds frequency k.
+__device__ __forceinline__ int col_freq(int k, int px, int lpx) {
+    if (!precond_split(px)) return k;
+    const int hh = px >> 1;
+    return 2 * bitrev(k & (hh - 1), lpx - 1) + (k >= hh ? 1 : 0);
+}
+
+// W_P^i = exp(-2 pi i i / P) (conjugated for the inverse), P = 2^lp <= kFftMax, i < P / 2
+__device__ __forceinline__ float2 tw_pow(const float2* __restrict__ tw, int i, int lp, bool inverse) {
+    float2 w = __ldg(tw + (i << (kFftMaxLog2 - lp)));
+    if (inverse) w.y = -w.y;
+    return w;
+}
+
+// barrier of the two warps (64 threads) of pair q of a 256-thread block (named barriers 1..4)
+__device__ __forceinline__ void pair_sync(int q) { asm volatile("bar.sync %0, 64;" ::"r"(q + 1) : "memory"); }
+
+static int ilog2_int(int v) {
+    int l = 0;
+    while ((1 << (l + 1)) <= v) ++l;
+    return l;
+}
+
+
 // The same radix-2 DIT FFT (same butterflies, twiddles and operation order, so the same results) held
 // in registers by one warp, for lengths 2^LOG with 5 <= LOG <= 10: lane t holds elements 32 m + t of the
 // bit-reversed sequence in v[m]. Stages with half < 32 pair lanes t and t ^ half (shuffles); stages with
@@ -129,50 +164,81 @@ __device__ __forceinline__ void fft_warp_regs(float2 (&v)[1 << (LOG - 5)], int l
     }
 }
 
+// Forward FFT of the same lengths by decimation in frequency, in registers: lane t holds element 32 m + t
+// of the natural-order sequence in v[m] on entry and element 32 m + t of the bit-reversed spectrum on
+// return (the order the inverse fft_warp_regs takes). Butterflies x0 + x1 and W (x0 - x1), the longest
+// stride first: the stages with half >= 32 within a lane, then the five shuffle stages.
+template <int LOG>
+__device__ __forceinline__ void fft_warp_regs_dif(float2 (&v)[1 << (LOG - 5)], int lane, const float2* __restrict__ tw) {
+    constexpr int M = 1 << (LOG - 5);
+#pragma unroll
+    for (int s = LOG - 1; s >= 5; --s) {
+        const int hs = 1 << (s - 5);
+#pragma unroll
+        for (int m = 0; m < M; ++m) {
+            if (m & hs) continue;
+            const float2 w = __ldg(tw + (((m & (hs - 1)) << 5) + lane) * (kFftMax >> (s + 1)));
+            const float2 a = v[m], b = v[m + hs];
+            v[m] = make_float2(a.x + b.x, a.y + b.y);
+            v[m + hs] = cmul(w, make_float2(a.x - b.x, a.y - b.y));
+        }
+    }
+#pragma unroll
+    for (int s = 4; s >= 0; --s) {
+        const int half = 1 << s;
+        const float2 w = __ldg(tw + (lane & (half - 1)) * (kFftMax >> (s + 1)));
+        const bool upper = (lane & half) != 0;
+#pragma unroll
+        for (int m = 0; m < M; ++m) {
+            const float2 o = make_float2(__shfl_xor_sync(0xffffffffu, v[m].x, half),
+                                         __shfl_xor_sync(0xffffffffu, v[m].y, half));
+            // the lower lane keeps x0 + x1, the upper lane W (x0 - x1), x0 being the lower lane's value
+            v[m] = upper ? cmul(w, make_float2(o.x - v[m].x, o.y - v[m].y)) : make_float2(v[m].x + o.x, v[m].y + o.y);
+        }
+    }
+}
+
 // Column group of k_fft_cols on the register path: 8 columns, warp c owns column c (blockDim 256).
 // buf holds the group's columns in bit-reversed order on entry; on return, rows in natural order.
+// Columns in the padded layout: column c at buf + c * col_stride(py), row j at spad(j).
 template <int LOG>
-__device__ void cols_regs(float2* buf, const float* __restrict__ hs, int px, int k0,
+__device__ void cols_regs(float2* buf, const float* __restrict__ hs, int px, int lpx, int k0,
                           const float2* __restrict__ tw) {
-    constexpr int M = 1 << (LOG - 5), py = 1 << LOG, C = 8;
+    constexpr int M = 1 << (LOG - 5), py = 1 << LOG, C = 8, S = col_stride(py);
     const int c = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    float2* col = buf + c * py;
+    float2* col = buf + c * S;
     float2 v[M];
 #pragma unroll
-    for (int m = 0; m < M; ++m) v[m] = col[(m << 5) + lane];
+    for (int m = 0; m < M; ++m) v[m] = col[spad((m << 5) + lane)];
     fft_warp_regs<LOG>(v, lane, false, tw);
     if (hs) {
 #pragma unroll
-        for (int m = 0; m < M; ++m) col[(m << 5) + lane] = v[m];
+        for (int m = 0; m < M; ++m) col[spad((m << 5) + lane)] = v[m];
         __syncthreads();
         for (int e = threadIdx.x; e < C * py; e += blockDim.x) {
             const int cc = e % C, j = e / C;
             const int k = k0 + cc;
-            const float h = k < px ? __ldg(hs + (size_t)j * px + k) : 0.f;
-            float2& x = buf[cc * py + j];
+            const float h = k < px ? __ldg(hs + (size_t)j * px + col_freq(k, px, lpx)) : 0.f;
+            float2& x = buf[cc * S + spad(j)];
             x.x *= h;
             x.y *= h;
         }
         __syncthreads();
 #pragma unroll
-        for (int m = 0; m < M; ++m) v[m] = col[bitrev((m << 5) + lane, LOG)];
+        for (int m = 0; m < M; ++m) v[m] = col[spad(bitrev((m << 5) + lane, LOG))];
         fft_warp_regs<LOG>(v, lane, true, tw);
     }
     // every lane has passed the shuffles above, so all reads of this column are done
 #pragma unroll
-    for (int m = 0; m < M; ++m) col[(m << 5) + lane] = v[m];
+    for (int m = 0; m < M; ++m) col[spad((m << 5) + lane)] = v[m];
 }
 
 
 
-// forward row FFTs of the image rows (Compton + i PE), zero-padded to px
-__global__ void __launch_bounds__(256) k_prec_rows_fwd(const SliceDesc* __restrict__ dsl, BlockMap map,
-                                                       const float2* __restrict__ r, float2* __restrict__ Z,
-                                                       const float2* __restrict__ tw) {
-    extern __shared__ float2 buf[];
-    int j;
-    const int s = slice_of(map, blockIdx.x, j);
-    const SliceDesc& d = dsl[s];
+// ---- fallback paths (padded length 32 or >= 4096): shared-memory stages, one row or C(py) columns -----
+
+__device__ void row_fwd_staged(const SliceDesc& d, int j, const float2* __restrict__ r, float2* __restrict__ Z,
+                               const float2* __restrict__ tw, float2* buf) {
     const int px = d.px, lp = d.lpx, nx = d.g.nx;
     const float2* row = r + d.img_off + (size_t)j * nx;
     for (int t = threadIdx.x; t < px; t += blockDim.x)
@@ -183,38 +249,40 @@ __global__ void __launch_bounds__(256) k_prec_rows_fwd(const SliceDesc* __restri
     for (int t = threadIdx.x; t < px; t += blockDim.x) zr[t] = buf[t];
 }
 
-// per group of columns: forward column FFT (rows >= rows_in are zero), optional multiplication by H,
-// inverse column FFT; writes rows [0, rows_out)
-__global__ void __launch_bounds__(256) k_fft_cols(const SliceDesc* __restrict__ dsl, BlockMap map,
-                                                  float2* __restrict__ Z, const float* __restrict__ H, int rows_in_all,
-                                                  int rows_out_all, const float2* __restrict__ tw) {
-    extern __shared__ float2 buf[];
-    int g;
-    const int s = slice_of(map, blockIdx.x, g);
-    const SliceDesc& d = dsl[s];
+// per group of C(py) columns: forward column FFT (rows >= rows_in are zero), optional multiplication by
+// H (at the column's frequency, col_freq), inverse column FFT; writes rows [0, rows_out). REGS: the
+// register path for 64 <= py <= 1024 is compiled in (the apply path reaches this only for py = 32 or
+// py >= 4096 and leaves it out, keeping its register count to the split path's).
+template <bool REGS>
+__device__ void cols_staged(const SliceDesc& d, int g, float2* __restrict__ Z, const float* __restrict__ H,
+                            int rows_in_all, int rows_out_all, const float2* __restrict__ tw, float2* buf) {
     const int px = d.px, py = d.py, lp = d.lpy;
     const int C = precond_cols_per_block(py);
     const int k0 = g * C;
     const int rows_in = rows_in_all ? py : d.g.ny;
     const int rows_out = rows_out_all ? py : d.g.ny;
     float2* zs = Z + d.fft_off;
+    // register path (32 <= py <= 1024): padded columns; otherwise columns py apart
+    const bool regs = lp >= 5 && lp <= 10;
+    const int S = regs ? col_stride(py) : py;
     // load: consecutive threads take consecutive columns of one row
     for (int e = threadIdx.x; e < C * py; e += blockDim.x) {
         const int c = e % C, j = e / C;
         const int k = k0 + c;
         float2 v = make_float2(0.f, 0.f);
         if (j < rows_in && k < px) v = zs[(size_t)j * px + k];
-        buf[c * py + bitrev(j, lp)] = v;
+        const int jb = bitrev(j, lp);
+        buf[c * S + (regs ? spad(jb) : jb)] = v;
     }
     __syncthreads();
     const float* hs = H ? H + d.h_off : nullptr;
     switch (lp) {  // one slice per block, so the branch is uniform
-        case 5: cols_regs<5>(buf, hs, px, k0, tw); break;
-        case 6: cols_regs<6>(buf, hs, px, k0, tw); break;
-        case 7: cols_regs<7>(buf, hs, px, k0, tw); break;
-        case 8: cols_regs<8>(buf, hs, px, k0, tw); break;
-        case 9: cols_regs<9>(buf, hs, px, k0, tw); break;
-        case 10: cols_regs<10>(buf, hs, px, k0, tw); break;
+        case 5: cols_regs<5>(buf, hs, px, d.lpx, k0, tw); break;
+        case 6: if constexpr (REGS) cols_regs<6>(buf, hs, px, d.lpx, k0, tw); break;
+        case 7: if constexpr (REGS) cols_regs<7>(buf, hs, px, d.lpx, k0, tw); break;
+        case 8: if constexpr (REGS) cols_regs<8>(buf, hs, px, d.lpx, k0, tw); break;
+        case 9: if constexpr (REGS) cols_regs<9>(buf, hs, px, d.lpx, k0, tw); break;
+        case 10: if constexpr (REGS) cols_regs<10>(buf, hs, px, d.lpx, k0, tw); break;
         default: {  // py < 32 or py >= 2048: shared-memory stages, C columns of blockDim/C threads each
             const int lanes = blockDim.x / C;
             const int c = threadIdx.x / lanes, lane = threadIdx.x % lanes;
@@ -223,7 +291,7 @@ __global__ void __launch_bounds__(256) k_fft_cols(const SliceDesc* __restrict__ 
                 for (int e = threadIdx.x; e < C * py; e += blockDim.x) {
                     const int cc = e % C, j = e / C;
                     const int k = k0 + cc;
-                    const float h = k < px ? __ldg(hs + (size_t)j * px + k) : 0.f;
+                    const float h = k < px ? __ldg(hs + (size_t)j * px + col_freq(k, px, d.lpx)) : 0.f;
                     float2& v = buf[cc * py + j];
                     v.x *= h;
                     v.y *= h;
@@ -238,19 +306,15 @@ __global__ void __launch_bounds__(256) k_fft_cols(const SliceDesc* __restrict__ 
     for (int e = threadIdx.x; e < C * rows_out; e += blockDim.x) {
         const int cc = e % C, j = e / C;
         const int k = k0 + cc;
-        if (k < px) zs[(size_t)j * px + k] = buf[cc * py + j];
+        if (k < px) zs[(size_t)j * px + k] = buf[cc * S + (regs ? spad(j) : j)];
     }
 }
 
-// inverse row FFTs, crop to nx, scale by 1/(px*py): s = {Re, Im}; partial <r, s> per channel
-__global__ void __launch_bounds__(256) k_prec_rows_inv(const SliceDesc* __restrict__ dsl, BlockMap map,
-                                                       const float2* __restrict__ Z, const float2* __restrict__ r,
-                                                       float2* __restrict__ s_out, double* __restrict__ partial,
-                                                       const float2* __restrict__ tw) {
-    extern __shared__ float2 buf[];
-    int j;
-    const int s = slice_of(map, blockIdx.x, j);
-    const SliceDesc& d = dsl[s];
+// inverse row FFT of row j, crop to nx, scale by 1/(px*py) into s_out; threads 0..31 return <r, s> of
+// the row per channel (a lane's products in float32, the lanes in float64), the others zero
+__device__ void row_inv_staged(const SliceDesc& d, int j, const float2* __restrict__ Z, const float2* __restrict__ r,
+                               float2* __restrict__ s_out, const float2* __restrict__ tw, float2* buf, double& dc,
+                               double& dp) {
     const int px = d.px, lp = d.lpx, nx = d.g.nx;
     const float2* zr = Z + d.fft_off + (size_t)j * px;
     for (int t = threadIdx.x; t < px; t += blockDim.x) buf[bitrev(t, lp)] = zr[t];
@@ -260,131 +324,317 @@ __global__ void __launch_bounds__(256) k_prec_rows_inv(const SliceDesc* __restri
     const size_t row = d.img_off + (size_t)j * nx;
     for (int t = threadIdx.x; t < nx; t += blockDim.x)
         s_out[row + t] = make_float2(buf[t].x * scale, buf[t].y * scale);
-    // <r, s> of the row in the order of the register path (lane l takes t = l, l + 32, ..., then a
-    // shuffle tree), so a slice gets the same partials whichever row kernel a batch launches
+    dc = dp = 0.0;
     if (threadIdx.x < 32) {
-        double dc = 0.0, dp = 0.0;
+        float fc = 0.f, fp = 0.f;
         for (int t = threadIdx.x; t < nx; t += 32) {
             const float2 v = make_float2(buf[t].x * scale, buf[t].y * scale);
             const float2 rv = __ldg(r + row + t);
-            dc = fma((double)rv.x, (double)v.x, dc);
-            dp = fma((double)rv.y, (double)v.y, dp);
+            fc = fmaf(rv.x, v.x, fc);
+            fp = fmaf(rv.y, v.y, fp);
         }
+        dc = (double)fc;
+        dp = (double)fp;
         for (int o = 16; o > 0; o >>= 1) {
             dc += __shfl_down_sync(0xffffffffu, dc, o);
             dp += __shfl_down_sync(0xffffffffu, dp, o);
         }
+    }
+}
+
+// The response path's column pass (H = nullptr) and any caller of the staged column pass.
+__global__ void __launch_bounds__(256) k_fft_cols(const SliceDesc* __restrict__ dsl, BlockMap map,
+                                                  float2* __restrict__ Z, const float* __restrict__ H, int rows_in_all,
+                                                  int rows_out_all, const float2* __restrict__ tw) {
+    extern __shared__ float2 buf[];
+    int g;
+    const int s = slice_of(map, blockIdx.x, g);
+    cols_staged<true>(dsl[s], g, Z, H, rows_in_all, rows_out_all, tw, buf);
+}
+
+// ---- the preconditioner's apply path: split-half register FFTs ----------------------------------------
+// Along an axis of padded length P (64..2048) only the first P/2 entries are non-zero (the grid pads
+// each image axis at least twice), so the length-P spectrum splits exactly into two length-P/2 ones:
+// X[2f + h] = DFT_{P/2}(x[i] W_P^{h i})[f], h = 0, 1. A pair of warps holds one row or column, warp h
+// computing half h in registers (fft_warp_regs_dif: natural order in, bit-reversed out). The inverse
+// takes each half back with fft_warp_regs (bit-reversed in, natural out) and recombines:
+// x[n] = z_0[n] + W_P^{-n} z_1[n] for the n < P/2 that are kept. A 256-thread block holds 4 pairs.
+// Slices with another padded length use the staged paths above in the same launch (one row, or C(py)
+// columns, per block); the choice depends on the slice alone.
+
+template <int L>
+__device__ __forceinline__ void split_row_fwd(const float2* __restrict__ row, int nx, float2* __restrict__ zr, int h,
+                                              const float2* __restrict__ tw) {
+    constexpr int M = 1 << (L - 5), HH = 1 << L;
+    const int lane = threadIdx.x & 31;
+    float2 v[M];
+#pragma unroll
+    for (int m = 0; m < M; ++m) {
+        const int i = (m << 5) + lane;
+        const float2 x = i < nx ? __ldg(row + i) : make_float2(0.f, 0.f);
+        v[m] = h ? cmul(tw_pow(tw, i, L + 1, false), x) : x;
+    }
+    fft_warp_regs_dif<L>(v, lane, tw);
+#pragma unroll
+    for (int m = 0; m < M; ++m) zr[h * HH + (m << 5) + lane] = v[m];
+}
+
+// forward row FFTs of the image rows (Compton + i PE), zero-padded to px: split rows 4 per block,
+// others one per block
+template <int LMAX>
+__global__ void __launch_bounds__(256) k_prec_rows_fwd(const SliceDesc* __restrict__ dsl, BlockMap map,
+                                                       const float2* __restrict__ r, float2* __restrict__ Z,
+                                                       const float2* __restrict__ tw) {
+    extern __shared__ float2 buf[];
+    int blk;
+    const int s = slice_of(map, blockIdx.x, blk);
+    const SliceDesc& d = dsl[s];
+    if (!precond_split(d.px)) {
+        row_fwd_staged(d, blk, r, Z, tw, buf);
+        return;
+    }
+    const int q = threadIdx.x >> 6, h = (threadIdx.x >> 5) & 1;
+    const int j = blk * 4 + q;
+    if (j >= d.g.ny) return;  // warp-uniform; this path has no barriers
+    const float2* row = r + d.img_off + (size_t)j * d.g.nx;
+    float2* zr = Z + d.fft_off + (size_t)j * d.px;
+    switch (d.lpx - 1) {
+        case 5: split_row_fwd<5>(row, d.g.nx, zr, h, tw); break;
+        case 6: split_row_fwd<(LMAX < 6 ? LMAX : 6)>(row, d.g.nx, zr, h, tw); break;
+        case 7: split_row_fwd<(LMAX < 7 ? LMAX : 7)>(row, d.g.nx, zr, h, tw); break;
+        case 8: split_row_fwd<(LMAX < 8 ? LMAX : 8)>(row, d.g.nx, zr, h, tw); break;
+        case 9: split_row_fwd<(LMAX < 9 ? LMAX : 9)>(row, d.g.nx, zr, h, tw); break;
+        default: split_row_fwd<LMAX>(row, d.g.nx, zr, h, tw); break;
+    }
+}
+
+// Column pair q of the block: staged column c = q in buf (padded, natural row order, rows < ny), Hp the
+// slice's permuted response (Hp[k][h P/2 + t] = H at row frequency 2 bitrev(t) + h, column frequency
+// col_freq(k)); the recombined column is written back to its staging column.
+template <int L>
+__device__ __forceinline__ void split_col(float2* col, const float* __restrict__ hp, int ny, int h, int q,
+                                          const float2* __restrict__ tw) {
+    constexpr int M = 1 << (L - 5), HH = 1 << L;
+    const int lane = threadIdx.x & 31;
+    float2 v[M];
+#pragma unroll
+    for (int m = 0; m < M; ++m) {
+        const int j = (m << 5) + lane;
+        const float2 x = j < ny ? col[spad(j)] : make_float2(0.f, 0.f);
+        v[m] = h ? cmul(tw_pow(tw, j, L + 1, false), x) : x;
+    }
+    pair_sync(q);  // both warps hold the column: its staging may be overwritten below
+    fft_warp_regs_dif<L>(v, lane, tw);
+#pragma unroll
+    for (int m = 0; m < M; ++m) {
+        const float hv = __ldg(hp + h * HH + (m << 5) + lane);
+        v[m].x *= hv;
+        v[m].y *= hv;
+    }
+    fft_warp_regs<L>(v, lane, true, tw);
+    if (h) {
+#pragma unroll
+        for (int m = 0; m < M; ++m) {
+            const int n = (m << 5) + lane;
+            if (n < ny) col[spad(n)] = cmul(tw_pow(tw, n, L + 1, true), v[m]);
+        }
+    }
+    pair_sync(q);
+    if (!h) {
+#pragma unroll
+        for (int m = 0; m < M; ++m) {
+            const int n = (m << 5) + lane;
+            if (n < ny) {
+                const float2 t = col[spad(n)];
+                col[spad(n)] = make_float2(v[m].x + t.x, v[m].y + t.y);
+            }
+        }
+    }
+}
+
+// the column pass of the apply: split columns 4 per block (staged through padded shared memory so the
+// loads and stores take 4 neighbouring columns of a row), others C(py) per block (cols_staged)
+template <int LMAX>
+__global__ void __launch_bounds__(256) k_prec_cols(const SliceDesc* __restrict__ dsl, BlockMap map,
+                                                   float2* __restrict__ Z, const float* __restrict__ H,
+                                                   const float* __restrict__ Hp, const float2* __restrict__ tw) {
+    extern __shared__ float2 buf[];
+    int g;
+    const int s = slice_of(map, blockIdx.x, g);
+    const SliceDesc& d = dsl[s];
+    if (!precond_split(d.py)) {
+        cols_staged<false>(d, g, Z, H, 0, 0, tw, buf);
+        return;
+    }
+    const int px = d.px, ny = d.g.ny, k0 = g * 4;
+    const int S = spad(d.py >> 1) + 2;  // padded staging column
+    float2* zs = Z + d.fft_off;
+    for (int e = threadIdx.x; e < 4 * ny; e += blockDim.x) {
+        const int c = e & 3, j = e >> 2, k = k0 + c;
+        buf[c * S + spad(j)] = k < px ? zs[(size_t)j * px + k] : make_float2(0.f, 0.f);
+    }
+    __syncthreads();
+    const int q = threadIdx.x >> 6, h = (threadIdx.x >> 5) & 1;
+    const int k = k0 + q;
+    if (k < px) {  // pair-uniform
+        float2* col = buf + q * S;
+        const float* hp = Hp + d.h_off + (size_t)k * d.py;
+        switch (d.lpy - 1) {
+            case 5: split_col<5>(col, hp, ny, h, q, tw); break;
+            case 6: split_col<(LMAX < 6 ? LMAX : 6)>(col, hp, ny, h, q, tw); break;
+            case 7: split_col<(LMAX < 7 ? LMAX : 7)>(col, hp, ny, h, q, tw); break;
+            case 8: split_col<(LMAX < 8 ? LMAX : 8)>(col, hp, ny, h, q, tw); break;
+            case 9: split_col<(LMAX < 9 ? LMAX : 9)>(col, hp, ny, h, q, tw); break;
+            default: split_col<LMAX>(col, hp, ny, h, q, tw); break;
+        }
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < 4 * ny; e += blockDim.x) {
+        const int c = e & 3, j = e >> 2, k = k0 + c;
+        if (k < px) zs[(size_t)j * px + k] = buf[c * S + spad(j)];
+    }
+}
+
+// Row pair q: inverse of the split row spectrum, recombined, cropped to nx and scaled into s_out; the
+// pair's first warp returns <r, s> of the row per channel (lane products in float32, lanes in float64).
+template <int L>
+__device__ __forceinline__ void split_row_inv(const float2* __restrict__ zr, const float2* __restrict__ rr,
+                                              float2* __restrict__ so, int nx, float scale, int h, int q, float2* ex,
+                                              const float2* __restrict__ tw, double& dc, double& dp) {
+    constexpr int M = 1 << (L - 5), HH = 1 << L;
+    const int lane = threadIdx.x & 31;
+    float2 v[M];
+#pragma unroll
+    for (int m = 0; m < M; ++m) v[m] = zr[h * HH + (m << 5) + lane];
+    fft_warp_regs<L>(v, lane, true, tw);
+    if (h) {
+#pragma unroll
+        for (int m = 0; m < M; ++m) {
+            const int n = (m << 5) + lane;
+            if (n < nx) ex[n] = cmul(tw_pow(tw, n, L + 1, true), v[m]);
+        }
+    }
+    pair_sync(q);
+    dc = dp = 0.0;
+    if (!h) {
+        float fc = 0.f, fp = 0.f;
+#pragma unroll
+        for (int m = 0; m < M; ++m) {
+            const int n = (m << 5) + lane;
+            if (n < nx) {
+                const float2 t = ex[n];
+                const float2 x = make_float2((v[m].x + t.x) * scale, (v[m].y + t.y) * scale);
+                so[n] = x;
+                const float2 rv = __ldg(rr + n);
+                fc = fmaf(rv.x, x.x, fc);
+                fp = fmaf(rv.y, x.y, fp);
+            }
+        }
+        dc = (double)fc;
+        dp = (double)fp;
+        for (int o = 16; o > 0; o >>= 1) {
+            dc += __shfl_down_sync(0xffffffffu, dc, o);
+            dp += __shfl_down_sync(0xffffffffu, dp, o);
+        }
+    }
+}
+
+// inverse row FFTs, crop to nx, scale by 1/(px*py): s = {Re, Im}; one partial <r, s> per block and
+// channel (split rows: the block's 4 rows added in order)
+template <int LMAX>
+__global__ void __launch_bounds__(256) k_prec_rows_inv(const SliceDesc* __restrict__ dsl, BlockMap map,
+                                                       const float2* __restrict__ Z, const float2* __restrict__ r,
+                                                       float2* __restrict__ s_out, double* __restrict__ partial,
+                                                       const float2* __restrict__ tw) {
+    extern __shared__ float2 buf[];
+    __shared__ double red[4][2];
+    int blk;
+    const int s = slice_of(map, blockIdx.x, blk);
+    const SliceDesc& d = dsl[s];
+    double dc = 0.0, dp = 0.0;
+    if (!precond_split(d.px)) {
+        row_inv_staged(d, blk, Z, r, s_out, tw, buf, dc, dp);
         if (threadIdx.x == 0) {
             partial[2 * (size_t)blockIdx.x] = dc;
             partial[2 * (size_t)blockIdx.x + 1] = dp;
         }
+        return;
     }
-}
-
-// Row passes on the register path (every slice's padded row length in 32..1024): one warp per row,
-// blockDim 32, the row staged in shared memory only for the bit-reversal.
-template <int LOG>
-__device__ void row_fwd_regs(const float2* __restrict__ row, int nx, float2* __restrict__ zr, float2* buf,
-                             const float2* __restrict__ tw) {
-    constexpr int M = 1 << (LOG - 5), n = 1 << LOG;
-    const int lane = threadIdx.x;
-    for (int t = lane; t < n; t += 32) buf[bitrev(t, LOG)] = t < nx ? __ldg(row + t) : make_float2(0.f, 0.f);
-    __syncwarp();
-    float2 v[M];
-#pragma unroll
-    for (int m = 0; m < M; ++m) v[m] = buf[(m << 5) + lane];
-    fft_warp_regs<LOG>(v, lane, false, tw);
-#pragma unroll
-    for (int m = 0; m < M; ++m) zr[(m << 5) + lane] = v[m];
-}
-
-template <int LOG>
-__device__ void row_inv_regs(const float2* __restrict__ zr, float2* buf, const float2* __restrict__ tw, float scale,
-                             const float2* __restrict__ r, float2* __restrict__ s_out, int nx, double& dc, double& dp) {
-    constexpr int M = 1 << (LOG - 5), n = 1 << LOG;
-    const int lane = threadIdx.x;
-    for (int t = lane; t < n; t += 32) buf[bitrev(t, LOG)] = zr[t];
-    __syncwarp();
-    float2 v[M];
-#pragma unroll
-    for (int m = 0; m < M; ++m) v[m] = buf[(m << 5) + lane];
-    fft_warp_regs<LOG>(v, lane, true, tw);
-#pragma unroll
-    for (int m = 0; m < M; ++m) {
-        const int t = (m << 5) + lane;
-        if (t < nx) {
-            const float2 x = make_float2(v[m].x * scale, v[m].y * scale);
-            s_out[t] = x;
-            const float2 rv = __ldg(r + t);
-            dc = fma((double)rv.x, (double)x.x, dc);
-            dp = fma((double)rv.y, (double)x.y, dp);
+    const int q = threadIdx.x >> 6, h = (threadIdx.x >> 5) & 1;
+    const int j = blk * 4 + q;
+    if (j < d.g.ny) {  // pair-uniform
+        const float scale = 1.0f / ((float)d.px * (float)d.py);
+        const float2* zr = Z + d.fft_off + (size_t)j * d.px;
+        const size_t row = d.img_off + (size_t)j * d.g.nx;
+        float2* ex = buf + q * (d.px >> 1);
+        switch (d.lpx - 1) {
+            case 5: split_row_inv<5>(zr, r + row, s_out + row, d.g.nx, scale, h, q, ex, tw, dc, dp); break;
+            case 6: split_row_inv<(LMAX < 6 ? LMAX : 6)>(zr, r + row, s_out + row, d.g.nx, scale, h, q, ex, tw, dc, dp); break;
+            case 7: split_row_inv<(LMAX < 7 ? LMAX : 7)>(zr, r + row, s_out + row, d.g.nx, scale, h, q, ex, tw, dc, dp); break;
+            case 8: split_row_inv<(LMAX < 8 ? LMAX : 8)>(zr, r + row, s_out + row, d.g.nx, scale, h, q, ex, tw, dc, dp); break;
+            case 9: split_row_inv<(LMAX < 9 ? LMAX : 9)>(zr, r + row, s_out + row, d.g.nx, scale, h, q, ex, tw, dc, dp); break;
+            default: split_row_inv<LMAX>(zr, r + row, s_out + row, d.g.nx, scale, h, q, ex, tw, dc, dp); break;
         }
     }
-}
-
-__global__ void __launch_bounds__(32) k_prec_rows_fwd_w(const SliceDesc* __restrict__ dsl, BlockMap map,
-                                                        const float2* __restrict__ r, float2* __restrict__ Z,
-                                                        const float2* __restrict__ tw) {
-    extern __shared__ float2 buf[];
-    int j;
-    const int s = slice_of(map, blockIdx.x, j);
-    const SliceDesc& d = dsl[s];
-    const float2* row = r + d.img_off + (size_t)j * d.g.nx;
-    float2* zr = Z + d.fft_off + (size_t)j * d.px;
-    switch (d.lpx) {
-        case 5: row_fwd_regs<5>(row, d.g.nx, zr, buf, tw); break;
-        case 6: row_fwd_regs<6>(row, d.g.nx, zr, buf, tw); break;
-        case 7: row_fwd_regs<7>(row, d.g.nx, zr, buf, tw); break;
-        case 8: row_fwd_regs<8>(row, d.g.nx, zr, buf, tw); break;
-        case 9: row_fwd_regs<9>(row, d.g.nx, zr, buf, tw); break;
-        default: row_fwd_regs<10>(row, d.g.nx, zr, buf, tw); break;
+    if ((threadIdx.x & 63) == 0) {
+        red[q][0] = dc;
+        red[q][1] = dp;
     }
-}
-
-__global__ void __launch_bounds__(32) k_prec_rows_inv_w(const SliceDesc* __restrict__ dsl, BlockMap map,
-                                                        const float2* __restrict__ Z, const float2* __restrict__ r,
-                                                        float2* __restrict__ s_out, double* __restrict__ partial,
-                                                        const float2* __restrict__ tw) {
-    extern __shared__ float2 buf[];
-    int j;
-    const int s = slice_of(map, blockIdx.x, j);
-    const SliceDesc& d = dsl[s];
-    const float2* zr = Z + d.fft_off + (size_t)j * d.px;
-    const size_t row = d.img_off + (size_t)j * d.g.nx;
-    const float scale = 1.0f / ((float)d.px * (float)d.py);
-    double dc = 0.0, dp = 0.0;
-    switch (d.lpx) {
-        case 5: row_inv_regs<5>(zr, buf, tw, scale, r + row, s_out + row, d.g.nx, dc, dp); break;
-        case 6: row_inv_regs<6>(zr, buf, tw, scale, r + row, s_out + row, d.g.nx, dc, dp); break;
-        case 7: row_inv_regs<7>(zr, buf, tw, scale, r + row, s_out + row, d.g.nx, dc, dp); break;
-        case 8: row_inv_regs<8>(zr, buf, tw, scale, r + row, s_out + row, d.g.nx, dc, dp); break;
-        case 9: row_inv_regs<9>(zr, buf, tw, scale, r + row, s_out + row, d.g.nx, dc, dp); break;
-        default: row_inv_regs<10>(zr, buf, tw, scale, r + row, s_out + row, d.g.nx, dc, dp); break;
-    }
-    for (int o = 16; o > 0; o >>= 1) {
-        dc += __shfl_down_sync(0xffffffffu, dc, o);
-        dp += __shfl_down_sync(0xffffffffu, dp, o);
-    }
+    __syncthreads();
     if (threadIdx.x == 0) {
-        partial[2 * (size_t)blockIdx.x] = dc;
-        partial[2 * (size_t)blockIdx.x + 1] = dp;
+        partial[2 * (size_t)blockIdx.x] = ((red[0][0] + red[1][0]) + red[2][0]) + red[3][0];
+        partial[2 * (size_t)blockIdx.x + 1] = ((red[0][1] + red[1][1]) + red[2][1]) + red[3][1];
     }
+}
+
+// Hp of a slice with a split column pass: Hp[k][h py/2 + t] = H[2 bitrev(t) + h][col_freq(k)]
+__global__ void k_permute_response(SliceDesc d, const float* __restrict__ H, float* __restrict__ Hp) {
+    const int64_t n = (int64_t)d.px * d.py;
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n) return;
+    const int k = (int)(e / d.py), qy = (int)(e % d.py);
+    const int hh = d.py >> 1;
+    const int ky = 2 * bitrev(qy & (hh - 1), d.lpy - 1) + (qy >= hh ? 1 : 0);
+    Hp[e] = H[(size_t)ky * d.px + col_freq(k, d.px, d.lpx)];
+}
+
+void launch_permute_response(const SliceDesc& d, const float* H, float* Hp, cudaStream_t st) {
+    if (!precond_split(d.py)) return;
+    const int64_t n = (int64_t)d.px * d.py;
+    k_permute_response<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(d, H + d.h_off, Hp + d.h_off);
+}
+
+template <int LMAX>
+static void precond_t(const SliceDesc* dsl, const BlockMap& rows_map, int nrows_blk, const BlockMap& cols_map,
+                      int ncols_blk, const float* H, const float* Hp, const float2* r, float2* s, float2* Z,
+                      double* partial_rs, const float2* tw, size_t smem_fwd, size_t smem_cols, size_t smem_inv,
+                      cudaStream_t st) {
+    k_prec_rows_fwd<LMAX><<<nrows_blk, 256, smem_fwd, st>>>(dsl, rows_map, r, Z, tw);
+    k_prec_cols<LMAX><<<ncols_blk, 256, smem_cols, st>>>(dsl, cols_map, Z, H, Hp, tw);
+    k_prec_rows_inv<LMAX><<<nrows_blk, 256, smem_inv, st>>>(dsl, rows_map, Z, r, s, partial_rs, tw);
 }
 
 void launch_precond(const SliceDesc* dsl, const BlockMap& rows_map, int nrows_blk, const BlockMap& cols_map,
-                    int ncols_blk, const float* H, const float2* r, float2* s, float2* Z, double* partial_rs,
-                    const float2* tw, int max_px, int min_px, cudaStream_t st) {
-    const bool warp_rows = min_px >= 32 && max_px <= 1024;
-    if (warp_rows)
-        k_prec_rows_fwd_w<<<nrows_blk, 32, sizeof(float2) * max_px, st>>>(dsl, rows_map, r, Z, tw);
+                    int ncols_blk, const float* H, const float* Hp, const float2* r, float2* s, float2* Z,
+                    double* partial_rs, const float2* tw, int max_px, int min_px, int max_py, int min_py,
+                    cudaStream_t st) {
+    // shared memory: the staged paths' row (px) or columns (kColsSmem) where some slice takes them; the
+    // split paths' 4 padded staging columns and 4 half-rows of exchange
+    const bool all_x = min_px >= 64 && max_px <= 2048, all_y = min_py >= 64 && max_py <= 2048;
+    const size_t f2 = sizeof(float2);
+    const size_t smem_fwd = all_x ? 0 : f2 * max_px;
+    const size_t smem_inv = f2 * std::max(all_x ? 0 : max_px, 4 * (std::min(max_px, 2048) / 2));
+    const size_t smem_cols = f2 * std::max(all_y ? 0 : kColsSmem, 4 * (spad(std::min(max_py, 2048) / 2) + 2));
+    const int lmax = std::max(ilog2_int(std::min(std::max(max_px, max_py), 2048)) - 1, 5);
+    if (lmax <= 8)
+        precond_t<8>(dsl, rows_map, nrows_blk, cols_map, ncols_blk, H, Hp, r, s, Z, partial_rs, tw, smem_fwd, smem_cols,
+                     smem_inv, st);
+    else if (lmax == 9)
+        precond_t<9>(dsl, rows_map, nrows_blk, cols_map, ncols_blk, H, Hp, r, s, Z, partial_rs, tw, smem_fwd, smem_cols,
+                     smem_inv, st);
     else
-        k_prec_rows_fwd<<<nrows_blk, 256, sizeof(float2) * max_px, st>>>(dsl, rows_map, r, Z, tw);
-    // C(py) * py <= 8192 complex entries for every py <= 4096
-    k_fft_cols<<<ncols_blk, 256, sizeof(float2) * 8192, st>>>(dsl, cols_map, Z, H, 0, 0, tw);
-    if (warp_rows)
-        k_prec_rows_inv_w<<<nrows_blk, 32, sizeof(float2) * max_px, st>>>(dsl, rows_map, Z, r, s, partial_rs, tw);
-    else
-        k_prec_rows_inv<<<nrows_blk, 256, sizeof(float2) * max_px, st>>>(dsl, rows_map, Z, r, s, partial_rs, tw);
+        precond_t<10>(dsl, rows_map, nrows_blk, cols_map, ncols_blk, H, Hp, r, s, Z, partial_rs, tw, smem_fwd,
+                      smem_cols, smem_inv, st);
 }
 
 // ---- response H from the point response of R^T R ---------------------------------------------
@@ -447,12 +697,17 @@ void launch_psf_to_response(const SliceDesc* d_dev, const SliceDesc& d, const Bl
     const int64_t n = (int64_t)d.px * d.py;
     k_embed_psf<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(d, psf, Z);
     k_fft_rows_full<<<d.py, 256, sizeof(float2) * d.px, st>>>(d, Z, tw);
-    k_fft_cols<<<ncols, 256, sizeof(float2) * 8192, st>>>(d_dev, cols_map, Z, nullptr, 1, 1, tw);
+    k_fft_cols<<<ncols, 256, sizeof(float2) * kColsSmem, st>>>(d_dev, cols_map, Z, nullptr, 1, 1, tw);
     k_response<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(d, Z, H, H_nograd, ramp);
 }
 
 cudaError_t fft_init_attributes() {
-    return cudaFuncSetAttribute(k_fft_cols, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(sizeof(float2) * 8192));
+    const int cols = (int)(sizeof(float2) * kColsSmem);
+    cudaError_t e = cudaFuncSetAttribute(k_fft_cols, cudaFuncAttributeMaxDynamicSharedMemorySize, cols);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_prec_cols<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, cols);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_prec_cols<9>, cudaFuncAttributeMaxDynamicSharedMemorySize, cols);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_prec_cols<10>, cudaFuncAttributeMaxDynamicSharedMemorySize, cols);
+    return e;
 }
 
 }  // namespace dect
