@@ -141,6 +141,11 @@ def joseph_weight_count(g) -> int:
 # keyed by the launch shape they were captured with (slices, view groups, tile side, cluster form,
 # slices per CTA, reduced form); from the counter captures in profiles/k_bp_sweep_512x720x1024.txt.
 # Reported only when the run uses one of these shapes.
+# Shared-memory wavefronts per slice of the backprojector sweep on the same workload (ncu
+# l1tex__data_pipe_lsu_wavefronts_mem_shared.sum), keyed by (tile side, slices per CTA); the count
+# follows the samples and staged rays, not the view-group count. The SM serves one wavefront per clock.
+SWEEP_SMEM_WAVEFRONTS = {(32, 1): 9.64e7, (32, 2): 8.65e7}
+
 SWEEP_TRAFFIC = {(8, 8, 32, 0, 1, 0): 134.0e6, (8, 6, 32, 0, 2, 0): 105.2e6, (8, 8, 32, 0, 2, 0): 134.9e6,
                  (8, 6, 32, 0, 2, 1): 56.9e6, (8, 8, 32, 0, 2, 1): 57.8e6, (8, 10, 32, 0, 2, 1): 59.2e6,
                  (8, 12, 32, 0, 2, 1): 60.2e6}
@@ -482,6 +487,15 @@ def run_dect(args):
             "avg_launch_ms": bp_ms, "algorithmic_flops_per_launch": B * 4 * nnz,
             "algorithmic_bytes_per_launch": bp_bytes, "hbm_achieved_gbs": bp_gbs, "hbm_peak_gbs": peak,
             "hbm_frac": bp_gbs / peak, "hbm_peak_kind": peak_kind}
+    wf = SWEEP_SMEM_WAVEFRONTS.get((st0["bp_tile"], st0["bp_slices"]))
+    if wf and top == "backproject":
+        # the sweep's actual limit: shared-memory wavefronts (accumulator read-modify-writes and staging)
+        clk = (clocks.get("sm_max_mhz") or 2070.0) * 1e6
+        achieved_wf = B * wf / (bp_ms / 1e3)
+        roof["onchip"] = {"resource": "shared-memory wavefronts", "per_launch": B * wf,
+                          "achieved_per_s": achieved_wf, "peak_per_s": n_sm * clk, "frac": achieved_wf / (n_sm * clk),
+                          "source": "per-slice count from a stored ncu capture "
+                                    "(profiles/k_bp_sweep_512x720x1024.txt); peak one per SM per clock"}
     # the HBM-bound phases (data read and written once per iteration; 8 slices exceed L2): the four
     # element-wise kernels of an iteration (b = a + u^a - R x: 32 B/ray; x, R x += alpha p, q: 24 B/pixel
     # + 24 B/ray; y, z, u^y, u^z of Eq. 9-11 with x: 104 B/pixel; the dual rescale moves nothing when
