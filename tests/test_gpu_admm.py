@@ -173,8 +173,8 @@ def test_graph_and_eager_are_bitwise_equal_and_deterministic(cuda_dev, small100)
 
     c, _, x0 = small100
     outs = []
-    for use_graph in (1, 0, 1):
-        sol = _solver(c, cuda_dev, x0, use_graph=use_graph)
+    for use_graph in (1, 0, 1):  # three solvers, one view-group count (the order of R^T's partial sums)
+        sol = _solver(c, cuda_dev, x0, use_graph=use_graph, bp_view_groups=4)
         sol.step(5)
         outs.append(sol.get(0, dect.X).cpu().numpy())
     assert np.array_equal(outs[0], outs[1]) and np.array_equal(outs[0], outs[2])
