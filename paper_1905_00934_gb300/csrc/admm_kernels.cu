@@ -7,6 +7,8 @@
 // to a slot indexed by its block number, and one block per slice adds its
 // slots in a fixed order. All scalars stay on the device.
 #include <cuda_runtime.h>
+
+#include <algorithm>
 #include <math.h>
 
 #include "admm_kernels.cuh"
@@ -219,21 +221,18 @@ __global__ void __launch_bounds__(256) k_rho_update(const double* __restrict__ p
     }
 }
 
-// scaled duals follow rho: u /= factor (no-op when both factors are 1)
+// scaled duals follow rho: u /= factor (no-op when both factors are 1). G blocks per slice stride over
+// the slice's pixels and rays, so a slice whose rho stayed costs its G blocks one test each.
 template <class S2>
-__global__ void __launch_bounds__(256) k_dual_rescale(const SliceDesc* __restrict__ dsl, BlockMap pix, int nblk_pix,
-                                                      BlockMap rays, const SliceScalars* __restrict__ sc,
-                                                      float4* __restrict__ uy, float2* __restrict__ uz,
-                                                      S2* __restrict__ ua) {
-    int local;
-    const bool img = (int)blockIdx.x < nblk_pix;
-    const int s = img ? slice_of(pix, blockIdx.x, local) : slice_of(rays, blockIdx.x - nblk_pix, local);
+__global__ void __launch_bounds__(256) k_dual_rescale(const SliceDesc* __restrict__ dsl, int G,
+                                                      const SliceScalars* __restrict__ sc, float4* __restrict__ uy,
+                                                      float2* __restrict__ uz, S2* __restrict__ ua) {
+    const int s = blockIdx.x / G, g = blockIdx.x % G;
     const float gc = sc[s].ifactor_f[0], gp = sc[s].ifactor_f[1];  // exactly 1, 1/tau or tau
     if (gc == 1.0f && gp == 1.0f) return;
     const SliceDesc& d = dsl[s];
-    const int64_t k = (int64_t)local * 256 + threadIdx.x;
-    if (img) {
-        if (k >= (int64_t)d.g.nx * d.g.ny) return;
+    const int64_t np = (int64_t)d.g.nx * d.g.ny, nr = (int64_t)d.g.nv * d.g.nb, step = (int64_t)G * blockDim.x;
+    for (int64_t k = (int64_t)g * blockDim.x + threadIdx.x; k < np; k += step) {
         const int64_t e = d.img_off + k;
         float4 u = uy[e];
         float2 w = uz[e];
@@ -245,8 +244,8 @@ __global__ void __launch_bounds__(256) k_dual_rescale(const SliceDesc* __restric
         w.x *= gc;
         w.y *= gp;
         uz[e] = w;
-    } else {
-        if (k >= (int64_t)d.g.nv * d.g.nb) return;
+    }
+    for (int64_t k = (int64_t)g * blockDim.x + threadIdx.x; k < nr; k += step) {
         const int64_t e = d.sino_off + k;
         float2 u = ld2(ua + e);
         u.x *= gc;
@@ -525,9 +524,14 @@ void launch_rho_update(const double* part_udm, const int* rays_prefix, const dou
                        SliceScalars* sc, int B, double mu_b, double tau, cudaStream_t st) {
     k_rho_update<<<B, 256, 0, st>>>(part_udm, rays_prefix, part_img, pix_prefix, sc, mu_b, tau);
 }
-void launch_dual_rescale(const SliceDesc* d, const BlockMap& pix, int np, const BlockMap& rays, int nr,
-                         const SliceScalars* sc, float4* uy, float2* uz, void* ua, int prec, cudaStream_t st) {
-    DISPATCH_S2(prec, (k_dual_rescale<S2><<<np + nr, 256, 0, st>>>(d, pix, np, rays, sc, uy, uz, (S2*)ua)));
+void launch_dual_rescale(const SliceDesc* d, int B, const SliceScalars* sc, float4* uy, float2* uz, void* ua, int prec,
+                         cudaStream_t st) {
+    // about eight blocks per SM over the batch, at least one per slice
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int G = std::max(1, std::min(1024, (8 * std::max(sms, 1) + B - 1) / B));
+    DISPATCH_S2(prec, (k_dual_rescale<S2><<<B * G, 256, 0, st>>>(d, G, sc, uy, uz, (S2*)ua)));
 }
 void launch_xi(const SliceDesc* d, const BlockMap& pix, int np, const float2* x, const float2* truth, double* partial,
                SliceScalars* sc, int B, cudaStream_t st) {

@@ -20,8 +20,8 @@ void launch_image_update(const SliceDesc* d, const BlockMap& pix, int np, const 
                          cudaStream_t st);
 void launch_rho_update(const double* part_udm, const int* rays_prefix, const double* part_img, const int* pix_prefix,
                        SliceScalars* sc, int B, double mu_b, double tau, cudaStream_t st);
-void launch_dual_rescale(const SliceDesc* d, const BlockMap& pix, int np, const BlockMap& rays, int nr,
-                         const SliceScalars* sc, float4* uy, float2* uz, void* ua, int prec, cudaStream_t st);
+void launch_dual_rescale(const SliceDesc* d, int B, const SliceScalars* sc, float4* uy, float2* uz, void* ua, int prec,
+                         cudaStream_t st);
 void launch_xi(const SliceDesc* d, const BlockMap& pix, int np, const float2* x, const float2* truth, double* partial,
                SliceScalars* sc, int B, cudaStream_t st);
 // Eq. 4's objective: TV partials per pixel block, then ray + pixel partials summed per slice into sc

@@ -843,7 +843,7 @@ static void enq_lmcg_iteration(dect_admm* A, cudaStream_t st) {
     launch_rho_update(A->part_udm, A->rays.d, A->part_img, A->pix.d, A->sc, B, A->P.rho_mu, A->P.rho_tau, st);
     pe(A, DECT_PHASE_REDUCE, 1, st);
     pb(A, st);
-    launch_dual_rescale(A->ds, A->pix.map(B), A->pix.total, A->rays.map(B), A->rays.total, A->sc, A->uy, A->uz, A->ua,
+    launch_dual_rescale(A->ds, B, A->sc, A->uy, A->uz, A->ua,
                         A->prec, st);
     pe(A, DECT_PHASE_UPDATE, 1, st);
 }
@@ -965,7 +965,7 @@ static void enq_iteration(dect_admm* A, cudaStream_t st) {
     launch_rho_update(A->part_udm, A->rays.d, A->part_img, A->pix.d, A->sc, B, A->P.rho_mu, A->P.rho_tau, st);
     pe(A, DECT_PHASE_REDUCE, 1, st);
     pb(A, st);
-    launch_dual_rescale(A->ds, A->pix.map(B), A->pix.total, A->rays.map(B), A->rays.total, A->sc, A->uy, A->uz, A->ua,
+    launch_dual_rescale(A->ds, B, A->sc, A->uy, A->uz, A->ua,
                         A->prec, st);
     pe(A, DECT_PHASE_UPDATE, 1, st);
 }

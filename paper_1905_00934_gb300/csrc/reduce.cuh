@@ -49,6 +49,8 @@ __device__ void slice_sum(const double* __restrict__ part, const int* __restrict
     const int b0 = prefix[s], b1 = prefix[s + 1];
     double acc[N];
     for (int q = 0; q < N; ++q) acc[q] = 0.0;
+    // unrolled so that several slots' loads are in flight; each thread still adds its slots in order
+#pragma unroll 8
     for (int b = b0 + threadIdx.x; b < b1; b += blockDim.x)
         for (int q = 0; q < N; ++q) acc[q] += part[N * (size_t)b + q];
     for (int q = 0; q < N; ++q) red[q][threadIdx.x] = acc[q];
