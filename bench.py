@@ -282,7 +282,7 @@ def _plain_ms(make_single, n, stream, flush, iters=ITERS):
 
 
 # a plain single-slice solver: eager launches, backprojector view groups from the occupancy rule
-PLAIN = dict(use_graph=0, bp_view_groups=-1, bp_tile=32, bp_cluster=-1)
+PLAIN = dict(use_graph=0, bp_view_groups=-1, bp_tile=32, bp_cluster=-1, proj_views=2)
 
 
 def _phase_ms(sol, iters=5):
@@ -327,7 +327,7 @@ def run_dect(args):
     storage = {"f32": 0, "f16": 1, "bf16": 2}[args.storage]
     # the backprojector's launch shape: autotuned at creation unless fixed on the command line
     shape = dict(bp_view_groups=args.bp_view_groups, bp_tile=args.bp_tile, bp_cluster=args.bp_cluster,
-                 bp_slices=args.bp_slices, bp_reduce=args.bp_reduce)
+                 bp_slices=args.bp_slices, bp_reduce=args.bp_reduce, proj_views=args.proj_views)
     sol = Solver(geo, spec, kappa=BAGGAGE_KAPPA, storage=storage, **shape)
     f32 = lambda a: torch.tensor(np.ascontiguousarray(a), dtype=torch.float32, device=dev)
     dev_data = [[f32(c[k]) for k in ("m_h", "m_l", "w_h", "w_l")] for c in cases]
@@ -389,7 +389,8 @@ def run_dect(args):
     cfg = {"workload": "fan 512x512, 720 views x 1024 bins, 40 objects, I0 2e5, UDM1-PCG1 x 100 + init",
            "iterations_fixed": ITERS, "batch_per_gpu": B, "l2": "flushed between steps (512 MB write)",
            "storage": args.storage, "bp_view_groups": st0["bp_view_groups"], "bp_tile": st0["bp_tile"],
-           "bp_cluster": st0["bp_cluster"], "bp_slices": st0["bp_slices"], "bp_reduce": st0["bp_reduce"]}
+           "bp_cluster": st0["bp_cluster"], "bp_slices": st0["bp_slices"], "bp_reduce": st0["bp_reduce"],
+           "proj_views": st0["proj_views"]}
     phases = _phase_ms(sol, 10)
     for p_, ms in phases.items():
         cfg[f"{args.storage}_ms_{p_}"] = round(ms, 4)
@@ -854,6 +855,7 @@ def main():
     ap.add_argument("--bp-tile", type=int, default=0, help="backprojector tile side, 32 or 64 (0: autotuned)")
     ap.add_argument("--bp-cluster", type=int, default=0, help="1 cluster form, -1 plain form, 0 autotuned")
     ap.add_argument("--bp-slices", type=int, default=0, help="slices per backprojector CTA, 1 or 2 (0: autotuned)")
+    ap.add_argument("--proj-views", type=int, default=0, help="views per projector CTA, 2, 4 or 8 (0: autotuned)")
     ap.add_argument("--bp-reduce", type=int, default=0,
                     help="-1: the finalize pass sums the view groups' partial images; 0/1: the last CTA of a tile does")
     ap.add_argument("--profile-run", type=int, default=0, metavar="ITERS",

@@ -326,6 +326,8 @@ typedef struct {
                                     the other partials' L2 lines, so they are not written back to DRAM; the
                                     finalize pass reads one image. 0 (default) or 1 on, -1 off (the finalize
                                     pass reads the C partials). Same bits either way. */
+    int32_t proj_views;          /* views per forward-projector CTA (tiles of views x 32 bins): 2, 4 or 8, or 0
+                                    (default) timed at creation. Same bits either way. */
 } dect_params;
 
 /* Fills *p with the paper's values and the defaults above. */
@@ -388,6 +390,7 @@ typedef struct {
     int32_t bp_cluster;          /* 1 if the backprojector's view groups reduce on chip (see bp_cluster) */
     int32_t bp_slices;           /* slices per backprojector CTA in use (see bp_slices; 0 for float64) */
     int32_t bp_reduce;           /* 1 if the backprojector's view groups are summed by its last CTA per tile */
+    int32_t proj_views;          /* views per forward-projector CTA in use (0 for float64 storage) */
 } dect_stats;
 dect_status dect_admm_stats(dect_admm* a, int32_t slice, dect_stats* out, void* stream);
 

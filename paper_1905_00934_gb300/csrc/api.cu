@@ -521,6 +521,7 @@ extern "C" void dect_params_default(dect_params* p) {
     p->bp_cluster = 0;
     p->bp_slices = 0;
     p->bp_reduce = 0;
+    p->proj_views = 0;
 }
 
 struct MapBuf {
@@ -542,6 +543,8 @@ struct dect_admm {
     // row-block prefix of the <r, s> partials the float32 preconditioner wrote
     const int* rs_prefix() const { return P.precondition ? prows.d : rows.d; }
     int n_groups = 0;                // projector groups: consecutive slices of one geometry (proj_group_size())
+    std::vector<int2> group_shape;   // {views, bins} per projector group
+    int proj_views = 2;              // views per projector CTA (2, 4 or 8; does not change results)
     int4* d_groups = nullptr;        // {slice, further slices or -1} per group
     int sweep_C = 1;                 // CTA groups (partial images) per backprojector tile
     int sweep_tile = kSweepTileDefault;  // backprojector tile side (32 or 64; does not change results)
@@ -667,7 +670,8 @@ static void enq_project(dect_admm* A, const float2* img, void* out, cudaStream_t
     launch_textures(A->ds, A->tx.map(B), A->tx.total, A->ty.map(B), A->ty.total, img, A->txb, A->tyb, A->prec, st);
     pe(A, DECT_PHASE_TEXTURE, 2, st);
     pb(A, st);
-    launch_project(A->ds, A->ptile.map(A->n_groups), A->ptile.total, A->d_groups, A->txb, A->tyb, out, A->prec, st);
+    launch_project(A->ds, A->ptile.map(A->n_groups), A->ptile.total, A->d_groups, A->txb, A->tyb, out, A->prec,
+                   A->proj_views, st);
     pe(A, DECT_PHASE_PROJECT, 1, st);
     if (A->counting) A->cR += 2;
 }
@@ -778,7 +782,8 @@ static void enq_lm_step(dect_admm* A, int b, cudaStream_t st) {
         launch_textures1(A->ds, A->tx.map(B), A->tx.total, A->ty.map(B), A->ty.total, A->lm_p, A->tx1, A->ty1, st);
         pe(A, DECT_PHASE_TEXTURE, 2, st);
         pb(A, st);
-        launch_project1(A->ds, A->ptile.map(A->n_groups), A->ptile.total, A->d_groups, A->tx1, A->ty1, A->lm_q, st);
+        launch_project1(A->ds, A->ptile.map(A->n_groups), A->ptile.total, A->d_groups, A->tx1, A->ty1, A->lm_q,
+                        A->proj_views, st);
         pe(A, DECT_PHASE_PROJECT, 1, st);
         pb(A, st);
         launch_bp_sweep1(A->ds, A->sweep.map(B), A->sweep.total, A->sweep_C, A->sweep_tile, A->sweep_cluster, A->lm_q,
@@ -1148,6 +1153,56 @@ static void sweep_prefix(const dect_admm* A, int C, int tile, int sg, std::vecto
         for (int b = 0; b < A->B; ++b) h.push_back(h.back() + sweep_tiles(A->hs[b].g.nx, A->hs[b].g.ny, tile) * C);
 }
 
+// the projector's tile prefix over the geometry groups for `views` views per CTA
+static void ptile_prefix(const dect_admm* A, int views, std::vector<int>& h) {
+    h.assign(1, 0);
+    for (const int2& g : A->group_shape) h.push_back(h.back() + proj_tiles(g.x, g.y, views));
+}
+
+// Times the forward projector on this batch for 2, 4 and 8 views per CTA (on the current textures; the
+// work does not depend on the values) and keeps the fastest (fewer views unless more are 1% faster).
+// Every choice gives the same bits. The tile map is rewritten for the choice.
+static cudaError_t autotune_projector(dect_admm* A) {
+    cudaStream_t st = A->cap;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    int best = A->proj_views;
+    float best_ms = 0.f;
+    bool first = true;
+    std::vector<int> h;
+    for (int views : {2, 4, 8}) {
+        if (e != cudaSuccess) break;
+        ptile_prefix(A, views, h);
+        e = cudaMemcpy(A->ptile.d, h.data(), sizeof(int) * h.size(), cudaMemcpyHostToDevice);
+        const BlockMap m{A->ptile.d, A->n_groups};
+        auto run = [&]() { launch_project(A->ds, m, h.back(), A->d_groups, A->txb, A->tyb, A->q, A->prec, views, st); };
+        run();  // warm-up
+        e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaEventRecord(e0, st);
+        for (int r = 0; r < 3 && e == cudaSuccess; ++r) {
+            run();
+            e = cudaGetLastError();
+        }
+        if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        float ms = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (e == cudaSuccess && (first || ms < 0.99f * best_ms)) {
+            best = views;
+            best_ms = ms;
+            first = false;
+        }
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (e != cudaSuccess) return e;
+    A->proj_views = best;
+    ptile_prefix(A, best, A->ptile.h);
+    A->ptile.total = A->ptile.h.back();
+    return cudaMemcpy(A->ptile.d, A->ptile.h.data(), sizeof(int) * A->ptile.h.size(), cudaMemcpyHostToDevice);
+}
+
 // Times the backprojector sweep on this batch (on a zero sinogram; the work does not depend on the
 // values) and keeps the fastest shape (fewer view groups unless more are 1% faster), in three stages:
 // slices per CTA x view groups C at the default tile side, then the other tile sides at the best of
@@ -1348,6 +1403,8 @@ extern "C" dect_status dect_admm_create(dect_geom* const* geoms, int32_t B, cons
         DECT_FAIL(DECT_EINVAL, "dect_admm_create: bp_slices must be 0 (autotuned), 1 or 2");
     if (P->bp_reduce < -1 || P->bp_reduce > 1)
         DECT_FAIL(DECT_EINVAL, "dect_admm_create: bp_reduce must be -1 (off), 0 (default: on) or 1 (on)");
+    if (P->proj_views != 0 && P->proj_views != 2 && P->proj_views != 4 && P->proj_views != 8)
+        DECT_FAIL(DECT_EINVAL, "dect_admm_create: proj_views must be 0 (autotuned), 2, 4 or 8");
     if (P->init != DECT_INIT_PCG && P->init != DECT_INIT_CDM_FBP)
         DECT_FAIL(DECT_EINVAL, "dect_admm_create: init must be DECT_INIT_PCG or DECT_INIT_CDM_FBP");
     if (P->init == DECT_INIT_CDM_FBP)
@@ -1510,7 +1567,9 @@ extern "C" dect_status dect_admm_create(dect_geom* const* geoms, int32_t B, cons
     }
     A->n_groups = (int)groups.size();
     for (const int4& gr : groups)
-        A->ptile.h.push_back(A->ptile.h.back() + proj_tiles(geoms[gr.x]->desc.n_views, geoms[gr.x]->desc.n_bins));
+        A->group_shape.push_back(make_int2(geoms[gr.x]->desc.n_views, geoms[gr.x]->desc.n_bins));
+    A->proj_views = P->proj_views ? P->proj_views : proj_default_views();
+    ptile_prefix(A, A->proj_views, A->ptile.h);
 
 #define ALLOC(ptr, n)                                                      \
     do {                                                                   \
@@ -1612,6 +1671,14 @@ extern "C" dect_status dect_admm_create(dect_geom* const* geoms, int32_t B, cons
         dect::set_error(std::string("dect_admm_create (backprojector autotuning): ") + cudaGetErrorString(e));
         free_admm(A);
         return e == cudaErrorMemoryAllocation ? DECT_ENOMEM : DECT_ECUDA;
+    }
+    if (A->prec != PREC_F64 && P->proj_views == 0) {
+        e = autotune_projector(A);
+        if (e != cudaSuccess) {
+            dect::set_error(std::string("dect_admm_create (projector autotuning): ") + cudaGetErrorString(e));
+            free_admm(A);
+            return DECT_ECUDA;
+        }
     }
     A->sweep_groups_in_use = A->sweep_C * sweep_groups_per_cta();
     if (P->scheme == DECT_SCHEME_LM_CG) {
@@ -2071,5 +2138,6 @@ extern "C" dect_status dect_admm_stats(dect_admm* A, int32_t b, dect_stats* out,
     out->bp_cluster = A->sweep_cluster ? 1 : 0;
     out->bp_slices = A->prec == PREC_F64 ? 0 : A->sweep_sg;
     out->bp_reduce = A->bp_parts() == 1 && !A->sweep_cluster && A->sweep_C > 1 ? 1 : 0;
+    out->proj_views = A->prec == PREC_F64 ? 0 : A->proj_views;
     return DECT_OK;
 }

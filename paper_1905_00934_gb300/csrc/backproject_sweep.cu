@@ -357,26 +357,35 @@ __global__ void __launch_bounds__(SweepShape<TILE>::kThreads) k_bp_sweep(
 }
 
 // (planar != nullptr: single slice, written as [nch][ny][nx] instead of interleaved into `out`)
+// A block finishes the 256 pixels of its map block with fin_threads(MODE) threads, each taking pixels
+// that many apart: four pixels per thread for the light epilogues (their stencil loads in flight
+// together), one for r0's (measured faster with its larger register footprint).
+__host__ __device__ constexpr int fin_threads(int mode) { return (mode == BP_R0 || mode == BP_R0_NOGRAD) ? 256 : 64; }
 template <int MODE>
-__global__ void __launch_bounds__(256) k_bp_finalize(const SliceDesc* __restrict__ dsl, BlockMap pix, int C,
-                                                     const float2* __restrict__ partial, int64_t stride,
-                                                     float2* __restrict__ out, BpEpilogue ep,
-                                                     float* __restrict__ planar, int nch) {
+__global__ void __launch_bounds__(fin_threads(MODE)) k_bp_finalize(const SliceDesc* __restrict__ dsl, BlockMap pix,
+                                                                   int C, const float2* __restrict__ partial,
+                                                                   int64_t stride, float2* __restrict__ out,
+                                                                   BpEpilogue ep, float* __restrict__ planar, int nch) {
+    constexpr int kFinThreads = fin_threads(MODE);
     int local;
     const int s = slice_of(pix, blockIdx.x, local);
     const SliceDesc& d = dsl[s];
-    const int64_t k = (int64_t)local * 256 + threadIdx.x;
+    const int64_t np = (int64_t)d.g.nx * d.g.ny;
     float dot_c = 0.f, dot_p = 0.f;
-    if (k < (int64_t)d.g.nx * d.g.ny) {
-        const int j = (int)(k / d.g.nx), i = (int)(k % d.g.nx);
-        const int64_t e = d.img_off + k;
-        float2 acc = make_float2(0.f, 0.f);
-        for (int c = 0; c < C; ++c) {
-            const float2 v = __ldg(partial + c * stride + e);
-            acc.x += v.x;
-            acc.y += v.y;
+#pragma unroll
+    for (int t = 0; t < 256 / kFinThreads; ++t) {
+        const int64_t k = (int64_t)local * 256 + t * kFinThreads + threadIdx.x;
+        if (k < np) {
+            const int j = (int)(k / d.g.nx), i = (int)(k % d.g.nx);
+            const int64_t e = d.img_off + k;
+            float2 acc = make_float2(0.f, 0.f);
+            for (int c = 0; c < C; ++c) {
+                const float2 v = __ldg(partial + c * stride + e);
+                acc.x += v.x;
+                acc.y += v.y;
+            }
+            bp_pixel_epilogue<MODE>(d, i, j, acc, ep, out, planar, nch, dot_c, dot_p);
         }
-        bp_pixel_epilogue<MODE>(d, i, j, acc, ep, out, planar, nch, dot_c, dot_p);
     }
     if (MODE == BP_AP || MODE == BP_AP_NOGRAD) bp_block_dots(dot_c, dot_p, ep.partial);
 }
@@ -531,7 +540,7 @@ void launch_bp_sweep1(const SliceDesc* dsl, const BlockMap& smap, int nsweep, in
 template <int MODE>
 static void finalize_t(const SliceDesc* dsl, const BlockMap& pix, int npix, int C, const float2* partial,
                        int64_t stride, float2* out, const BpEpilogue& ep, cudaStream_t st) {
-    k_bp_finalize<MODE><<<npix, 256, 0, st>>>(dsl, pix, C, partial, stride, out, ep, nullptr, 0);
+    k_bp_finalize<MODE><<<npix, fin_threads(MODE), 0, st>>>(dsl, pix, C, partial, stride, out, ep, nullptr, 0);
 }
 
 void launch_bp_finalize(int mode, const SliceDesc* dsl, const BlockMap& pix, int npix, int C, const float2* partial,
@@ -553,7 +562,7 @@ void backproject_single(const SliceDesc& sd, const SliceDesc* d_dev, const int* 
     const BlockMap smap{maps, 1}, pmap{maps + 2, 1};
     launch_bp_sweep(d_dev, smap, sweep_tiles(sd.g.nx, sd.g.ny, tile) * C, C, tile, false, 1, nullptr, packed, partial,
                     np, PREC_F32, nullptr, st);
-    k_bp_finalize<BP_PLAIN><<<(unsigned)((np + 255) / 256), 256, 0, st>>>(d_dev, pmap, C, partial, np, nullptr,
+    k_bp_finalize<BP_PLAIN><<<(unsigned)((np + 255) / 256), fin_threads(BP_PLAIN), 0, st>>>(d_dev, pmap, C, partial, np, nullptr,
                                                                          BpEpilogue{}, out, nch);
 }
 

@@ -145,14 +145,16 @@ void launch_textures(const SliceDesc* dsl, const BlockMap& mx, int nbx, const Bl
                      const float2* img, void* tx, void* ty, int prec, cudaStream_t st);
 void launch_textures1(const SliceDesc* dsl, const BlockMap& mx, int nbx, const BlockMap& my, int nby,
                       const float* img, float2* tx, float2* ty, cudaStream_t st);
-// projector CTAs (tiles of views x bins) of a slice; the projector's block maps count these per
-// geometry group: up to proj_group_size() slices of one geometry, given as int4 {slice, slices or -1}
-int proj_tiles(int nv, int nb);
+// projector CTAs (tiles of `views` views x 32 bins; views = 2, 4 or 8) of a slice; the projector's block
+// maps count these per geometry group: up to proj_group_size() slices of one geometry, given as int4
+// {slice, slices or -1}. The view count does not change results.
+int proj_tiles(int nv, int nb, int views);
+int proj_default_views();
 int proj_group_size();
 void launch_project1(const SliceDesc* dsl, const BlockMap& map, int nblk, const int4* groups, const float2* tx,
-                     const float2* ty, float* out, cudaStream_t st);
+                     const float2* ty, float* out, int views, cudaStream_t st);
 void launch_project(const SliceDesc* dsl, const BlockMap& map, int nblk, const int4* groups, const void* tx,
-                    const void* ty, void* out, int prec, cudaStream_t st);
+                    const void* ty, void* out, int prec, int views, cudaStream_t st);
 // backproject_sweep.cu: the solver's backprojector (two kernels: sweep into C partial images, then
 // the fixed-order sum of the partials with the epilogue; partial dots over the `pix` blocks)
 int sweep_ctas_for_groups(int view_groups);

@@ -303,20 +303,23 @@ __device__ __forceinline__ float2 ray_sum_sync(const int4 P, bool valid, const G
     return make_float2(ac, ap);
 }
 
-// A CTA takes a tile of kProjViews consecutive views x 32 consecutive bins, one warp per view: the
-// rays of neighbouring views through the same bins cross nearly the same texels, so the tile's warps
-// share them in L1.
+// A CTA takes a tile of V consecutive views x 32 consecutive bins, one warp per view: the rays of
+// neighbouring views through the same bins cross nearly the same texels, so the tile's warps share them
+// in L1. V = 2, 4 or 8 is timed by the solver at creation (a ray's sum does not depend on its tile, so
+// every V gives the same bits); kProjViews is the default and the single-slice projector's.
 constexpr int kProjViews = DECT_PROJ_VIEWS;
 constexpr int kProjGroup = DECT_PROJ_GROUP;  // slices of one geometry projected by one CTA (<= 4)
 
 __host__ __device__ __forceinline__ int proj_bin_tiles(int nb) { return (nb + 31) / 32; }
 
-int proj_tiles(int nv, int nb) { return ((nv + kProjViews - 1) / kProjViews) * proj_bin_tiles(nb); }
+int proj_tiles(int nv, int nb, int views) { return ((nv + views - 1) / views) * proj_bin_tiles(nb); }
+int proj_default_views() { return kProjViews; }
 
-// (view, bin) of this thread in tile `local` of a slice with nv views and nb bins
+// (view, bin) of this thread in tile `local` of a slice with nv views and nb bins, V views per tile
+template <int V>
 __device__ __forceinline__ bool proj_ray(int local, int nv, int nb, int& v, int& k) {
     const int nbt = proj_bin_tiles(nb);
-    v = (local / nbt) * kProjViews + (int)(threadIdx.x >> 5);
+    v = (local / nbt) * V + (int)(threadIdx.x >> 5);
     k = (local % nbt) * 32 + (int)(threadIdx.x & 31);
     return v < nv && k < nb;
 }
@@ -388,11 +391,12 @@ __device__ __forceinline__ void ray_sum_group(const int4 P, bool valid, const Ge
 
 // One CTA per (geometry group, tile): group gi holds up to kProjGroup slices of one geometry (their
 // indices in groups[gi], -1 past the group's size); the block map counts tiles per group.
-template <class S2, class TX>
-__global__ void __launch_bounds__(32 * kProjViews, DECT_PROJ_MINB) k_project(const SliceDesc* __restrict__ dsl, BlockMap map,
-                                                             const int4* __restrict__ groups,
-                                                             const TX* __restrict__ tx, const TX* __restrict__ ty,
-                                                             S2* __restrict__ out) {
+// (the register budget allows DECT_PROJ_MINB 64-thread CTAs per SM, the same warps for every V)
+template <class S2, class TX, int V>
+__global__ void __launch_bounds__(32 * V, DECT_PROJ_MINB * 2 / V) k_project(const SliceDesc* __restrict__ dsl,
+                                                                          BlockMap map, const int4* __restrict__ groups,
+                                                                          const TX* __restrict__ tx,
+                                                                          const TX* __restrict__ ty, S2* __restrict__ out) {
     int local;
     const int gi = slice_of(map, blockIdx.x, local);
     const int4 gs = __ldg(groups + gi);
@@ -403,7 +407,7 @@ __global__ void __launch_bounds__(32 * kProjViews, DECT_PROJ_MINB) k_project(con
     const int count = 1 + (gs.y >= 0) + (gs.z >= 0) + (gs.w >= 0);
     const SliceDesc& d = dsl[sl[0]];
     int v, k;
-    const bool valid = proj_ray(local, d.g.nv, d.g.nb, v, k);
+    const bool valid = proj_ray<V>(local, d.g.nv, d.g.nb, v, k);
     const int64_t r = (int64_t)v * d.g.nb + k;
     const int4 P = valid ? __ldg(d.g.rays + r) : make_int4(0, 0, 0, 0);
     const TX* txs[kProjGroup];
@@ -428,7 +432,7 @@ __global__ void __launch_bounds__(32 * kProjViews, DECT_PROJ_MINB) k_project_pla
                                                                     float* __restrict__ out, int nch) {
     const int64_t n = (int64_t)d.g.nv * d.g.nb;
     int v, k;
-    const bool valid = proj_ray(blockIdx.x, d.g.nv, d.g.nb, v, k);
+    const bool valid = proj_ray<kProjViews>(blockIdx.x, d.g.nv, d.g.nb, v, k);
     const int64_t r = (int64_t)v * d.g.nb + k;
     const int4 P = valid ? __ldg(d.g.rays + r) : make_int4(0, 0, 0, 0);
     const float2 acc = ray_sum_sync(P, valid, d.g, tx, ty);
@@ -438,24 +442,31 @@ __global__ void __launch_bounds__(32 * kProjViews, DECT_PROJ_MINB) k_project_pla
     if (nch > 1) out[n + r] = w * acc.y;
 }
 
-void launch_project(const SliceDesc* dsl, const BlockMap& map, int nblk, const int4* groups, const void* tx,
-                    const void* ty, void* out, int prec, cudaStream_t st) {
-    constexpr int T = 32 * kProjViews;
-    if (prec == PREC_F16)
-        k_project<__half2, TexH><<<nblk, T, 0, st>>>(dsl, map, groups, (const TexH*)tx, (const TexH*)ty,
-                                                      (__half2*)out);
-    else if (prec == PREC_BF16)
-        k_project<__nv_bfloat162, TexB><<<nblk, T, 0, st>>>(dsl, map, groups, (const TexB*)tx, (const TexB*)ty,
-                                                             (__nv_bfloat162*)out);
+template <class S2, class TX>
+static void project_t(const SliceDesc* dsl, const BlockMap& map, int nblk, const int4* groups, const TX* tx,
+                      const TX* ty, S2* out, int views, cudaStream_t st) {
+    if (views == 8)
+        k_project<S2, TX, 8><<<nblk, 256, 0, st>>>(dsl, map, groups, tx, ty, out);
+    else if (views == 4)
+        k_project<S2, TX, 4><<<nblk, 128, 0, st>>>(dsl, map, groups, tx, ty, out);
     else
-        k_project<float2, float4><<<nblk, T, 0, st>>>(dsl, map, groups, (const float4*)tx, (const float4*)ty,
-                                                       (float2*)out);
+        k_project<S2, TX, 2><<<nblk, 64, 0, st>>>(dsl, map, groups, tx, ty, out);
+}
+
+void launch_project(const SliceDesc* dsl, const BlockMap& map, int nblk, const int4* groups, const void* tx,
+                    const void* ty, void* out, int prec, int views, cudaStream_t st) {
+    if (prec == PREC_F16)
+        project_t(dsl, map, nblk, groups, (const TexH*)tx, (const TexH*)ty, (__half2*)out, views, st);
+    else if (prec == PREC_BF16)
+        project_t(dsl, map, nblk, groups, (const TexB*)tx, (const TexB*)ty, (__nv_bfloat162*)out, views, st);
+    else
+        project_t(dsl, map, nblk, groups, (const float4*)tx, (const float4*)ty, (float2*)out, views, st);
 }
 
 // single channel: float out, float2 texels
 void launch_project1(const SliceDesc* dsl, const BlockMap& map, int nblk, const int4* groups, const float2* tx,
-                     const float2* ty, float* out, cudaStream_t st) {
-    k_project<float, float2><<<nblk, 32 * kProjViews, 0, st>>>(dsl, map, groups, tx, ty, out);
+                     const float2* ty, float* out, int views, cudaStream_t st) {
+    project_t(dsl, map, nblk, groups, tx, ty, out, views, st);
 }
 
 int proj_group_size() { return kProjGroup; }
@@ -505,7 +516,7 @@ void project_single(const SliceDesc& sd_in, const float* img, int nch, float2* s
     k_pack_planar<<<(unsigned)((np + 255) / 256), 256, 0, st>>>(img, nch, np, scratch);
     k_texture_x_single<<<tx_blocks(sd.g.nx, sd.g.ny), 256, 0, st>>>(sd, scratch, tx);
     k_texture_y_single<<<ty_blocks(sd.g.nx, sd.g.ny), 256, 0, st>>>(sd, scratch, ty);
-    k_project_planar<<<proj_tiles(sd.g.nv, sd.g.nb), 32 * kProjViews, 0, st>>>(sd, tx, ty, out, nch);
+    k_project_planar<<<proj_tiles(sd.g.nv, sd.g.nb, kProjViews), 32 * kProjViews, 0, st>>>(sd, tx, ty, out, nch);
 }
 
 void launch_pack_planar(const float* in, int nch, int64_t n, float2* out, cudaStream_t st) {

@@ -51,7 +51,8 @@ class Params(ctypes.Structure):
                 ("precondition", ctypes.c_int32), ("use_graph", ctypes.c_int32), ("bp_view_groups", ctypes.c_int32),
                 ("storage", ctypes.c_int32), ("scheme", ctypes.c_int32), ("init", ctypes.c_int32),
                 ("udm_f64", ctypes.c_int32), ("objective_every", ctypes.c_int32), ("bp_tile", ctypes.c_int32),
-                ("bp_cluster", ctypes.c_int32), ("bp_slices", ctypes.c_int32), ("bp_reduce", ctypes.c_int32)]
+                ("bp_cluster", ctypes.c_int32), ("bp_slices", ctypes.c_int32), ("bp_reduce", ctypes.c_int32),
+                ("proj_views", ctypes.c_int32)]
 
 
 class Stats(ctypes.Structure):
@@ -60,7 +61,8 @@ class Stats(ctypes.Structure):
                 ("count_RT", ctypes.c_int64), ("count_f", ctypes.c_int64), ("count_launches", ctypes.c_int64),
                 ("bp_view_groups", ctypes.c_int32), ("objective", ctypes.c_double),
                 ("objective_iteration", ctypes.c_int32), ("bp_tile", ctypes.c_int32), ("bp_cluster", ctypes.c_int32),
-                ("bp_slices", ctypes.c_int32), ("bp_reduce", ctypes.c_int32)]
+                ("bp_slices", ctypes.c_int32), ("bp_reduce", ctypes.c_int32),
+                ("proj_views", ctypes.c_int32)]
 
 
 # every symbol declared in include/dect.h, with its ctypes signature
@@ -317,7 +319,7 @@ def admm_stats(h, slice_index, stream=None) -> dict:
             "xi_db": list(s.xi_db), "count_R": s.count_R, "count_RT": s.count_RT, "count_f": s.count_f,
             "count_launches": s.count_launches, "bp_view_groups": s.bp_view_groups, "objective": s.objective,
             "objective_iteration": s.objective_iteration, "bp_tile": s.bp_tile, "bp_cluster": s.bp_cluster,
-            "bp_slices": s.bp_slices, "bp_reduce": s.bp_reduce}
+            "bp_slices": s.bp_slices, "bp_reduce": s.bp_reduce, "proj_views": s.proj_views}
 
 
 def admm_save(h, stream=None) -> np.ndarray:

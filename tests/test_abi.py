@@ -70,4 +70,4 @@ def test_params_default_are_the_papers():
     assert (p.lambda_c, p.lambda_p, p.rho0_c, p.rho0_p) == (1e-5, 1e-5, 1e-3, 1e-3)
     assert (p.m_udm, p.n_pcg) == (1, 1)
     assert (p.storage, p.udm_f64) == (dect.STORE_F32, 0)
-    assert (p.objective_every, p.bp_tile, p.bp_cluster, p.bp_slices, p.bp_reduce) == (0, 0, 0, 0, 0)
+    assert (p.objective_every, p.bp_tile, p.bp_cluster, p.bp_slices, p.bp_reduce, p.proj_views) == (0,) * 6

@@ -124,6 +124,27 @@ def test_backprojector_tile_side_does_not_change_results(cuda_dev):
         assert np.array_equal(outs[0][b], outs[1][b])
 
 
+def test_projector_views_per_cta_do_not_change_results(cuda_dev):
+    # a ray's sum does not depend on the tile (views x 32 bins) its CTA takes, so the projector's timed
+    # choice of 2, 4 or 8 views per CTA is free: every fixed choice gives the same bits, and a solver
+    # given the autotuned choice reproduces it
+    from paper_1905_00934_gb300 import dect
+
+    cases = _same_geometry_cases()[:2] + _small_cases()[1:2]
+    outs = []
+    for views in (2, 4, 8):
+        sol = _solver(cases, cuda_dev, [None] * 3, bp_view_groups=4, proj_views=views)
+        assert sol.stats(0)["proj_views"] == views
+        sol.reconstruct(3)
+        outs.append([sol.get(b, dect.X).cpu().numpy() for b in range(3)])
+    tuned = _solver(cases, cuda_dev, [None] * 3, bp_view_groups=4)
+    assert tuned.stats(0)["proj_views"] in (2, 4, 8)
+    tuned.reconstruct(3)
+    for b in range(3):
+        assert np.array_equal(outs[0][b], outs[1][b]) and np.array_equal(outs[0][b], outs[2][b]), b
+        assert np.array_equal(outs[0][b], tuned.get(b, dect.X).cpu().numpy()), b
+
+
 def _same_geometry_cases():
     g = G.fan_geometry(128, 180, 256)
     cases = [make_case(g, lambda gg, r: baggage_phantom(gg, r, n_objects=10), 2e5, 80 + k, e_ref_kev=100.0)
