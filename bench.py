@@ -518,6 +518,11 @@ def run_dect(args):
                 cfg.update(uneven_leg(args.uneven_slices, stream))
             except Exception as exc:
                 cfg["uneven_error"] = f"{type(exc).__name__}: {exc}"[:90]
+        if args.stack_slices:
+            try:
+                cfg.update(stack_leg(args.stack_slices, stream))
+            except Exception as exc:
+                cfg["stack_error"] = f"{type(exc).__name__}: {exc}"[:90]
 
     # ---- the paper's comparison (Sec. 4): time to the same PE error, new splitting vs LM x CG ----
     if gold is not None and not args.no_comparison:
@@ -587,6 +592,58 @@ def size_scan(args, stream, flush):
         t_p = per_iter(singles)
         out[f"scan{n}_batched_over_plain"] = t_p / t_b
         out[f"scan{n}_batched_ms_per_iter"] = t_b
+    return out
+
+
+def stack_leg(n_slices, stream):
+    """The mixed-precision stack: n_slices fan slices of 1024^2 with 1440 views and 2048 bins in one solver
+    per storage format (one seeded slice's measurements on every slice: the kernels' work does not
+    depend on the values), device ms per ADMM iteration after the initial image, against the plain
+    single-slice FP32 solver on one slice, times n_slices; and the 16-bit formats' xi_p after the
+    initial image and 10 iterations next to FP32's on that slice."""
+    import torch
+
+    from paper_1905_00934_gb300 import Geometry, Solver, Spectra, dect
+    from synth.workloads import BAGGAGE_KAPPA, MIXED_SEED_BASE, baggage_fan_case
+
+    dev = torch.device("cuda", torch.cuda.current_device())
+    c = baggage_fan_case(slice_index=MIXED_SEED_BASE, n=1024, n_views=1440, n_bins=2048)
+    spec = Spectra.from_tables(c["spectra"])
+    geo = Geometry(c["geom"])
+    data = [torch.tensor(np.ascontiguousarray(c[k]), dtype=torch.float32, device=dev)
+            for k in ("m_h", "m_l", "w_h", "w_l")]
+    truth = torch.tensor(np.stack([c["truth_c"], c["truth_p"]]), dtype=torch.float32, device=dev)
+    del c
+
+    def per_iter(sol, iters):
+        sol.reconstruct(0)
+        sol.step(1)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        sol.step(iters)
+        e1.record(stream)
+        e1.synchronize()
+        return e0.elapsed_time(e1) / iters
+
+    out = {"stack_slices": n_slices, "stack_workload": "fan 1024x1024, 1440 views x 2048 bins"}
+    one = Solver([geo], spec, kappa=BAGGAGE_KAPPA, **PLAIN)
+    one.set_data(0, *data)
+    t_plain = per_iter(one, 3) * n_slices
+    del one
+    out["stack_plain_ms_per_iter"] = t_plain
+    for name, code in (("f32", dect.STORE_F32), ("f16", dect.STORE_F16), ("bf16", dect.STORE_BF16)):
+        sol = Solver([geo] * n_slices, spec, kappa=BAGGAGE_KAPPA, storage=code)
+        for b in range(n_slices):
+            sol.set_data(b, *data)
+        sol.set_truth(0, truth)
+        t = per_iter(sol, 3)
+        sol.step(10 - 4)
+        out[f"stack_{name}_ms_per_iter"] = t
+        out[f"stack_{name}_over_plain"] = t_plain / t
+        out[f"stack_{name}_xi_p_db_at_10"] = sol.stats(0)["xi_db"][1]
+        del sol
+        torch.cuda.empty_cache()
     return out
 
 
@@ -848,6 +905,8 @@ def main():
                     help="skip the time-to-target comparison with the LM x CG splitting")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the plain forms, the 16-bit arms, the slice-size scan and the uneven batch")
+    ap.add_argument("--stack-slices", type=int, default=128,
+                    help="slices of the 1024^2 mixed-precision stack leg of the bench line (0 skips it)")
     ap.add_argument("--uneven-slices", type=int, default=64,
                     help="slices of the uneven-batch leg of the bench line (0 skips it)")
     ap.add_argument("--bp-view-groups", type=int, default=0,
