@@ -325,25 +325,40 @@ __global__ void __launch_bounds__(SweepShape<TILE>::kThreads) k_bp_sweep(
         if (!last) return;
         __threadfence();
         const int iw = min(TILE, nx - ti), jh = min(TILE, ny - tj);
+        // four pixels per thread at a time, their C partials loaded view group by view group, so that
+        // several loads are in flight per thread; each pixel still adds its partials in order 0..C-1
+        constexpr int U = 4;
         for (int q = 0; q < count; ++q) {
             Acc* img = partial + dsl[sl[q]].img_off;
-            for (int px = threadIdx.x; px < TILE * TILE; px += blockDim.x) {
-                const int rr = px / TILE, cc = px % TILE;
-                if (cc < iw && rr < jh) {
-                    const size_t e = (size_t)(tj + rr) * nx + ti + cc;
-                    Acc sum{};
-#pragma unroll 4
-                    for (int k = 0; k < C; ++k) {
-                        const Acc a = __ldcg(img + k * stride + e);
+            for (int px0 = threadIdx.x; px0 < TILE * TILE; px0 += U * blockDim.x) {
+                size_t e[U];
+                bool in[U];
+                Acc sum[U];
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    const int px = px0 + u * (int)blockDim.x;
+                    const int rr = px / TILE, cc = px % TILE;
+                    in[u] = px < TILE * TILE && cc < iw && rr < jh;
+                    e[u] = in[u] ? (size_t)(tj + rr) * nx + ti + cc : 0;
+                    sum[u] = Acc{};
+                }
+#pragma unroll 2
+                for (int k = 0; k < C; ++k) {
+#pragma unroll
+                    for (int u = 0; u < U; ++u) {
+                        if (!in[u]) continue;
+                        const Acc a = __ldcg(img + k * stride + e[u]);
                         if constexpr (NCH == 2) {
-                            sum.x += a.x;
-                            sum.y += a.y;
+                            sum[u].x += a.x;
+                            sum[u].y += a.y;
                         } else {
-                            sum += a;
+                            sum[u] += a;
                         }
                     }
-                    img[e] = sum;
                 }
+#pragma unroll
+                for (int u = 0; u < U; ++u)
+                    if (in[u]) img[e[u]] = sum[u];
             }
         }
         __syncthreads();  // every partial of the tile has been read
