@@ -144,6 +144,9 @@ def joseph_weight_count(g) -> int:
 # Shared-memory wavefronts per slice of the backprojector sweep on the same workload (ncu
 # l1tex__data_pipe_lsu_wavefronts_mem_shared.sum), keyed by (tile side, slices per CTA); the count
 # follows the samples and staged rays, not the view-group count. The SM serves one wavefront per clock.
+# the workload both arms of the bench line name (the reference arm times a bounded sample of it)
+WORKLOAD = "fan 512x512, 720 views x 1024 bins, 40 objects, I0 2e5, UDM1-PCG1 x 100 + init"
+
 SWEEP_SMEM_WAVEFRONTS = {(32, 1): 9.64e7, (32, 2): 8.65e7}
 
 SWEEP_TRAFFIC = {(8, 8, 32, 0, 1, 0): 134.0e6, (8, 6, 32, 0, 2, 0): 105.2e6, (8, 8, 32, 0, 2, 0): 134.9e6,
@@ -229,7 +232,7 @@ def run_reference(args):
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * float(np.mean(times)), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": "fan beam 512x512, 720 views x 1024 bins, 40 objects, I0 2e5, UDM1-PCG1 x 100",
+        "config": {"workload": WORKLOAD,
                    "batch": 1, "step": "one ADMM iteration of the FP64 oracle (a bounded sample)"},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                          "sample": f"initial image ({t_init:.1f} s) + {args.steps} timed ADMM iterations, "
@@ -386,7 +389,7 @@ def run_dect(args):
     if rank != 0:
         return 0
 
-    cfg = {"workload": "fan 512x512, 720 views x 1024 bins, 40 objects, I0 2e5, UDM1-PCG1 x 100 + init",
+    cfg = {"workload": WORKLOAD,
            "iterations_fixed": ITERS, "batch_per_gpu": B, "l2": "flushed between steps (512 MB write)",
            "storage": args.storage, "bp_view_groups": st0["bp_view_groups"], "bp_tile": st0["bp_tile"],
            "bp_cluster": st0["bp_cluster"], "bp_slices": st0["bp_slices"], "bp_reduce": st0["bp_reduce"],
