@@ -140,15 +140,42 @@ __global__ void __launch_bounds__(SweepShape<TILE>::kThreads) k_bp_sweep(
     const S2* sn1 = sino + dsl[sl[SG - 1]].sino_off;  // the second slice's sinogram (SG = 2)
     const long long a0q = (long long)ba << 30;
 
-    // chunk cursor: view v, first bin k0 of the chunk, last candidate bin khi of the view
-    int v = empty ? g.nv : grp, k0 = 0, khi = -1;
+    // chunk cursor: view v, first bin k0 of the chunk, last bin khi of the current candidate interval,
+    // [k2, k2hi] a second interval of the view still to come. A view's candidates are the bins whose
+    // rays can reach the band, restricted to the bins of this warp's axis (the view's axis layout), so
+    // the warp fetches only rays it stages; the rays keep their bin order.
+    int v = empty ? g.nv : grp, k0 = 0, khi = -1, k2 = 1, k2hi = 0;
     auto seek = [&](int vv) {
         for (v = vv; v < g.nv; v += G) {
             const float4 V = __ldg(g.views + v);
             const CandRange cr = rect_candidates(g, V.x, V.y, xc, yc, hx, hy);
-            if (cr.lo <= cr.hi) {
-                k0 = cr.lo;
-                khi = cr.hi;
+            if (cr.lo > cr.hi) continue;
+            int a1 = 0, b1 = g.nb - 1, a2 = 1, b2 = 0;  // a mixed layout: every bin, one interval
+            if (V.w >= 0.f && fabsf(V.z) >= 1.f) {
+                const bool ax0 = V.z < 0.f;
+                const int s1 = (int)fabsf(V.z) - 1, s2 = (int)V.w;
+                if (ax0 == my_axis) {
+                    b1 = s1 - 1;
+                    a2 = s2;
+                    b2 = g.nb - 1;
+                } else {
+                    a1 = s1;
+                    b1 = s2 - 1;
+                }
+            }
+            const int l1 = max(cr.lo, a1), h1 = min(cr.hi, b1), l2 = max(cr.lo, a2), h2 = min(cr.hi, b2);
+            if (l1 <= h1) {
+                k0 = l1;
+                khi = h1;
+                k2 = l2;
+                k2hi = h2;
+                return;
+            }
+            if (l2 <= h2) {
+                k0 = l2;
+                khi = h2;
+                k2 = 1;
+                k2hi = 0;
                 return;
             }
         }
@@ -199,7 +226,16 @@ __global__ void __launch_bounds__(SweepShape<TILE>::kThreads) k_bp_sweep(
         }
         // advance the cursor and fetch the next chunk while this one is processed
         k0 += 32;
-        if (k0 > khi) seek(v + G);
+        if (k0 > khi) {
+            if (k2 <= k2hi) {
+                k0 = k2;
+                khi = k2hi;
+                k2 = 1;
+                k2hi = 0;
+            } else {
+                seek(v + G);
+            }
+        }
         fetch();
         __syncwarp();
         for (int r0 = 0; r0 < nr; r0 += kSwUnroll) {

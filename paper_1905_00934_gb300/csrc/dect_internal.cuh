@@ -40,7 +40,7 @@ struct GeomDev {
     float inv_du;           // 1 / du
     float k0, k1;           // fractional bin of detector coordinate u: k = u * inv_du + k0; k1 = sdd * inv_du
     const int4* rays;       // [nv*nb] {q0 lo, q0 hi, slope, +-w}
-    const float4* views;    // [nv] {cos, sin, 0, 0}
+    const float4* views;    // [nv] {cos, sin, axis layout: +-(s1 + 1), s2 or -1} (k_view_axes)
 };
 
 // One slice of a batched solver.

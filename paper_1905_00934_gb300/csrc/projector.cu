@@ -77,12 +77,34 @@ __global__ void k_ray_table(dect_geom_desc d, int4* __restrict__ rays, float4* _
     const float wf = (float)w;
     rays[r] = make_int4((int)(unsigned)(q0_fx & 0xffffffffll), (int)(q0_fx >> 32), slope_fx,
                         __float_as_int(axis ? -wf : wf));
-    if (k == 0) views[v] = make_float4((float)c, (float)s, 0.0f, 0.0f);
+    if (k == 0) views[v] = make_float4((float)c, (float)s, 0.0f, -1.0f);  // z, w: k_view_axes
+}
+
+// Axis layout of each view, from the table's own axis bits: bins [0, s1) take the axis of bin 0, bins
+// [s1, s2) the other, bins [s2, nb) that of bin 0 again (a flat fan's ray directions span less than a
+// quarter turn, so a view switches axis at most twice). Stored in views[v].z = +-(s1 + 1), negative when
+// bin 0 is sampled per row, and views[v].w = s2; w = -1 marks a view with more switches (consumers then
+// take every bin for both axes).
+__global__ void k_view_axes(int nv, int nb, const int4* __restrict__ rays, float4* __restrict__ views) {
+    const int v = blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= nv) return;
+    const int4* rv = rays + (size_t)v * nb;
+    const bool a0 = rv[0].w < 0;
+    int k = 1;
+    while (k < nb && (rv[k].w < 0) == a0) ++k;
+    const int s1 = k;
+    while (k < nb && (rv[k].w < 0) != a0) ++k;
+    const int s2 = k;
+    while (k < nb && (rv[k].w < 0) == a0) ++k;
+    const bool mixed = k < nb;
+    views[v].z = a0 ? -(float)(s1 + 1) : (float)(s1 + 1);
+    views[v].w = mixed ? -1.0f : (float)s2;
 }
 
 cudaError_t build_ray_table(const dect_geom_desc& d, int4* rays, float4* views, cudaStream_t st) {
     const int64_t n = (int64_t)d.n_views * d.n_bins;
     k_ray_table<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(d, rays, views);
+    k_view_axes<<<(unsigned)((d.n_views + 127) / 128), 128, 0, st>>>(d.n_views, d.n_bins, rays, views);
     return cudaGetLastError();
 }
 
