@@ -147,11 +147,9 @@ def joseph_weight_count(g) -> int:
 # the workload both arms of the bench line name (the reference arm times a bounded sample of it)
 WORKLOAD = "fan 512x512, 720 views x 1024 bins, 40 objects, I0 2e5, UDM1-PCG1 x 100 + init"
 
-SWEEP_SMEM_WAVEFRONTS = {(32, 1): 9.64e7, (32, 2): 8.65e7}
+SWEEP_SMEM_WAVEFRONTS = {(32, 2): 8.54e7}
 
-SWEEP_TRAFFIC = {(8, 8, 32, 0, 1, 0): 134.0e6, (8, 6, 32, 0, 2, 0): 105.2e6, (8, 8, 32, 0, 2, 0): 134.9e6,
-                 (8, 6, 32, 0, 2, 1): 56.9e6, (8, 8, 32, 0, 2, 1): 57.8e6, (8, 10, 32, 0, 2, 1): 59.2e6,
-                 (8, 12, 32, 0, 2, 1): 60.2e6}
+SWEEP_TRAFFIC = {(8, 6, 32, 0, 2, 1): 56.6e6, (8, 8, 32, 0, 2, 1): 57.8e6}
 
 
 # ------------------------------------------------------------------------------------------------
