@@ -9,8 +9,12 @@
 // forward column FFT, the multiplication by H and the inverse column FFT (rows
 // >= ny are known zeros on input and are not needed on output); inverse row
 // FFTs of the ny rows, cropped to nx, fused with the partial sums of <r, s>.
-// The FFTs are radix-2 decimation in time in shared memory with a float32
-// twiddle table computed once in float64 on the host.
+// The FFTs are radix 2 with a float32 twiddle table computed once in float64
+// on the host. An axis whose padded length is 64..2048 splits, by its zero
+// upper half, into two half-length FFTs held in the registers of a warp pair
+// (forward by decimation in frequency, inverse by decimation in time, so no
+// bit-reversal pass); other lengths, and the response's forward transform, use
+// decimation in time staged through shared memory.
 #include <cuda_runtime.h>
 #include <math.h>
 
