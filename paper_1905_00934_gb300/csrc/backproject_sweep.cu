@@ -4,7 +4,8 @@
 // A CTA owns a pixel tile (32 x 32 or 64 x 64, see SweepShape) and a group of views; its warps take
 // the rays sampled once per column (axis 0) or once per row (axis 1) over bands of the tile. For each
 // view a warp stages its rays that can reach the tile (32 at a time) in shared memory, in bin
-// order, and walks them. For an axis-0 ray lane c evaluates the sample at column ti + c with the
+// order, and walks them; it fetches only the bins of its own axis (each view's axis layout is
+// recorded with the geometry: a view switches axis at most twice). For an axis-0 ray lane c evaluates the sample at column ti + c with the
 // same fixed-point integers as the forward projector and adds (1 - f) w s and f w s to the two rows
 // it interpolates between; for an axis-1 ray lane r does the same for row tj + r. Each lane thus
 // only touches its own column of the warp's accumulator tile ([row][column] for axis 0,
