@@ -97,6 +97,9 @@ __global__ void __launch_bounds__(SweepShape<TILE>::kThreads) k_bp_sweep(
     extern __shared__ __align__(16) unsigned char sweep_smem[];
     Acc(*acc_all)[Sh::kWarps][Sh::kRows][32] = reinterpret_cast<Acc(*)[Sh::kWarps][Sh::kRows][32]>(sweep_smem);
     Acc(*acc)[Sh::kRows][32] = acc_all[0];
+    // SG = 2: one float4 {c, p of the first slice, c, p of the second} per accumulator cell, so a sample's
+    // update of both slices is one 16-byte read-modify-write per row (the same bytes as two 8-byte ones)
+    float4(*acc4)[Sh::kRows][32] = reinterpret_cast<float4(*)[Sh::kRows][32]>(sweep_smem);
     __shared__ int4 st_ray[Sh::kWarps][32];                 // {position lo, position hi, slope, w s_c}
     __shared__ __align__(16) float st_wp[Sh::kWarps][32];   // w s_p (SG = 1)
     __shared__ float4 st_w2[SG == 2 ? Sh::kWarps : 1][32];   // {w s_p, w s_c, w s_p of the second slice} (SG = 2)
@@ -122,9 +125,11 @@ __global__ void __launch_bounds__(SweepShape<TILE>::kThreads) k_bp_sweep(
     const int w = threadIdx.x / 32, lane = threadIdx.x % 32;
     const bool my_axis = w >= Sh::kBands;
     const int band = w % Sh::kBands;
-#pragma unroll
-    for (int q = 0; q < SG; ++q)
-        for (int r = 0; r < Sh::kRows; ++r) acc_all[q][w][r][lane] = Acc{};
+    if constexpr (SG == 2) {
+        for (int r = 0; r < Sh::kRows; ++r) acc4[w][r][lane] = make_float4(0.f, 0.f, 0.f, 0.f);
+    } else {
+        for (int r = 0; r < Sh::kRows; ++r) acc[w][r][lane] = Acc{};
+    }
     const int G = C, grp = c;
     // this warp's band: 32 sampled indices from bi (columns for axis 0, rows for axis 1) by the tile's
     // TILE across indices from ba; rays with a weight at its in-image pixels pass within one pixel of
@@ -264,22 +269,18 @@ __global__ void __launch_bounds__(SweepShape<TILE>::kThreads) k_bp_sweep(
                     const float wc1 = x.y, wp1 = x.z;
                     wp[u] = x.x;
                     if ((unsigned)(hh[u] + 1) < (unsigned)(TILE + 1)) {
-                        float2* a = &acc_all[0][w][hh[u] + 1][lane];
-                        float2* b = &acc_all[1][w][hh[u] + 1][lane];
-                        float2 x0 = a[0], x1 = a[32];
-                        float2 y0 = b[0], y1 = b[32];
+                        float4* a = &acc4[w][hh[u] + 1][lane];
+                        float4 x0 = a[0], x1 = a[32];
                         x0.x = fmaf(1.0f - ff[u], wc[u], x0.x);
                         x0.y = fmaf(1.0f - ff[u], wp[u], x0.y);
                         x1.x = fmaf(ff[u], wc[u], x1.x);
                         x1.y = fmaf(ff[u], wp[u], x1.y);
-                        y0.x = fmaf(1.0f - ff[u], wc1, y0.x);
-                        y0.y = fmaf(1.0f - ff[u], wp1, y0.y);
-                        y1.x = fmaf(ff[u], wc1, y1.x);
-                        y1.y = fmaf(ff[u], wp1, y1.y);
+                        x0.z = fmaf(1.0f - ff[u], wc1, x0.z);
+                        x0.w = fmaf(1.0f - ff[u], wp1, x0.w);
+                        x1.z = fmaf(ff[u], wc1, x1.z);
+                        x1.w = fmaf(ff[u], wp1, x1.w);
                         a[0] = x0;
                         a[32] = x1;
-                        b[0] = y0;
-                        b[32] = y1;
                     }
                 }
                 continue;
@@ -333,13 +334,20 @@ __global__ void __launch_bounds__(SweepShape<TILE>::kThreads) k_bp_sweep(
         cl.sync();  // the peers' shared memory stays valid until every rank has read it
     } else {
         for (int q = 0; q < count; ++q) {
-            Acc(*aq)[Sh::kRows][32] = acc_all[q];
             const int64_t off = c * stride + dsl[sl[q]].img_off;
             for (int px = threadIdx.x; px < TILE * TILE; px += blockDim.x) {
                 const int rr = px / TILE, cc = px % TILE;
                 const int i = ti + cc, j = tj + rr;
                 if (i < nx && j < ny) {
-                    const Acc a = aq[cc / 32][rr + 1][cc % 32], b = aq[Sh::kBands + rr / 32][cc + 1][rr % 32];
+                    Acc a, b;
+                    if constexpr (SG == 2) {
+                        const float4 a4 = acc4[cc / 32][rr + 1][cc % 32], b4 = acc4[Sh::kBands + rr / 32][cc + 1][rr % 32];
+                        a = q == 0 ? make_float2(a4.x, a4.y) : make_float2(a4.z, a4.w);
+                        b = q == 0 ? make_float2(b4.x, b4.y) : make_float2(b4.z, b4.w);
+                    } else {
+                        a = acc[cc / 32][rr + 1][cc % 32];
+                        b = acc[Sh::kBands + rr / 32][cc + 1][rr % 32];
+                    }
                     Acc sum{};
                     if constexpr (NCH == 2) {
                         sum.x += a.x + b.x;
