@@ -29,7 +29,7 @@ class _Project(torch.autograd.Function):
         xf = x.reshape(-1, g.ny, g.nx).contiguous()
         out = torch.empty((xf.shape[0], g.n_views, g.n_bins), dtype=x.dtype, device=x.device)
         for a, b in _chunks(xf.shape[0]):
-            dect.project(g.handle, xf[a:b], out[a:b])
+            dect.project(g, xf[a:b], out[a:b])
         return out.reshape(*lead, g.n_views, g.n_bins)
 
     @staticmethod
@@ -39,7 +39,7 @@ class _Project(torch.autograd.Function):
         gf = grad.reshape(-1, g.n_views, g.n_bins).contiguous()
         out = torch.empty((gf.shape[0], g.ny, g.nx), dtype=grad.dtype, device=grad.device)
         for a, b in _chunks(gf.shape[0]):
-            dect.backproject(g.handle, gf[a:b], out[a:b])
+            dect.backproject(g, gf[a:b], out[a:b])
         return out.reshape(*lead, g.ny, g.nx), None
 
 

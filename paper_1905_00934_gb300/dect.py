@@ -193,9 +193,75 @@ def _dtype(t):
     raise TypeError(f"dect supports float32 and float64 tensors, not {t.dtype}")
 
 
+# Argument checks before a pointer reaches the library: the C entry points take plain pointers and
+# trust their sizes, so a tensor of the wrong dtype, shape or device is refused here.
+def _tensor(t, name, dtype=None, shape=None, numel=None, cuda=True):
+    import torch
+
+    if not isinstance(t, torch.Tensor):
+        raise TypeError(f"{name} must be a torch.Tensor")
+    if dtype is not None and t.dtype not in (dtype if isinstance(dtype, tuple) else (dtype,)):
+        raise TypeError(f"{name} must be {dtype}, not {t.dtype}")
+    if shape is not None and tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} must have shape {tuple(shape)}, not {tuple(t.shape)}")
+    if numel is not None and t.numel() != numel:
+        raise ValueError(f"{name} must have {numel} elements, not {t.numel()}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if cuda and not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    return t
+
+
+def _cuda(**tensors):
+    """Every given tensor is a CUDA tensor, all on one device."""
+    dev = None
+    for name, t in tensors.items():
+        if t is None:
+            continue
+        if not t.is_cuda:
+            raise ValueError(f"{name} must be a CUDA tensor")
+        if dev is None:
+            dev = t.device
+        elif t.device != dev:
+            raise ValueError(f"{name} is on {t.device}, the other arrays on {dev}")
+
+
+def _geom(geom):
+    """(handle, (nx, ny, n_views, n_bins) or None): a solver.Geometry also gives its shape."""
+    h = getattr(geom, "handle", geom)
+    if all(hasattr(geom, k) for k in ("nx", "ny", "n_views", "n_bins")):
+        return h, (geom.nx, geom.ny, geom.n_views, geom.n_bins)
+    return h, None
+
+
+def _pair(x, out, name_in, name_out, shape_in, shape_out, dtypes):
+    """Checks an (input, output) pair of one dtype; shapes [nch, ...] with nch 1 or 2."""
+    import torch
+
+    _tensor(x, name_in, dtype=dtypes, cuda=False)
+    if x.dim() != 3 or x.shape[0] not in (1, 2):
+        raise ValueError(f"{name_in} must be [n_channels (1 or 2), ...], not {tuple(x.shape)}")
+    _tensor(out, name_out, dtype=x.dtype, cuda=False)
+    if out.dim() != 3 or out.shape[0] != x.shape[0]:
+        raise ValueError(f"{name_out} must be [{x.shape[0]}, ...], not {tuple(out.shape)}")
+    if shape_in is not None and tuple(x.shape[1:]) != tuple(shape_in):
+        raise ValueError(f"{name_in} must be [n_channels, {shape_in[0]}, {shape_in[1]}], not {tuple(x.shape)}")
+    if shape_out is not None and tuple(out.shape[1:]) != tuple(shape_out):
+        raise ValueError(f"{name_out} must be [n_channels, {shape_out[0]}, {shape_out[1]}], not {tuple(out.shape)}")
+    if not (x.is_cuda and out.is_cuda) or x.device != out.device:
+        raise ValueError(f"{name_in} and {name_out} must be CUDA tensors on one device")
+
+
 def project(geom, x, out, stream=None):
-    """out[c] = R x[c]; x [nch, ny, nx], out [nch, n_views, n_bins] (CUDA float32 or float64)."""
-    _check(lib().dect_project(geom, x.shape[0], _dtype(x), _ptr(x), _ptr(out), _stream(stream)))
+    """out[c] = R x[c]; x [nch, ny, nx], out [nch, n_views, n_bins] (CUDA float32 or float64, one dtype).
+    geom is a geometry handle or a solver.Geometry; with the latter the shapes are checked too."""
+    import torch
+
+    h, dims = _geom(geom)
+    _pair(x, out, "x", "out", None if dims is None else (dims[1], dims[0]),
+          None if dims is None else (dims[2], dims[3]), (torch.float32, torch.float64))
+    _check(lib().dect_project(h, x.shape[0], _dtype(x), _ptr(x), _ptr(out), _stream(stream)))
     return out
 
 
@@ -229,40 +295,86 @@ def project_noalloc(geom, x, out, stream=None):
 
 
 def backproject(geom, sino, out, stream=None):
-    """out[c] = R^T sino[c] (exact adjoint of project)."""
-    _check(lib().dect_backproject(geom, sino.shape[0], _dtype(sino), _ptr(sino), _ptr(out), _stream(stream)))
+    """out[c] = R^T sino[c] (exact adjoint of project); sino [nch, n_views, n_bins], out [nch, ny, nx]
+    (CUDA float32 or float64, one dtype)."""
+    import torch
+
+    h, dims = _geom(geom)
+    _pair(sino, out, "sino", "out", None if dims is None else (dims[2], dims[3]),
+          None if dims is None else (dims[1], dims[0]), (torch.float32, torch.float64))
+    _check(lib().dect_backproject(h, sino.shape[0], _dtype(sino), _ptr(sino), _ptr(out), _stream(stream)))
     return out
 
 
 def decompose_rays(spec, m_h, m_l, w_h, w_l, v_c, v_p, rho_c, rho_p, iters, a_c, a_p, mu, status=None, stream=None):
-    """Eq. 13 per ray; a_c, a_p, mu are updated in place."""
-    n = a_c.numel()
+    """Eq. 13 per ray; a_c, a_p, mu are updated in place (CUDA float32 arrays of one length; status uint8)."""
+    import torch
+
+    n = _tensor(a_c, "a_c", dtype=torch.float32, cuda=False).numel()
+    for name, t in (("m_h", m_h), ("m_l", m_l), ("w_h", w_h), ("w_l", w_l), ("v_c", v_c), ("v_p", v_p),
+                    ("a_p", a_p), ("mu", mu)):
+        _tensor(t, name, dtype=torch.float32, numel=n, cuda=False)
+    if status is not None:
+        _tensor(status, "status", dtype=torch.uint8, numel=n, cuda=False)
+    _cuda(m_h=m_h, m_l=m_l, w_h=w_h, w_l=w_l, v_c=v_c, v_p=v_p, a_c=a_c, a_p=a_p, mu=mu, status=status)
     _check(lib().dect_decompose_rays(spec, n, _ptr(m_h), _ptr(m_l), _ptr(w_h), _ptr(w_l), _ptr(v_c), _ptr(v_p),
                                      float(rho_c), float(rho_p), int(iters), _ptr(a_c), _ptr(a_p), _ptr(mu),
                                      _ptr(status), _stream(stream)))
 
 
 def fbp(geom, sino, out, clamp_nonneg=False, stream=None):
-    """out[c] = filtered backprojection of sino[c] (float32 [nch, V, Nb] -> [nch, ny, nx])."""
-    _check(lib().dect_fbp(geom, sino.shape[0], _ptr(sino), _ptr(out), 1 if clamp_nonneg else 0, _stream(stream)))
+    """out[c] = filtered backprojection of sino[c] (CUDA float32 [nch, V, Nb] -> [nch, ny, nx])."""
+    import torch
+
+    h, dims = _geom(geom)
+    _pair(sino, out, "sino", "out", None if dims is None else (dims[2], dims[3]),
+          None if dims is None else (dims[1], dims[0]), torch.float32)
+    _check(lib().dect_fbp(h, sino.shape[0], _ptr(sino), _ptr(out), 1 if clamp_nonneg else 0, _stream(stream)))
     return out
 
 
 def cdm_fbp(geom, spec, m_h, m_l, w_h, w_l, iters, out, work=None, stream=None):
-    """CDM-FBP: per-ray decomposition with rho = 0, a >= 0, FBP of both bases into out [2, ny, nx]."""
-    _check(lib().dect_cdm_fbp(geom, spec, _ptr(m_h), _ptr(m_l), _ptr(w_h), _ptr(w_l), int(iters), _ptr(work),
+    """CDM-FBP: per-ray decomposition with rho = 0, a >= 0, FBP of both bases into out [2, ny, nx]
+    (CUDA float32; measurements [n_views, n_bins]; work None or 4 n_views n_bins floats)."""
+    import torch
+
+    h, dims = _geom(geom)
+    n = None if dims is None else dims[2] * dims[3]
+    _tensor(m_h, "m_h", dtype=torch.float32, numel=n, cuda=False)
+    n = m_h.numel()
+    for name, t in (("m_l", m_l), ("w_h", w_h), ("w_l", w_l)):
+        _tensor(t, name, dtype=torch.float32, numel=n, cuda=False)
+    _tensor(out, "out", dtype=torch.float32, shape=None if dims is None else (2, dims[1], dims[0]), cuda=False)
+    if work is not None:
+        _tensor(work, "work", dtype=torch.float32, numel=4 * n, cuda=False)
+    _cuda(m_h=m_h, m_l=m_l, w_h=w_h, w_l=w_l, out=out, work=work)
+    _check(lib().dect_cdm_fbp(h, spec, _ptr(m_h), _ptr(m_l), _ptr(w_h), _ptr(w_l), int(iters), _ptr(work),
                               _ptr(out), _stream(stream)))
     return out
 
 
 def forward_model(spec, a_c, a_p, f_h=None, f_l=None, jac=None, stream=None):
-    """Eq. 3 per ray (and its Jacobian [n, 4] if jac is given)."""
+    """Eq. 3 per ray (and its Jacobian [n, 4] if jac is given); CUDA arrays of one dtype (float32/float64)."""
+    import torch
+
+    n = _tensor(a_c, "a_c", dtype=(torch.float32, torch.float64), cuda=False).numel()
+    _tensor(a_p, "a_p", dtype=a_c.dtype, numel=n, cuda=False)
+    for name, t, k in (("f_h", f_h, n), ("f_l", f_l, n), ("jac", jac, 4 * n)):
+        if t is not None:
+            _tensor(t, name, dtype=a_c.dtype, numel=k, cuda=False)
+    _cuda(a_c=a_c, a_p=a_p, f_h=f_h, f_l=f_l, jac=jac)
     _check(lib().dect_forward_model(spec, a_c.numel(), _dtype(a_c), _ptr(a_c), _ptr(a_p), _ptr(f_h), _ptr(f_l),
                                     _ptr(jac), _stream(stream)))
 
 
 def forward_model_vjp(spec, a_c, a_p, g_h, g_l, grad_c, grad_p, stream=None):
-    """Transpose of the forward model's Jacobian applied to (g_h, g_l)."""
+    """Transpose of the forward model's Jacobian applied to (g_h, g_l); CUDA arrays of one dtype."""
+    import torch
+
+    n = _tensor(a_c, "a_c", dtype=(torch.float32, torch.float64), cuda=False).numel()
+    for name, t in (("a_p", a_p), ("g_h", g_h), ("g_l", g_l), ("grad_c", grad_c), ("grad_p", grad_p)):
+        _tensor(t, name, dtype=a_c.dtype, numel=n, cuda=False)
+    _cuda(a_c=a_c, a_p=a_p, g_h=g_h, g_l=g_l, grad_c=grad_c, grad_p=grad_p)
     _check(lib().dect_forward_model_vjp(spec, a_c.numel(), _dtype(a_c), _ptr(a_c), _ptr(a_p), _ptr(g_h), _ptr(g_l),
                                         _ptr(grad_c), _ptr(grad_p), _stream(stream)))
 
@@ -289,12 +401,25 @@ def admm_destroy(h):
     lib().dect_admm_destroy(h)
 
 
-def admm_set_data(h, slice_index, m_h, m_l, w_h, w_l, x0=None, stream=None):
+def admm_set_data(h, slice_index, m_h, m_l, w_h, w_l, x0=None, stream=None, n_rays=None, n_pix=None):
+    """Measurements float32 [n_views][n_bins] and an optional start image float32 [2][ny][nx], host or
+    device (sizes checked when n_rays / n_pix are given)."""
+    import torch
+
+    n_rays = _tensor(m_h, "m_h", dtype=torch.float32, numel=n_rays, cuda=False).numel()
+    for name, t in (("m_l", m_l), ("w_h", w_h), ("w_l", w_l)):
+        _tensor(t, name, dtype=torch.float32, numel=n_rays, cuda=False)
+    if x0 is not None:
+        _tensor(x0, "x0", dtype=torch.float32, numel=None if n_pix is None else 2 * n_pix, cuda=False)
     _check(lib().dect_admm_set_data(h, slice_index, _ptr(m_h), _ptr(m_l), _ptr(w_h), _ptr(w_l), _ptr(x0),
                                     _stream(stream)))
 
 
-def admm_set_truth(h, slice_index, truth, stream=None):
+def admm_set_truth(h, slice_index, truth, stream=None, n_pix=None):
+    """Ground truth float32 [2][ny][nx], host or device."""
+    import torch
+
+    _tensor(truth, "truth", dtype=torch.float32, numel=None if n_pix is None else 2 * n_pix, cuda=False)
     _check(lib().dect_admm_set_truth(h, slice_index, _ptr(truth), _stream(stream)))
 
 

@@ -18,16 +18,16 @@ class Geometry:
         squeeze = x.dim() == 2
         x = x.reshape(-1, self.ny, self.nx)
         if out is None:
-            out = torch.empty((x.shape[0], self.n_views, self.n_bins), device=x.device, dtype=torch.float32)
-        dect.project(self.handle, x, out, stream)
+            out = torch.empty((x.shape[0], self.n_views, self.n_bins), device=x.device, dtype=x.dtype)
+        dect.project(self, x, out, stream)
         return out[0] if squeeze else out
 
     def backproject(self, s: torch.Tensor, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
         squeeze = s.dim() == 2
         s = s.reshape(-1, self.n_views, self.n_bins)
         if out is None:
-            out = torch.empty((s.shape[0], self.ny, self.nx), device=s.device, dtype=torch.float32)
-        dect.backproject(self.handle, s, out, stream)
+            out = torch.empty((s.shape[0], self.ny, self.nx), device=s.device, dtype=s.dtype)
+        dect.backproject(self, s, out, stream)
         return out[0] if squeeze else out
 
     def fbp(self, s: torch.Tensor, out: torch.Tensor | None = None, clamp_nonneg: bool = False,
@@ -37,7 +37,7 @@ class Geometry:
         s = s.reshape(-1, self.n_views, self.n_bins)
         if out is None:
             out = torch.empty((s.shape[0], self.ny, self.nx), device=s.device, dtype=torch.float32)
-        dect.fbp(self.handle, s, out, clamp_nonneg, stream)
+        dect.fbp(self, s, out, clamp_nonneg, stream)
         return out[0] if squeeze else out
 
     def __del__(self):
@@ -51,7 +51,7 @@ def cdm_fbp(geo: Geometry, spec: "Spectra", m_h, m_l, w_h, w_l, iters: int = 20,
     """The CDM-FBP comparison method: [2, ny, nx] (Compton, PE). work, if given, is a float32 device
     tensor of 4 V Nb elements and holds the per-ray line integrals (a_c, a_p) on return."""
     out = torch.empty((2, geo.ny, geo.nx), device=m_h.device, dtype=torch.float32)
-    dect.cdm_fbp(geo.handle, spec.handle, m_h, m_l, w_h, w_l, iters, out, work, stream)
+    dect.cdm_fbp(geo, spec.handle, m_h, m_l, w_h, w_l, iters, out, work, stream)
     return out
 
 
@@ -86,10 +86,13 @@ class Solver:
         self.handle = dect.admm_create([g.handle for g in self.geoms], spectra.handle, self.params)
 
     def set_data(self, b, m_h, m_l, w_h, w_l, x0=None, stream=None):
-        dect.admm_set_data(self.handle, b, m_h, m_l, w_h, w_l, x0, stream)
+        g = self.geoms[b]
+        dect.admm_set_data(self.handle, b, m_h, m_l, w_h, w_l, x0, stream, n_rays=g.n_views * g.n_bins,
+                           n_pix=g.nx * g.ny)
 
     def set_truth(self, b, truth, stream=None):
-        dect.admm_set_truth(self.handle, b, truth, stream)
+        g = self.geoms[b]
+        dect.admm_set_truth(self.handle, b, truth, stream, n_pix=g.nx * g.ny)
 
     def step(self, iters=1, stream=None):
         dect.admm_step(self.handle, iters, stream)
