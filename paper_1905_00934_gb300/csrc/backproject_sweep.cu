@@ -46,7 +46,13 @@ namespace dect {
 // fan workload: 72 % of a staged ray's lanes sample the band at 32 rows, 83 % at 64), at the price of
 // twice the accumulator per warp. Both shapes evaluate every sample once, in the same order per
 // pixel within a view group, and the autotuner of the solver picks one by timing.
-constexpr int kSwUnroll = 8;
+#ifndef DECT_SW_UNROLL
+#define DECT_SW_UNROLL 8
+#endif
+constexpr int kSwUnroll = DECT_SW_UNROLL;  // rays per block of the sweep's inner loop (a multiple of 4)
+// 4 and 8 give the same bits (both measured); 16 ran as fast but its images drifted from theirs within a
+// few iterations, for a reason not found, so it is not allowed.
+static_assert(kSwUnroll == 4 || kSwUnroll == 8, "rays per block: 4 or 8");
 
 // Drop the L2 lines that lie wholly inside [lo, hi) without writing them back (discard.global.L2,
 // 128-byte lines; their contents become undefined). The caller owns every byte of the range.
@@ -247,11 +253,15 @@ __global__ void __launch_bounds__(SweepShape<TILE>::kThreads) k_bp_sweep(
         for (int r0 = 0; r0 < nr; r0 += kSwUnroll) {
             int hh[kSwUnroll];
             float ff[kSwUnroll], wc[kSwUnroll], wp[kSwUnroll];
-            if constexpr (NCH == 2 && SG == 1) {  // w s_p of the block's rays: two broadcast 16-byte loads
-                const float4 p0 = *reinterpret_cast<const float4*>(&st_wp[w][r0]);
-                const float4 p1 = *reinterpret_cast<const float4*>(&st_wp[w][r0 + 4]);
-                wp[0] = p0.x; wp[1] = p0.y; wp[2] = p0.z; wp[3] = p0.w;
-                wp[4] = p1.x; wp[5] = p1.y; wp[6] = p1.z; wp[7] = p1.w;
+            if constexpr (NCH == 2 && SG == 1) {  // w s_p of the block's rays: broadcast 16-byte loads
+#pragma unroll
+                for (int v4 = 0; v4 < kSwUnroll / 4; ++v4) {
+                    const float4 p = *reinterpret_cast<const float4*>(&st_wp[w][r0 + 4 * v4]);
+                    wp[4 * v4] = p.x;
+                    wp[4 * v4 + 1] = p.y;
+                    wp[4 * v4 + 2] = p.z;
+                    wp[4 * v4 + 3] = p.w;
+                }
             }
 #pragma unroll
             for (int u = 0; u < kSwUnroll; ++u) {
