@@ -137,19 +137,19 @@ def joseph_weight_count(g) -> int:
     return total
 
 
+# the workload both arms of the bench line name (the reference arm times a bounded sample of it)
+WORKLOAD = "fan 512x512, 720 views x 1024 bins, 40 objects, I0 2e5, UDM1-PCG1 x 100 + init"
+
+# Shared-memory wavefronts per slice of the backprojector sweep on the same workload (ncu
+# l1tex__data_pipe_lsu_wavefronts_mem_shared.sum), keyed by (tile side, slices per CTA); the count
+# follows the samples and staged rays, not the view-group count. The SM serves one wavefront per clock.
+SWEEP_SMEM_WAVEFRONTS = {(32, 2): 8.01e7}
+
 # DRAM bytes (read + write) per launch of the backprojector sweep at the bench workload (8 slices),
 # keyed by the launch shape they were captured with (slices, view groups, tile side, cluster form,
 # slices per CTA, reduced form); from the counter captures in profiles/k_bp_sweep_512x720x1024.txt.
 # Reported only when the run uses one of these shapes.
-# Shared-memory wavefronts per slice of the backprojector sweep on the same workload (ncu
-# l1tex__data_pipe_lsu_wavefronts_mem_shared.sum), keyed by (tile side, slices per CTA); the count
-# follows the samples and staged rays, not the view-group count. The SM serves one wavefront per clock.
-# the workload both arms of the bench line name (the reference arm times a bounded sample of it)
-WORKLOAD = "fan 512x512, 720 views x 1024 bins, 40 objects, I0 2e5, UDM1-PCG1 x 100 + init"
-
-SWEEP_SMEM_WAVEFRONTS = {(32, 2): 8.54e7}
-
-SWEEP_TRAFFIC = {(8, 6, 32, 0, 2, 1): 56.6e6, (8, 8, 32, 0, 2, 1): 57.8e6}
+SWEEP_TRAFFIC = {(8, 6, 32, 0, 2, 1): 56.7e6}
 
 
 # ------------------------------------------------------------------------------------------------
