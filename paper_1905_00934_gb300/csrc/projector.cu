@@ -26,6 +26,7 @@
 #include "bp_epilogue.cuh"
 #include "prec.cuh"
 #include "ray_fixed.cuh"
+#include "f32x2.cuh"
 
 namespace dect {
 
@@ -245,6 +246,13 @@ __device__ __forceinline__ void trimmed_range(const int4 P, const GeomDev& g, in
     }
 }
 
+// One sample's interpolated {c, p} from the texel pair {c0, p0, c1, p1} at upper weight f, as a
+// packed pair: {fma(f, c1 - c0, c0), fma(f, p1 - p0, p0)}, each element rounded as in scalar code.
+__device__ __forceinline__ f32x2 lerp2(float f, const float4 v) {
+    const f32x2 lo = pack2(v.x, v.y);
+    return fma2(pack2(f, f), sub2(pack2(v.z, v.w), lo), lo);
+}
+
 // Sum over a ray's samples of the interpolated {c, p} (unweighted), with the warp stepping in lock
 // step: every lane visits the same sampled index t, from the warp's lowest first index to its highest
 // last one, so at each step the lanes (neighbouring rays) read neighbouring texels of one texture row
@@ -264,8 +272,9 @@ __device__ __forceinline__ float2 ray_sum_sync(const int4 P, bool valid, const G
     const bool any = lo <= hi;
     const int t0 = __reduce_min_sync(0xffffffffu, any ? lo : 0x7fffffff);
     const int t1 = __reduce_max_sync(0xffffffffu, any ? hi : -1);
-    float ac = 0.f, ap = 0.f;
-    if (t0 > t1) return make_float2(ac, ap);  // no lane of the warp samples the image (warp-uniform)
+    // {c, p} sums as one packed pair: each element's terms and order are those of two scalar sums
+    f32x2 acc = pack2(0.f, 0.f);
+    if (t0 > t1) return unpack2(acc);  // no lane of the warp samples the image (warp-uniform)
     // from here 0 <= t0 <= t1 < max(nx, ny): the bounds below cannot overflow
     const long long step = ray_step(P), q0 = ray_q0(P);
     int t = t0;
@@ -290,10 +299,7 @@ __device__ __forceinline__ float2 ray_sum_sync(const int4 P, bool valid, const G
         }
         rel += kProjBatch;
 #pragma unroll
-        for (int u = 0; u < kProjBatch; ++u) {
-            ac += fmaf(f[u], v[u].z - v[u].x, v[u].x);
-            ap += fmaf(f[u], v[u].w - v[u].y, v[u].y);
-        }
+        for (int u = 0; u < kProjBatch; ++u) acc = add2(acc, lerp2(f[u], v[u]));
     }
 #else
     for (; t <= t1 - (kProjBatch - 1); t += kProjBatch) {
@@ -309,20 +315,15 @@ __device__ __forceinline__ float2 ray_sum_sync(const int4 P, bool valid, const G
             f[u] = frac_of(qu);
         }
 #pragma unroll
-        for (int u = 0; u < kProjBatch; ++u) {
-            ac += fmaf(f[u], v[u].z - v[u].x, v[u].x);
-            ap += fmaf(f[u], v[u].w - v[u].y, v[u].y);
-        }
+        for (int u = 0; u < kProjBatch; ++u) acc = add2(acc, lerp2(f[u], v[u]));
     }
 #endif
     for (; t <= t1; ++t) {
         const long long q1 = q0 + (long long)t * step;
         const float4 v = ldtex(tex + ((t >= lo && t <= hi) ? t * ld + 2 + pos_floor(q1) : 0));
-        const float f = frac_of(q1);
-        ac += fmaf(f, v.z - v.x, v.x);
-        ap += fmaf(f, v.w - v.y, v.y);
+        acc = add2(acc, lerp2(frac_of(q1), v));
     }
-    return make_float2(ac, ap);
+    return unpack2(acc);
 }
 
 // A CTA takes a tile of V consecutive views x 32 consecutive bins, one warp per view: the rays of
@@ -361,9 +362,9 @@ __device__ __forceinline__ void ray_sum_group(const int4 P, bool valid, const Ge
     const bool any = lo <= hi;
     const int t0 = __reduce_min_sync(0xffffffffu, any ? lo : 0x7fffffff);
     const int t1 = __reduce_max_sync(0xffffffffu, any ? hi : -1);
-    float ac[G], ap[G];
+    f32x2 acc2[G];  // {c, p} sums per slice as packed pairs
 #pragma unroll
-    for (int k = 0; k < G; ++k) ac[k] = ap[k] = 0.f;
+    for (int k = 0; k < G; ++k) acc2[k] = pack2(0.f, 0.f);
     if (t0 <= t1) {  // some lane of the warp samples the image (warp-uniform)
         // from here 0 <= t0 <= t1 < max(nx, ny): the bounds below cannot overflow
         const long long step = ray_step(P), q0 = ray_q0(P);
@@ -388,10 +389,7 @@ __device__ __forceinline__ void ray_sum_group(const int4 P, bool valid, const Ge
 #pragma unroll
                 for (int u = 0; u < kProjBatch; ++u) v[u] = ldtex(tex[k] + idx[u]);
 #pragma unroll
-                for (int u = 0; u < kProjBatch; ++u) {
-                    ac[k] += fmaf(f[u], v[u].z - v[u].x, v[u].x);
-                    ap[k] += fmaf(f[u], v[u].w - v[u].y, v[u].y);
-                }
+                for (int u = 0; u < kProjBatch; ++u) acc2[k] = add2(acc2[k], lerp2(f[u], v[u]));
             }
         }
         for (; t <= t1; ++t) {
@@ -401,14 +399,12 @@ __device__ __forceinline__ void ray_sum_group(const int4 P, bool valid, const Ge
 #pragma unroll
             for (int k = 0; k < G; ++k) {
                 if (k >= count) break;
-                const float4 v = ldtex(tex[k] + i1);
-                ac[k] += fmaf(f, v.z - v.x, v.x);
-                ap[k] += fmaf(f, v.w - v.y, v.y);
+                acc2[k] = add2(acc2[k], lerp2(f, ldtex(tex[k] + i1)));
             }
         }
     }
 #pragma unroll
-    for (int k = 0; k < G; ++k) acc[k] = make_float2(ac[k], ap[k]);
+    for (int k = 0; k < G; ++k) acc[k] = unpack2(acc2[k]);
 }
 
 // One CTA per (geometry group, tile): group gi holds up to kProjGroup slices of one geometry (their
