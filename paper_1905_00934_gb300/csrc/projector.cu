@@ -199,9 +199,9 @@ __global__ void k_pack_planar(const float* __restrict__ in, int nch, int64_t n, 
 
 // Launch shape of the forward projector (compile-time; the defaults are the measured best on GB300):
 // samples whose texel loads are issued together per lane, views (warps) per CTA, the CTAs per SM the
-// register allocation must allow, slices of one geometry per CTA (1, 2 or 4), and whether positions
-// advance incrementally or are recomputed from the index at every sample (both give the same integers,
-// so the same results).
+// register allocation must allow, slices of one geometry per CTA (1, 2 or 4), and whether the
+// single-slice sum's positions advance incrementally or are recomputed from the index at every sample
+// (both give the same integers, so the same results; the grouped sum always steps incrementally).
 #ifndef DECT_PROJ_BATCH
 #define DECT_PROJ_BATCH 8
 #endif
@@ -372,15 +372,19 @@ __device__ __forceinline__ void ray_sum_group(const int4 P, bool valid, const Ge
 #pragma unroll
         for (int k = 0; k < G; ++k) tex[k] = ax ? tys[k] : txs[k];
         int t = t0;
+        // position and texel row of sample t, stepped exactly: q = q0 + t step, base = t ld + 2
+        long long q = q0 + (long long)t0 * step;
+        int base = t0 * ld + 2;
         for (; t <= t1 - (kProjBatch - 1); t += kProjBatch) {
             int idx[kProjBatch];
             float f[kProjBatch];
 #pragma unroll
             for (int u = 0; u < kProjBatch; ++u) {
                 const int tt = t + u;
-                const long long qu = q0 + (long long)tt * step;
-                idx[u] = (tt >= lo && tt <= hi) ? tt * ld + 2 + pos_floor(qu) : 0;  // texel 0: zero padding
-                f[u] = frac_of(qu);
+                idx[u] = (tt >= lo && tt <= hi) ? base + pos_floor(q) : 0;  // texel 0: zero padding
+                f[u] = frac_of(q);
+                q += step;
+                base += ld;
             }
 #pragma unroll
             for (int k = 0; k < G; ++k) {
@@ -392,10 +396,9 @@ __device__ __forceinline__ void ray_sum_group(const int4 P, bool valid, const Ge
                 for (int u = 0; u < kProjBatch; ++u) acc2[k] = add2(acc2[k], lerp2(f[u], v[u]));
             }
         }
-        for (; t <= t1; ++t) {
-            const long long q1 = q0 + (long long)t * step;
-            const int i1 = (t >= lo && t <= hi) ? t * ld + 2 + pos_floor(q1) : 0;
-            const float f = frac_of(q1);
+        for (; t <= t1; ++t, q += step, base += ld) {
+            const int i1 = (t >= lo && t <= hi) ? base + pos_floor(q) : 0;
+            const float f = frac_of(q);
 #pragma unroll
             for (int k = 0; k < G; ++k) {
                 if (k >= count) break;

@@ -21,6 +21,7 @@
 #include "dect_internal.cuh"
 #include "prec.cuh"
 #include "reduce.cuh"
+#include "f32x2.cuh"
 
 namespace dect {
 
@@ -122,8 +123,26 @@ __device__ __forceinline__ void spectral_sums_jac(const float4* __restrict__ t1,
     for (int e0 = 0; e0 < sp.ne; e0 += 8) {
         float bh = 0.f, bl = 0.f;
         if (e0 + 8 <= sp.n_both) {
+            // both spectra: the sum pairs {b_h, b_l}, {s_hc, s_hp}, {s_lc, s_lp} advance as packed float32
+            // pairs, each sum taking bin_jac<3>'s terms in its order (the same bits, half the instructions)
+            f32x2 bhl = pack2(0.f, 0.f), sh2 = pack2(shc, shp), sl2 = pack2(slc, slp);
 #pragma unroll
-            for (int u = 0; u < 8; ++u) bin_jac<3>(t1, t2, e0 + u, ac, ap, bh, bl, shc, shp, slc, slp);
+            for (int u = 0; u < 8; ++u) {
+                const float4 a = t1[e0 + u];
+                const float4 b = t2[e0 + u];
+                const float t = exp2f(-fmaf(a.x, ac, a.y * ap));
+                const f32x2 tt = pack2(t, t);
+                bhl = fma2(pack2(a.z, a.w), tt, bhl);
+                sh2 = fma2(pack2(b.x, b.y), tt, sh2);
+                sl2 = fma2(pack2(b.z, b.w), tt, sl2);
+            }
+            const float2 x = unpack2(bhl), y = unpack2(sh2), z = unpack2(sl2);
+            bh = x.x;
+            bl = x.y;
+            shc = y.x;
+            shp = y.y;
+            slc = z.x;
+            slp = z.y;
         } else if (e0 >= sp.n_both && e0 + 8 <= sp.n_end) {
             if (sp.tail_high) {
 #pragma unroll
