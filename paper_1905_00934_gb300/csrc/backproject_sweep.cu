@@ -36,6 +36,7 @@
 #include "dect_internal.cuh"
 #include "prec.cuh"
 #include "ray_fixed.cuh"
+#include "f32x2.cuh"
 
 namespace dect {
 
@@ -108,7 +109,8 @@ __global__ void __launch_bounds__(SweepShape<TILE>::kThreads) k_bp_sweep(
     float4(*acc4)[Sh::kRows][32] = reinterpret_cast<float4(*)[Sh::kRows][32]>(sweep_smem);
     __shared__ int4 st_ray[Sh::kWarps][32];                 // {position lo, position hi, slope, w s_c}
     __shared__ __align__(16) float st_wp[Sh::kWarps][32];   // w s_p (SG = 1)
-    __shared__ float4 st_w2[SG == 2 ? Sh::kWarps : 1][32];   // {w s_p, w s_c, w s_p of the second slice} (SG = 2)
+    // SG = 2: {w s_c, w s_p, w s_c', w s_p'} of both slices, as two packed pairs for the accumulator update
+    __shared__ float4 st_w2[SG == 2 ? Sh::kWarps : 1][32];
     int local;
     const int unit = slice_of(map, blockIdx.x, local);
     int sl[SG];
@@ -226,7 +228,7 @@ __global__ void __launch_bounds__(SweepShape<TILE>::kThreads) k_bp_sweep(
             if constexpr (SG == 1)
                 st_wp[w][at] = wr * sv.y;
             else
-                st_w2[w][at] = make_float4(wr * sv.y, wr * sv1.x, wr * sv1.y, 0.f);
+                st_w2[w][at] = make_float4(wr * sv.x, wr * sv.y, wr * sv1.x, wr * sv1.y);
         }
         const int nr = (n + kSwUnroll - 1) / kSwUnroll * kSwUnroll;
         if (lane >= n && lane < nr) {  // null rays pad the stage to a multiple of kSwUnroll
@@ -272,25 +274,22 @@ __global__ void __launch_bounds__(SweepShape<TILE>::kThreads) k_bp_sweep(
                 wc[u] = __int_as_float(S.w);
             }
             if constexpr (SG == 2) {
-                // the second slice: its weights per ray; both slices' updates of a ray are independent
+                // both slices' weights per ray; a row's four sums {c, p, c', p'} advance as two packed
+                // float32 pairs (fma.rn.f32x2, each element rounded as fmaf)
 #pragma unroll
                 for (int u = 0; u < kSwUnroll; ++u) {
                     const float4 x = st_w2[w][r0 + u];
-                    const float wc1 = x.y, wp1 = x.z;
-                    wp[u] = x.x;
                     if ((unsigned)(hh[u] + 1) < (unsigned)(TILE + 1)) {
                         float4* a = &acc4[w][hh[u] + 1][lane];
-                        float4 x0 = a[0], x1 = a[32];
-                        x0.x = fmaf(1.0f - ff[u], wc[u], x0.x);
-                        x0.y = fmaf(1.0f - ff[u], wp[u], x0.y);
-                        x1.x = fmaf(ff[u], wc[u], x1.x);
-                        x1.y = fmaf(ff[u], wp[u], x1.y);
-                        x0.z = fmaf(1.0f - ff[u], wc1, x0.z);
-                        x0.w = fmaf(1.0f - ff[u], wp1, x0.w);
-                        x1.z = fmaf(ff[u], wc1, x1.z);
-                        x1.w = fmaf(ff[u], wp1, x1.w);
-                        a[0] = x0;
-                        a[32] = x1;
+                        const float4 x0 = a[0], x1 = a[32];
+                        const f32x2 g0 = pack2(1.0f - ff[u], 1.0f - ff[u]), g1 = pack2(ff[u], ff[u]);
+                        const f32x2 w01 = pack2(x.x, x.y), w23 = pack2(x.z, x.w);
+                        const float2 y00 = unpack2(fma2(g0, w01, pack2(x0.x, x0.y)));
+                        const float2 y01 = unpack2(fma2(g0, w23, pack2(x0.z, x0.w)));
+                        const float2 y10 = unpack2(fma2(g1, w01, pack2(x1.x, x1.y)));
+                        const float2 y11 = unpack2(fma2(g1, w23, pack2(x1.z, x1.w)));
+                        a[0] = make_float4(y00.x, y00.y, y01.x, y01.y);
+                        a[32] = make_float4(y10.x, y10.y, y11.x, y11.y);
                     }
                 }
                 continue;
