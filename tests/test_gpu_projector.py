@@ -112,3 +112,35 @@ def test_full_size_baggage_fan(cuda_dev):
     gotb = geo.backproject(to_dev(y, cuda_dev)).cpu().numpy()
     refb = np.stack([oproj.backproject(g, y[ch]) for ch in range(2)])
     assert rel_l2(gotb, refb) <= TOL
+
+
+@pytest.mark.slow
+def test_largest_workload_geometry(cuda_dev):
+    # the largest workload's geometry (1024 x 1024 fan, 1440 views x 2048 bins): R and R^T through the
+    # single-slice entry points, and R through the batched solver, whose two slices of one geometry are
+    # projected by one CTA (the initial state of a solver given start images holds R x0)
+    from paper_1905_00934_gb300 import Geometry, Solver, Spectra, dect
+    from synth.spectra import SpectralTables
+
+    g = G.baggage_fan_geometry(1024, 1440, 2048)
+    geo = Geometry(g)
+    rng = np.random.default_rng(31)
+    x = rng.uniform(0.0, 1.0, size=(2, g.ny, g.nx)).astype(np.float32).astype(np.float64)
+    ref = np.stack([oproj.project(g, x[ch]) for ch in range(2)])
+    got = geo.project(to_dev(x, cuda_dev)).cpu().numpy()
+    assert rel_l2(got[0], ref[0]) <= TOL and rel_l2(got[1], ref[1]) <= TOL
+    y = rng.normal(size=(2, g.n_views, g.n_bins)).astype(np.float32).astype(np.float64)
+    refb = np.stack([oproj.backproject(g, y[ch]) for ch in range(2)])
+    gotb = geo.backproject(to_dev(y, cuda_dev)).cpu().numpy()
+    assert rel_l2(gotb[0], refb[0]) <= TOL and rel_l2(gotb[1], refb[1]) <= TOL
+
+    sol = Solver([geo, geo], Spectra.from_tables(SpectralTables(e_ref_kev=100.0)), proj_views=2)
+    zero = torch.zeros((g.n_views, g.n_bins), dtype=torch.float32, device=cuda_dev)
+    one = torch.ones_like(zero)
+    for b, img in enumerate((x, x[::-1].copy())):  # the second slice: the channels swapped
+        sol.set_data(b, zero, zero, one, one, to_dev(img, cuda_dev))
+    sol.reconstruct(0)
+    torch.cuda.synchronize()
+    for b, r in enumerate((ref, ref[::-1])):
+        rx = sol.get(b, dect.RX).cpu().numpy()
+        assert rel_l2(rx[0], r[0]) <= TOL and rel_l2(rx[1], r[1]) <= TOL, b
