@@ -655,8 +655,10 @@ static void free_admm(dect_admm* A) {
     delete A;
 }
 
-static cudaError_t upload_map(MapBuf& m) {
-    cudaError_t e = dalloc(&m.d, m.h.size());
+// Device copy of a block map; capacity (entries) may exceed the current prefix when the map is later
+// rewritten for another layout (the sweep's one-slice and slice-pair layouts).
+static cudaError_t upload_map(MapBuf& m, size_t capacity = 0) {
+    cudaError_t e = dalloc(&m.d, std::max(m.h.size(), capacity));
     if (e != cudaSuccess) return e;
     m.total = m.h.back();
     return cudaMemcpy(m.d, m.h.data(), sizeof(int) * m.h.size(), cudaMemcpyHostToDevice);
@@ -1639,9 +1641,12 @@ extern "C" dect_status dect_admm_create(dect_geom* const* geoms, int32_t B, cons
     if (e == cudaSuccess && A->prec != PREC_F64) e = dalloc(&A->bp_partial, (size_t)A->sweep_C * A->n_img);
     if (e == cudaSuccess && A->prec != PREC_F64) e = dalloc(&A->tile_count, (size_t)A->n_tile_count);
     if (e == cudaSuccess && A->prec != PREC_F64) e = cudaMemset(A->tile_count, 0, sizeof(int) * A->n_tile_count);
+    // the sweep map holds one entry per unit (slice, or pair of slices of one geometry) plus one; the
+    // autotuner's cluster-form trials use the one-slice layout whatever the slices per CTA, so it is
+    // sized for B units
     for (MapBuf* m : {&A->rays, &A->pix, &A->tx, &A->ty, &A->rows, &A->cols, &A->sweep, &A->cols64, &A->ptile,
                       &A->prows, &A->pcols})
-        if (e == cudaSuccess) e = upload_map(*m);
+        if (e == cudaSuccess) e = upload_map(*m, m == &A->sweep ? (size_t)B + 1 : 0);
     if (e == cudaSuccess) e = dalloc(&A->d_groups, groups.size());
     if (e == cudaSuccess) e = dalloc(&A->d_sgroups, A->sgroups.size());
     if (e == cudaSuccess)

@@ -260,3 +260,25 @@ def test_uneven_64_slice_batch_full_size(cuda_dev):
             xs = batched.get(small, dect.X).cpu().numpy()
             e_c, e_p = rel_l2(xs[0], ref.x[0]), rel_l2(xs[1], ref.x[1])
             assert e_c <= 1e-4 and e_p <= 1e-4, (shapes[small], e_c, e_p)
+
+
+@pytest.mark.slow
+def test_stack_of_one_geometry_at_the_largest_size(cuda_dev):
+    # 16 slices of the largest workload's geometry (1024 x 1024 fan, 1440 views x 2048 bins) in one
+    # solver, one seeded slice's measurements on every slice: pairs of slices share projector and
+    # backprojector CTAs; sampled slices equal their single-slice solves bit for bit after the initial
+    # image and 2 iterations
+    from paper_1905_00934_gb300 import dect
+
+    c = quick_fan_case(0, 1024, 1440, 2048)
+    cases = [c] * 16
+    batched = _solver(cases, cuda_dev, [None] * 16, bp_view_groups=4, bp_slices=2)
+    batched.reconstruct(2)
+    torch.cuda.synchronize()
+    single = _solver([c], cuda_dev, [None], bp_view_groups=4, bp_slices=2)
+    single.reconstruct(2)
+    xs, a_s = single.get(0, dect.X).cpu().numpy(), single.get(0, dect.A).cpu().numpy()
+    assert np.all(np.isfinite(xs))
+    for b in (0, 5, 15):
+        assert np.array_equal(batched.get(b, dect.X).cpu().numpy(), xs), b
+        assert np.array_equal(batched.get(b, dect.A).cpu().numpy(), a_s), b
