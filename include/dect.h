@@ -314,12 +314,14 @@ typedef struct {
     int32_t bp_cluster;          /* the backprojector's view groups of a tile as one thread-block cluster that
                                     adds their accumulators on chip (distributed shared memory, in rank order)
                                     into one partial image, instead of C partial images through L2 / DRAM:
-                                    1 on (2 <= view groups <= 16), -1 off, 0 (default) timed by the autotuner
-                                    against the plain form. Both forms give the same bits. */
+                                    1 on (2 <= view groups <= 16; one slice per CTA, so bp_slices = 2 with
+                                    it is DECT_EINVAL), -1 off, 0 (default) timed by the autotuner against
+                                    the plain form. Both forms give the same bits. */
     int32_t bp_slices;           /* slices per backprojector CTA: 2 backprojects the same rays into two
                                     consecutive slices of one geometry at once (shared staging and sample
                                     positions, one accumulator per slice; UDM-PCG scheme), 1 one slice,
-                                    0 (default) timed by the autotuner. Same bits either way. */
+                                    0 (default) timed by the autotuner (one slice when bp_cluster = 1).
+                                    Same bits either way. */
     int32_t bp_reduce;           /* plain (non-cluster) backprojector with C >= 2 view groups: the last CTA of a
                                     tile to finish sums the tile's C partial images (in view-group order, the
                                     finalize pass's order) into partial image 0 while they are in L2 and drops

@@ -1403,6 +1403,9 @@ extern "C" dect_status dect_admm_create(dect_geom* const* geoms, int32_t B, cons
         DECT_FAIL(DECT_EINVAL, "dect_admm_create: bp_cluster must be -1 (off), 0 (autotuned) or 1 (on)");
     if (P->bp_slices < 0 || P->bp_slices > 2)
         DECT_FAIL(DECT_EINVAL, "dect_admm_create: bp_slices must be 0 (autotuned), 1 or 2");
+    if (P->bp_cluster == 1 && P->bp_slices == 2)
+        DECT_FAIL(DECT_EINVAL, "dect_admm_create: bp_cluster = 1 (the cluster form takes one slice per CTA) "
+                               "excludes bp_slices = 2");
     if (P->bp_reduce < -1 || P->bp_reduce > 1)
         DECT_FAIL(DECT_EINVAL, "dect_admm_create: bp_reduce must be -1 (off), 0 (default: on) or 1 (on)");
     if (P->proj_views != 0 && P->proj_views != 2 && P->proj_views != 4 && P->proj_views != 8)
@@ -1478,7 +1481,7 @@ extern "C" dect_status dect_admm_create(dect_geom* const* geoms, int32_t B, cons
         }
         const bool sg_ok = pairs && P->scheme == DECT_SCHEME_UDM_PCG && P->storage != DECT_STORE_F64;
         if (P->bp_slices == 2 && sg_ok) A->sg_cands = {2};
-        else if (P->bp_slices == 0 && sg_ok) A->sg_cands = {1, 2};
+        else if (P->bp_slices == 0 && sg_ok && P->bp_cluster != 1) A->sg_cands = {1, 2};
         else A->sg_cands = {1};
         A->sweep_sg = A->sg_cands.size() == 1 ? A->sg_cands[0] : 1;
         if (P->storage == DECT_STORE_F64) {
@@ -1671,7 +1674,7 @@ extern "C" dect_status dect_admm_create(dect_geom* const* geoms, int32_t B, cons
          (A->cluster_cands.size() > 1 && tune[0] >= 2)))
         e = autotune_sweep(A, tune, tune_tiles);
     else if (A->prec != PREC_F64)
-        A->sweep_cluster = P->bp_cluster > 0 && A->sweep_C >= 2 && A->sweep_C <= 16;
+        A->sweep_cluster = P->bp_cluster > 0 && A->sweep_sg == 1 && A->sweep_C >= 2 && A->sweep_C <= 16;
     if (e != cudaSuccess) {
         dect::set_error(std::string("dect_admm_create (backprojector autotuning): ") + cudaGetErrorString(e));
         free_admm(A);

@@ -71,3 +71,17 @@ def test_params_default_are_the_papers():
     assert (p.m_udm, p.n_pcg) == (1, 1)
     assert (p.storage, p.udm_f64) == (dect.STORE_F32, 0)
     assert (p.objective_every, p.bp_tile, p.bp_cluster, p.bp_slices, p.bp_reduce, p.proj_views) == (0,) * 6
+
+
+def test_cluster_form_with_two_slices_per_cta_is_refused():
+    # the cluster form takes one slice per CTA: asking for both is refused with the other parameter
+    # checks, before any handle is used (the handles here are placeholders that are never read)
+    from paper_1905_00934_gb300 import dect
+
+    dummy = ctypes.create_string_buffer(4096)
+    geoms = (ctypes.c_void_p * 1)(ctypes.addressof(dummy))
+    h = ctypes.c_void_p()
+    p = dect.params_default(bp_cluster=1, bp_slices=2)
+    assert dect.lib().dect_admm_create(ctypes.cast(geoms, ctypes.c_void_p), 1, ctypes.addressof(dummy),
+                                       ctypes.byref(p), ctypes.byref(h)) == dect.EINVAL
+    assert b"bp_slices" in dect.lib().dect_last_error()
