@@ -382,6 +382,12 @@ def forward_model_vjp(spec, a_c, a_p, g_h, g_l, grad_c, grad_p, stream=None):
 # ---- ADMM solver ----------------------------------------------------------------------------------
 
 def params_default(**kw) -> Params:
+    """The library's defaults (the paper's parameters), with the given fields replaced; an unknown
+    field name raises TypeError instead of being dropped."""
+    fields = {f[0] for f in Params._fields_}
+    unknown = sorted(set(kw) - fields)
+    if unknown:
+        raise TypeError(f"unknown solver parameter(s) {unknown}; the fields are {sorted(fields)}")
     p = Params()
     lib().dect_params_default(ctypes.byref(p))
     for k, v in kw.items():

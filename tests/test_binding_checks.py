@@ -81,3 +81,9 @@ def test_cdm_fbp_is_sized():
 def test_solver_data_sizes_follow_the_first_array():
     with pytest.raises(ValueError):
         dect.admm_set_data(None, 0, z(35), z(35), z(36), z(35))
+
+
+def test_unknown_solver_parameters_are_refused():
+    with pytest.raises(TypeError):
+        dect.params_default(bp_view_group=4)  # a misspelt field would otherwise be dropped
+    assert dect.params_default(bp_view_groups=4).bp_view_groups == 4
