@@ -149,7 +149,7 @@ SWEEP_SMEM_WAVEFRONTS = {(32, 2): 8.01e7}
 # keyed by the launch shape they were captured with (slices, view groups, tile side, cluster form,
 # slices per CTA, reduced form); from the counter captures in profiles/k_bp_sweep_512x720x1024.txt.
 # Reported only when the run uses one of these shapes.
-SWEEP_TRAFFIC = {(8, 6, 32, 0, 2, 1): 56.4e6}
+SWEEP_TRAFFIC = {(8, 6, 32, 0, 2, 1): 56.4e6, (8, 8, 32, 0, 2, 1): 57.8e6, (8, 10, 32, 0, 2, 1): 58.3e6}
 
 
 # ------------------------------------------------------------------------------------------------
