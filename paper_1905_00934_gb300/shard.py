@@ -28,11 +28,25 @@ def _fits(costs: Sequence[float], parts: int, cap: float) -> bool:
     return used <= parts
 
 
+def _greedy(costs: Sequence[float], cap: float) -> list[tuple[int, int]]:
+    """Contiguous ranges filled in order up to `cap` each (the rule _fits counts)."""
+    ranges, start, load = [], 0, 0.0
+    for i, c in enumerate(costs):
+        if load + c > cap and i > start:
+            ranges.append((start, i))
+            start, load = i, 0.0
+        load += c
+    ranges.append((start, len(costs)))
+    return ranges
+
+
 def partition(costs: Sequence[float], parts: int) -> list[tuple[int, int]]:
     """Splits slices 0..n-1 into `parts` contiguous ranges [lo, hi) minimising the largest range cost.
 
-    Exact over the candidate capacities (the sums of contiguous runs); ranges may be empty when there
-    are fewer slices than parts.
+    Exact: feasibility is monotone in the capacity, so bisection over doubles finds the smallest
+    feasible capacity to the last bit; the greedy ranges at that capacity have the optimal largest
+    cost (a run sum, and no run sum lies between the optimum and that capacity). O(n) per step,
+    about 64 steps. Ranges may be empty when there are fewer slices than parts.
     """
     if parts < 1:
         raise ValueError("parts must be >= 1")
@@ -41,27 +55,23 @@ def partition(costs: Sequence[float], parts: int) -> list[tuple[int, int]]:
         raise ValueError("costs must be >= 0")
     if n == 0:
         return [(0, 0)] * parts
-    # the optimal bottleneck is the sum of some contiguous run: bisect over the sorted run sums
-    prefix = [0.0]
+    # the bounds: the largest slice (may be infeasible) and the total, added in order as _fits adds
+    # (Python's sum() of floats is compensated and can land one ulp below that running total)
+    total = 0.0
     for c in costs:
-        prefix.append(prefix[-1] + c)
-    cands = sorted({prefix[j] - prefix[i] for i in range(n) for j in range(i + 1, n + 1)})
-    lo, hi = 0, len(cands) - 1
-    while lo < hi:
-        mid = (lo + hi) // 2
-        if _fits(costs, parts, cands[mid]):
+        total += c
+    lo, hi = max(costs), total
+    if _fits(costs, parts, lo):
+        hi = lo
+    while True:
+        mid = lo + (hi - lo) / 2
+        if mid <= lo or mid >= hi:
+            break
+        if _fits(costs, parts, mid):
             hi = mid
         else:
-            lo = mid + 1
-    cap = cands[lo]
-    # greedy fill at the optimal capacity, then pad with empty ranges
-    ranges, start, load = [], 0, 0.0
-    for i, c in enumerate(costs):
-        if load + c > cap and i > start:
-            ranges.append((start, i))
-            start, load = i, 0.0
-        load += c
-    ranges.append((start, n))
+            lo = mid
+    ranges = _greedy(costs, hi)
     while len(ranges) < parts:
         ranges.append((n, n))
     return ranges

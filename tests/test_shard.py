@@ -86,3 +86,35 @@ def test_two_ranks_gloo_disjoint_cover_and_max_time():
         assert slowest == 11.0                                    # max over ranks
     loads = [sum(costs[s] for s in part) for part in res[0][0]]
     assert max(loads) == pytest.approx(_brute(costs, ws))
+
+
+def _run_sum(a):
+    t = 0.0
+    for c in a:
+        t += c
+    return t
+
+
+def test_partition_is_exact_where_run_sums_round():
+    # a candidate cap formed as a difference of prefix sums can fall one ulp below the running sum
+    # that the fill compares with; the partition must still reach the optimum (here 4e6 + the tail)
+    costs = [4e6, 4e6, 0.0, 3.5, 6.074379962852603, 7.0, 0.0, 0.0, 9.391491627785106]
+    r = shard.partition(costs, 2)
+    assert r == [(0, 1), (1, 9)]
+    # one part: the whole batch, even where Python's compensated sum() differs from the running total
+    costs = [0.0, 4e6, 7.0, 2.0, 3.5, 1.7467058960990223, 4e6, 3.5, 7.0, 2e6, 2.0, 9.206200381334538, 2.0] * 3
+    assert shard.partition(costs, 1) == [(0, len(costs))]
+
+
+def test_partition_of_the_largest_batch_is_fast_and_balanced():
+    import random
+    import time
+
+    rnd = random.Random(3)
+    costs = [rnd.uniform(1.0, 100.0) for _ in range(4096)]  # the solver's largest batch
+    t0 = time.perf_counter()
+    r = shard.partition(costs, 8)
+    assert time.perf_counter() - t0 < 2.0
+    assert len(r) == 8 and r[0][0] == 0 and r[-1][1] == 4096
+    worst = max(_run_sum(costs[lo:hi]) for lo, hi in r)
+    assert worst <= _run_sum(costs) / 8 + max(costs)  # within one slice of the even share
